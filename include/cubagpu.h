@@ -1,0 +1,162 @@
+/*
+ * cubagpu.h -- C ABI of the GB300 (sm_103a) Vegas sampling library.
+ *
+ * The library implements the sampling hot path of Cuba's integrators as
+ * described in "Concurrent Cuba" (T. Hahn): the routine that samples n
+ * points for an integrator (DoSample, Sect. 2.1), driven by Vegas, whose
+ * argument list (ndim, ncomp, integrand, userdata, nvec, epsrel, epsabs,
+ * flags, seed, mineval, maxeval, nstart, nincrease, nbatch, ..., neval,
+ * fail, integral, error, prob) is given in Sect. 3.2.2.  The paper leaves
+ * the Vegas algorithm itself to the Cuba manual; this library follows
+ * Lepage (1978) for the importance grid, Sobol (1967) with the Gray-code
+ * order of Antonov and Saleev (1979) for the points, and Genz (1984) for
+ * the built-in test integrands.
+ *
+ * Conventions for every call:
+ *   - Return value: CV_OK (0) or a negative CV_E* code; cv_strerror() names
+ *     it and cv_last_error() gives the context's last message.
+ *   - "_dev" pointers are device memory the caller owns (for example from
+ *     torch); every other pointer is host memory.  Device work is enqueued
+ *     on the context's stream; calls that return host results synchronise
+ *     that stream first.
+ *   - Arrays are C order.  A grid is edges[ndim][nbins+1] (double), a
+ *     histogram hist[ndim][nbins] (double), coordinates Y[ndim][n].
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef CUBAGPU_H
+#define CUBAGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- limits */
+#define CV_MAX_DIM 32          /* dimensions of the Sobol table            */
+#define CV_MAX_COMP 4          /* integrand components                     */
+#define CV_MIN_BINS 2
+#define CV_MAX_BINS 256        /* grid bins per axis                       */
+#define CV_INDEX_LIMIT (1ull << 52) /* Sobol indices must stay below this  */
+
+/* ---------------------------------------------------------------- errors */
+#define CV_OK 0
+#define CV_EINVAL (-1)         /* an argument is out of range              */
+#define CV_ENOMEM (-2)         /* device or host allocation failed         */
+#define CV_ECUDA (-3)          /* a CUDA call failed                       */
+#define CV_EABORT (-4)         /* the integrand returned -999              */
+#define CV_ETIMEOUT (-5)       /* a bounded wait gave up                   */
+#define CV_EADMIT (-6)         /* admission refused (memory budget)        */
+#define CV_EBUSY (-7)          /* no free slot                             */
+#define CV_ENOTFOUND (-8)      /* unknown request id                       */
+
+/* ------------------------------------------------- built-in integrands */
+/* Genz (1984) test families over [0,1]^ndim with parameters a_i > 0 and
+ * u_i in [0,1]:
+ *   CV_OSCILLATORY    cos(2 pi u_1 + sum a_i x_i)
+ *   CV_PRODUCT_PEAK   prod (a_i^-2 + (x_i - u_i)^2)^-1
+ *   CV_CORNER_PEAK    (1 + sum a_i x_i)^-(ndim+1)
+ *   CV_GAUSSIAN       exp(-sum a_i^2 (x_i - u_i)^2)
+ *   CV_C0             exp(-sum a_i |x_i - u_i|)
+ *   CV_DISCONTINUOUS  0 if x_1 > u_1 or x_2 > u_2, else exp(sum a_i x_i)
+ *   CV_CONST          1 (for exact checks)                                */
+#define CV_OSCILLATORY 0
+#define CV_PRODUCT_PEAK 1
+#define CV_CORNER_PEAK 2
+#define CV_GAUSSIAN 3
+#define CV_C0 4
+#define CV_DISCONTINUOUS 5
+#define CV_CONST 6
+#define CV_NUM_FAMILIES 7
+
+/* ------------------------------------------------------------------ flags */
+/* bits 0-1: verbosity (as Cuba's flags word).  CV_FP64 selects the plain
+ * FP64 path (Sobol coordinate with 52 fraction bits, FP64 map, integrand and
+ * sums); without it the point, map and integrand run in FP32 (23 fraction
+ * bits) with Kahan-compensated per-thread sums and FP64 block/global
+ * reduction, refinement and combination.  CV_PLAIN launches each kernel of
+ * each iteration separately and synchronises the host after every
+ * iteration (the one-launch-per-iteration comparator); without it the
+ * iterations are replayed from a captured CUDA graph and stop on the
+ * device. */
+#define CV_VERBOSE_MASK 0x3
+#define CV_FP64 0x100
+#define CV_PLAIN 0x200
+
+/* One integral: ncomp components of one ndim-dimensional Genz problem.
+ * a[c][i], u[c][i] are the parameters of component c (unused entries
+ * ignored).  Component 0 drives the grid refinement. */
+typedef struct {
+    int ndim;
+    int ncomp;
+    int family[CV_MAX_COMP];
+    double a[CV_MAX_COMP][CV_MAX_DIM];
+    double u[CV_MAX_COMP][CV_MAX_DIM];
+} cv_genz;
+
+typedef struct cv_ctx cv_ctx;
+
+/* Create a context on CUDA device `device`, enqueueing on `stream` (a
+ * cudaStream_t; NULL = the context creates its own non-blocking stream;
+ * pass cudaStreamLegacy, (void *)1, for the legacy default stream).
+ * The context owns the library's device memory; cv_destroy releases it
+ * (the analogue of cubawait for the spinning workers, Sect. 3.2.3). */
+int cv_create(cv_ctx **ctx, int device, void *stream);
+void cv_destroy(cv_ctx *ctx);
+const char *cv_strerror(int code);
+const char *cv_last_error(const cv_ctx *ctx);
+/* Wait for all work enqueued by the context. */
+int cv_synchronize(cv_ctx *ctx);
+
+/* ------------------------------------------------ DoSample building blocks */
+
+/* Sobol coordinates (Sect. 2: the master alone generates samples, each
+ * index used once): Y_dev[d*n + j] = X_d(start + j) >> (64 - bits), where
+ * X_d(i) is the 64-bit Sobol word of index i in Gray-code order.  bits is
+ * 23 (the FP32 path's coordinate) or 52 (the FP64 path's).  Requires
+ * 1 <= ndim <= CV_MAX_DIM, n >= 0, start + n <= CV_INDEX_LIMIT. */
+int cv_sobol(cv_ctx *ctx, int ndim, uint64_t start, int64_t n, int bits,
+             uint64_t *Y_dev);
+
+/* One sampling pass (DoSample, Sect. 2.1): the n points with Sobol indices
+ * start..start+n-1 mapped through the grid edges_dev, evaluated by the
+ * built-in integrand, ADDED to the accumulators:
+ *   S1_dev[c] += sum J f_c,  S2_dev[c] += sum (J f_c)^2,
+ *   hist_dev[d*nbins + k] += sum over points in bin k of axis d of (J f_0)^2
+ * with J = prod_d nbins (e_(k_d+1) - e_(k_d)).  flags: CV_FP64 or 0 (see
+ * above).  2 <= nbins <= CV_MAX_BINS, edges increasing from 0 to 1. */
+int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins,
+              const double *edges_dev, uint64_t start, int64_t n, int flags,
+              double *S1_dev, double *S2_dev, double *hist_dev);
+
+/* Grid refinement (Lepage 1978) in FP64, in place, per axis: smooth the
+ * histogram, compress with exponent 1.5, and rebin so that every new bin
+ * holds an equal share.  An axis whose histogram is all zero or not finite
+ * keeps its grid. */
+int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_dev,
+              double *edges_dev);
+
+/* ------------------------------------------------------------ Vegas */
+
+/* The Vegas call with the paper's argument list (Sect. 3.2.2) for a
+ * built-in integrand.  ndim/ncomp must equal g->ndim/g->ncomp.  Iteration
+ * j = 1, 2, ... samples n_j = nstart + (j-1) nincrease points, Sobol
+ * indices continuing from 1; the run stops with fail = 0 once
+ * neval >= mineval and every component has error <= max(epsabs,
+ * epsrel |integral|), or with fail = 1 when the next iteration would exceed
+ * maxeval.  nbatch is a performance hint only (it never changes results);
+ * seed is accepted for interface parity (the Sobol stream is unscrambled
+ * and seed-independent).  integral/error/prob receive ncomp values each;
+ * prob is the chi-square probability that the iteration results are not
+ * consistent (P((m-1)/2, chi2/2) over m iterations). */
+int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g,
+             double epsrel, double epsabs, int flags, int seed,
+             int64_t mineval, int64_t maxeval, int64_t nstart,
+             int64_t nincrease, int64_t nbatch, int nbins, int64_t *neval,
+             int *fail, double integral[], double error[], double prob[]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUBAGPU_H */

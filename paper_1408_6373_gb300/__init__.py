@@ -1,0 +1,197 @@
+"""Python binding of libcubagpu, the GB300 Vegas sampling library.
+
+Argument marshalling only: every step of the sampling path runs in the CUDA
+kernels of the shared library (include/cubagpu.h).  PyTorch tensors serve as
+device buffers; the library enqueues on the stream the context was created
+with (by default torch's current stream).  If the library has not been
+built, the calls raise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import LIB as LIB_PATH, build as build_library  # noqa: F401
+
+MAX_DIM = 32
+MAX_COMP = 4
+MIN_BINS = 2
+MAX_BINS = 256
+INDEX_LIMIT = 1 << 52
+
+OSCILLATORY, PRODUCT_PEAK, CORNER_PEAK, GAUSSIAN, C0, DISCONTINUOUS, CONST = range(7)
+FAMILIES = {"oscillatory": 0, "product_peak": 1, "corner_peak": 2, "gaussian": 3,
+            "c0": 4, "discontinuous": 5, "const": 6}
+
+FP64 = 0x100
+PLAIN = 0x200
+
+OK, EINVAL, ENOMEM, ECUDA, EABORT, ETIMEOUT, EADMIT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
+
+STREAM_LEGACY = 1  # cudaStreamLegacy
+
+
+class CubaGpuError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class Genz(ctypes.Structure):
+    """cv_genz: one integral of ncomp Genz components in ndim dimensions."""
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("ncomp", ctypes.c_int),
+        ("family", ctypes.c_int * MAX_COMP),
+        ("a", (ctypes.c_double * MAX_DIM) * MAX_COMP),
+        ("u", (ctypes.c_double * MAX_DIM) * MAX_COMP),
+    ]
+
+
+def genz(ndim: int, families, a, u) -> Genz:
+    """Build a cv_genz from family ids and [ncomp, ndim] parameter arrays."""
+    fams = [FAMILIES[f] if isinstance(f, str) else int(f) for f in families]
+    nc = len(fams)
+    a = np.broadcast_to(np.asarray(a, dtype=np.float64), (nc, ndim))
+    u = np.broadcast_to(np.asarray(u, dtype=np.float64), (nc, ndim))
+    g = Genz()
+    g.ndim, g.ncomp = ndim, nc
+    for c in range(nc):
+        g.family[c] = fams[c]
+        for d in range(ndim):
+            g.a[c][d] = float(a[c, d])
+            g.u[c][d] = float(u[c, d])
+    return g
+
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_d = ctypes.c_double
+
+_SIGNATURES = {
+    "cv_create": (_i, [_P(_vp), _i, _vp]),
+    "cv_destroy": (None, [_vp]),
+    "cv_strerror": (ctypes.c_char_p, [_i]),
+    "cv_last_error": (ctypes.c_char_p, [_vp]),
+    "cv_synchronize": (_i, [_vp]),
+    "cv_sobol": (_i, [_vp, _i, _u64, _i64, _i, _vp]),
+    "cv_sample": (_i, [_vp, _P(Genz), _i, _vp, _u64, _i64, _i, _vp, _vp, _vp]),
+    "cv_refine": (_i, [_vp, _i, _i, _vp, _vp]),
+    "cv_vegas": (_i, [_vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64, _i64,
+                      _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded shared library (raises if it was never built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with paper_1408_6373_gb300.build_library() "
+                "(nvcc, sm_103a); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def _ptr(t) -> int:
+    """Device address of a torch tensor (or an int)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+@dataclass
+class VegasResult:
+    neval: int
+    fail: int
+    integral: np.ndarray
+    error: np.ndarray
+    prob: np.ndarray
+
+
+class Context:
+    """cv_ctx: a device, a stream, and the library's device memory."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = lib()
+        if stream is None:
+            import torch
+            s = torch.cuda.current_stream(device).cuda_stream
+            stream = s if s else STREAM_LEGACY
+        self._h = ctypes.c_void_p()
+        rc = self._lib.cv_create(ctypes.byref(self._h), device, stream)
+        if rc != OK:
+            raise CubaGpuError(rc, "cv_create failed: " + self._lib.cv_strerror(rc).decode())
+
+    def close(self):
+        if self._h:
+            self._lib.cv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, what: str):
+        if rc != OK:
+            msg = self._lib.cv_last_error(self._h).decode()
+            raise CubaGpuError(rc, f"{what}: {msg}")
+
+    def synchronize(self):
+        self._check(self._lib.cv_synchronize(self._h), "cv_synchronize")
+
+    # ---------------------------------------------------- building blocks
+    def sobol(self, ndim: int, start: int, n: int, bits: int, out):
+        """Y[d, j] = X_d(start+j) >> (64-bits) into `out` (int64 [ndim, n])."""
+        self._check(self._lib.cv_sobol(self._h, ndim, start, n, bits, _ptr(out)), "cv_sobol")
+
+    def sample(self, g: Genz, nbins: int, edges, start: int, n: int, flags: int, S1, S2, H):
+        """DoSample: add sum J f, sum (J f)^2 and the f^2 histogram of n points."""
+        self._check(self._lib.cv_sample(self._h, ctypes.byref(g), nbins, _ptr(edges), start, n,
+                                        flags, _ptr(S1), _ptr(S2), _ptr(H)), "cv_sample")
+
+    def refine(self, ndim: int, nbins: int, H, edges):
+        self._check(self._lib.cv_refine(self._h, ndim, nbins, _ptr(H), _ptr(edges)), "cv_refine")
+
+    # ---------------------------------------------------- Vegas
+    def vegas(self, g: Genz, epsrel=0.0, epsabs=0.0, flags=0, seed=0, mineval=0,
+              maxeval=10 ** 6, nstart=10 ** 4, nincrease=0, nbatch=1000, nbins=64) -> VegasResult:
+        nc = g.ncomp
+        integral = np.zeros(nc)
+        error = np.zeros(nc)
+        prob = np.zeros(nc)
+        neval, fail = ctypes.c_int64(), ctypes.c_int()
+        rc = self._lib.cv_vegas(self._h, g.ndim, nc, ctypes.byref(g), epsrel, epsabs, flags, seed,
+                                mineval, maxeval, nstart, nincrease, nbatch, nbins,
+                                ctypes.byref(neval), ctypes.byref(fail),
+                                integral.ctypes.data, error.ctypes.data, prob.ctypes.data)
+        self._check(rc, "cv_vegas")
+        return VegasResult(neval.value, fail.value, integral, error, prob)

@@ -1,0 +1,543 @@
+// cv_api.cu -- the C ABI (include/cubagpu.h): contexts, argument checks,
+// launch configuration, and the Vegas iteration driver.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "cv_internal.cuh"
+
+#define CV_FOR_EACH_NDIM(X)                                                                  \
+    X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) \
+    X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30)    \
+    X(31) X(32)
+
+namespace cv {
+// explicit instantiations live in cv_sample_*.cu
+#define CV_EXTERN(D)                                                                        \
+    extern template cudaError_t launch_sample<D, float>(const SampleArgs<float> &, int,     \
+                                                        cudaStream_t);                      \
+    extern template cudaError_t launch_sample<D, double>(const SampleArgs<double> &, int,   \
+                                                         cudaStream_t);                     \
+    extern template cudaError_t sample_occupancy<D, float>(int, int *);                     \
+    extern template cudaError_t sample_occupancy<D, double>(int, int *);                    \
+    extern template cudaError_t launch_sobol<D, unsigned int>(                              \
+        unsigned long long, long long, int, unsigned long long *, int, cudaStream_t);       \
+    extern template cudaError_t launch_sobol<D, unsigned long long>(                        \
+        unsigned long long, long long, int, unsigned long long *, int, cudaStream_t);
+CV_FOR_EACH_NDIM(CV_EXTERN)
+#undef CV_EXTERN
+
+template <typename Real>
+static cudaError_t dispatch_sample(int ndim, const SampleArgs<Real> &a, int grid, cudaStream_t s)
+{
+    switch (ndim) {
+#define CV_CASE(D) case D: return launch_sample<D, Real>(a, grid, s);
+        CV_FOR_EACH_NDIM(CV_CASE)
+#undef CV_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename Real>
+static cudaError_t dispatch_occupancy(int ndim, int nbins, int *occ)
+{
+    switch (ndim) {
+#define CV_CASE(D) case D: return sample_occupancy<D, Real>(nbins, occ);
+        CV_FOR_EACH_NDIM(CV_CASE)
+#undef CV_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename W>
+static cudaError_t dispatch_sobol(int ndim, unsigned long long start, long long n, int bits,
+                                  unsigned long long *Y, int grid, cudaStream_t s)
+{
+    switch (ndim) {
+#define CV_CASE(D) case D: return launch_sobol<D, W>(start, n, bits, Y, grid, s);
+        CV_FOR_EACH_NDIM(CV_CASE)
+#undef CV_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace cv
+
+using namespace cv;
+
+struct cv_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // graph capture happens here
+    bool own_stream = false;
+    int sms = 0;
+    char msg[512] = {0};
+    // cached occupancy, [precision][ndim][nbins]; 0 = unknown
+    std::vector<int> occ;
+};
+
+static int fail_msg(cv_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->msg, sizeof(ctx->msg), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+static int cuda_fail(cv_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail_msg(ctx, CV_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CV_CUDA(ctx, call)                                                  \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);          \
+    } while (0)
+
+extern "C" const char *cv_strerror(int code)
+{
+    switch (code) {
+    case CV_OK: return "ok";
+    case CV_EINVAL: return "invalid argument";
+    case CV_ENOMEM: return "out of memory";
+    case CV_ECUDA: return "CUDA error";
+    case CV_EABORT: return "integrand aborted (-999)";
+    case CV_ETIMEOUT: return "timed out";
+    case CV_EADMIT: return "admission refused";
+    case CV_EBUSY: return "busy";
+    case CV_ENOTFOUND: return "not found";
+    }
+    return "unknown error";
+}
+
+extern "C" const char *cv_last_error(const cv_ctx *ctx) { return ctx ? ctx->msg : "no context"; }
+
+extern "C" int cv_create(cv_ctx **out, int device, void *stream)
+{
+    if (!out) return CV_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CV_ECUDA;
+    cv_ctx *ctx = new cv_ctx();
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete ctx;
+        return CV_ECUDA;
+    }
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return CV_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return CV_ECUDA;
+    }
+    ctx->occ.assign(2 * (CV_MAX_DIM + 1) * (CV_MAX_BINS + 1), 0);
+    *out = ctx;
+    return CV_OK;
+}
+
+extern "C" void cv_destroy(cv_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" int cv_synchronize(cv_ctx *ctx)
+{
+    if (!ctx) return CV_EINVAL;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CV_OK;
+}
+
+// ------------------------------------------------------------ helpers
+static int check_genz(cv_ctx *ctx, const cv_genz *g)
+{
+    if (!g) return fail_msg(ctx, CV_EINVAL, "null integrand description");
+    if (g->ndim < 1 || g->ndim > CV_MAX_DIM)
+        return fail_msg(ctx, CV_EINVAL, "ndim %d outside 1..%d", g->ndim, CV_MAX_DIM);
+    if (g->ncomp < 1 || g->ncomp > CV_MAX_COMP)
+        return fail_msg(ctx, CV_EINVAL, "ncomp %d outside 1..%d", g->ncomp, CV_MAX_COMP);
+    for (int c = 0; c < g->ncomp; ++c) {
+        if (g->family[c] < 0 || g->family[c] >= CV_NUM_FAMILIES)
+            return fail_msg(ctx, CV_EINVAL, "family %d of component %d unknown", g->family[c], c);
+        for (int d = 0; d < g->ndim; ++d)
+            if (!std::isfinite(g->a[c][d]) || !std::isfinite(g->u[c][d]))
+                return fail_msg(ctx, CV_EINVAL, "non-finite parameter a/u[%d][%d]", c, d);
+    }
+    return CV_OK;
+}
+
+static const double kTwoPi = 6.283185307179586476925286766559;
+
+template <typename Real>
+static void fill_params(const cv_genz *g, GenzParams<Real> *p)
+{
+    memset(p, 0, sizeof(*p));
+    p->ndim = g->ndim;
+    p->ncomp = g->ncomp;
+    const bool f32 = sizeof(Real) == 4;
+    for (int c = 0; c < g->ncomp; ++c) {
+        const int fam = g->family[c];
+        p->family[c] = fam;
+        for (int d = 0; d < g->ndim; ++d) {
+            const double a = g->a[c][d], u = g->u[c][d];
+            double p0 = 0.0, p1 = 0.0;
+            switch (fam) {
+            case CV_OSCILLATORY: p0 = f32 ? a / kTwoPi : a; break;
+            case CV_PRODUCT_PEAK: p0 = 1.0 / (a * a); p1 = u; break;
+            case CV_CORNER_PEAK: p0 = a; break;
+            case CV_GAUSSIAN:
+                if (f32) { p0 = a; p1 = a * u; }
+                else { p0 = a * a; p1 = u; }
+                break;
+            case CV_C0: p0 = a; p1 = u; break;
+            case CV_DISCONTINUOUS: p0 = a; p1 = u; break;
+            default: break;
+            }
+            p->p0[c][d] = (Real)p0;
+            p->p1[c][d] = (Real)p1;
+        }
+        if (fam == CV_OSCILLATORY) p->q0[c] = (Real)(f32 ? g->u[c][0] : 2.0 * 3.14159265358979323846264338327950288 * g->u[c][0]);
+    }
+}
+
+static int occupancy(cv_ctx *ctx, int ndim, int nbins, bool fp64, int *occ)
+{
+    int &slot = ctx->occ[((fp64 ? 1 : 0) * (CV_MAX_DIM + 1) + ndim) * (CV_MAX_BINS + 1) + nbins];
+    if (slot == 0) {
+        int o = 0;
+        cudaError_t e = fp64 ? dispatch_occupancy<double>(ndim, nbins, &o)
+                             : dispatch_occupancy<float>(ndim, nbins, &o);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy query");
+        slot = o > 0 ? o : 1;
+    }
+    *occ = slot;
+    return CV_OK;
+}
+
+// Blocks for a pass over n points: enough warps that every warp gets a few
+// dozen 32-point steps, at most one full wave of resident blocks.
+static int sample_grid(cv_ctx *ctx, int occ, long long n)
+{
+    const long long nblk = (n + 63) / 32;
+    long long want = (nblk + (long long)kWarpsPerBlock * 16 - 1) / ((long long)kWarpsPerBlock * 16);
+    const long long cap = (long long)ctx->sms * occ;
+    if (want > cap) want = cap;
+    if (want < 1) want = 1;
+    return (int)want;
+}
+
+template <typename Real>
+static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *edges,
+                       unsigned long long start, long long n, long long n_grid,
+                       double *S1, double *S2, double *H, const DevState *st)
+{
+    SampleArgs<Real> a;
+    memset(&a, 0, sizeof(a));
+    fill_params<Real>(g, &a.g);
+    a.nbins = nbins;
+    a.chunk_min = 4;
+    a.edges = edges;
+    a.S1 = S1;
+    a.S2 = S2;
+    a.H = H;
+    a.start = start;
+    a.n = n;
+    a.st = st;
+    int occ = 0, rc = occupancy(ctx, g->ndim, nbins, sizeof(Real) == 8, &occ);
+    if (rc) return rc;
+    const int grid = sample_grid(ctx, occ, n_grid);
+    cudaError_t e = dispatch_sample<Real>(g->ndim, a, grid, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sampling kernel launch");
+    return CV_OK;
+}
+
+// ------------------------------------------------------------ building blocks
+extern "C" int cv_sobol(cv_ctx *ctx, int ndim, uint64_t start, int64_t n, int bits,
+                        uint64_t *Y_dev)
+{
+    if (!ctx) return CV_EINVAL;
+    if (ndim < 1 || ndim > CV_MAX_DIM) return fail_msg(ctx, CV_EINVAL, "ndim %d outside 1..%d", ndim, CV_MAX_DIM);
+    if (bits != 23 && bits != 52) return fail_msg(ctx, CV_EINVAL, "bits must be 23 or 52");
+    if (n < 0 || start > CV_INDEX_LIMIT || (uint64_t)n > CV_INDEX_LIMIT - start)
+        return fail_msg(ctx, CV_EINVAL, "index range beyond 2^52");
+    if (n == 0) return CV_OK;
+    if (!Y_dev) return fail_msg(ctx, CV_EINVAL, "null output");
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    long long nblk = (n + 63) / 32;
+    long long grid = (nblk + kWarpsPerBlock * 4 - 1) / (kWarpsPerBlock * 4);
+    if (grid > (long long)ctx->sms * 8) grid = (long long)ctx->sms * 8;
+    cudaError_t e = bits == 23
+        ? dispatch_sobol<unsigned int>(ndim, start, n, bits, (unsigned long long *)Y_dev, (int)grid, ctx->stream)
+        : dispatch_sobol<unsigned long long>(ndim, start, n, bits, (unsigned long long *)Y_dev, (int)grid, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sobol kernel launch");
+    return CV_OK;
+}
+
+extern "C" int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins, const double *edges_dev,
+                         uint64_t start, int64_t n, int flags, double *S1_dev, double *S2_dev,
+                         double *hist_dev)
+{
+    if (!ctx) return CV_EINVAL;
+    int rc = check_genz(ctx, g);
+    if (rc) return rc;
+    if (nbins < CV_MIN_BINS || nbins > CV_MAX_BINS)
+        return fail_msg(ctx, CV_EINVAL, "nbins %d outside %d..%d", nbins, CV_MIN_BINS, CV_MAX_BINS);
+    if (n < 0 || start > CV_INDEX_LIMIT || (uint64_t)n > CV_INDEX_LIMIT - start)
+        return fail_msg(ctx, CV_EINVAL, "index range beyond 2^52");
+    if (n == 0) return CV_OK;
+    if (!edges_dev || !S1_dev || !S2_dev || !hist_dev) return fail_msg(ctx, CV_EINVAL, "null buffer");
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (flags & CV_FP64)
+        return launch_pass<double>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr);
+    return launch_pass<float>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr);
+}
+
+extern "C" int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_dev, double *edges_dev)
+{
+    if (!ctx) return CV_EINVAL;
+    if (ndim < 1 || ndim > CV_MAX_DIM) return fail_msg(ctx, CV_EINVAL, "ndim %d outside 1..%d", ndim, CV_MAX_DIM);
+    if (nbins < CV_MIN_BINS || nbins > CV_MAX_BINS) return fail_msg(ctx, CV_EINVAL, "nbins out of range");
+    if (!hist_dev || !edges_dev) return fail_msg(ctx, CV_EINVAL, "null buffer");
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaError_t e = launch_refine(ndim, nbins, const_cast<double *>(hist_dev), edges_dev, 0, nullptr, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refine kernel launch");
+    return CV_OK;
+}
+
+// ------------------------------------------------------------ Vegas driver
+namespace {
+
+struct Run {
+    cv_ctx *ctx = nullptr;
+    cv_genz g;
+    int nbins = 0;
+    int flags = 0;
+    double epsrel = 0, epsabs = 0;
+    long long mineval = 0, maxeval = 0, nstart = 0, nincrease = 0;
+    // device buffers (one allocation)
+    void *mem = nullptr;
+    DevState *st = nullptr;
+    double *edges = nullptr, *H = nullptr, *log_I = nullptr, *log_var = nullptr;
+    int jmax = 0;
+    long long nmax = 0;
+
+    ~Run() {
+        if (mem) cudaFree(mem);
+    }
+};
+
+// Number of iterations the sample budget allows, and the largest one.
+void plan(long long nstart, long long nincrease, long long maxeval, int *jmax, long long *nmax)
+{
+    long long sum = 0, nj = nstart;
+    int j = 0;
+    while (j < (1 << 20) && nj <= maxeval - sum) {
+        sum += nj;
+        *nmax = nj;
+        ++j;
+        nj += nincrease;
+    }
+    *jmax = j;
+}
+
+int run_setup(Run &r)
+{
+    cv_ctx *ctx = r.ctx;
+    const int ndim = r.g.ndim, N = r.nbins;
+    const size_t sz_state = (sizeof(DevState) + 255) & ~(size_t)255;
+    const size_t sz_edges = (((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255;
+    const size_t sz_H = (((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255;
+    const size_t sz_log = (size_t)kLogCap * CV_MAX_COMP * sizeof(double);
+    if (cudaMalloc(&r.mem, sz_state + sz_edges + sz_H + 2 * sz_log) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_msg(ctx, CV_ENOMEM, "device allocation of the Vegas state failed");
+    }
+    char *p = (char *)r.mem;
+    r.st = (DevState *)p;
+    r.edges = (double *)(p + sz_state);
+    r.H = (double *)(p + sz_state + sz_edges);
+    r.log_I = (double *)(p + sz_state + sz_edges + sz_H);
+    r.log_var = (double *)(p + sz_state + sz_edges + sz_H + sz_log);
+
+    DevState h;
+    memset(&h, 0, sizeof(h));
+    h.next_index = 1;  // index 0, the all-zero point, is skipped
+    h.n_cur = r.nstart;
+    std::vector<double> e((size_t)ndim * (N + 1));
+    for (int d = 0; d < ndim; ++d)
+        for (int k = 0; k <= N; ++k) e[(size_t)d * (N + 1) + k] = (double)k / (double)N;
+    CV_CUDA(ctx, cudaMemcpyAsync(r.st, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(r.edges, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemsetAsync(r.H, 0, (size_t)ndim * N * sizeof(double), ctx->stream));
+    // the host buffers above go out of scope: wait for the copies
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CV_OK;
+}
+
+// Enqueue one iteration (sample -> refine -> combine) on `s`.
+int enqueue_iteration(Run &r, cudaStream_t s)
+{
+    cv_ctx *ctx = r.ctx;
+    cudaStream_t keep = ctx->stream;
+    ctx->stream = s;
+    int rc = (r.flags & CV_FP64)
+        ? launch_pass<double>(ctx, &r.g, r.nbins, r.edges, 0, 0, r.nmax, r.st->S1, r.st->S2, r.H, r.st)
+        : launch_pass<float>(ctx, &r.g, r.nbins, r.edges, 0, 0, r.nmax, r.st->S1, r.st->S2, r.H, r.st);
+    ctx->stream = keep;
+    if (rc) return rc;
+    cudaError_t e = launch_refine(r.g.ndim, r.nbins, r.H, r.edges, 1, r.st, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refine kernel launch");
+    CombineArgs ca;
+    ca.st = r.st;
+    ca.ncomp = r.g.ncomp;
+    ca.epsrel = r.epsrel;
+    ca.epsabs = r.epsabs;
+    ca.mineval = r.mineval;
+    ca.maxeval = r.maxeval;
+    ca.nstart = r.nstart;
+    ca.nincrease = r.nincrease;
+    ca.log_I = r.log_I;
+    ca.log_var = r.log_var;
+    e = launch_combine(ca, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "combine kernel launch");
+    return CV_OK;
+}
+
+int read_stopped(Run &r, int *stopped)
+{
+    cv_ctx *ctx = r.ctx;
+    CV_CUDA(ctx, cudaMemcpyAsync(stopped, &r.st->stopped, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CV_OK;
+}
+
+int run_iterations(Run &r)
+{
+    cv_ctx *ctx = r.ctx;
+    int stopped = 0;
+    if (r.flags & CV_PLAIN) {
+        for (int j = 0; j < r.jmax && !stopped; ++j) {
+            int rc = enqueue_iteration(r, ctx->stream);
+            if (rc) return rc;
+            rc = read_stopped(r, &stopped);
+            if (rc) return rc;
+        }
+        return CV_OK;
+    }
+    // Graph mode: capture K iterations once, replay until the device says stop.
+    // (the occupancy query sets kernel attributes: do it before capturing)
+    int occ = 0;
+    int rc0 = occupancy(ctx, r.g.ndim, r.nbins, (r.flags & CV_FP64) != 0, &occ);
+    if (rc0) return rc0;
+    const int K = r.jmax < 32 ? r.jmax : 32;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CV_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = CV_OK;
+    for (int j = 0; j < K && rc == CV_OK; ++j) rc = enqueue_iteration(r, ctx->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+    for (int done = 0; done < r.jmax && !stopped; done += K) {
+        e = cudaGraphLaunch(exec, ctx->stream);
+        if (e != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            return cuda_fail(ctx, e, "graph launch");
+        }
+        if (done + K < r.jmax) {
+            rc = read_stopped(r, &stopped);
+            if (rc) break;
+        }
+    }
+    cudaGraphExecDestroy(exec);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, double epsrel,
+                        double epsabs, int flags, int seed, int64_t mineval, int64_t maxeval,
+                        int64_t nstart, int64_t nincrease, int64_t nbatch, int nbins,
+                        int64_t *neval, int *fail, double integral[], double error[],
+                        double prob[])
+{
+    (void)seed;
+    (void)nbatch;
+    if (!ctx) return CV_EINVAL;
+    int rc = check_genz(ctx, g);
+    if (rc) return rc;
+    if (g->ndim != ndim || g->ncomp != ncomp)
+        return fail_msg(ctx, CV_EINVAL, "ndim/ncomp disagree with the integrand description");
+    if (nbins < CV_MIN_BINS || nbins > CV_MAX_BINS)
+        return fail_msg(ctx, CV_EINVAL, "nbins %d outside %d..%d", nbins, CV_MIN_BINS, CV_MAX_BINS);
+    if (nstart < 2 || nincrease < 0 || maxeval < nstart || mineval < 0)
+        return fail_msg(ctx, CV_EINVAL, "need 2 <= nstart <= maxeval, nincrease >= 0, mineval >= 0");
+    if ((uint64_t)maxeval >= CV_INDEX_LIMIT)
+        return fail_msg(ctx, CV_EINVAL, "maxeval beyond the 2^52 Sobol index range");
+    if (!(epsrel >= 0) || !(epsabs >= 0)) return fail_msg(ctx, CV_EINVAL, "negative tolerance");
+    if (!neval || !fail || !integral || !error || !prob) return fail_msg(ctx, CV_EINVAL, "null output");
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+
+    Run r;
+    r.ctx = ctx;
+    r.g = *g;
+    r.nbins = nbins;
+    r.flags = flags;
+    r.epsrel = epsrel;
+    r.epsabs = epsabs;
+    r.mineval = mineval;
+    r.maxeval = maxeval;
+    r.nstart = nstart;
+    r.nincrease = nincrease;
+    plan(nstart, nincrease, maxeval, &r.jmax, &r.nmax);
+    rc = run_setup(r);
+    if (rc) return rc;
+    rc = run_iterations(r);
+    if (rc) return rc;
+    DevState h;
+    CV_CUDA(ctx, cudaMemcpyAsync(&h, r.st, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *neval = h.neval;
+    *fail = h.stopped ? h.fail : 1;  // iteration cap reached without a decision
+    for (int c = 0; c < ncomp; ++c) {
+        integral[c] = h.integral[c];
+        error[c] = h.error[c];
+        prob[c] = h.prob[c];
+    }
+    if (flags & CV_VERBOSE_MASK) {
+        std::vector<double> lI(kLogCap * CV_MAX_COMP), lV(kLogCap * CV_MAX_COMP);
+        cudaMemcpy(lI.data(), r.log_I, lI.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(lV.data(), r.log_var, lV.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        for (int j = 0; j < h.iter && j < kLogCap; ++j)
+            for (int c = 0; c < ncomp; ++c)
+                fprintf(stderr, "cv_vegas iteration %d comp %d: %.15g +- %.6g\n", j + 1, c,
+                        lI[j * CV_MAX_COMP + c], std::sqrt(std::fabs(lV[j * CV_MAX_COMP + c])));
+    }
+    return CV_OK;
+}

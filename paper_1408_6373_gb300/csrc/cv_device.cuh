@@ -1,0 +1,483 @@
+// cv_device.cuh -- device code of the fused sampling path (one pass of
+// DoSample, "Concurrent Cuba" Sect. 2.1, as Vegas drives it):
+//
+//   Sobol word X_d(i) (Gray-code order, skip-ahead + recurrence)
+//     -> y-coordinate with b fraction bits (b = 23 FP32 path, 52 FP64 path)
+//     -> Vegas grid map x_d = e_k + w_k frac, J = prod_d N w_k (Lepage 1978)
+//     -> Genz integrand f_c(x) (Genz 1984)
+//     -> per-thread sums of J f_c and (J f_c)^2 (Kahan in FP32)
+//     -> f^2 histogram H[d][k_d] += (J f_0)^2 in shared memory
+//     -> FP64 block/global reduction.
+//
+// Work decomposition.  The n indices of one pass are cut into aligned
+// blocks of 32 (one index per lane), and every warp owns a contiguous run of
+// such blocks (a "chunk").  Lane l of a warp handles index 32 q + l of block
+// q, so the 32 points a warp evaluates together form an aligned Gray-code
+// block: by the (0,1)-property of each Sobol coordinate they fall into 32
+// distinct 1/32-strata of every axis, which keeps the shared-memory
+// histogram nearly free of same-address conflicts.  Stepping from block q
+// to q+1 changes the Gray code of every lane's index by the same two bits,
+// 4 and 5 + ctz(q+1), so each coordinate advances with one warp-uniform
+// table lookup and one XOR.
+#pragma once
+
+#include "cv_internal.cuh"
+#include "sobol_dirs.h"
+
+namespace cv {
+
+// Direction words in constant memory (every access below is warp-uniform).
+static __constant__ unsigned long long c_V64[CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_V64_INIT;
+static __constant__ unsigned int c_V32[CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_V32_INIT;
+
+template <typename W> struct Dir;
+template <> struct Dir<unsigned long long> {
+    static __device__ __forceinline__ unsigned long long v(int d, int k) { return c_V64[d][k]; }
+};
+template <> struct Dir<unsigned int> {
+    static __device__ __forceinline__ unsigned int v(int d, int k) { return c_V32[d][k]; }
+};
+
+// Sobol words of index i = 32 q + lane for every dimension (skip-ahead):
+// X_d(i) = XOR over the set bits k of g(i) = i ^ (i >> 1) of V_d[k].  The
+// bits of g above bit 4 are g(q) and the same for the whole warp; bits 0-4
+// depend on the lane.
+template <int NDIM, typename W>
+__device__ __forceinline__ void sobol_skip(W (&X)[NDIM], unsigned long long q, int lane)
+{
+    const unsigned long long i = q * 32ull + (unsigned long long)lane;
+    const unsigned long long g = i ^ (i >> 1);
+    const unsigned glo = (unsigned)g & 31u;
+    unsigned long long ghi = g >> 5;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        W x = 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            x ^= ((glo >> k) & 1u) ? Dir<W>::v(d, k) : W(0);
+        X[d] = x;
+    }
+    while (ghi) {  // warp-uniform
+        const int k = __ffsll((long long)ghi) - 1 + 5;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d)
+            X[d] ^= Dir<W>::v(d, k);
+        ghi &= ghi - 1;
+    }
+}
+
+// Advance every lane from block q to block q+1:
+// g(32(q+1)+l) ^ g(32q+l) = 2^4 ^ 2^(5 + ctz(q+1)).
+template <int NDIM, typename W>
+__device__ __forceinline__ void sobol_step(W (&X)[NDIM], unsigned long long q)
+{
+    const int c = __ffsll((long long)(q + 1ull)) - 1;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d)
+        X[d] ^= Dir<W>::v(d, 4) ^ Dir<W>::v(d, 5 + c);
+}
+
+// ------------------------------------------------------------ precision traits
+template <typename Real> struct Prec;
+
+// FP32 path: 32-bit word = top half of the 64-bit word; y has 23 fraction
+// bits, so frac is exact as the mantissa of 1.frac minus 1.
+template <> struct Prec<float> {
+    using Word = unsigned int;
+    using Real2 = float2;
+    static constexpr int kBits = 23;
+    static __device__ __forceinline__ int bin(Word X, unsigned N, float *frac)
+    {
+        const unsigned t = (X >> 9) * N;  // Y * N < 2^31
+        *frac = __uint_as_float(0x3f800000u | (t & 0x7fffffu)) - 1.0f;
+        return (int)(t >> 23);
+    }
+    static __device__ __forceinline__ int bin_only(Word X, unsigned N)
+    {
+        return (int)(((X >> 9) * N) >> 23);
+    }
+    static __device__ __forceinline__ float2 stage(double e0, double e1)
+    {
+        return make_float2(__double2float_rn(e0), __double2float_rn(e1 - e0));
+    }
+};
+
+// FP64 path: 64-bit word, y has 52 fraction bits.
+template <> struct Prec<double> {
+    using Word = unsigned long long;
+    using Real2 = double2;
+    static constexpr int kBits = 52;
+    static __device__ __forceinline__ int bin(Word X, unsigned N, double *frac)
+    {
+        const unsigned long long t = (X >> 12) * (unsigned long long)N;  // < 2^60
+        *frac = __longlong_as_double((long long)(0x3ff0000000000000ull |
+                                                 (t & 0xfffffffffffffull))) - 1.0;
+        return (int)(t >> 52);
+    }
+    static __device__ __forceinline__ int bin_only(Word X, unsigned N)
+    {
+        return (int)(((X >> 12) * (unsigned long long)N) >> 52);
+    }
+    static __device__ __forceinline__ double2 stage(double e0, double e1)
+    {
+        return make_double2(e0, e1 - e0);
+    }
+};
+
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ------------------------------------------------------------ integrands
+template <int E>
+__device__ __forceinline__ float ipow(float r)
+{
+    // r^E by repeated squaring (E is a compile-time constant)
+    float acc = 1.0f, b = r;
+    int e = E;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        if (e & 1) acc *= b;
+        e >>= 1;
+        if (e) b *= b;
+    }
+    return acc;
+}
+
+// FP32 Genz evaluation of one component.
+template <int NDIM>
+__device__ __forceinline__ float genz_f32(int fam, const float *p0, const float *p1,
+                                          float q0, const float (&x)[NDIM])
+{
+    switch (fam) {
+    case CV_OSCILLATORY: {
+        float t = q0;  // phase in turns
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) t = __fmaf_rn(p0[d], x[d], t);
+        t -= rintf(t);
+        return __cosf(6.28318530717958647692f * t);
+    }
+    case CV_PRODUCT_PEAK: {
+        float P = 1.0f;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            const float dx = x[d] - p1[d];
+            P *= __fmaf_rn(dx, dx, p0[d]);
+        }
+        return __frcp_rn(P);
+    }
+    case CV_CORNER_PEAK: {
+        float s = 1.0f;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(p0[d], x[d], s);
+        return ipow<NDIM + 1>(__frcp_rn(s));
+    }
+    case CV_GAUSSIAN: {
+        float s = 0.0f;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            const float t = __fmaf_rn(p0[d], x[d], -p1[d]);
+            s = __fmaf_rn(t, t, s);
+        }
+        return __expf(-s);
+    }
+    case CV_C0: {
+        float s = 0.0f;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(p0[d], fabsf(x[d] - p1[d]), s);
+        return __expf(-s);
+    }
+    case CV_DISCONTINUOUS: {
+        bool out = x[0] > p1[0];
+        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > p1[NDIM > 1 ? 1 : 0]);
+        float s = 0.0f;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(p0[d], x[d], s);
+        return out ? 0.0f : __expf(s);
+    }
+    default:
+        return 1.0f;
+    }
+}
+
+// FP64 Genz evaluation of one component (same formulas in double).
+template <int NDIM>
+__device__ __forceinline__ double genz_f64(int fam, const double *p0, const double *p1,
+                                           double q0, const double (&x)[NDIM])
+{
+    double s = 0.0, P = 1.0;
+    switch (fam) {
+    case CV_OSCILLATORY:
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(p0[d], x[d], s);
+        return cos(q0 + s);
+    case CV_PRODUCT_PEAK:
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            const double dx = x[d] - p1[d];
+            P *= 1.0 / __fma_rn(dx, dx, p0[d]);
+        }
+        return P;
+    case CV_CORNER_PEAK:
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(p0[d], x[d], s);
+        return pow(1.0 + s, -(double)(NDIM + 1));
+    case CV_GAUSSIAN:
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            const double dx = x[d] - p1[d];
+            s = __fma_rn(p0[d] * dx, dx, s);
+        }
+        return exp(-s);
+    case CV_C0:
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(p0[d], fabs(x[d] - p1[d]), s);
+        return exp(-s);
+    case CV_DISCONTINUOUS: {
+        bool out = x[0] > p1[0];
+        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > p1[NDIM > 1 ? 1 : 0]);
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(p0[d], x[d], s);
+        return out ? 0.0 : exp(s);
+    }
+    default:
+        return 1.0;
+    }
+}
+
+template <int NDIM>
+__device__ __forceinline__ float genz_eval(int fam, const float *p0, const float *p1, float q0,
+                                           const float (&x)[NDIM])
+{
+    return genz_f32<NDIM>(fam, p0, p1, q0, x);
+}
+template <int NDIM>
+__device__ __forceinline__ double genz_eval(int fam, const double *p0, const double *p1,
+                                            double q0, const double (&x)[NDIM])
+{
+    return genz_f64<NDIM>(fam, p0, p1, q0, x);
+}
+
+// ------------------------------------------------------------ sums
+// FP32 path: Kahan-compensated per-thread sums (value = s - c).
+// FP64 path: plain per-thread sums.
+template <typename Real> struct Acc;
+template <> struct Acc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------ the kernel
+template <int NDIM, typename Real>
+__global__ void __launch_bounds__(kBlock)
+k_sample(const __grid_constant__ SampleArgs<Real> A)
+{
+    using P = Prec<Real>;
+    using W = typename P::Word;
+    using Real2 = typename P::Real2;
+
+    unsigned long long start;
+    long long n;
+    if (A.st) {
+        if (*(volatile const int *)&A.st->stopped) return;
+        start = A.st->next_index;
+        n = A.st->n_cur;
+    } else {
+        start = A.start;
+        n = A.n;
+    }
+    const int N = A.nbins;
+    const int ncomp = A.g.ncomp;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real2 *sg = reinterpret_cast<Real2 *>(smem_raw);          // [NDIM*N] {e_k, w_k}
+    Real *sh = reinterpret_cast<Real *>(sg + NDIM * N);        // [NDIM*N] histogram
+
+    for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+        const int d = idx / N, k = idx - d * N;
+        const double *e = A.edges + (size_t)d * (N + 1);
+        sg[idx] = P::stage(e[k], e[k + 1]);
+        sh[idx] = Real(0);
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const unsigned long long qa = start >> 5;
+    const unsigned long long end = start + (unsigned long long)n;
+    const unsigned long long qb = (end + 31ull) >> 5;
+    const unsigned long long nblk = n > 0 ? qb - qa : 0ull;
+    const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const unsigned long long twarps = (unsigned long long)gridDim.x * kWarpsPerBlock;
+    unsigned long long plen = (nblk + twarps - 1) / twarps;
+    if (plen < (unsigned long long)A.chunk_min) plen = A.chunk_min;
+    const unsigned long long nchunk = (nblk + plen - 1) / plen;
+    const Real Nr = (Real)N;
+
+    Acc<Real> s1[CV_MAX_COMP], s2[CV_MAX_COMP];
+
+    for (unsigned long long ch = gwarp; ch < nchunk; ch += twarps) {
+        const unsigned long long q0 = qa + ch * plen;
+        const unsigned long long q1 = min(q0 + plen, qb);
+        W X[NDIM];
+        sobol_skip<NDIM, W>(X, q0, lane);
+        for (unsigned long long q = q0; q < q1; ++q) {
+            const unsigned long long i = q * 32ull + (unsigned long long)lane;
+            const bool valid = (i >= start) && (i < end);
+            Real x[NDIM];
+            Real J = Real(1);
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                Real frac;
+                const int k = P::bin(X[d], (unsigned)N, &frac);
+                const Real2 ew = sg[d * N + k];
+                x[d] = fma_rn(ew.y, frac, ew.x);
+                J = J * (Nr * ew.y);
+            }
+            Real f0 = Real(0);
+#pragma unroll
+            for (int c = 0; c < CV_MAX_COMP; ++c) {
+                if (c < ncomp) {
+                    const Real f = genz_eval<NDIM>(A.g.family[c], A.g.p0[c], A.g.p1[c],
+                                                   A.g.q0[c], x);
+                    const Real v = J * f;
+                    if (valid) {
+                        s1[c].add(v);
+                        s2[c].add(v * v);
+                    }
+                    if (c == 0) f0 = v;
+                }
+            }
+            const Real h = f0 * f0;
+            if (valid && h != Real(0)) {
+#pragma unroll
+                for (int d = 0; d < NDIM; ++d)
+                    atomicAdd(&sh[d * N + P::bin_only(X[d], (unsigned)N)], h);
+            }
+            if (q + 1 < q1) sobol_step<NDIM, W>(X, q);
+        }
+    }
+
+    // FP64 reduction: warp shuffle, then across the block's warps.
+    __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < CV_MAX_COMP; ++c) {
+        if (c < ncomp) {
+            const double a = warp_sum(s1[c].value());
+            const double b = warp_sum(s2[c].value());
+            if (lane == 0) {
+                red[warp][2 * c] = a;
+                red[warp][2 * c + 1] = b;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * ncomp) {
+        double t = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) t += red[w][threadIdx.x];
+        const int c = threadIdx.x >> 1;
+        atomicAdd((threadIdx.x & 1) ? &A.S2[c] : &A.S1[c], t);
+    }
+    for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+        const Real v = sh[idx];
+        if (v != Real(0)) atomicAdd(&A.H[idx], (double)v);
+    }
+}
+
+// Sobol coordinates only (the point generator of the sampling kernels,
+// written out for bit-exact checks): Y[d*n + j] = X_d(start + j) >> shift.
+template <int NDIM, typename W>
+__global__ void __launch_bounds__(kBlock)
+k_sobol(unsigned long long start, long long n, int shift, unsigned long long *Y)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long qa = start >> 5;
+    const unsigned long long end = start + (unsigned long long)n;
+    const unsigned long long qb = (end + 31ull) >> 5;
+    const unsigned long long nblk = n > 0 ? qb - qa : 0ull;
+    const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const unsigned long long twarps = (unsigned long long)gridDim.x * kWarpsPerBlock;
+    unsigned long long plen = (nblk + twarps - 1) / twarps;
+    if (plen < 4) plen = 4;
+    const unsigned long long nchunk = (nblk + plen - 1) / plen;
+    for (unsigned long long ch = gwarp; ch < nchunk; ch += twarps) {
+        const unsigned long long q0 = qa + ch * plen;
+        const unsigned long long q1 = min(q0 + plen, qb);
+        W X[NDIM];
+        sobol_skip<NDIM, W>(X, q0, lane);
+        for (unsigned long long q = q0; q < q1; ++q) {
+            const unsigned long long i = q * 32ull + (unsigned long long)lane;
+            if (i >= start && i < end) {
+                const unsigned long long j = i - start;
+#pragma unroll
+                for (int d = 0; d < NDIM; ++d)
+                    Y[(size_t)d * n + j] = (unsigned long long)(X[d] >> shift);
+            }
+            if (q + 1 < q1) sobol_step<NDIM, W>(X, q);
+        }
+    }
+}
+
+// ------------------------------------------------------------ launchers
+template <int NDIM, typename Real>
+cudaError_t launch_sample(const SampleArgs<Real> &a, int grid, cudaStream_t s)
+{
+    // (sample_occupancy, always called first, sets the shared-memory limit)
+    const size_t smem = sample_smem_bytes(NDIM, a.nbins, sizeof(Real) == 8);
+    k_sample<NDIM, Real><<<grid, kBlock, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NDIM, typename Real>
+cudaError_t sample_occupancy(int nbins, int *blocks_per_sm)
+{
+    const size_t smem = sample_smem_bytes(NDIM, nbins, sizeof(Real) == 8);
+    cudaError_t e = cudaFuncSetAttribute(k_sample<NDIM, Real>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sample_smem_bytes(NDIM, CV_MAX_BINS, sizeof(Real) == 8));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sample<NDIM, Real>,
+                                                         kBlock, smem);
+}
+
+template <int NDIM, typename W>
+cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
+                         unsigned long long *Y, int grid, cudaStream_t s)
+{
+    const int shift = (int)(8 * sizeof(W)) - bits;
+    k_sobol<NDIM, W><<<grid, kBlock, 0, s>>>(start, n, shift, Y);
+    return cudaGetLastError();
+}
+
+}  // namespace cv
+
+#define CV_INSTANTIATE_NDIM(D)                                                              \
+    template cudaError_t cv::launch_sample<D, float>(const cv::SampleArgs<float> &, int,    \
+                                                     cudaStream_t);                         \
+    template cudaError_t cv::launch_sample<D, double>(const cv::SampleArgs<double> &, int,  \
+                                                      cudaStream_t);                        \
+    template cudaError_t cv::sample_occupancy<D, float>(int, int *);                        \
+    template cudaError_t cv::sample_occupancy<D, double>(int, int *);                       \
+    template cudaError_t cv::launch_sobol<D, unsigned int>(unsigned long long, long long,   \
+                                                           int, unsigned long long *, int,  \
+                                                           cudaStream_t);                   \
+    template cudaError_t cv::launch_sobol<D, unsigned long long>(                           \
+        unsigned long long, long long, int, unsigned long long *, int, cudaStream_t);

@@ -1,0 +1,107 @@
+// cv_internal.cuh -- internal types shared by the CUDA translation units of
+// the Vegas sampling library (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/cubagpu.h"
+
+namespace cv {
+
+constexpr int kWarp = 32;
+constexpr int kBlock = 256;                 // threads per sampling block
+constexpr int kWarpsPerBlock = kBlock / kWarp;
+constexpr int kLogCap = 256;                // iterations logged per integral
+
+// Device-resident state of one integral between iterations: the analogue of
+// Cuba's spinning workers keeping their state (Sect. 3.2.3), here kept in
+// HBM so iterations chain on the device without host round trips.
+struct DevState {
+    unsigned long long next_index;  // Sobol index of the next iteration's first point
+    long long n_cur;                // points of the next iteration
+    long long neval;                // points sampled so far
+    int iter;                       // iterations completed
+    int stopped;                    // 1 once the run has terminated
+    int fail;                       // Cuba's fail: 0 accuracy reached, 1 maxeval
+    int status;                     // bit 0: a non-finite iteration result
+    double S1[CV_MAX_COMP];         // sum J f_c of the running iteration
+    double S2[CV_MAX_COMP];         // sum (J f_c)^2
+    // inverse-variance combination (West's weighted incremental update)
+    double W[CV_MAX_COMP];          // sum 1/var_j
+    double mean[CV_MAX_COMP];       // weighted mean
+    double M2[CV_MAX_COMP];         // sum (I_j - mean)^2 / var_j
+    double sumI[CV_MAX_COMP];       // plain sum of I_j (zero-variance fallback)
+    int zero[CV_MAX_COMP];          // a var_j <= 0 was seen
+    double integral[CV_MAX_COMP];
+    double error[CV_MAX_COMP];
+    double chi2[CV_MAX_COMP];
+    double prob[CV_MAX_COMP];
+};
+
+// Per-component integrand parameters in the precision of the evaluation,
+// pre-transformed on the host so the inner loop is FMA-shaped:
+//   oscillatory   p0 = a/(2 pi) (turns) [FP32] or a [FP64];  q0 = u_1 or 2 pi u_1
+//   product peak  p0 = 1/a^2, p1 = u
+//   corner peak   p0 = a
+//   gaussian      p0 = a, p1 = a u [FP32];  p0 = a^2, p1 = u [FP64]
+//   c0            p0 = a, p1 = u
+//   discontinuous p0 = a, p1 = u
+template <typename Real>
+struct GenzParams {
+    int ndim;
+    int ncomp;
+    int family[CV_MAX_COMP];
+    Real p0[CV_MAX_COMP][CV_MAX_DIM];
+    Real p1[CV_MAX_COMP][CV_MAX_DIM];
+    Real q0[CV_MAX_COMP];
+};
+
+// Arguments of one sampling launch.  When `st` is non-null the launch reads
+// its index range from the device state (and returns at once if the run has
+// stopped), which is what lets a captured graph replay iterations whose
+// sizes are decided on the device.
+template <typename Real>
+struct SampleArgs {
+    GenzParams<Real> g;
+    int nbins;
+    int chunk_min;                  // minimum warp-steps per chunk
+    const double *edges;            // [ndim][nbins+1]
+    double *S1;                     // [ncomp]
+    double *S2;                     // [ncomp]
+    double *H;                      // [ndim][nbins]
+    unsigned long long start;
+    long long n;
+    const DevState *st;
+};
+
+struct CombineArgs {
+    DevState *st;
+    int ncomp;
+    double epsrel, epsabs;
+    long long mineval, maxeval, nstart, nincrease;
+    double *log_I;                  // [kLogCap][CV_MAX_COMP] or null
+    double *log_var;
+};
+
+// ---- launchers (template definitions in cv_device.cuh, instantiated per
+// ---- dimension range in cv_sample_*.cu) ----
+template <int NDIM, typename Real>
+cudaError_t launch_sample(const SampleArgs<Real> &a, int grid, cudaStream_t s);
+template <int NDIM, typename Real>
+cudaError_t sample_occupancy(int nbins, int *blocks_per_sm);
+template <int NDIM, typename Word>
+cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
+                         unsigned long long *Y, int grid, cudaStream_t s);
+
+// cv_refine.cu
+cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges,
+                          int zero_hist, const DevState *st, cudaStream_t s);
+cudaError_t launch_combine(const CombineArgs &a, cudaStream_t s);
+
+inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64) {
+    // grid {e, w} pairs plus the block histogram
+    return (size_t)ndim * nbins * (fp64 ? 3 * sizeof(double) : 3 * sizeof(float));
+}
+
+}  // namespace cv

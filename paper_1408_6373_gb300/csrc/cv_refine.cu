@@ -1,0 +1,231 @@
+// cv_refine.cu -- FP64 grid refinement and iteration combination kernels.
+//
+// Refinement (Lepage 1978; the paper gives only the Vegas arguments,
+// Sect. 3.2.2): per axis, smooth the f^2 histogram over neighbouring bins,
+// compress it with exponent 1.5, and move the N-1 interior edges so every
+// new bin holds an equal share of the compressed weight.  One CTA per axis;
+// the order of every FP64 operation is fixed so the result is reproducible.
+//
+// Combination: per component, the iteration result I_j = S1/n and
+// var_j = (S2/n - I_j^2)/(n-1) are folded into the inverse-variance weighted
+// mean with West's (1979) incremental update, which also yields
+// chi^2 = sum_j (I_j - mean)^2 / var_j without cancellation; the chi-square
+// probability P((m-1)/2, chi^2/2) uses the regularized incomplete gamma
+// function (series for x < a+1, Legendre continued fraction otherwise).
+#include <cfloat>
+
+#include "cv_internal.cuh"
+
+namespace cv {
+
+// Regularized lower incomplete gamma P(a, x), a > 0, x >= 0.
+__device__ double gamma_p(double a, double x)
+{
+    if (!(x > 0.0)) return 0.0;
+    const double lg = lgamma(a);
+    if (x < a + 1.0) {
+        // P = e^{-x} x^a / Gamma(a) * sum_n x^n / (a (a+1) ... (a+n))
+        double ap = a, term = 1.0 / a, sum = term;
+        for (int n = 0; n < 1000; ++n) {
+            ap += 1.0;
+            term *= x / ap;
+            sum += term;
+            if (fabs(term) < fabs(sum) * 1e-17) break;
+        }
+        return sum * exp(-x + a * log(x) - lg);
+    }
+    // Q by the continued fraction 1/(x+1-a- 1(1-a)/(x+3-a- 2(2-a)/(x+5-a- ...)))
+    // evaluated with the modified Lentz method.
+    const double tiny = 1e-300;
+    double b = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / b, h = d;
+    for (int i = 1; i < 1000; ++i) {
+        const double an = -i * (i - a);
+        b += 2.0;
+        d = an * d + b;
+        if (fabs(d) < tiny) d = tiny;
+        c = b + an / c;
+        if (fabs(c) < tiny) c = tiny;
+        d = 1.0 / d;
+        const double del = d * c;
+        h *= del;
+        if (fabs(del - 1.0) < 1e-17) break;
+    }
+    const double Q = exp(-x + a * log(x) - lg) * h;
+    return 1.0 - Q;
+}
+
+__global__ void __launch_bounds__(256)
+k_refine(int N, double *H, double *edges, int zero_hist, const DevState *st)
+{
+    if (st && *(volatile const int *)&st->stopped) return;
+    const int d = blockIdx.x;
+    double *Hd = H + (size_t)d * N;
+    double *e = edges + (size_t)d * (N + 1);
+    __shared__ double sH[CV_MAX_BINS], sh[CV_MAX_BINS], sr[CV_MAX_BINS];
+    __shared__ double sC[CV_MAX_BINS + 1], se[CV_MAX_BINS + 1];
+    __shared__ double s_sum, s_R;
+    __shared__ int s_use;
+
+    for (int k = threadIdx.x; k < N; k += blockDim.x) sH[k] = Hd[k];
+    for (int k = threadIdx.x; k <= N; k += blockDim.x) se[k] = e[k];
+    __syncthreads();
+    // smoothing over the neighbours
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        double h;
+        if (k == 0) h = __ddiv_rn(__dadd_rn(sH[0], sH[1]), 2.0);
+        else if (k == N - 1) h = __ddiv_rn(__dadd_rn(sH[N - 2], sH[N - 1]), 2.0);
+        else h = __ddiv_rn(__dadd_rn(__dadd_rn(sH[k - 1], sH[k]), sH[k + 1]), 3.0);
+        sh[k] = h;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int usable = 0, finite = 1;
+        double s = 0.0;
+        for (int k = 0; k < N; ++k) {
+            if (!isfinite(sH[k])) finite = 0;
+            if (sH[k] != 0.0) usable = 1;
+            s = __dadd_rn(s, sh[k]);
+        }
+        s_sum = s;
+        s_use = usable && finite;
+    }
+    __syncthreads();
+    if (s_use) {
+        const double s = s_sum;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            const double h = sh[k];
+            double r;
+            if (h == 0.0) r = 0.0;
+            else if (h == s) r = 1.0;
+            else {
+                const double q = __ddiv_rn(__dadd_rn(1.0, -__ddiv_rn(h, s)), log(__ddiv_rn(s, h)));
+                r = __dmul_rn(q, sqrt(q));
+            }
+            sr[k] = r;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double rmax = 0.0;
+            for (int k = 0; k < N; ++k) rmax = sr[k] > rmax ? sr[k] : rmax;
+            if (rmax > 0.0) {
+                double C = 0.0;
+                sC[0] = 0.0;
+                for (int k = 0; k < N; ++k) {
+                    sr[k] = __ddiv_rn(sr[k], rmax);
+                    C = __dadd_rn(C, sr[k]);
+                    sC[k + 1] = C;
+                }
+                s_R = C;
+            } else {
+                s_R = -1.0;
+            }
+        }
+        __syncthreads();
+        if (s_R > 0.0) {
+            const double R = s_R;
+            for (int m = 1 + threadIdx.x; m < N; m += blockDim.x) {
+                const double t = __ddiv_rn(__dmul_rn((double)m, R), (double)N);
+                // largest k in [0, N-1] with C_k <= t
+                int lo = 0, hi = N - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sC[mid] <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int k = lo;
+                e[m] = __fma_rn(__dadd_rn(se[k + 1], -se[k]),
+                                __ddiv_rn(__dadd_rn(t, -sC[k]), sr[k]), se[k]);
+            }
+        }
+    }
+    if (zero_hist) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < N; k += blockDim.x) Hd[k] = 0.0;
+    }
+}
+
+// One thread per component, then thread 0 updates the iteration control.
+__global__ void k_combine(const CombineArgs A)
+{
+    DevState *st = A.st;
+    if (*(volatile int *)&st->stopped) return;
+    const int c = threadIdx.x;
+    const long long n = st->n_cur;
+    const int j = st->iter;
+    __shared__ int s_ok[CV_MAX_COMP];
+    if (c < A.ncomp) {
+        const double dn = (double)n;
+        const double I = __ddiv_rn(st->S1[c], dn);
+        const double var = __ddiv_rn(__dadd_rn(__ddiv_rn(st->S2[c], dn), -__dmul_rn(I, I)),
+                                     (double)(n - 1));
+        if (A.log_I && j < kLogCap) {
+            A.log_I[j * CV_MAX_COMP + c] = I;
+            A.log_var[j * CV_MAX_COMP + c] = var;
+        }
+        if (!isfinite(I) || !isfinite(var)) atomicOr(&st->status, 1);
+        const int m = j + 1;
+        st->sumI[c] += I;
+        if (!(var > 0.0)) st->zero[c] = 1;
+        if (!st->zero[c]) {
+            const double w = 1.0 / var;
+            const double Wn = st->W[c] + w;
+            const double dI = I - st->mean[c];
+            const double mean = st->mean[c] + dI * (w / Wn);
+            st->M2[c] += w * dI * (I - mean);
+            st->mean[c] = mean;
+            st->W[c] = Wn;
+        }
+        double integral, error, chi2, prob;
+        if (st->zero[c]) {
+            integral = st->sumI[c] / (double)m;
+            error = chi2 = prob = 0.0;
+        } else {
+            integral = st->mean[c];
+            error = sqrt(1.0 / st->W[c]);
+            chi2 = st->M2[c] > 0.0 ? st->M2[c] : 0.0;
+            prob = m > 1 ? gamma_p(0.5 * (m - 1), 0.5 * chi2) : 0.0;
+        }
+        st->integral[c] = integral;
+        st->error[c] = error;
+        st->chi2[c] = chi2;
+        st->prob[c] = prob;
+        const double tol = fmax(A.epsabs, A.epsrel * fabs(integral));
+        s_ok[c] = error <= tol;
+        st->S1[c] = 0.0;
+        st->S2[c] = 0.0;
+    }
+    __syncthreads();
+    if (c == 0) {
+        int ok = 1;
+        for (int i = 0; i < A.ncomp; ++i) ok &= s_ok[i];
+        const long long neval = st->neval + n;
+        st->neval = neval;
+        st->iter = j + 1;
+        const long long next = A.nstart + (long long)(j + 1) * A.nincrease;
+        if (neval >= A.mineval && ok) {
+            st->fail = 0;
+            st->stopped = 1;
+        } else if (neval + next > A.maxeval) {
+            st->fail = 1;
+            st->stopped = 1;
+        } else {
+            st->next_index += (unsigned long long)n;
+            st->n_cur = next;
+        }
+    }
+}
+
+cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, int zero_hist,
+                          const DevState *st, cudaStream_t s)
+{
+    k_refine<<<ndim, 256, 0, s>>>(nbins, H, edges, zero_hist, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const CombineArgs &a, cudaStream_t s)
+{
+    k_combine<<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace cv

@@ -1,0 +1,245 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64
+oracle, element by element, on the same seeded inputs.
+
+Tolerances (the arithmetic behind them is in the design notes):
+  - Sobol coordinates and bin assignment: bit-exact.
+  - FP64 path: S1, S2 within 1e-12 relative; histogram within 1e-12 of the
+    row maximum; refined edges within 1e-14 absolute.
+  - FP32 path (FP32 point/map/integrand, Kahan, FP64 reduction): S1, S2
+    within 1e-6 of the magnitude sqrt(n S2) >= sum |J f|; histogram within
+    1e-5 of the row maximum.  Where a float decides a branch (the
+    discontinuous family) the oracle takes it in binary32 too.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1408_6373_gb300 as cg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cg.build_library()
+    c = cg.Context(0)
+    yield c
+    c.close()
+
+
+def _random_grid(ndim, nbins, seed):
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(0.2, 1.0, (ndim, nbins))
+    c = np.concatenate([np.zeros((ndim, 1)), np.cumsum(w, axis=1)], axis=1)
+    e = c / c[:, -1:]
+    e[:, 0], e[:, -1] = 0.0, 1.0
+    return e
+
+
+def _params(ndim, ncomp, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.3, 1.5, (ncomp, ndim))
+    a *= min(ndim, 8) / a.sum(axis=1, keepdims=True)
+    u = rng.uniform(0.1, 0.9, (ncomp, ndim))
+    return a, u
+
+
+def _gpu_sample(ctx, g, edges, start, n, flags):
+    ndim, nbins = edges.shape[0], edges.shape[1] - 1
+    e = torch.tensor(edges, dtype=torch.float64, device="cuda")
+    S1 = torch.zeros(g.ncomp, dtype=torch.float64, device="cuda")
+    S2 = torch.zeros_like(S1)
+    H = torch.zeros((ndim, nbins), dtype=torch.float64, device="cuda")
+    ctx.sample(g, nbins, e, start, n, flags, S1, S2, H)
+    ctx.synchronize()
+    return S1.cpu().numpy(), S2.cpu().numpy(), H.cpu().numpy()
+
+
+# ------------------------------------------------------------------ Sobol
+@pytest.mark.parametrize("bits", [23, 52])
+@pytest.mark.parametrize("ndim,start,n", [
+    (1, 0, 1), (3, 1, 10000), (8, 7, 33333), (17, 2 ** 20 + 3, 5000),
+    (32, 12345, 70001), (5, 2 ** 40 + 11, 2049), (2, 2 ** 52 - 1000, 1000)])
+def test_sobol_bit_exact(ctx, bits, ndim, start, n):
+    Y = torch.empty((ndim, n), dtype=torch.int64, device="cuda")
+    ctx.sobol(ndim, start, n, bits, Y)
+    ctx.synchronize()
+    ref = O.sobol_coords(ndim, start, n, bits)
+    assert np.array_equal(Y.cpu().numpy().view(np.uint64), ref)
+
+
+# ------------------------------------------------------------------ FP64 pass
+FAMS = [O.OSCILLATORY, O.PRODUCT_PEAK, O.CORNER_PEAK, O.GAUSSIAN, O.C0, O.DISCONTINUOUS, O.CONST]
+
+
+@pytest.mark.parametrize("fam", FAMS)
+@pytest.mark.parametrize("ndim,nbins,start,n", [(3, 50, 1, 20001), (8, 128, 1000003, 30000)])
+def test_sample_fp64_matches_oracle(ctx, fam, ndim, nbins, start, n):
+    a, u = _params(ndim, 1, 10 + fam)
+    edges = _random_grid(ndim, nbins, fam)
+    g = cg.genz(ndim, [fam], a, u)
+    S1, S2, H = _gpu_sample(ctx, g, edges, start, n, cg.FP64)
+    p = O.Problem(ndim, [fam], a, u, nbins=nbins, bits=52)
+    oS1, oS2, oH = O.sample(p, edges, start, n)
+    np.testing.assert_allclose(S1, oS1, rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(S2, oS2, rtol=1e-12, atol=1e-300)
+    scale = np.maximum(oH.max(axis=1, keepdims=True), 1e-300)
+    assert np.all(np.abs(H - oH) <= 1e-12 * scale)
+    # bins bit-exact: the points that reached each bin are the same
+    assert np.array_equal(H == 0, oH == 0)
+
+
+@pytest.mark.parametrize("ndim,ncomp,nbins", [(1, 2, 2), (4, 4, 64), (13, 3, 100), (32, 4, 256)])
+def test_sample_fp64_multicomponent_and_sizes(ctx, ndim, ncomp, nbins):
+    a, u = _params(ndim, ncomp, 100 + ndim)
+    fams = [O.GAUSSIAN, O.OSCILLATORY, O.C0, O.PRODUCT_PEAK][:ncomp]
+    edges = _random_grid(ndim, nbins, ndim)
+    g = cg.genz(ndim, fams, a, u)
+    n = 12345
+    S1, S2, H = _gpu_sample(ctx, g, edges, 5, n, cg.FP64)
+    p = O.Problem(ndim, fams, a, u, nbins=nbins, bits=52)
+    oS1, oS2, oH = O.sample(p, edges, 5, n)
+    np.testing.assert_allclose(S1, oS1, rtol=1e-12)
+    np.testing.assert_allclose(S2, oS2, rtol=1e-12)
+    scale = np.maximum(oH.max(axis=1, keepdims=True), 1e-300)
+    assert np.all(np.abs(H - oH) <= 1e-12 * scale)
+
+
+# ------------------------------------------------------------------ FP32 pass
+@pytest.mark.parametrize("fam", FAMS)
+@pytest.mark.parametrize("ndim,nbins,start,n", [(3, 50, 1, 20001), (8, 128, 77, 100000)])
+def test_sample_fp32_matches_oracle(ctx, fam, ndim, nbins, start, n):
+    a, u = _params(ndim, 1, 20 + fam)
+    edges = _random_grid(ndim, nbins, 50 + fam)
+    g = cg.genz(ndim, [fam], a, u)
+    S1, S2, H = _gpu_sample(ctx, g, edges, start, n, 0)
+    p = O.Problem(ndim, [fam], a, u, nbins=nbins, bits=23, fp32_decide=True)
+    oS1, oS2, oH = O.sample(p, edges, start, n)
+    mag = math.sqrt(n * oS2[0]) if oS2[0] > 0 else 1.0
+    assert abs(S1[0] - oS1[0]) <= 1e-6 * mag, (S1, oS1)
+    assert abs(S2[0] - oS2[0]) <= 1e-6 * oS2[0] + 1e-300, (S2, oS2)
+    scale = np.maximum(oH.max(axis=1, keepdims=True), 1e-300)
+    assert np.all(np.abs(H - oH) <= 1e-5 * scale)
+
+
+def test_sample_fp32_const_is_exact(ctx):
+    # f = 1, uniform power-of-two grid: J = 1, S1 = S2 = n, exact counts.
+    ndim, N, n = 6, 64, 2 ** 16
+    g = cg.genz(ndim, [cg.CONST], 1.0, 0.5)
+    S1, S2, H = _gpu_sample(ctx, g, O.grid_uniform(ndim, N), 2 ** 16, n, 0)
+    assert S1[0] == n and S2[0] == n
+    assert np.all(H == n // N)
+
+
+def test_sample_accumulates_and_zero_n_is_noop(ctx):
+    ndim, N = 2, 16
+    g = cg.genz(ndim, [cg.GAUSSIAN], 2.0, 0.5)
+    e = torch.tensor(O.grid_uniform(ndim, N), device="cuda")
+    S1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    S2 = torch.zeros_like(S1)
+    H = torch.zeros((ndim, N), dtype=torch.float64, device="cuda")
+    ctx.sample(g, N, e, 1, 0, cg.FP64, S1, S2, H)
+    ctx.synchronize()
+    assert S1.item() == 0.0
+    ctx.sample(g, N, e, 1, 1000, cg.FP64, S1, S2, H)
+    ctx.sample(g, N, e, 1001, 1000, cg.FP64, S1, S2, H)
+    ctx.synchronize()
+    p = O.Problem(ndim, [O.GAUSSIAN], np.full((1, ndim), 2.0), np.full((1, ndim), 0.5), nbins=N)
+    oS1, _, _ = O.sample(p, O.grid_uniform(ndim, N), 1, 2000)
+    assert S1.item() == pytest.approx(oS1[0], rel=1e-12)
+
+
+# ------------------------------------------------------------------ refine
+@pytest.mark.parametrize("ndim,nbins", [(1, 2), (3, 50), (8, 128), (32, 256)])
+def test_refine_matches_oracle(ctx, ndim, nbins):
+    rng = np.random.default_rng(nbins)
+    edges = _random_grid(ndim, nbins, 3)
+    H = rng.random((ndim, nbins)) ** 3
+    H[0, : nbins // 3] = 0.0
+    if ndim > 2:
+        H[1] = 0.0          # all-zero axis keeps its grid
+        H[2] = 1.0          # equal histogram keeps its grid
+    e = torch.tensor(edges, device="cuda")
+    h = torch.tensor(H, device="cuda")
+    ctx.refine(ndim, nbins, h, e)
+    ctx.synchronize()
+    ref = O.refine(edges, H)
+    assert np.max(np.abs(e.cpu().numpy() - ref)) <= 1e-14
+    if ndim > 2:
+        assert np.array_equal(e.cpu().numpy()[1:3], edges[1:3])
+
+
+# ------------------------------------------------------------------ Vegas
+def test_vegas_cfg1_fp64_matches_oracle(ctx):
+    ndim, N, n = 3, 50, 10 ** 4
+    g = cg.genz(ndim, [cg.GAUSSIAN], 5.0, 0.5)
+    p = O.Problem(ndim, [O.GAUSSIAN], np.full((1, 3), 5.0), np.full((1, 3), 0.5), nbins=N)
+    o = O.vegas(p, maxeval=10 * n, nstart=n)
+    for flags in (cg.FP64, cg.FP64 | cg.PLAIN):
+        r = ctx.vegas(g, flags=flags, maxeval=10 * n, nstart=n, nbins=N)
+        assert (r.neval, r.fail) == (o.neval, o.fail)
+        assert r.integral[0] == pytest.approx(o.integral[0], rel=1e-12)
+        assert r.error[0] == pytest.approx(o.error[0], rel=1e-10)
+        assert r.prob[0] == pytest.approx(o.prob[0], abs=1e-10)
+    exact = (math.sqrt(math.pi) / 5 * math.erf(2.5)) ** 3
+    assert abs(r.integral[0] - exact) < 3 * r.error[0]
+
+
+def test_vegas_fp32_within_three_sigma_and_close_to_oracle(ctx):
+    ndim, ncomp = 8, 4
+    a, u = _params(ndim, ncomp, 7)
+    fams = [O.OSCILLATORY, O.PRODUCT_PEAK, O.CORNER_PEAK, O.GAUSSIAN]
+    g = cg.genz(ndim, fams, a, u)
+    r = ctx.vegas(g, flags=0, maxeval=10 * 2 ** 15, nstart=2 ** 15, nbins=128)
+    p = O.Problem(ndim, fams, a, u, nbins=128, bits=23, fp32_decide=True)
+    exact = p.exact()
+    for c in range(ncomp):
+        assert abs(r.integral[c] - exact[c]) < 3 * r.error[c] + 1e-7 * abs(exact[c])
+
+
+def test_vegas_stops_on_accuracy_same_iteration_as_oracle(ctx):
+    ndim = 4
+    a, u = _params(ndim, 1, 3)
+    g = cg.genz(ndim, [cg.GAUSSIAN], a, u)
+    p = O.Problem(ndim, [O.GAUSSIAN], a, u, nbins=64)
+    o = O.vegas(p, epsrel=2e-4, maxeval=10 ** 6, nstart=5000, nincrease=2500)
+    r = ctx.vegas(g, epsrel=2e-4, flags=cg.FP64, maxeval=10 ** 6, nstart=5000, nincrease=2500, nbins=64)
+    assert (r.neval, r.fail) == (o.neval, o.fail) and o.fail == 0
+    assert r.integral[0] == pytest.approx(o.integral[0], rel=1e-12)
+
+
+def test_vegas_const_exact(ctx):
+    g = cg.genz(5, [cg.CONST], 1.0, 0.5)
+    for flags in (0, cg.FP64):
+        r = ctx.vegas(g, epsrel=1e-3, flags=flags, maxeval=10 ** 5, nstart=1024, nbins=64)
+        assert r.integral[0] == 1.0 and r.error[0] == 0.0 and r.fail == 0 and r.neval == 1024
+
+
+def test_vegas_nbatch_does_not_change_results(ctx):
+    g = cg.genz(3, [cg.C0], 1.0, 0.4)
+    r1 = ctx.vegas(g, flags=cg.FP64, maxeval=6 * 4000, nstart=4000, nbatch=100, nbins=32)
+    r2 = ctx.vegas(g, flags=cg.FP64, maxeval=6 * 4000, nstart=4000, nbatch=100000, nbins=32)
+    assert r1.integral[0] == pytest.approx(r2.integral[0], rel=1e-14)
+
+
+def test_invalid_arguments_rejected(ctx):
+    g = cg.genz(3, [cg.GAUSSIAN], 1.0, 0.5)
+    with pytest.raises(cg.CubaGpuError) as ei:
+        ctx.vegas(g, nbins=1)
+    assert ei.value.code == cg.EINVAL
+    with pytest.raises(cg.CubaGpuError):
+        ctx.vegas(g, nstart=1)
+    Y = torch.empty((3, 4), dtype=torch.int64, device="cuda")
+    with pytest.raises(cg.CubaGpuError):
+        ctx.sobol(3, 2 ** 52 - 2, 4, 52, Y)
+    with pytest.raises(cg.CubaGpuError):
+        ctx.sobol(3, 0, 4, 30, Y)
+    bad = cg.genz(3, [9], 1.0, 0.5)
+    with pytest.raises(cg.CubaGpuError):
+        ctx.vegas(bad)
