@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Vegas sampling path.
+
+One step = one complete Vegas integration of the mixed-precision Genz
+workload (ndim 8, four components: oscillatory, product peak, corner peak,
+Gaussian; 20 iterations x 1e7 Sobol points; 128 bins per axis): reset of
+the device-resident grid and sums, then every iteration's fused sampling
+pass, FP64 refinement and FP64 combination, replayed from a CUDA graph.
+
+Printed (one JSON line on rank 0):
+  value      samples/s over all ranks, device-timed with CUDA events, inputs
+             resident, L2 flushed (256 MiB write) before every step
+  e2e        samples/s through the public call cv_vegas (host integrand
+             description in, host results out) timed on the host
+  roofline   the fused sampling kernel against the FP32 pipe peak
+             (152 SMs x 128 lanes x 2 flop x the maximum SM clock)
+  cpu_baseline  the FP64 CPU oracle on the host cores, bounded sample
+  plain_fp64 the FP64 one-launch-per-iteration comparator, same workload
+
+--impl reference times the CPU oracle instead (the reference arm).
+Multi-GPU (torchrun): every rank runs its own replica of the workload
+(weak scaling); the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Vegas samples/s"
+UNIT = "samples/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _workload_name(p) -> str:
+    return (f"genz8d4c: Vegas FP32 eval / FP64 reduce, ndim {p.ndim}, ncomp {p.ncomp} "
+            f"(oscillatory, product peak, corner peak, gaussian), {p.maxeval // p.nstart} iterations "
+            f"x {p.nstart:.0e} Sobol points, {p.nbins} bins")
+
+
+# ------------------------------------------------------------------ FLOP count
+def alg_flops_per_sample(ndim: int, families) -> int:
+    """Algorithmic FP32 FLOPs of one sample of the fused pass (FMA = 2; the
+    special-function unit's exp/cos/rcp are not FP32-pipe FLOPs):
+    map 5/dim (frac, x FMA, Jacobian 2 mul); per component J*f, (J f)^2 and
+    two Kahan additions (4 each) = 10; the histogram value f0^2 = 1; and the
+    family's own arithmetic."""
+    per = {
+        0: 2 * ndim + 2,                      # phase FMAs, wrap, scale
+        1: 4 * ndim,                          # sub, FMA, mul per dim
+        2: 2 * ndim + _ipow_muls(ndim + 1),   # FMAs, power by squaring
+        3: 4 * ndim + 1,                      # 2 FMA per dim, scale
+        4: 3 * ndim + 1,                      # sub, FMA per dim, negate
+        5: 2 * ndim + 1,
+        6: 0,
+    }
+    return 5 * ndim + sum(per[f] + 10 for f in families) + 1
+
+
+def _ipow_muls(e: int) -> int:
+    return max(0, e.bit_length() - 1) + max(0, bin(e).count("1") - 1)
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        uuid = _gpu_uuid(device_index)
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_uuid(idx: int):
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(idx).uuid
+        return f"GPU-{u}" if u else None
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ helpers
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1408_6373_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic():
+    """DRAM bytes per launch of the sampling kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "k_sample_genz8d4c.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, _, v = line.strip()[2:].partition(":")
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != _kernel_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_rate(p, target_s: float, threads: int):
+    """Time the FP64 CPU oracle on a bounded sample of workload p: two
+    iterations of n points, n sized for about target_s seconds."""
+    import numpy as np
+
+    import oracle as O
+    prob = O.Problem(p.ndim, list(p.families), np.asarray(p.a), np.asarray(p.u),
+                     nbins=p.nbins, bits=23, fp32_decide=True)
+    prob.directions()
+    n0 = 2000 * threads
+    t = time.perf_counter()
+    O.vegas(prob, maxeval=n0, nstart=n0, nthreads=threads)
+    rate0 = n0 / max(time.perf_counter() - t, 1e-6)
+    n = max(n0, int(rate0 * target_s / 2))
+    t = time.perf_counter()
+    O.vegas(prob, maxeval=2 * n, nstart=n, nthreads=threads)
+    dt = time.perf_counter() - t
+    return 2 * n / dt, dt, n
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1408_6373_gb300 import workloads as W
+    p = W.genz8d4c()
+    threads = os.cpu_count() or 1
+    per_step_s = 3.0
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, dt, n = cpu_oracle_rate(p, per_step_s, threads)
+        if i >= args.warmup:
+            rates.append((r, dt, n))
+    tot_n = sum(2 * n for _, _, n in rates)
+    tot_t = sum(dt for _, dt, _ in rates)
+    value = tot_n / tot_t
+    sample = (f"per step: 2 Vegas iterations x {rates[-1][2]} points of the same workload "
+              f"(FP64 oracle, {threads} threads)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / len(rates), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _workload_name(p)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1408_6373_gb300 as cg
+    from paper_1408_6373_gb300 import workloads as W
+
+    world, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cg.build_library()
+
+    p = W.genz8d4c()
+    g = cg.genz(p.ndim, p.families, p.a, p.u)
+    sp = cg.spec(g, nbins=p.nbins, flags=0, maxeval=p.maxeval, nstart=p.nstart,
+                 nincrease=p.nincrease, nbatch=p.nstart)
+    samples_per_step = p.maxeval
+    ctx = cg.Context(local)
+    integ = ctx.integral(sp)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step():
+        integ.reset()
+        integ.run()
+
+    # ---- device-timed steps
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    events = []
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        step()
+        e.record()
+        events.append((s, e))
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    dev_ms = sum(s.elapsed_time(e) for s, e in events)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = t.item()
+    res = integ.result()
+    value = world * samples_per_step * args.steps / (dev_ms / 1e3)
+    launches = integ.kernels_per_run() * args.steps
+
+    # ---- the sampling kernel alone, for the roofline
+    edges = torch.tensor(integ.grid(), dtype=torch.float64, device="cuda")
+    S1 = torch.zeros(p.ncomp, dtype=torch.float64, device="cuda")
+    S2 = torch.zeros_like(S1)
+    H = torch.zeros((p.ndim, p.nbins), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ctx.sample(g, p.nbins, edges, 1, p.nstart, 0, S1, S2, H)
+    torch.cuda.synchronize()
+    kev = []
+    for _ in range(10):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        ctx.sample(g, p.nbins, edges, 1, p.nstart, 0, S1, S2, H)
+        e.record()
+        kev.append((s, e))
+    torch.cuda.synchronize()
+    k_ms = statistics.mean(s.elapsed_time(e) for s, e in kev)
+    flops = alg_flops_per_sample(p.ndim, p.families) * p.nstart
+    achieved = flops / (k_ms / 1e3) / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sm_max)
+    traffic = _profile_traffic()
+
+    # ---- end to end through cv_vegas (host description in, host results out)
+    h2d, d2h = cg.vegas_io_bytes(p.ndim, p.nbins)
+    ctx.vegas(g, flags=0, maxeval=p.maxeval, nstart=p.nstart, nincrease=p.nincrease, nbins=p.nbins)
+    barrier()
+    e2e_t = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        ctx.vegas(g, flags=0, maxeval=p.maxeval, nstart=p.nstart, nincrease=p.nincrease,
+                  nbins=p.nbins)
+        e2e_t.append(time.perf_counter() - t)
+    e2e_value = world * samples_per_step / statistics.mean(e2e_t)
+
+    # ---- the plain FP64 one-launch-per-iteration comparator
+    plain_steps = max(1, min(2, args.steps))
+    ctx.vegas(g, flags=cg.FP64 | cg.PLAIN, maxeval=2 * p.nstart, nstart=p.nstart, nbins=p.nbins)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(plain_steps):
+        rp = ctx.vegas(g, flags=cg.FP64 | cg.PLAIN, maxeval=p.maxeval, nstart=p.nstart,
+                       nbins=p.nbins)
+    plain_s = (time.perf_counter() - t) / plain_steps
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": _workload_name(p), "samples_per_step": samples_per_step,
+                   "l2": "flushed before every step (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": f"k_sample<{p.ndim},float>", "kernel_ms": k_ms,
+                     "flops_per_sample": alg_flops_per_sample(p.ndim, p.families),
+                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                   f"{sm_max:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"},
+        "plain_fp64": {"value": world * samples_per_step / plain_s, "unit": UNIT,
+                       "ms_per_step": 1e3 * plain_s,
+                       "speedup_of_value": value / (world * samples_per_step / plain_s)},
+        "result": {"integral": list(res.integral)[: p.ncomp], "error": list(res.error)[: p.ncomp],
+                   "plain_fp64_integral": list(rp.integral)[: p.ncomp],
+                   "plain_fp64_error": list(rp.error)[: p.ncomp]},
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, dt, n = cpu_oracle_rate(p, args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"2 Vegas iterations x {n} points of the same workload, "
+                                          f"FP64 oracle, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    integ.close()
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

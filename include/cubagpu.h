@@ -155,6 +155,58 @@ int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g,
              int64_t nincrease, int64_t nbatch, int nbins, int64_t *neval,
              int *fail, double integral[], double error[], double prob[]);
 
+/* Bytes cv_vegas moves between host and device per call for an integral of
+ * this shape: kernel parameters in (h2d), the final state out (d2h). */
+int cv_vegas_io_bytes(int ndim, int nbins, int64_t *h2d, int64_t *d2h);
+
+/* ------------------------------------------- device-resident integrals */
+/* A Vegas problem whose grid, sums and combination state stay in device
+ * memory between iterations and between runs -- the GPU analogue of the
+ * paper's spinning cores (Sect. 3.2.3), which keep workers alive across
+ * integrations.  cv_vegas is create + reset + run + result + destroy. */
+typedef struct {
+    cv_genz g;
+    int nbins;
+    int flags;                 /* CV_FP64, CV_PLAIN, verbosity            */
+    double epsrel, epsabs;
+    int64_t mineval, maxeval, nstart, nincrease, nbatch;
+} cv_spec;
+
+typedef struct {
+    int64_t neval;
+    int fail;                  /* 0 accuracy reached, 1 maxeval           */
+    int iterations;
+    int status;                /* bit 0: a non-finite iteration result    */
+    double integral[CV_MAX_COMP];
+    double error[CV_MAX_COMP];
+    double prob[CV_MAX_COMP];
+    double chi2[CV_MAX_COMP];
+} cv_result;
+
+typedef struct cv_integral cv_integral;
+
+/* Allocate the device state of one problem (validated as for cv_vegas). */
+int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral **out);
+/* Enqueue a fresh start: uniform grid, empty sums, Sobol index 1. */
+int cv_integral_reset(cv_integral *I);
+/* Enqueue the iterations until the run stops.  Without an accuracy goal
+ * (epsrel = epsabs = 0) this is fully asynchronous: the captured iteration
+ * graph is replayed and later iterations return at once once the device has
+ * stopped the run.  With a goal, the host polls the stop flag every 32
+ * iterations.  CV_PLAIN: one launch per kernel and a host sync per
+ * iteration. */
+int cv_integral_run(cv_integral *I);
+/* Synchronise and copy the results of the last run. */
+int cv_integral_result(cv_integral *I, cv_result *out);
+/* Synchronise and copy the current grid edges[ndim][nbins+1]. */
+int cv_integral_grid(cv_integral *I, double *edges);
+/* Synchronise and copy up to max_iter logged iteration results
+ * I[j][c] = S1/n, var[j][c] (j < 256), ncomp values per iteration. */
+int cv_integral_log(cv_integral *I, int max_iter, double *iter_I, double *iter_var);
+/* Kernels one reset + run enqueues when it runs to the sample budget. */
+int cv_integral_kernels_per_run(const cv_integral *I);
+void cv_integral_destroy(cv_integral *I);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,45 @@ def genz(ndim: int, families, a, u) -> Genz:
     return g
 
 
+class Spec(ctypes.Structure):
+    """cv_spec: a Vegas problem for a device-resident integral."""
+    _fields_ = [
+        ("g", Genz),
+        ("nbins", ctypes.c_int),
+        ("flags", ctypes.c_int),
+        ("epsrel", ctypes.c_double),
+        ("epsabs", ctypes.c_double),
+        ("mineval", ctypes.c_int64),
+        ("maxeval", ctypes.c_int64),
+        ("nstart", ctypes.c_int64),
+        ("nincrease", ctypes.c_int64),
+        ("nbatch", ctypes.c_int64),
+    ]
+
+
+class Result(ctypes.Structure):
+    """cv_result."""
+    _fields_ = [
+        ("neval", ctypes.c_int64),
+        ("fail", ctypes.c_int),
+        ("iterations", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("integral", ctypes.c_double * MAX_COMP),
+        ("error", ctypes.c_double * MAX_COMP),
+        ("prob", ctypes.c_double * MAX_COMP),
+        ("chi2", ctypes.c_double * MAX_COMP),
+    ]
+
+
+def spec(g: Genz, nbins=64, flags=0, epsrel=0.0, epsabs=0.0, mineval=0, maxeval=10 ** 6,
+         nstart=10 ** 4, nincrease=0, nbatch=1000) -> Spec:
+    s = Spec()
+    s.g = g
+    s.nbins, s.flags, s.epsrel, s.epsabs = nbins, flags, epsrel, epsabs
+    s.mineval, s.maxeval, s.nstart, s.nincrease, s.nbatch = mineval, maxeval, nstart, nincrease, nbatch
+    return s
+
+
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -85,6 +124,15 @@ _SIGNATURES = {
     "cv_refine": (_i, [_vp, _i, _i, _vp, _vp]),
     "cv_vegas": (_i, [_vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64, _i64,
                       _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
+    "cv_vegas_io_bytes": (_i, [_i, _i, _P(_i64), _P(_i64)]),
+    "cv_integral_create": (_i, [_vp, _P(Spec), _P(_vp)]),
+    "cv_integral_reset": (_i, [_vp]),
+    "cv_integral_run": (_i, [_vp]),
+    "cv_integral_result": (_i, [_vp, _P(Result)]),
+    "cv_integral_grid": (_i, [_vp, _vp]),
+    "cv_integral_log": (_i, [_vp, _i, _vp, _vp]),
+    "cv_integral_kernels_per_run": (_i, [_vp]),
+    "cv_integral_destroy": (None, [_vp]),
 }
 
 _lib = None
@@ -195,3 +243,64 @@ class Context:
                                 integral.ctypes.data, error.ctypes.data, prob.ctypes.data)
         self._check(rc, "cv_vegas")
         return VegasResult(neval.value, fail.value, integral, error, prob)
+
+    def integral(self, sp: Spec) -> "Integral":
+        return Integral(self, sp)
+
+
+def vegas_io_bytes(ndim: int, nbins: int):
+    h2d, d2h = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib().cv_vegas_io_bytes(ndim, nbins, ctypes.byref(h2d), ctypes.byref(d2h))
+    if rc != OK:
+        raise CubaGpuError(rc, "cv_vegas_io_bytes")
+    return h2d.value, d2h.value
+
+
+class Integral:
+    """cv_integral: one Vegas problem whose state stays on the device."""
+
+    def __init__(self, ctx: Context, sp: Spec):
+        self.ctx = ctx
+        self.spec = sp
+        self._h = ctypes.c_void_p()
+        ctx._check(ctx._lib.cv_integral_create(ctx._h, ctypes.byref(sp), ctypes.byref(self._h)),
+                   "cv_integral_create")
+
+    def close(self):
+        if self._h:
+            self.ctx._lib.cv_integral_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        self.ctx._check(self.ctx._lib.cv_integral_reset(self._h), "cv_integral_reset")
+
+    def run(self):
+        self.ctx._check(self.ctx._lib.cv_integral_run(self._h), "cv_integral_run")
+
+    def result(self) -> Result:
+        r = Result()
+        self.ctx._check(self.ctx._lib.cv_integral_result(self._h, ctypes.byref(r)),
+                        "cv_integral_result")
+        return r
+
+    def grid(self) -> np.ndarray:
+        e = np.zeros((self.spec.g.ndim, self.spec.nbins + 1))
+        self.ctx._check(self.ctx._lib.cv_integral_grid(self._h, e.ctypes.data), "cv_integral_grid")
+        return e
+
+    def log(self, max_iter: int):
+        nc = self.spec.g.ncomp
+        I = np.zeros((max_iter, nc))
+        V = np.zeros((max_iter, nc))
+        self.ctx._check(self.ctx._lib.cv_integral_log(self._h, max_iter, I.ctypes.data,
+                                                      V.ctypes.data), "cv_integral_log")
+        return I, V
+
+    def kernels_per_run(self) -> int:
+        return self.ctx._lib.cv_integral_kernels_per_run(self._h)

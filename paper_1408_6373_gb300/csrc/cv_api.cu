@@ -325,29 +325,39 @@ extern "C" int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_de
 }
 
 // ------------------------------------------------------------ Vegas driver
-namespace {
 
-struct Run {
+// One integral's device-resident run: parameters, state, grid, histogram
+// and the captured iteration graph.
+struct cv_integral {
     cv_ctx *ctx = nullptr;
-    cv_genz g;
-    int nbins = 0;
-    int flags = 0;
-    double epsrel = 0, epsabs = 0;
-    long long mineval = 0, maxeval = 0, nstart = 0, nincrease = 0;
-    // device buffers (one allocation)
+    cv_spec spec;
     void *mem = nullptr;
     DevState *st = nullptr;
     double *edges = nullptr, *H = nullptr, *log_I = nullptr, *log_var = nullptr;
-    int jmax = 0;
-    long long nmax = 0;
-
-    ~Run() {
-        if (mem) cudaFree(mem);
-    }
+    int jmax = 0;              // iterations the sample budget allows
+    long long nmax = 0;        // largest iteration
+    int K = 0;                 // iterations per graph replay
+    cudaGraphExec_t exec = nullptr;
+    int launched_kernels = 0;  // kernels in one run (reset + iterations)
 };
 
+static int check_spec(cv_ctx *ctx, const cv_spec *sp)
+{
+    if (!sp) return fail_msg(ctx, CV_EINVAL, "null spec");
+    int rc = check_genz(ctx, &sp->g);
+    if (rc) return rc;
+    if (sp->nbins < CV_MIN_BINS || sp->nbins > CV_MAX_BINS)
+        return fail_msg(ctx, CV_EINVAL, "nbins %d outside %d..%d", sp->nbins, CV_MIN_BINS, CV_MAX_BINS);
+    if (sp->nstart < 2 || sp->nincrease < 0 || sp->maxeval < sp->nstart || sp->mineval < 0)
+        return fail_msg(ctx, CV_EINVAL, "need 2 <= nstart <= maxeval, nincrease >= 0, mineval >= 0");
+    if ((uint64_t)sp->maxeval >= CV_INDEX_LIMIT)
+        return fail_msg(ctx, CV_EINVAL, "maxeval beyond the 2^52 Sobol index range");
+    if (!(sp->epsrel >= 0) || !(sp->epsabs >= 0)) return fail_msg(ctx, CV_EINVAL, "negative tolerance");
+    return CV_OK;
+}
+
 // Number of iterations the sample budget allows, and the largest one.
-void plan(long long nstart, long long nincrease, long long maxeval, int *jmax, long long *nmax)
+static void plan(long long nstart, long long nincrease, long long maxeval, int *jmax, long long *nmax)
 {
     long long sum = 0, nj = nstart;
     int j = 0;
@@ -360,126 +370,209 @@ void plan(long long nstart, long long nincrease, long long maxeval, int *jmax, l
     *jmax = j;
 }
 
-int run_setup(Run &r)
-{
-    cv_ctx *ctx = r.ctx;
-    const int ndim = r.g.ndim, N = r.nbins;
-    const size_t sz_state = (sizeof(DevState) + 255) & ~(size_t)255;
-    const size_t sz_edges = (((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255;
-    const size_t sz_H = (((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255;
-    const size_t sz_log = (size_t)kLogCap * CV_MAX_COMP * sizeof(double);
-    if (cudaMalloc(&r.mem, sz_state + sz_edges + sz_H + 2 * sz_log) != cudaSuccess) {
-        cudaGetLastError();
-        return fail_msg(ctx, CV_ENOMEM, "device allocation of the Vegas state failed");
-    }
-    char *p = (char *)r.mem;
-    r.st = (DevState *)p;
-    r.edges = (double *)(p + sz_state);
-    r.H = (double *)(p + sz_state + sz_edges);
-    r.log_I = (double *)(p + sz_state + sz_edges + sz_H);
-    r.log_var = (double *)(p + sz_state + sz_edges + sz_H + sz_log);
-
-    DevState h;
-    memset(&h, 0, sizeof(h));
-    h.next_index = 1;  // index 0, the all-zero point, is skipped
-    h.n_cur = r.nstart;
-    std::vector<double> e((size_t)ndim * (N + 1));
-    for (int d = 0; d < ndim; ++d)
-        for (int k = 0; k <= N; ++k) e[(size_t)d * (N + 1) + k] = (double)k / (double)N;
-    CV_CUDA(ctx, cudaMemcpyAsync(r.st, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
-    CV_CUDA(ctx, cudaMemcpyAsync(r.edges, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CV_CUDA(ctx, cudaMemsetAsync(r.H, 0, (size_t)ndim * N * sizeof(double), ctx->stream));
-    // the host buffers above go out of scope: wait for the copies
-    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return CV_OK;
-}
-
 // Enqueue one iteration (sample -> refine -> combine) on `s`.
-int enqueue_iteration(Run &r, cudaStream_t s)
+static int enqueue_iteration(cv_integral *I, cudaStream_t s)
 {
-    cv_ctx *ctx = r.ctx;
+    cv_ctx *ctx = I->ctx;
+    const cv_spec &sp = I->spec;
     cudaStream_t keep = ctx->stream;
     ctx->stream = s;
-    int rc = (r.flags & CV_FP64)
-        ? launch_pass<double>(ctx, &r.g, r.nbins, r.edges, 0, 0, r.nmax, r.st->S1, r.st->S2, r.H, r.st)
-        : launch_pass<float>(ctx, &r.g, r.nbins, r.edges, 0, 0, r.nmax, r.st->S1, r.st->S2, r.H, r.st);
+    int rc = (sp.flags & CV_FP64)
+        ? launch_pass<double>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st)
+        : launch_pass<float>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st);
     ctx->stream = keep;
     if (rc) return rc;
-    cudaError_t e = launch_refine(r.g.ndim, r.nbins, r.H, r.edges, 1, r.st, s);
+    cudaError_t e = launch_refine(sp.g.ndim, sp.nbins, I->H, I->edges, 1, I->st, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "refine kernel launch");
     CombineArgs ca;
-    ca.st = r.st;
-    ca.ncomp = r.g.ncomp;
-    ca.epsrel = r.epsrel;
-    ca.epsabs = r.epsabs;
-    ca.mineval = r.mineval;
-    ca.maxeval = r.maxeval;
-    ca.nstart = r.nstart;
-    ca.nincrease = r.nincrease;
-    ca.log_I = r.log_I;
-    ca.log_var = r.log_var;
+    ca.st = I->st;
+    ca.ncomp = sp.g.ncomp;
+    ca.epsrel = sp.epsrel;
+    ca.epsabs = sp.epsabs;
+    ca.mineval = sp.mineval;
+    ca.maxeval = sp.maxeval;
+    ca.nstart = sp.nstart;
+    ca.nincrease = sp.nincrease;
+    ca.log_I = I->log_I;
+    ca.log_var = I->log_var;
     e = launch_combine(ca, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "combine kernel launch");
     return CV_OK;
 }
 
-int read_stopped(Run &r, int *stopped)
+static int read_stopped(cv_integral *I, int *stopped)
 {
-    cv_ctx *ctx = r.ctx;
-    CV_CUDA(ctx, cudaMemcpyAsync(stopped, &r.st->stopped, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    cv_ctx *ctx = I->ctx;
+    CV_CUDA(ctx, cudaMemcpyAsync(stopped, &I->st->stopped, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return CV_OK;
 }
 
-int run_iterations(Run &r)
+static int capture_graph(cv_integral *I)
 {
-    cv_ctx *ctx = r.ctx;
-    int stopped = 0;
-    if (r.flags & CV_PLAIN) {
-        for (int j = 0; j < r.jmax && !stopped; ++j) {
-            int rc = enqueue_iteration(r, ctx->stream);
-            if (rc) return rc;
-            rc = read_stopped(r, &stopped);
-            if (rc) return rc;
-        }
-        return CV_OK;
-    }
-    // Graph mode: capture K iterations once, replay until the device says stop.
-    // (the occupancy query sets kernel attributes: do it before capturing)
+    cv_ctx *ctx = I->ctx;
+    // the occupancy query sets kernel attributes: do it before capturing
     int occ = 0;
-    int rc0 = occupancy(ctx, r.g.ndim, r.nbins, (r.flags & CV_FP64) != 0, &occ);
-    if (rc0) return rc0;
-    const int K = r.jmax < 32 ? r.jmax : 32;
+    int rc = occupancy(ctx, I->spec.g.ndim, I->spec.nbins, (I->spec.flags & CV_FP64) != 0, &occ);
+    if (rc) return rc;
+    I->K = I->jmax < 32 ? I->jmax : 32;
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     CV_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = CV_OK;
-    for (int j = 0; j < K && rc == CV_OK; ++j) rc = enqueue_iteration(r, ctx->cap_stream);
+    for (int j = 0; j < I->K && rc == CV_OK; ++j) rc = enqueue_iteration(I, ctx->cap_stream);
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
     if (rc) {
         if (graph) cudaGraphDestroy(graph);
         return rc;
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
-    e = cudaGraphInstantiate(&exec, graph, 0);
+    e = cudaGraphInstantiate(&I->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
-    for (int done = 0; done < r.jmax && !stopped; done += K) {
-        e = cudaGraphLaunch(exec, ctx->stream);
-        if (e != cudaSuccess) {
-            cudaGraphExecDestroy(exec);
-            return cuda_fail(ctx, e, "graph launch");
-        }
-        if (done + K < r.jmax) {
-            rc = read_stopped(r, &stopped);
-            if (rc) break;
-        }
-    }
-    cudaGraphExecDestroy(exec);
-    return rc;
+    return CV_OK;
 }
 
-}  // namespace
+extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral **out)
+{
+    if (!ctx || !out) return CV_EINVAL;
+    *out = nullptr;
+    int rc = check_spec(ctx, spec);
+    if (rc) return rc;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    cv_integral *I = new cv_integral();
+    I->ctx = ctx;
+    I->spec = *spec;
+    plan(spec->nstart, spec->nincrease, spec->maxeval, &I->jmax, &I->nmax);
+    const int ndim = spec->g.ndim, N = spec->nbins;
+    const size_t sz_state = (sizeof(DevState) + 255) & ~(size_t)255;
+    const size_t sz_edges = (((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255;
+    const size_t sz_H = (((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255;
+    const size_t sz_log = (size_t)kLogCap * CV_MAX_COMP * sizeof(double);
+    if (cudaMalloc(&I->mem, sz_state + sz_edges + sz_H + 2 * sz_log) != cudaSuccess) {
+        cudaGetLastError();
+        delete I;
+        return fail_msg(ctx, CV_ENOMEM, "device allocation of the Vegas state failed");
+    }
+    char *p = (char *)I->mem;
+    I->st = (DevState *)p;
+    I->edges = (double *)(p + sz_state);
+    I->H = (double *)(p + sz_state + sz_edges);
+    I->log_I = (double *)(p + sz_state + sz_edges + sz_H);
+    I->log_var = (double *)(p + sz_state + sz_edges + sz_H + sz_log);
+    I->launched_kernels = 1 + 3 * I->jmax;
+    *out = I;
+    return CV_OK;
+}
+
+extern "C" void cv_integral_destroy(cv_integral *I)
+{
+    if (!I) return;
+    cudaSetDevice(I->ctx->device);
+    cudaStreamSynchronize(I->ctx->stream);
+    if (I->exec) cudaGraphExecDestroy(I->exec);
+    if (I->mem) cudaFree(I->mem);
+    delete I;
+}
+
+extern "C" int cv_integral_reset(cv_integral *I)
+{
+    if (!I) return CV_EINVAL;
+    cv_ctx *ctx = I->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaError_t e = launch_reset(I->st, I->edges, I->H, I->spec.g.ndim, I->spec.nbins,
+                                 I->spec.nstart, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reset kernel launch");
+    return CV_OK;
+}
+
+extern "C" int cv_integral_run(cv_integral *I)
+{
+    if (!I) return CV_EINVAL;
+    cv_ctx *ctx = I->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    int stopped = 0, rc = CV_OK;
+    if (I->spec.flags & CV_PLAIN) {
+        for (int j = 0; j < I->jmax && !stopped; ++j) {
+            rc = enqueue_iteration(I, ctx->stream);
+            if (rc) return rc;
+            rc = read_stopped(I, &stopped);
+            if (rc) return rc;
+        }
+        return CV_OK;
+    }
+    if (!I->exec) {
+        rc = capture_graph(I);
+        if (rc) return rc;
+    }
+    // Without an accuracy goal the iteration count is fixed and every replay
+    // is enqueued at once; otherwise poll the device between replays.
+    const bool fixed = I->spec.epsrel == 0.0 && I->spec.epsabs == 0.0;
+    for (int done = 0; done < I->jmax && !stopped; done += I->K) {
+        cudaError_t e = cudaGraphLaunch(I->exec, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+        if (!fixed && done + I->K < I->jmax) {
+            rc = read_stopped(I, &stopped);
+            if (rc) return rc;
+        }
+    }
+    return CV_OK;
+}
+
+extern "C" int cv_integral_result(cv_integral *I, cv_result *out)
+{
+    if (!I || !out) return CV_EINVAL;
+    cv_ctx *ctx = I->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    DevState h;
+    CV_CUDA(ctx, cudaMemcpyAsync(&h, I->st, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    memset(out, 0, sizeof(*out));
+    out->neval = h.neval;
+    out->fail = h.stopped ? h.fail : 1;  // iteration cap reached without a decision
+    out->iterations = h.iter;
+    out->status = h.status;
+    for (int c = 0; c < I->spec.g.ncomp; ++c) {
+        out->integral[c] = h.integral[c];
+        out->error[c] = h.error[c];
+        out->prob[c] = h.prob[c];
+        out->chi2[c] = h.chi2[c];
+    }
+    return CV_OK;
+}
+
+extern "C" int cv_integral_grid(cv_integral *I, double *edges)
+{
+    if (!I || !edges) return CV_EINVAL;
+    cv_ctx *ctx = I->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t bytes = (size_t)I->spec.g.ndim * (I->spec.nbins + 1) * sizeof(double);
+    CV_CUDA(ctx, cudaMemcpyAsync(edges, I->edges, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CV_OK;
+}
+
+extern "C" int cv_integral_log(cv_integral *I, int max_iter, double *iter_I, double *iter_var)
+{
+    if (!I || max_iter < 0 || (max_iter > 0 && (!iter_I || !iter_var))) return CV_EINVAL;
+    cv_ctx *ctx = I->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    std::vector<double> lI(kLogCap * CV_MAX_COMP), lV(kLogCap * CV_MAX_COMP);
+    CV_CUDA(ctx, cudaMemcpyAsync(lI.data(), I->log_I, lI.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(lV.data(), I->log_var, lV.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int nc = I->spec.g.ncomp;
+    const int m = max_iter < kLogCap ? max_iter : kLogCap;
+    for (int j = 0; j < m; ++j)
+        for (int c = 0; c < nc; ++c) {
+            iter_I[(size_t)j * nc + c] = lI[(size_t)j * CV_MAX_COMP + c];
+            iter_var[(size_t)j * nc + c] = lV[(size_t)j * CV_MAX_COMP + c];
+        }
+    return CV_OK;
+}
+
+extern "C" int cv_integral_kernels_per_run(const cv_integral *I)
+{
+    return I ? I->launched_kernels : 0;
+}
 
 extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, double epsrel,
                         double epsabs, int flags, int seed, int64_t mineval, int64_t maxeval,
@@ -488,56 +581,56 @@ extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, doub
                         double prob[])
 {
     (void)seed;
-    (void)nbatch;
     if (!ctx) return CV_EINVAL;
-    int rc = check_genz(ctx, g);
-    if (rc) return rc;
+    if (!g) return fail_msg(ctx, CV_EINVAL, "null integrand description");
     if (g->ndim != ndim || g->ncomp != ncomp)
         return fail_msg(ctx, CV_EINVAL, "ndim/ncomp disagree with the integrand description");
-    if (nbins < CV_MIN_BINS || nbins > CV_MAX_BINS)
-        return fail_msg(ctx, CV_EINVAL, "nbins %d outside %d..%d", nbins, CV_MIN_BINS, CV_MAX_BINS);
-    if (nstart < 2 || nincrease < 0 || maxeval < nstart || mineval < 0)
-        return fail_msg(ctx, CV_EINVAL, "need 2 <= nstart <= maxeval, nincrease >= 0, mineval >= 0");
-    if ((uint64_t)maxeval >= CV_INDEX_LIMIT)
-        return fail_msg(ctx, CV_EINVAL, "maxeval beyond the 2^52 Sobol index range");
-    if (!(epsrel >= 0) || !(epsabs >= 0)) return fail_msg(ctx, CV_EINVAL, "negative tolerance");
     if (!neval || !fail || !integral || !error || !prob) return fail_msg(ctx, CV_EINVAL, "null output");
-    CV_CUDA(ctx, cudaSetDevice(ctx->device));
-
-    Run r;
-    r.ctx = ctx;
-    r.g = *g;
-    r.nbins = nbins;
-    r.flags = flags;
-    r.epsrel = epsrel;
-    r.epsabs = epsabs;
-    r.mineval = mineval;
-    r.maxeval = maxeval;
-    r.nstart = nstart;
-    r.nincrease = nincrease;
-    plan(nstart, nincrease, maxeval, &r.jmax, &r.nmax);
-    rc = run_setup(r);
+    cv_spec sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.g = *g;
+    sp.nbins = nbins;
+    sp.flags = flags;
+    sp.epsrel = epsrel;
+    sp.epsabs = epsabs;
+    sp.mineval = mineval;
+    sp.maxeval = maxeval;
+    sp.nstart = nstart;
+    sp.nincrease = nincrease;
+    sp.nbatch = nbatch;
+    cv_integral *I = nullptr;
+    int rc = cv_integral_create(ctx, &sp, &I);
     if (rc) return rc;
-    rc = run_iterations(r);
+    cv_result res;
+    rc = cv_integral_reset(I);
+    if (!rc) rc = cv_integral_run(I);
+    if (!rc) rc = cv_integral_result(I, &res);
+    if (!rc && (flags & CV_VERBOSE_MASK)) {
+        std::vector<double> lI((size_t)kLogCap * ncomp), lV((size_t)kLogCap * ncomp);
+        if (cv_integral_log(I, kLogCap, lI.data(), lV.data()) == CV_OK)
+            for (int j = 0; j < res.iterations && j < kLogCap; ++j)
+                for (int c = 0; c < ncomp; ++c)
+                    fprintf(stderr, "cv_vegas iteration %d comp %d: %.15g +- %.6g\n", j + 1, c,
+                            lI[(size_t)j * ncomp + c], std::sqrt(std::fabs(lV[(size_t)j * ncomp + c])));
+    }
+    cv_integral_destroy(I);
     if (rc) return rc;
-    DevState h;
-    CV_CUDA(ctx, cudaMemcpyAsync(&h, r.st, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
-    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    *neval = h.neval;
-    *fail = h.stopped ? h.fail : 1;  // iteration cap reached without a decision
+    *neval = res.neval;
+    *fail = res.fail;
     for (int c = 0; c < ncomp; ++c) {
-        integral[c] = h.integral[c];
-        error[c] = h.error[c];
-        prob[c] = h.prob[c];
+        integral[c] = res.integral[c];
+        error[c] = res.error[c];
+        prob[c] = res.prob[c];
     }
-    if (flags & CV_VERBOSE_MASK) {
-        std::vector<double> lI(kLogCap * CV_MAX_COMP), lV(kLogCap * CV_MAX_COMP);
-        cudaMemcpy(lI.data(), r.log_I, lI.size() * sizeof(double), cudaMemcpyDeviceToHost);
-        cudaMemcpy(lV.data(), r.log_var, lV.size() * sizeof(double), cudaMemcpyDeviceToHost);
-        for (int j = 0; j < h.iter && j < kLogCap; ++j)
-            for (int c = 0; c < ncomp; ++c)
-                fprintf(stderr, "cv_vegas iteration %d comp %d: %.15g +- %.6g\n", j + 1, c,
-                        lI[j * CV_MAX_COMP + c], std::sqrt(std::fabs(lV[j * CV_MAX_COMP + c])));
-    }
+    return CV_OK;
+}
+
+extern "C" int cv_vegas_io_bytes(int ndim, int nbins, int64_t *h2d, int64_t *d2h)
+{
+    if (!h2d || !d2h || ndim < 1 || nbins < 1) return CV_EINVAL;
+    // kernel parameters of one iteration (integrand + launch arguments) and
+    // the final state read back; the grid and state start on the device.
+    *h2d = (int64_t)sizeof(SampleArgs<double>) + (int64_t)sizeof(CombineArgs);
+    *d2h = (int64_t)sizeof(DevState);
     return CV_OK;
 }

@@ -98,6 +98,8 @@ cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
 cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges,
                           int zero_hist, const DevState *st, cudaStream_t s);
 cudaError_t launch_combine(const CombineArgs &a, cudaStream_t s);
+cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int nbins,
+                         long long nstart, cudaStream_t s);
 
 inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64) {
     // grid {e, w} pairs plus the block histogram

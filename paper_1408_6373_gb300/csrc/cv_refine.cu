@@ -215,6 +215,33 @@ __global__ void k_combine(const CombineArgs A)
     }
 }
 
+// Start of a run: uniform grid e_k = k/N, empty histogram and sums, Sobol
+// index 1 (index 0, the all-zero point, is skipped).
+__global__ void k_reset(DevState *st, double *edges, double *H, int ndim, int N, long long nstart)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = tid; i < ndim * (N + 1); i += stride) {
+        const int k = i % (N + 1);
+        edges[i] = (double)k / (double)N;
+    }
+    for (int i = tid; i < ndim * N; i += stride) H[i] = 0.0;
+    int *w = reinterpret_cast<int *>(st);
+    for (int i = tid; i < (int)(sizeof(DevState) / sizeof(int)); i += stride) w[i] = 0;
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->next_index = 1ull;
+        st->n_cur = nstart;
+    }
+}
+
+cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int nbins,
+                         long long nstart, cudaStream_t s)
+{
+    k_reset<<<1, 256, 0, s>>>(st, edges, H, ndim, nbins, nstart);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, int zero_hist,
                           const DevState *st, cudaStream_t s)
 {

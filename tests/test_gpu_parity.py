@@ -243,3 +243,61 @@ def test_invalid_arguments_rejected(ctx):
     bad = cg.genz(3, [9], 1.0, 0.5)
     with pytest.raises(cg.CubaGpuError):
         ctx.vegas(bad)
+
+
+# ------------------------------------------------------------------ integral handle
+def test_integral_handle_reruns_identically_and_matches_cv_vegas(ctx):
+    ndim = 5
+    a, u = _params(ndim, 2, 11)
+    g = cg.genz(ndim, [cg.GAUSSIAN, cg.C0], a, u)
+    sp = cg.spec(g, nbins=64, flags=cg.FP64, maxeval=6 * 8000, nstart=8000)
+    I = ctx.integral(sp)
+    I.reset()
+    I.run()
+    r1 = I.result()
+    e1 = I.grid()
+    I.reset()
+    I.run()
+    r2 = I.result()
+    assert r1.iterations == 6 and r1.neval == 48000
+    assert list(r1.integral)[:2] == pytest.approx(list(r2.integral)[:2], rel=1e-14)
+    assert np.max(np.abs(I.grid() - e1)) <= 1e-15
+    rv = ctx.vegas(g, flags=cg.FP64, maxeval=6 * 8000, nstart=8000, nbins=64)
+    assert rv.integral[0] == pytest.approx(r1.integral[0], rel=1e-14)
+    # the per-iteration log and final grid match the oracle's
+    p = O.Problem(ndim, [O.GAUSSIAN, O.C0], a, u, nbins=64)
+    o = O.vegas(p, maxeval=6 * 8000, nstart=8000)
+    lI, lV = I.log(6)
+    np.testing.assert_allclose(lI, o.iter_I, rtol=1e-12)
+    np.testing.assert_allclose(lV, o.iter_var, rtol=1e-9)
+    assert np.max(np.abs(I.grid() - o.edges)) <= 1e-13
+    assert I.kernels_per_run() == 1 + 3 * 6
+    I.close()
+
+
+def test_fp32_iterations_with_grid_handed_to_oracle(ctx):
+    # per-iteration parity of the FP32 path: each iteration's sums against
+    # the oracle on the GPU's own grid, and the GPU refinement against the
+    # oracle's refinement of the GPU histogram.
+    ndim, N, n = 8, 128, 200000
+    a, u = _params(ndim, 4, 21)
+    fams = [O.OSCILLATORY, O.PRODUCT_PEAK, O.CORNER_PEAK, O.GAUSSIAN]
+    g = cg.genz(ndim, fams, a, u)
+    p = O.Problem(ndim, fams, a, u, nbins=N, bits=23, fp32_decide=True)
+    edges = O.grid_uniform(ndim, N)
+    start = 1
+    for it in range(4):
+        S1, S2, H = _gpu_sample(ctx, g, edges, start, n, 0)
+        oS1, oS2, oH = O.sample(p, edges, start, n, nthreads=8)
+        for c in range(4):
+            mag = math.sqrt(n * oS2[c])
+            assert abs(S1[c] - oS1[c]) <= 1e-6 * mag, (it, c, S1[c], oS1[c])
+            assert abs(S2[c] - oS2[c]) <= 1e-6 * oS2[c]
+        e = torch.tensor(edges, device="cuda")
+        h = torch.tensor(H, device="cuda")
+        ctx.refine(ndim, N, h, e)
+        ctx.synchronize()
+        new = e.cpu().numpy()
+        assert np.max(np.abs(new - O.refine(edges, H))) <= 1e-14
+        edges = new
+        start += n
