@@ -246,16 +246,44 @@ static int sample_grid(cv_ctx *ctx, int occ, long long n)
     return (int)want;
 }
 
+// Uniform constants of the FP32 map for N bins (see MapParams).
+static MapParams make_map(int N)
+{
+    MapParams m;
+    memset(&m, 0, sizeof(m));
+    m.pow2 = (N & (N - 1)) == 0;
+    if (m.pow2) {
+        int L = 0;
+        while ((1 << L) < N) ++L;
+        m.L = L;
+        m.sF = 9 - L;
+        m.mF = 0x7fffffu & ~((1u << L) - 1u);
+        m.expL = (unsigned)(127 - L) << 23;
+        m.twoNegL = ldexpf(1.0f, -L);
+        if (L >= 5) {
+            m.sA = 27 - L;
+            m.mA = ((1u << (L - 5)) - 1u) << 5;
+            m.sB = 27;
+        } else {
+            m.sA = 0;
+            m.mA = 0;
+            m.sB = 32 - L;
+        }
+    }
+    return m;
+}
+
 template <typename Real>
 static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *edges,
                        unsigned long long start, long long n, long long n_grid,
-                       double *S1, double *S2, double *H, const DevState *st)
+                       double *S1, double *S2, double *H, DevState *st)
 {
     SampleArgs<Real> a;
     memset(&a, 0, sizeof(a));
     fill_params<Real>(g, &a.g);
     a.nbins = nbins;
     a.chunk_min = 4;
+    a.map = make_map(nbins);
     a.edges = edges;
     a.S1 = S1;
     a.S2 = S2;
@@ -319,7 +347,7 @@ extern "C" int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_de
     if (nbins < CV_MIN_BINS || nbins > CV_MAX_BINS) return fail_msg(ctx, CV_EINVAL, "nbins out of range");
     if (!hist_dev || !edges_dev) return fail_msg(ctx, CV_EINVAL, "null buffer");
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
-    cudaError_t e = launch_refine(ndim, nbins, const_cast<double *>(hist_dev), edges_dev, 0, nullptr, ctx->stream);
+    cudaError_t e = launch_refine(ndim, nbins, const_cast<double *>(hist_dev), edges_dev, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "refine kernel launch");
     return CV_OK;
 }
@@ -382,8 +410,6 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
         : launch_pass<float>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st);
     ctx->stream = keep;
     if (rc) return rc;
-    cudaError_t e = launch_refine(sp.g.ndim, sp.nbins, I->H, I->edges, 1, I->st, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "refine kernel launch");
     CombineArgs ca;
     ca.st = I->st;
     ca.ncomp = sp.g.ncomp;
@@ -395,8 +421,8 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
     ca.nincrease = sp.nincrease;
     ca.log_I = I->log_I;
     ca.log_var = I->log_var;
-    e = launch_combine(ca, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "combine kernel launch");
+    cudaError_t e = launch_refine_combine(sp.g.ndim, sp.nbins, I->H, I->edges, ca, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refine/combine kernel launch");
     return CV_OK;
 }
 
@@ -458,7 +484,7 @@ extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral 
     I->H = (double *)(p + sz_state + sz_edges);
     I->log_I = (double *)(p + sz_state + sz_edges + sz_H);
     I->log_var = (double *)(p + sz_state + sz_edges + sz_H + sz_log);
-    I->launched_kernels = 1 + 3 * I->jmax;
+    I->launched_kernels = 1 + 2 * I->jmax;
     *out = I;
     return CV_OK;
 }

@@ -77,55 +77,40 @@ __device__ __forceinline__ void sobol_step(W (&X)[NDIM], unsigned long long q)
         X[d] ^= Dir<W>::v(d, 4) ^ Dir<W>::v(d, 5 + c);
 }
 
-// ------------------------------------------------------------ precision traits
-template <typename Real> struct Prec;
+// ------------------------------------------------------------ maps
+// FP32 path: the 32-bit word is the top half of the 64-bit Sobol word and y
+// keeps its top 23 bits, so frac is exact as the mantissa of 1.frac minus 1.
+// FP64 path: 64-bit word, y keeps 52 bits.
+//
+// Shared-memory layout of a block's grid and histogram.  For N = 2^L with
+// L >= 5 the bins of an axis are stored stratum-major: bin k = j R + r
+// (j = k / R the 1/32-stratum, R = N/32) sits at slot r*32 + j.  The 32
+// lanes of a warp always hold 32 distinct strata, so their 32 slots fall in
+// 32 distinct banks -- every grid gather and histogram atomic of a warp is
+// conflict-free.  Other N use slot = k.
 
-// FP32 path: 32-bit word = top half of the 64-bit word; y has 23 fraction
-// bits, so frac is exact as the mantissa of 1.frac minus 1.
-template <> struct Prec<float> {
-    using Word = unsigned int;
-    using Real2 = float2;
-    static constexpr int kBits = 23;
-    static __device__ __forceinline__ int bin(Word X, unsigned N, float *frac)
-    {
-        const unsigned t = (X >> 9) * N;  // Y * N < 2^31
-        *frac = __uint_as_float(0x3f800000u | (t & 0x7fffffu)) - 1.0f;
-        return (int)(t >> 23);
-    }
-    static __device__ __forceinline__ int bin_only(Word X, unsigned N)
-    {
-        return (int)(((X >> 9) * N) >> 23);
-    }
-    static __device__ __forceinline__ float2 stage(double e0, double e1)
-    {
-        return make_float2(__double2float_rn(e0), __double2float_rn(e1 - e0));
-    }
-};
-
-// FP64 path: 64-bit word, y has 52 fraction bits.
-template <> struct Prec<double> {
-    using Word = unsigned long long;
-    using Real2 = double2;
-    static constexpr int kBits = 52;
-    static __device__ __forceinline__ int bin(Word X, unsigned N, double *frac)
-    {
-        const unsigned long long t = (X >> 12) * (unsigned long long)N;  // < 2^60
-        *frac = __longlong_as_double((long long)(0x3ff0000000000000ull |
-                                                 (t & 0xfffffffffffffull))) - 1.0;
-        return (int)(t >> 52);
-    }
-    static __device__ __forceinline__ int bin_only(Word X, unsigned N)
-    {
-        return (int)(((X >> 12) * (unsigned long long)N) >> 52);
-    }
-    static __device__ __forceinline__ double2 stage(double e0, double e1)
-    {
-        return make_double2(e0, e1 - e0);
-    }
-};
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// slot of bin k (staging and flush run once per block; the sampling loop
+// computes the slot straight from the Sobol word)
+__device__ __forceinline__ int slot_of_bin(int k, const MapParams &m)
+{
+    if (m.pow2 && m.L >= 5) return ((k & ((1 << (m.L - 5)) - 1)) << 5) | (k >> (m.L - 5));
+    return k;
+}
+__device__ __forceinline__ int bin_of_slot(int p, const MapParams &m)
+{
+    if (m.pow2 && m.L >= 5) return ((p & 31) << (m.L - 5)) | (p >> 5);
+    return p;
+}
 
 // ------------------------------------------------------------ integrands
 template <int E>
@@ -150,7 +135,7 @@ __device__ __forceinline__ float genz_f32(int fam, const float *p0, const float 
 {
     switch (fam) {
     case CV_OSCILLATORY: {
-        float t = q0;  // phase in turns
+        float t = q0;  // phase in turns, reduced to [-1/2, 1/2]
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) t = __fmaf_rn(p0[d], x[d], t);
         t -= rintf(t);
@@ -163,13 +148,13 @@ __device__ __forceinline__ float genz_f32(int fam, const float *p0, const float 
             const float dx = x[d] - p1[d];
             P *= __fmaf_rn(dx, dx, p0[d]);
         }
-        return __frcp_rn(P);
+        return rcp_approx(P);
     }
     case CV_CORNER_PEAK: {
         float s = 1.0f;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(p0[d], x[d], s);
-        return ipow<NDIM + 1>(__frcp_rn(s));
+        return ipow<NDIM + 1>(rcp_approx(s));
     }
     case CV_GAUSSIAN: {
         float s = 0.0f;
@@ -285,19 +270,124 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// ------------------------------------------------------------ sampling steps
+// Shared-memory views of one block.
+template <typename Real> struct Smem;
+template <> struct Smem<float> {
+    float *e, *w, *h;  // [NDIM*N] each: e_k, w_k (N w_k on the power-of-two map), histogram
+};
+template <> struct Smem<double> {
+    double2 *ew;       // [NDIM*N] {e_k, w_k}
+    double *h;         // [NDIM*N]
+};
+
+// Map one FP32 coordinate: returns x, multiplies the Jacobian, and gives the
+// histogram slot.  Power-of-two N: frac/N = 2^-L (1.frac) - 2^-L straight
+// from the word's bits, x = fma(N w, frac/N, e) (the same value as
+// fma(w, frac, e): the scalings are exact), J *= N w.
+template <bool POW2>
+__device__ __forceinline__ float map_f32(unsigned X, int d, int N, const MapParams &m,
+                                         const Smem<float> &sm, float &J, int &slot)
+{
+    if (POW2) {
+        const unsigned fb = (X >> m.sF) & m.mF;
+        const float fs = __uint_as_float(m.expL | fb) - m.twoNegL;
+        const int p = d * N + (int)(((X >> m.sA) & m.mA) | (X >> m.sB));
+        const float w = sm.w[p];
+        J *= w;
+        slot = p;
+        return __fmaf_rn(w, fs, sm.e[p]);
+    } else {
+        const unsigned t = (X >> 9) * (unsigned)N;
+        const float frac = __uint_as_float(0x3f800000u | (t & 0x7fffffu)) - 1.0f;
+        const int p = d * N + (int)(t >> 23);
+        const float w = sm.w[p];
+        J = J * ((float)N * w);
+        slot = p;
+        return __fmaf_rn(w, frac, sm.e[p]);
+    }
+}
+
+__device__ __forceinline__ double map_f64(unsigned long long X, int d, int N,
+                                          const Smem<double> &sm, double &J, int &slot)
+{
+    const unsigned long long t = (X >> 12) * (unsigned long long)N;  // < 2^60
+    const double frac = __longlong_as_double((long long)(0x3ff0000000000000ull |
+                                                         (t & 0xfffffffffffffull))) - 1.0;
+    const int p = d * N + (int)(t >> 52);
+    const double2 ew = sm.ew[p];
+    J = J * ((double)N * ew.y);
+    slot = p;
+    return __fma_rn(ew.y, frac, ew.x);
+}
+
+template <typename Real> struct Word;
+template <> struct Word<float> { using type = unsigned int; };
+template <> struct Word<double> { using type = unsigned long long; };
+
+// nsteps consecutive 32-point blocks starting at block q0.  EDGE: the range
+// touches the first or last (partial) block and every index is checked.
+template <int NDIM, typename Real, bool POW2, bool EDGE>
+__device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<Real> &sm,
+                                          typename Word<Real>::type (&X)[NDIM],
+                                          unsigned long long q0, unsigned nsteps,
+                                          unsigned long long start, unsigned long long end,
+                                          int lane, Acc<Real> (&s1)[CV_MAX_COMP],
+                                          Acc<Real> (&s2)[CV_MAX_COMP])
+{
+    const int N = A.nbins;
+    const int ncomp = A.g.ncomp;
+    for (unsigned st = 0; st < nsteps; ++st) {
+        const unsigned long long q = q0 + st;
+        bool valid = true;
+        if (EDGE) {
+            const unsigned long long i = q * 32ull + (unsigned long long)lane;
+            valid = (i >= start) && (i < end);
+        }
+        Real x[NDIM];
+        int slot[NDIM];
+        Real J = Real(1);
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            if constexpr (sizeof(Real) == 4)
+                x[d] = map_f32<POW2>(X[d], d, N, A.map, sm, J, slot[d]);
+            else
+                x[d] = map_f64(X[d], d, N, sm, J, slot[d]);
+        }
+        Real f0 = Real(0);
+#pragma unroll
+        for (int c = 0; c < CV_MAX_COMP; ++c) {
+            if (c < ncomp) {
+                const Real f = genz_eval<NDIM>(A.g.family[c], A.g.p0[c], A.g.p1[c], A.g.q0[c], x);
+                const Real v = J * f;
+                if (valid) {
+                    s1[c].add(v);
+                    s2[c].add(v * v);
+                }
+                if (c == 0) f0 = v;
+            }
+        }
+        if (valid) {
+            const Real h = f0 * f0;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[slot[d]], h);
+        }
+        if (st + 1 < nsteps) sobol_step<NDIM, typename Word<Real>::type>(X, q);
+    }
+}
+
 // ------------------------------------------------------------ the kernel
-template <int NDIM, typename Real>
+template <int NDIM, typename Real, bool POW2>
 __global__ void __launch_bounds__(kBlock)
 k_sample(const __grid_constant__ SampleArgs<Real> A)
 {
-    using P = Prec<Real>;
-    using W = typename P::Word;
-    using Real2 = typename P::Real2;
-
+    using W = typename Word<Real>::type;
     unsigned long long start;
     long long n;
     if (A.st) {
-        if (*(volatile const int *)&A.st->stopped) return;
+        const int stopped = *(volatile const int *)&A.st->stopped;
+        if (blockIdx.x == 0 && threadIdx.x == 0) A.st->pass_active = stopped ? 0 : 1;
+        if (stopped) return;
         start = A.st->next_index;
         n = A.st->n_cur;
     } else {
@@ -308,14 +398,29 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
     const int ncomp = A.g.ncomp;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real2 *sg = reinterpret_cast<Real2 *>(smem_raw);          // [NDIM*N] {e_k, w_k}
-    Real *sh = reinterpret_cast<Real *>(sg + NDIM * N);        // [NDIM*N] histogram
-
-    for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-        const int d = idx / N, k = idx - d * N;
-        const double *e = A.edges + (size_t)d * (N + 1);
-        sg[idx] = P::stage(e[k], e[k + 1]);
-        sh[idx] = Real(0);
+    Smem<Real> sm;
+    if constexpr (sizeof(Real) == 4) {
+        sm.e = reinterpret_cast<float *>(smem_raw);
+        sm.w = sm.e + NDIM * N;
+        sm.h = sm.w + NDIM * N;
+        for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+            const int d = idx / N, k = idx - d * N;
+            const double *e = A.edges + (size_t)d * (N + 1);
+            const int p = d * N + slot_of_bin(k, A.map);
+            const double w = e[k + 1] - e[k];
+            sm.e[p] = __double2float_rn(e[k]);
+            sm.w[p] = __double2float_rn(POW2 ? (double)N * w : w);
+            sm.h[p] = 0.0f;
+        }
+    } else {
+        sm.ew = reinterpret_cast<double2 *>(smem_raw);
+        sm.h = reinterpret_cast<double *>(sm.ew + NDIM * N);
+        for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+            const int d = idx / N, k = idx - d * N;
+            const double *e = A.edges + (size_t)d * (N + 1);
+            sm.ew[idx] = make_double2(e[k], e[k + 1] - e[k]);
+            sm.h[idx] = 0.0;
+        }
     }
     __syncthreads();
 
@@ -329,7 +434,6 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
     unsigned long long plen = (nblk + twarps - 1) / twarps;
     if (plen < (unsigned long long)A.chunk_min) plen = A.chunk_min;
     const unsigned long long nchunk = (nblk + plen - 1) / plen;
-    const Real Nr = (Real)N;
 
     Acc<Real> s1[CV_MAX_COMP], s2[CV_MAX_COMP];
 
@@ -338,41 +442,11 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
         const unsigned long long q1 = min(q0 + plen, qb);
         W X[NDIM];
         sobol_skip<NDIM, W>(X, q0, lane);
-        for (unsigned long long q = q0; q < q1; ++q) {
-            const unsigned long long i = q * 32ull + (unsigned long long)lane;
-            const bool valid = (i >= start) && (i < end);
-            Real x[NDIM];
-            Real J = Real(1);
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d) {
-                Real frac;
-                const int k = P::bin(X[d], (unsigned)N, &frac);
-                const Real2 ew = sg[d * N + k];
-                x[d] = fma_rn(ew.y, frac, ew.x);
-                J = J * (Nr * ew.y);
-            }
-            Real f0 = Real(0);
-#pragma unroll
-            for (int c = 0; c < CV_MAX_COMP; ++c) {
-                if (c < ncomp) {
-                    const Real f = genz_eval<NDIM>(A.g.family[c], A.g.p0[c], A.g.p1[c],
-                                                   A.g.q0[c], x);
-                    const Real v = J * f;
-                    if (valid) {
-                        s1[c].add(v);
-                        s2[c].add(v * v);
-                    }
-                    if (c == 0) f0 = v;
-                }
-            }
-            const Real h = f0 * f0;
-            if (valid && h != Real(0)) {
-#pragma unroll
-                for (int d = 0; d < NDIM; ++d)
-                    atomicAdd(&sh[d * N + P::bin_only(X[d], (unsigned)N)], h);
-            }
-            if (q + 1 < q1) sobol_step<NDIM, W>(X, q);
-        }
+        const bool interior = (q0 * 32ull >= start) && (q1 * 32ull <= end);
+        if (interior)
+            run_steps<NDIM, Real, POW2, false>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
+        else
+            run_steps<NDIM, Real, POW2, true>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
     }
 
     // FP64 reduction: warp shuffle, then across the block's warps.
@@ -396,9 +470,13 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
         const int c = threadIdx.x >> 1;
         atomicAdd((threadIdx.x & 1) ? &A.S2[c] : &A.S1[c], t);
     }
-    for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-        const Real v = sh[idx];
-        if (v != Real(0)) atomicAdd(&A.H[idx], (double)v);
+    for (int p = threadIdx.x; p < NDIM * N; p += blockDim.x) {
+        const Real v = sm.h[p];
+        if (v != Real(0)) {
+            int d = p / N, k = p - d * N;
+            if constexpr (sizeof(Real) == 4) k = bin_of_slot(k, A.map);
+            atomicAdd(&A.H[d * N + k], (double)v);
+        }
     }
 }
 
@@ -438,11 +516,25 @@ k_sobol(unsigned long long start, long long n, int shift, unsigned long long *Y)
 
 // ------------------------------------------------------------ launchers
 template <int NDIM, typename Real>
+static void *sample_fn(bool pow2)
+{
+    if constexpr (sizeof(Real) == 4)
+        return pow2 ? (void *)k_sample<NDIM, float, true> : (void *)k_sample<NDIM, float, false>;
+    else
+        return (void *)k_sample<NDIM, double, false>;
+}
+
+template <int NDIM, typename Real>
 cudaError_t launch_sample(const SampleArgs<Real> &a, int grid, cudaStream_t s)
 {
     // (sample_occupancy, always called first, sets the shared-memory limit)
     const size_t smem = sample_smem_bytes(NDIM, a.nbins, sizeof(Real) == 8);
-    k_sample<NDIM, Real><<<grid, kBlock, smem, s>>>(a);
+    if constexpr (sizeof(Real) == 4) {
+        if (a.map.pow2) k_sample<NDIM, float, true><<<grid, kBlock, smem, s>>>(a);
+        else k_sample<NDIM, float, false><<<grid, kBlock, smem, s>>>(a);
+    } else {
+        k_sample<NDIM, double, false><<<grid, kBlock, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -450,11 +542,14 @@ template <int NDIM, typename Real>
 cudaError_t sample_occupancy(int nbins, int *blocks_per_sm)
 {
     const size_t smem = sample_smem_bytes(NDIM, nbins, sizeof(Real) == 8);
-    cudaError_t e = cudaFuncSetAttribute(k_sample<NDIM, Real>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sample_smem_bytes(NDIM, CV_MAX_BINS, sizeof(Real) == 8));
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sample<NDIM, Real>,
+    const bool pow2 = (nbins & (nbins - 1)) == 0;
+    const int maxsmem = (int)sample_smem_bytes(NDIM, CV_MAX_BINS, sizeof(Real) == 8);
+    for (int v = 0; v < 2; ++v) {
+        cudaError_t e = cudaFuncSetAttribute(sample_fn<NDIM, Real>(v == 1),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sample_fn<NDIM, Real>(pow2),
                                                          kBlock, smem);
 }
 

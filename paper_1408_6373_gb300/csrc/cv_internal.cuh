@@ -25,6 +25,7 @@ struct DevState {
     int stopped;                    // 1 once the run has terminated
     int fail;                       // Cuba's fail: 0 accuracy reached, 1 maxeval
     int status;                     // bit 0: a non-finite iteration result
+    int pass_active;                // the last sampling launch ran (set by that launch)
     double S1[CV_MAX_COMP];         // sum J f_c of the running iteration
     double S2[CV_MAX_COMP];         // sum (J f_c)^2
     // inverse-variance combination (West's weighted incremental update)
@@ -57,6 +58,16 @@ struct GenzParams {
     Real q0[CV_MAX_COMP];
 };
 
+// Uniform constants of the FP32 map for N = 2^L (see cv_device.cuh).
+struct MapParams {
+    int pow2;                       // N is a power of two
+    int L;                          // log2 N
+    unsigned sF, mF;                // mantissa bits of frac: (X >> sF) & mF
+    unsigned expL;                  // exponent field of 2^-L
+    float twoNegL;                  // 2^-L
+    unsigned sA, mA, sB;            // slot = ((X >> sA) & mA) | (X >> sB)
+};
+
 // Arguments of one sampling launch.  When `st` is non-null the launch reads
 // its index range from the device state (and returns at once if the run has
 // stopped), which is what lets a captured graph replay iterations whose
@@ -66,13 +77,14 @@ struct SampleArgs {
     GenzParams<Real> g;
     int nbins;
     int chunk_min;                  // minimum warp-steps per chunk
+    MapParams map;
     const double *edges;            // [ndim][nbins+1]
     double *S1;                     // [ncomp]
     double *S2;                     // [ncomp]
     double *H;                      // [ndim][nbins]
     unsigned long long start;
     long long n;
-    const DevState *st;
+    DevState *st;
 };
 
 struct CombineArgs {
@@ -95,9 +107,9 @@ cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
                          unsigned long long *Y, int grid, cudaStream_t s);
 
 // cv_refine.cu
-cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges,
-                          int zero_hist, const DevState *st, cudaStream_t s);
-cudaError_t launch_combine(const CombineArgs &a, cudaStream_t s);
+cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, cudaStream_t s);
+cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
+                                  const CombineArgs &a, cudaStream_t s);
 cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int nbins,
                          long long nstart, cudaStream_t s);
 

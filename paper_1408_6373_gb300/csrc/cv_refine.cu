@@ -54,105 +54,122 @@ __device__ double gamma_p(double a, double x)
     return 1.0 - Q;
 }
 
-__global__ void __launch_bounds__(256)
-k_refine(int N, double *H, double *edges, int zero_hist, const DevState *st)
+__device__ __forceinline__ double warp_sum_d(double v)
 {
-    if (st && *(volatile const int *)&st->stopped) return;
-    const int d = blockIdx.x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Refine axis `d` of the grid in place (one CTA of 256 threads, N <= 256).
+// Every reduction has a fixed order, so the result is reproducible.
+__device__ void refine_axis(int d, int N, double *H, double *edges, int zero_hist)
+{
     double *Hd = H + (size_t)d * N;
     double *e = edges + (size_t)d * (N + 1);
-    __shared__ double sH[CV_MAX_BINS], sh[CV_MAX_BINS], sr[CV_MAX_BINS];
+    __shared__ double sH[CV_MAX_BINS], sr[CV_MAX_BINS];
     __shared__ double sC[CV_MAX_BINS + 1], se[CV_MAX_BINS + 1];
-    __shared__ double s_sum, s_R;
-    __shared__ int s_use;
+    __shared__ double wred[8];
+    const int k = threadIdx.x;            // bin of this thread
+    const int lane = k & 31, warp = k >> 5;
 
-    for (int k = threadIdx.x; k < N; k += blockDim.x) sH[k] = Hd[k];
-    for (int k = threadIdx.x; k <= N; k += blockDim.x) se[k] = e[k];
+    if (k < N) sH[k] = Hd[k];
+    for (int i = k; i <= N; i += blockDim.x) se[i] = e[i];
     __syncthreads();
-    // smoothing over the neighbours
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        double h;
-        if (k == 0) h = __ddiv_rn(__dadd_rn(sH[0], sH[1]), 2.0);
-        else if (k == N - 1) h = __ddiv_rn(__dadd_rn(sH[N - 2], sH[N - 1]), 2.0);
-        else h = __ddiv_rn(__dadd_rn(__dadd_rn(sH[k - 1], sH[k]), sH[k + 1]), 3.0);
-        sh[k] = h;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int usable = 0, finite = 1;
-        double s = 0.0;
-        for (int k = 0; k < N; ++k) {
-            if (!isfinite(sH[k])) finite = 0;
-            if (sH[k] != 0.0) usable = 1;
-            s = __dadd_rn(s, sh[k]);
+    const bool bad = k < N && !isfinite(sH[k]);
+    const bool nz = k < N && sH[k] != 0.0;
+    const int any_bad = __syncthreads_or(bad);
+    const int any_nz = __syncthreads_or(nz);
+    if (!any_bad && any_nz) {
+        // smoothing over the neighbours
+        double h = 0.0;
+        if (k < N) {
+            if (k == 0) h = __ddiv_rn(__dadd_rn(sH[0], sH[1]), 2.0);
+            else if (k == N - 1) h = __ddiv_rn(__dadd_rn(sH[N - 2], sH[N - 1]), 2.0);
+            else h = __ddiv_rn(__dadd_rn(__dadd_rn(sH[k - 1], sH[k]), sH[k + 1]), 3.0);
         }
-        s_sum = s;
-        s_use = usable && finite;
-    }
-    __syncthreads();
-    if (s_use) {
-        const double s = s_sum;
-        for (int k = threadIdx.x; k < N; k += blockDim.x) {
-            const double h = sh[k];
-            double r;
+        // s = sum_k h_k
+        double ws = warp_sum_d(h);
+        if (lane == 0) wred[warp] = ws;
+        __syncthreads();
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s = __dadd_rn(s, wred[w]);
+        __syncthreads();
+        // compression
+        double r = 0.0;
+        if (k < N) {
             if (h == 0.0) r = 0.0;
             else if (h == s) r = 1.0;
             else {
                 const double q = __ddiv_rn(__dadd_rn(1.0, -__ddiv_rn(h, s)), log(__ddiv_rn(s, h)));
                 r = __dmul_rn(q, sqrt(q));
             }
-            sr[k] = r;
         }
+        const double wm = warp_max_d(r);
+        if (lane == 0) wred[warp] = wm;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double rmax = 0.0;
-            for (int k = 0; k < N; ++k) rmax = sr[k] > rmax ? sr[k] : rmax;
-            if (rmax > 0.0) {
-                double C = 0.0;
-                sC[0] = 0.0;
-                for (int k = 0; k < N; ++k) {
-                    sr[k] = __ddiv_rn(sr[k], rmax);
-                    C = __dadd_rn(C, sr[k]);
-                    sC[k + 1] = C;
-                }
-                s_R = C;
-            } else {
-                s_R = -1.0;
+        double rmax = 0.0;
+        for (int w = 0; w < 8; ++w) rmax = fmax(rmax, wred[w]);
+        __syncthreads();
+        if (rmax > 0.0) {
+            r = __ddiv_rn(r, rmax);
+            if (k < N) sr[k] = r;
+            // inclusive prefix sum C_(k+1) = r_0 + ... + r_k
+            double c = r;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double t = __shfl_up_sync(0xffffffffu, c, o);
+                if (lane >= o) c = __dadd_rn(t, c);
             }
-        }
-        __syncthreads();
-        if (s_R > 0.0) {
-            const double R = s_R;
-            for (int m = 1 + threadIdx.x; m < N; m += blockDim.x) {
+            if (lane == 31) wred[warp] = c;
+            __syncthreads();
+            double off = 0.0;
+            for (int w = 0; w < warp; ++w) off = __dadd_rn(off, wred[w]);
+            c = __dadd_rn(off, c);
+            if (k < N) sC[k + 1] = c;
+            if (k == 0) sC[0] = 0.0;
+            __syncthreads();
+            const double R = sC[N];
+            const int m = k;
+            if (m >= 1 && m < N) {
                 const double t = __ddiv_rn(__dmul_rn((double)m, R), (double)N);
-                // largest k in [0, N-1] with C_k <= t
+                // largest j in [0, N-1] with C_j <= t
                 int lo = 0, hi = N - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (sC[mid] <= t) lo = mid;
                     else hi = mid - 1;
                 }
-                const int k = lo;
-                e[m] = __fma_rn(__dadd_rn(se[k + 1], -se[k]),
-                                __ddiv_rn(__dadd_rn(t, -sC[k]), sr[k]), se[k]);
+                e[m] = __fma_rn(__dadd_rn(se[lo + 1], -se[lo]),
+                                __ddiv_rn(__dadd_rn(t, -sC[lo]), sr[lo]), se[lo]);
             }
         }
     }
-    if (zero_hist) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < N; k += blockDim.x) Hd[k] = 0.0;
-    }
+    if (zero_hist && k < N) Hd[k] = 0.0;
 }
 
-// One thread per component, then thread 0 updates the iteration control.
-__global__ void k_combine(const CombineArgs A)
+__global__ void __launch_bounds__(256) k_refine(int N, double *H, double *edges)
+{
+    refine_axis(blockIdx.x, N, H, edges, 0);
+}
+
+// Per component: fold the iteration result into the combination; thread 0
+// then updates the iteration control.  The chi-square probability is only
+// needed for the final answer and is evaluated when the run stops.
+__device__ void combine_iteration(const CombineArgs &A)
 {
     DevState *st = A.st;
-    if (*(volatile int *)&st->stopped) return;
     const int c = threadIdx.x;
     const long long n = st->n_cur;
     const int j = st->iter;
     __shared__ int s_ok[CV_MAX_COMP];
+    __shared__ int s_stop;
     if (c < A.ncomp) {
         const double dn = (double)n;
         const double I = __ddiv_rn(st->S1[c], dn);
@@ -175,20 +192,18 @@ __global__ void k_combine(const CombineArgs A)
             st->mean[c] = mean;
             st->W[c] = Wn;
         }
-        double integral, error, chi2, prob;
+        double integral, error, chi2;
         if (st->zero[c]) {
             integral = st->sumI[c] / (double)m;
-            error = chi2 = prob = 0.0;
+            error = chi2 = 0.0;
         } else {
             integral = st->mean[c];
             error = sqrt(1.0 / st->W[c]);
             chi2 = st->M2[c] > 0.0 ? st->M2[c] : 0.0;
-            prob = m > 1 ? gamma_p(0.5 * (m - 1), 0.5 * chi2) : 0.0;
         }
         st->integral[c] = integral;
         st->error[c] = error;
         st->chi2[c] = chi2;
-        st->prob[c] = prob;
         const double tol = fmax(A.epsabs, A.epsrel * fabs(integral));
         s_ok[c] = error <= tol;
         st->S1[c] = 0.0;
@@ -202,17 +217,39 @@ __global__ void k_combine(const CombineArgs A)
         st->neval = neval;
         st->iter = j + 1;
         const long long next = A.nstart + (long long)(j + 1) * A.nincrease;
+        int stop = 0;
         if (neval >= A.mineval && ok) {
             st->fail = 0;
-            st->stopped = 1;
+            stop = 1;
         } else if (neval + next > A.maxeval) {
             st->fail = 1;
-            st->stopped = 1;
+            stop = 1;
         } else {
             st->next_index += (unsigned long long)n;
             st->n_cur = next;
         }
+        s_stop = stop;
     }
+    __syncthreads();
+    if (c < A.ncomp) {
+        const int m = j + 1;
+        st->prob[c] = (s_stop && !st->zero[c] && m > 1) ? gamma_p(0.5 * (m - 1), 0.5 * st->chi2[c]) : 0.0;
+    }
+    __syncthreads();
+    // read by the next sampling launch only, so no block of this launch
+    // sees the change
+    if (c == 0 && s_stop) st->stopped = 1;
+}
+
+// One Vegas iteration after its sampling pass: blocks 0..ndim-1 refine one
+// axis each from the histogram (and clear it), block ndim combines the
+// iteration.  Runs only if the sampling launch before it ran.
+__global__ void __launch_bounds__(256)
+k_refine_combine(int ndim, int N, double *H, double *edges, const CombineArgs A)
+{
+    if (!*(volatile const int *)&A.st->pass_active) return;
+    if ((int)blockIdx.x < ndim) refine_axis(blockIdx.x, N, H, edges, 1);
+    else combine_iteration(A);
 }
 
 // Start of a run: uniform grid e_k = k/N, empty histogram and sums, Sobol
@@ -242,16 +279,16 @@ cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int n
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, int zero_hist,
-                          const DevState *st, cudaStream_t s)
+cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, cudaStream_t s)
 {
-    k_refine<<<ndim, 256, 0, s>>>(nbins, H, edges, zero_hist, st);
+    k_refine<<<ndim, 256, 0, s>>>(nbins, H, edges);
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const CombineArgs &a, cudaStream_t s)
+cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
+                                  const CombineArgs &a, cudaStream_t s)
 {
-    k_combine<<<1, 32, 0, s>>>(a);
+    k_refine_combine<<<ndim + 1, 256, 0, s>>>(ndim, nbins, H, edges, a);
     return cudaGetLastError();
 }
 

@@ -301,3 +301,32 @@ def test_fp32_iterations_with_grid_handed_to_oracle(ctx):
         assert np.max(np.abs(new - O.refine(edges, H))) <= 1e-14
         edges = new
         start += n
+
+
+@pytest.mark.parametrize("nbins", [2, 16, 32, 64, 96, 256])
+def test_sample_fp32_every_bin_layout(ctx, nbins):
+    # power-of-two N >= 32 use the stratum-major shared-memory layout, other
+    # N the plain one; both must give the oracle's sums and histogram.
+    ndim, n = 5, 40001
+    a, u = _params(ndim, 2, nbins)
+    fams = [O.GAUSSIAN, O.DISCONTINUOUS]
+    edges = _random_grid(ndim, nbins, nbins + 1)
+    g = cg.genz(ndim, fams, a, u)
+    S1, S2, H = _gpu_sample(ctx, g, edges, 3, n, 0)
+    p = O.Problem(ndim, fams, a, u, nbins=nbins, bits=23, fp32_decide=True)
+    oS1, oS2, oH = O.sample(p, edges, 3, n)
+    for c in range(2):
+        assert abs(S1[c] - oS1[c]) <= 1e-6 * math.sqrt(n * oS2[c])
+        assert abs(S2[c] - oS2[c]) <= 1e-6 * oS2[c]
+    scale = np.maximum(oH.max(axis=1, keepdims=True), 1e-300)
+    assert np.all(np.abs(H - oH) <= 1e-5 * scale)
+    # the same points reach the same bins
+    assert np.array_equal(H == 0, oH == 0)
+
+
+@pytest.mark.parametrize("nbins", [32, 256])
+def test_sample_fp32_const_counts_exact_permuted_layout(ctx, nbins):
+    ndim, n = 3, 2 ** 15
+    g = cg.genz(ndim, [cg.CONST], 1.0, 0.5)
+    S1, S2, H = _gpu_sample(ctx, g, O.grid_uniform(ndim, nbins), 5 * n, n, 0)
+    assert S1[0] == n and S2[0] == n and np.all(H == n // nbins)
