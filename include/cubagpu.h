@@ -99,8 +99,10 @@ typedef struct cv_ctx cv_ctx;
 /* Create a context on CUDA device `device`, enqueueing on `stream` (a
  * cudaStream_t; NULL = the context creates its own non-blocking stream;
  * pass cudaStreamLegacy, (void *)1, for the legacy default stream).
- * The context owns the library's device memory; cv_destroy releases it
- * (the analogue of cubawait for the spinning workers, Sect. 3.2.3). */
+ * The context owns the library's device memory; cv_destroy releases it,
+ * including every cv_integral still attached to it, whose handles then
+ * become invalid (the analogue of cubawait for the spinning workers,
+ * Sect. 3.2.3). */
 int cv_create(cv_ctx **ctx, int device, void *stream);
 void cv_destroy(cv_ctx *ctx);
 const char *cv_strerror(int code);
@@ -205,6 +207,7 @@ int cv_integral_grid(cv_integral *I, double *edges);
 int cv_integral_log(cv_integral *I, int max_iter, double *iter_I, double *iter_var);
 /* Kernels one reset + run enqueues when it runs to the sample budget. */
 int cv_integral_kernels_per_run(const cv_integral *I);
+/* Release an integral; a no-op on a handle its context already released. */
 void cv_integral_destroy(cv_integral *I);
 
 #ifdef __cplusplus

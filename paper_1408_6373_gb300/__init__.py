@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -187,12 +188,15 @@ class Context:
             s = torch.cuda.current_stream(device).cuda_stream
             stream = s if s else STREAM_LEGACY
         self._h = ctypes.c_void_p()
+        self._children = weakref.WeakSet()
         rc = self._lib.cv_create(ctypes.byref(self._h), device, stream)
         if rc != OK:
             raise CubaGpuError(rc, "cv_create failed: " + self._lib.cv_strerror(rc).decode())
 
     def close(self):
         if self._h:
+            for child in list(self._children):
+                child.close()
             self._lib.cv_destroy(self._h)
             self._h = ctypes.c_void_p()
 
@@ -265,10 +269,12 @@ class Integral:
         self._h = ctypes.c_void_p()
         ctx._check(ctx._lib.cv_integral_create(ctx._h, ctypes.byref(sp), ctypes.byref(self._h)),
                    "cv_integral_create")
+        ctx._children.add(self)
 
     def close(self):
         if self._h:
-            self.ctx._lib.cv_integral_destroy(self._h)
+            if self.ctx._h:
+                self.ctx._lib.cv_integral_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <set>
 #include <vector>
 
 #include "cv_internal.cuh"
@@ -76,7 +77,12 @@ struct cv_ctx {
     char msg[512] = {0};
     // cached occupancy, [precision][ndim][nbins]; 0 = unknown
     std::vector<int> occ;
+    // integrals created on this context (released by cv_destroy if the
+    // caller has not destroyed them)
+    std::set<struct cv_integral *> integrals;
 };
+
+static void integral_free(struct cv_integral *I);
 
 static int fail_msg(cv_ctx *ctx, int code, const char *fmt, ...)
 {
@@ -155,6 +161,8 @@ extern "C" void cv_destroy(cv_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (struct cv_integral *I : ctx->integrals) integral_free(I);
+    ctx->integrals.clear();
     cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -485,18 +493,26 @@ extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral 
     I->log_I = (double *)(p + sz_state + sz_edges + sz_H);
     I->log_var = (double *)(p + sz_state + sz_edges + sz_H + sz_log);
     I->launched_kernels = 1 + 2 * I->jmax;
+    ctx->integrals.insert(I);
     *out = I;
     return CV_OK;
+}
+
+static void integral_free(cv_integral *I)
+{
+    if (I->exec) cudaGraphExecDestroy(I->exec);
+    if (I->mem) cudaFree(I->mem);
+    delete I;
 }
 
 extern "C" void cv_integral_destroy(cv_integral *I)
 {
     if (!I) return;
-    cudaSetDevice(I->ctx->device);
-    cudaStreamSynchronize(I->ctx->stream);
-    if (I->exec) cudaGraphExecDestroy(I->exec);
-    if (I->mem) cudaFree(I->mem);
-    delete I;
+    cv_ctx *ctx = I->ctx;
+    if (!ctx->integrals.erase(I)) return;  // not (or no longer) a live handle
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    integral_free(I);
 }
 
 extern "C" int cv_integral_reset(cv_integral *I)

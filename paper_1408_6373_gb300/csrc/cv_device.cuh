@@ -128,16 +128,16 @@ __device__ __forceinline__ float ipow(float r)
     return acc;
 }
 
-// FP32 Genz evaluation of one component.
-template <int NDIM>
-__device__ __forceinline__ float genz_f32(int fam, const float *p0, const float *p1,
-                                          float q0, const float (&x)[NDIM])
+// FP32 Genz evaluation of component C (parameters read straight from the
+// kernel's parameter space, so they are constant-bank operands).
+template <int NDIM, int C>
+__device__ __forceinline__ float genz_f32(const GenzParams<float> &g, const float (&x)[NDIM])
 {
-    switch (fam) {
+    switch (g.family[C]) {
     case CV_OSCILLATORY: {
-        float t = q0;  // phase in turns, reduced to [-1/2, 1/2]
+        float t = g.q0[C];  // phase in turns, reduced to [-1/2, 1/2]
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) t = __fmaf_rn(p0[d], x[d], t);
+        for (int d = 0; d < NDIM; ++d) t = __fmaf_rn(g.p0[C][d], x[d], t);
         t -= rintf(t);
         return __cosf(6.28318530717958647692f * t);
     }
@@ -145,22 +145,22 @@ __device__ __forceinline__ float genz_f32(int fam, const float *p0, const float 
         float P = 1.0f;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const float dx = x[d] - p1[d];
-            P *= __fmaf_rn(dx, dx, p0[d]);
+            const float dx = x[d] - g.p1[C][d];
+            P *= __fmaf_rn(dx, dx, g.p0[C][d]);
         }
         return rcp_approx(P);
     }
     case CV_CORNER_PEAK: {
         float s = 1.0f;
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(p0[d], x[d], s);
+        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(g.p0[C][d], x[d], s);
         return ipow<NDIM + 1>(rcp_approx(s));
     }
     case CV_GAUSSIAN: {
         float s = 0.0f;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const float t = __fmaf_rn(p0[d], x[d], -p1[d]);
+            const float t = __fmaf_rn(g.p0[C][d], x[d], -g.p1[C][d]);
             s = __fmaf_rn(t, t, s);
         }
         return __expf(-s);
@@ -168,15 +168,15 @@ __device__ __forceinline__ float genz_f32(int fam, const float *p0, const float 
     case CV_C0: {
         float s = 0.0f;
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(p0[d], fabsf(x[d] - p1[d]), s);
+        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(g.p0[C][d], fabsf(x[d] - g.p1[C][d]), s);
         return __expf(-s);
     }
     case CV_DISCONTINUOUS: {
-        bool out = x[0] > p1[0];
-        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > p1[NDIM > 1 ? 1 : 0]);
+        bool out = x[0] > g.p1[C][0];
+        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > g.p1[C][NDIM > 1 ? 1 : 0]);
         float s = 0.0f;
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(p0[d], x[d], s);
+        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(g.p0[C][d], x[d], s);
         return out ? 0.0f : __expf(s);
     }
     default:
@@ -184,44 +184,43 @@ __device__ __forceinline__ float genz_f32(int fam, const float *p0, const float 
     }
 }
 
-// FP64 Genz evaluation of one component (same formulas in double).
-template <int NDIM>
-__device__ __forceinline__ double genz_f64(int fam, const double *p0, const double *p1,
-                                           double q0, const double (&x)[NDIM])
+// FP64 Genz evaluation of component C (same formulas in double).
+template <int NDIM, int C>
+__device__ __forceinline__ double genz_f64(const GenzParams<double> &g, const double (&x)[NDIM])
 {
     double s = 0.0, P = 1.0;
-    switch (fam) {
+    switch (g.family[C]) {
     case CV_OSCILLATORY:
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fma_rn(p0[d], x[d], s);
-        return cos(q0 + s);
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(g.p0[C][d], x[d], s);
+        return cos(g.q0[C] + s);
     case CV_PRODUCT_PEAK:
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const double dx = x[d] - p1[d];
-            P *= 1.0 / __fma_rn(dx, dx, p0[d]);
+            const double dx = x[d] - g.p1[C][d];
+            P *= 1.0 / __fma_rn(dx, dx, g.p0[C][d]);
         }
         return P;
     case CV_CORNER_PEAK:
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fma_rn(p0[d], x[d], s);
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(g.p0[C][d], x[d], s);
         return pow(1.0 + s, -(double)(NDIM + 1));
     case CV_GAUSSIAN:
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const double dx = x[d] - p1[d];
-            s = __fma_rn(p0[d] * dx, dx, s);
+            const double dx = x[d] - g.p1[C][d];
+            s = __fma_rn(g.p0[C][d] * dx, dx, s);
         }
         return exp(-s);
     case CV_C0:
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fma_rn(p0[d], fabs(x[d] - p1[d]), s);
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(g.p0[C][d], fabs(x[d] - g.p1[C][d]), s);
         return exp(-s);
     case CV_DISCONTINUOUS: {
-        bool out = x[0] > p1[0];
-        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > p1[NDIM > 1 ? 1 : 0]);
+        bool out = x[0] > g.p1[C][0];
+        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > g.p1[C][NDIM > 1 ? 1 : 0]);
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fma_rn(p0[d], x[d], s);
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(g.p0[C][d], x[d], s);
         return out ? 0.0 : exp(s);
     }
     default:
@@ -229,21 +228,20 @@ __device__ __forceinline__ double genz_f64(int fam, const double *p0, const doub
     }
 }
 
-template <int NDIM>
-__device__ __forceinline__ float genz_eval(int fam, const float *p0, const float *p1, float q0,
-                                           const float (&x)[NDIM])
+template <int NDIM, int C>
+__device__ __forceinline__ float genz_eval(const GenzParams<float> &g, const float (&x)[NDIM])
 {
-    return genz_f32<NDIM>(fam, p0, p1, q0, x);
+    return genz_f32<NDIM, C>(g, x);
 }
-template <int NDIM>
-__device__ __forceinline__ double genz_eval(int fam, const double *p0, const double *p1,
-                                            double q0, const double (&x)[NDIM])
+template <int NDIM, int C>
+__device__ __forceinline__ double genz_eval(const GenzParams<double> &g, const double (&x)[NDIM])
 {
-    return genz_f64<NDIM>(fam, p0, p1, q0, x);
+    return genz_f64<NDIM, C>(g, x);
 }
 
 // ------------------------------------------------------------ sums
-// FP32 path: Kahan-compensated per-thread sums (value = s - c).
+// FP32 path: per-thread Kahan-compensated sums, fed with plain FP32 partial
+// sums over short runs of steps (blocked Kahan summation); value = s - c.
 // FP64 path: plain per-thread sums.
 template <typename Real> struct Acc;
 template <> struct Acc<float> {
@@ -255,35 +253,64 @@ template <> struct Acc<float> {
         c = (t - s) - y;
         s = t;
     }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 template <> struct Acc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double value() const { return s; }
 };
 
-__device__ __forceinline__ double warp_sum(double v)
+// Warp sum of per-lane values, returned on every lane in FP64.  The FP32
+// path reduces the Kahan pairs as float-float numbers (Knuth's TwoSum) so
+// that FP64 arithmetic, slow on this GPU, runs once per warp.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ double warp_total(const Acc<float> &a)
+{
+    float hi = a.s, lo = -a.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, ohi, s, e);
+        e += lo + olo;
+        hi = s + e;
+        lo = e - (hi - s);
+    }
+    return (double)hi + (double)lo;
+}
+
+__device__ __forceinline__ double warp_total(const Acc<double> &a)
+{
+    double v = a.s;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
 // ------------------------------------------------------------ sampling steps
-// Shared-memory views of one block.
+// Shared-memory views of one block.  Every axis owns a stride of
+// CV_MAX_BINS slots, so the offsets of axis d in the three arrays are
+// compile-time constants and one register (the slot) addresses all three.
+constexpr int kStride = CV_MAX_BINS;
+
 template <typename Real> struct Smem;
 template <> struct Smem<float> {
-    float *e, *w, *h;  // [NDIM*N] each: e_k, w_k (N w_k on the power-of-two map), histogram
+    float *e, *w, *h;  // [NDIM][kStride]: e_k, w_k (N w_k on the power-of-two map), histogram
 };
 template <> struct Smem<double> {
-    double2 *ew;       // [NDIM*N] {e_k, w_k}
-    double *h;         // [NDIM*N]
+    double2 *ew;       // [NDIM][kStride] {e_k, w_k}
+    double *h;         // [NDIM][kStride]
 };
 
 // Map one FP32 coordinate: returns x, multiplies the Jacobian, and gives the
-// histogram slot.  Power-of-two N: frac/N = 2^-L (1.frac) - 2^-L straight
-// from the word's bits, x = fma(N w, frac/N, e) (the same value as
+// axis-local slot of its bin.  Power-of-two N: frac/N = 2^-L (1.frac) - 2^-L
+// straight from the word's bits, x = fma(N w, frac/N, e) (the same value as
 // fma(w, frac, e): the scalings are exact), J *= N w.
 template <bool POW2>
 __device__ __forceinline__ float map_f32(unsigned X, int d, int N, const MapParams &m,
@@ -292,19 +319,19 @@ __device__ __forceinline__ float map_f32(unsigned X, int d, int N, const MapPara
     if (POW2) {
         const unsigned fb = (X >> m.sF) & m.mF;
         const float fs = __uint_as_float(m.expL | fb) - m.twoNegL;
-        const int p = d * N + (int)(((X >> m.sA) & m.mA) | (X >> m.sB));
-        const float w = sm.w[p];
+        const int p = (int)(((X >> m.sA) & m.mA) | (X >> m.sB));
+        const float w = sm.w[d * kStride + p];
         J *= w;
         slot = p;
-        return __fmaf_rn(w, fs, sm.e[p]);
+        return __fmaf_rn(w, fs, sm.e[d * kStride + p]);
     } else {
         const unsigned t = (X >> 9) * (unsigned)N;
         const float frac = __uint_as_float(0x3f800000u | (t & 0x7fffffu)) - 1.0f;
-        const int p = d * N + (int)(t >> 23);
-        const float w = sm.w[p];
+        const int p = (int)(t >> 23);
+        const float w = sm.w[d * kStride + p];
         J = J * ((float)N * w);
         slot = p;
-        return __fmaf_rn(w, frac, sm.e[p]);
+        return __fmaf_rn(w, frac, sm.e[d * kStride + p]);
     }
 }
 
@@ -314,8 +341,8 @@ __device__ __forceinline__ double map_f64(unsigned long long X, int d, int N,
     const unsigned long long t = (X >> 12) * (unsigned long long)N;  // < 2^60
     const double frac = __longlong_as_double((long long)(0x3ff0000000000000ull |
                                                          (t & 0xfffffffffffffull))) - 1.0;
-    const int p = d * N + (int)(t >> 52);
-    const double2 ew = sm.ew[p];
+    const int p = (int)(t >> 52);
+    const double2 ew = sm.ew[d * kStride + p];
     J = J * ((double)N * ew.y);
     slot = p;
     return __fma_rn(ew.y, frac, ew.x);
@@ -325,8 +352,27 @@ template <typename Real> struct Word;
 template <> struct Word<float> { using type = unsigned int; };
 template <> struct Word<double> { using type = unsigned long long; };
 
+// Evaluate component C of the point and add it to the partial sums.
+template <int NDIM, int C, typename Real, bool EDGE>
+__device__ __forceinline__ void eval_comp(const GenzParams<Real> &g, const Real (&x)[NDIM],
+                                          Real J, bool valid, Real (&p1)[CV_MAX_COMP],
+                                          Real (&p2)[CV_MAX_COMP], Real &f0)
+{
+    if (C < g.ncomp) {
+        Real v = J * genz_eval<NDIM, C>(g, x);
+        if (EDGE && !valid) v = Real(0);
+        p1[C] += v;
+        p2[C] += v * v;
+        if (C == 0) f0 = v;
+    }
+}
+
 // nsteps consecutive 32-point blocks starting at block q0.  EDGE: the range
 // touches the first or last (partial) block and every index is checked.
+// FP32: the values are summed in FP32 over runs of kRun steps, and each
+// run's sum is added to the Kahan accumulators.
+constexpr unsigned kRun = 16;
+
 template <int NDIM, typename Real, bool POW2, bool EDGE>
 __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<Real> &sm,
                                           typename Word<Real>::type (&X)[NDIM],
@@ -336,49 +382,59 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
                                           Acc<Real> (&s2)[CV_MAX_COMP])
 {
     const int N = A.nbins;
-    const int ncomp = A.g.ncomp;
-    for (unsigned st = 0; st < nsteps; ++st) {
-        const unsigned long long q = q0 + st;
-        bool valid = true;
-        if (EDGE) {
-            const unsigned long long i = q * 32ull + (unsigned long long)lane;
-            valid = (i >= start) && (i < end);
-        }
-        Real x[NDIM];
-        int slot[NDIM];
-        Real J = Real(1);
+    for (unsigned r0 = 0; r0 < nsteps; r0 += kRun) {
+        const unsigned r1 = min(r0 + kRun, nsteps);
+        Real p1[CV_MAX_COMP], p2[CV_MAX_COMP];
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) {
-            if constexpr (sizeof(Real) == 4)
-                x[d] = map_f32<POW2>(X[d], d, N, A.map, sm, J, slot[d]);
-            else
-                x[d] = map_f64(X[d], d, N, sm, J, slot[d]);
+        for (int c = 0; c < CV_MAX_COMP; ++c) p1[c] = p2[c] = Real(0);
+        for (unsigned st = r0; st < r1; ++st) {
+            const unsigned long long q = q0 + st;
+            bool valid = true;
+            if (EDGE) {
+                const unsigned long long i = q * 32ull + (unsigned long long)lane;
+                valid = (i >= start) && (i < end);
+            }
+            Real x[NDIM];
+            int slot[NDIM];
+            Real J = Real(1);
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                if constexpr (sizeof(Real) == 4)
+                    x[d] = map_f32<POW2>(X[d], d, N, A.map, sm, J, slot[d]);
+                else
+                    x[d] = map_f64(X[d], d, N, sm, J, slot[d]);
+            }
+            Real f0 = Real(0);
+            eval_comp<NDIM, 0, Real, EDGE>(A.g, x, J, valid, p1, p2, f0);
+            eval_comp<NDIM, 1, Real, EDGE>(A.g, x, J, valid, p1, p2, f0);
+            eval_comp<NDIM, 2, Real, EDGE>(A.g, x, J, valid, p1, p2, f0);
+            eval_comp<NDIM, 3, Real, EDGE>(A.g, x, J, valid, p1, p2, f0);
+            if (!EDGE || valid) {
+                const Real h = f0 * f0;
+#pragma unroll
+                for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * kStride + slot[d]], h);
+            }
+            if (st + 1 < nsteps) sobol_step<NDIM, typename Word<Real>::type>(X, q);
         }
-        Real f0 = Real(0);
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c) {
-            if (c < ncomp) {
-                const Real f = genz_eval<NDIM>(A.g.family[c], A.g.p0[c], A.g.p1[c], A.g.q0[c], x);
-                const Real v = J * f;
-                if (valid) {
-                    s1[c].add(v);
-                    s2[c].add(v * v);
-                }
-                if (c == 0) f0 = v;
+            if (c < A.g.ncomp) {
+                s1[c].add(p1[c]);
+                s2[c].add(p2[c]);
             }
         }
-        if (valid) {
-            const Real h = f0 * f0;
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[slot[d]], h);
-        }
-        if (st + 1 < nsteps) sobol_step<NDIM, typename Word<Real>::type>(X, q);
     }
 }
 
 // ------------------------------------------------------------ the kernel
+// Register budget: three resident blocks of 256 threads per SM for up to 8
+// FP32 dimensions (80 registers), two up to 16; wider problems get what
+// they need.
+template <int NDIM, typename Real>
+constexpr int kMinBlocks = sizeof(Real) != 4 ? 1 : (NDIM <= 8 ? 3 : (NDIM <= 16 ? 2 : 1));
+
 template <int NDIM, typename Real, bool POW2>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, Real>))
 k_sample(const __grid_constant__ SampleArgs<Real> A)
 {
     using W = typename Word<Real>::type;
@@ -401,12 +457,12 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
     Smem<Real> sm;
     if constexpr (sizeof(Real) == 4) {
         sm.e = reinterpret_cast<float *>(smem_raw);
-        sm.w = sm.e + NDIM * N;
-        sm.h = sm.w + NDIM * N;
+        sm.w = sm.e + NDIM * kStride;
+        sm.h = sm.w + NDIM * kStride;
         for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
             const int d = idx / N, k = idx - d * N;
             const double *e = A.edges + (size_t)d * (N + 1);
-            const int p = d * N + slot_of_bin(k, A.map);
+            const int p = d * kStride + slot_of_bin(k, A.map);
             const double w = e[k + 1] - e[k];
             sm.e[p] = __double2float_rn(e[k]);
             sm.w[p] = __double2float_rn(POW2 ? (double)N * w : w);
@@ -414,12 +470,12 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
         }
     } else {
         sm.ew = reinterpret_cast<double2 *>(smem_raw);
-        sm.h = reinterpret_cast<double *>(sm.ew + NDIM * N);
+        sm.h = reinterpret_cast<double *>(sm.ew + NDIM * kStride);
         for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
             const int d = idx / N, k = idx - d * N;
             const double *e = A.edges + (size_t)d * (N + 1);
-            sm.ew[idx] = make_double2(e[k], e[k + 1] - e[k]);
-            sm.h[idx] = 0.0;
+            sm.ew[d * kStride + k] = make_double2(e[k], e[k + 1] - e[k]);
+            sm.h[d * kStride + k] = 0.0;
         }
     }
     __syncthreads();
@@ -449,14 +505,14 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
             run_steps<NDIM, Real, POW2, true>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
     }
 
-    // FP64 reduction: warp shuffle, then across the block's warps.
+    // Reduction: warp, then across the block's warps in FP64.
     __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
     const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c < CV_MAX_COMP; ++c) {
         if (c < ncomp) {
-            const double a = warp_sum(s1[c].value());
-            const double b = warp_sum(s2[c].value());
+            const double a = warp_total(s1[c]);
+            const double b = warp_total(s2[c]);
             if (lane == 0) {
                 red[warp][2 * c] = a;
                 red[warp][2 * c + 1] = b;
@@ -470,13 +526,12 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
         const int c = threadIdx.x >> 1;
         atomicAdd((threadIdx.x & 1) ? &A.S2[c] : &A.S1[c], t);
     }
-    for (int p = threadIdx.x; p < NDIM * N; p += blockDim.x) {
-        const Real v = sm.h[p];
-        if (v != Real(0)) {
-            int d = p / N, k = p - d * N;
-            if constexpr (sizeof(Real) == 4) k = bin_of_slot(k, A.map);
-            atomicAdd(&A.H[d * N + k], (double)v);
-        }
+    for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+        const int d = idx / N, k = idx - d * N;
+        int p = k;
+        if constexpr (sizeof(Real) == 4) p = slot_of_bin(k, A.map);
+        const Real v = sm.h[d * kStride + p];
+        if (v != Real(0)) atomicAdd(&A.H[idx], (double)v);
     }
 }
 

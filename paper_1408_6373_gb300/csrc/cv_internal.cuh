@@ -114,8 +114,9 @@ cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int n
                          long long nstart, cudaStream_t s);
 
 inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64) {
-    // grid {e, w} pairs plus the block histogram
-    return (size_t)ndim * nbins * (fp64 ? 3 * sizeof(double) : 3 * sizeof(float));
+    // grid {e, w} pairs plus the block histogram, CV_MAX_BINS slots per axis
+    (void)nbins;
+    return (size_t)ndim * CV_MAX_BINS * (fp64 ? 3 * sizeof(double) : 3 * sizeof(float));
 }
 
 }  // namespace cv
