@@ -49,6 +49,8 @@ extern "C" {
 #define CV_EADMIT (-6)         /* admission refused (memory budget)        */
 #define CV_EBUSY (-7)          /* no free slot                             */
 #define CV_ENOTFOUND (-8)      /* unknown request id                       */
+#define CV_ESCRATCH (-9)       /* the problem does not fit the static scratch
+                                  area of cv_vegas_noalloc                 */
 
 /* ------------------------------------------------- built-in integrands */
 /* Genz (1984) test families over [0,1]^ndim with parameters a_i > 0 and
@@ -160,6 +162,35 @@ int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g,
 /* Bytes cv_vegas moves between host and device per call for an integral of
  * this shape: kernel parameters in (h2d), the final state out (d2h). */
 int cv_vegas_io_bytes(int ndim, int nbins, int64_t *h2d, int64_t *d2h);
+
+/* ------------------------------------------- no-allocation Vegas call */
+/* cv_vegas for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this entry point exists because some callers of a GPU
+ * library may not call cudaMalloc: a process whose device memory belongs to
+ * another framework's caching allocator, a component running while a pool
+ * holds every byte of the device, or code that is handed only a device and
+ * a stream.  It computes what cv_vegas computes (same arguments, same
+ * kernels, same results) without allocating anything: the device state,
+ * grid and histogram of the run live in one static device array of
+ * CV_STATIC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.  No context is needed: `device` is the CUDA device and
+ * `stream` the cudaStream_t to run on (NULL = the legacy default stream).
+ * Limits: ndim * (2 nbins + 1) * 8 + 512 bytes must fit the array, else the
+ * call returns CV_ESCRATCH (16 dimensions x 256 bins fit, 32 x 256 do
+ * not); otherwise the arguments and return codes are those of cv_vegas.
+ * The first call on a device looks up the array's device address, so make
+ * it before capturing a stream into a CUDA graph.  Every call on a device
+ * shares the one array and leaves its last contents there (each run clears
+ * what must start at zero itself); calls whose GPU work overlaps -- two
+ * streams, two host threads -- race and corrupt each other: serialise
+ * them. */
+#define CV_STATIC_SCRATCH_BYTES (128 * 1024)
+int cv_vegas_noalloc(int device, void *stream, int ndim, int ncomp,
+                     const cv_genz *g, double epsrel, double epsabs, int flags,
+                     int seed, int64_t mineval, int64_t maxeval,
+                     int64_t nstart, int64_t nincrease, int64_t nbatch,
+                     int nbins, int64_t *neval, int *fail, double integral[],
+                     double error[], double prob[]);
 
 /* ------------------------------------------- device-resident integrals */
 /* A Vegas problem whose grid, sums and combination state stay in device

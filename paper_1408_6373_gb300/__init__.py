@@ -31,6 +31,8 @@ FP64 = 0x100
 PLAIN = 0x200
 
 OK, EINVAL, ENOMEM, ECUDA, EABORT, ETIMEOUT, EADMIT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
+ESCRATCH = -9
+STATIC_SCRATCH_BYTES = 128 * 1024
 
 STREAM_LEGACY = 1  # cudaStreamLegacy
 
@@ -126,6 +128,8 @@ _SIGNATURES = {
     "cv_vegas": (_i, [_vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64, _i64,
                       _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_vegas_io_bytes": (_i, [_i, _i, _P(_i64), _P(_i64)]),
+    "cv_vegas_noalloc": (_i, [_i, _vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64,
+                              _i64, _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_integral_create": (_i, [_vp, _P(Spec), _P(_vp)]),
     "cv_integral_reset": (_i, [_vp]),
     "cv_integral_run": (_i, [_vp]),
@@ -250,6 +254,27 @@ class Context:
 
     def integral(self, sp: Spec) -> "Integral":
         return Integral(self, sp)
+
+
+def vegas_noalloc(g: Genz, device: int = 0, stream=None, epsrel=0.0, epsabs=0.0, flags=0,
+                  seed=0, mineval=0, maxeval=10 ** 6, nstart=10 ** 4, nincrease=0, nbatch=1000,
+                  nbins=64) -> VegasResult:
+    """cv_vegas_noalloc: the Vegas call for callers that cannot allocate
+    device memory (scratch in a static device array; see cubagpu.h).
+    `stream` defaults to torch's current stream on `device`."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(device).cuda_stream or None
+    nc = g.ncomp
+    integral, error, prob = np.zeros(nc), np.zeros(nc), np.zeros(nc)
+    neval, fail = ctypes.c_int64(), ctypes.c_int()
+    rc = lib().cv_vegas_noalloc(device, stream, g.ndim, nc, ctypes.byref(g), epsrel, epsabs,
+                                flags, seed, mineval, maxeval, nstart, nincrease, nbatch, nbins,
+                                ctypes.byref(neval), ctypes.byref(fail), integral.ctypes.data,
+                                error.ctypes.data, prob.ctypes.data)
+    if rc != OK:
+        raise CubaGpuError(rc, "cv_vegas_noalloc: " + lib().cv_strerror(rc).decode())
+    return VegasResult(neval.value, fail.value, integral, error, prob)
 
 
 def vegas_io_bytes(ndim: int, nbins: int):

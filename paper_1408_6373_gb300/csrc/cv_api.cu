@@ -118,6 +118,7 @@ extern "C" const char *cv_strerror(int code)
     case CV_EADMIT: return "admission refused";
     case CV_EBUSY: return "busy";
     case CV_ENOTFOUND: return "not found";
+    case CV_ESCRATCH: return "problem too large for the static scratch area";
     }
     return "unknown error";
 }
