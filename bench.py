@@ -149,13 +149,16 @@ def _dist():
     return world, rank, local
 
 
+KERNEL_SOURCES = ("cv_device.cuh", "cv_internal.cuh", "sobol_dirs.h")
+
+
 def _kernel_source_hash() -> str:
+    """Hash of the files that define the sampling kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1408_6373_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
