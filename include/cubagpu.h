@@ -102,8 +102,8 @@ typedef struct cv_ctx cv_ctx;
  * cudaStream_t; NULL = the context creates its own non-blocking stream;
  * pass cudaStreamLegacy, (void *)1, for the legacy default stream).
  * The context owns the library's device memory; cv_destroy releases it,
- * including every cv_integral still attached to it, whose handles then
- * become invalid (the analogue of cubawait for the spinning workers,
+ * including every cv_integral and cv_batch still attached to it, whose
+ * handles then become invalid (the analogue of cubawait for the spinning workers,
  * Sect. 3.2.3). */
 int cv_create(cv_ctx **ctx, int device, void *stream);
 void cv_destroy(cv_ctx *ctx);
@@ -240,6 +240,37 @@ int cv_integral_log(cv_integral *I, int max_iter, double *iter_I, double *iter_v
 int cv_integral_kernels_per_run(const cv_integral *I);
 /* Release an integral; a no-op on a handle its context already released. */
 void cv_integral_destroy(cv_integral *I);
+
+/* ------------------------------------------------- batched persistent runs */
+/* Many independent Vegas integrals run together (the paper's "n/N points
+ * per core" of Sect. 2.1 applied across integrals as well as within one):
+ * every iteration, one persistent sampling launch per dimension class walks
+ * a queue of (integral, iteration, 32-point-block range) tiles of uneven
+ * size, then one launch refines every axis of every integral and one
+ * combines every integral; all iterations are one captured CUDA graph and
+ * each integral stops on the device when its own goal or budget is reached.
+ * FP32 path only (CV_FP64 / CV_PLAIN are rejected).  Each integral's result
+ * equals what cv_vegas returns for it alone, up to FP32 summation order.
+ * The tile size of each class comes from a cost model (four tiles per
+ * resident CTA, 64..4096 blocks), the environment (CUBAGPU_TILE, points per
+ * tile), or cv_batch_autotune. */
+typedef struct cv_batch cv_batch;
+int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_batch **out);
+/* Enqueue one complete run of every integral (asynchronous). */
+int cv_batch_run(cv_batch *B);
+/* Synchronise and copy count results. */
+int cv_batch_results(cv_batch *B, cv_result *out);
+/* Time each class's first-iteration sampling with tile sizes 2^11..2^17
+ * points and keep the fastest (resets the integrals; call before run). */
+int cv_batch_autotune(cv_batch *B);
+/* Tile size in points chosen for the class (ndim, power-of-two bins). */
+int cv_batch_tile_points(const cv_batch *B, int ndim, int pow2_bins);
+/* Kernels one cv_batch_run enqueues. */
+int cv_batch_kernels_per_run(const cv_batch *B);
+/* Release a batch; a no-op on a handle its context already released. */
+void cv_batch_destroy(cv_batch *B);
+/* create + run + results + destroy. */
+int cv_batch_vegas(cv_ctx *ctx, int count, const cv_spec *specs, cv_result *out);
 
 #ifdef __cplusplus
 }

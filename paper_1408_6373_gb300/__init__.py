@@ -138,6 +138,14 @@ _SIGNATURES = {
     "cv_integral_log": (_i, [_vp, _i, _vp, _vp]),
     "cv_integral_kernels_per_run": (_i, [_vp]),
     "cv_integral_destroy": (None, [_vp]),
+    "cv_batch_create": (_i, [_vp, _i, _vp, _P(_vp)]),
+    "cv_batch_run": (_i, [_vp]),
+    "cv_batch_results": (_i, [_vp, _vp]),
+    "cv_batch_autotune": (_i, [_vp]),
+    "cv_batch_tile_points": (_i, [_vp, _i, _i]),
+    "cv_batch_kernels_per_run": (_i, [_vp]),
+    "cv_batch_destroy": (None, [_vp]),
+    "cv_batch_vegas": (_i, [_vp, _i, _vp, _vp]),
 }
 
 _lib = None
@@ -255,6 +263,16 @@ class Context:
     def integral(self, sp: Spec) -> "Integral":
         return Integral(self, sp)
 
+    def batch(self, specs) -> "Batch":
+        return Batch(self, specs)
+
+    def batch_vegas(self, specs):
+        """cv_batch_vegas: run every spec together; list of Result."""
+        arr = (Spec * len(specs))(*specs)
+        res = (Result * len(specs))()
+        self._check(self._lib.cv_batch_vegas(self._h, len(specs), arr, res), "cv_batch_vegas")
+        return list(res)
+
 
 def vegas_noalloc(g: Genz, device: int = 0, stream=None, epsrel=0.0, epsabs=0.0, flags=0,
                   seed=0, mineval=0, maxeval=10 ** 6, nstart=10 ** 4, nincrease=0, nbatch=1000,
@@ -335,3 +353,45 @@ class Integral:
 
     def kernels_per_run(self) -> int:
         return self.ctx._lib.cv_integral_kernels_per_run(self._h)
+
+
+class Batch:
+    """cv_batch: many Vegas integrals run together from one CUDA graph."""
+
+    def __init__(self, ctx: Context, specs):
+        self.ctx = ctx
+        self.count = len(specs)
+        self._specs = (Spec * self.count)(*specs)
+        self._h = ctypes.c_void_p()
+        ctx._check(ctx._lib.cv_batch_create(ctx._h, self.count, self._specs, ctypes.byref(self._h)),
+                   "cv_batch_create")
+        ctx._children.add(self)
+
+    def close(self):
+        if self._h:
+            if self.ctx._h:
+                self.ctx._lib.cv_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self):
+        self.ctx._check(self.ctx._lib.cv_batch_run(self._h), "cv_batch_run")
+
+    def autotune(self):
+        self.ctx._check(self.ctx._lib.cv_batch_autotune(self._h), "cv_batch_autotune")
+
+    def results(self):
+        res = (Result * self.count)()
+        self.ctx._check(self.ctx._lib.cv_batch_results(self._h, res), "cv_batch_results")
+        return list(res)
+
+    def tile_points(self, ndim: int, pow2_bins: bool = True) -> int:
+        return self.ctx._lib.cv_batch_tile_points(self._h, ndim, 1 if pow2_bins else 0)
+
+    def kernels_per_run(self) -> int:
+        return self.ctx._lib.cv_batch_kernels_per_run(self._h)

@@ -80,9 +80,11 @@ struct cv_ctx {
     // integrals created on this context (released by cv_destroy if the
     // caller has not destroyed them)
     std::set<struct cv_integral *> integrals;
+    std::set<struct cv_batch *> batches;
 };
 
 static void integral_free(struct cv_integral *I);
+static void batch_release(struct cv_batch *B);
 
 static int fail_msg(cv_ctx *ctx, int code, const char *fmt, ...)
 {
@@ -164,6 +166,8 @@ extern "C" void cv_destroy(cv_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     for (struct cv_integral *I : ctx->integrals) integral_free(I);
     ctx->integrals.clear();
+    for (struct cv_batch *B : ctx->batches) batch_release(B);
+    ctx->batches.clear();
     cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -676,4 +680,454 @@ extern "C" int cv_vegas_io_bytes(int ndim, int nbins, int64_t *h2d, int64_t *d2h
     *h2d = (int64_t)sizeof(SampleArgs<double>) + (int64_t)sizeof(CombineArgs);
     *d2h = (int64_t)sizeof(DevState);
     return CV_OK;
+}
+
+// ------------------------------------------------------------ batched runs
+namespace cv {
+#define CV_EXTERN_B(D)                                                                       \
+    extern template cudaError_t launch_batch_sample<D, true>(const BatchSampleArgs &, int,   \
+                                                             cudaStream_t);                  \
+    extern template cudaError_t launch_batch_sample<D, false>(const BatchSampleArgs &, int,  \
+                                                              cudaStream_t);                 \
+    extern template cudaError_t batch_occupancy<D>(bool, int *);
+CV_FOR_EACH_NDIM(CV_EXTERN_B)
+#undef CV_EXTERN_B
+
+static cudaError_t dispatch_batch_sample(int ndim, bool pow2, const BatchSampleArgs &b, int grid,
+                                         cudaStream_t s)
+{
+    switch (ndim) {
+#define CV_CASE(D) \
+    case D: return pow2 ? launch_batch_sample<D, true>(b, grid, s) : launch_batch_sample<D, false>(b, grid, s);
+        CV_FOR_EACH_NDIM(CV_CASE)
+#undef CV_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+static cudaError_t dispatch_batch_occupancy(int ndim, bool pow2, int *occ)
+{
+    switch (ndim) {
+#define CV_CASE(D) case D: return batch_occupancy<D>(pow2, occ);
+        CV_FOR_EACH_NDIM(CV_CASE)
+#undef CV_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace cv
+
+// A set of integrals run together: per iteration one persistent sampling
+// launch per dimension class (ndim, power-of-two bins) over a queue of
+// tiles, then one batched refinement and one batched combination.
+struct cv_batch {
+    cv_ctx *ctx = nullptr;
+    int count = 0;
+    std::vector<cv_spec> specs;
+    std::vector<int> jmax;                       // iterations of each integral
+    std::vector<long long> n0;                   // first iteration size
+    void *mem = nullptr;                         // states, grids, histograms
+    BatchItem *d_items = nullptr;
+    CombineArgs *d_cargs = nullptr;
+    int2 *d_axes = nullptr;
+    int naxes = 0;
+    Tile *d_tiles = nullptr;
+    int *d_counters = nullptr;
+    size_t tiles_cap = 0, counters_cap = 0;
+    int J = 0;                                   // iterations of the longest run
+    // classes and their tile sizes (in 32-point blocks)
+    struct Class { int ndim; bool pow2; int tile_blocks; int grid; };
+    std::vector<Class> classes;
+    std::vector<int> item_class;
+    // launch plan: per iteration, per class: tile offset and count, counter index
+    struct Launch { int j, cls, tile_off, ntiles, counter; };
+    std::vector<Launch> plan;
+    cudaGraphExec_t exec = nullptr;
+    int kernels_per_run = 0;
+};
+
+static void batch_free_device(cv_batch *B)
+{
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+    if (B->mem) cudaFree(B->mem);
+    if (B->d_tiles) cudaFree(B->d_tiles);
+    if (B->d_counters) cudaFree(B->d_counters);
+    B->mem = nullptr;
+    B->d_tiles = nullptr;
+    B->d_counters = nullptr;
+}
+
+// Generate every tile of every iteration for the current tile sizes.
+static int batch_build_tiles(cv_batch *B, int only_first_iteration)
+{
+    cv_ctx *ctx = B->ctx;
+    std::vector<Tile> tiles;
+    B->plan.clear();
+    const int J = only_first_iteration ? 1 : B->J;
+    int counter = 0;
+    for (int j = 0; j < J; ++j) {
+        for (size_t c = 0; c < B->classes.size(); ++c) {
+            const int off = (int)tiles.size();
+            const int TB = B->classes[c].tile_blocks;
+            for (int i = 0; i < B->count; ++i) {
+                if (B->item_class[i] != (int)c || j >= B->jmax[i]) continue;
+                const cv_spec &sp = B->specs[i];
+                // start index and size of iteration j (the device follows the same plan)
+                unsigned long long s = 1;
+                for (int jj = 0; jj < j; ++jj) s += (unsigned long long)(sp.nstart + (long long)jj * sp.nincrease);
+                const unsigned long long n = (unsigned long long)(sp.nstart + (long long)j * sp.nincrease);
+                const unsigned long long qa = s >> 5, qb = (s + n + 31) >> 5;
+                for (unsigned long long q = qa; q < qb; q += (unsigned long long)TB) {
+                    Tile t;
+                    t.item = i;
+                    t.nblk = (int)(qb - q < (unsigned long long)TB ? qb - q : (unsigned long long)TB);
+                    t.q0 = q;
+                    tiles.push_back(t);
+                }
+            }
+            const int nt = (int)tiles.size() - off;
+            if (nt > 0) B->plan.push_back({j, (int)c, off, nt, counter++});
+        }
+    }
+    if (tiles.size() > B->tiles_cap) {
+        if (B->d_tiles) cudaFree(B->d_tiles);
+        B->d_tiles = nullptr;
+        if (cudaMalloc(&B->d_tiles, tiles.size() * sizeof(Tile)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail_msg(ctx, CV_ENOMEM, "tile queue allocation failed");
+        }
+        B->tiles_cap = tiles.size();
+    }
+    if ((size_t)counter > B->counters_cap) {
+        if (B->d_counters) cudaFree(B->d_counters);
+        B->d_counters = nullptr;
+        if (cudaMalloc(&B->d_counters, (size_t)counter * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail_msg(ctx, CV_ENOMEM, "tile counter allocation failed");
+        }
+        B->counters_cap = counter;
+    }
+    if (!tiles.empty()) {
+        CV_CUDA(ctx, cudaMemcpyAsync(B->d_tiles, tiles.data(), tiles.size() * sizeof(Tile),
+                                     cudaMemcpyHostToDevice, ctx->stream));
+        CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return CV_OK;
+}
+
+// Enqueue the whole run (reset + every iteration) on stream s.
+static int batch_enqueue(cv_batch *B, cudaStream_t s, int first_iteration_sampling_only)
+{
+    cv_ctx *ctx = B->ctx;
+    int kernels = 0;
+    if (B->counters_cap)
+        CV_CUDA(ctx, cudaMemsetAsync(B->d_counters, 0, B->counters_cap * sizeof(int), s));
+    CV_CUDA(ctx, launch_batch_reset(B->d_items, B->d_cargs, B->count, s));
+    ++kernels;
+    size_t p = 0;
+    const int J = first_iteration_sampling_only ? 1 : B->J;
+    for (int j = 0; j < J; ++j) {
+        for (; p < B->plan.size() && B->plan[p].j == j; ++p) {
+            const cv_batch::Launch &L = B->plan[p];
+            const cv_batch::Class &C = B->classes[L.cls];
+            BatchSampleArgs a;
+            a.items = B->d_items;
+            a.tiles = B->d_tiles + L.tile_off;
+            a.ntiles = L.ntiles;
+            a.counter = B->d_counters + L.counter;
+            const int grid = C.grid < L.ntiles ? C.grid : L.ntiles;
+            CV_CUDA(ctx, dispatch_batch_sample(C.ndim, C.pow2, a, grid, s));
+            ++kernels;
+        }
+        if (first_iteration_sampling_only) break;
+        CV_CUDA(ctx, launch_batch_refine(B->d_items, B->d_axes, B->naxes, s));
+        CV_CUDA(ctx, launch_batch_combine(B->d_cargs, B->count, s));
+        kernels += 2;
+    }
+    B->kernels_per_run = kernels;
+    return CV_OK;
+}
+
+static int batch_capture(cv_batch *B)
+{
+    cv_ctx *ctx = B->ctx;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    CV_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_enqueue(B, ctx->cap_stream, 0);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch graph capture");
+    e = cudaGraphInstantiate(&B->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch graph instantiate");
+    return CV_OK;
+}
+
+// Cost-model tile size: enough tiles for four per resident CTA, between 64
+// and 4096 blocks (2048 .. 131072 points).  CUBAGPU_TILE (points) overrides.
+static void batch_default_tiles(cv_batch *B)
+{
+    const char *env = getenv("CUBAGPU_TILE");
+    const long long forced = env ? atoll(env) : 0;
+    for (size_t c = 0; c < B->classes.size(); ++c) {
+        long long blocks = 0;
+        for (int i = 0; i < B->count; ++i)
+            if (B->item_class[i] == (int)c) blocks += (B->n0[i] + 31) / 32;
+        long long tb = blocks / (4LL * (B->classes[c].grid > 0 ? B->classes[c].grid : 1));
+        tb = (tb + 7) / 8 * 8;
+        if (tb < 64) tb = 64;
+        if (tb > 4096) tb = 4096;
+        if (forced > 0) tb = forced / 32 > 0 ? forced / 32 : 1;
+        B->classes[c].tile_blocks = (int)tb;
+    }
+}
+
+extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_batch **out)
+{
+    if (!ctx || !out) return CV_EINVAL;
+    *out = nullptr;
+    if (count < 1 || !specs) return fail_msg(ctx, CV_EINVAL, "empty batch");
+    for (int i = 0; i < count; ++i) {
+        int rc = check_spec(ctx, &specs[i]);
+        if (rc) return rc;
+        if (specs[i].flags & (CV_FP64 | CV_PLAIN))
+            return fail_msg(ctx, CV_EINVAL, "batched runs use the FP32 path (item %d asks for CV_FP64/CV_PLAIN)", i);
+    }
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    cv_batch *B = new cv_batch();
+    B->ctx = ctx;
+    B->count = count;
+    B->specs.assign(specs, specs + count);
+    B->jmax.resize(count);
+    B->n0.resize(count);
+    B->item_class.resize(count);
+    // per-integral device memory: state, grid, histogram
+    const size_t sz_state = (sizeof(DevState) + 255) & ~(size_t)255;
+    std::vector<size_t> off(count);
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        const int ndim = specs[i].g.ndim, N = specs[i].nbins;
+        long long nmax = 0;
+        plan(specs[i].nstart, specs[i].nincrease, specs[i].maxeval, &B->jmax[i], &nmax);
+        B->n0[i] = specs[i].nstart;
+        B->J = B->J > B->jmax[i] ? B->J : B->jmax[i];
+        off[i] = total;
+        total += sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255) +
+                 ((((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255);
+        const bool p2 = (N & (N - 1)) == 0;
+        int c = -1;
+        for (size_t k = 0; k < B->classes.size(); ++k)
+            if (B->classes[k].ndim == ndim && B->classes[k].pow2 == p2) c = (int)k;
+        if (c < 0) {
+            int occ = 0;
+            cudaError_t e = dispatch_batch_occupancy(ndim, p2, &occ);
+            if (e != cudaSuccess) {
+                delete B;
+                return cuda_fail(ctx, e, "batch occupancy query");
+            }
+            B->classes.push_back({ndim, p2, 64, ctx->sms * (occ > 0 ? occ : 1)});
+            c = (int)B->classes.size() - 1;
+        }
+        B->item_class[i] = c;
+    }
+    size_t sz_items = (((size_t)count * sizeof(BatchItem)) + 255) & ~(size_t)255;
+    size_t sz_cargs = (((size_t)count * sizeof(CombineArgs)) + 255) & ~(size_t)255;
+    B->naxes = 0;
+    for (int i = 0; i < count; ++i) B->naxes += specs[i].g.ndim;
+    size_t sz_axes = (size_t)B->naxes * sizeof(int2);
+    if (cudaMalloc(&B->mem, total + sz_items + sz_cargs + sz_axes) != cudaSuccess) {
+        cudaGetLastError();
+        delete B;
+        return fail_msg(ctx, CV_ENOMEM, "device allocation of %zu bytes for the batch failed", total);
+    }
+    char *base = (char *)B->mem;
+    B->d_items = (BatchItem *)(base + total);
+    B->d_cargs = (CombineArgs *)(base + total + sz_items);
+    B->d_axes = (int2 *)(base + total + sz_items + sz_cargs);
+    std::vector<BatchItem> items(count);
+    std::vector<CombineArgs> cargs(count);
+    std::vector<int2> axes;
+    axes.reserve(B->naxes);
+    for (int i = 0; i < count; ++i) {
+        const cv_spec &sp = specs[i];
+        const int ndim = sp.g.ndim, N = sp.nbins;
+        char *p = base + off[i];
+        BatchItem &it = items[i];
+        memset(&it, 0, sizeof(it));
+        fill_params<float>(&sp.g, &it.a.g);
+        it.a.nbins = N;
+        it.a.chunk_min = 4;
+        it.a.map = make_map(N);
+        it.st = (DevState *)p;
+        it.edges = (double *)(p + sz_state);
+        it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
+        CombineArgs &ca = cargs[i];
+        ca.st = it.st;
+        ca.ncomp = sp.g.ncomp;
+        ca.epsrel = sp.epsrel;
+        ca.epsabs = sp.epsabs;
+        ca.mineval = sp.mineval;
+        ca.maxeval = sp.maxeval;
+        ca.nstart = sp.nstart;
+        ca.nincrease = sp.nincrease;
+        ca.log_I = nullptr;
+        ca.log_var = nullptr;
+        for (int d = 0; d < ndim; ++d) axes.push_back(make_int2(i, d));
+    }
+    int rc = CV_OK;
+    cudaError_t e = cudaMemcpyAsync(B->d_items, items.data(), count * sizeof(BatchItem), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_cargs, cargs.data(), count * sizeof(CombineArgs), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_axes, axes.data(), axes.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "batch upload");
+    if (!rc) {
+        batch_default_tiles(B);
+        rc = batch_build_tiles(B, 0);
+    }
+    if (rc) {
+        batch_free_device(B);
+        delete B;
+        return rc;
+    }
+    ctx->batches.insert(B);
+    *out = B;
+    return CV_OK;
+}
+
+static void batch_release(cv_batch *B)
+{
+    batch_free_device(B);
+    delete B;
+}
+
+extern "C" void cv_batch_destroy(cv_batch *B)
+{
+    if (!B) return;
+    cv_ctx *ctx = B->ctx;
+    if (!ctx->batches.erase(B)) return;  // not (or no longer) a live handle
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    batch_release(B);
+}
+
+extern "C" int cv_batch_run(cv_batch *B)
+{
+    if (!B) return CV_EINVAL;
+    cv_ctx *ctx = B->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (!B->exec) {
+        int rc = batch_capture(B);
+        if (rc) return rc;
+    }
+    CV_CUDA(ctx, cudaGraphLaunch(B->exec, ctx->stream));
+    return CV_OK;
+}
+
+extern "C" int cv_batch_results(cv_batch *B, cv_result *out)
+{
+    if (!B || !out) return CV_EINVAL;
+    cv_ctx *ctx = B->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    std::vector<BatchItem> items(B->count);
+    CV_CUDA(ctx, cudaMemcpyAsync(items.data(), B->d_items, B->count * sizeof(BatchItem), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < B->count; ++i) {
+        DevState h;
+        CV_CUDA(ctx, cudaMemcpyAsync(&h, items[i].st, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+        CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cv_result &r = out[i];
+        memset(&r, 0, sizeof(r));
+        r.neval = h.neval;
+        r.fail = h.stopped ? h.fail : 1;
+        r.iterations = h.iter;
+        r.status = h.status;
+        for (int c = 0; c < B->specs[i].g.ncomp; ++c) {
+            r.integral[c] = h.integral[c];
+            r.error[c] = h.error[c];
+            r.prob[c] = h.prob[c];
+            r.chi2[c] = h.chi2[c];
+        }
+    }
+    return CV_OK;
+}
+
+extern "C" int cv_batch_kernels_per_run(const cv_batch *B) { return B ? B->kernels_per_run : 0; }
+
+extern "C" int cv_batch_tile_points(const cv_batch *B, int ndim, int pow2_bins)
+{
+    if (!B) return 0;
+    for (const cv_batch::Class &c : B->classes)
+        if (c.ndim == ndim && c.pow2 == (pow2_bins != 0)) return c.tile_blocks * 32;
+    return 0;
+}
+
+// Measured tuning: for every class, time its first-iteration sampling
+// launches with tile sizes 64..4096 blocks (a reset before each trial, so no
+// result is affected) and keep the fastest.
+extern "C" int cv_batch_autotune(cv_batch *B)
+{
+    if (!B) return CV_EINVAL;
+    cv_ctx *ctx = B->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    static const int cand[] = {64, 256, 1024, 4096};
+    const size_t ncls = B->classes.size();
+    std::vector<float> best(ncls, 1e30f);
+    std::vector<int> best_tb(ncls, 64);
+    cudaEvent_t e0, e1;
+    CV_CUDA(ctx, cudaEventCreate(&e0));
+    CV_CUDA(ctx, cudaEventCreate(&e1));
+    int rc = CV_OK;
+    for (int ci = 0; ci < 4 && !rc; ++ci) {
+        for (size_t c = 0; c < ncls; ++c) B->classes[c].tile_blocks = cand[ci];
+        rc = batch_build_tiles(B, 1);
+        if (rc) break;
+        if (B->counters_cap) cudaMemsetAsync(B->d_counters, 0, B->counters_cap * sizeof(int), ctx->stream);
+        launch_batch_reset(B->d_items, B->d_cargs, B->count, ctx->stream);
+        for (const cv_batch::Launch &L : B->plan) {
+            const cv_batch::Class &C = B->classes[L.cls];
+            BatchSampleArgs a;
+            a.items = B->d_items;
+            a.tiles = B->d_tiles + L.tile_off;
+            a.ntiles = L.ntiles;
+            a.counter = B->d_counters + L.counter;
+            cudaEventRecord(e0, ctx->stream);
+            cudaError_t e = dispatch_batch_sample(C.ndim, C.pow2, a, C.grid < L.ntiles ? C.grid : L.ntiles, ctx->stream);
+            cudaEventRecord(e1, ctx->stream);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(ctx, e, "autotune launch");
+                break;
+            }
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best[L.cls]) {
+                best[L.cls] = ms;
+                best_tb[L.cls] = cand[ci];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (size_t c = 0; c < ncls; ++c) B->classes[c].tile_blocks = best_tb[c];
+    if (!rc) rc = batch_build_tiles(B, 0);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+    return rc;
+}
+
+extern "C" int cv_batch_vegas(cv_ctx *ctx, int count, const cv_spec *specs, cv_result *out)
+{
+    if (!out) return fail_msg(ctx, CV_EINVAL, "null output");
+    cv_batch *B = nullptr;
+    int rc = cv_batch_create(ctx, count, specs, &B);
+    if (rc) return rc;
+    rc = cv_batch_run(B);
+    if (!rc) rc = cv_batch_results(B, out);
+    cv_batch_destroy(B);
+    return rc;
 }

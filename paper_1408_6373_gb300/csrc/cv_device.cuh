@@ -535,6 +535,110 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
     }
 }
 
+// ------------------------------------------------------------ batched kernel
+// Persistent sampling over a queue of tiles of many integrals (one
+// dimension class per launch).  A CTA takes the next tile from a device
+// counter; when the tile belongs to another integral than the last one, it
+// flushes its shared histogram to the old integral and stages the new
+// integral's grid and parameters.  Each tile's 32-point blocks are split
+// over the CTA's warps, and its sums go to the integral's FP64 accumulators.
+template <int NDIM>
+__device__ __forceinline__ void batch_flush_hist(const BatchItem &it, int N, const MapParams &m,
+                                                 const Smem<float> &sm)
+{
+    for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+        const int d = idx / N, k = idx - d * N;
+        const float v = sm.h[d * kStride + slot_of_bin(k, m)];
+        if (v != 0.0f) atomicAdd(&it.H[idx], (double)v);
+    }
+}
+
+template <int NDIM, bool POW2>
+__global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, float>))
+k_batch_sample(const BatchSampleArgs B)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<float> sm;
+    sm.e = reinterpret_cast<float *>(smem_raw);
+    sm.w = sm.e + NDIM * kStride;
+    sm.h = sm.w + NDIM * kStride;
+    __shared__ SampleArgs<float> A;
+    __shared__ int s_tile;
+    __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(B.counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= B.ntiles) break;
+        const Tile tile = B.tiles[t];
+        const BatchItem &it = B.items[tile.item];
+        if (*(volatile const int *)&it.st->stopped) {
+            __syncthreads();
+            continue;
+        }
+        if (tile.item != cur) {
+            if (cur >= 0) batch_flush_hist<NDIM>(B.items[cur], A.nbins, A.map, sm);
+            __syncthreads();
+            // stage the integral's parameters and grid
+            const int *src = reinterpret_cast<const int *>(&it.a);
+            int *dst = reinterpret_cast<int *>(&A);
+            for (int i = threadIdx.x; i < (int)(sizeof(SampleArgs<float>) / sizeof(int)); i += blockDim.x)
+                dst[i] = src[i];
+            __syncthreads();
+            const int N = A.nbins;
+            for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+                const int d = idx / N, k = idx - d * N;
+                const double *e = it.edges + (size_t)d * (N + 1);
+                const int p = d * kStride + slot_of_bin(k, A.map);
+                const double w = e[k + 1] - e[k];
+                sm.e[p] = __double2float_rn(e[k]);
+                sm.w[p] = __double2float_rn(POW2 ? (double)N * w : w);
+                sm.h[p] = 0.0f;
+            }
+            cur = tile.item;
+            __syncthreads();
+        }
+        const unsigned long long start = it.st->next_index;
+        const unsigned long long end = start + (unsigned long long)it.st->n_cur;
+        Acc<float> s1[CV_MAX_COMP], s2[CV_MAX_COMP];
+        const unsigned per = ((unsigned)tile.nblk + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const unsigned long long w0 = tile.q0 + (unsigned long long)warp * per;
+        const unsigned long long w1 = min(w0 + per, tile.q0 + (unsigned long long)tile.nblk);
+        if (w0 < w1) {
+            unsigned X[NDIM];
+            sobol_skip<NDIM, unsigned>(X, w0, lane);
+            const bool interior = (w0 * 32ull >= start) && (w1 * 32ull <= end);
+            if (interior)
+                run_steps<NDIM, float, POW2, false>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
+            else
+                run_steps<NDIM, float, POW2, true>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
+        }
+        const int ncomp = A.g.ncomp;
+#pragma unroll
+        for (int c = 0; c < CV_MAX_COMP; ++c) {
+            if (c < ncomp) {
+                const double a = warp_total(s1[c]);
+                const double b = warp_total(s2[c]);
+                if (lane == 0) {
+                    red[warp][2 * c] = a;
+                    red[warp][2 * c + 1] = b;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 2 * ncomp) {
+            double v = 0.0;
+            for (int w = 0; w < kWarpsPerBlock; ++w) v += red[w][threadIdx.x];
+            const int c = threadIdx.x >> 1;
+            atomicAdd((threadIdx.x & 1) ? &it.st->S2[c] : &it.st->S1[c], v);
+        }
+        __syncthreads();
+    }
+    if (cur >= 0) batch_flush_hist<NDIM>(B.items[cur], A.nbins, A.map, sm);
+}
+
 // Sobol coordinates only (the point generator of the sampling kernels,
 // written out for bit-exact checks): Y[d*n + j] = X_d(start + j) >> shift.
 template <int NDIM, typename W>
@@ -608,6 +712,25 @@ cudaError_t sample_occupancy(int nbins, int *blocks_per_sm)
                                                          kBlock, smem);
 }
 
+template <int NDIM, bool POW2>
+cudaError_t launch_batch_sample(const BatchSampleArgs &b, int grid, cudaStream_t s)
+{
+    // (batch_occupancy, always called first, sets the shared-memory limit)
+    const size_t smem = sample_smem_bytes(NDIM, CV_MAX_BINS, false);
+    k_batch_sample<NDIM, POW2><<<grid, kBlock, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <int NDIM>
+cudaError_t batch_occupancy(bool pow2, int *blocks_per_sm)
+{
+    const size_t smem = sample_smem_bytes(NDIM, CV_MAX_BINS, false);
+    void *f = pow2 ? (void *)k_batch_sample<NDIM, true> : (void *)k_batch_sample<NDIM, false>;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBlock, smem);
+}
+
 template <int NDIM, typename W>
 cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
                          unsigned long long *Y, int grid, cudaStream_t s)
@@ -626,6 +749,11 @@ cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
                                                       cudaStream_t);                        \
     template cudaError_t cv::sample_occupancy<D, float>(int, int *);                        \
     template cudaError_t cv::sample_occupancy<D, double>(int, int *);                       \
+    template cudaError_t cv::launch_batch_sample<D, true>(const cv::BatchSampleArgs &, int,  \
+                                                          cudaStream_t);                    \
+    template cudaError_t cv::launch_batch_sample<D, false>(const cv::BatchSampleArgs &, int, \
+                                                           cudaStream_t);                   \
+    template cudaError_t cv::batch_occupancy<D>(bool, int *);                               \
     template cudaError_t cv::launch_sobol<D, unsigned int>(unsigned long long, long long,   \
                                                            int, unsigned long long *, int,  \
                                                            cudaStream_t);                   \

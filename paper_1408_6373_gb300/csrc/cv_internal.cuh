@@ -96,12 +96,40 @@ struct CombineArgs {
     double *log_var;
 };
 
+// ---- batched persistent launch (many integrals) ----
+// One integral of a batch as the device sees it.
+struct BatchItem {
+    SampleArgs<float> a;            // parameters, map, nbins (pointers unused)
+    DevState *st;
+    double *edges;                  // [ndim][nbins+1]
+    double *H;                      // [ndim][nbins]
+};
+
+// A tile: nblk consecutive 32-point Sobol blocks of one integral's
+// iteration, starting at absolute block q0.
+struct Tile {
+    int item;
+    int nblk;
+    unsigned long long q0;
+};
+
+struct BatchSampleArgs {
+    const BatchItem *items;
+    const Tile *tiles;
+    int ntiles;
+    int *counter;                   // next tile to take (zero before the launch)
+};
+
 // ---- launchers (template definitions in cv_device.cuh, instantiated per
 // ---- dimension range in cv_sample_*.cu) ----
 template <int NDIM, typename Real>
 cudaError_t launch_sample(const SampleArgs<Real> &a, int grid, cudaStream_t s);
 template <int NDIM, typename Real>
 cudaError_t sample_occupancy(int nbins, int *blocks_per_sm);
+template <int NDIM, bool POW2>
+cudaError_t launch_batch_sample(const BatchSampleArgs &b, int grid, cudaStream_t s);
+template <int NDIM>
+cudaError_t batch_occupancy(bool pow2, int *blocks_per_sm);
 template <int NDIM, typename Word>
 cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
                          unsigned long long *Y, int grid, cudaStream_t s);
@@ -112,6 +140,11 @@ cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
                                   const CombineArgs &a, cudaStream_t s);
 cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int nbins,
                          long long nstart, cudaStream_t s);
+cudaError_t launch_batch_reset(const BatchItem *items, const CombineArgs *cargs, int count,
+                               cudaStream_t s);
+cudaError_t launch_batch_refine(const BatchItem *items, const int2 *axes, int naxes,
+                                cudaStream_t s);
+cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream_t s);
 
 inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64) {
     // grid {e, w} pairs plus the block histogram, CV_MAX_BINS slots per axis

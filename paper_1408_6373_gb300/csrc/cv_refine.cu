@@ -272,6 +272,61 @@ __global__ void k_reset(DevState *st, double *edges, double *H, int ndim, int N,
     }
 }
 
+// ---- batched forms: one CTA per integral (reset, combine) or per
+// (integral, axis) (refine).  An integral whose run has stopped is skipped;
+// its stop flag is only ever set by a later combine launch.
+__global__ void k_batch_reset(const BatchItem *items, const CombineArgs *cargs)
+{
+    const BatchItem &it = items[blockIdx.x];
+    const int N = it.a.nbins, ndim = it.a.g.ndim;
+    for (int i = threadIdx.x; i < ndim * (N + 1); i += blockDim.x) {
+        const int k = i % (N + 1);
+        it.edges[i] = (double)k / (double)N;
+    }
+    for (int i = threadIdx.x; i < ndim * N; i += blockDim.x) it.H[i] = 0.0;
+    int *w = reinterpret_cast<int *>(it.st);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevState) / sizeof(int)); i += blockDim.x) w[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        it.st->next_index = 1ull;
+        it.st->n_cur = cargs[blockIdx.x].nstart;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_refine(const BatchItem *items, const int2 *axes)
+{
+    const int2 ax = axes[blockIdx.x];
+    const BatchItem &it = items[ax.x];
+    if (*(volatile const int *)&it.st->stopped) return;
+    refine_axis(ax.y, it.a.nbins, it.H, it.edges, 1);
+}
+
+__global__ void k_batch_combine(const CombineArgs *cargs)
+{
+    const CombineArgs &A = cargs[blockIdx.x];
+    if (*(volatile const int *)&A.st->stopped) return;
+    combine_iteration(A);
+}
+
+cudaError_t launch_batch_reset(const BatchItem *items, const CombineArgs *cargs, int count,
+                               cudaStream_t s)
+{
+    k_batch_reset<<<count, 256, 0, s>>>(items, cargs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_refine(const BatchItem *items, const int2 *axes, int naxes, cudaStream_t s)
+{
+    k_batch_refine<<<naxes, 256, 0, s>>>(items, axes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream_t s)
+{
+    k_batch_combine<<<count, 32, 0, s>>>(cargs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int nbins,
                          long long nstart, cudaStream_t s)
 {

@@ -1,0 +1,101 @@
+"""GPU tests of the batched persistent path (cv_batch_*): every integral of
+a batch against the same integral run alone (cv_vegas, FP32 path) and
+against the FP64 oracle's closed forms; uneven sizes, mixed dimensions and
+bin counts, early stops, and the tile autotuner."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1408_6373_gb300 as cg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cg.build_library()
+    c = cg.Context(0)
+    yield c
+    c.close()
+
+
+def _specs(count, seed, nmin=300, nmax=60000, iters=5, nbins_choices=(64, 32, 50)):
+    rng = np.random.default_rng(seed)
+    specs, probs = [], []
+    for i in range(count):
+        ndim = int(rng.integers(1, 17))
+        fam = int(rng.integers(0, 6))
+        a = 0.5 + rng.random(ndim)
+        u = rng.random(ndim)
+        n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
+        nbins = int(rng.choice(nbins_choices))
+        g = cg.genz(ndim, [fam], a, u)
+        specs.append(cg.spec(g, nbins=nbins, maxeval=iters * n, nstart=n))
+        probs.append(O.Problem(ndim, [fam], a[None], u[None], nbins=nbins, bits=23, fp32_decide=True))
+    return specs, probs
+
+
+def test_batch_matches_single_runs(ctx):
+    specs, probs = _specs(24, 1)
+    res = ctx.batch_vegas(specs)
+    for sp, r, p in zip(specs, res, probs):
+        single = ctx.vegas(sp.g, flags=0, maxeval=sp.maxeval, nstart=sp.nstart, nbins=sp.nbins)
+        assert (r.neval, r.fail) == (single.neval, single.fail)
+        assert r.integral[0] == pytest.approx(single.integral[0], rel=2e-5, abs=1e-9 * abs(single.error[0]) + 1e-30)
+        exact = p.exact()[0]
+        assert abs(r.integral[0] - exact) <= 4 * r.error[0] + 2e-6 * abs(exact) + 1e-12
+
+
+def test_batch_alone_equals_in_mix(ctx):
+    specs, _ = _specs(10, 2)
+    mix = ctx.batch_vegas(specs)
+    for k in (0, 4, 9):
+        alone = ctx.batch_vegas([specs[k]])[0]
+        assert alone.neval == mix[k].neval
+        assert alone.integral[0] == pytest.approx(mix[k].integral[0], rel=2e-5)
+        assert alone.error[0] == pytest.approx(mix[k].error[0], rel=1e-3)
+
+
+def test_batch_accuracy_goals_stop_each_integral(ctx):
+    specs, _ = _specs(12, 3, nmin=2000, nmax=20000, iters=30)
+    for i, sp in enumerate(specs):
+        if i % 2 == 0:
+            sp.epsrel = 1e-3
+            sp.nincrease = 1000
+            sp.maxeval = 10 ** 6
+    res = ctx.batch_vegas(specs)
+    for i, (sp, r) in enumerate(zip(specs, res)):
+        single = ctx.vegas(sp.g, epsrel=sp.epsrel, flags=0, maxeval=sp.maxeval, nstart=sp.nstart,
+                           nincrease=sp.nincrease, nbins=sp.nbins)
+        assert (r.neval, r.fail) == (single.neval, single.fail)
+        if i % 2 == 0 and r.fail == 0:
+            assert r.error[0] <= 1e-3 * abs(r.integral[0])
+
+
+def test_batch_rerun_and_autotune_keep_results(ctx):
+    specs, _ = _specs(16, 4, nmin=1000, nmax=100000, iters=4)
+    B = ctx.batch(specs)
+    B.run()
+    r1 = B.results()
+    B.autotune()
+    assert B.tile_points(specs[0].g.ndim, (specs[0].nbins & (specs[0].nbins - 1)) == 0) >= 2048
+    B.run()
+    r2 = B.results()
+    for a, b in zip(r1, r2):
+        assert a.neval == b.neval
+        assert a.integral[0] == pytest.approx(b.integral[0], rel=2e-5)
+    assert B.kernels_per_run() > 0
+    B.close()
+
+
+def test_batch_tiny_and_ragged_sizes(ctx):
+    g = cg.genz(3, [cg.CONST], 1.0, 0.5)
+    specs = [cg.spec(g, nbins=32, maxeval=2 * n, nstart=n) for n in (2, 31, 33, 1000)]
+    for r, sp in zip(ctx.batch_vegas(specs), specs):
+        assert r.integral[0] == 1.0 and r.error[0] == 0.0 and r.neval == sp.nstart
