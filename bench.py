@@ -368,6 +368,8 @@ def run_ours(args):
                    "plain_fp64_error": list(rp.error)[: p.ncomp]},
         "wall_s_timed_region": wall,
     }
+    if not args.no_batch:
+        line["batch4096"] = measure_batch(ctx, cg, W, args.warmup, args.steps)
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         rate, dt, n = cpu_oracle_rate(p, args.cpu_seconds, threads)
@@ -384,6 +386,57 @@ def run_ours(args):
     return 0
 
 
+def measure_batch(ctx, cg, W, warmup: int, steps: int, subset: int = 32) -> dict:
+    """The batched persistent path on the 4096-integral workload: device-timed
+    runs after autotuning, plus the plain FP64 one-launch-per-iteration
+    comparator (host sync per iteration) on a seeded subset of integrals."""
+    import torch
+    probs = W.batch4096()
+    specs = [cg.spec(cg.genz(p.ndim, p.families, p.a, p.u), nbins=p.nbins, maxeval=p.maxeval,
+                     nstart=p.nstart, nincrease=p.nincrease) for p in probs]
+    samples = sum(p.maxeval for p in probs)
+    B = ctx.batch(specs)
+    t = time.perf_counter()
+    B.autotune()
+    tune_s = time.perf_counter() - t
+    for _ in range(max(1, warmup // 3)):
+        B.run()
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(max(1, steps // 2)):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        B.run()
+        s1.record()
+        ev.append((s0, s1))
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    res = B.results()
+    launches = B.kernels_per_run()
+    tiles = {d: B.tile_points(d, True) for d in sorted({p.ndim for p in probs})}
+    B.close()
+    # plain FP64 comparator on a subset (the full set would take ~30 s)
+    idx = list(range(0, len(probs), len(probs) // subset))[:subset]
+    sub_samples = sum(probs[i].maxeval for i in idx)
+    t = time.perf_counter()
+    dev = []
+    for i in idx:
+        p = probs[i]
+        rp = ctx.vegas(cg.genz(p.ndim, p.families, p.a, p.u), flags=cg.FP64 | cg.PLAIN,
+                       maxeval=p.maxeval, nstart=p.nstart, nbins=p.nbins)
+        r = res[i]
+        dev.append(abs(r.integral[0] - rp.integral[0]) / max(rp.error[0], 1e-300))
+    plain_s = time.perf_counter() - t
+    return {"workload": "batch4096: 4096 integrals, ndim U{2..16}, family U{0..5}, n/iter "
+                        "log-uniform 1e4..1e7, 10 iterations, 64 bins, FP32 eval / FP64 reduce",
+            "value": samples / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "samples_per_step": samples, "gpu_launches_per_step": launches,
+            "autotune_s": tune_s, "tile_points_by_ndim": tiles,
+            "plain_fp64_subset": {"integrals": len(idx), "value": sub_samples / plain_s,
+                                  "unit": UNIT,
+                                  "max_abs_diff_in_sigma": max(dev)}}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,6 +444,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 4096-integral batch")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps

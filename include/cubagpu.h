@@ -102,8 +102,8 @@ typedef struct cv_ctx cv_ctx;
  * cudaStream_t; NULL = the context creates its own non-blocking stream;
  * pass cudaStreamLegacy, (void *)1, for the legacy default stream).
  * The context owns the library's device memory; cv_destroy releases it,
- * including every cv_integral and cv_batch still attached to it, whose
- * handles then become invalid (the analogue of cubawait for the spinning workers,
+ * including every cv_integral, cv_batch and cv_server still attached to
+ * it, whose handles then become invalid (the analogue of cubawait for the spinning workers,
  * Sect. 3.2.3). */
 int cv_create(cv_ctx **ctx, int device, void *stream);
 void cv_destroy(cv_ctx *ctx);
@@ -271,6 +271,44 @@ int cv_batch_kernels_per_run(const cv_batch *B);
 void cv_batch_destroy(cv_batch *B);
 /* create + run + results + destroy. */
 int cv_batch_vegas(cv_ctx *ctx, int count, const cv_spec *specs, cv_result *out);
+
+/* --------------------------------------------------------------- serving */
+/* A request loop with continuous batching: requests of any ndim, ncomp and
+ * accuracy goal are submitted from any host thread; a worker thread admits
+ * them in arrival order while a slot and the device-memory budget allow,
+ * keeps each admitted request's grid and sums resident on the device, and
+ * runs rounds in which every admitted request advances by one iteration
+ * through the batched kernels (requests that arrive meanwhile join at the
+ * next round boundary).  A request whose goal or budget is reached leaves
+ * at once and frees its slot and memory.  Each request's result equals
+ * what cv_vegas returns for it alone (FP32 path), up to summation order.
+ * The analogue of the paper's spinning cores (Sect. 3.2.3): the worker and
+ * its device state persist between integrations until cv_server_stop. */
+typedef struct {
+    int64_t hbm_budget_bytes;  /* device memory for request state (0: 1 GiB) */
+    int max_live;              /* requests on the device at once (0: 4096)    */
+    int tile_points;           /* points per tile (0: automatic)              */
+} cv_server_opts;
+
+typedef struct {
+    int64_t submitted, completed, rounds, samples;
+    int max_live;              /* most requests on the device in one round    */
+    int pending;               /* requests waiting for admission now          */
+    double p50_ms, p99_ms, max_ms;  /* submit-to-result latency               */
+    double busy_s, wall_s;     /* time in rounds, time since start            */
+} cv_serve_stats;
+
+typedef struct cv_server cv_server;
+int cv_server_start(cv_ctx *ctx, const cv_server_opts *opts, cv_server **out);
+/* Queue a request (FP32 path); CV_EADMIT if it can never fit the budget. */
+int cv_submit(cv_server *S, const cv_spec *spec, uint64_t *id);
+/* CV_OK with the result, CV_EBUSY while it runs, CV_ENOTFOUND. */
+int cv_poll(cv_server *S, uint64_t id, cv_result *out);
+/* Wait up to timeout_ms; CV_ETIMEOUT if it has not finished. */
+int cv_wait(cv_server *S, uint64_t id, int timeout_ms, cv_result *out);
+int cv_server_stats(cv_server *S, cv_serve_stats *out);
+/* Finish every submitted request, stop the worker, release the server. */
+int cv_server_stop(cv_server *S);
 
 #ifdef __cplusplus
 }

@@ -109,6 +109,22 @@ def spec(g: Genz, nbins=64, flags=0, epsrel=0.0, epsabs=0.0, mineval=0, maxeval=
     return s
 
 
+class ServerOpts(ctypes.Structure):
+    """cv_server_opts."""
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_live", ctypes.c_int),
+                ("tile_points", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    """cv_serve_stats."""
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rounds", ctypes.c_int64), ("samples", ctypes.c_int64),
+                ("max_live", ctypes.c_int), ("pending", ctypes.c_int),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("wall_s", ctypes.c_double)]
+
+
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -146,6 +162,12 @@ _SIGNATURES = {
     "cv_batch_kernels_per_run": (_i, [_vp]),
     "cv_batch_destroy": (None, [_vp]),
     "cv_batch_vegas": (_i, [_vp, _i, _vp, _vp]),
+    "cv_server_start": (_i, [_vp, _P(ServerOpts), _P(_vp)]),
+    "cv_submit": (_i, [_vp, _P(Spec), _P(_u64)]),
+    "cv_poll": (_i, [_vp, _u64, _P(Result)]),
+    "cv_wait": (_i, [_vp, _u64, _i, _P(Result)]),
+    "cv_server_stats": (_i, [_vp, _P(ServeStats)]),
+    "cv_server_stop": (_i, [_vp]),
 }
 
 _lib = None
@@ -262,6 +284,9 @@ class Context:
 
     def integral(self, sp: Spec) -> "Integral":
         return Integral(self, sp)
+
+    def server(self, hbm_budget_bytes=0, max_live=0, tile_points=0) -> "Server":
+        return Server(self, hbm_budget_bytes, max_live, tile_points)
 
     def batch(self, specs) -> "Batch":
         return Batch(self, specs)
@@ -395,3 +420,54 @@ class Batch:
 
     def kernels_per_run(self) -> int:
         return self.ctx._lib.cv_batch_kernels_per_run(self._h)
+
+
+class Server:
+    """cv_server: continuous-batching request loop on the device."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes=0, max_live=0, tile_points=0):
+        self.ctx = ctx
+        o = ServerOpts(hbm_budget_bytes, max_live, tile_points)
+        self._h = ctypes.c_void_p()
+        ctx._check(ctx._lib.cv_server_start(ctx._h, ctypes.byref(o), ctypes.byref(self._h)),
+                   "cv_server_start")
+        ctx._children.add(self)
+
+    def submit(self, sp: Spec) -> int:
+        rid = ctypes.c_uint64()
+        self.ctx._check(self.ctx._lib.cv_submit(self._h, ctypes.byref(sp), ctypes.byref(rid)),
+                        "cv_submit")
+        return rid.value
+
+    def poll(self, rid: int):
+        """Result, or None while the request runs."""
+        r = Result()
+        rc = self.ctx._lib.cv_poll(self._h, rid, ctypes.byref(r))
+        if rc == EBUSY:
+            return None
+        self.ctx._check(rc, "cv_poll")
+        return r
+
+    def wait(self, rid: int, timeout_ms: int = 60000) -> Result:
+        r = Result()
+        self.ctx._check(self.ctx._lib.cv_wait(self._h, rid, timeout_ms, ctypes.byref(r)), "cv_wait")
+        return r
+
+    def stats(self) -> ServeStats:
+        st = ServeStats()
+        self.ctx._check(self.ctx._lib.cv_server_stats(self._h, ctypes.byref(st)), "cv_server_stats")
+        return st
+
+    def stop(self):
+        if self._h:
+            h, self._h = self._h, ctypes.c_void_p()
+            if self.ctx._h:
+                self.ctx._check(self.ctx._lib.cv_server_stop(h), "cv_server_stop")
+
+    close = stop
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

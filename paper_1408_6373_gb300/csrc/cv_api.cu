@@ -81,10 +81,12 @@ struct cv_ctx {
     // caller has not destroyed them)
     std::set<struct cv_integral *> integrals;
     std::set<struct cv_batch *> batches;
+    std::set<struct cv_server *> servers;
 };
 
 static void integral_free(struct cv_integral *I);
 static void batch_release(struct cv_batch *B);
+static void server_release(struct cv_server *S);
 
 static int fail_msg(cv_ctx *ctx, int code, const char *fmt, ...)
 {
@@ -168,6 +170,8 @@ extern "C" void cv_destroy(cv_ctx *ctx)
     ctx->integrals.clear();
     for (struct cv_batch *B : ctx->batches) batch_release(B);
     ctx->batches.clear();
+    for (struct cv_server *S : ctx->servers) server_release(S);
+    ctx->servers.clear();
     cudaStreamDestroy(ctx->cap_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1130,4 +1134,479 @@ extern "C" int cv_batch_vegas(cv_ctx *ctx, int count, const cv_spec *specs, cv_r
     if (!rc) rc = cv_batch_results(B, out);
     cv_batch_destroy(B);
     return rc;
+}
+
+// ------------------------------------------------------------ serving loop
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator of device offsets inside the server's arena (the HBM
+// budget), 256-byte granules, neighbours coalesced on free.
+class Arena {
+public:
+    explicit Arena(size_t bytes) { free_[0] = bytes; }
+    bool alloc(size_t bytes, size_t *off)
+    {
+        bytes = (bytes + 255) & ~(size_t)255;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = (bytes + 255) & ~(size_t)255;
+        auto it = free_.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+private:
+    std::map<size_t, size_t> free_;
+};
+
+size_t request_bytes(const cv_spec &sp)
+{
+    const size_t st = (sizeof(DevState) + 255) & ~(size_t)255;
+    const size_t e = (((size_t)sp.g.ndim * (sp.nbins + 1) * sizeof(double)) + 255) & ~(size_t)255;
+    const size_t h = (((size_t)sp.g.ndim * sp.nbins * sizeof(double)) + 255) & ~(size_t)255;
+    return st + e + h;
+}
+
+struct Request {
+    uint64_t id;
+    cv_spec spec;
+    Clock::time_point arrival;
+    // while live
+    int slot = -1;
+    size_t off = 0, bytes = 0;
+    int j = 0;                          // iterations done (host mirror of the device plan)
+    unsigned long long next_index = 1;
+    int jmax = 0;
+};
+
+}  // namespace
+
+struct cv_server {
+    cv_ctx *ctx = nullptr;
+    cv_server_opts opts;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_new, cv_done;
+    bool stopping = false;
+    int error = CV_OK;
+    uint64_t next_id = 1;
+    std::deque<Request> pending;
+    std::map<uint64_t, cv_result> done;
+    std::map<uint64_t, double> latency_ms;
+    // statistics
+    int64_t submitted = 0, completed = 0, rounds = 0, samples = 0;
+    int max_live_seen = 0;
+    double busy_s = 0;
+    Clock::time_point t_start;
+    // device resources (worker thread only)
+    cudaStream_t stream = nullptr;
+    void *arena_mem = nullptr;
+    BatchItem *d_items = nullptr;
+    CombineArgs *d_cargs = nullptr;
+    int *d_lists = nullptr;              // reset list | combine/gather list
+    int2 *d_axes = nullptr;
+    Tile *d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    int *d_counters = nullptr;
+    DevState *d_gather = nullptr;
+    DevState *h_gather = nullptr;        // pinned
+    std::vector<int> class_grid;         // persistent grid per (ndim, pow2) class, 0 = unknown
+};
+
+namespace {
+
+int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
+                 std::vector<int> &free_slots)
+{
+    cv_ctx *ctx = S->ctx;
+    const int max_live = S->opts.max_live;
+    // ---- admission: FIFO, while a slot and the budget allow
+    std::vector<int> fresh;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        while (!S->pending.empty() && !free_slots.empty()) {
+            Request &r = S->pending.front();
+            size_t off;
+            if (!arena.alloc(r.bytes, &off)) break;
+            r.off = off;
+            r.slot = free_slots.back();
+            free_slots.pop_back();
+            long long nmax = 0;
+            plan(r.spec.nstart, r.spec.nincrease, r.spec.maxeval, &r.jmax, &nmax);
+            live.push_back(r);
+            fresh.push_back(r.slot);
+            S->pending.pop_front();
+        }
+    }
+    (void)max_live;
+    if (live.empty()) return CV_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if ((int)live.size() > S->max_live_seen) S->max_live_seen = (int)live.size();
+    }
+    const auto t0 = Clock::now();
+    // descriptors of newly admitted requests
+    const size_t sz_state = (sizeof(DevState) + 255) & ~(size_t)255;
+    for (const Request &r : live) {
+        if (std::find(fresh.begin(), fresh.end(), r.slot) == fresh.end()) continue;
+        const cv_spec &sp = r.spec;
+        const int ndim = sp.g.ndim, N = sp.nbins;
+        char *p = (char *)S->arena_mem + r.off;
+        BatchItem it;
+        memset(&it, 0, sizeof(it));
+        fill_params<float>(&sp.g, &it.a.g);
+        it.a.nbins = N;
+        it.a.chunk_min = 4;
+        it.a.map = make_map(N);
+        it.st = (DevState *)p;
+        it.edges = (double *)(p + sz_state);
+        it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
+        CombineArgs ca;
+        ca.st = it.st;
+        ca.ncomp = sp.g.ncomp;
+        ca.epsrel = sp.epsrel;
+        ca.epsabs = sp.epsabs;
+        ca.mineval = sp.mineval;
+        ca.maxeval = sp.maxeval;
+        ca.nstart = sp.nstart;
+        ca.nincrease = sp.nincrease;
+        ca.log_I = nullptr;
+        ca.log_var = nullptr;
+        CV_CUDA(ctx, cudaMemcpyAsync(S->d_items + r.slot, &it, sizeof(it), cudaMemcpyHostToDevice, S->stream));
+        CV_CUDA(ctx, cudaMemcpyAsync(S->d_cargs + r.slot, &ca, sizeof(ca), cudaMemcpyHostToDevice, S->stream));
+    }
+    // ---- this round's work: one iteration of every live request
+    std::vector<int> lists(fresh);
+    const int nfresh = (int)fresh.size();
+    std::vector<int2> axes;
+    for (const Request &r : live) {
+        lists.push_back(r.slot);
+        for (int d = 0; d < r.spec.g.ndim; ++d) axes.push_back(make_int2(r.slot, d));
+    }
+    const int nlive = (int)live.size();
+    // tiles grouped by dimension class
+    struct Cls { int ndim; bool pow2; std::vector<Tile> tiles; };
+    std::vector<Cls> cls;
+    long long round_blocks = 0;
+    int64_t round_samples = 0;
+    for (const Request &r : live) round_blocks += (r.spec.nstart + (long long)r.j * r.spec.nincrease + 31) / 32;
+    long long tb = round_blocks / (4LL * ctx->sms * 2);
+    tb = std::max(64LL, std::min(4096LL, (tb + 7) / 8 * 8));
+    if (S->opts.tile_points > 0) tb = std::max(1, S->opts.tile_points / 32);
+    for (const Request &r : live) {
+        const int ndim = r.spec.g.ndim;
+        const bool p2 = (r.spec.nbins & (r.spec.nbins - 1)) == 0;
+        Cls *c = nullptr;
+        for (Cls &k : cls)
+            if (k.ndim == ndim && k.pow2 == p2) c = &k;
+        if (!c) {
+            cls.push_back({ndim, p2, {}});
+            c = &cls.back();
+        }
+        const unsigned long long s = r.next_index;
+        const unsigned long long n = (unsigned long long)(r.spec.nstart + (long long)r.j * r.spec.nincrease);
+        const unsigned long long qa = s >> 5, qb = (s + n + 31) >> 5;
+        for (unsigned long long q = qa; q < qb; q += (unsigned long long)tb) {
+            Tile t;
+            t.item = r.slot;
+            t.nblk = (int)std::min<unsigned long long>(qb - q, (unsigned long long)tb);
+            t.q0 = q;
+            c->tiles.push_back(t);
+        }
+        round_samples += (int64_t)n;
+    }
+    size_t ntiles = 0;
+    for (const Cls &c : cls) ntiles += c.tiles.size();
+    if (ntiles > S->tiles_cap) {
+        if (S->d_tiles) cudaFree(S->d_tiles);
+        S->d_tiles = nullptr;
+        const size_t cap = std::max(ntiles, 2 * S->tiles_cap);
+        CV_CUDA(ctx, cudaMalloc(&S->d_tiles, cap * sizeof(Tile)));
+        S->tiles_cap = cap;
+    }
+    std::vector<Tile> all;
+    all.reserve(ntiles);
+    for (const Cls &c : cls) all.insert(all.end(), c.tiles.begin(), c.tiles.end());
+    CV_CUDA(ctx, cudaMemcpyAsync(S->d_tiles, all.data(), all.size() * sizeof(Tile), cudaMemcpyHostToDevice, S->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(S->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, S->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(S->d_axes, axes.data(), axes.size() * sizeof(int2), cudaMemcpyHostToDevice, S->stream));
+    CV_CUDA(ctx, cudaMemsetAsync(S->d_counters, 0, 2 * (CV_MAX_DIM + 1) * sizeof(int), S->stream));
+    CV_CUDA(ctx, launch_batch_reset(S->d_items, S->d_cargs, nfresh, S->stream, S->d_lists));
+    size_t off = 0;
+    for (const Cls &c : cls) {
+        int &g = S->class_grid[(c.pow2 ? 1 : 0) * (CV_MAX_DIM + 1) + c.ndim];
+        if (!g) {
+            int occ = 0;
+            CV_CUDA(ctx, dispatch_batch_occupancy(c.ndim, c.pow2, &occ));
+            g = ctx->sms * std::max(occ, 1);
+        }
+        BatchSampleArgs a;
+        a.items = S->d_items;
+        a.tiles = S->d_tiles + off;
+        a.ntiles = (int)c.tiles.size();
+        a.counter = S->d_counters + (c.pow2 ? 1 : 0) * (CV_MAX_DIM + 1) + c.ndim;
+        CV_CUDA(ctx, dispatch_batch_sample(c.ndim, c.pow2, a, std::min<int>(g, a.ntiles), S->stream));
+        off += c.tiles.size();
+    }
+    CV_CUDA(ctx, launch_batch_refine(S->d_items, S->d_axes, (int)axes.size(), S->stream));
+    CV_CUDA(ctx, launch_batch_combine(S->d_cargs, nlive, S->stream, S->d_lists + nfresh));
+    CV_CUDA(ctx, launch_gather_states(S->d_items, S->d_lists + nfresh, nlive, S->d_gather, S->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(S->h_gather, S->d_gather, nlive * sizeof(DevState), cudaMemcpyDeviceToHost, S->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(S->stream));
+    const auto t1 = Clock::now();
+    // ---- retire finished requests, advance the rest
+    std::vector<Request> keep;
+    keep.reserve(live.size());
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->busy_s += std::chrono::duration<double>(t1 - t0).count();
+        ++S->rounds;
+        S->samples += round_samples;
+        for (int k = 0; k < nlive; ++k) {
+            Request &r = live[k];
+            const DevState &h = S->h_gather[k];
+            if (h.stopped || r.j + 1 >= r.jmax) {
+                cv_result res;
+                memset(&res, 0, sizeof(res));
+                res.neval = h.neval;
+                res.fail = h.stopped ? h.fail : 1;
+                res.iterations = h.iter;
+                res.status = h.status;
+                for (int c = 0; c < r.spec.g.ncomp; ++c) {
+                    res.integral[c] = h.integral[c];
+                    res.error[c] = h.error[c];
+                    res.prob[c] = h.prob[c];
+                    res.chi2[c] = h.chi2[c];
+                }
+                S->done[r.id] = res;
+                S->latency_ms[r.id] = std::chrono::duration<double, std::milli>(t1 - r.arrival).count();
+                ++S->completed;
+                arena.release(r.off, r.bytes);
+                free_slots.push_back(r.slot);
+            } else {
+                r.next_index += (unsigned long long)(r.spec.nstart + (long long)r.j * r.spec.nincrease);
+                r.j += 1;
+                keep.push_back(r);
+            }
+        }
+    }
+    live.swap(keep);
+    S->cv_done.notify_all();
+    return CV_OK;
+}
+
+void server_main(cv_server *S)
+{
+    cv_ctx *ctx = S->ctx;
+    cudaSetDevice(ctx->device);
+    Arena arena((size_t)S->opts.hbm_budget_bytes);
+    std::vector<int> free_slots;
+    for (int i = S->opts.max_live - 1; i >= 0; --i) free_slots.push_back(i);
+    std::vector<Request> live;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (live.empty()) {
+                S->cv_new.wait(lk, [&] { return S->stopping || !S->pending.empty(); });
+                if (S->stopping && S->pending.empty()) break;
+            }
+        }
+        int rc = server_round(S, live, arena, free_slots);
+        if (rc) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->error = rc;
+            S->stopping = true;
+            S->cv_done.notify_all();
+            break;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int cv_server_start(cv_ctx *ctx, const cv_server_opts *opts, cv_server **out)
+{
+    if (!ctx || !out) return CV_EINVAL;
+    *out = nullptr;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    cv_server *S = new cv_server();
+    S->ctx = ctx;
+    memset(&S->opts, 0, sizeof(S->opts));
+    if (opts) S->opts = *opts;
+    if (S->opts.hbm_budget_bytes <= 0) S->opts.hbm_budget_bytes = (int64_t)1 << 30;
+    if (S->opts.max_live <= 0) S->opts.max_live = 4096;
+    const int L = S->opts.max_live;
+    S->class_grid.assign(2 * (CV_MAX_DIM + 1), 0);
+    cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&S->arena_mem, (size_t)S->opts.hbm_budget_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_items, (size_t)L * sizeof(BatchItem));
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_cargs, (size_t)L * sizeof(CombineArgs));
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_lists, (size_t)2 * L * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_axes, (size_t)L * CV_MAX_DIM * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_counters, 2 * (CV_MAX_DIM + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_gather, (size_t)L * sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMallocHost(&S->h_gather, (size_t)L * sizeof(DevState));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(S->arena_mem);
+        cudaFree(S->d_items);
+        cudaFree(S->d_cargs);
+        cudaFree(S->d_lists);
+        cudaFree(S->d_axes);
+        cudaFree(S->d_counters);
+        cudaFree(S->d_gather);
+        if (S->h_gather) cudaFreeHost(S->h_gather);
+        if (S->stream) cudaStreamDestroy(S->stream);
+        delete S;
+        return fail_msg(ctx, CV_ENOMEM, "server allocation failed: %s", cudaGetErrorString(e));
+    }
+    S->t_start = Clock::now();
+    S->worker = std::thread(server_main, S);
+    ctx->servers.insert(S);
+    *out = S;
+    return CV_OK;
+}
+
+extern "C" int cv_submit(cv_server *S, const cv_spec *spec, uint64_t *id)
+{
+    if (!S || !id) return CV_EINVAL;
+    int rc = check_spec(S->ctx, spec);
+    if (rc) return rc;
+    if (spec->flags & (CV_FP64 | CV_PLAIN))
+        return fail_msg(S->ctx, CV_EINVAL, "served requests use the FP32 path");
+    Request r;
+    r.spec = *spec;
+    r.bytes = request_bytes(*spec);
+    if ((int64_t)r.bytes > S->opts.hbm_budget_bytes)
+        return fail_msg(S->ctx, CV_EADMIT, "request needs %zu bytes, the budget is %lld", r.bytes,
+                        (long long)S->opts.hbm_budget_bytes);
+    r.arrival = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stopping) return fail_msg(S->ctx, CV_EBUSY, "server is stopping");
+        if (S->error) return S->error;
+        r.id = S->next_id++;
+        *id = r.id;
+        S->pending.push_back(r);
+        ++S->submitted;
+    }
+    S->cv_new.notify_one();
+    return CV_OK;
+}
+
+extern "C" int cv_poll(cv_server *S, uint64_t id, cv_result *out)
+{
+    if (!S || !out) return CV_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->done.find(id);
+    if (it != S->done.end()) {
+        *out = it->second;
+        return CV_OK;
+    }
+    if (id == 0 || id >= S->next_id) return CV_ENOTFOUND;
+    return S->error ? S->error : CV_EBUSY;
+}
+
+extern "C" int cv_wait(cv_server *S, uint64_t id, int timeout_ms, cv_result *out)
+{
+    if (!S || !out) return CV_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (id == 0 || id >= S->next_id) return CV_ENOTFOUND;
+    const bool ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                        [&] { return S->done.count(id) || S->error; });
+    if (S->done.count(id)) {
+        *out = S->done[id];
+        return CV_OK;
+    }
+    if (S->error) return S->error;
+    return ok ? CV_EBUSY : CV_ETIMEOUT;
+}
+
+extern "C" int cv_server_stats(cv_server *S, cv_serve_stats *out)
+{
+    if (!S || !out) return CV_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    memset(out, 0, sizeof(*out));
+    out->submitted = S->submitted;
+    out->completed = S->completed;
+    out->rounds = S->rounds;
+    out->samples = S->samples;
+    out->max_live = S->max_live_seen;
+    out->pending = (int)S->pending.size();
+    out->busy_s = S->busy_s;
+    out->wall_s = std::chrono::duration<double>(Clock::now() - S->t_start).count();
+    std::vector<double> lat;
+    lat.reserve(S->latency_ms.size());
+    for (auto &kv : S->latency_ms) lat.push_back(kv.second);
+    if (!lat.empty()) {
+        std::sort(lat.begin(), lat.end());
+        auto q = [&](double p) { return lat[std::min(lat.size() - 1, (size_t)(p * (lat.size() - 1) + 0.5))]; };
+        out->p50_ms = q(0.50);
+        out->p99_ms = q(0.99);
+        out->max_ms = lat.back();
+    }
+    return CV_OK;
+}
+
+static void server_release(cv_server *S)
+{
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stopping = true;
+    }
+    S->cv_new.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    cudaSetDevice(S->ctx->device);
+    cudaFree(S->arena_mem);
+    cudaFree(S->d_items);
+    cudaFree(S->d_cargs);
+    cudaFree(S->d_lists);
+    cudaFree(S->d_axes);
+    cudaFree(S->d_counters);
+    cudaFree(S->d_gather);
+    if (S->d_tiles) cudaFree(S->d_tiles);
+    if (S->h_gather) cudaFreeHost(S->h_gather);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+}
+
+extern "C" int cv_server_stop(cv_server *S)
+{
+    if (!S) return CV_EINVAL;
+    cv_ctx *ctx = S->ctx;
+    if (!ctx->servers.erase(S)) return CV_EINVAL;
+    const int err = S->error;
+    server_release(S);
+    return err;
 }

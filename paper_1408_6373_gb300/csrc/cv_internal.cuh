@@ -140,11 +140,15 @@ cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
                                   const CombineArgs &a, cudaStream_t s);
 cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int nbins,
                          long long nstart, cudaStream_t s);
+// (list: optional indices of the integrals to act on, else 0..count-1)
 cudaError_t launch_batch_reset(const BatchItem *items, const CombineArgs *cargs, int count,
-                               cudaStream_t s);
+                               cudaStream_t s, const int *list = nullptr);
 cudaError_t launch_batch_refine(const BatchItem *items, const int2 *axes, int naxes,
                                 cudaStream_t s);
-cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream_t s);
+cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream_t s,
+                                 const int *list = nullptr);
+cudaError_t launch_gather_states(const BatchItem *items, const int *list, int count,
+                                 DevState *out, cudaStream_t s);
 
 inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64) {
     // grid {e, w} pairs plus the block histogram, CV_MAX_BINS slots per axis

@@ -275,9 +275,10 @@ __global__ void k_reset(DevState *st, double *edges, double *H, int ndim, int N,
 // ---- batched forms: one CTA per integral (reset, combine) or per
 // (integral, axis) (refine).  An integral whose run has stopped is skipped;
 // its stop flag is only ever set by a later combine launch.
-__global__ void k_batch_reset(const BatchItem *items, const CombineArgs *cargs)
+__global__ void k_batch_reset(const BatchItem *items, const CombineArgs *cargs, const int *list)
 {
-    const BatchItem &it = items[blockIdx.x];
+    const int i = list ? list[blockIdx.x] : (int)blockIdx.x;
+    const BatchItem &it = items[i];
     const int N = it.a.nbins, ndim = it.a.g.ndim;
     for (int i = threadIdx.x; i < ndim * (N + 1); i += blockDim.x) {
         const int k = i % (N + 1);
@@ -289,7 +290,7 @@ __global__ void k_batch_reset(const BatchItem *items, const CombineArgs *cargs)
     __syncthreads();
     if (threadIdx.x == 0) {
         it.st->next_index = 1ull;
-        it.st->n_cur = cargs[blockIdx.x].nstart;
+        it.st->n_cur = cargs[i].nstart;
     }
 }
 
@@ -301,29 +302,48 @@ __global__ void __launch_bounds__(256) k_batch_refine(const BatchItem *items, co
     refine_axis(ax.y, it.a.nbins, it.H, it.edges, 1);
 }
 
-__global__ void k_batch_combine(const CombineArgs *cargs)
+__global__ void k_batch_combine(const CombineArgs *cargs, const int *list)
 {
-    const CombineArgs &A = cargs[blockIdx.x];
+    const CombineArgs &A = cargs[list ? list[blockIdx.x] : (int)blockIdx.x];
     if (*(volatile const int *)&A.st->stopped) return;
     combine_iteration(A);
 }
 
 cudaError_t launch_batch_reset(const BatchItem *items, const CombineArgs *cargs, int count,
-                               cudaStream_t s)
+                               cudaStream_t s, const int *list)
 {
-    k_batch_reset<<<count, 256, 0, s>>>(items, cargs);
+    if (count <= 0) return cudaSuccess;
+    k_batch_reset<<<count, 256, 0, s>>>(items, cargs, list);
+    return cudaGetLastError();
+}
+
+// Copy the states of the listed integrals into one contiguous array.
+__global__ void k_gather_states(const BatchItem *items, const int *list, DevState *out)
+{
+    const int *src = reinterpret_cast<const int *>(items[list[blockIdx.x]].st);
+    int *dst = reinterpret_cast<int *>(out + blockIdx.x);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevState) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_gather_states(const BatchItem *items, const int *list, int count, DevState *out,
+                                 cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_gather_states<<<count, 32, 0, s>>>(items, list, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_refine(const BatchItem *items, const int2 *axes, int naxes, cudaStream_t s)
 {
+    if (naxes <= 0) return cudaSuccess;
     k_batch_refine<<<naxes, 256, 0, s>>>(items, axes);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream_t s)
+cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream_t s, const int *list)
 {
-    k_batch_combine<<<count, 32, 0, s>>>(cargs);
+    if (count <= 0) return cudaSuccess;
+    k_batch_combine<<<count, 32, 0, s>>>(cargs, list);
     return cudaGetLastError();
 }
 

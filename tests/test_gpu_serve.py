@@ -1,0 +1,131 @@
+"""GPU tests of the serving loop (cv_server_*): continuous batching of
+requests with different ndim, ncomp and goals; each result equals the same
+request run alone; admission by the device-memory budget; statistics."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1408_6373_gb300 as cg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cg.build_library()
+    c = cg.Context(0)
+    yield c
+    c.close()
+
+
+def _request(rng):
+    ndim = int(rng.integers(2, 33))
+    ncomp = int(rng.integers(1, 5))
+    fams = [int(f) for f in rng.integers(0, 6, ncomp)]
+    a = 0.5 + rng.random((ncomp, ndim))
+    u = rng.random((ncomp, ndim))
+    eps = float(np.exp(rng.uniform(np.log(1e-4), np.log(1e-2))))
+    g = cg.genz(ndim, fams, a, u)
+    return cg.spec(g, nbins=64, epsrel=eps, maxeval=2 * 10 ** 6, nstart=4000, nincrease=8000)
+
+
+def _close(r, ref, nc):
+    assert (r.neval, r.fail, r.iterations) == (ref.neval, ref.fail, ref.iterations)
+    for c in range(nc):
+        assert abs(r.integral[c] - ref.integral[c]) <= 2e-5 * abs(ref.integral[c]) + 1e-2 * ref.error[c]
+
+
+def test_each_result_same_alone_and_in_the_mix(ctx):
+    rng = np.random.default_rng(7)
+    specs = [_request(rng) for _ in range(40)]
+    S = ctx.server(hbm_budget_bytes=256 << 20)
+    ids = [S.submit(sp) for sp in specs]
+    res = [S.wait(i, 120000) for i in ids]
+    st = S.stats()
+    S.stop()
+    assert st.completed == 40 and st.max_live > 1
+    for sp, r in zip(specs, res):
+        alone = ctx.vegas(sp.g, epsrel=sp.epsrel, flags=0, maxeval=sp.maxeval, nstart=sp.nstart,
+                          nincrease=sp.nincrease, nbins=sp.nbins)
+        assert (r.neval, r.fail) == (alone.neval, alone.fail)
+        for c in range(sp.g.ncomp):
+            assert abs(r.integral[c] - alone.integral[c]) <= \
+                2e-5 * abs(alone.integral[c]) + 1e-2 * alone.error[c]
+
+
+def test_arrivals_while_busy_join_later_rounds(ctx):
+    rng = np.random.default_rng(8)
+    S = ctx.server(hbm_budget_bytes=64 << 20)
+    first = [S.submit(_request(rng)) for _ in range(8)]
+    time.sleep(0.002)
+    late = [S.submit(_request(rng)) for _ in range(8)]
+    out = [S.wait(i, 120000) for i in first + late]
+    st = S.stats()
+    S.stop()
+    assert all(r.neval > 0 for r in out)
+    assert st.rounds >= max(r.iterations for r in out)
+    assert st.p50_ms > 0 and st.p99_ms >= st.p50_ms
+
+
+def test_budget_admission_and_rejection(ctx):
+    rng = np.random.default_rng(9)
+    sp = _request(rng)
+    # 32 dimensions x 256 bins need 132,096 bytes of state: a 200 KB budget
+    # holds one such request at a time, and all still complete, one by one
+    def big():
+        g = cg.genz(32, [cg.GAUSSIAN], 0.5 + rng.random(32), rng.random(32))
+        return cg.spec(g, nbins=256, maxeval=3 * 5000, nstart=5000)
+    S = ctx.server(hbm_budget_bytes=200 * 1024)
+    ids = [S.submit(big()) for _ in range(5)]
+    res = [S.wait(i, 120000) for i in ids]
+    st = S.stats()
+    assert st.max_live == 1 and all(r.neval > 0 for r in res)
+    # a request that can never fit is refused at submission
+    tiny = ctx.server(hbm_budget_bytes=4096)
+    with pytest.raises(cg.CubaGpuError) as ei:
+        tiny.submit(sp)
+    assert ei.value.code == cg.EADMIT
+    tiny.stop()
+    S.stop()
+
+
+def test_submit_from_two_threads_and_poll(ctx):
+    rng = np.random.default_rng(10)
+    specs = [_request(rng) for _ in range(16)]
+    S = ctx.server()
+    ids = [None] * 16
+
+    def worker(k0):
+        for k in range(k0, 16, 2):
+            ids[k] = S.submit(specs[k])
+
+    th = [threading.Thread(target=worker, args=(k,)) for k in (0, 1)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert len(set(ids)) == 16
+    deadline = time.time() + 120
+    pending = set(ids)
+    while pending and time.time() < deadline:
+        pending = {i for i in pending if S.poll(i) is None}
+        time.sleep(0.001)
+    assert not pending
+    with pytest.raises(cg.CubaGpuError) as ei:
+        S.poll(10 ** 9)
+    assert ei.value.code == cg.ENOTFOUND
+    S.stop()
+
+
+def test_stop_finishes_submitted_requests(ctx):
+    rng = np.random.default_rng(11)
+    S = ctx.server()
+    ids = [S.submit(_request(rng)) for _ in range(6)]
+    st_before = S.stats()
+    S.stop()  # waits for every submitted request
+    assert st_before.submitted == 6
