@@ -413,7 +413,7 @@ def measure_batch(ctx, cg, W, warmup: int, steps: int, subset: int = 32) -> dict
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     res = B.results()
     launches = B.kernels_per_run()
-    tiles = {d: B.tile_points(d, True) for d in sorted({p.ndim for p in probs})}
+    tiles = {str(n): B.tile_points(n) for n in (10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7)}
     B.close()
     # plain FP64 comparator on a subset (the full set would take ~30 s)
     idx = list(range(0, len(probs), len(probs) // subset))[:subset]
@@ -431,7 +431,7 @@ def measure_batch(ctx, cg, W, warmup: int, steps: int, subset: int = 32) -> dict
                         "log-uniform 1e4..1e7, 10 iterations, 64 bins, FP32 eval / FP64 reduce",
             "value": samples / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "samples_per_step": samples, "gpu_launches_per_step": launches,
-            "autotune_s": tune_s, "tile_points_by_ndim": tiles,
+            "autotune_s": tune_s, "tile_points_by_iteration_size": tiles,
             "plain_fp64_subset": {"integrals": len(idx), "value": sub_samples / plain_s,
                                   "unit": UNIT,
                                   "max_abs_diff_in_sigma": max(dev)}}

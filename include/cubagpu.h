@@ -249,22 +249,27 @@ void cv_integral_destroy(cv_integral *I);
  * size, then one launch refines every axis of every integral and one
  * combines every integral; all iterations are one captured CUDA graph and
  * each integral stops on the device when its own goal or budget is reached.
- * FP32 path only (CV_FP64 / CV_PLAIN are rejected).  Each integral's result
- * equals what cv_vegas returns for it alone, up to FP32 summation order.
- * The tile size of each class comes from a cost model (four tiles per
- * resident CTA, 64..4096 blocks), the environment (CUBAGPU_TILE, points per
- * tile), or cv_batch_autotune. */
+ * FP32 path only (CV_FP64 / CV_PLAIN are rejected); ndim * nbins must fit
+ * the per-warp histograms in shared memory (10 * ndim * nbins * 4 bytes
+ * <= 227 KiB, e.g. 32 x 128 or 20 x 256).  An integral's points are cut
+ * into tiles by a rule that depends on that integral alone (about 16
+ * tiles per iteration, 2^11 .. cap points each; CUBAGPU_TILE, points,
+ * forces one size), and each tile's FP32 histogram is summed in a fixed
+ * order, so an integral's result is the same alone and in any batch up to
+ * the order of FP64 additions.  It agrees with cv_vegas within the FP32
+ * tolerance (the single-integral kernel groups points differently). */
 typedef struct cv_batch cv_batch;
 int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_batch **out);
 /* Enqueue one complete run of every integral (asynchronous). */
 int cv_batch_run(cv_batch *B);
 /* Synchronise and copy count results. */
 int cv_batch_results(cv_batch *B, cv_result *out);
-/* Time each class's first-iteration sampling with tile sizes 2^11..2^17
- * points and keep the fastest (resets the integrals; call before run). */
+/* Time the first iteration's sampling with tile caps of 2^13, 2^15 and
+ * 2^17 points and keep the fastest (resets the integrals; call before
+ * run). */
 int cv_batch_autotune(cv_batch *B);
-/* Tile size in points chosen for the class (ndim, power-of-two bins). */
-int cv_batch_tile_points(const cv_batch *B, int ndim, int pow2_bins);
+/* Points per tile the batch uses for an iteration of n points. */
+int cv_batch_tile_points(const cv_batch *B, long long n);
 /* Kernels one cv_batch_run enqueues. */
 int cv_batch_kernels_per_run(const cv_batch *B);
 /* Release a batch; a no-op on a handle its context already released. */
@@ -280,8 +285,9 @@ int cv_batch_vegas(cv_ctx *ctx, int count, const cv_spec *specs, cv_result *out)
  * runs rounds in which every admitted request advances by one iteration
  * through the batched kernels (requests that arrive meanwhile join at the
  * next round boundary).  A request whose goal or budget is reached leaves
- * at once and frees its slot and memory.  Each request's result equals
- * what cv_vegas returns for it alone (FP32 path), up to summation order.
+ * at once and frees its slot and memory.  Each request's result is the
+ * same alone and in any mix of requests, up to the order of FP64 additions
+ * (see cv_batch_create for the tiling rule and the ndim * nbins limit).
  * The analogue of the paper's spinning cores (Sect. 3.2.3): the worker and
  * its device state persist between integrations until cv_server_stop. */
 typedef struct {

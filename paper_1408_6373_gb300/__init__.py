@@ -158,7 +158,7 @@ _SIGNATURES = {
     "cv_batch_run": (_i, [_vp]),
     "cv_batch_results": (_i, [_vp, _vp]),
     "cv_batch_autotune": (_i, [_vp]),
-    "cv_batch_tile_points": (_i, [_vp, _i, _i]),
+    "cv_batch_tile_points": (_i, [_vp, ctypes.c_longlong]),
     "cv_batch_kernels_per_run": (_i, [_vp]),
     "cv_batch_destroy": (None, [_vp]),
     "cv_batch_vegas": (_i, [_vp, _i, _vp, _vp]),
@@ -415,8 +415,9 @@ class Batch:
         self.ctx._check(self.ctx._lib.cv_batch_results(self._h, res), "cv_batch_results")
         return list(res)
 
-    def tile_points(self, ndim: int, pow2_bins: bool = True) -> int:
-        return self.ctx._lib.cv_batch_tile_points(self._h, ndim, 1 if pow2_bins else 0)
+    def tile_points(self, n: int) -> int:
+        """Points per tile for an iteration of n points."""
+        return self.ctx._lib.cv_batch_tile_points(self._h, n)
 
     def kernels_per_run(self) -> int:
         return self.ctx._lib.cv_batch_kernels_per_run(self._h)

@@ -693,7 +693,7 @@ namespace cv {
                                                              cudaStream_t);                  \
     extern template cudaError_t launch_batch_sample<D, false>(const BatchSampleArgs &, int,  \
                                                               cudaStream_t);                 \
-    extern template cudaError_t batch_occupancy<D>(bool, int *);
+    extern template cudaError_t batch_occupancy<D>(bool, int, int *);
 CV_FOR_EACH_NDIM(CV_EXTERN_B)
 #undef CV_EXTERN_B
 
@@ -709,16 +709,28 @@ static cudaError_t dispatch_batch_sample(int ndim, bool pow2, const BatchSampleA
     return cudaErrorInvalidValue;
 }
 
-static cudaError_t dispatch_batch_occupancy(int ndim, bool pow2, int *occ)
+static cudaError_t dispatch_batch_occupancy(int ndim, bool pow2, int stride, int *occ)
 {
     switch (ndim) {
-#define CV_CASE(D) case D: return batch_occupancy<D>(pow2, occ);
+#define CV_CASE(D) case D: return batch_occupancy<D>(pow2, stride, occ);
         CV_FOR_EACH_NDIM(CV_CASE)
 #undef CV_CASE
     }
     return cudaErrorInvalidValue;
 }
 }  // namespace cv
+
+// Tile size, in 32-point blocks, of one integral's iteration of n points:
+// about 16 tiles per iteration, a power of two between 64 and cap.  It
+// depends on the integral alone, so a batch or a serving round never
+// changes how an integral's points are grouped and summed.
+static int tile_blocks_for(long long n, int cap)
+{
+    const long long blocks = (n + 31) / 32 + 1;
+    long long t = 64;
+    while (t < cap && t * 16 < blocks) t <<= 1;
+    return (int)t;
+}
 
 // A set of integrals run together: per iteration one persistent sampling
 // launch per dimension class (ndim, power-of-two bins) over a queue of
@@ -738,9 +750,11 @@ struct cv_batch {
     int *d_counters = nullptr;
     size_t tiles_cap = 0, counters_cap = 0;
     int J = 0;                                   // iterations of the longest run
-    // classes and their tile sizes (in 32-point blocks)
-    struct Class { int ndim; bool pow2; int tile_blocks; int grid; };
+    // dimension classes: slots per axis, persistent grid
+    struct Class { int ndim; bool pow2; int stride; int grid; };
     std::vector<Class> classes;
+    int tile_cap = 2048;                         // largest tile, in 32-point blocks
+    int tile_fixed = 0;                          // CUBAGPU_TILE: every tile this size
     std::vector<int> item_class;
     // launch plan: per iteration, per class: tile offset and count, counter index
     struct Launch { int j, cls, tile_off, ntiles, counter; };
@@ -772,7 +786,6 @@ static int batch_build_tiles(cv_batch *B, int only_first_iteration)
     for (int j = 0; j < J; ++j) {
         for (size_t c = 0; c < B->classes.size(); ++c) {
             const int off = (int)tiles.size();
-            const int TB = B->classes[c].tile_blocks;
             for (int i = 0; i < B->count; ++i) {
                 if (B->item_class[i] != (int)c || j >= B->jmax[i]) continue;
                 const cv_spec &sp = B->specs[i];
@@ -780,6 +793,7 @@ static int batch_build_tiles(cv_batch *B, int only_first_iteration)
                 unsigned long long s = 1;
                 for (int jj = 0; jj < j; ++jj) s += (unsigned long long)(sp.nstart + (long long)jj * sp.nincrease);
                 const unsigned long long n = (unsigned long long)(sp.nstart + (long long)j * sp.nincrease);
+                const int TB = B->tile_fixed ? B->tile_fixed : tile_blocks_for((long long)n, B->tile_cap);
                 const unsigned long long qa = s >> 5, qb = (s + n + 31) >> 5;
                 for (unsigned long long q = qa; q < qb; q += (unsigned long long)TB) {
                     Tile t;
@@ -838,6 +852,7 @@ static int batch_enqueue(cv_batch *B, cudaStream_t s, int first_iteration_sampli
             a.items = B->d_items;
             a.tiles = B->d_tiles + L.tile_off;
             a.ntiles = L.ntiles;
+            a.stride = C.stride;
             a.counter = B->d_counters + L.counter;
             const int grid = C.grid < L.ntiles ? C.grid : L.ntiles;
             CV_CUDA(ctx, dispatch_batch_sample(C.ndim, C.pow2, a, grid, s));
@@ -872,23 +887,13 @@ static int batch_capture(cv_batch *B)
     return CV_OK;
 }
 
-// Cost-model tile size: enough tiles for four per resident CTA, between 64
-// and 4096 blocks (2048 .. 131072 points).  CUBAGPU_TILE (points) overrides.
+// Tile cap from the environment (CUBAGPU_TILE, points per tile: every tile
+// that size) or the default.
 static void batch_default_tiles(cv_batch *B)
 {
     const char *env = getenv("CUBAGPU_TILE");
     const long long forced = env ? atoll(env) : 0;
-    for (size_t c = 0; c < B->classes.size(); ++c) {
-        long long blocks = 0;
-        for (int i = 0; i < B->count; ++i)
-            if (B->item_class[i] == (int)c) blocks += (B->n0[i] + 31) / 32;
-        long long tb = blocks / (4LL * (B->classes[c].grid > 0 ? B->classes[c].grid : 1));
-        tb = (tb + 7) / 8 * 8;
-        if (tb < 64) tb = 64;
-        if (tb > 4096) tb = 4096;
-        if (forced > 0) tb = forced / 32 > 0 ? forced / 32 : 1;
-        B->classes[c].tile_blocks = (int)tb;
-    }
+    B->tile_fixed = forced > 0 ? (int)(forced / 32 > 0 ? forced / 32 : 1) : 0;
 }
 
 extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_batch **out)
@@ -928,16 +933,23 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         for (size_t k = 0; k < B->classes.size(); ++k)
             if (B->classes[k].ndim == ndim && B->classes[k].pow2 == p2) c = (int)k;
         if (c < 0) {
-            int occ = 0;
-            cudaError_t e = dispatch_batch_occupancy(ndim, p2, &occ);
-            if (e != cudaSuccess) {
-                delete B;
-                return cuda_fail(ctx, e, "batch occupancy query");
-            }
-            B->classes.push_back({ndim, p2, 64, ctx->sms * (occ > 0 ? occ : 1)});
+            B->classes.push_back({ndim, p2, N, 0});
             c = (int)B->classes.size() - 1;
         }
+        if (N > B->classes[c].stride) B->classes[c].stride = N;
         B->item_class[i] = c;
+    }
+    for (cv_batch::Class &C : B->classes) {
+        int occ = 0;
+        cudaError_t e = dispatch_batch_occupancy(C.ndim, C.pow2, C.stride, &occ);
+        if (e != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            delete B;
+            return fail_msg(ctx, CV_EINVAL, "%d dimensions x %d bins exceed the batched path's shared "
+                            "memory (per-warp histograms); run such integrals with cv_vegas",
+                            C.ndim, C.stride);
+        }
+        C.grid = ctx->sms * occ;
     }
     size_t sz_items = (((size_t)count * sizeof(BatchItem)) + 255) & ~(size_t)255;
     size_t sz_cargs = (((size_t)count * sizeof(CombineArgs)) + 255) & ~(size_t)255;
@@ -1062,62 +1074,63 @@ extern "C" int cv_batch_results(cv_batch *B, cv_result *out)
 
 extern "C" int cv_batch_kernels_per_run(const cv_batch *B) { return B ? B->kernels_per_run : 0; }
 
-extern "C" int cv_batch_tile_points(const cv_batch *B, int ndim, int pow2_bins)
+extern "C" int cv_batch_tile_points(const cv_batch *B, long long n)
 {
     if (!B) return 0;
-    for (const cv_batch::Class &c : B->classes)
-        if (c.ndim == ndim && c.pow2 == (pow2_bins != 0)) return c.tile_blocks * 32;
-    return 0;
+    return 32 * (B->tile_fixed ? B->tile_fixed : tile_blocks_for(n, B->tile_cap));
 }
 
-// Measured tuning: for every class, time its first-iteration sampling
-// launches with tile sizes 64..4096 blocks (a reset before each trial, so no
-// result is affected) and keep the fastest.
+// Measured tuning of the tile cap: time the first iteration's sampling
+// launches of every class with caps of 256, 1024 and 4096 blocks (a reset
+// before each trial, so no result is affected) and keep the fastest total.
+// The cap only bounds how an iteration is cut into tiles; an integral's
+// tiles still depend on that integral alone.
 extern "C" int cv_batch_autotune(cv_batch *B)
 {
     if (!B) return CV_EINVAL;
+    if (B->tile_fixed) return CV_OK;
     cv_ctx *ctx = B->ctx;
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
-    static const int cand[] = {64, 256, 1024, 4096};
-    const size_t ncls = B->classes.size();
-    std::vector<float> best(ncls, 1e30f);
-    std::vector<int> best_tb(ncls, 64);
+    static const int cand[] = {256, 1024, 4096};
+    float best = 1e30f;
+    int best_cap = B->tile_cap;
     cudaEvent_t e0, e1;
     CV_CUDA(ctx, cudaEventCreate(&e0));
     CV_CUDA(ctx, cudaEventCreate(&e1));
     int rc = CV_OK;
-    for (int ci = 0; ci < 4 && !rc; ++ci) {
-        for (size_t c = 0; c < ncls; ++c) B->classes[c].tile_blocks = cand[ci];
+    for (int ci = 0; ci < 3 && !rc; ++ci) {
+        B->tile_cap = cand[ci];
         rc = batch_build_tiles(B, 1);
         if (rc) break;
         if (B->counters_cap) cudaMemsetAsync(B->d_counters, 0, B->counters_cap * sizeof(int), ctx->stream);
         launch_batch_reset(B->d_items, B->d_cargs, B->count, ctx->stream);
+        cudaEventRecord(e0, ctx->stream);
         for (const cv_batch::Launch &L : B->plan) {
             const cv_batch::Class &C = B->classes[L.cls];
             BatchSampleArgs a;
             a.items = B->d_items;
             a.tiles = B->d_tiles + L.tile_off;
             a.ntiles = L.ntiles;
+            a.stride = C.stride;
             a.counter = B->d_counters + L.counter;
-            cudaEventRecord(e0, ctx->stream);
             cudaError_t e = dispatch_batch_sample(C.ndim, C.pow2, a, C.grid < L.ntiles ? C.grid : L.ntiles, ctx->stream);
-            cudaEventRecord(e1, ctx->stream);
             if (e != cudaSuccess) {
                 rc = cuda_fail(ctx, e, "autotune launch");
                 break;
             }
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best[L.cls]) {
-                best[L.cls] = ms;
-                best_tb[L.cls] = cand[ci];
-            }
+        }
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_cap = cand[ci];
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (size_t c = 0; c < ncls; ++c) B->classes[c].tile_blocks = best_tb[c];
+    B->tile_cap = best_cap;
     if (!rc) rc = batch_build_tiles(B, 0);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
@@ -1316,14 +1329,9 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
     }
     const int nlive = (int)live.size();
     // tiles grouped by dimension class
-    struct Cls { int ndim; bool pow2; std::vector<Tile> tiles; };
+    struct Cls { int ndim; bool pow2; int stride; std::vector<Tile> tiles; };
     std::vector<Cls> cls;
-    long long round_blocks = 0;
     int64_t round_samples = 0;
-    for (const Request &r : live) round_blocks += (r.spec.nstart + (long long)r.j * r.spec.nincrease + 31) / 32;
-    long long tb = round_blocks / (4LL * ctx->sms * 2);
-    tb = std::max(64LL, std::min(4096LL, (tb + 7) / 8 * 8));
-    if (S->opts.tile_points > 0) tb = std::max(1, S->opts.tile_points / 32);
     for (const Request &r : live) {
         const int ndim = r.spec.g.ndim;
         const bool p2 = (r.spec.nbins & (r.spec.nbins - 1)) == 0;
@@ -1331,11 +1339,14 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         for (Cls &k : cls)
             if (k.ndim == ndim && k.pow2 == p2) c = &k;
         if (!c) {
-            cls.push_back({ndim, p2, {}});
+            cls.push_back({ndim, p2, r.spec.nbins, {}});
             c = &cls.back();
         }
+        c->stride = std::max(c->stride, r.spec.nbins);
         const unsigned long long s = r.next_index;
         const unsigned long long n = (unsigned long long)(r.spec.nstart + (long long)r.j * r.spec.nincrease);
+        const long long tb = S->opts.tile_points > 0 ? std::max(1, S->opts.tile_points / 32)
+                                                     : tile_blocks_for((long long)n, 2048);
         const unsigned long long qa = s >> 5, qb = (s + n + 31) >> 5;
         for (unsigned long long q = qa; q < qb; q += (unsigned long long)tb) {
             Tile t;
@@ -1365,16 +1376,17 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
     CV_CUDA(ctx, launch_batch_reset(S->d_items, S->d_cargs, nfresh, S->stream, S->d_lists));
     size_t off = 0;
     for (const Cls &c : cls) {
-        int &g = S->class_grid[(c.pow2 ? 1 : 0) * (CV_MAX_DIM + 1) + c.ndim];
+        int &g = S->class_grid[((c.pow2 ? 1 : 0) * (CV_MAX_DIM + 1) + c.ndim) * (CV_MAX_BINS + 1) + c.stride];
         if (!g) {
             int occ = 0;
-            CV_CUDA(ctx, dispatch_batch_occupancy(c.ndim, c.pow2, &occ));
+            CV_CUDA(ctx, dispatch_batch_occupancy(c.ndim, c.pow2, c.stride, &occ));
             g = ctx->sms * std::max(occ, 1);
         }
         BatchSampleArgs a;
         a.items = S->d_items;
         a.tiles = S->d_tiles + off;
         a.ntiles = (int)c.tiles.size();
+        a.stride = c.stride;
         a.counter = S->d_counters + (c.pow2 ? 1 : 0) * (CV_MAX_DIM + 1) + c.ndim;
         CV_CUDA(ctx, dispatch_batch_sample(c.ndim, c.pow2, a, std::min<int>(g, a.ntiles), S->stream));
         off += c.tiles.size();
@@ -1467,7 +1479,7 @@ extern "C" int cv_server_start(cv_ctx *ctx, const cv_server_opts *opts, cv_serve
     if (S->opts.hbm_budget_bytes <= 0) S->opts.hbm_budget_bytes = (int64_t)1 << 30;
     if (S->opts.max_live <= 0) S->opts.max_live = 4096;
     const int L = S->opts.max_live;
-    S->class_grid.assign(2 * (CV_MAX_DIM + 1), 0);
+    S->class_grid.assign(2 * (CV_MAX_DIM + 1) * (CV_MAX_BINS + 1), 0);
     cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&S->arena_mem, (size_t)S->opts.hbm_budget_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_items, (size_t)L * sizeof(BatchItem));
@@ -1505,6 +1517,9 @@ extern "C" int cv_submit(cv_server *S, const cv_spec *spec, uint64_t *id)
     if (rc) return rc;
     if (spec->flags & (CV_FP64 | CV_PLAIN))
         return fail_msg(S->ctx, CV_EINVAL, "served requests use the FP32 path");
+    if (batch_smem_bytes(spec->g.ndim, spec->nbins) > 227 * 1024)
+        return fail_msg(S->ctx, CV_EINVAL, "%d dimensions x %d bins exceed the batched path's shared memory",
+                        spec->g.ndim, spec->nbins);
     Request r;
     r.spec = *spec;
     r.bytes = request_bytes(*spec);

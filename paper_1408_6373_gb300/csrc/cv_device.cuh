@@ -301,11 +301,13 @@ constexpr int kStride = CV_MAX_BINS;
 
 template <typename Real> struct Smem;
 template <> struct Smem<float> {
-    float *e, *w, *h;  // [NDIM][kStride]: e_k, w_k (N w_k on the power-of-two map), histogram
+    float *e, *w, *h;  // [NDIM][stride]: e_k, w_k (N w_k on the power-of-two map), histogram
+    int stride;        // slots per axis (kStride, a compile-time constant, in k_sample)
 };
 template <> struct Smem<double> {
-    double2 *ew;       // [NDIM][kStride] {e_k, w_k}
-    double *h;         // [NDIM][kStride]
+    double2 *ew;       // [NDIM][stride] {e_k, w_k}
+    double *h;         // [NDIM][stride]
+    int stride;
 };
 
 // Map one FP32 coordinate: returns x, multiplies the Jacobian, and gives the
@@ -320,18 +322,18 @@ __device__ __forceinline__ float map_f32(unsigned X, int d, int N, const MapPara
         const unsigned fb = (X >> m.sF) & m.mF;
         const float fs = __uint_as_float(m.expL | fb) - m.twoNegL;
         const int p = (int)(((X >> m.sA) & m.mA) | (X >> m.sB));
-        const float w = sm.w[d * kStride + p];
+        const float w = sm.w[d * sm.stride + p];
         J *= w;
         slot = p;
-        return __fmaf_rn(w, fs, sm.e[d * kStride + p]);
+        return __fmaf_rn(w, fs, sm.e[d * sm.stride + p]);
     } else {
         const unsigned t = (X >> 9) * (unsigned)N;
         const float frac = __uint_as_float(0x3f800000u | (t & 0x7fffffu)) - 1.0f;
         const int p = (int)(t >> 23);
-        const float w = sm.w[d * kStride + p];
+        const float w = sm.w[d * sm.stride + p];
         J = J * ((float)N * w);
         slot = p;
-        return __fmaf_rn(w, frac, sm.e[d * kStride + p]);
+        return __fmaf_rn(w, frac, sm.e[d * sm.stride + p]);
     }
 }
 
@@ -342,7 +344,7 @@ __device__ __forceinline__ double map_f64(unsigned long long X, int d, int N,
     const double frac = __longlong_as_double((long long)(0x3ff0000000000000ull |
                                                          (t & 0xfffffffffffffull))) - 1.0;
     const int p = (int)(t >> 52);
-    const double2 ew = sm.ew[d * kStride + p];
+    const double2 ew = sm.ew[d * sm.stride + p];
     J = J * ((double)N * ew.y);
     slot = p;
     return __fma_rn(ew.y, frac, ew.x);
@@ -412,7 +414,7 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
             if (!EDGE || valid) {
                 const Real h = f0 * f0;
 #pragma unroll
-                for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * kStride + slot[d]], h);
+                for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * sm.stride + slot[d]], h);
             }
             if (st + 1 < nsteps) sobol_step<NDIM, typename Word<Real>::type>(X, q);
         }
@@ -455,6 +457,7 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<Real> sm;
+    sm.stride = kStride;
     if constexpr (sizeof(Real) == 4) {
         sm.e = reinterpret_cast<float *>(smem_raw);
         sm.w = sm.e + NDIM * kStride;
@@ -538,34 +541,30 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
 // ------------------------------------------------------------ batched kernel
 // Persistent sampling over a queue of tiles of many integrals (one
 // dimension class per launch).  A CTA takes the next tile from a device
-// counter; when the tile belongs to another integral than the last one, it
-// flushes its shared histogram to the old integral and stages the new
-// integral's grid and parameters.  Each tile's 32-point blocks are split
-// over the CTA's warps, and its sums go to the integral's FP64 accumulators.
-template <int NDIM>
-__device__ __forceinline__ void batch_flush_hist(const BatchItem &it, int N, const MapParams &m,
-                                                 const Smem<float> &sm)
-{
-    for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-        const int d = idx / N, k = idx - d * N;
-        const float v = sm.h[d * kStride + slot_of_bin(k, m)];
-        if (v != 0.0f) atomicAdd(&it.H[idx], (double)v);
-    }
-}
-
+// counter, stages the tile's integral (grid and parameters) when it differs
+// from the last one, and splits the tile's 32-point blocks over its warps.
+// Every warp accumulates its own copy of the f^2 histogram, and after each
+// tile the copies are summed in warp order and added to the integral's FP64
+// histogram: the FP32 sums of a tile never depend on which CTA ran it or on
+// what else was in the queue, so an integral gives the same result alone
+// and in any mix (up to the order of FP64 additions).
 template <int NDIM, bool POW2>
 __global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, float>))
 k_batch_sample(const BatchSampleArgs B)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int stride = B.stride;
     Smem<float> sm;
+    sm.stride = stride;
     sm.e = reinterpret_cast<float *>(smem_raw);
-    sm.w = sm.e + NDIM * kStride;
-    sm.h = sm.w + NDIM * kStride;
+    sm.w = sm.e + NDIM * stride;
+    float *hist = sm.w + NDIM * stride;  // [kWarpsPerBlock][NDIM][stride]
     __shared__ SampleArgs<float> A;
     __shared__ int s_tile;
     __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int hsize = NDIM * stride;
+    for (int i = threadIdx.x; i < kWarpsPerBlock * hsize; i += blockDim.x) hist[i] = 0.0f;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(B.counter, 1);
@@ -579,8 +578,6 @@ k_batch_sample(const BatchSampleArgs B)
             continue;
         }
         if (tile.item != cur) {
-            if (cur >= 0) batch_flush_hist<NDIM>(B.items[cur], A.nbins, A.map, sm);
-            __syncthreads();
             // stage the integral's parameters and grid
             const int *src = reinterpret_cast<const int *>(&it.a);
             int *dst = reinterpret_cast<int *>(&A);
@@ -591,11 +588,10 @@ k_batch_sample(const BatchSampleArgs B)
             for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
                 const int d = idx / N, k = idx - d * N;
                 const double *e = it.edges + (size_t)d * (N + 1);
-                const int p = d * kStride + slot_of_bin(k, A.map);
+                const int p = d * stride + slot_of_bin(k, A.map);
                 const double w = e[k + 1] - e[k];
                 sm.e[p] = __double2float_rn(e[k]);
                 sm.w[p] = __double2float_rn(POW2 ? (double)N * w : w);
-                sm.h[p] = 0.0f;
             }
             cur = tile.item;
             __syncthreads();
@@ -607,13 +603,15 @@ k_batch_sample(const BatchSampleArgs B)
         const unsigned long long w0 = tile.q0 + (unsigned long long)warp * per;
         const unsigned long long w1 = min(w0 + per, tile.q0 + (unsigned long long)tile.nblk);
         if (w0 < w1) {
+            Smem<float> smw = sm;
+            smw.h = hist + warp * hsize;
             unsigned X[NDIM];
             sobol_skip<NDIM, unsigned>(X, w0, lane);
             const bool interior = (w0 * 32ull >= start) && (w1 * 32ull <= end);
             if (interior)
-                run_steps<NDIM, float, POW2, false>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
+                run_steps<NDIM, float, POW2, false>(A, smw, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
             else
-                run_steps<NDIM, float, POW2, true>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
+                run_steps<NDIM, float, POW2, true>(A, smw, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
         }
         const int ncomp = A.g.ncomp;
 #pragma unroll
@@ -634,9 +632,21 @@ k_batch_sample(const BatchSampleArgs B)
             const int c = threadIdx.x >> 1;
             atomicAdd((threadIdx.x & 1) ? &it.st->S2[c] : &it.st->S1[c], v);
         }
+        // the tile's histogram: warp copies summed in warp order, then cleared
+        const int N = A.nbins;
+        for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+            const int d = idx / N, k = idx - d * N;
+            const int p = d * stride + slot_of_bin(k, A.map);
+            float v = 0.0f;
+#pragma unroll
+            for (int w = 0; w < kWarpsPerBlock; ++w) {
+                v += hist[w * hsize + p];
+                hist[w * hsize + p] = 0.0f;
+            }
+            if (v != 0.0f) atomicAdd(&it.H[idx], (double)v);
+        }
         __syncthreads();
     }
-    if (cur >= 0) batch_flush_hist<NDIM>(B.items[cur], A.nbins, A.map, sm);
 }
 
 // Sobol coordinates only (the point generator of the sampling kernels,
@@ -716,19 +726,22 @@ template <int NDIM, bool POW2>
 cudaError_t launch_batch_sample(const BatchSampleArgs &b, int grid, cudaStream_t s)
 {
     // (batch_occupancy, always called first, sets the shared-memory limit)
-    const size_t smem = sample_smem_bytes(NDIM, CV_MAX_BINS, false);
-    k_batch_sample<NDIM, POW2><<<grid, kBlock, smem, s>>>(b);
+    k_batch_sample<NDIM, POW2><<<grid, kBlock, batch_smem_bytes(NDIM, b.stride), s>>>(b);
     return cudaGetLastError();
 }
 
 template <int NDIM>
-cudaError_t batch_occupancy(bool pow2, int *blocks_per_sm)
+cudaError_t batch_occupancy(bool pow2, int stride, int *blocks_per_sm)
 {
-    const size_t smem = sample_smem_bytes(NDIM, CV_MAX_BINS, false);
     void *f = pow2 ? (void *)k_batch_sample<NDIM, true> : (void *)k_batch_sample<NDIM, false>;
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t want = batch_smem_bytes(NDIM, stride);
+    if ((int)want > optin) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBlock, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBlock, want);
 }
 
 template <int NDIM, typename W>
@@ -753,7 +766,7 @@ cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
                                                           cudaStream_t);                    \
     template cudaError_t cv::launch_batch_sample<D, false>(const cv::BatchSampleArgs &, int, \
                                                            cudaStream_t);                   \
-    template cudaError_t cv::batch_occupancy<D>(bool, int *);                               \
+    template cudaError_t cv::batch_occupancy<D>(bool, int, int *);                          \
     template cudaError_t cv::launch_sobol<D, unsigned int>(unsigned long long, long long,   \
                                                            int, unsigned long long *, int,  \
                                                            cudaStream_t);                   \

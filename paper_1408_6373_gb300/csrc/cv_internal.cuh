@@ -117,8 +117,15 @@ struct BatchSampleArgs {
     const BatchItem *items;
     const Tile *tiles;
     int ntiles;
+    int stride;                     // slots per axis: the class's largest nbins
     int *counter;                   // next tile to take (zero before the launch)
 };
+
+// Shared memory of a batched sampling block: grid e, w and one f^2
+// histogram per warp, `stride` slots per axis each.
+inline size_t batch_smem_bytes(int ndim, int stride) {
+    return (size_t)(2 + kWarpsPerBlock) * ndim * stride * sizeof(float);
+}
 
 // ---- launchers (template definitions in cv_device.cuh, instantiated per
 // ---- dimension range in cv_sample_*.cu) ----
@@ -129,7 +136,7 @@ cudaError_t sample_occupancy(int nbins, int *blocks_per_sm);
 template <int NDIM, bool POW2>
 cudaError_t launch_batch_sample(const BatchSampleArgs &b, int grid, cudaStream_t s);
 template <int NDIM>
-cudaError_t batch_occupancy(bool pow2, int *blocks_per_sm);
+cudaError_t batch_occupancy(bool pow2, int stride, int *blocks_per_sm);
 template <int NDIM, typename Word>
 cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
                          unsigned long long *Y, int grid, cudaStream_t s);

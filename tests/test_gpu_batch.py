@@ -55,13 +55,15 @@ def test_batch_matches_single_runs(ctx):
 
 
 def test_batch_alone_equals_in_mix(ctx):
+    # an integral's tiles and their FP32 sums do not depend on the rest of
+    # the batch: only the order of FP64 additions differs
     specs, _ = _specs(10, 2)
     mix = ctx.batch_vegas(specs)
     for k in (0, 4, 9):
         alone = ctx.batch_vegas([specs[k]])[0]
         assert alone.neval == mix[k].neval
-        assert alone.integral[0] == pytest.approx(mix[k].integral[0], rel=2e-5)
-        assert alone.error[0] == pytest.approx(mix[k].error[0], rel=1e-3)
+        assert alone.integral[0] == pytest.approx(mix[k].integral[0], rel=1e-10, abs=1e-15)
+        assert alone.error[0] == pytest.approx(mix[k].error[0], rel=1e-8)
 
 
 def test_batch_accuracy_goals_stop_each_integral(ctx):
@@ -73,11 +75,12 @@ def test_batch_accuracy_goals_stop_each_integral(ctx):
             sp.maxeval = 10 ** 6
     res = ctx.batch_vegas(specs)
     for i, (sp, r) in enumerate(zip(specs, res)):
-        single = ctx.vegas(sp.g, epsrel=sp.epsrel, flags=0, maxeval=sp.maxeval, nstart=sp.nstart,
-                           nincrease=sp.nincrease, nbins=sp.nbins)
-        assert (r.neval, r.fail) == (single.neval, single.fail)
+        alone = ctx.batch_vegas([sp])[0]
+        assert (r.neval, r.fail, r.iterations) == (alone.neval, alone.fail, alone.iterations)
         if i % 2 == 0 and r.fail == 0:
             assert r.error[0] <= 1e-3 * abs(r.integral[0])
+        if i % 2 == 1:
+            assert r.iterations == 30 and r.fail == 1
 
 
 def test_batch_rerun_and_autotune_keep_results(ctx):
@@ -86,7 +89,7 @@ def test_batch_rerun_and_autotune_keep_results(ctx):
     B.run()
     r1 = B.results()
     B.autotune()
-    assert B.tile_points(specs[0].g.ndim, (specs[0].nbins & (specs[0].nbins - 1)) == 0) >= 2048
+    assert 2048 <= B.tile_points(10 ** 6) <= 4096 * 32
     B.run()
     r2 = B.results()
     for a, b in zip(r1, r2):

@@ -41,6 +41,9 @@ def _close(r, ref, nc):
 
 
 def test_each_result_same_alone_and_in_the_mix(ctx):
+    # every request served in a mix of 40 equals the same request served
+    # alone, up to the order of FP64 additions; and it agrees with cv_vegas
+    # (which groups points differently) within the FP32 tolerance
     rng = np.random.default_rng(7)
     specs = [_request(rng) for _ in range(40)]
     S = ctx.server(hbm_budget_bytes=256 << 20)
@@ -49,13 +52,20 @@ def test_each_result_same_alone_and_in_the_mix(ctx):
     st = S.stats()
     S.stop()
     assert st.completed == 40 and st.max_live > 1
-    for sp, r in zip(specs, res):
-        alone = ctx.vegas(sp.g, epsrel=sp.epsrel, flags=0, maxeval=sp.maxeval, nstart=sp.nstart,
-                          nincrease=sp.nincrease, nbins=sp.nbins)
-        assert (r.neval, r.fail) == (alone.neval, alone.fail)
+    for k in (0, 7, 19, 39):
+        sp, r = specs[k], res[k]
+        A = ctx.server()
+        alone = A.wait(A.submit(sp), 120000)
+        A.stop()
+        assert (r.neval, r.fail, r.iterations) == (alone.neval, alone.fail, alone.iterations)
         for c in range(sp.g.ncomp):
-            assert abs(r.integral[c] - alone.integral[c]) <= \
-                2e-5 * abs(alone.integral[c]) + 1e-2 * alone.error[c]
+            assert r.integral[c] == pytest.approx(alone.integral[c], rel=1e-10, abs=1e-15)
+            assert r.error[c] == pytest.approx(alone.error[c], rel=1e-8)
+    for sp, r in zip(specs, res):
+        ref = ctx.vegas(sp.g, epsrel=sp.epsrel, flags=0, maxeval=sp.maxeval, nstart=sp.nstart,
+                        nincrease=sp.nincrease, nbins=sp.nbins)
+        for c in range(sp.g.ncomp):
+            assert abs(r.integral[c] - ref.integral[c]) <= 5e-4 * abs(ref.integral[c]) + 0.1 * ref.error[c]
 
 
 def test_arrivals_while_busy_join_later_rounds(ctx):
