@@ -944,10 +944,11 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         cudaError_t e = dispatch_batch_occupancy(C.ndim, C.pow2, C.stride, &occ);
         if (e != cudaSuccess || occ < 1) {
             cudaGetLastError();
+            const int nd = C.ndim, st = C.stride;
             delete B;
             return fail_msg(ctx, CV_EINVAL, "%d dimensions x %d bins exceed the batched path's shared "
                             "memory (per-warp histograms); run such integrals with cv_vegas",
-                            C.ndim, C.stride);
+                            nd, st);
         }
         C.grid = ctx->sms * occ;
     }
@@ -1517,7 +1518,7 @@ extern "C" int cv_submit(cv_server *S, const cv_spec *spec, uint64_t *id)
     if (rc) return rc;
     if (spec->flags & (CV_FP64 | CV_PLAIN))
         return fail_msg(S->ctx, CV_EINVAL, "served requests use the FP32 path");
-    if (batch_smem_bytes(spec->g.ndim, spec->nbins) > 227 * 1024)
+    if (batch_smem_bytes(spec->g.ndim, spec->nbins) > 223 * 1024)
         return fail_msg(S->ctx, CV_EINVAL, "%d dimensions x %d bins exceed the batched path's shared memory",
                         spec->g.ndim, spec->nbins);
     Request r;

@@ -737,9 +737,13 @@ cudaError_t batch_occupancy(bool pow2, int stride, int *blocks_per_sm)
     int optin = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static shared memory counts too
     const size_t want = batch_smem_bytes(NDIM, stride);
-    if ((int)want > optin) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if ((int)want > dyn_max) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBlock, want);
 }
