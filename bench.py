@@ -370,6 +370,8 @@ def run_ours(args):
     }
     if not args.no_batch:
         line["batch4096"] = measure_batch(ctx, cg, W, args.warmup, args.steps)
+    if not args.no_serve:
+        line["serve"] = measure_serve(ctx, cg, W, duration=args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         rate, dt, n = cpu_oracle_rate(p, args.cpu_seconds, threads)
@@ -437,6 +439,61 @@ def measure_batch(ctx, cg, W, warmup: int, steps: int, subset: int = 32) -> dict
                                   "max_abs_diff_in_sigma": max(dev)}}
 
 
+def measure_serve(ctx, cg, W, duration: float = 1.0, rate: float = 2000.0,
+                  plain_subset: int = 100) -> dict:
+    """The serving loop under Poisson arrivals (ndim U{2..32}, ncomp U{1..4},
+    epsrel log-uniform 1e-5..1e-3, maxeval 1e8), submitted in real time; and
+    the plain FP64 one-request-at-a-time server on the same arrival times:
+    a FIFO queue whose service times are measured on the GPU (cv_vegas with
+    CV_FP64 | CV_PLAIN) for the first `plain_subset` requests."""
+    reqs = W.serve_requests(rate=rate, duration=duration)
+    specs = [cg.spec(cg.genz(p.ndim, p.families, p.a, p.u), nbins=p.nbins, epsrel=p.epsrel,
+                     maxeval=p.maxeval, nstart=p.nstart, nincrease=p.nincrease) for _, p in reqs]
+    S = ctx.server(hbm_budget_bytes=8 << 30)
+    for sp in specs[:8]:  # warm-up: kernel attributes, first launches
+        S.wait(S.submit(sp), 600000)
+    S.stop()
+    S = ctx.server(hbm_budget_bytes=8 << 30)
+    ids = []
+    t0 = time.perf_counter()
+    for (t, _), sp in zip(reqs, specs):
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        ids.append(S.submit(sp))
+    res = [S.wait(i, 600000) for i in ids]
+    wall = time.perf_counter() - t0
+    st = S.stats()
+    S.stop()
+    samples = sum(r.neval for r in res)
+    ok = sum(1 for r in res if r.fail == 0)
+    service = []
+    for sp in specs[:plain_subset]:
+        t = time.perf_counter()
+        ctx.vegas(sp.g, epsrel=sp.epsrel, flags=cg.FP64 | cg.PLAIN, maxeval=sp.maxeval,
+                  nstart=sp.nstart, nincrease=sp.nincrease, nbins=sp.nbins)
+        service.append(time.perf_counter() - t)
+    finish, lat = 0.0, []
+    for (t, _), sv in zip(reqs[:plain_subset], service):
+        begin = max(t, finish)
+        finish = begin + sv
+        lat.append(finish - t)
+    lat.sort()
+    q = lambda p: 1e3 * lat[min(len(lat) - 1, int(p * (len(lat) - 1) + 0.5))]
+    return {"workload": f"serve: Poisson {rate:.0f} req/s for {duration:g} s ({len(reqs)} requests), "
+                        "ndim U{2..32}, ncomp U{1..4}, Genz families, epsrel log-uniform 1e-5..1e-3, "
+                        "maxeval 1e8, nstart 1e4, nincrease 5e4, 64 bins, FP32 eval / FP64 reduce",
+            "requests": len(reqs), "reached_accuracy": ok,
+            "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": st.max_ms,
+            "throughput": {"value": samples / wall, "unit": UNIT},
+            "requests_per_s": len(reqs) / wall, "rounds": st.rounds, "max_live": st.max_live,
+            "wall_s": wall, "busy_s": st.busy_s,
+            "plain_fp64_fifo": {"requests": len(service), "p50_ms": q(0.5), "p99_ms": q(0.99),
+                                "throughput": {"value": sum(r.neval for r in res[:plain_subset]) / sum(service),
+                                               "unit": UNIT},
+                                "mean_service_ms": 1e3 * sum(service) / len(service)}}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,6 +502,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-integral batch")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window of the serving run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
