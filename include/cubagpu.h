@@ -84,6 +84,7 @@ extern "C" {
 #define CV_VERBOSE_MASK 0x3
 #define CV_FP64 0x100
 #define CV_PLAIN 0x200
+#define CV_AOS 0x400           /* cv_vegas_cb: x[nvec][ndim], f[nvec][ncomp] */
 
 /* One integral: ncomp components of one ndim-dimensional Genz problem.
  * a[c][i], u[c][i] are the parameters of component c (unused entries
@@ -158,6 +159,45 @@ int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g,
              int64_t mineval, int64_t maxeval, int64_t nstart,
              int64_t nincrease, int64_t nbatch, int nbins, int64_t *neval,
              int *fail, double integral[], double error[], double prob[]);
+
+/* ------------------------------------------- user integrands (materialised) */
+/* The integrand contract of Sect. 3.2.1-3.2.2 on the device: the library
+ * writes up to nvec points to device memory and calls the integrand, which
+ * fills f and returns 0, or -999 to abort the integration at once.  *nvec
+ * is the actual number of points of this call (<= the requested nvec).
+ * x_dev / f_dev hold float (FP32 path) or double (CV_FP64) values: by
+ * default dimension-major x[d*nvec_cap + j], f[c*nvec_cap + j] (coalesced;
+ * *nvec_cap, passed as userdata-independent argument `ld`, is the row
+ * stride), with CV_AOS the paper's point-major x[j*ndim + d],
+ * f[j*ncomp + c].  `stream` is the cudaStream_t the points were written on;
+ * the integrand must enqueue its device work on it (or finish it before
+ * returning).  The buffers are valid only during the call. */
+typedef int (*cv_integrand_dev)(const int *ndim, const void *x_dev, const int *ncomp,
+                                void *f_dev, void *userdata, const int64_t *nvec,
+                                const int64_t *ld, void *stream);
+
+/* Vegas with a user integrand (materialised-sample mode).  Per iteration
+ * the points are written in tiles of at most nvec, the integrand is called
+ * per tile, and the values are accumulated, with bins and Jacobians
+ * recomputed from the Sobol index.  Arguments and results as cv_vegas;
+ * flags may add CV_AOS.  Returns CV_EABORT (and *fail = -999) when the
+ * integrand returns -999. */
+int cv_vegas_cb(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev integrand,
+                void *userdata, int64_t nvec, double epsrel, double epsabs,
+                int flags, int seed, int64_t mineval, int64_t maxeval,
+                int64_t nstart, int64_t nincrease, int64_t nbatch, int nbins,
+                int64_t *neval, int *fail, double integral[], double error[],
+                double prob[]);
+
+/* A ready-made device integrand: the Genz components of `g` evaluated on
+ * the materialised points (userdata = cv_genz_cb_data*; its flags carry
+ * CV_FP64 / CV_AOS to match the call). */
+typedef struct {
+    cv_genz g;
+    int flags;
+} cv_genz_cb_data;
+int cv_genz_callback(const int *ndim, const void *x_dev, const int *ncomp, void *f_dev,
+                     void *userdata, const int64_t *nvec, const int64_t *ld, void *stream);
 
 /* Bytes cv_vegas moves between host and device per call for an integral of
  * this shape: kernel parameters in (h2d), the final state out (d2h). */

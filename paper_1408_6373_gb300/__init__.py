@@ -29,6 +29,7 @@ FAMILIES = {"oscillatory": 0, "product_peak": 1, "corner_peak": 2, "gaussian": 3
 
 FP64 = 0x100
 PLAIN = 0x200
+AOS = 0x400
 
 OK, EINVAL, ENOMEM, ECUDA, EABORT, ETIMEOUT, EADMIT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
 ESCRATCH = -9
@@ -132,6 +133,17 @@ _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
 _d = ctypes.c_double
 
+INTEGRAND = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                             ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                             ctypes.c_void_p)
+
+
+class GenzCallbackData(ctypes.Structure):
+    """cv_genz_cb_data: userdata of the library's own device integrand."""
+    _fields_ = [("g", Genz), ("flags", ctypes.c_int)]
+
+
 _SIGNATURES = {
     "cv_create": (_i, [_P(_vp), _i, _vp]),
     "cv_destroy": (None, [_vp]),
@@ -162,6 +174,9 @@ _SIGNATURES = {
     "cv_batch_kernels_per_run": (_i, [_vp]),
     "cv_batch_destroy": (None, [_vp]),
     "cv_batch_vegas": (_i, [_vp, _i, _vp, _vp]),
+    "cv_vegas_cb": (_i, [_vp, _i, _i, _vp, _vp, _i64, _d, _d, _i, _i, _i64, _i64, _i64, _i64,
+                         _i64, _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
+    "cv_genz_callback": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "cv_server_start": (_i, [_vp, _P(ServerOpts), _P(_vp)]),
     "cv_submit": (_i, [_vp, _P(Spec), _P(_u64)]),
     "cv_poll": (_i, [_vp, _u64, _P(Result)]),
@@ -280,6 +295,32 @@ class Context:
                                 ctypes.byref(neval), ctypes.byref(fail),
                                 integral.ctypes.data, error.ctypes.data, prob.ctypes.data)
         self._check(rc, "cv_vegas")
+        return VegasResult(neval.value, fail.value, integral, error, prob)
+
+    def vegas_cb(self, integrand, ndim: int, ncomp: int, userdata=None, nvec=10 ** 6,
+                 epsrel=0.0, epsabs=0.0, flags=0, seed=0, mineval=0, maxeval=10 ** 6,
+                 nstart=10 ** 4, nincrease=0, nbatch=1000, nbins=64) -> VegasResult:
+        """cv_vegas_cb with a device integrand: a ctypes INTEGRAND, an int
+        function address (e.g. builtin_integrand()), or a Python callable
+        f(x, fvals, nvec, stream) -> int receiving torch views of the device
+        buffers (x: [ndim, nvec], fvals: [ncomp, nvec]; CV_AOS: transposed)."""
+        if isinstance(integrand, int):
+            fn = ctypes.cast(integrand, INTEGRAND)
+        elif isinstance(integrand, INTEGRAND):
+            fn = integrand
+        else:
+            fn = _torch_integrand(integrand, flags)
+        nc = ncomp
+        integral, error, prob = np.zeros(nc), np.zeros(nc), np.zeros(nc)
+        neval, fail = ctypes.c_int64(), ctypes.c_int()
+        ud = ctypes.cast(ctypes.pointer(userdata), ctypes.c_void_p) if userdata is not None else None
+        rc = self._lib.cv_vegas_cb(self._h, ndim, nc, ctypes.cast(fn, ctypes.c_void_p), ud, nvec,
+                                   epsrel, epsabs, flags, seed, mineval, maxeval, nstart,
+                                   nincrease, nbatch, nbins, ctypes.byref(neval), ctypes.byref(fail),
+                                   integral.ctypes.data, error.ctypes.data, prob.ctypes.data)
+        if rc == EABORT:
+            return VegasResult(neval.value, fail.value, integral, error, prob)
+        self._check(rc, "cv_vegas_cb")
         return VegasResult(neval.value, fail.value, integral, error, prob)
 
     def integral(self, sp: Spec) -> "Integral":
@@ -472,3 +513,39 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+def builtin_integrand() -> int:
+    """Address of cv_genz_callback, the library's device integrand (its
+    userdata is a GenzCallbackData)."""
+    return ctypes.cast(lib().cv_genz_callback, ctypes.c_void_p).value
+
+
+class _DeviceBuffer:
+    """__cuda_array_interface__ view of a device pointer for torch."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": shape,
+                                         "typestr": typestr, "version": 3, "strides": None}
+
+
+def _torch_integrand(fn, flags):
+    import torch
+    typestr = "<f8" if flags & FP64 else "<f4"
+
+    def tramp(ndim_p, x, ncomp_p, f, userdata, nvec_p, ld_p, stream):
+        ndim, ncomp, nvec, ld = ndim_p[0], ncomp_p[0], nvec_p[0], ld_p[0]
+        if flags & AOS:
+            xv = torch.as_tensor(_DeviceBuffer(x, (nvec, ndim), typestr), device="cuda")
+            fv = torch.as_tensor(_DeviceBuffer(f, (nvec, ncomp), typestr), device="cuda")
+        else:
+            xv = torch.as_tensor(_DeviceBuffer(x, (ndim, ld), typestr), device="cuda")[:, :nvec]
+            fv = torch.as_tensor(_DeviceBuffer(f, (ncomp, ld), typestr), device="cuda")[:, :nvec]
+        return int(fn(xv, fv, nvec, stream))
+
+    cb = INTEGRAND(tramp)
+    _KEEP.append(cb)
+    return cb
+
+
+_KEEP = []

@@ -1626,3 +1626,224 @@ extern "C" int cv_server_stop(cv_server *S)
     server_release(S);
     return err;
 }
+
+// ------------------------------------------------------------ user integrands
+namespace cv {
+#define CV_EXTERN_M(D)                                                                               \
+    extern template cudaError_t launch_materialise<D, float, false>(const MatArgs<float> &, int, cudaStream_t);   \
+    extern template cudaError_t launch_materialise<D, float, true>(const MatArgs<float> &, int, cudaStream_t);    \
+    extern template cudaError_t launch_materialise<D, double, false>(const MatArgs<double> &, int, cudaStream_t); \
+    extern template cudaError_t launch_materialise<D, double, true>(const MatArgs<double> &, int, cudaStream_t);  \
+    extern template cudaError_t launch_accumulate<D, float, false>(const MatArgs<float> &, int, cudaStream_t);    \
+    extern template cudaError_t launch_accumulate<D, float, true>(const MatArgs<float> &, int, cudaStream_t);     \
+    extern template cudaError_t launch_accumulate<D, double, false>(const MatArgs<double> &, int, cudaStream_t);  \
+    extern template cudaError_t launch_accumulate<D, double, true>(const MatArgs<double> &, int, cudaStream_t);
+CV_FOR_EACH_NDIM(CV_EXTERN_M)
+#undef CV_EXTERN_M
+
+template <typename Real>
+static cudaError_t dispatch_matpass(int ndim, bool aos, bool acc, const MatArgs<Real> &a, int grid,
+                                    cudaStream_t s)
+{
+    switch (ndim) {
+#define CV_CASE(D)                                                                       \
+    case D:                                                                              \
+        if (acc) return aos ? launch_accumulate<D, Real, true>(a, grid, s)              \
+                            : launch_accumulate<D, Real, false>(a, grid, s);             \
+        return aos ? launch_materialise<D, Real, true>(a, grid, s)                       \
+                   : launch_materialise<D, Real, false>(a, grid, s);
+        CV_FOR_EACH_NDIM(CV_CASE)
+#undef CV_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename Real>
+static cudaError_t dispatch_genz_points(int ndim, bool aos, const GenzParams<Real> &g, const Real *x,
+                                        Real *f, long long n, long long ld, int grid, cudaStream_t s)
+{
+    switch (ndim) {
+#define CV_CASE(D)                                                                                  \
+    case D: return aos ? launch_genz_points<D, Real, true>(g, x, f, n, ld, grid, s)               \
+                       : launch_genz_points<D, Real, false>(g, x, f, n, ld, grid, s);
+        CV_FOR_EACH_NDIM(CV_CASE)
+#undef CV_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace cv
+
+extern "C" int cv_genz_callback(const int *ndim, const void *x_dev, const int *ncomp, void *f_dev,
+                                void *userdata, const int64_t *nvec, const int64_t *ld, void *stream)
+{
+    const cv_genz_cb_data *u = (const cv_genz_cb_data *)userdata;
+    if (!u || !ndim || !ncomp || !nvec || !ld || *ndim != u->g.ndim || *ncomp != u->g.ncomp) return -999;
+    const long long n = *nvec;
+    if (n <= 0) return 0;
+    long long grid = (n + kBlock - 1) / kBlock;
+    if (grid > 152 * 16) grid = 152 * 16;
+    const bool aos = (u->flags & CV_AOS) != 0;
+    cudaError_t e;
+    if (u->flags & CV_FP64) {
+        GenzParams<double> g;
+        fill_params<double>(&u->g, &g);
+        e = dispatch_genz_points<double>(*ndim, aos, g, (const double *)x_dev, (double *)f_dev, n, *ld,
+                                         (int)grid, (cudaStream_t)stream);
+    } else {
+        GenzParams<float> g;
+        fill_params<float>(&u->g, &g);
+        e = dispatch_genz_points<float>(*ndim, aos, g, (const float *)x_dev, (float *)f_dev, n, *ld,
+                                        (int)grid, (cudaStream_t)stream);
+    }
+    return e == cudaSuccess ? 0 : -999;
+}
+
+template <typename Real>
+static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, void *userdata,
+                        long long nvec, const cv_spec &sp, cv_result *res)
+{
+    const bool aos = (sp.flags & CV_AOS) != 0;
+    const int N = sp.nbins;
+    int jmax = 0;
+    long long nmax = 0;
+    plan(sp.nstart, sp.nincrease, sp.maxeval, &jmax, &nmax);
+    const long long tile = nvec < nmax ? nvec : nmax;
+    // device memory: state, grid, histogram, x, f
+    const size_t sz_state = (sizeof(DevState) + 255) & ~(size_t)255;
+    const size_t sz_edges = (((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255;
+    const size_t sz_H = (((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255;
+    const size_t sz_x = (((size_t)ndim * tile * sizeof(Real)) + 255) & ~(size_t)255;
+    const size_t sz_f = (size_t)ncomp * tile * sizeof(Real);
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, sz_state + sz_edges + sz_H + sz_x + sz_f) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_msg(ctx, CV_ENOMEM, "device allocation for %lld materialised points failed", tile);
+    }
+    char *p = (char *)mem;
+    DevState *st = (DevState *)p;
+    double *edges = (double *)(p + sz_state);
+    double *H = (double *)(p + sz_state + sz_edges);
+    Real *x = (Real *)(p + sz_state + sz_edges + sz_H);
+    Real *f = (Real *)(p + sz_state + sz_edges + sz_H + sz_x);
+    int rc = CV_OK;
+    cudaStream_t s = ctx->stream;
+    CombineArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.st = st;
+    ca.ncomp = ncomp;
+    ca.epsrel = sp.epsrel;
+    ca.epsabs = sp.epsabs;
+    ca.mineval = sp.mineval;
+    ca.maxeval = sp.maxeval;
+    ca.nstart = sp.nstart;
+    ca.nincrease = sp.nincrease;
+    MatArgs<Real> a;
+    memset(&a, 0, sizeof(a));
+    a.nbins = N;
+    a.ncomp = ncomp;
+    a.map = make_map(N);
+    a.edges = edges;
+    a.ld = tile;
+    a.x = x;
+    a.f = f;
+    a.S1 = st->S1;
+    a.S2 = st->S2;
+    a.H = H;
+    const int one = 1;
+    int aborted = 0;
+    cudaError_t e = launch_reset(st, edges, H, ndim, N, sp.nstart, s);
+    unsigned long long start = 1;
+    for (int j = 0; j < jmax && e == cudaSuccess && !aborted; ++j) {
+        const long long nj = sp.nstart + (long long)j * sp.nincrease;
+        for (long long off = 0; off < nj && e == cudaSuccess; off += tile) {
+            const long long m = nj - off < tile ? nj - off : tile;
+            a.start = start + (unsigned long long)off;
+            a.n = m;
+            long long grid = (m + 32 * 8 * 16 - 1) / (32 * 8 * 16);
+            if (grid > (long long)ctx->sms * 4) grid = (long long)ctx->sms * 4;
+            if (grid < 1) grid = 1;
+            e = dispatch_matpass<Real>(ndim, aos, false, a, (int)grid, s);
+            if (e != cudaSuccess) break;
+            const int64_t nv = m, ld = tile;
+            const int r = cb(&ndim, x, &ncomp, f, userdata, &nv, &ld, (void *)s);
+            if (r == -999) {
+                aborted = 1;
+                break;
+            }
+            e = dispatch_matpass<Real>(ndim, aos, true, a, (int)grid, s);
+        }
+        if (aborted || e != cudaSuccess) break;
+        e = cudaMemcpyAsync(&st->pass_active, &one, sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_refine_combine(ndim, N, H, edges, ca, s);
+        int stopped = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&stopped, &st->stopped, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        start += (unsigned long long)nj;
+        if (stopped) break;
+    }
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "materialised pass");
+    DevState h;
+    memset(&h, 0, sizeof(h));
+    if (!rc) {
+        e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "result copy");
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(mem);
+    if (rc) return rc;
+    memset(res, 0, sizeof(*res));
+    res->neval = h.neval;
+    res->iterations = h.iter;
+    res->fail = aborted ? -999 : (h.stopped ? h.fail : 1);
+    for (int c = 0; c < ncomp; ++c) {
+        res->integral[c] = h.integral[c];
+        res->error[c] = h.error[c];
+        res->prob[c] = h.prob[c];
+    }
+    if (aborted) return fail_msg(ctx, CV_EABORT, "the integrand returned -999");
+    return CV_OK;
+}
+
+extern "C" int cv_vegas_cb(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev integrand,
+                           void *userdata, int64_t nvec, double epsrel, double epsabs, int flags,
+                           int seed, int64_t mineval, int64_t maxeval, int64_t nstart,
+                           int64_t nincrease, int64_t nbatch, int nbins, int64_t *neval, int *fail,
+                           double integral[], double error[], double prob[])
+{
+    (void)seed;
+    (void)nbatch;
+    if (!ctx) return CV_EINVAL;
+    if (!integrand) return fail_msg(ctx, CV_EINVAL, "null integrand");
+    if (ndim < 1 || ndim > CV_MAX_DIM || ncomp < 1 || ncomp > CV_MAX_COMP)
+        return fail_msg(ctx, CV_EINVAL, "ndim/ncomp out of range");
+    if (nvec < 1) return fail_msg(ctx, CV_EINVAL, "nvec must be >= 1");
+    cv_spec sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.g.ndim = ndim;
+    sp.g.ncomp = ncomp;
+    sp.nbins = nbins;
+    sp.flags = flags;
+    sp.epsrel = epsrel;
+    sp.epsabs = epsabs;
+    sp.mineval = mineval;
+    sp.maxeval = maxeval;
+    sp.nstart = nstart;
+    sp.nincrease = nincrease;
+    int rc = check_spec(ctx, &sp);
+    if (rc) return rc;
+    if (!neval || !fail || !integral || !error || !prob) return fail_msg(ctx, CV_EINVAL, "null output");
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    cv_result res;
+    rc = (flags & CV_FP64) ? vegas_cb_run<double>(ctx, ndim, ncomp, integrand, userdata, nvec, sp, &res)
+                           : vegas_cb_run<float>(ctx, ndim, ncomp, integrand, userdata, nvec, sp, &res);
+    if (rc && rc != CV_EABORT) return rc;
+    *neval = res.neval;
+    *fail = res.fail;
+    for (int c = 0; c < ncomp; ++c) {
+        integral[c] = res.integral[c];
+        error[c] = res.error[c];
+        prob[c] = res.prob[c];
+    }
+    return rc;
+}

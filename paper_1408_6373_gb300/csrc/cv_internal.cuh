@@ -96,6 +96,25 @@ struct CombineArgs {
     double *log_var;
 };
 
+// ---- materialised samples (user integrand) ----
+// One tile of n points (Sobol indices start..start+n-1) written out as x and,
+// after the user's integrand has filled f, accumulated like a fused pass.
+// Layout: SoA x[d*ld + j], f[c*ld + j]; AoS (the paper's integrand
+// contract) x[j*ndim + d], f[j*ncomp + c].
+template <typename Real>
+struct MatArgs {
+    int nbins;
+    int ncomp;
+    MapParams map;
+    const double *edges;
+    unsigned long long start;
+    long long n;
+    long long ld;
+    Real *x;
+    const Real *f;
+    double *S1, *S2, *H;
+};
+
 // ---- batched persistent launch (many integrals) ----
 // One integral of a batch as the device sees it.
 struct BatchItem {
@@ -140,6 +159,15 @@ cudaError_t batch_occupancy(bool pow2, int stride, int *blocks_per_sm);
 template <int NDIM, typename Word>
 cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
                          unsigned long long *Y, int grid, cudaStream_t s);
+
+template <int NDIM, typename Real, bool AOS>
+cudaError_t launch_materialise(const MatArgs<Real> &a, int grid, cudaStream_t s);
+template <int NDIM, typename Real, bool AOS>
+cudaError_t launch_accumulate(const MatArgs<Real> &a, int grid, cudaStream_t s);
+
+template <int NDIM, typename Real, bool AOS>
+cudaError_t launch_genz_points(const GenzParams<Real> &g, const Real *x, Real *f, long long n,
+                               long long ld, int grid, cudaStream_t s);
 
 // cv_refine.cu
 cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, cudaStream_t s);

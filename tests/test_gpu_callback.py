@@ -1,0 +1,117 @@
+"""GPU tests of the materialised-sample mode (cv_vegas_cb): the integrand
+contract of Sect. 3.2.1-3.2.2 on the device -- up to nvec points per call,
+the actual count passed, -999 aborts -- in both layouts, against the fused
+path and the FP64 oracle."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1408_6373_gb300 as cg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cg.build_library()
+    c = cg.Context(0)
+    yield c
+    c.close()
+
+
+def _genz(ndim=5, seed=3):
+    rng = np.random.default_rng(seed)
+    a = 0.5 + rng.random((2, ndim))
+    u = rng.random((2, ndim))
+    return cg.genz(ndim, [cg.GAUSSIAN, cg.PRODUCT_PEAK], a, u), a, u
+
+
+@pytest.mark.parametrize("aos", [False, True])
+def test_builtin_integrand_fp64_matches_oracle_and_fused(ctx, aos):
+    g, a, u = _genz()
+    flags = cg.FP64 | (cg.AOS if aos else 0)
+    ud = cg.GenzCallbackData(g, flags)
+    kw = dict(maxeval=6 * 12000, nstart=12000, nbins=50)
+    r = ctx.vegas_cb(cg.builtin_integrand(), 5, 2, userdata=ud, nvec=5000, flags=flags, **kw)
+    fused = ctx.vegas(g, flags=cg.FP64, **kw)
+    o = O.vegas(O.Problem(5, [O.GAUSSIAN, O.PRODUCT_PEAK], a, u, nbins=50), maxeval=kw["maxeval"],
+                nstart=kw["nstart"])
+    assert (r.neval, r.fail) == (o.neval, o.fail)
+    np.testing.assert_allclose(r.integral, o.integral, rtol=1e-12)
+    np.testing.assert_allclose(r.integral, fused.integral, rtol=1e-12)
+    np.testing.assert_allclose(r.error, o.error, rtol=1e-10)
+
+
+def test_builtin_integrand_fp32_close_to_fused(ctx):
+    g, a, u = _genz(seed=4)
+    ud = cg.GenzCallbackData(g, 0)
+    kw = dict(maxeval=5 * 20000, nstart=20000, nbins=64)
+    r = ctx.vegas_cb(cg.builtin_integrand(), 5, 2, userdata=ud, nvec=1 << 20, flags=0, **kw)
+    fused = ctx.vegas(g, flags=0, **kw)
+    for c in range(2):
+        assert abs(r.integral[c] - fused.integral[c]) <= 2e-5 * abs(fused.integral[c]) + 1e-2 * fused.error[c]
+
+
+def test_tiles_do_not_change_results(ctx):
+    g, _, _ = _genz(seed=5)
+    ud = cg.GenzCallbackData(g, cg.FP64)
+    kw = dict(flags=cg.FP64, maxeval=4 * 10000, nstart=10000, nbins=32)
+    one = ctx.vegas_cb(cg.builtin_integrand(), 5, 2, userdata=ud, nvec=10000, **kw)
+    many = ctx.vegas_cb(cg.builtin_integrand(), 5, 2, userdata=ud, nvec=777, **kw)
+    np.testing.assert_allclose(one.integral, many.integral, rtol=1e-13)
+
+
+def test_torch_integrand_and_nvec_contract(ctx):
+    # a user integrand written with torch on the device buffers
+    ndim = 4
+    a = torch.tensor([3.0, 2.0, 2.5, 1.5], device="cuda")
+    u = torch.tensor([0.5, 0.4, 0.6, 0.3], device="cuda")
+    seen = []
+
+    def gauss(x, f, nvec, stream):
+        seen.append(nvec)
+        f[0].copy_(torch.exp(-(((x - u[:, None]) * a[:, None]) ** 2).sum(0)))
+        return 0
+
+    r = ctx.vegas_cb(gauss, ndim, 1, nvec=3000, flags=0, maxeval=5 * 8000, nstart=8000, nbins=32)
+    assert max(seen) <= 3000 and sum(seen) == 5 * 8000
+    exact = O.genz_exact(O.GAUSSIAN, a.cpu().numpy(), u.cpu().numpy())
+    assert abs(r.integral[0] - exact) < 3 * r.error[0] + 1e-6 * exact
+    g = cg.genz(ndim, [cg.GAUSSIAN], a.cpu().numpy(), u.cpu().numpy())
+    ref = ctx.vegas_cb(cg.builtin_integrand(), ndim, 1, userdata=cg.GenzCallbackData(g, 0), nvec=3000,
+                       flags=0, maxeval=5 * 8000, nstart=8000, nbins=32)
+    assert r.integral[0] == pytest.approx(ref.integral[0], rel=1e-5)
+
+
+def test_integrand_abort(ctx):
+    calls = []
+
+    def abort_second(x, f, nvec, stream):
+        calls.append(nvec)
+        f.fill_(1.0)
+        return -999 if len(calls) == 2 else 0
+
+    r = ctx.vegas_cb(abort_second, 3, 1, nvec=1000, flags=0, maxeval=10 * 5000, nstart=5000, nbins=16)
+    assert r.fail == -999 and len(calls) == 2
+
+
+def test_aos_layout_seen_by_integrand(ctx):
+    shapes = []
+
+    def rec(x, f, nvec, stream):
+        shapes.append(tuple(x.shape))
+        f[:, 0].copy_(x.sum(1))
+        return 0
+
+    r = ctx.vegas_cb(rec, 3, 1, nvec=2048, flags=cg.AOS | cg.FP64, maxeval=2 * 4096, nstart=4096,
+                     nbins=16)
+    assert shapes[0] == (2048, 3)
+    # integral of x1 + x2 + x3 over the unit cube
+    assert r.integral[0] == pytest.approx(1.5, rel=1e-4)
