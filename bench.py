@@ -370,6 +370,8 @@ def run_ours(args):
     }
     if not args.no_batch:
         line["batch4096"] = measure_batch(ctx, cg, W, args.warmup, args.steps)
+    if not args.no_materialised:
+        line["materialised"] = measure_materialised(ctx, cg, W)
     if not args.no_serve:
         line["serve"] = measure_serve(ctx, cg, W, duration=args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline:
@@ -439,6 +441,33 @@ def measure_batch(ctx, cg, W, warmup: int, steps: int, subset: int = 32) -> dict
                                   "max_abs_diff_in_sigma": max(dev)}}
 
 
+def measure_materialised(ctx, cg, W) -> dict:
+    """The materialised-sample mode on the genz8d4c shape: every iteration's
+    1e7 points written to HBM (FP32, dimension-major), evaluated by the
+    library's own device integrand, and accumulated.  Reports samples/s and
+    the HBM bytes per sample of the library's two kernels (write x, read f;
+    the integrand's own traffic, read x and write f, is the caller's)."""
+    import torch
+    p = W.genz8d4c()
+    g = cg.genz(p.ndim, p.families, p.a, p.u)
+    ud = cg.GenzCallbackData(g, 0)
+    kw = dict(userdata=ud, nvec=p.nstart, flags=0, maxeval=p.maxeval, nstart=p.nstart, nbins=p.nbins)
+    ctx.vegas_cb(cg.builtin_integrand(), p.ndim, p.ncomp, **dict(kw, maxeval=2 * p.nstart))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    r = ctx.vegas_cb(cg.builtin_integrand(), p.ndim, p.ncomp, **kw)
+    dt = time.perf_counter() - t
+    lib_bytes = 4 * p.ndim + 4 * p.ncomp
+    all_bytes = 2 * lib_bytes
+    rate = p.maxeval / dt
+    return {"workload": "genz8d4c with the integrand called on materialised points (nvec = 1e7, "
+                        "x and f dimension-major in HBM, library's own Genz integrand)",
+            "value": rate, "unit": UNIT, "ms_per_step": 1e3 * dt,
+            "library_bytes_per_sample": lib_bytes, "all_bytes_per_sample": all_bytes,
+            "hbm_gbs_all_kernels": rate * all_bytes / 1e9,
+            "integral": list(r.integral)}
+
+
 def measure_serve(ctx, cg, W, duration: float = 1.0, rate: float = 2000.0,
                   plain_subset: int = 100) -> dict:
     """The serving loop under Poisson arrivals (ndim U{2..32}, ncomp U{1..4},
@@ -467,6 +496,20 @@ def measure_serve(ctx, cg, W, duration: float = 1.0, rate: float = 2000.0,
     S.stop()
     samples = sum(r.neval for r in res)
     ok = sum(1 for r in res if r.fail == 0)
+    # the same first requests served alone, at their arrival times: the
+    # latency to compare with the plain FP64 server below
+    S = ctx.server(hbm_budget_bytes=8 << 30)
+    ids = []
+    t0 = time.perf_counter()
+    for (t, _), sp in zip(reqs[:plain_subset], specs[:plain_subset]):
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        ids.append(S.submit(sp))
+    for i in ids:
+        S.wait(i, 600000)
+    st_sub = S.stats()
+    S.stop()
     service = []
     for sp in specs[:plain_subset]:
         t = time.perf_counter()
@@ -488,6 +531,8 @@ def measure_serve(ctx, cg, W, duration: float = 1.0, rate: float = 2000.0,
             "throughput": {"value": samples / wall, "unit": UNIT},
             "requests_per_s": len(reqs) / wall, "rounds": st.rounds, "max_live": st.max_live,
             "wall_s": wall, "busy_s": st.busy_s,
+            "served_first_requests": {"requests": plain_subset, "p50_ms": st_sub.p50_ms,
+                                      "p99_ms": st_sub.p99_ms},
             "plain_fp64_fifo": {"requests": len(service), "p50_ms": q(0.5), "p99_ms": q(0.99),
                                 "throughput": {"value": sum(r.neval for r in res[:plain_subset]) / sum(service),
                                                "unit": UNIT},
@@ -503,6 +548,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-integral batch")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--no-materialised", action="store_true", help="skip the materialised-sample run")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window of the serving run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
