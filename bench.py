@@ -370,6 +370,8 @@ def run_ours(args):
     }
     if not args.no_batch:
         line["batch4096"] = measure_batch(ctx, cg, W, args.warmup, args.steps)
+    if not args.no_large:
+        line["large30d"] = measure_large(ctx, cg, W)
     if not args.no_materialised:
         line["materialised"] = measure_materialised(ctx, cg, W)
     if not args.no_serve:
@@ -468,6 +470,38 @@ def measure_materialised(ctx, cg, W) -> dict:
             "integral": list(r.integral)}
 
 
+def measure_large(ctx, cg, W, steps: int = 1) -> dict:
+    """The large single-integral configuration: ndim 30, 256 bins,
+    15 iterations x 1e9 points (indices past 2^33), C0 and discontinuous
+    integrands, one device-resident integral each, device-timed."""
+    import torch
+    out = {"workload": "large30d: ndim 30, C0 and discontinuous, a = 1/2, u ~ U(0,1), 256 bins, "
+                       "15 iterations x 1e9 Sobol points, FP32 eval / FP64 reduce"}
+    total_ms, total = 0.0, 0
+    res = []
+    for p in W.large30d():
+        g = cg.genz(p.ndim, p.families, p.a, p.u)
+        I = ctx.integral(cg.spec(g, nbins=p.nbins, maxeval=p.maxeval, nstart=p.nstart))
+        I.reset()
+        I.run()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            I.reset()
+            I.run()
+            s1.record()
+            torch.cuda.synchronize()
+            total_ms += s0.elapsed_time(s1)
+            total += p.maxeval
+        r = I.result()
+        res.append({"family": p.families[0], "integral": r.integral[0], "error": r.error[0]})
+        I.close()
+    out.update({"value": total / (total_ms / 1e3), "unit": UNIT, "ms_per_step": total_ms / steps,
+                "samples_per_step": total // steps, "results": res})
+    return out
+
+
 def measure_serve(ctx, cg, W, duration: float = 1.0, rate: float = 2000.0,
                   plain_subset: int = 100) -> dict:
     """The serving loop under Poisson arrivals (ndim U{2..32}, ncomp U{1..4},
@@ -549,6 +583,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-integral batch")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--no-materialised", action="store_true", help="skip the materialised-sample run")
+    ap.add_argument("--no-large", action="store_true", help="skip the 30-dimension 1e9-point run")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window of the serving run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
