@@ -176,7 +176,7 @@ def test_refine_matches_oracle(ctx, ndim, nbins):
 
 
 # ------------------------------------------------------------------ Vegas
-def test_vegas_cfg1_fp64_matches_oracle(ctx):
+def test_vegas_gaussian3d_fp64_matches_oracle(ctx):
     ndim, N, n = 3, 50, 10 ** 4
     g = cg.genz(ndim, [cg.GAUSSIAN], 5.0, 0.5)
     p = O.Problem(ndim, [O.GAUSSIAN], np.full((1, 3), 5.0), np.full((1, 3), 0.5), nbins=N)

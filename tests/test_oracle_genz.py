@@ -56,7 +56,7 @@ def test_closed_form_3d_against_gauss_legendre(fam):
     assert acc == pytest.approx(O.genz_exact(fam, a, u), rel=1e-10)
 
 
-def test_gaussian_cfg1_closed_form():
+def test_gaussian3d_a5_closed_form():
     # a_i = 5, u_i = 1/2 in 3 dimensions: (sqrt(pi)/5 erf(5/2))^3.
     expect = (math.sqrt(math.pi) / 5.0 * math.erf(2.5)) ** 3
     val = O.genz_exact(O.GAUSSIAN, [5.0] * 3, [0.5] * 3)

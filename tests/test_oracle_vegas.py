@@ -253,7 +253,7 @@ def test_combine_worked_examples():
 
 
 # ---------------------------------------------------------------- driver
-def test_vegas_cfg1_gaussian_within_three_sigma():
+def test_vegas_gaussian3d_within_three_sigma():
     p = _problem(3, [O.GAUSSIAN], 5.0, 0.5, nbins=50)
     r = O.vegas(p, maxeval=10 * 10 ** 4, nstart=10 ** 4)
     exact = (math.sqrt(math.pi) / 5.0 * math.erf(2.5)) ** 3
