@@ -26,7 +26,12 @@
 #ifndef CUBAGPU_H
 #define CUBAGPU_H
 
+#if defined(__CUDACC_RTC__)
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+#else
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -85,6 +90,14 @@ extern "C" {
 #define CV_FP64 0x100
 #define CV_PLAIN 0x200
 #define CV_AOS 0x400           /* cv_vegas_cb: x[nvec][ndim], f[nvec][ncomp] */
+/* CV_JIT: FP32 path only -- sample with a kernel compiled at run time
+ * (NVRTC) for this integrand: its component families and parameters become
+ * compile-time constants (bit-identical values), which removes the
+ * per-point family dispatch and parameter loads.  The first use of a given
+ * integrand compiles (about a second) and caches the kernel for the
+ * process; without NVRTC, or if a compile fails, the generic kernel runs.
+ * Results equal those of the generic kernel. */
+#define CV_JIT 0x800
 
 /* One integral: ncomp components of one ndim-dimensional Genz problem.
  * a[c][i], u[c][i] are the parameters of component c (unused entries
@@ -198,6 +211,10 @@ typedef struct {
 } cv_genz_cb_data;
 int cv_genz_callback(const int *ndim, const void *x_dev, const int *ncomp, void *f_dev,
                      void *userdata, const int64_t *nvec, const int64_t *ld, void *stream);
+
+/* Number of specialised kernels compiled so far in this process (CV_JIT);
+ * *available is 1 if run-time compilation can be used at all. */
+int cv_jit_info(int *available, int *compiled);
 
 /* Bytes cv_vegas moves between host and device per call for an integral of
  * this shape: kernel parameters in (h2d), the final state out (d2h). */

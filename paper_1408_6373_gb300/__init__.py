@@ -30,6 +30,7 @@ FAMILIES = {"oscillatory": 0, "product_peak": 1, "corner_peak": 2, "gaussian": 3
 FP64 = 0x100
 PLAIN = 0x200
 AOS = 0x400
+JIT = 0x800
 
 OK, EINVAL, ENOMEM, ECUDA, EABORT, ETIMEOUT, EADMIT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
 ESCRATCH = -9
@@ -156,6 +157,7 @@ _SIGNATURES = {
     "cv_vegas": (_i, [_vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64, _i64,
                       _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_vegas_io_bytes": (_i, [_i, _i, _P(_i64), _P(_i64)]),
+    "cv_jit_info": (_i, [_P(_i), _P(_i)]),
     "cv_vegas_noalloc": (_i, [_i, _vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64,
                               _i64, _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_integral_create": (_i, [_vp, _P(Spec), _P(_vp)]),
@@ -359,6 +361,14 @@ def vegas_noalloc(g: Genz, device: int = 0, stream=None, epsrel=0.0, epsabs=0.0,
     if rc != OK:
         raise CubaGpuError(rc, "cv_vegas_noalloc: " + lib().cv_strerror(rc).decode())
     return VegasResult(neval.value, fail.value, integral, error, prob)
+
+
+def jit_info():
+    """(available, compiled): can kernels be specialised at run time, and how
+    many have been in this process (CV_JIT)."""
+    a, c = ctypes.c_int(), ctypes.c_int()
+    lib().cv_jit_info(ctypes.byref(a), ctypes.byref(c))
+    return bool(a.value), c.value
 
 
 def vegas_io_bytes(ndim: int, nbins: int):

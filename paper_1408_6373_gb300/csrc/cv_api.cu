@@ -290,10 +290,13 @@ static MapParams make_map(int N)
     return m;
 }
 
+// Register budget the generic kernel uses (kMinBlocks in cv_device.cuh).
+static int min_blocks_f32(int ndim) { return ndim <= 8 ? 3 : (ndim <= 16 ? 2 : 1); }
+
 template <typename Real>
 static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *edges,
                        unsigned long long start, long long n, long long n_grid,
-                       double *S1, double *S2, double *H, DevState *st)
+                       double *S1, double *S2, double *H, DevState *st, bool jit = false)
 {
     SampleArgs<Real> a;
     memset(&a, 0, sizeof(a));
@@ -308,11 +311,34 @@ static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *e
     a.start = start;
     a.n = n;
     a.st = st;
+    if constexpr (sizeof(Real) == 4) {
+        if (jit) {
+            JitKernel k;
+            std::string err;
+            if (jit_sample_kernel(ctx->device, a, g->ndim, a.map.pow2 != 0, min_blocks_f32(g->ndim), &k, &err) == 0) {
+                const int grid = sample_grid(ctx, k.occ, n_grid);
+                cudaError_t e = launch_jit_sample(k, a, grid, ctx->stream);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "specialised sampling kernel launch");
+                return CV_OK;
+            }
+            snprintf(ctx->msg, sizeof(ctx->msg), "run-time specialisation unavailable (%s); generic kernel used",
+                     err.c_str());
+        }
+    }
     int occ = 0, rc = occupancy(ctx, g->ndim, nbins, sizeof(Real) == 8, &occ);
     if (rc) return rc;
     const int grid = sample_grid(ctx, occ, n_grid);
     cudaError_t e = dispatch_sample<Real>(g->ndim, a, grid, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sampling kernel launch");
+    return CV_OK;
+}
+
+extern "C" int cv_jit_info(int *available, int *compiled)
+{
+    int c = 0;
+    const int a = jit_info(&c);
+    if (available) *available = a;
+    if (compiled) *compiled = c;
     return CV_OK;
 }
 
@@ -354,7 +380,8 @@ extern "C" int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins, const double 
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
     if (flags & CV_FP64)
         return launch_pass<double>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr);
-    return launch_pass<float>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr);
+    return launch_pass<float>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr,
+                              (flags & CV_JIT) != 0);
 }
 
 extern "C" int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_dev, double *edges_dev)
@@ -424,7 +451,8 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
     ctx->stream = s;
     int rc = (sp.flags & CV_FP64)
         ? launch_pass<double>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st)
-        : launch_pass<float>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st);
+        : launch_pass<float>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st,
+                             (sp.flags & CV_JIT) != 0);
     ctx->stream = keep;
     if (rc) return rc;
     CombineArgs ca;
@@ -454,10 +482,21 @@ static int read_stopped(cv_integral *I, int *stopped)
 static int capture_graph(cv_integral *I)
 {
     cv_ctx *ctx = I->ctx;
-    // the occupancy query sets kernel attributes: do it before capturing
+    // the occupancy query sets kernel attributes, and a run-time
+    // specialisation compiles and loads a module: both before capturing
     int occ = 0;
     int rc = occupancy(ctx, I->spec.g.ndim, I->spec.nbins, (I->spec.flags & CV_FP64) != 0, &occ);
     if (rc) return rc;
+    if ((I->spec.flags & CV_JIT) && !(I->spec.flags & CV_FP64)) {
+        SampleArgs<float> a;
+        memset(&a, 0, sizeof(a));
+        fill_params<float>(&I->spec.g, &a.g);
+        a.nbins = I->spec.nbins;
+        a.map = make_map(I->spec.nbins);
+        JitKernel k;
+        std::string err;
+        jit_sample_kernel(ctx->device, a, I->spec.g.ndim, a.map.pow2 != 0, min_blocks_f32(I->spec.g.ndim), &k, &err);
+    }
     I->K = I->jmax < 32 ? I->jmax : 32;
     cudaGraph_t graph = nullptr;
     CV_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));

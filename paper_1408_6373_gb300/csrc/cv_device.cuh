@@ -128,16 +128,29 @@ __device__ __forceinline__ float ipow(float r)
     return acc;
 }
 
-// FP32 Genz evaluation of component C (parameters read straight from the
-// kernel's parameter space, so they are constant-bank operands).
-template <int NDIM, int C>
+// Integrand policies: where component C's family and parameters come from.
+// RuntimeIntegrand reads them from the launch's parameter block (constant
+// bank operands).  A policy generated for one problem returns compile-time
+// constants instead, so the family dispatch folds away and the parameters
+// become instruction immediates.
+template <typename Real>
+struct RuntimeIntegrand {
+    template <int C> __device__ __forceinline__ static int family(const GenzParams<Real> &g) { return g.family[C]; }
+    __device__ __forceinline__ static int ncomp(const GenzParams<Real> &g) { return g.ncomp; }
+    template <int C> __device__ __forceinline__ static Real p0(const GenzParams<Real> &g, int d) { return g.p0[C][d]; }
+    template <int C> __device__ __forceinline__ static Real p1(const GenzParams<Real> &g, int d) { return g.p1[C][d]; }
+    template <int C> __device__ __forceinline__ static Real q0(const GenzParams<Real> &g) { return g.q0[C]; }
+};
+
+// FP32 Genz evaluation of component C.
+template <int NDIM, int C, class I>
 __device__ __forceinline__ float genz_f32(const GenzParams<float> &g, const float (&x)[NDIM])
 {
-    switch (g.family[C]) {
+    switch (I::template family<C>(g)) {
     case CV_OSCILLATORY: {
-        float t = g.q0[C];  // phase in turns, reduced to [-1/2, 1/2]
+        float t = I::template q0<C>(g);  // phase in turns, reduced to [-1/2, 1/2]
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) t = __fmaf_rn(g.p0[C][d], x[d], t);
+        for (int d = 0; d < NDIM; ++d) t = __fmaf_rn(I::template p0<C>(g, d), x[d], t);
         t -= rintf(t);
         return __cosf(6.28318530717958647692f * t);
     }
@@ -145,22 +158,22 @@ __device__ __forceinline__ float genz_f32(const GenzParams<float> &g, const floa
         float P = 1.0f;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const float dx = x[d] - g.p1[C][d];
-            P *= __fmaf_rn(dx, dx, g.p0[C][d]);
+            const float dx = x[d] - I::template p1<C>(g, d);
+            P *= __fmaf_rn(dx, dx, I::template p0<C>(g, d));
         }
         return rcp_approx(P);
     }
     case CV_CORNER_PEAK: {
         float s = 1.0f;
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(g.p0[C][d], x[d], s);
+        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(I::template p0<C>(g, d), x[d], s);
         return ipow<NDIM + 1>(rcp_approx(s));
     }
     case CV_GAUSSIAN: {
         float s = 0.0f;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const float t = __fmaf_rn(g.p0[C][d], x[d], -g.p1[C][d]);
+            const float t = __fmaf_rn(I::template p0<C>(g, d), x[d], -I::template p1<C>(g, d));
             s = __fmaf_rn(t, t, s);
         }
         return __expf(-s);
@@ -168,15 +181,16 @@ __device__ __forceinline__ float genz_f32(const GenzParams<float> &g, const floa
     case CV_C0: {
         float s = 0.0f;
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(g.p0[C][d], fabsf(x[d] - g.p1[C][d]), s);
+        for (int d = 0; d < NDIM; ++d)
+            s = __fmaf_rn(I::template p0<C>(g, d), fabsf(x[d] - I::template p1<C>(g, d)), s);
         return __expf(-s);
     }
     case CV_DISCONTINUOUS: {
-        bool out = x[0] > g.p1[C][0];
-        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > g.p1[C][NDIM > 1 ? 1 : 0]);
+        bool out = x[0] > I::template p1<C>(g, 0);
+        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > I::template p1<C>(g, NDIM > 1 ? 1 : 0));
         float s = 0.0f;
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(g.p0[C][d], x[d], s);
+        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(I::template p0<C>(g, d), x[d], s);
         return out ? 0.0f : __expf(s);
     }
     default:
@@ -185,42 +199,43 @@ __device__ __forceinline__ float genz_f32(const GenzParams<float> &g, const floa
 }
 
 // FP64 Genz evaluation of component C (same formulas in double).
-template <int NDIM, int C>
+template <int NDIM, int C, class I>
 __device__ __forceinline__ double genz_f64(const GenzParams<double> &g, const double (&x)[NDIM])
 {
     double s = 0.0, P = 1.0;
-    switch (g.family[C]) {
+    switch (I::template family<C>(g)) {
     case CV_OSCILLATORY:
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fma_rn(g.p0[C][d], x[d], s);
-        return cos(g.q0[C] + s);
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(I::template p0<C>(g, d), x[d], s);
+        return cos(I::template q0<C>(g) + s);
     case CV_PRODUCT_PEAK:
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const double dx = x[d] - g.p1[C][d];
-            P *= 1.0 / __fma_rn(dx, dx, g.p0[C][d]);
+            const double dx = x[d] - I::template p1<C>(g, d);
+            P *= 1.0 / __fma_rn(dx, dx, I::template p0<C>(g, d));
         }
         return P;
     case CV_CORNER_PEAK:
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fma_rn(g.p0[C][d], x[d], s);
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(I::template p0<C>(g, d), x[d], s);
         return pow(1.0 + s, -(double)(NDIM + 1));
     case CV_GAUSSIAN:
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const double dx = x[d] - g.p1[C][d];
-            s = __fma_rn(g.p0[C][d] * dx, dx, s);
+            const double dx = x[d] - I::template p1<C>(g, d);
+            s = __fma_rn(I::template p0<C>(g, d) * dx, dx, s);
         }
         return exp(-s);
     case CV_C0:
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fma_rn(g.p0[C][d], fabs(x[d] - g.p1[C][d]), s);
+        for (int d = 0; d < NDIM; ++d)
+            s = __fma_rn(I::template p0<C>(g, d), fabs(x[d] - I::template p1<C>(g, d)), s);
         return exp(-s);
     case CV_DISCONTINUOUS: {
-        bool out = x[0] > g.p1[C][0];
-        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > g.p1[C][NDIM > 1 ? 1 : 0]);
+        bool out = x[0] > I::template p1<C>(g, 0);
+        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > I::template p1<C>(g, NDIM > 1 ? 1 : 0));
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fma_rn(g.p0[C][d], x[d], s);
+        for (int d = 0; d < NDIM; ++d) s = __fma_rn(I::template p0<C>(g, d), x[d], s);
         return out ? 0.0 : exp(s);
     }
     default:
@@ -228,15 +243,15 @@ __device__ __forceinline__ double genz_f64(const GenzParams<double> &g, const do
     }
 }
 
-template <int NDIM, int C>
+template <int NDIM, int C, class I = RuntimeIntegrand<float>>
 __device__ __forceinline__ float genz_eval(const GenzParams<float> &g, const float (&x)[NDIM])
 {
-    return genz_f32<NDIM, C>(g, x);
+    return genz_f32<NDIM, C, I>(g, x);
 }
-template <int NDIM, int C>
+template <int NDIM, int C, class I = RuntimeIntegrand<double>>
 __device__ __forceinline__ double genz_eval(const GenzParams<double> &g, const double (&x)[NDIM])
 {
-    return genz_f64<NDIM, C>(g, x);
+    return genz_f64<NDIM, C, I>(g, x);
 }
 
 // ------------------------------------------------------------ sums
@@ -355,13 +370,13 @@ template <> struct Word<float> { using type = unsigned int; };
 template <> struct Word<double> { using type = unsigned long long; };
 
 // Evaluate component C of the point and add it to the partial sums.
-template <int NDIM, int C, typename Real, bool EDGE>
+template <int NDIM, int C, typename Real, bool EDGE, class I>
 __device__ __forceinline__ void eval_comp(const GenzParams<Real> &g, const Real (&x)[NDIM],
                                           Real J, bool valid, Real (&p1)[CV_MAX_COMP],
                                           Real (&p2)[CV_MAX_COMP], Real &f0)
 {
-    if (C < g.ncomp) {
-        Real v = J * genz_eval<NDIM, C>(g, x);
+    if (C < I::ncomp(g)) {
+        Real v = J * genz_eval<NDIM, C, I>(g, x);
         if (EDGE && !valid) v = Real(0);
         p1[C] += v;
         p2[C] += v * v;
@@ -375,7 +390,7 @@ __device__ __forceinline__ void eval_comp(const GenzParams<Real> &g, const Real 
 // run's sum is added to the Kahan accumulators.
 constexpr unsigned kRun = 16;
 
-template <int NDIM, typename Real, bool POW2, bool EDGE>
+template <int NDIM, typename Real, bool POW2, bool EDGE, class I = RuntimeIntegrand<Real>>
 __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<Real> &sm,
                                           typename Word<Real>::type (&X)[NDIM],
                                           unsigned long long q0, unsigned nsteps,
@@ -407,10 +422,10 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
                     x[d] = map_f64(X[d], d, N, sm, J, slot[d]);
             }
             Real f0 = Real(0);
-            eval_comp<NDIM, 0, Real, EDGE>(A.g, x, J, valid, p1, p2, f0);
-            eval_comp<NDIM, 1, Real, EDGE>(A.g, x, J, valid, p1, p2, f0);
-            eval_comp<NDIM, 2, Real, EDGE>(A.g, x, J, valid, p1, p2, f0);
-            eval_comp<NDIM, 3, Real, EDGE>(A.g, x, J, valid, p1, p2, f0);
+            eval_comp<NDIM, 0, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+            eval_comp<NDIM, 1, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+            eval_comp<NDIM, 2, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+            eval_comp<NDIM, 3, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
             if (!EDGE || valid) {
                 const Real h = f0 * f0;
 #pragma unroll
@@ -420,7 +435,7 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
         }
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c) {
-            if (c < A.g.ncomp) {
+            if (c < I::ncomp(A.g)) {
                 s1[c].add(p1[c]);
                 s2[c].add(p2[c]);
             }
@@ -435,9 +450,9 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
 template <int NDIM, typename Real>
 constexpr int kMinBlocks = sizeof(Real) != 4 ? 1 : (NDIM <= 8 ? 3 : (NDIM <= 16 ? 2 : 1));
 
-template <int NDIM, typename Real, bool POW2>
-__global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, Real>))
-k_sample(const __grid_constant__ SampleArgs<Real> A)
+// One fused sampling pass (the kernel body, shared by every specialisation).
+template <int NDIM, typename Real, bool POW2, class I>
+__device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
 {
     using W = typename Word<Real>::type;
     unsigned long long start;
@@ -503,9 +518,9 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
         sobol_skip<NDIM, W>(X, q0, lane);
         const bool interior = (q0 * 32ull >= start) && (q1 * 32ull <= end);
         if (interior)
-            run_steps<NDIM, Real, POW2, false>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
+            run_steps<NDIM, Real, POW2, false, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
         else
-            run_steps<NDIM, Real, POW2, true>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
+            run_steps<NDIM, Real, POW2, true, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
     }
 
     // Reduction: warp, then across the block's warps in FP64.
@@ -536,6 +551,13 @@ k_sample(const __grid_constant__ SampleArgs<Real> A)
         const Real v = sm.h[d * kStride + p];
         if (v != Real(0)) atomicAdd(&A.H[idx], (double)v);
     }
+}
+
+template <int NDIM, typename Real, bool POW2>
+__global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, Real>))
+k_sample(const __grid_constant__ SampleArgs<Real> A)
+{
+    sample_pass<NDIM, Real, POW2, RuntimeIntegrand<Real>>(A);
 }
 
 // ------------------------------------------------------------ batched kernel
@@ -831,6 +853,7 @@ k_sobol(unsigned long long start, long long n, int shift, unsigned long long *Y)
 }
 
 // ------------------------------------------------------------ launchers
+#if !defined(__CUDACC_RTC__)
 template <int NDIM, typename Real>
 static void *sample_fn(bool pow2)
 {
@@ -935,6 +958,8 @@ cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
     k_sobol<NDIM, W><<<grid, kBlock, 0, s>>>(start, n, shift, Y);
     return cudaGetLastError();
 }
+
+#endif  // !__CUDACC_RTC__
 
 }  // namespace cv
 

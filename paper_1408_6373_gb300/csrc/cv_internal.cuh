@@ -2,8 +2,10 @@
 // the Vegas sampling library (not part of the public C ABI).
 #pragma once
 
+#if !defined(__CUDACC_RTC__)
 #include <cuda_runtime.h>
 #include <cstdint>
+#endif
 
 #include "../../include/cubagpu.h"
 
@@ -146,6 +148,7 @@ inline size_t batch_smem_bytes(int ndim, int stride) {
     return (size_t)(2 + kWarpsPerBlock) * ndim * stride * sizeof(float);
 }
 
+#if !defined(__CUDACC_RTC__)
 // ---- launchers (template definitions in cv_device.cuh, instantiated per
 // ---- dimension range in cv_sample_*.cu) ----
 template <int NDIM, typename Real>
@@ -184,6 +187,22 @@ cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream
                                  const int *list = nullptr);
 cudaError_t launch_gather_states(const BatchItem *items, const int *list, int count,
                                  DevState *out, cudaStream_t s);
+
+// cv_jit.cu: the sampling kernel specialised at run time for one integrand
+struct JitKernel {
+    cudaLibrary_t lib;
+    cudaKernel_t kernel;
+    int occ;                        // resident blocks per SM
+    size_t smem;
+};
+}  // namespace cv
+#include <string>
+namespace cv {
+int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks,
+                      JitKernel *out, std::string *err);
+cudaError_t launch_jit_sample(const JitKernel &k, const SampleArgs<float> &a, int grid, cudaStream_t s);
+int jit_info(int *compiled);
+#endif  // !__CUDACC_RTC__
 
 inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64) {
     // grid {e, w} pairs plus the block histogram, CV_MAX_BINS slots per axis

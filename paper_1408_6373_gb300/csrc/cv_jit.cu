@@ -1,0 +1,199 @@
+// cv_jit.cu -- runtime specialisation of the FP32 sampling kernel.
+//
+// The generic sampling kernel reads each component's family and parameters
+// from its launch parameters, so every point pays for a per-component
+// family dispatch and for parameter loads.  For one integral run many times
+// (a device-resident integral, a Vegas run of many iterations) the library
+// can instead compile, at run time with NVRTC, the same kernel body with an
+// integrand policy whose families and parameters are compile-time constants
+// (hexadecimal float literals, so the values are bit-identical): the
+// dispatch folds away and the parameters become instruction immediates.
+// The kernel source is the library's own device header, embedded at build
+// time.  NVRTC is loaded with dlopen; when it is missing or a compile
+// fails, callers fall back to the generic kernel.  Compiled kernels are
+// cached per device and source for the life of the process.
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "cv_internal.cuh"
+#include "cv_jit_sources.inc"  // generated: kJitHeaderNames[], kJitHeaderTexts[], kJitHeaderCount
+
+namespace cv {
+
+namespace {
+
+struct Nvrtc {
+    bool tried = false, ok = false;
+    nvrtcResult (*create)(nvrtcProgram *, const char *, const char *, int, const char *const *,
+                          const char *const *) = nullptr;
+    nvrtcResult (*compile)(nvrtcProgram, int, const char *const *) = nullptr;
+    nvrtcResult (*log_size)(nvrtcProgram, size_t *) = nullptr;
+    nvrtcResult (*log)(nvrtcProgram, char *) = nullptr;
+    nvrtcResult (*cubin_size)(nvrtcProgram, size_t *) = nullptr;
+    nvrtcResult (*cubin)(nvrtcProgram, char *) = nullptr;
+    nvrtcResult (*destroy)(nvrtcProgram *) = nullptr;
+};
+
+std::mutex g_mu;
+Nvrtc g_nvrtc;
+std::map<std::string, JitKernel> g_cache;  // key: device + source
+
+bool load_nvrtc(std::string *err)
+{
+    if (g_nvrtc.tried) return g_nvrtc.ok;
+    g_nvrtc.tried = true;
+    const char *names[] = {"libnvrtc.so.13", "libnvrtc.so"};
+    void *h = nullptr;
+    for (const char *n : names)
+        if ((h = dlopen(n, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) {
+        *err = "libnvrtc not found";
+        return false;
+    }
+#define CV_SYM(field, name)                                                          \
+    g_nvrtc.field = reinterpret_cast<decltype(g_nvrtc.field)>(dlsym(h, name));        \
+    if (!g_nvrtc.field) {                                                             \
+        *err = "libnvrtc lacks " name;                                                \
+        return false;                                                                 \
+    }
+    CV_SYM(create, "nvrtcCreateProgram")
+    CV_SYM(compile, "nvrtcCompileProgram")
+    CV_SYM(log_size, "nvrtcGetProgramLogSize")
+    CV_SYM(log, "nvrtcGetProgramLog")
+    CV_SYM(cubin_size, "nvrtcGetCUBINSize")
+    CV_SYM(cubin, "nvrtcGetCUBIN")
+    CV_SYM(destroy, "nvrtcDestroyProgram")
+#undef CV_SYM
+    g_nvrtc.ok = true;
+    return true;
+}
+
+void hexf(std::string &s, float v)
+{
+    char buf[64];
+    snprintf(buf, sizeof(buf), "%af", (double)v);
+    s += buf;
+}
+
+// Source of the specialised kernel for these parameters.
+std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks)
+{
+    const GenzParams<float> &g = a.g;
+    std::string s = "#include \"cv_device.cuh\"\nnamespace cv {\nstruct JitIntegrand {\n";
+    s += "  template <int C> __device__ __forceinline__ static constexpr int family(const GenzParams<float>&) { constexpr int f[4] = {";
+    for (int c = 0; c < 4; ++c) s += std::to_string(c < g.ncomp ? g.family[c] : CV_CONST) + (c < 3 ? "," : "");
+    s += "}; return f[C]; }\n";
+    s += "  __device__ __forceinline__ static constexpr int ncomp(const GenzParams<float>&) { return " +
+         std::to_string(g.ncomp) + "; }\n";
+    const float(*tabs[2])[CV_MAX_DIM] = {g.p0, g.p1};
+    const char *names[2] = {"p0", "p1"};
+    for (int t = 0; t < 2; ++t) {
+        s += "  template <int C> __device__ __forceinline__ static float ";
+        s += names[t];
+        s += "(const GenzParams<float>&, int d) { constexpr float v[4][" + std::to_string(ndim) + "] = {";
+        for (int c = 0; c < 4; ++c) {
+            s += "{";
+            for (int d = 0; d < ndim; ++d) {
+                hexf(s, c < g.ncomp ? tabs[t][c][d] : 0.0f);
+                if (d + 1 < ndim) s += ",";
+            }
+            s += c < 3 ? "}," : "}";
+        }
+        s += "}; return v[C][d]; }\n";
+    }
+    s += "  template <int C> __device__ __forceinline__ static float q0(const GenzParams<float>&) { constexpr float v[4] = {";
+    for (int c = 0; c < 4; ++c) {
+        hexf(s, c < g.ncomp ? g.q0[c] : 0.0f);
+        if (c < 3) s += ",";
+    }
+    s += "}; return v[C]; }\n};\n}\n";
+    s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(kBlock) + ", " +
+         std::to_string(min_blocks) + ") cv_jit_sample(const __grid_constant__ cv::SampleArgs<float> A)\n{\n";
+    s += "    cv::sample_pass<" + std::to_string(ndim) + ", float, " + (pow2 ? "true" : "false") +
+         ", cv::JitIntegrand>(A);\n}\n";
+    return s;
+}
+
+}  // namespace
+
+int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks,
+                      JitKernel *out, std::string *err)
+{
+    const std::string src = specialised_source(a, ndim, pow2, min_blocks);
+    const std::string key = std::to_string(device) + "\n" + src;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        *out = it->second;
+        return 0;
+    }
+    if (!load_nvrtc(err)) return -1;
+    nvrtcProgram prog;
+    if (g_nvrtc.create(&prog, src.c_str(), "cv_jit_sample.cu", kJitHeaderCount, kJitHeaderTexts,
+                       kJitHeaderNames) != NVRTC_SUCCESS) {
+        *err = "nvrtcCreateProgram failed";
+        return -1;
+    }
+    // (-default-device: the C ABI prototypes in the embedded header are then
+    // unused device declarations instead of host functions NVRTC rejects)
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
+    const nvrtcResult rc = g_nvrtc.compile(prog, 3, opts);
+    if (rc != NVRTC_SUCCESS) {
+        size_t n = 0;
+        g_nvrtc.log_size(prog, &n);
+        std::string log(n, '\0');
+        if (n) g_nvrtc.log(prog, &log[0]);
+        *err = "NVRTC compile failed: " + log.substr(0, 400);
+        g_nvrtc.destroy(&prog);
+        return -1;
+    }
+    size_t n = 0;
+    g_nvrtc.cubin_size(prog, &n);
+    std::vector<char> cubin(n);
+    g_nvrtc.cubin(prog, cubin.data());
+    g_nvrtc.destroy(&prog);
+    JitKernel k;
+    if (cudaLibraryLoadData(&k.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
+        cudaLibraryGetKernel(&k.kernel, k.lib, "cv_jit_sample") != cudaSuccess) {
+        cudaGetLastError();
+        *err = "loading the specialised kernel failed";
+        return -1;
+    }
+    k.smem = sample_smem_bytes(ndim, CV_MAX_BINS, false);
+    if (cudaFuncSetAttribute((const void *)k.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)k.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k.occ, (const void *)k.kernel, kBlock, k.smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        *err = "configuring the specialised kernel failed";
+        return -1;
+    }
+    if (k.occ < 1) k.occ = 1;
+    g_cache[key] = k;
+    *out = k;
+    return 0;
+}
+
+int jit_info(int *compiled)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    std::string err;
+    const bool ok = load_nvrtc(&err);
+    *compiled = (int)g_cache.size();
+    return ok ? 1 : 0;
+}
+
+cudaError_t launch_jit_sample(const JitKernel &k, const SampleArgs<float> &a, int grid, cudaStream_t s)
+{
+    void *args[1] = {const_cast<SampleArgs<float> *>(&a)};
+    return cudaLaunchKernel((const void *)k.kernel, dim3(grid), dim3(kBlock), args, k.smem, s);
+}
+
+}  // namespace cv

@@ -344,3 +344,38 @@ def test_context_release_outlives_integral_handles():
     c.close()
     I1.close()
     I2.close()
+
+
+# ------------------------------------------------------------------ run-time specialisation
+def test_jit_specialised_kernel_matches_generic(ctx):
+    ndim, N = 8, 128
+    a, u = _params(ndim, 4, 33)
+    fams = [O.OSCILLATORY, O.PRODUCT_PEAK, O.CORNER_PEAK, O.GAUSSIAN]
+    g = cg.genz(ndim, fams, a, u)
+    edges = _random_grid(ndim, N, 3)
+    gen = _gpu_sample(ctx, g, edges, 1, 300000, 0)
+    jit = _gpu_sample(ctx, g, edges, 1, 300000, cg.JIT)
+    available, compiled = cg.jit_info()
+    assert available and compiled >= 1
+    for c in range(4):
+        assert jit[0][c] == pytest.approx(gen[0][c], rel=1e-6, abs=1e-6 * math.sqrt(300000 * gen[1][c]))
+        assert jit[1][c] == pytest.approx(gen[1][c], rel=1e-6)
+    np.testing.assert_allclose(jit[2], gen[2], rtol=1e-5, atol=1e-5 * gen[2].max())
+    # and against the oracle on the same grid
+    p = O.Problem(ndim, fams, a, u, nbins=N, bits=23, fp32_decide=True)
+    oS1, oS2, _ = O.sample(p, edges, 1, 300000, nthreads=8)
+    for c in range(4):
+        assert abs(jit[0][c] - oS1[c]) <= 1e-6 * math.sqrt(300000 * oS2[c])
+
+
+@pytest.mark.parametrize("ndim,fams,nbins", [(3, [O.DISCONTINUOUS], 50), (12, [O.C0, O.GAUSSIAN], 64),
+                                             (1, [O.CORNER_PEAK], 32)])
+def test_jit_vegas_runs_match_generic(ctx, ndim, fams, nbins):
+    a, u = _params(ndim, len(fams), ndim)
+    g = cg.genz(ndim, fams, a, u)
+    kw = dict(maxeval=6 * 20000, nstart=20000, nbins=nbins)
+    r0 = ctx.vegas(g, flags=0, **kw)
+    r1 = ctx.vegas(g, flags=cg.JIT, **kw)
+    assert r0.neval == r1.neval
+    for c in range(len(fams)):
+        assert abs(r1.integral[c] - r0.integral[c]) <= 2e-5 * abs(r0.integral[c]) + 1e-2 * r0.error[c]
