@@ -277,15 +277,8 @@ static MapParams make_map(int N)
         m.mF = 0x7fffffu & ~((1u << L) - 1u);
         m.expL = (unsigned)(127 - L) << 23;
         m.twoNegL = ldexpf(1.0f, -L);
-        if (L >= 5) {
-            m.sA = 27 - L;
-            m.mA = ((1u << (L - 5)) - 1u) << 5;
-            m.sB = 27;
-        } else {
-            m.sA = 0;
-            m.mA = 0;
-            m.sB = 32 - L;
-        }
+        m.li = L >= 6 ? L - 5 : 0;
+        m.sK = 32 - L;
     }
     return m;
 }

@@ -28,14 +28,18 @@ namespace cv {
 
 // Direction words in constant memory (every access below is warp-uniform).
 static __constant__ unsigned long long c_V64[CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_V64_INIT;
-static __constant__ unsigned int c_V32[CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_V32_INIT;
+// Top 32 bits of the words; table li > 0 has the top 5 + li bits rotated
+// left by 5 (the bin-slot layout of N = 2^(5 + li), see the maps below).
+// A bit permutation commutes with XOR, so a point's rotated word is the
+// rotation of its word.
+static __constant__ unsigned int c_V32R[4][CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_V32R_INIT;
 
 template <typename W> struct Dir;
 template <> struct Dir<unsigned long long> {
-    static __device__ __forceinline__ unsigned long long v(int d, int k) { return c_V64[d][k]; }
+    static __device__ __forceinline__ unsigned long long v(int, int d, int k) { return c_V64[d][k]; }
 };
 template <> struct Dir<unsigned int> {
-    static __device__ __forceinline__ unsigned int v(int d, int k) { return c_V32[d][k]; }
+    static __device__ __forceinline__ unsigned int v(int li, int d, int k) { return c_V32R[li][d][k]; }
 };
 
 // Sobol words of index i = 32 q + lane for every dimension (skip-ahead):
@@ -43,7 +47,7 @@ template <> struct Dir<unsigned int> {
 // bits of g above bit 4 are g(q) and the same for the whole warp; bits 0-4
 // depend on the lane.
 template <int NDIM, typename W>
-__device__ __forceinline__ void sobol_skip(W (&X)[NDIM], unsigned long long q, int lane)
+__device__ __forceinline__ void sobol_skip(W (&X)[NDIM], unsigned long long q, int lane, int li = 0)
 {
     const unsigned long long i = q * 32ull + (unsigned long long)lane;
     const unsigned long long g = i ^ (i >> 1);
@@ -54,14 +58,14 @@ __device__ __forceinline__ void sobol_skip(W (&X)[NDIM], unsigned long long q, i
         W x = 0;
 #pragma unroll
         for (int k = 0; k < 5; ++k)
-            x ^= ((glo >> k) & 1u) ? Dir<W>::v(d, k) : W(0);
+            x ^= ((glo >> k) & 1u) ? Dir<W>::v(li, d, k) : W(0);
         X[d] = x;
     }
     while (ghi) {  // warp-uniform
         const int k = __ffsll((long long)ghi) - 1 + 5;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d)
-            X[d] ^= Dir<W>::v(d, k);
+            X[d] ^= Dir<W>::v(li, d, k);
         ghi &= ghi - 1;
     }
 }
@@ -69,12 +73,12 @@ __device__ __forceinline__ void sobol_skip(W (&X)[NDIM], unsigned long long q, i
 // Advance every lane from block q to block q+1:
 // g(32(q+1)+l) ^ g(32q+l) = 2^4 ^ 2^(5 + ctz(q+1)).
 template <int NDIM, typename W>
-__device__ __forceinline__ void sobol_step(W (&X)[NDIM], unsigned long long q)
+__device__ __forceinline__ void sobol_step(W (&X)[NDIM], unsigned long long q, int li = 0)
 {
     const int c = __ffsll((long long)(q + 1ull)) - 1;
 #pragma unroll
     for (int d = 0; d < NDIM; ++d)
-        X[d] ^= Dir<W>::v(d, 4) ^ Dir<W>::v(d, 5 + c);
+        X[d] ^= Dir<W>::v(li, d, 4) ^ Dir<W>::v(li, d, 5 + c);
 }
 
 // ------------------------------------------------------------ maps
@@ -334,9 +338,10 @@ __device__ __forceinline__ float map_f32(unsigned X, int d, int N, const MapPara
                                          const Smem<float> &sm, float &J, int &slot)
 {
     if (POW2) {
+        // X is the rotated word (table m.li): its top L bits are the slot
         const unsigned fb = (X >> m.sF) & m.mF;
         const float fs = __uint_as_float(m.expL | fb) - m.twoNegL;
-        const int p = (int)(((X >> m.sA) & m.mA) | (X >> m.sB));
+        const int p = (int)(X >> m.sK);
         const float w = sm.w[d * sm.stride + p];
         J *= w;
         slot = p;
@@ -399,6 +404,7 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
                                           Acc<Real> (&s2)[CV_MAX_COMP])
 {
     const int N = A.nbins;
+    const int li = (sizeof(Real) == 4 && POW2) ? A.map.li : 0;  // direction table
     for (unsigned r0 = 0; r0 < nsteps; r0 += kRun) {
         const unsigned r1 = min(r0 + kRun, nsteps);
         Real p1[CV_MAX_COMP], p2[CV_MAX_COMP];
@@ -431,7 +437,7 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
 #pragma unroll
                 for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * sm.stride + slot[d]], h);
             }
-            if (st + 1 < nsteps) sobol_step<NDIM, typename Word<Real>::type>(X, q);
+            if (st + 1 < nsteps) sobol_step<NDIM, typename Word<Real>::type>(X, q, li);
         }
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c) {
@@ -515,7 +521,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         const unsigned long long q0 = qa + ch * plen;
         const unsigned long long q1 = min(q0 + plen, qb);
         W X[NDIM];
-        sobol_skip<NDIM, W>(X, q0, lane);
+        sobol_skip<NDIM, W>(X, q0, lane, (sizeof(Real) == 4 && POW2) ? A.map.li : 0);
         const bool interior = (q0 * 32ull >= start) && (q1 * 32ull <= end);
         if (interior)
             run_steps<NDIM, Real, POW2, false, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
@@ -628,7 +634,7 @@ k_batch_sample(const BatchSampleArgs B)
             Smem<float> smw = sm;
             smw.h = hist + warp * hsize;
             unsigned X[NDIM];
-            sobol_skip<NDIM, unsigned>(X, w0, lane);
+            sobol_skip<NDIM, unsigned>(X, w0, lane, POW2 ? A.map.li : 0);
             const bool interior = (w0 * 32ull >= start) && (w1 * 32ull <= end);
             if (interior)
                 run_steps<NDIM, float, POW2, false>(A, smw, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);

@@ -67,7 +67,8 @@ struct MapParams {
     unsigned sF, mF;                // mantissa bits of frac: (X >> sF) & mF
     unsigned expL;                  // exponent field of 2^-L
     float twoNegL;                  // 2^-L
-    unsigned sA, mA, sB;            // slot = ((X >> sA) & mA) | (X >> sB)
+    int li;                         // direction table: top L bits rotated by 5 (L >= 6)
+    unsigned sK;                    // slot = rotated word >> sK, sK = 32 - L
 };
 
 // Arguments of one sampling launch.  When `st` is non-null the launch reads
