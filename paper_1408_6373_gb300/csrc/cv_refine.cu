@@ -67,8 +67,11 @@ __device__ __forceinline__ double warp_max_d(double v)
     return v;
 }
 
-// Refine axis `d` of the grid in place (one CTA of 256 threads, N <= 256).
-// Every reduction has a fixed order, so the result is reproducible.
+// Refine axis `d` of the grid in place (one CTA of at least N threads, at
+// most 256).  Every reduction has a fixed order, so the result is
+// reproducible.  GB300 issues FP64 at a small fraction of the FP32 rate, so
+// the CTA is sized to the bins: idle warps would still spend FP64 issue
+// slots on the reductions.
 __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_hist)
 {
     double *Hd = H + (size_t)d * N;
@@ -78,6 +81,7 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
     __shared__ double wred[8];
     const int k = threadIdx.x;            // bin of this thread
     const int lane = k & 31, warp = k >> 5;
+    const int nw = blockDim.x >> 5;
 
     if (k < N) sH[k] = Hd[k];
     for (int i = k; i <= N; i += blockDim.x) se[i] = e[i];
@@ -99,7 +103,7 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
         if (lane == 0) wred[warp] = ws;
         __syncthreads();
         double s = 0.0;
-        for (int w = 0; w < 8; ++w) s = __dadd_rn(s, wred[w]);
+        for (int w = 0; w < nw; ++w) s = __dadd_rn(s, wred[w]);
         __syncthreads();
         // compression
         double r = 0.0;
@@ -115,7 +119,7 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
         if (lane == 0) wred[warp] = wm;
         __syncthreads();
         double rmax = 0.0;
-        for (int w = 0; w < 8; ++w) rmax = fmax(rmax, wred[w]);
+        for (int w = 0; w < nw; ++w) rmax = fmax(rmax, wred[w]);
         __syncthreads();
         if (rmax > 0.0) {
             r = __ddiv_rn(r, rmax);
@@ -354,16 +358,20 @@ cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int n
     return cudaGetLastError();
 }
 
+// Threads of a refinement CTA: the bins rounded up to whole warps, at least
+// two warps (the combination CTA of k_refine_combine needs one).
+static int refine_threads(int nbins) { return nbins <= 64 ? 64 : (nbins + 31) / 32 * 32; }
+
 cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, cudaStream_t s)
 {
-    k_refine<<<ndim, 256, 0, s>>>(nbins, H, edges);
+    k_refine<<<ndim, refine_threads(nbins), 0, s>>>(nbins, H, edges);
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
                                   const CombineArgs &a, cudaStream_t s)
 {
-    k_refine_combine<<<ndim + 1, 256, 0, s>>>(ndim, nbins, H, edges, a);
+    k_refine_combine<<<ndim + 1, refine_threads(nbins), 0, s>>>(ndim, nbins, H, edges, a);
     return cudaGetLastError();
 }
 
