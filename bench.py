@@ -142,6 +142,18 @@ def _gpu_uuid(idx: int):
 
 
 # ------------------------------------------------------------------ helpers
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest value of x over all ranks (the slowest rank's time); the
+    value itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -291,12 +303,7 @@ def run_ours(args):
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    dev_ms = sum(s.elapsed_time(e) for s, e in events)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = t.item()
+    dev_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in events), device="cuda")
     res = integ.result()
     value = world * samples_per_step * args.steps / (dev_ms / 1e3)
     launches = integ.kernels_per_run() * args.steps

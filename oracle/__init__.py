@@ -78,12 +78,8 @@ _int = ctypes.c_int
 _vp = ctypes.c_void_p
 
 
-def _load():
-    global _lib
-    with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
-            sig = {
+def _bind(lib):
+    sig = {
                 "or_sobol_directions": (_int, [_int, _vp, _vp, _int, _vp]),
                 "or_sobol_word": (None, [_int, _vp, _u64, _vp]),
                 "or_sobol_coords": (_int, [_int, _vp, _u64, _i64, _int, _vp]),
@@ -101,13 +97,56 @@ def _load():
                 "or_vegas": (_int, [_P(_Problem), _vp, _d, _d, _i64, _i64, _i64,
                                     _i64, _int, _vp, _P(_i64), _P(_int), _P(_int),
                                     _vp, _vp, _vp, _vp, _int, _vp, _vp]),
-            }
-            for name, (res, args) in sig.items():
-                fn = getattr(lib, name)
-                fn.restype = res
-                fn.argtypes = args
-            _lib = lib
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def compile_variant(source_text: str, path: str) -> str:
+    """Compile another version of the oracle's C source (the tests plant
+    mistakes in copies to show that the pins catch them)."""
+    src = path + ".c"
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", "-o", path, src, "-lm", "-lpthread"])
+    return path
+
+
+class use_library:
+    """Context manager: route every oracle call to the library at `path`."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        with _lock:
+            self._saved = _lib
+            _lib = _bind(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self._saved
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _ptr(a: np.ndarray):
