@@ -68,10 +68,14 @@ static cudaError_t dispatch_sobol(int ndim, unsigned long long start, long long 
 
 using namespace cv;
 
+constexpr int kSideStreams = 8;  // concurrent per-class launches of a batched iteration
+
 struct cv_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // graph capture happens here
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kSideStreams] = {};
     bool own_stream = false;
     int sms = 0;
     char msg[512] = {0};
@@ -157,6 +161,15 @@ extern "C" int cv_create(cv_ctx **out, int device, void *stream)
         return CV_ECUDA;
     }
     ctx->occ.assign(2 * (CV_MAX_DIM + 1) * (CV_MAX_BINS + 1), 0);
+    bool ok = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kSideStreams && ok; ++k)
+        ok = cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cv_destroy(ctx);
+        return CV_ECUDA;
+    }
     *out = ctx;
     return CV_OK;
 }
@@ -173,6 +186,11 @@ extern "C" void cv_destroy(cv_ctx *ctx)
     for (struct cv_server *S : ctx->servers) server_release(S);
     ctx->servers.clear();
     cudaStreamDestroy(ctx->cap_stream);
+    for (int k = 0; k < kSideStreams; ++k) {
+        if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+        if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -877,6 +895,10 @@ static int batch_enqueue(cv_batch *B, cudaStream_t s, int first_iteration_sampli
     size_t p = 0;
     const int J = first_iteration_sampling_only ? 1 : B->J;
     for (int j = 0; j < J; ++j) {
+        // the classes of an iteration run concurrently on side streams
+        CV_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+        for (int k = 0; k < kSideStreams; ++k) CV_CUDA(ctx, cudaStreamWaitEvent(ctx->side[k], ctx->ev_fork, 0));
+        int used = 0;
         for (; p < B->plan.size() && B->plan[p].j == j; ++p) {
             const cv_batch::Launch &L = B->plan[p];
             const cv_batch::Class &C = B->classes[L.cls];
@@ -887,8 +909,13 @@ static int batch_enqueue(cv_batch *B, cudaStream_t s, int first_iteration_sampli
             a.stride = C.stride;
             a.counter = B->d_counters + L.counter;
             const int grid = C.grid < L.ntiles ? C.grid : L.ntiles;
-            CV_CUDA(ctx, dispatch_batch_sample(C.ndim, C.pow2, a, grid, s));
+            CV_CUDA(ctx, dispatch_batch_sample(C.ndim, C.pow2, a, grid, ctx->side[used % kSideStreams]));
+            ++used;
             ++kernels;
+        }
+        for (int k = 0; k < kSideStreams; ++k) {
+            CV_CUDA(ctx, cudaEventRecord(ctx->ev_join[k], ctx->side[k]));
+            CV_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join[k], 0));
         }
         if (first_iteration_sampling_only) break;
         CV_CUDA(ctx, launch_batch_refine(B->d_items, B->d_axes, B->naxes, s));
@@ -1277,6 +1304,8 @@ struct cv_server {
     Clock::time_point t_start;
     // device resources (worker thread only)
     cudaStream_t stream = nullptr;
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kSideStreams] = {};
     void *arena_mem = nullptr;
     BatchItem *d_items = nullptr;
     CombineArgs *d_cargs = nullptr;
@@ -1407,8 +1436,24 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
     CV_CUDA(ctx, cudaMemcpyAsync(S->d_axes, axes.data(), axes.size() * sizeof(int2), cudaMemcpyHostToDevice, S->stream));
     CV_CUDA(ctx, cudaMemsetAsync(S->d_counters, 0, 2 * (CV_MAX_DIM + 1) * sizeof(int), S->stream));
     CV_CUDA(ctx, launch_batch_reset(S->d_items, S->d_cargs, nfresh, S->stream, S->d_lists));
-    size_t off = 0;
-    for (const Cls &c : cls) {
+    // classes run concurrently on side streams, the largest first
+    std::vector<int> order(cls.size());
+    for (size_t i = 0; i < cls.size(); ++i) order[i] = (int)i;
+    std::vector<size_t> offs(cls.size());
+    {
+        size_t o = 0;
+        for (size_t i = 0; i < cls.size(); ++i) {
+            offs[i] = o;
+            o += cls[i].tiles.size();
+        }
+    }
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cls[x].tiles.size() > cls[y].tiles.size(); });
+    CV_CUDA(ctx, cudaEventRecord(S->ev_fork, S->stream));
+    for (int k = 0; k < kSideStreams; ++k) CV_CUDA(ctx, cudaStreamWaitEvent(S->side[k], S->ev_fork, 0));
+    int used = 0;
+    for (int ci : order) {
+        const Cls &c = cls[ci];
+        const size_t off = offs[ci];
         int &g = S->class_grid[((c.pow2 ? 1 : 0) * (CV_MAX_DIM + 1) + c.ndim) * (CV_MAX_BINS + 1) + c.stride];
         if (!g) {
             int occ = 0;
@@ -1421,8 +1466,13 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         a.ntiles = (int)c.tiles.size();
         a.stride = c.stride;
         a.counter = S->d_counters + (c.pow2 ? 1 : 0) * (CV_MAX_DIM + 1) + c.ndim;
-        CV_CUDA(ctx, dispatch_batch_sample(c.ndim, c.pow2, a, std::min<int>(g, a.ntiles), S->stream));
-        off += c.tiles.size();
+        CV_CUDA(ctx, dispatch_batch_sample(c.ndim, c.pow2, a, std::min<int>(g, a.ntiles),
+                                           S->side[used % kSideStreams]));
+        ++used;
+    }
+    for (int k = 0; k < kSideStreams; ++k) {
+        CV_CUDA(ctx, cudaEventRecord(S->ev_join[k], S->side[k]));
+        CV_CUDA(ctx, cudaStreamWaitEvent(S->stream, S->ev_join[k], 0));
     }
     CV_CUDA(ctx, launch_batch_refine(S->d_items, S->d_axes, (int)axes.size(), S->stream));
     CV_CUDA(ctx, launch_batch_combine(S->d_cargs, nlive, S->stream, S->d_lists + nfresh));
@@ -1514,6 +1564,11 @@ extern "C" int cv_server_start(cv_ctx *ctx, const cv_server_opts *opts, cv_serve
     const int L = S->opts.max_live;
     S->class_grid.assign(2 * (CV_MAX_DIM + 1) * (CV_MAX_BINS + 1), 0);
     cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming);
+    for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&S->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_join[k], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&S->arena_mem, (size_t)S->opts.hbm_budget_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&S->d_items, (size_t)L * sizeof(BatchItem));
     if (e == cudaSuccess) e = cudaMalloc(&S->d_cargs, (size_t)L * sizeof(CombineArgs));
@@ -1646,6 +1701,11 @@ static void server_release(cv_server *S)
     if (S->d_tiles) cudaFree(S->d_tiles);
     if (S->h_gather) cudaFreeHost(S->h_gather);
     if (S->stream) cudaStreamDestroy(S->stream);
+    for (int k = 0; k < kSideStreams; ++k) {
+        if (S->side[k]) cudaStreamDestroy(S->side[k]);
+        if (S->ev_join[k]) cudaEventDestroy(S->ev_join[k]);
+    }
+    if (S->ev_fork) cudaEventDestroy(S->ev_fork);
     delete S;
 }
 
