@@ -75,7 +75,9 @@ __device__ __forceinline__ void sobol_skip(W (&X)[NDIM], unsigned long long q, i
 template <int NDIM, typename W>
 __device__ __forceinline__ void sobol_step(W (&X)[NDIM], unsigned long long q, int li = 0)
 {
-    const int c = __ffsll((long long)(q + 1ull)) - 1;
+    // (c <= 46 for every q + 1 < 2^47; clamped so that a step past the last
+    // block of the index range stays inside the table)
+    const int c = min(__ffsll((long long)(q + 1ull)) - 1, CV_SOBOL_BITS - 6);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d)
         X[d] ^= Dir<W>::v(li, d, 4) ^ Dir<W>::v(li, d, 5 + c);
@@ -144,6 +146,7 @@ struct RuntimeIntegrand {
     template <int C> __device__ __forceinline__ static Real p0(const GenzParams<Real> &g, int d) { return g.p0[C][d]; }
     template <int C> __device__ __forceinline__ static Real p1(const GenzParams<Real> &g, int d) { return g.p1[C][d]; }
     template <int C> __device__ __forceinline__ static Real q0(const GenzParams<Real> &g) { return g.q0[C]; }
+    __device__ __forceinline__ static int table(const MapParams &m) { return m.li; }
 };
 
 // FP32 Genz evaluation of component C.
@@ -404,7 +407,7 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
                                           Acc<Real> (&s2)[CV_MAX_COMP])
 {
     const int N = A.nbins;
-    const int li = (sizeof(Real) == 4 && POW2) ? A.map.li : 0;  // direction table
+    const int li = (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0;  // direction table
     for (unsigned r0 = 0; r0 < nsteps; r0 += kRun) {
         const unsigned r1 = min(r0 + kRun, nsteps);
         Real p1[CV_MAX_COMP], p2[CV_MAX_COMP];
@@ -437,7 +440,7 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
 #pragma unroll
                 for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * sm.stride + slot[d]], h);
             }
-            if (st + 1 < nsteps) sobol_step<NDIM, typename Word<Real>::type>(X, q, li);
+            sobol_step<NDIM, typename Word<Real>::type>(X, q, li);
         }
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c) {
@@ -521,7 +524,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         const unsigned long long q0 = qa + ch * plen;
         const unsigned long long q1 = min(q0 + plen, qb);
         W X[NDIM];
-        sobol_skip<NDIM, W>(X, q0, lane, (sizeof(Real) == 4 && POW2) ? A.map.li : 0);
+        sobol_skip<NDIM, W>(X, q0, lane, (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0);
         const bool interior = (q0 * 32ull >= start) && (q1 * 32ull <= end);
         if (interior)
             run_steps<NDIM, Real, POW2, false, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);

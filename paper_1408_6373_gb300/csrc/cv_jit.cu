@@ -113,7 +113,10 @@ std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, 
         hexf(s, c < g.ncomp ? g.q0[c] : 0.0f);
         if (c < 3) s += ",";
     }
-    s += "}; return v[C]; }\n};\n}\n";
+    s += "}; return v[C]; }\n";
+    s += "  __device__ __forceinline__ static constexpr int table(const MapParams&) { return " +
+         std::to_string(pow2 ? a.map.li : 0) + "; }\n";
+    s += "};\n}\n";
     s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(kBlock) + ", " +
          std::to_string(min_blocks) + ") cv_jit_sample(const __grid_constant__ cv::SampleArgs<float> A)\n{\n";
     s += "    cv::sample_pass<" + std::to_string(ndim) + ", float, " + (pow2 ? "true" : "false") +
