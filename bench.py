@@ -174,10 +174,10 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _profile_traffic():
+def _profile_traffic(name: str):
     """DRAM bytes per launch of the sampling kernel from the committed ncu
-    summary, if it was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "k_sample_genz8d4c.md")
+    summary `name`, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         text = open(path).read()
     except OSError:
@@ -335,7 +335,8 @@ def run_ours(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(sm_max)
-    traffic = _profile_traffic()
+    traffic = _profile_traffic("sampling_specialised_genz8d4c.md" if jit_compiled
+                               else "k_sample_generic_genz8d4c.md")
 
     # ---- end to end through cv_vegas (host description in, host results out)
     h2d, d2h = cg.vegas_io_bytes(p.ndim, p.nbins)
