@@ -295,6 +295,21 @@ int cv_integral_grid(cv_integral *I, double *edges);
 int cv_integral_log(cv_integral *I, int max_iter, double *iter_I, double *iter_var);
 /* Kernels one reset + run enqueues when it runs to the sample budget. */
 int cv_integral_kernels_per_run(const cv_integral *I);
+/* Enqueue at most max_iter more iterations (fewer if the run stops). */
+int cv_integral_step(cv_integral *I, int max_iter);
+/* Checkpoint and resume -- the statefile of the Vegas prototype
+ * (Sect. 3.2.2): save writes the device state, grid, histogram and
+ * iteration log of I to `path` (synchronising first); load restores such
+ * a file into an integral of the same problem (same dimensions, bins,
+ * integrand, goals, schedule and precision flags; otherwise CV_EINVAL), after
+ * which cv_integral_step / cv_integral_run continue exactly where the saved
+ * run stopped, Sobol index included. */
+int cv_integral_save(cv_integral *I, const char *path);
+int cv_integral_load(cv_integral *I, const char *path);
+/* Grid reuse (the role of Vegas's gridno): replace the grid of I, after a
+ * reset, with edges[ndim][nbins+1] (increasing from 0 to 1), e.g. the
+ * refined grid of an earlier integral from cv_integral_grid. */
+int cv_integral_set_grid(cv_integral *I, const double *edges);
 /* Release an integral; a no-op on a handle its context already released. */
 void cv_integral_destroy(cv_integral *I);
 

@@ -168,6 +168,10 @@ _SIGNATURES = {
     "cv_integral_log": (_i, [_vp, _i, _vp, _vp]),
     "cv_integral_kernels_per_run": (_i, [_vp]),
     "cv_integral_destroy": (None, [_vp]),
+    "cv_integral_step": (_i, [_vp, _i]),
+    "cv_integral_save": (_i, [_vp, ctypes.c_char_p]),
+    "cv_integral_load": (_i, [_vp, ctypes.c_char_p]),
+    "cv_integral_set_grid": (_i, [_vp, _vp]),
     "cv_batch_create": (_i, [_vp, _i, _vp, _P(_vp)]),
     "cv_batch_run": (_i, [_vp]),
     "cv_batch_results": (_i, [_vp, _vp]),
@@ -429,6 +433,19 @@ class Integral:
 
     def kernels_per_run(self) -> int:
         return self.ctx._lib.cv_integral_kernels_per_run(self._h)
+
+    def step(self, max_iter: int):
+        self.ctx._check(self.ctx._lib.cv_integral_step(self._h, max_iter), "cv_integral_step")
+
+    def save(self, path: str):
+        self.ctx._check(self.ctx._lib.cv_integral_save(self._h, os.fsencode(path)), "cv_integral_save")
+
+    def load(self, path: str):
+        self.ctx._check(self.ctx._lib.cv_integral_load(self._h, os.fsencode(path)), "cv_integral_load")
+
+    def set_grid(self, edges: np.ndarray):
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        self.ctx._check(self.ctx._lib.cv_integral_set_grid(self._h, e.ctypes.data), "cv_integral_set_grid")
 
 
 class Batch:

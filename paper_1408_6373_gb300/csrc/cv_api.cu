@@ -670,6 +670,149 @@ extern "C" int cv_integral_log(cv_integral *I, int max_iter, double *iter_I, dou
     return CV_OK;
 }
 
+// ---- checkpoint / resume and grid reuse
+extern "C" int cv_integral_step(cv_integral *I, int max_iter)
+{
+    if (!I || max_iter < 0) return CV_EINVAL;
+    cv_ctx *ctx = I->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    if ((I->spec.flags & CV_JIT) && !(I->spec.flags & CV_FP64)) {
+        // compile (if needed) before the first launch
+        SampleArgs<float> a;
+        memset(&a, 0, sizeof(a));
+        fill_params<float>(&I->spec.g, &a.g);
+        a.nbins = I->spec.nbins;
+        a.map = make_map(I->spec.nbins);
+        JitKernel k;
+        std::string err;
+        jit_sample_kernel(ctx->device, a, I->spec.g.ndim, a.map.pow2 != 0, min_blocks_f32(I->spec.g.ndim), &k, &err);
+    }
+    // iterations past the device's stop decision return at once
+    for (int j = 0; j < max_iter; ++j) {
+        int rc = enqueue_iteration(I, ctx->stream);
+        if (rc) return rc;
+    }
+    return CV_OK;
+}
+
+namespace {
+struct StateFileHeader {
+    char magic[8];                 // "CUBAGPU\0"
+    unsigned version;              // 1
+    unsigned state_bytes;          // sizeof(DevState)
+    int ndim, ncomp, nbins, flags;
+    int family[CV_MAX_COMP];
+    double a[CV_MAX_COMP][CV_MAX_DIM], u[CV_MAX_COMP][CV_MAX_DIM];
+    double epsrel, epsabs;
+    long long mineval, maxeval, nstart, nincrease;
+};
+
+void fill_header(const cv_spec &sp, StateFileHeader *h)
+{
+    memset(h, 0, sizeof(*h));
+    memcpy(h->magic, "CUBAGPU", 8);
+    h->version = 1;
+    h->state_bytes = (unsigned)sizeof(DevState);
+    h->ndim = sp.g.ndim;
+    h->ncomp = sp.g.ncomp;
+    h->nbins = sp.nbins;
+    h->flags = sp.flags & (CV_FP64 | CV_JIT);
+    for (int c = 0; c < sp.g.ncomp; ++c) {
+        h->family[c] = sp.g.family[c];
+        for (int d = 0; d < sp.g.ndim; ++d) {
+            h->a[c][d] = sp.g.a[c][d];
+            h->u[c][d] = sp.g.u[c][d];
+        }
+    }
+    h->epsrel = sp.epsrel;
+    h->epsabs = sp.epsabs;
+    h->mineval = sp.mineval;
+    h->maxeval = sp.maxeval;
+    h->nstart = sp.nstart;
+    h->nincrease = sp.nincrease;
+}
+}  // namespace
+
+extern "C" int cv_integral_save(cv_integral *I, const char *path)
+{
+    if (!I || !path) return CV_EINVAL;
+    cv_ctx *ctx = I->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int ndim = I->spec.g.ndim, N = I->spec.nbins;
+    std::vector<char> st(sizeof(DevState));
+    std::vector<double> e((size_t)ndim * (N + 1)), H((size_t)ndim * N);
+    std::vector<double> lI((size_t)kLogCap * CV_MAX_COMP), lV((size_t)kLogCap * CV_MAX_COMP);
+    CV_CUDA(ctx, cudaMemcpyAsync(st.data(), I->st, st.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(e.data(), I->edges, e.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(H.data(), I->H, H.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(lI.data(), I->log_I, lI.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(lV.data(), I->log_var, lV.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    StateFileHeader h;
+    fill_header(I->spec, &h);
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail_msg(ctx, CV_EINVAL, "cannot open %s for writing", path);
+    bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(st.data(), st.size(), 1, f) == 1 &&
+              fwrite(e.data(), sizeof(double), e.size(), f) == e.size() &&
+              fwrite(H.data(), sizeof(double), H.size(), f) == H.size() &&
+              fwrite(lI.data(), sizeof(double), lI.size(), f) == lI.size() &&
+              fwrite(lV.data(), sizeof(double), lV.size(), f) == lV.size();
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail_msg(ctx, CV_EINVAL, "writing %s failed", path);
+    return CV_OK;
+}
+
+extern "C" int cv_integral_load(cv_integral *I, const char *path)
+{
+    if (!I || !path) return CV_EINVAL;
+    cv_ctx *ctx = I->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail_msg(ctx, CV_EINVAL, "cannot open %s", path);
+    StateFileHeader h, want;
+    fill_header(I->spec, &want);
+    const int ndim = I->spec.g.ndim, N = I->spec.nbins;
+    std::vector<char> st(sizeof(DevState));
+    std::vector<double> e((size_t)ndim * (N + 1)), H((size_t)ndim * N);
+    std::vector<double> lI((size_t)kLogCap * CV_MAX_COMP), lV((size_t)kLogCap * CV_MAX_COMP);
+    bool ok = fread(&h, sizeof(h), 1, f) == 1;
+    if (ok && memcmp(&h, &want, sizeof(h)) != 0) {
+        fclose(f);
+        return fail_msg(ctx, CV_EINVAL, "%s holds the state of another problem or format", path);
+    }
+    ok = ok && fread(st.data(), st.size(), 1, f) == 1 &&
+         fread(e.data(), sizeof(double), e.size(), f) == e.size() &&
+         fread(H.data(), sizeof(double), H.size(), f) == H.size() &&
+         fread(lI.data(), sizeof(double), lI.size(), f) == lI.size() &&
+         fread(lV.data(), sizeof(double), lV.size(), f) == lV.size();
+    fclose(f);
+    if (!ok) return fail_msg(ctx, CV_EINVAL, "%s is truncated", path);
+    CV_CUDA(ctx, cudaMemcpyAsync(I->st, st.data(), st.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->edges, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->H, H.data(), H.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->log_I, lI.data(), lI.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->log_var, lV.data(), lV.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CV_OK;
+}
+
+extern "C" int cv_integral_set_grid(cv_integral *I, const double *edges)
+{
+    if (!I || !edges) return CV_EINVAL;
+    cv_ctx *ctx = I->ctx;
+    const int ndim = I->spec.g.ndim, N = I->spec.nbins;
+    for (int d = 0; d < ndim; ++d) {
+        const double *e = edges + (size_t)d * (N + 1);
+        if (e[0] != 0.0 || e[N] != 1.0) return fail_msg(ctx, CV_EINVAL, "grid axis %d must run from 0 to 1", d);
+        for (int k = 0; k < N; ++k)
+            if (!(e[k + 1] > e[k])) return fail_msg(ctx, CV_EINVAL, "grid axis %d is not increasing", d);
+    }
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->edges, edges, (size_t)ndim * (N + 1) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return CV_OK;
+}
+
 extern "C" int cv_integral_kernels_per_run(const cv_integral *I)
 {
     return I ? I->launched_kernels : 0;
