@@ -281,28 +281,7 @@ static int sample_grid(cv_ctx *ctx, int occ, long long n)
     return (int)want;
 }
 
-// Uniform constants of the FP32 map for N bins (see MapParams).
-static MapParams make_map(int N)
-{
-    MapParams m;
-    memset(&m, 0, sizeof(m));
-    m.pow2 = (N & (N - 1)) == 0;
-    if (m.pow2) {
-        int L = 0;
-        while ((1 << L) < N) ++L;
-        m.L = L;
-        m.sF = 9 - L;
-        m.mF = 0x7fffffu & ~((1u << L) - 1u);
-        m.expL = (unsigned)(127 - L) << 23;
-        m.twoNegL = ldexpf(1.0f, -L);
-        m.li = L >= 6 ? L - 5 : 0;
-        m.sK = 32 - L;
-    }
-    return m;
-}
 
-// Register budget the generic kernel uses (kMinBlocks in cv_device.cuh).
-static int min_blocks_f32(int ndim) { return ndim <= 8 ? 3 : (ndim <= 16 ? 2 : 1); }
 
 template <typename Real>
 static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *edges,
@@ -314,7 +293,7 @@ static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *e
     fill_params<Real>(g, &a.g);
     a.nbins = nbins;
     a.chunk_min = 4;
-    a.map = make_map(nbins);
+    a.map = make_map(nbins, g->ndim, sizeof(Real) == 8);
     a.edges = edges;
     a.S1 = S1;
     a.S2 = S2;
@@ -503,7 +482,7 @@ static int capture_graph(cv_integral *I)
         memset(&a, 0, sizeof(a));
         fill_params<float>(&I->spec.g, &a.g);
         a.nbins = I->spec.nbins;
-        a.map = make_map(I->spec.nbins);
+        a.map = make_map(I->spec.nbins, I->spec.g.ndim, false);
         JitKernel k;
         std::string err;
         jit_sample_kernel(ctx->device, a, I->spec.g.ndim, a.map.pow2 != 0, min_blocks_f32(I->spec.g.ndim), &k, &err);
@@ -682,7 +661,7 @@ extern "C" int cv_integral_step(cv_integral *I, int max_iter)
         memset(&a, 0, sizeof(a));
         fill_params<float>(&I->spec.g, &a.g);
         a.nbins = I->spec.nbins;
-        a.map = make_map(I->spec.nbins);
+        a.map = make_map(I->spec.nbins, I->spec.g.ndim, false);
         JitKernel k;
         std::string err;
         jit_sample_kernel(ctx->device, a, I->spec.g.ndim, a.map.pow2 != 0, min_blocks_f32(I->spec.g.ndim), &k, &err);
@@ -1181,7 +1160,8 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         fill_params<float>(&sp.g, &it.a.g);
         it.a.nbins = N;
         it.a.chunk_min = 4;
-        it.a.map = make_map(N);
+        it.a.map = make_map(N, ndim, false);
+        it.a.map.priv = it.a.map.pow2 && it.a.map.L >= 5;  // every warp has its own histogram
         it.st = (DevState *)p;
         it.edges = (double *)(p + sz_state);
         it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
@@ -1506,7 +1486,8 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         fill_params<float>(&sp.g, &it.a.g);
         it.a.nbins = N;
         it.a.chunk_min = 4;
-        it.a.map = make_map(N);
+        it.a.map = make_map(N, ndim, false);
+        it.a.map.priv = it.a.map.pow2 && it.a.map.L >= 5;  // every warp has its own histogram
         it.st = (DevState *)p;
         it.edges = (double *)(p + sz_state);
         it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
@@ -1976,7 +1957,7 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     memset(&a, 0, sizeof(a));
     a.nbins = N;
     a.ncomp = ncomp;
-    a.map = make_map(N);
+    a.map = make_map(N, ndim, sizeof(Real) == 8);
     a.edges = edges;
     a.ld = tile;
     a.x = x;

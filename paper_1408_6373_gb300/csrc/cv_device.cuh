@@ -26,20 +26,23 @@
 
 namespace cv {
 
-// Direction words in constant memory (every access below is warp-uniform).
-static __constant__ unsigned long long c_V64[CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_V64_INIT;
+// Direction words in constant memory (every access below is warp-uniform),
+// in step form: entry k is V_k for k < 5 and V_4 ^ V_k for k >= 5, so the
+// step between aligned 32-point blocks (Gray-code bits 4 and 5 + c flip
+// together) is one word.
+static __constant__ unsigned long long c_W64[CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_W64_INIT;
 // Top 32 bits of the words; table li > 0 has the top 5 + li bits rotated
 // left by 5 (the bin-slot layout of N = 2^(5 + li), see the maps below).
 // A bit permutation commutes with XOR, so a point's rotated word is the
 // rotation of its word.
-static __constant__ unsigned int c_V32R[4][CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_V32R_INIT;
+static __constant__ unsigned int c_W32R[4][CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_W32R_INIT;
 
 template <typename W> struct Dir;
 template <> struct Dir<unsigned long long> {
-    static __device__ __forceinline__ unsigned long long v(int, int d, int k) { return c_V64[d][k]; }
+    static __device__ __forceinline__ unsigned long long w(int, int d, int k) { return c_W64[d][k]; }
 };
 template <> struct Dir<unsigned int> {
-    static __device__ __forceinline__ unsigned int v(int li, int d, int k) { return c_V32R[li][d][k]; }
+    static __device__ __forceinline__ unsigned int w(int li, int d, int k) { return c_W32R[li][d][k]; }
 };
 
 // Sobol words of index i = 32 q + lane for every dimension (skip-ahead):
@@ -58,14 +61,16 @@ __device__ __forceinline__ void sobol_skip(W (&X)[NDIM], unsigned long long q, i
         W x = 0;
 #pragma unroll
         for (int k = 0; k < 5; ++k)
-            x ^= ((glo >> k) & 1u) ? Dir<W>::v(li, d, k) : W(0);
+            x ^= ((glo >> k) & 1u) ? Dir<W>::w(li, d, k) : W(0);
+        // V_k = W_k ^ W_4 for k >= 5: W_4 once per set bit of ghi
+        if (__popcll(ghi) & 1) x ^= Dir<W>::w(li, d, 4);
         X[d] = x;
     }
     while (ghi) {  // warp-uniform
         const int k = __ffsll((long long)ghi) - 1 + 5;
 #pragma unroll
         for (int d = 0; d < NDIM; ++d)
-            X[d] ^= Dir<W>::v(li, d, k);
+            X[d] ^= Dir<W>::w(li, d, k);
         ghi &= ghi - 1;
     }
 }
@@ -80,7 +85,7 @@ __device__ __forceinline__ void sobol_step(W (&X)[NDIM], unsigned long long q, i
     const int c = min(__ffsll((long long)(q + 1ull)) - 1, CV_SOBOL_BITS - 6);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d)
-        X[d] ^= Dir<W>::v(li, d, 4) ^ Dir<W>::v(li, d, 5 + c);
+        X[d] ^= Dir<W>::w(li, d, 5 + c);
 }
 
 // ------------------------------------------------------------ maps
@@ -147,6 +152,8 @@ struct RuntimeIntegrand {
     template <int C> __device__ __forceinline__ static Real p1(const GenzParams<Real> &g, int d) { return g.p1[C][d]; }
     template <int C> __device__ __forceinline__ static Real q0(const GenzParams<Real> &g) { return g.q0[C]; }
     __device__ __forceinline__ static int table(const MapParams &m) { return m.li; }
+    __device__ __forceinline__ static bool priv(const MapParams &m) { return m.priv != 0; }
+    __device__ __forceinline__ static int nbins(int n) { return n; }
 };
 
 // FP32 Genz evaluation of component C.
@@ -323,13 +330,15 @@ constexpr int kStride = CV_MAX_BINS;
 
 template <typename Real> struct Smem;
 template <> struct Smem<float> {
-    float *e, *w, *h;  // [NDIM][stride]: e_k, w_k (N w_k on the power-of-two map), histogram
-    int stride;        // slots per axis (kStride, a compile-time constant, in k_sample)
+    float *e, *w;      // [NDIM][stride]: e_k, w_k (N w_k on the power-of-two map)
+    float *h;          // [NDIM][hs]: the f^2 histogram (block's, or this warp's own copy)
+    int stride;        // grid slots per axis (kStride, a compile-time constant, in k_sample)
+    int hs;            // histogram slots per axis
 };
 template <> struct Smem<double> {
     double2 *ew;       // [NDIM][stride] {e_k, w_k}
-    double *h;         // [NDIM][stride]
-    int stride;
+    double *h;         // [NDIM][hs]
+    int stride, hs;
 };
 
 // Map one FP32 coordinate: returns x, multiplies the Jacobian, and gives the
@@ -406,8 +415,11 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
                                           int lane, Acc<Real> (&s1)[CV_MAX_COMP],
                                           Acc<Real> (&s2)[CV_MAX_COMP])
 {
-    const int N = A.nbins;
+    const int N = I::nbins(A.nbins);
     const int li = (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0;  // direction table
+    // a warp-private histogram (FP32, N = 2^L >= 32): the lanes' bins are
+    // distinct, so the update is a plain read-modify-write
+    const bool priv = sizeof(Real) == 4 && POW2 && I::priv(A.map);
     for (unsigned r0 = 0; r0 < nsteps; r0 += kRun) {
         const unsigned r1 = min(r0 + kRun, nsteps);
         Real p1[CV_MAX_COMP], p2[CV_MAX_COMP];
@@ -437,9 +449,16 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
             eval_comp<NDIM, 3, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
             if (!EDGE || valid) {
                 const Real h = f0 * f0;
+                if (priv) {
 #pragma unroll
-                for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * sm.stride + slot[d]], h);
+                    for (int d = 0; d < NDIM; ++d) sm.h[d * sm.hs + slot[d]] += h;
+                } else {
+#pragma unroll
+                    for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * sm.hs + slot[d]], h);
+                }
             }
+            // the next step's reads of the private copy see this step's writes
+            if (priv) __syncwarp();
             sobol_step<NDIM, typename Word<Real>::type>(X, q, li);
         }
 #pragma unroll
@@ -476,16 +495,22 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         start = A.start;
         n = A.n;
     }
-    const int N = A.nbins;
+    const int N = I::nbins(A.nbins);
     const int ncomp = A.g.ncomp;
+    const bool priv = sizeof(Real) == 4 && POW2 && I::priv(A.map);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<Real> sm;
     sm.stride = kStride;
+    sm.hs = kStride;
     if constexpr (sizeof(Real) == 4) {
         sm.e = reinterpret_cast<float *>(smem_raw);
         sm.w = sm.e + NDIM * kStride;
         sm.h = sm.w + NDIM * kStride;
+        if (priv) {
+            // [kWarpsPerBlock][NDIM][N]: every warp's own copy
+            for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * N; i += blockDim.x) sm.h[i] = 0.0f;
+        }
         for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
             const int d = idx / N, k = idx - d * N;
             const double *e = A.edges + (size_t)d * (N + 1);
@@ -493,7 +518,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
             const double w = e[k + 1] - e[k];
             sm.e[p] = __double2float_rn(e[k]);
             sm.w[p] = __double2float_rn(POW2 ? (double)N * w : w);
-            sm.h[p] = 0.0f;
+            if (!priv) sm.h[p] = 0.0f;
         }
     } else {
         sm.ew = reinterpret_cast<double2 *>(smem_raw);
@@ -506,6 +531,11 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         }
     }
     __syncthreads();
+    float *const hblock = reinterpret_cast<float *>(sm.h);  // (FP32: the private copies' base)
+    if (priv) {
+        sm.h = sm.h + (threadIdx.x >> 5) * NDIM * N;
+        sm.hs = N;
+    }
 
     const int lane = threadIdx.x & 31;
     const unsigned long long qa = start >> 5;
@@ -555,9 +585,20 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
     }
     for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
         const int d = idx / N, k = idx - d * N;
-        int p = k;
-        if constexpr (sizeof(Real) == 4) p = slot_of_bin(k, A.map);
-        const Real v = sm.h[d * kStride + p];
+        Real v;
+        if constexpr (sizeof(Real) == 4) {
+            const int p = slot_of_bin(k, A.map);
+            if (priv) {
+                // the warps' copies, summed in warp order
+                v = 0.0f;
+#pragma unroll
+                for (int w = 0; w < kWarpsPerBlock; ++w) v += hblock[(w * NDIM + d) * N + p];
+            } else {
+                v = hblock[d * kStride + p];
+            }
+        } else {
+            v = sm.h[d * kStride + k];
+        }
         if (v != Real(0)) atomicAdd(&A.H[idx], (double)v);
     }
 }
@@ -587,6 +628,7 @@ k_batch_sample(const BatchSampleArgs B)
     const int stride = B.stride;
     Smem<float> sm;
     sm.stride = stride;
+    sm.hs = stride;
     sm.e = reinterpret_cast<float *>(smem_raw);
     sm.w = sm.e + NDIM * stride;
     float *hist = sm.w + NDIM * stride;  // [kWarpsPerBlock][NDIM][stride]
@@ -876,7 +918,7 @@ template <int NDIM, typename Real>
 cudaError_t launch_sample(const SampleArgs<Real> &a, int grid, cudaStream_t s)
 {
     // (sample_occupancy, always called first, sets the shared-memory limit)
-    const size_t smem = sample_smem_bytes(NDIM, a.nbins, sizeof(Real) == 8);
+    const size_t smem = sample_smem_bytes(NDIM, a.nbins, sizeof(Real) == 8, a.map.priv != 0);
     if constexpr (sizeof(Real) == 4) {
         if (a.map.pow2) k_sample<NDIM, float, true><<<grid, kBlock, smem, s>>>(a);
         else k_sample<NDIM, float, false><<<grid, kBlock, smem, s>>>(a);
@@ -889,15 +931,21 @@ cudaError_t launch_sample(const SampleArgs<Real> &a, int grid, cudaStream_t s)
 template <int NDIM, typename Real>
 cudaError_t sample_occupancy(int nbins, int *blocks_per_sm)
 {
-    const size_t smem = sample_smem_bytes(NDIM, nbins, sizeof(Real) == 8);
-    const bool pow2 = (nbins & (nbins - 1)) == 0;
-    const int maxsmem = (int)sample_smem_bytes(NDIM, CV_MAX_BINS, sizeof(Real) == 8);
+    const MapParams m = make_map(nbins, NDIM, sizeof(Real) == 8);
+    const size_t smem = sample_smem_bytes(NDIM, nbins, sizeof(Real) == 8, m.priv != 0);
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     for (int v = 0; v < 2; ++v) {
-        cudaError_t e = cudaFuncSetAttribute(sample_fn<NDIM, Real>(v == 1),
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem);
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, sample_fn<NDIM, Real>(v == 1));
+        if (e != cudaSuccess) return e;
+        // (the limit, not the launch size: static shared memory counts too)
+        e = cudaFuncSetAttribute(sample_fn<NDIM, Real>(v == 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return e;
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sample_fn<NDIM, Real>(pow2),
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sample_fn<NDIM, Real>(m.pow2 != 0),
                                                          kBlock, smem);
 }
 

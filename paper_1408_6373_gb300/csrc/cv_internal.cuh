@@ -4,7 +4,9 @@
 
 #if !defined(__CUDACC_RTC__)
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 #endif
 
 #include "../../include/cubagpu.h"
@@ -69,6 +71,7 @@ struct MapParams {
     float twoNegL;                  // 2^-L
     int li;                         // direction table: top L bits rotated by 5 (L >= 6)
     unsigned sK;                    // slot = rotated word >> sK, sK = 32 - L
+    int priv;                       // per-warp f^2 histograms updated without atomics
 };
 
 // Arguments of one sampling launch.  When `st` is non-null the launch reads
@@ -205,10 +208,54 @@ cudaError_t launch_jit_sample(const JitKernel &k, const SampleArgs<float> &a, in
 int jit_info(int *compiled);
 #endif  // !__CUDACC_RTC__
 
-inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64) {
-    // grid {e, w} pairs plus the block histogram, CV_MAX_BINS slots per axis
-    (void)nbins;
-    return (size_t)ndim * CV_MAX_BINS * (fp64 ? 3 * sizeof(double) : 3 * sizeof(float));
+// Shared memory of a sampling block: the grid {e, w} with CV_MAX_BINS slots
+// per axis, then either one block histogram (CV_MAX_BINS slots per axis) or,
+// with private histograms, one copy of nbins slots per axis for each warp.
+inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64, bool priv) {
+    if (fp64) return (size_t)ndim * CV_MAX_BINS * 3 * sizeof(double);
+    return (size_t)ndim * CV_MAX_BINS * 2 * sizeof(float) +
+           (priv ? (size_t)kWarpsPerBlock * ndim * nbins : (size_t)ndim * CV_MAX_BINS) * sizeof(float);
 }
+
+// Resident 256-thread blocks per SM the FP32 sampling kernels are compiled
+// for (their __launch_bounds__): three up to 8 dimensions, two up to 16,
+// else one.
+inline int min_blocks_f32(int ndim) { return ndim <= 8 ? 3 : (ndim <= 16 ? 2 : 1); }
+
+constexpr size_t kSmemPerSM = 228 * 1024;     // shared memory of one SM
+constexpr size_t kSmemBlockReserve = 2048;    // per block: runtime reserve + static arrays
+
+#if !defined(__CUDACC_RTC__)
+// Map constants of an axis with N bins for the sampling kernels.
+//   Power-of-two N = 2^L: frac/N and the bin come straight from the bits of
+//   the Sobol word (table li = L - 5 holds the words with their top L bits
+//   rotated so that the bin's slot is word >> (32 - L)).
+//   priv: for N >= 32 the 32 points of an aligned block fall into 32
+//   distinct 1/32-strata of every axis, hence into 32 distinct bins, so a
+//   warp can keep its own f^2 histogram and update it with plain loads and
+//   stores.  Used on the FP32 path when every warp's copy fits beside the
+//   grid at the occupancy the kernel is compiled for.
+inline MapParams make_map(int N, int ndim, bool fp64)
+{
+    MapParams m;
+    memset(&m, 0, sizeof(m));
+    m.pow2 = (N & (N - 1)) == 0;
+    if (m.pow2) {
+        int L = 0;
+        while ((1 << L) < N) ++L;
+        m.L = L;
+        m.sF = 9 - L;
+        m.mF = 0x7fffffu & ~((1u << L) - 1u);
+        m.expL = (unsigned)(127 - L) << 23;
+        m.twoNegL = ldexpf(1.0f, -L);
+        m.li = L >= 6 ? L - 5 : 0;
+        m.sK = 32 - L;
+        const int blocks = min_blocks_f32(ndim);
+        m.priv = !fp64 && L >= 5 &&
+                 (size_t)blocks * (sample_smem_bytes(ndim, N, false, true) + kSmemBlockReserve) <= kSmemPerSM;
+    }
+    return m;
+}
+#endif
 
 }  // namespace cv

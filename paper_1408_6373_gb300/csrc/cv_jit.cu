@@ -116,6 +116,10 @@ std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, 
     s += "}; return v[C]; }\n";
     s += "  __device__ __forceinline__ static constexpr int table(const MapParams&) { return " +
          std::to_string(pow2 ? a.map.li : 0) + "; }\n";
+    s += "  __device__ __forceinline__ static constexpr bool priv(const MapParams&) { return " +
+         std::string(pow2 && a.map.priv ? "true" : "false") + "; }\n";
+    s += "  __device__ __forceinline__ static constexpr int nbins(int) { return " + std::to_string(a.nbins) +
+         "; }\n";
     s += "};\n}\n";
     s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(kBlock) + ", " +
          std::to_string(min_blocks) + ") cv_jit_sample(const __grid_constant__ cv::SampleArgs<float> A)\n{\n";
@@ -169,7 +173,7 @@ int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow
         *err = "loading the specialised kernel failed";
         return -1;
     }
-    k.smem = sample_smem_bytes(ndim, CV_MAX_BINS, false);
+    k.smem = sample_smem_bytes(ndim, a.nbins, false, pow2 && a.map.priv);
     if (cudaFuncSetAttribute((const void *)k.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)k.smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k.occ, (const void *)k.kernel, kBlock, k.smem) !=

@@ -91,25 +91,6 @@ void fill(const cv_genz *g, cv::GenzParams<Real> *p)
     }
 }
 
-cv::MapParams map_params(int N)
-{
-    cv::MapParams m;
-    memset(&m, 0, sizeof(m));
-    m.pow2 = (N & (N - 1)) == 0;
-    if (m.pow2) {
-        int L = 0;
-        while ((1 << L) < N) ++L;
-        m.L = L;
-        m.sF = 9 - L;
-        m.mF = 0x7fffffu & ~((1u << L) - 1u);
-        m.expL = (unsigned)(127 - L) << 23;
-        m.twoNegL = ldexpf(1.0f, -L);
-        m.li = L >= 6 ? L - 5 : 0;
-        m.sK = 32 - L;
-    }
-    return m;
-}
-
 #define CV_NA_FOR_EACH_NDIM(X)                                                               \
     X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) \
     X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30)    \
@@ -147,7 +128,7 @@ cudaError_t run(const cv_genz *g, int nbins, int sms, long long nmax, int jmax, 
     fill<Real>(g, &a.g);
     a.nbins = nbins;
     a.chunk_min = 4;
-    a.map = map_params(nbins);
+    a.map = cv::make_map(nbins, g->ndim, sizeof(Real) == 8);
     a.edges = edges;
     a.S1 = st->S1;
     a.S2 = st->S2;
