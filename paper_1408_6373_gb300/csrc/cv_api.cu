@@ -966,7 +966,8 @@ static int batch_build_tiles(cv_batch *B, int only_first_iteration)
                 for (int jj = 0; jj < j; ++jj) s += (unsigned long long)(sp.nstart + (long long)jj * sp.nincrease);
                 const unsigned long long n = (unsigned long long)(sp.nstart + (long long)j * sp.nincrease);
                 const int TB = B->tile_fixed ? B->tile_fixed : tile_blocks_for((long long)n, B->tile_cap);
-                const unsigned long long qa = s >> 5, qb = (s + n + 31) >> 5;
+                // (tiles start on even 32-point blocks: see run_steps)
+                const unsigned long long qa = (s >> 5) & ~1ull, qb = (s + n + 31) >> 5;
                 for (unsigned long long q = qa; q < qb; q += (unsigned long long)TB) {
                     Tile t;
                     t.item = i;
@@ -1161,7 +1162,7 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         it.a.nbins = N;
         it.a.chunk_min = 4;
         it.a.map = make_map(N, ndim, false);
-        it.a.map.priv = it.a.map.pow2 && it.a.map.L >= 5;  // every warp has its own histogram
+        it.a.map.priv = it.a.map.pow2;  // every warp has its own histogram
         it.st = (DevState *)p;
         it.edges = (double *)(p + sz_state);
         it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
@@ -1487,7 +1488,7 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         it.a.nbins = N;
         it.a.chunk_min = 4;
         it.a.map = make_map(N, ndim, false);
-        it.a.map.priv = it.a.map.pow2 && it.a.map.L >= 5;  // every warp has its own histogram
+        it.a.map.priv = it.a.map.pow2;  // every warp has its own histogram
         it.st = (DevState *)p;
         it.edges = (double *)(p + sz_state);
         it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
@@ -1533,7 +1534,7 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         const unsigned long long n = (unsigned long long)(r.spec.nstart + (long long)r.j * r.spec.nincrease);
         const long long tb = S->opts.tile_points > 0 ? std::max(1, S->opts.tile_points / 32)
                                                      : tile_blocks_for((long long)n, 2048);
-        const unsigned long long qa = s >> 5, qb = (s + n + 31) >> 5;
+        const unsigned long long qa = (s >> 5) & ~1ull, qb = (s + n + 31) >> 5;
         for (unsigned long long q = qa; q < qb; q += (unsigned long long)tb) {
             Tile t;
             t.item = r.slot;

@@ -31,18 +31,19 @@ namespace cv {
 // step between aligned 32-point blocks (Gray-code bits 4 and 5 + c flip
 // together) is one word.
 static __constant__ unsigned long long c_W64[CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_W64_INIT;
-// Top 32 bits of the words; table li > 0 has the top 5 + li bits rotated
-// left by 5 (the bin-slot layout of N = 2^(5 + li), see the maps below).
-// A bit permutation commutes with XOR, so a point's rotated word is the
-// rotation of its word.
-static __constant__ unsigned int c_W32R[4][CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_W32R_INIT;
+// Top 32 bits of the words: table 0 as they are; table li = L - 4 for
+// N = 2^L bins (L = 5..8) with the bits permuted so that the bin's slot is
+// the word's top L bits and the fraction's bits sit at mantissa position
+// (layout at the maps below).  A bit permutation commutes with XOR, so a point's
+// permuted word is the permutation of its word.
+static __constant__ unsigned int c_W32P[5][CV_SOBOL_DIMS][CV_SOBOL_BITS] = CV_SOBOL_W32P_INIT;
 
 template <typename W> struct Dir;
 template <> struct Dir<unsigned long long> {
     static __device__ __forceinline__ unsigned long long w(int, int d, int k) { return c_W64[d][k]; }
 };
 template <> struct Dir<unsigned int> {
-    static __device__ __forceinline__ unsigned int w(int li, int d, int k) { return c_W32R[li][d][k]; }
+    static __device__ __forceinline__ unsigned int w(int li, int d, int k) { return c_W32P[li][d][k]; }
 };
 
 // Sobol words of index i = 32 q + lane for every dimension (skip-ahead):
@@ -88,17 +89,30 @@ __device__ __forceinline__ void sobol_step(W (&X)[NDIM], unsigned long long q, i
         X[d] ^= Dir<W>::w(li, d, 5 + c);
 }
 
+// The step from an even block q (q + 1 is odd, c = 0): a fixed word.
+template <int NDIM, typename W>
+__device__ __forceinline__ void sobol_step_even(W (&X)[NDIM], int li = 0)
+{
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d)
+        X[d] ^= Dir<W>::w(li, d, 5);
+}
+
 // ------------------------------------------------------------ maps
 // FP32 path: the 32-bit word is the top half of the 64-bit Sobol word and y
 // keeps its top 23 bits, so frac is exact as the mantissa of 1.frac minus 1.
 // FP64 path: 64-bit word, y keeps 52 bits.
 //
-// Shared-memory layout of a block's grid and histogram.  For N = 2^L with
-// L >= 5 the bins of an axis are stored stratum-major: bin k = j R + r
-// (j = k / R the 1/32-stratum, R = N/32) sits at slot r*32 + j.  The 32
-// lanes of a warp always hold 32 distinct strata, so their 32 slots fall in
-// 32 distinct banks -- every grid gather and histogram atomic of a warp is
-// conflict-free.  Other N use slot = k.
+// Shared-memory layout of a block's grid and histogram.  For N = 2^L >= 32
+// the bins of an axis are stored stratum-major.  Writing the bin index
+// k = y_1 .. y_L (the top L bits of y), bin k sits at slot
+//   s = (y_6 .. y_L) * 32 + y_5 * 16 + (y_1 .. y_4),
+// which is exactly the top L bits of the point's permuted word.  The 32
+// lanes of a warp always hold 32 distinct 1/32-strata (y_1 .. y_5), so their
+// slots are distinct mod 32 -- every histogram access of a warp hits 32
+// distinct banks -- and each half-warp (lanes 0-15 or 16-31: Gray-code
+// bit 4 fixed) holds 16 distinct y_1 .. y_4, so the 8-byte {e, w} gathers
+// are conflict-free too.  Other N use slot = k.
 
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -111,15 +125,21 @@ __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fm
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // slot of bin k (staging and flush run once per block; the sampling loop
-// computes the slot straight from the Sobol word)
+// takes the slot straight from the permuted Sobol word)
 __device__ __forceinline__ int slot_of_bin(int k, const MapParams &m)
 {
-    if (m.pow2 && m.L >= 5) return ((k & ((1 << (m.L - 5)) - 1)) << 5) | (k >> (m.L - 5));
+    if (m.pow2) {
+        const int L = m.L;
+        return ((k & ((1 << (L - 5)) - 1)) << 5) | (((k >> (L - 5)) & 1) << 4) | (k >> (L - 4));
+    }
     return k;
 }
 __device__ __forceinline__ int bin_of_slot(int p, const MapParams &m)
 {
-    if (m.pow2 && m.L >= 5) return ((p & 31) << (m.L - 5)) | (p >> 5);
+    if (m.pow2) {
+        const int L = m.L;
+        return ((p & 15) << (L - 4)) | (((p >> 4) & 1) << (L - 5)) | (p >> 5);
+    }
     return p;
 }
 
@@ -330,7 +350,7 @@ constexpr int kStride = CV_MAX_BINS;
 
 template <typename Real> struct Smem;
 template <> struct Smem<float> {
-    float *e, *w;      // [NDIM][stride]: e_k, w_k (N w_k on the power-of-two map)
+    float2 *ew;        // [NDIM][stride]: {e_k, w_k} (w_k scaled by N on the power-of-two map)
     float *h;          // [NDIM][hs]: the f^2 histogram (block's, or this warp's own copy)
     int stride;        // grid slots per axis (kStride, a compile-time constant, in k_sample)
     int hs;            // histogram slots per axis
@@ -350,22 +370,22 @@ __device__ __forceinline__ float map_f32(unsigned X, int d, int N, const MapPara
                                          const Smem<float> &sm, float &J, int &slot)
 {
     if (POW2) {
-        // X is the rotated word (table m.li): its top L bits are the slot
-        const unsigned fb = (X >> m.sF) & m.mF;
-        const float fs = __uint_as_float(m.expL | fb) - m.twoNegL;
+        // X is the permuted word (table m.li): slot in the top L bits, the
+        // fraction's 23 - L bits at mantissa bits 22..L
+        const float fs = __uint_as_float((X & m.mF) | m.expL) - m.twoNegL;
         const int p = (int)(X >> m.sK);
-        const float w = sm.w[d * sm.stride + p];
-        J *= w;
+        const float2 ew = sm.ew[d * sm.stride + p];
+        J *= ew.y;
         slot = p;
-        return __fmaf_rn(w, fs, sm.e[d * sm.stride + p]);
+        return __fmaf_rn(ew.y, fs, ew.x);
     } else {
         const unsigned t = (X >> 9) * (unsigned)N;
         const float frac = __uint_as_float(0x3f800000u | (t & 0x7fffffu)) - 1.0f;
         const int p = (int)(t >> 23);
-        const float w = sm.w[d * sm.stride + p];
-        J = J * ((float)N * w);
+        const float2 ew = sm.ew[d * sm.stride + p];
+        J = J * ((float)N * ew.y);
         slot = p;
-        return __fmaf_rn(w, frac, sm.e[d * sm.stride + p]);
+        return __fmaf_rn(ew.y, frac, ew.x);
     }
 }
 
@@ -401,10 +421,60 @@ __device__ __forceinline__ void eval_comp(const GenzParams<Real> &g, const Real 
     }
 }
 
-// nsteps consecutive 32-point blocks starting at block q0.  EDGE: the range
-// touches the first or last (partial) block and every index is checked.
-// FP32: the values are summed in FP32 over runs of kRun steps, and each
-// run's sum is added to the Kahan accumulators.
+// One aligned 32-point block q: map, integrand, partial sums, histogram.
+// EDGE: the block may hold indices outside [start, end), which add nothing.
+template <int NDIM, typename Real, bool POW2, bool EDGE, class I>
+__device__ __forceinline__ void sample_block(const SampleArgs<Real> &A, const Smem<Real> &sm,
+                                             const typename Word<Real>::type (&X)[NDIM],
+                                             unsigned long long q, unsigned long long start,
+                                             unsigned long long end, int lane, bool priv,
+                                             Real (&p1)[CV_MAX_COMP], Real (&p2)[CV_MAX_COMP])
+{
+    const int N = I::nbins(A.nbins);
+    bool valid = true;
+    if (EDGE) {
+        const unsigned long long i = q * 32ull + (unsigned long long)lane;
+        valid = (i >= start) && (i < end);
+    }
+    Real x[NDIM];
+    int slot[NDIM];
+    Real J = Real(1);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        if constexpr (sizeof(Real) == 4)
+            x[d] = map_f32<POW2>(X[d], d, N, A.map, sm, J, slot[d]);
+        else
+            x[d] = map_f64(X[d], d, N, sm, J, slot[d]);
+    }
+    Real f0 = Real(0);
+    eval_comp<NDIM, 0, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+    eval_comp<NDIM, 1, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+    eval_comp<NDIM, 2, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+    eval_comp<NDIM, 3, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+    if (!EDGE || valid) {
+        const Real h = f0 * f0;
+        if (priv) {
+            // a warp-private histogram (FP32, N = 2^L >= 32): the lanes'
+            // bins are distinct, so the update is a plain read-modify-write
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) sm.h[d * sm.hs + slot[d]] += h;
+        } else {
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * sm.hs + slot[d]], h);
+        }
+    }
+    // the next block's reads of the private copy see this block's writes
+    if (priv) __syncwarp();
+}
+
+// nsteps consecutive 32-point blocks starting at block q0, every lane's
+// words advanced past them.  FP32: the values are summed in FP32 over runs
+// of kRun blocks, and each run's sum is added to the Kahan accumulators.
+//   EDGE = false: every index of the range is inside [start, end), q0 and
+//   nsteps are even; the blocks go in (even, odd) pairs, and the step out
+//   of an even block is the fixed word W_5.
+//   EDGE = true: any range (the first and last chunks of a pass), one block
+//   at a time.
 constexpr unsigned kRun = 16;
 
 template <int NDIM, typename Real, bool POW2, bool EDGE, class I = RuntimeIntegrand<Real>>
@@ -415,51 +485,25 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
                                           int lane, Acc<Real> (&s1)[CV_MAX_COMP],
                                           Acc<Real> (&s2)[CV_MAX_COMP])
 {
-    const int N = I::nbins(A.nbins);
+    using W = typename Word<Real>::type;
     const int li = (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0;  // direction table
-    // a warp-private histogram (FP32, N = 2^L >= 32): the lanes' bins are
-    // distinct, so the update is a plain read-modify-write
     const bool priv = sizeof(Real) == 4 && POW2 && I::priv(A.map);
+    const unsigned per = EDGE ? 1u : 2u;  // blocks per loop trip
     for (unsigned r0 = 0; r0 < nsteps; r0 += kRun) {
         const unsigned r1 = min(r0 + kRun, nsteps);
         Real p1[CV_MAX_COMP], p2[CV_MAX_COMP];
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c) p1[c] = p2[c] = Real(0);
-        for (unsigned st = r0; st < r1; ++st) {
+        for (unsigned st = r0; st < r1; st += per) {
             const unsigned long long q = q0 + st;
-            bool valid = true;
+            sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2);
             if (EDGE) {
-                const unsigned long long i = q * 32ull + (unsigned long long)lane;
-                valid = (i >= start) && (i < end);
+                sobol_step<NDIM, W>(X, q, li);
+            } else {
+                sobol_step_even<NDIM, W>(X, li);
+                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2);
+                sobol_step<NDIM, W>(X, q + 1, li);
             }
-            Real x[NDIM];
-            int slot[NDIM];
-            Real J = Real(1);
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d) {
-                if constexpr (sizeof(Real) == 4)
-                    x[d] = map_f32<POW2>(X[d], d, N, A.map, sm, J, slot[d]);
-                else
-                    x[d] = map_f64(X[d], d, N, sm, J, slot[d]);
-            }
-            Real f0 = Real(0);
-            eval_comp<NDIM, 0, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-            eval_comp<NDIM, 1, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-            eval_comp<NDIM, 2, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-            eval_comp<NDIM, 3, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-            if (!EDGE || valid) {
-                const Real h = f0 * f0;
-                if (priv) {
-#pragma unroll
-                    for (int d = 0; d < NDIM; ++d) sm.h[d * sm.hs + slot[d]] += h;
-                } else {
-#pragma unroll
-                    for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * sm.hs + slot[d]], h);
-                }
-            }
-            // the next step's reads of the private copy see this step's writes
-            if (priv) __syncwarp();
-            sobol_step<NDIM, typename Word<Real>::type>(X, q, li);
         }
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c) {
@@ -504,9 +548,8 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
     sm.stride = kStride;
     sm.hs = kStride;
     if constexpr (sizeof(Real) == 4) {
-        sm.e = reinterpret_cast<float *>(smem_raw);
-        sm.w = sm.e + NDIM * kStride;
-        sm.h = sm.w + NDIM * kStride;
+        sm.ew = reinterpret_cast<float2 *>(smem_raw);
+        sm.h = reinterpret_cast<float *>(sm.ew + NDIM * kStride);
         if (priv) {
             // [kWarpsPerBlock][NDIM][N]: every warp's own copy
             for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * N; i += blockDim.x) sm.h[i] = 0.0f;
@@ -516,8 +559,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
             const double *e = A.edges + (size_t)d * (N + 1);
             const int p = d * kStride + slot_of_bin(k, A.map);
             const double w = e[k + 1] - e[k];
-            sm.e[p] = __double2float_rn(e[k]);
-            sm.w[p] = __double2float_rn(POW2 ? (double)N * w : w);
+            sm.ew[p] = make_float2(__double2float_rn(e[k]), __double2float_rn(POW2 ? (double)N * w : w));
             if (!priv) sm.h[p] = 0.0f;
         }
     } else {
@@ -538,7 +580,9 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
     }
 
     const int lane = threadIdx.x & 31;
-    const unsigned long long qa = start >> 5;
+    // blocks [qa, qb) cover the pass; qa and the chunk length are even, so
+    // every chunk starts on an even block
+    const unsigned long long qa = (start >> 5) & ~1ull;
     const unsigned long long end = start + (unsigned long long)n;
     const unsigned long long qb = (end + 31ull) >> 5;
     const unsigned long long nblk = n > 0 ? qb - qa : 0ull;
@@ -546,6 +590,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
     const unsigned long long twarps = (unsigned long long)gridDim.x * kWarpsPerBlock;
     unsigned long long plen = (nblk + twarps - 1) / twarps;
     if (plen < (unsigned long long)A.chunk_min) plen = A.chunk_min;
+    plen = (plen + 1ull) & ~1ull;
     const unsigned long long nchunk = (nblk + plen - 1) / plen;
 
     Acc<Real> s1[CV_MAX_COMP], s2[CV_MAX_COMP];
@@ -555,7 +600,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         const unsigned long long q1 = min(q0 + plen, qb);
         W X[NDIM];
         sobol_skip<NDIM, W>(X, q0, lane, (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0);
-        const bool interior = (q0 * 32ull >= start) && (q1 * 32ull <= end);
+        const bool interior = (q0 * 32ull >= start) && (q1 * 32ull <= end) && !((q0 | q1) & 1ull);
         if (interior)
             run_steps<NDIM, Real, POW2, false, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
         else
@@ -629,9 +674,8 @@ k_batch_sample(const BatchSampleArgs B)
     Smem<float> sm;
     sm.stride = stride;
     sm.hs = stride;
-    sm.e = reinterpret_cast<float *>(smem_raw);
-    sm.w = sm.e + NDIM * stride;
-    float *hist = sm.w + NDIM * stride;  // [kWarpsPerBlock][NDIM][stride]
+    sm.ew = reinterpret_cast<float2 *>(smem_raw);
+    float *hist = reinterpret_cast<float *>(sm.ew + NDIM * stride);  // [kWarpsPerBlock][NDIM][stride]
     __shared__ SampleArgs<float> A;
     __shared__ int s_tile;
     __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
@@ -663,8 +707,7 @@ k_batch_sample(const BatchSampleArgs B)
                 const double *e = it.edges + (size_t)d * (N + 1);
                 const int p = d * stride + slot_of_bin(k, A.map);
                 const double w = e[k + 1] - e[k];
-                sm.e[p] = __double2float_rn(e[k]);
-                sm.w[p] = __double2float_rn(POW2 ? (double)N * w : w);
+                sm.ew[p] = make_float2(__double2float_rn(e[k]), __double2float_rn(POW2 ? (double)N * w : w));
             }
             cur = tile.item;
             __syncthreads();
@@ -672,7 +715,8 @@ k_batch_sample(const BatchSampleArgs B)
         const unsigned long long start = it.st->next_index;
         const unsigned long long end = start + (unsigned long long)it.st->n_cur;
         Acc<float> s1[CV_MAX_COMP], s2[CV_MAX_COMP];
-        const unsigned per = ((unsigned)tile.nblk + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        // (an even share, so that warps start on even blocks of an even tile)
+        const unsigned per = ((((unsigned)tile.nblk + kWarpsPerBlock - 1) / kWarpsPerBlock) + 1u) & ~1u;
         const unsigned long long w0 = tile.q0 + (unsigned long long)warp * per;
         const unsigned long long w1 = min(w0 + per, tile.q0 + (unsigned long long)tile.nblk);
         if (w0 < w1) {
@@ -680,7 +724,7 @@ k_batch_sample(const BatchSampleArgs B)
             smw.h = hist + warp * hsize;
             unsigned X[NDIM];
             sobol_skip<NDIM, unsigned>(X, w0, lane, POW2 ? A.map.li : 0);
-            const bool interior = (w0 * 32ull >= start) && (w1 * 32ull <= end);
+            const bool interior = (w0 * 32ull >= start) && (w1 * 32ull <= end) && !((w0 | w1) & 1ull);
             if (interior)
                 run_steps<NDIM, float, POW2, false>(A, smw, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
             else

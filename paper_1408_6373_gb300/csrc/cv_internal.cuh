@@ -64,13 +64,13 @@ struct GenzParams {
 
 // Uniform constants of the FP32 map for N = 2^L (see cv_device.cuh).
 struct MapParams {
-    int pow2;                       // N is a power of two
+    int pow2;                       // N = 2^L with L >= 5: the bit-level map below
     int L;                          // log2 N
-    unsigned sF, mF;                // mantissa bits of frac: (X >> sF) & mF
+    unsigned mF;                    // mantissa bits of frac in the permuted word
     unsigned expL;                  // exponent field of 2^-L
     float twoNegL;                  // 2^-L
-    int li;                         // direction table: top L bits rotated by 5 (L >= 6)
-    unsigned sK;                    // slot = rotated word >> sK, sK = 32 - L
+    int li;                         // direction table: L - 4 (permuted words), else 0
+    unsigned sK;                    // slot = permuted word >> sK, sK = 32 - L
     int priv;                       // per-warp f^2 histograms updated without atomics
 };
 
@@ -227,9 +227,10 @@ constexpr size_t kSmemBlockReserve = 2048;    // per block: runtime reserve + st
 
 #if !defined(__CUDACC_RTC__)
 // Map constants of an axis with N bins for the sampling kernels.
-//   Power-of-two N = 2^L: frac/N and the bin come straight from the bits of
-//   the Sobol word (table li = L - 5 holds the words with their top L bits
-//   rotated so that the bin's slot is word >> (32 - L)).
+//   N = 2^L >= 32: frac/N and the bin's slot come straight from the bits of
+//   the Sobol word (table li = L - 4 holds the words bit-permuted so that
+//   the slot is word >> (32 - L) and the fraction's bits sit at mantissa
+//   position: word & mF).  Other N take the generic map.
 //   priv: for N >= 32 the 32 points of an aligned block fall into 32
 //   distinct 1/32-strata of every axis, hence into 32 distinct bins, so a
 //   warp can keep its own f^2 histogram and update it with plain loads and
@@ -239,19 +240,18 @@ inline MapParams make_map(int N, int ndim, bool fp64)
 {
     MapParams m;
     memset(&m, 0, sizeof(m));
-    m.pow2 = (N & (N - 1)) == 0;
+    m.pow2 = (N & (N - 1)) == 0 && N >= 32;
     if (m.pow2) {
         int L = 0;
         while ((1 << L) < N) ++L;
         m.L = L;
-        m.sF = 9 - L;
         m.mF = 0x7fffffu & ~((1u << L) - 1u);
         m.expL = (unsigned)(127 - L) << 23;
         m.twoNegL = ldexpf(1.0f, -L);
-        m.li = L >= 6 ? L - 5 : 0;
+        m.li = L - 4;
         m.sK = 32 - L;
         const int blocks = min_blocks_f32(ndim);
-        m.priv = !fp64 && L >= 5 &&
+        m.priv = !fp64 &&
                  (size_t)blocks * (sample_smem_bytes(ndim, N, false, true) + kSmemBlockReserve) <= kSmemPerSM;
     }
     return m;
