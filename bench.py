@@ -161,7 +161,7 @@ def _dist():
     return world, rank, local
 
 
-KERNEL_SOURCES = ("cv_device.cuh", "cv_internal.cuh", "sobol_dirs.h")
+KERNEL_SOURCES = ("cv_device.cuh", "cv_internal.cuh", "sobol_dirs.h", "cv_jit.cu")
 
 
 def _kernel_source_hash() -> str:
