@@ -60,28 +60,38 @@ __device__ __forceinline__ double warp_sum_d(double v)
     for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
-__device__ __forceinline__ double warp_max_d(double v)
+// Maximum of non-negative doubles through their bit patterns: for x, y >= 0
+// the IEEE order is the order of the 64-bit integers, and integer compares
+// avoid the long FP64 latency of this part.
+__device__ __forceinline__ long long warp_max_bits(long long v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
 // Refine axis `d` of the grid in place (one CTA of at least N threads, at
 // most 256).  Every reduction has a fixed order, so the result is
 // reproducible.  GB300 issues FP64 at a small fraction of the FP32 rate, so
-// the CTA is sized to the bins: idle warps would still spend FP64 issue
-// slots on the reductions.
+// the CTA is sized to the bins (idle warps would still spend FP64 issue
+// slots on the reductions), the per-axis scalars (1/s, 1/max r, R/N) are
+// computed once, and the per-bin divisions other than the smoothing's are
+// multiplications by correctly rounded reciprocals (each result within
+// 1.5 ulp of the quotient).  FP64 results take ~200 cycles here, so the
+// refinement is bound by its chain of dependent FP64 operations: maxima
+// and searches over non-negative doubles compare bit patterns instead.
 __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_hist)
 {
     double *Hd = H + (size_t)d * N;
     double *e = edges + (size_t)d * (N + 1);
-    __shared__ double sH[CV_MAX_BINS], sr[CV_MAX_BINS];
+    __shared__ double sH[CV_MAX_BINS], sq[CV_MAX_BINS];
     __shared__ double sC[CV_MAX_BINS + 1], se[CV_MAX_BINS + 1];
     __shared__ double wred[8];
+    __shared__ double s_sum, s_inv, s_rmax, s_RN;
     const int k = threadIdx.x;            // bin of this thread
     const int lane = k & 31, warp = k >> 5;
     const int nw = blockDim.x >> 5;
+    const double invN = __drcp_rn((double)N);  // (off the dependent chain)
 
     if (k < N) sH[k] = Hd[k];
     for (int i = k; i <= N; i += blockDim.x) se[i] = e[i];
@@ -91,39 +101,54 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
     const int any_bad = __syncthreads_or(bad);
     const int any_nz = __syncthreads_or(nz);
     if (!any_bad && any_nz) {
-        // smoothing over the neighbours
+        // smoothing over the neighbours (correctly rounded: an even
+        // histogram stays exactly even)
         double h = 0.0;
         if (k < N) {
-            if (k == 0) h = __ddiv_rn(__dadd_rn(sH[0], sH[1]), 2.0);
-            else if (k == N - 1) h = __ddiv_rn(__dadd_rn(sH[N - 2], sH[N - 1]), 2.0);
+            if (k == 0) h = __dmul_rn(__dadd_rn(sH[0], sH[1]), 0.5);
+            else if (k == N - 1) h = __dmul_rn(__dadd_rn(sH[N - 2], sH[N - 1]), 0.5);
             else h = __ddiv_rn(__dadd_rn(__dadd_rn(sH[k - 1], sH[k]), sH[k + 1]), 3.0);
         }
-        // s = sum_k h_k
+        // s = sum_k h_k (warp sums, then the warps in order by one thread;
+        // the per-axis scalars are computed once and shared)
         double ws = warp_sum_d(h);
         if (lane == 0) wred[warp] = ws;
         __syncthreads();
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s = __dadd_rn(s, wred[w]);
+        if (k == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t = __dadd_rn(t, wred[w]);
+            s_sum = t;
+            s_inv = __drcp_rn(t);
+        }
         __syncthreads();
-        // compression
+        const double s = s_sum;
+        // compression r = ((1 - h/s) / ln(s/h))^1.5 = ((x - 1) / ln x)^1.5,
+        // x = h/s in (0, 1]
         double r = 0.0;
-        if (k < N) {
-            if (h == 0.0) r = 0.0;
-            else if (h == s) r = 1.0;
-            else {
-                const double q = __ddiv_rn(__dadd_rn(1.0, -__ddiv_rn(h, s)), log(__ddiv_rn(s, h)));
+        if (k < N && h != 0.0) {
+            const double x = __dmul_rn(h, s_inv);
+            if (h == s || !(x < 1.0)) {
+                r = 1.0;
+            } else {
+                const double q = __dmul_rn(__dadd_rn(x, -1.0), __drcp_rn(log(x)));
                 r = __dmul_rn(q, sqrt(q));
             }
         }
-        const double wm = warp_max_d(r);
-        if (lane == 0) wred[warp] = wm;
+        const long long wm = warp_max_bits(__double_as_longlong(r));
+        if (lane == 0) wred[warp] = __longlong_as_double(wm);
         __syncthreads();
-        double rmax = 0.0;
-        for (int w = 0; w < nw; ++w) rmax = fmax(rmax, wred[w]);
+        if (k == 0) {
+            long long t = 0;
+            for (int w = 0; w < nw; ++w) t = max(t, __double_as_longlong(wred[w]));
+            s_rmax = __longlong_as_double(t);
+            s_inv = t > 0 ? __drcp_rn(__longlong_as_double(t)) : 0.0;
+        }
         __syncthreads();
-        if (rmax > 0.0) {
-            r = __ddiv_rn(r, rmax);
-            if (k < N) sr[k] = r;
+        const long long rmax_bits = __double_as_longlong(s_rmax);
+        if (rmax_bits > 0) {
+            // scale to max 1 (the largest bins exactly 1)
+            r = (__double_as_longlong(r) == rmax_bits) ? 1.0 : __dmul_rn(r, s_inv);
+            if (k < N) sq[k] = r > 0.0 ? __drcp_rn(r) : 0.0;
             // inclusive prefix sum C_(k+1) = r_0 + ... + r_k
             double c = r;
 #pragma unroll
@@ -138,20 +163,22 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
             c = __dadd_rn(off, c);
             if (k < N) sC[k + 1] = c;
             if (k == 0) sC[0] = 0.0;
+            if (k == N - 1) s_RN = __dmul_rn(c, invN);  // R / N, R = C_N
             __syncthreads();
-            const double R = sC[N];
             const int m = k;
             if (m >= 1 && m < N) {
-                const double t = __ddiv_rn(__dmul_rn((double)m, R), (double)N);
-                // largest j in [0, N-1] with C_j <= t
+                // new edge m at compressed weight t = m R / N
+                const double t = __dmul_rn((double)m, s_RN);
+                // largest j in [0, N-1] with C_j <= t (C, t >= 0: bit-pattern compares)
+                const long long tb = __double_as_longlong(t);
                 int lo = 0, hi = N - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (sC[mid] <= t) lo = mid;
+                    if (__double_as_longlong(sC[mid]) <= tb) lo = mid;
                     else hi = mid - 1;
                 }
                 e[m] = __fma_rn(__dadd_rn(se[lo + 1], -se[lo]),
-                                __ddiv_rn(__dadd_rn(t, -sC[lo]), sr[lo]), se[lo]);
+                                __dmul_rn(__dadd_rn(t, -sC[lo]), sq[lo]), se[lo]);
             }
         }
     }
@@ -175,35 +202,47 @@ __device__ void combine_iteration(const CombineArgs &A)
     __shared__ int s_ok[CV_MAX_COMP];
     __shared__ int s_stop;
     if (c < A.ncomp) {
+        // every input first (independent loads), then the arithmetic: FP64
+        // latency is high, so divisions are reciprocal multiplications
+        // except where a reciprocal itself is the result
+        const double S1 = st->S1[c], S2 = st->S2[c];
+        const double sumI0 = st->sumI[c], W0 = st->W[c], mean0 = st->mean[c], M20 = st->M2[c];
+        int zero = st->zero[c];
         const double dn = (double)n;
-        const double I = __ddiv_rn(st->S1[c], dn);
-        const double var = __ddiv_rn(__dadd_rn(__ddiv_rn(st->S2[c], dn), -__dmul_rn(I, I)),
-                                     (double)(n - 1));
+        const double inv_n = __drcp_rn(dn);
+        const double inv_n1 = __drcp_rn((double)(n - 1));
+        const double I = __dmul_rn(S1, inv_n);
+        const double var = __dmul_rn(__fma_rn(-I, I, __dmul_rn(S2, inv_n)), inv_n1);
         if (A.log_I && j < kLogCap) {
             A.log_I[j * CV_MAX_COMP + c] = I;
             A.log_var[j * CV_MAX_COMP + c] = var;
         }
         if (!isfinite(I) || !isfinite(var)) atomicOr(&st->status, 1);
         const int m = j + 1;
-        st->sumI[c] += I;
-        if (!(var > 0.0)) st->zero[c] = 1;
-        if (!st->zero[c]) {
-            const double w = 1.0 / var;
-            const double Wn = st->W[c] + w;
-            const double dI = I - st->mean[c];
-            const double mean = st->mean[c] + dI * (w / Wn);
-            st->M2[c] += w * dI * (I - mean);
+        const double sumI = sumI0 + I;
+        st->sumI[c] = sumI;
+        if (!(var > 0.0)) zero = 1;
+        double W = W0, mean = mean0, M2 = M20;
+        if (!zero) {
+            const double w = __drcp_rn(var);
+            W = W0 + w;
+            const double dI = I - mean0;
+            mean = __fma_rn(dI, __dmul_rn(w, __drcp_rn(W)), mean0);
+            M2 = __fma_rn(__dmul_rn(w, dI), I - mean, M20);
             st->mean[c] = mean;
-            st->W[c] = Wn;
+            st->W[c] = W;
+            st->M2[c] = M2;
+        } else {
+            st->zero[c] = 1;
         }
         double integral, error, chi2;
-        if (st->zero[c]) {
-            integral = st->sumI[c] / (double)m;
+        if (zero) {
+            integral = sumI / (double)m;
             error = chi2 = 0.0;
         } else {
-            integral = st->mean[c];
-            error = sqrt(1.0 / st->W[c]);
-            chi2 = st->M2[c] > 0.0 ? st->M2[c] : 0.0;
+            integral = mean;
+            error = rsqrt(W);
+            chi2 = M2 > 0.0 ? M2 : 0.0;
         }
         st->integral[c] = integral;
         st->error[c] = error;
