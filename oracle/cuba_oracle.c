@@ -426,14 +426,16 @@ static void *sample_range(void *arg)
             Y[d] = X[d] >> (64 - p->bits);
         double J = map_point(ndim, N, job->edges, Y, p->bits, x, kbin);
         if (p->fp32_decide) {
-            /* the binary32 point as the FP32 path forms it:
-             * fmaf((float)w, frac, (float)e) */
+            /* the binary32 point as the FP32 path forms it: with
+             * w = e_(k+1) - e_k, x = fmaf((float)w, 1 + frac, (float)(e_k - w))
+             * (w (1 + frac) is exact in binary32, so one rounding) */
             for (int d = 0; d < ndim; ++d) {
                 const double *e = job->edges + (size_t)d * (N + 1);
                 int k = kbin[d];
                 uint64_t t = Y[d] * (uint64_t)N;
-                float frac = (float)ldexp((double)(t & mask), -p->bits);
-                x32[d] = fmaf((float)(e[k + 1] - e[k]), frac, (float)e[k]);
+                double frac = ldexp((double)(t & mask), -p->bits);
+                double w = e[k + 1] - e[k];
+                x32[d] = fmaf((float)w, (float)(1.0 + frac), (float)(e[k] - w));
             }
         }
         double Jf0 = 0.0;

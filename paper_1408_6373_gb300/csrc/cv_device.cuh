@@ -350,7 +350,7 @@ constexpr int kStride = CV_MAX_BINS;
 
 template <typename Real> struct Smem;
 template <> struct Smem<float> {
-    float2 *ew;        // [NDIM][stride]: {e_k, w_k} (w_k scaled by N on the power-of-two map)
+    float2 *ew;        // [NDIM][stride]: {e_k - w_k, w_k} (w_k scaled by N on the power-of-two map)
     float *h;          // [NDIM][hs]: the f^2 histogram (block's, or this warp's own copy)
     int stride;        // grid slots per axis (kStride, a compile-time constant, in k_sample)
     int hs;            // histogram slots per axis
@@ -362,9 +362,11 @@ template <> struct Smem<double> {
 };
 
 // Map one FP32 coordinate: returns x, multiplies the Jacobian, and gives the
-// axis-local slot of its bin.  Power-of-two N: frac/N = 2^-L (1.frac) - 2^-L
-// straight from the word's bits, x = fma(N w, frac/N, e) (the same value as
-// fma(w, frac, e): the scalings are exact), J *= N w.
+// axis-local slot of its bin.  The grid holds e'_k = e_k - w_k (rounded
+// once from FP64) beside w_k, so with the mantissa trick's 1 + frac the
+// point is x = fma(w, 1 + frac, e') -- w (1 + frac) is exact, one rounding.
+// Power-of-two N: 2^-L (1 + frac) straight from the word's bits and
+// N w_k stored (the scalings are exact), J *= N w.
 template <bool POW2>
 __device__ __forceinline__ float map_f32(unsigned X, int d, int N, const MapParams &m,
                                          const Smem<float> &sm, float &J, int &slot)
@@ -372,20 +374,20 @@ __device__ __forceinline__ float map_f32(unsigned X, int d, int N, const MapPara
     if (POW2) {
         // X is the permuted word (table m.li): slot in the top L bits, the
         // fraction's 23 - L bits at mantissa bits 22..L
-        const float fs = __uint_as_float((X & m.mF) | m.expL) - m.twoNegL;
+        const float f1 = __uint_as_float((X & m.mF) | m.expL);  // 2^-L (1 + frac)
         const int p = (int)(X >> m.sK);
         const float2 ew = sm.ew[d * sm.stride + p];
         J *= ew.y;
         slot = p;
-        return __fmaf_rn(ew.y, fs, ew.x);
+        return __fmaf_rn(ew.y, f1, ew.x);
     } else {
         const unsigned t = (X >> 9) * (unsigned)N;
-        const float frac = __uint_as_float(0x3f800000u | (t & 0x7fffffu)) - 1.0f;
+        const float f1 = __uint_as_float(0x3f800000u | (t & 0x7fffffu));  // 1 + frac
         const int p = (int)(t >> 23);
         const float2 ew = sm.ew[d * sm.stride + p];
         J = J * ((float)N * ew.y);
         slot = p;
-        return __fmaf_rn(ew.y, frac, ew.x);
+        return __fmaf_rn(ew.y, f1, ew.x);
     }
 }
 
@@ -559,7 +561,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
             const double *e = A.edges + (size_t)d * (N + 1);
             const int p = d * kStride + slot_of_bin(k, A.map);
             const double w = e[k + 1] - e[k];
-            sm.ew[p] = make_float2(__double2float_rn(e[k]), __double2float_rn(POW2 ? (double)N * w : w));
+            sm.ew[p] = make_float2(__double2float_rn(e[k] - w), __double2float_rn(POW2 ? (double)N * w : w));
             if (!priv) sm.h[p] = 0.0f;
         }
     } else {
@@ -707,7 +709,7 @@ k_batch_sample(const BatchSampleArgs B)
                 const double *e = it.edges + (size_t)d * (N + 1);
                 const int p = d * stride + slot_of_bin(k, A.map);
                 const double w = e[k + 1] - e[k];
-                sm.ew[p] = make_float2(__double2float_rn(e[k]), __double2float_rn(POW2 ? (double)N * w : w));
+                sm.ew[p] = make_float2(__double2float_rn(e[k] - w), __double2float_rn(POW2 ? (double)N * w : w));
             }
             cur = tile.item;
             __syncthreads();

@@ -68,7 +68,6 @@ struct MapParams {
     int L;                          // log2 N
     unsigned mF;                    // mantissa bits of frac in the permuted word
     unsigned expL;                  // exponent field of 2^-L
-    float twoNegL;                  // 2^-L
     int li;                         // direction table: L - 4 (permuted words), else 0
     unsigned sK;                    // slot = permuted word >> sK, sK = 32 - L
     int priv;                       // per-warp f^2 histograms updated without atomics
@@ -247,7 +246,6 @@ inline MapParams make_map(int N, int ndim, bool fp64)
         m.L = L;
         m.mF = 0x7fffffu & ~((1u << L) - 1u);
         m.expL = (unsigned)(127 - L) << 23;
-        m.twoNegL = ldexpf(1.0f, -L);
         m.li = L - 4;
         m.sK = 32 - L;
         const int blocks = min_blocks_f32(ndim);
