@@ -215,6 +215,13 @@ int cv_genz_callback(const int *ndim, const void *x_dev, const int *ncomp, void 
 /* Number of specialised kernels compiled so far in this process (CV_JIT);
  * *available is 1 if run-time compilation can be used at all. */
 int cv_jit_info(int *available, int *compiled);
+/* Compile (without loading) the specialised sampling kernel CV_JIT would
+ * build for integrand g with nbins bins: a check that run-time
+ * compilation works here and accepts this problem.  Needs no device.
+ * Returns CV_OK, CV_EINVAL for an invalid g or nbins, or CV_ENOTFOUND when
+ * NVRTC is missing or rejects the source; then `log` (log_len bytes,
+ * may be null) receives the reason. */
+int cv_jit_check(const cv_genz *g, int nbins, char *log, int log_len);
 
 /* Bytes cv_vegas moves between host and device per call for an integral of
  * this shape: kernel parameters in (h2d), the final state out (d2h). */

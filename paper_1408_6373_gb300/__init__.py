@@ -158,6 +158,7 @@ _SIGNATURES = {
                       _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_vegas_io_bytes": (_i, [_i, _i, _P(_i64), _P(_i64)]),
     "cv_jit_info": (_i, [_P(_i), _P(_i)]),
+    "cv_jit_check": (_i, [_vp, _i, ctypes.c_char_p, _i]),
     "cv_vegas_noalloc": (_i, [_i, _vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64,
                               _i64, _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_integral_create": (_i, [_vp, _P(Spec), _P(_vp)]),
@@ -373,6 +374,16 @@ def jit_info():
     a, c = ctypes.c_int(), ctypes.c_int()
     lib().cv_jit_info(ctypes.byref(a), ctypes.byref(c))
     return bool(a.value), c.value
+
+
+def jit_check(g: Genz, nbins: int):
+    """cv_jit_check: compile, without loading, the specialised kernel CV_JIT
+    would build for g and nbins.  Returns (ok, reason)."""
+    buf = ctypes.create_string_buffer(512)
+    rc = lib().cv_jit_check(ctypes.byref(g), nbins, buf, len(buf))
+    if rc == EINVAL:
+        raise CubaGpuError(rc, "cv_jit_check")
+    return rc == OK, buf.value.decode(errors="replace")
 
 
 def vegas_io_bytes(ndim: int, nbins: int):

@@ -323,6 +323,21 @@ static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *e
     return CV_OK;
 }
 
+extern "C" int cv_jit_check(const cv_genz *g, int nbins, char *log, int log_len)
+{
+    if (log && log_len > 0) log[0] = '\0';
+    if (check_genz(nullptr, g) || nbins < CV_MIN_BINS || nbins > CV_MAX_BINS) return CV_EINVAL;
+    SampleArgs<float> a;
+    memset(&a, 0, sizeof(a));
+    fill_params<float>(g, &a.g);
+    a.nbins = nbins;
+    a.map = make_map(nbins, g->ndim, false);
+    std::string err;
+    const int rc = jit_compile_check(a, g->ndim, a.map.pow2 != 0, min_blocks_f32(g->ndim), &err);
+    if (rc && log && log_len > 0) snprintf(log, (size_t)log_len, "%s", err.c_str());
+    return rc ? CV_ENOTFOUND : CV_OK;
+}
+
 extern "C" int cv_jit_info(int *available, int *compiled)
 {
     int c = 0;
@@ -1846,29 +1861,22 @@ extern "C" int cv_server_stop(cv_server *S)
 
 // ------------------------------------------------------------ user integrands
 namespace cv {
-#define CV_EXTERN_M(D)                                                                               \
-    extern template cudaError_t launch_materialise<D, float, false>(const MatArgs<float> &, int, cudaStream_t);   \
-    extern template cudaError_t launch_materialise<D, float, true>(const MatArgs<float> &, int, cudaStream_t);    \
-    extern template cudaError_t launch_materialise<D, double, false>(const MatArgs<double> &, int, cudaStream_t); \
-    extern template cudaError_t launch_materialise<D, double, true>(const MatArgs<double> &, int, cudaStream_t);  \
-    extern template cudaError_t launch_accumulate<D, float, false>(const MatArgs<float> &, int, cudaStream_t);    \
-    extern template cudaError_t launch_accumulate<D, float, true>(const MatArgs<float> &, int, cudaStream_t);     \
-    extern template cudaError_t launch_accumulate<D, double, false>(const MatArgs<double> &, int, cudaStream_t);  \
-    extern template cudaError_t launch_accumulate<D, double, true>(const MatArgs<double> &, int, cudaStream_t);
+#define CV_EXTERN_M(D)                                                                          \
+    extern template cudaError_t launch_matpass<D, float, 1>(const SampleArgs<float> &, int, cudaStream_t);   \
+    extern template cudaError_t launch_matpass<D, float, 2>(const SampleArgs<float> &, int, cudaStream_t);   \
+    extern template cudaError_t launch_matpass<D, double, 1>(const SampleArgs<double> &, int, cudaStream_t); \
+    extern template cudaError_t launch_matpass<D, double, 2>(const SampleArgs<double> &, int, cudaStream_t);
 CV_FOR_EACH_NDIM(CV_EXTERN_M)
 #undef CV_EXTERN_M
 
+// acc = false: store the points; acc = true: accumulate the caller's values
 template <typename Real>
-static cudaError_t dispatch_matpass(int ndim, bool aos, bool acc, const MatArgs<Real> &a, int grid,
-                                    cudaStream_t s)
+static cudaError_t dispatch_matpass(int ndim, bool acc, const SampleArgs<Real> &a, int grid, cudaStream_t s)
 {
     switch (ndim) {
 #define CV_CASE(D)                                                                       \
     case D:                                                                              \
-        if (acc) return aos ? launch_accumulate<D, Real, true>(a, grid, s)              \
-                            : launch_accumulate<D, Real, false>(a, grid, s);             \
-        return aos ? launch_materialise<D, Real, true>(a, grid, s)                       \
-                   : launch_materialise<D, Real, false>(a, grid, s);
+        return acc ? launch_matpass<D, Real, 2>(a, grid, s) : launch_matpass<D, Real, 1>(a, grid, s);
         CV_FOR_EACH_NDIM(CV_CASE)
 #undef CV_CASE
     }
@@ -1954,18 +1962,27 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     ca.maxeval = sp.maxeval;
     ca.nstart = sp.nstart;
     ca.nincrease = sp.nincrease;
-    MatArgs<Real> a;
+    SampleArgs<Real> a;
     memset(&a, 0, sizeof(a));
+    a.g.ndim = ndim;
+    a.g.ncomp = ncomp;
     a.nbins = N;
-    a.ncomp = ncomp;
+    a.chunk_min = 4;
     a.map = make_map(N, ndim, sizeof(Real) == 8);
     a.edges = edges;
     a.ld = tile;
+    a.aos = aos ? 1 : 0;
     a.x = x;
     a.f = f;
     a.S1 = st->S1;
     a.S2 = st->S2;
     a.H = H;
+    int occ = 0;
+    rc = occupancy(ctx, ndim, N, sizeof(Real) == 8, &occ);
+    if (rc) {
+        cudaFree(mem);
+        return rc;
+    }
     const int one = 1;
     int aborted = 0;
     cudaError_t e = launch_reset(st, edges, H, ndim, N, sp.nstart, s);
@@ -1976,10 +1993,9 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
             const long long m = nj - off < tile ? nj - off : tile;
             a.start = start + (unsigned long long)off;
             a.n = m;
-            long long grid = (m + 32 * 8 * 16 - 1) / (32 * 8 * 16);
-            if (grid > (long long)ctx->sms * 4) grid = (long long)ctx->sms * 4;
-            if (grid < 1) grid = 1;
-            e = dispatch_matpass<Real>(ndim, aos, false, a, (int)grid, s);
+            // (the same grid as a fused pass: the kernels share its occupancy)
+            const int grid = sample_grid(ctx, occ, m);
+            e = dispatch_matpass<Real>(ndim, false, a, grid, s);
             if (e != cudaSuccess) break;
             const int64_t nv = m, ld = tile;
             const int r = cb(&ndim, x, &ncomp, f, userdata, &nv, &ld, (void *)s);
@@ -1987,7 +2003,7 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
                 aborted = 1;
                 break;
             }
-            e = dispatch_matpass<Real>(ndim, aos, true, a, (int)grid, s);
+            e = dispatch_matpass<Real>(ndim, true, a, grid, s);
         }
         if (aborted || e != cudaSuccess) break;
         e = cudaMemcpyAsync(&st->pass_active, &one, sizeof(int), cudaMemcpyHostToDevice, s);

@@ -166,6 +166,7 @@ __device__ __forceinline__ float ipow(float r)
 // become instruction immediates.
 template <typename Real>
 struct RuntimeIntegrand {
+    static constexpr int kMode = 0;  // the integrand is evaluated in the pass
     template <int C> __device__ __forceinline__ static int family(const GenzParams<Real> &g) { return g.family[C]; }
     __device__ __forceinline__ static int ncomp(const GenzParams<Real> &g) { return g.ncomp; }
     template <int C> __device__ __forceinline__ static Real p0(const GenzParams<Real> &g, int d) { return g.p0[C][d]; }
@@ -174,6 +175,14 @@ struct RuntimeIntegrand {
     __device__ __forceinline__ static int table(const MapParams &m) { return m.li; }
     __device__ __forceinline__ static bool priv(const MapParams &m) { return m.priv != 0; }
     __device__ __forceinline__ static int nbins(int n) { return n; }
+};
+
+// Materialised samples (the caller's integrand): the same pass either
+// stores the mapped points (MODE 1) or accumulates the caller's values
+// read back from HBM (MODE 2) instead of evaluating a Genz integrand.
+template <typename Real, int MODE>
+struct MatIntegrand : RuntimeIntegrand<Real> {
+    static constexpr int kMode = MODE;
 };
 
 // FP32 Genz evaluation of component C.
@@ -448,11 +457,37 @@ __device__ __forceinline__ void sample_block(const SampleArgs<Real> &A, const Sm
         else
             x[d] = map_f64(X[d], d, N, sm, J, slot[d]);
     }
+    const long long j = (long long)(q * 32ull + (unsigned long long)lane - start);  // materialised slot
+    if constexpr (I::kMode == 1) {
+        // store the point for the caller's integrand
+        if (!EDGE || valid) {
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                if (A.aos) A.x[j * NDIM + d] = x[d];
+                else A.x[(long long)d * A.ld + j] = x[d];
+            }
+        }
+        return;
+    }
     Real f0 = Real(0);
-    eval_comp<NDIM, 0, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-    eval_comp<NDIM, 1, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-    eval_comp<NDIM, 2, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-    eval_comp<NDIM, 3, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+    if constexpr (I::kMode == 2) {
+        // the caller's values
+#pragma unroll
+        for (int c = 0; c < CV_MAX_COMP; ++c) {
+            if (c < A.g.ncomp) {
+                Real v = Real(0);
+                if (!EDGE || valid) v = J * (A.aos ? A.f[j * A.g.ncomp + c] : A.f[(long long)c * A.ld + j]);
+                p1[c] += v;
+                p2[c] += v * v;
+                if (c == 0) f0 = v;
+            }
+        }
+    } else {
+        eval_comp<NDIM, 0, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+        eval_comp<NDIM, 1, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+        eval_comp<NDIM, 2, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+        eval_comp<NDIM, 3, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+    }
     if (!EDGE || valid) {
         const Real h = f0 * f0;
         if (priv) {
@@ -552,7 +587,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
     if constexpr (sizeof(Real) == 4) {
         sm.ew = reinterpret_cast<float2 *>(smem_raw);
         sm.h = reinterpret_cast<float *>(sm.ew + NDIM * kStride);
-        if (priv) {
+        if (priv && I::kMode != 1) {
             // [kWarpsPerBlock][NDIM][N]: every warp's own copy
             for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * N; i += blockDim.x) sm.h[i] = 0.0f;
         }
@@ -608,6 +643,8 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         else
             run_steps<NDIM, Real, POW2, true, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
     }
+
+    if constexpr (I::kMode == 1) return;  // points stored: nothing to reduce
 
     // Reduction: warp, then across the block's warps in FP64.
     __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
@@ -769,125 +806,17 @@ k_batch_sample(const BatchSampleArgs B)
 }
 
 // ------------------------------------------------------------ materialised samples
-// The two halves of a pass whose integrand is the caller's: k_materialise
-// writes the mapped points (32 consecutive indices per warp and dimension:
-// fully coalesced SoA stores), k_accumulate reads the caller's f back and
-// recomputes each point's bins and Jacobian from its Sobol index (nothing
-// but x and f goes through HBM).  Generic bin layout (slot = bin).
-template <int NDIM, typename Real>
-__device__ __forceinline__ void stage_generic(const double *edges, int N, Real *se, Real *sw, int tid, int nth)
+// The two halves of a pass whose integrand is the caller's, both the fused
+// pass with a different integrand policy: MODE 1 writes the mapped points
+// (dimension-major: each warp store covers 32 consecutive points, fully
+// coalesced; or the paper's point-major layout), MODE 2 reads the caller's
+// values back and accumulates them, recomputing each point's bins and
+// Jacobian from its Sobol index -- nothing but x and f goes through HBM.
+template <int NDIM, typename Real, bool POW2, int MODE>
+__global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, Real>))
+k_matpass(const __grid_constant__ SampleArgs<Real> A)
 {
-    for (int idx = tid; idx < NDIM * N; idx += nth) {
-        const int d = idx / N, k = idx - d * N;
-        const double *e = edges + (size_t)d * (N + 1);
-        se[idx] = (Real)e[k];
-        sw[idx] = (Real)(e[k + 1] - e[k]);
-    }
-}
-
-template <typename Real>
-__device__ __forceinline__ Real map_generic(typename Word<Real>::type X, int d, int N, const Real *se,
-                                            const Real *sw, Real &J, int &k)
-{
-    Real frac;
-    if constexpr (sizeof(Real) == 4) {
-        const unsigned t = (X >> 9) * (unsigned)N;
-        frac = __uint_as_float(0x3f800000u | (t & 0x7fffffu)) - 1.0f;
-        k = (int)(t >> 23);
-    } else {
-        const unsigned long long t = (X >> 12) * (unsigned long long)N;
-        frac = __longlong_as_double((long long)(0x3ff0000000000000ull | (t & 0xfffffffffffffull))) - 1.0;
-        k = (int)(t >> 52);
-    }
-    const Real w = sw[d * N + k];
-    J = J * ((Real)N * w);
-    return fma_rn(w, frac, se[d * N + k]);
-}
-
-template <int NDIM, typename Real, bool AOS, bool ACC>
-__global__ void __launch_bounds__(kBlock) k_matpass(const MatArgs<Real> A)
-{
-    using W = typename Word<Real>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = A.nbins;
-    Real *se = reinterpret_cast<Real *>(smem_raw);
-    Real *sw = se + NDIM * N;
-    Real *sh = sw + NDIM * N;  // histogram (accumulate pass)
-    stage_generic<NDIM, Real>(A.edges, N, se, sw, threadIdx.x, blockDim.x);
-    if (ACC)
-        for (int i = threadIdx.x; i < NDIM * N; i += blockDim.x) sh[i] = Real(0);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const unsigned long long start = A.start, end = A.start + (unsigned long long)A.n;
-    const unsigned long long qa = start >> 5, qb = (end + 31ull) >> 5;
-    const unsigned long long nblk = A.n > 0 ? qb - qa : 0ull;
-    const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const unsigned long long twarps = (unsigned long long)gridDim.x * kWarpsPerBlock;
-    unsigned long long plen = (nblk + twarps - 1) / twarps;
-    if (plen < 4) plen = 4;
-    const unsigned long long nchunk = (nblk + plen - 1) / plen;
-    Acc<Real> s1[CV_MAX_COMP], s2[CV_MAX_COMP];
-    for (unsigned long long ch = gwarp; ch < nchunk; ch += twarps) {
-        const unsigned long long q0 = qa + ch * plen, q1 = min(q0 + plen, qb);
-        W X[NDIM];
-        sobol_skip<NDIM, W>(X, q0, lane);
-        for (unsigned long long q = q0; q < q1; ++q) {
-            const unsigned long long i = q * 32ull + (unsigned long long)lane;
-            const bool valid = i >= start && i < end;
-            const long long j = (long long)(i - start);
-            Real J = Real(1);
-            int kb[NDIM];
-            Real x[NDIM];
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d) x[d] = map_generic<Real>(X[d], d, N, se, sw, J, kb[d]);
-            if (valid) {
-                if (!ACC) {
-#pragma unroll
-                    for (int d = 0; d < NDIM; ++d) {
-                        if (AOS) A.x[j * NDIM + d] = x[d];
-                        else A.x[(long long)d * A.ld + j] = x[d];
-                    }
-                } else {
-                    Real f0 = Real(0);
-#pragma unroll
-                    for (int c = 0; c < CV_MAX_COMP; ++c) {
-                        if (c < A.ncomp) {
-                            const Real f = AOS ? A.f[j * A.ncomp + c] : A.f[(long long)c * A.ld + j];
-                            const Real v = J * f;
-                            s1[c].add(v);
-                            s2[c].add(v * v);
-                            if (c == 0) f0 = v;
-                        }
-                    }
-#pragma unroll
-                    for (int d = 0; d < NDIM; ++d) atomicAdd(&sh[d * N + kb[d]], f0 * f0);
-                }
-            }
-            if (q + 1 < q1) sobol_step<NDIM, W>(X, q);
-        }
-    }
-    if (!ACC) return;
-    __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
-    const int warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int c = 0; c < CV_MAX_COMP; ++c) {
-        if (c < A.ncomp) {
-            const double a = warp_total(s1[c]);
-            const double b = warp_total(s2[c]);
-            if (lane == 0) {
-                red[warp][2 * c] = a;
-                red[warp][2 * c + 1] = b;
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 2 * A.ncomp) {
-        double t = 0.0;
-        for (int w = 0; w < kWarpsPerBlock; ++w) t += red[w][threadIdx.x];
-        atomicAdd((threadIdx.x & 1) ? &A.S2[threadIdx.x >> 1] : &A.S1[threadIdx.x >> 1], t);
-    }
-    for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x)
-        if (sh[idx] != Real(0)) atomicAdd(&A.H[idx], (double)sh[idx]);
+    sample_pass<NDIM, Real, POW2, MatIntegrand<Real, MODE>>(A);
 }
 
 // Built-in integrand on materialised points (the library's own callback):
@@ -1021,28 +950,24 @@ cudaError_t batch_occupancy(bool pow2, int stride, int *blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBlock, want);
 }
 
-template <int NDIM, typename Real, bool AOS, bool ACC>
-static cudaError_t launch_matpass(const MatArgs<Real> &a, int grid, cudaStream_t s)
+template <int NDIM, typename Real, bool POW2, int MODE>
+static cudaError_t launch_matpass_v(const SampleArgs<Real> &a, int grid, cudaStream_t s)
 {
-    const size_t smem = (size_t)3 * NDIM * a.nbins * sizeof(Real);
-    cudaError_t e = cudaFuncSetAttribute(k_matpass<NDIM, Real, AOS, ACC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)3 * NDIM * CV_MAX_BINS * sizeof(Real)));
+    const size_t smem = sample_smem_bytes(NDIM, a.nbins, sizeof(Real) == 8, a.map.priv != 0);
+    cudaError_t e = cudaFuncSetAttribute(k_matpass<NDIM, Real, POW2, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_matpass<NDIM, Real, AOS, ACC><<<grid, kBlock, smem, s>>>(a);
+    k_matpass<NDIM, Real, POW2, MODE><<<grid, kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int NDIM, typename Real, bool AOS>
-cudaError_t launch_materialise(const MatArgs<Real> &a, int grid, cudaStream_t s)
+template <int NDIM, typename Real, int MODE>
+cudaError_t launch_matpass(const SampleArgs<Real> &a, int grid, cudaStream_t s)
 {
-    return launch_matpass<NDIM, Real, AOS, false>(a, grid, s);
-}
-
-template <int NDIM, typename Real, bool AOS>
-cudaError_t launch_accumulate(const MatArgs<Real> &a, int grid, cudaStream_t s)
-{
-    return launch_matpass<NDIM, Real, AOS, true>(a, grid, s);
+    if constexpr (sizeof(Real) == 4) {
+        if (a.map.pow2) return launch_matpass_v<NDIM, float, true, MODE>(a, grid, s);
+    }
+    return launch_matpass_v<NDIM, Real, false, MODE>(a, grid, s);
 }
 
 template <int NDIM, typename Real, bool AOS>
@@ -1078,14 +1003,10 @@ cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
     template cudaError_t cv::launch_batch_sample<D, false>(const cv::BatchSampleArgs &, int, \
                                                            cudaStream_t);                   \
     template cudaError_t cv::batch_occupancy<D>(bool, int, int *);                          \
-    template cudaError_t cv::launch_materialise<D, float, false>(const cv::MatArgs<float> &, int, cudaStream_t);   \
-    template cudaError_t cv::launch_materialise<D, float, true>(const cv::MatArgs<float> &, int, cudaStream_t);    \
-    template cudaError_t cv::launch_materialise<D, double, false>(const cv::MatArgs<double> &, int, cudaStream_t); \
-    template cudaError_t cv::launch_materialise<D, double, true>(const cv::MatArgs<double> &, int, cudaStream_t);  \
-    template cudaError_t cv::launch_accumulate<D, float, false>(const cv::MatArgs<float> &, int, cudaStream_t);    \
-    template cudaError_t cv::launch_accumulate<D, float, true>(const cv::MatArgs<float> &, int, cudaStream_t);     \
-    template cudaError_t cv::launch_accumulate<D, double, false>(const cv::MatArgs<double> &, int, cudaStream_t);  \
-    template cudaError_t cv::launch_accumulate<D, double, true>(const cv::MatArgs<double> &, int, cudaStream_t);   \
+    template cudaError_t cv::launch_matpass<D, float, 1>(const cv::SampleArgs<float> &, int, cudaStream_t);      \
+    template cudaError_t cv::launch_matpass<D, float, 2>(const cv::SampleArgs<float> &, int, cudaStream_t);      \
+    template cudaError_t cv::launch_matpass<D, double, 1>(const cv::SampleArgs<double> &, int, cudaStream_t);    \
+    template cudaError_t cv::launch_matpass<D, double, 2>(const cv::SampleArgs<double> &, int, cudaStream_t);    \
     template cudaError_t cv::launch_genz_points<D, float, false>(const cv::GenzParams<float> &, const float *, float *, long long, long long, int, cudaStream_t); \
     template cudaError_t cv::launch_genz_points<D, float, true>(const cv::GenzParams<float> &, const float *, float *, long long, long long, int, cudaStream_t); \
     template cudaError_t cv::launch_genz_points<D, double, false>(const cv::GenzParams<double> &, const double *, double *, long long, long long, int, cudaStream_t); \

@@ -90,6 +90,13 @@ struct SampleArgs {
     unsigned long long start;
     long long n;
     DevState *st;
+    // materialised samples (the caller's integrand): the points written to
+    // x, the values read from f, point j = index - start of the launch at
+    // x[d ld + j], f[c ld + j] (aos = 0) or x[j ndim + d], f[j ncomp + c]
+    Real *x;
+    const Real *f;
+    long long ld;
+    int aos;
 };
 
 struct CombineArgs {
@@ -99,25 +106,6 @@ struct CombineArgs {
     long long mineval, maxeval, nstart, nincrease;
     double *log_I;                  // [kLogCap][CV_MAX_COMP] or null
     double *log_var;
-};
-
-// ---- materialised samples (user integrand) ----
-// One tile of n points (Sobol indices start..start+n-1) written out as x and,
-// after the user's integrand has filled f, accumulated like a fused pass.
-// Layout: SoA x[d*ld + j], f[c*ld + j]; AoS (the paper's integrand
-// contract) x[j*ndim + d], f[j*ncomp + c].
-template <typename Real>
-struct MatArgs {
-    int nbins;
-    int ncomp;
-    MapParams map;
-    const double *edges;
-    unsigned long long start;
-    long long n;
-    long long ld;
-    Real *x;
-    const Real *f;
-    double *S1, *S2, *H;
 };
 
 // ---- batched persistent launch (many integrals) ----
@@ -166,10 +154,10 @@ template <int NDIM, typename Word>
 cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
                          unsigned long long *Y, int grid, cudaStream_t s);
 
-template <int NDIM, typename Real, bool AOS>
-cudaError_t launch_materialise(const MatArgs<Real> &a, int grid, cudaStream_t s);
-template <int NDIM, typename Real, bool AOS>
-cudaError_t launch_accumulate(const MatArgs<Real> &a, int grid, cudaStream_t s);
+// materialised samples: store the points (mode 1) or accumulate the
+// caller's values (mode 2) over [a.start, a.start + a.n)
+template <int NDIM, typename Real, int MODE>
+cudaError_t launch_matpass(const SampleArgs<Real> &a, int grid, cudaStream_t s);
 
 template <int NDIM, typename Real, bool AOS>
 cudaError_t launch_genz_points(const GenzParams<Real> &g, const Real *x, Real *f, long long n,
@@ -203,6 +191,8 @@ struct JitKernel {
 namespace cv {
 int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks,
                       JitKernel *out, std::string *err);
+// compile the specialised source without loading it (checks NVRTC and the source)
+int jit_compile_check(const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks, std::string *err);
 cudaError_t launch_jit_sample(const JitKernel &k, const SampleArgs<float> &a, int grid, cudaStream_t s);
 int jit_info(int *compiled);
 #endif  // !__CUDACC_RTC__

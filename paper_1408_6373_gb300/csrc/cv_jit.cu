@@ -87,6 +87,7 @@ std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, 
 {
     const GenzParams<float> &g = a.g;
     std::string s = "#include \"cv_device.cuh\"\nnamespace cv {\nstruct JitIntegrand {\n";
+    s += "  static constexpr int kMode = 0;\n";
     s += "  template <int C> __device__ __forceinline__ static constexpr int family(const GenzParams<float>&) { constexpr int f[4] = {";
     for (int c = 0; c < 4; ++c) s += std::to_string(c < g.ncomp ? g.family[c] : CV_CONST) + (c < 3 ? "," : "");
     s += "}; return f[C]; }\n";
@@ -130,17 +131,9 @@ std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, 
 
 }  // namespace
 
-int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks,
-                      JitKernel *out, std::string *err)
+// Compile a specialised source to a cubin (NVRTC; no device needed).
+int compile_source(const std::string &src, std::vector<char> *cubin, std::string *err)
 {
-    const std::string src = specialised_source(a, ndim, pow2, min_blocks);
-    const std::string key = std::to_string(device) + "\n" + src;
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_cache.find(key);
-    if (it != g_cache.end()) {
-        *out = it->second;
-        return 0;
-    }
     if (!load_nvrtc(err)) return -1;
     nvrtcProgram prog;
     if (g_nvrtc.create(&prog, src.c_str(), "cv_jit_sample.cu", kJitHeaderCount, kJitHeaderTexts,
@@ -163,9 +156,32 @@ int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow
     }
     size_t n = 0;
     g_nvrtc.cubin_size(prog, &n);
-    std::vector<char> cubin(n);
-    g_nvrtc.cubin(prog, cubin.data());
+    cubin->resize(n);
+    g_nvrtc.cubin(prog, cubin->data());
     g_nvrtc.destroy(&prog);
+    return 0;
+}
+
+int jit_compile_check(const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks, std::string *err)
+{
+    std::vector<char> cubin;
+    std::lock_guard<std::mutex> lk(g_mu);
+    return compile_source(specialised_source(a, ndim, pow2, min_blocks), &cubin, err);
+}
+
+int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks,
+                      JitKernel *out, std::string *err)
+{
+    const std::string src = specialised_source(a, ndim, pow2, min_blocks);
+    const std::string key = std::to_string(device) + "\n" + src;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        *out = it->second;
+        return 0;
+    }
+    std::vector<char> cubin;
+    if (compile_source(src, &cubin, err)) return -1;
     JitKernel k;
     if (cudaLibraryLoadData(&k.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
         cudaLibraryGetKernel(&k.kernel, k.lib, "cv_jit_sample") != cudaSuccess) {
