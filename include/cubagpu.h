@@ -194,7 +194,10 @@ typedef int (*cv_integrand_dev)(const int *ndim, const void *x_dev, const int *n
  * per tile, and the values are accumulated, with bins and Jacobians
  * recomputed from the Sobol index.  Arguments and results as cv_vegas;
  * flags may add CV_AOS.  Returns CV_EABORT (and *fail = -999) when the
- * integrand returns -999. */
+ * integrand returns -999.  The points, values and state live in a device
+ * scratch area of the context (about (ndim + ncomp) * nvec values), grown
+ * on demand and kept until cv_destroy, so calls on one context must not
+ * overlap. */
 int cv_vegas_cb(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev integrand,
                 void *userdata, int64_t nvec, double epsrel, double epsabs,
                 int flags, int seed, int64_t mineval, int64_t maxeval,

@@ -86,6 +86,12 @@ struct cv_ctx {
     std::set<struct cv_integral *> integrals;
     std::set<struct cv_batch *> batches;
     std::set<struct cv_server *> servers;
+    // materialised-sample scratch (state, grid, histogram, x, f), grown on
+    // demand and kept until cv_destroy; pinned words for the per-iteration
+    // stop check of that mode
+    void *mat_mem = nullptr;
+    size_t mat_cap = 0;
+    int *pinned = nullptr;  // [0] = 1 (pass_active), [1] = stopped read back
 };
 
 static void integral_free(struct cv_integral *I);
@@ -191,6 +197,8 @@ extern "C" void cv_destroy(cv_ctx *ctx)
         if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->mat_mem) cudaFree(ctx->mat_mem);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -1939,12 +1947,29 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     const size_t sz_H = (((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255;
     const size_t sz_x = (((size_t)ndim * tile * sizeof(Real)) + 255) & ~(size_t)255;
     const size_t sz_f = (size_t)ncomp * tile * sizeof(Real);
-    void *mem = nullptr;
-    if (cudaMalloc(&mem, sz_state + sz_edges + sz_H + sz_x + sz_f) != cudaSuccess) {
-        cudaGetLastError();
-        return fail_msg(ctx, CV_ENOMEM, "device allocation for %lld materialised points failed", tile);
+    const size_t need = sz_state + sz_edges + sz_H + sz_x + sz_f;
+    if (!ctx->pinned) {
+        if (cudaHostAlloc((void **)&ctx->pinned, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->pinned = nullptr;
+            return fail_msg(ctx, CV_ENOMEM, "pinned host allocation failed");
+        }
     }
-    char *p = (char *)mem;
+    if (need > ctx->mat_cap) {
+        // the previous scratch may still be in use by work on the stream
+        CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->mat_mem) cudaFree(ctx->mat_mem);
+        ctx->mat_mem = nullptr;
+        ctx->mat_cap = 0;
+        if (cudaMalloc(&ctx->mat_mem, need) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->mat_mem = nullptr;
+            return fail_msg(ctx, CV_ENOMEM, "device allocation for %lld materialised points failed", tile);
+        }
+        ctx->mat_cap = need;
+    }
+    int *const pin = ctx->pinned;
+    char *p = (char *)ctx->mat_mem;
     DevState *st = (DevState *)p;
     double *edges = (double *)(p + sz_state);
     double *H = (double *)(p + sz_state + sz_edges);
@@ -1979,11 +2004,8 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     a.H = H;
     int occ = 0;
     rc = occupancy(ctx, ndim, N, sizeof(Real) == 8, &occ);
-    if (rc) {
-        cudaFree(mem);
-        return rc;
-    }
-    const int one = 1;
+    if (rc) return rc;
+    pin[0] = 1;
     int aborted = 0;
     cudaError_t e = launch_reset(st, edges, H, ndim, N, sp.nstart, s);
     unsigned long long start = 1;
@@ -2006,13 +2028,12 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
             e = dispatch_matpass<Real>(ndim, true, a, grid, s);
         }
         if (aborted || e != cudaSuccess) break;
-        e = cudaMemcpyAsync(&st->pass_active, &one, sizeof(int), cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(&st->pass_active, &pin[0], sizeof(int), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = launch_refine_combine(ndim, N, H, edges, ca, s);
-        int stopped = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&stopped, &st->stopped, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&pin[1], &st->stopped, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         start += (unsigned long long)nj;
-        if (stopped) break;
+        if (pin[1]) break;
     }
     if (e != cudaSuccess) rc = cuda_fail(ctx, e, "materialised pass");
     DevState h;
@@ -2023,7 +2044,6 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
         if (e != cudaSuccess) rc = cuda_fail(ctx, e, "result copy");
     }
     cudaStreamSynchronize(s);
-    cudaFree(mem);
     if (rc) return rc;
     memset(res, 0, sizeof(*res));
     res->neval = h.neval;

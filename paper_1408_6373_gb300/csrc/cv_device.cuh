@@ -432,14 +432,36 @@ __device__ __forceinline__ void eval_comp(const GenzParams<Real> &g, const Real 
     }
 }
 
+// The caller's values of this lane's point in block q (materialised
+// samples, accumulate mode), 0 outside [start, end).
+template <int NDIM, typename Real, bool EDGE>
+__device__ __forceinline__ void load_values(const SampleArgs<Real> &A, unsigned long long q,
+                                            unsigned long long start, unsigned long long end, int lane,
+                                            Real (&fv)[CV_MAX_COMP])
+{
+    const unsigned long long i = q * 32ull + (unsigned long long)lane;
+    const bool valid = !EDGE || (i >= start && i < end);
+    const long long j = (long long)(i - start);
+    // both layouts as strides: value c of point j at f[j sj + c sc]
+    const long long sj = A.aos ? A.g.ncomp : 1, sc = A.aos ? 1 : A.ld;
+    const Real *fp = A.f + j * sj;
+#pragma unroll
+    for (int c = 0; c < CV_MAX_COMP; ++c) {
+        fv[c] = Real(0);
+        if (c < A.g.ncomp && valid) fv[c] = fp[c * sc];
+    }
+}
+
 // One aligned 32-point block q: map, integrand, partial sums, histogram.
 // EDGE: the block may hold indices outside [start, end), which add nothing.
+// fv: the caller's values of the block (accumulate mode only).
 template <int NDIM, typename Real, bool POW2, bool EDGE, class I>
 __device__ __forceinline__ void sample_block(const SampleArgs<Real> &A, const Smem<Real> &sm,
                                              const typename Word<Real>::type (&X)[NDIM],
                                              unsigned long long q, unsigned long long start,
                                              unsigned long long end, int lane, bool priv,
-                                             Real (&p1)[CV_MAX_COMP], Real (&p2)[CV_MAX_COMP])
+                                             Real (&p1)[CV_MAX_COMP], Real (&p2)[CV_MAX_COMP],
+                                             const Real (&fv)[CV_MAX_COMP])
 {
     const int N = I::nbins(A.nbins);
     bool valid = true;
@@ -461,22 +483,21 @@ __device__ __forceinline__ void sample_block(const SampleArgs<Real> &A, const Sm
     if constexpr (I::kMode == 1) {
         // store the point for the caller's integrand
         if (!EDGE || valid) {
+            // both layouts as strides: coordinate d of point j at x[j sj + d sd]
+            const long long sj = A.aos ? NDIM : 1, sd = A.aos ? 1 : A.ld;
+            Real *xp = A.x + j * sj;
 #pragma unroll
-            for (int d = 0; d < NDIM; ++d) {
-                if (A.aos) A.x[j * NDIM + d] = x[d];
-                else A.x[(long long)d * A.ld + j] = x[d];
-            }
+            for (int d = 0; d < NDIM; ++d) xp[d * sd] = x[d];
         }
         return;
     }
     Real f0 = Real(0);
     if constexpr (I::kMode == 2) {
-        // the caller's values
+        // the caller's values (loaded ahead by the caller of this function)
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c) {
             if (c < A.g.ncomp) {
-                Real v = Real(0);
-                if (!EDGE || valid) v = J * (A.aos ? A.f[j * A.g.ncomp + c] : A.f[(long long)c * A.ld + j]);
+                const Real v = J * fv[c];
                 p1[c] += v;
                 p2[c] += v * v;
                 if (c == 0) f0 = v;
@@ -533,12 +554,19 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
         for (int c = 0; c < CV_MAX_COMP; ++c) p1[c] = p2[c] = Real(0);
         for (unsigned st = r0; st < r1; st += per) {
             const unsigned long long q = q0 + st;
-            sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2);
+            // accumulate mode: both blocks' values are requested before any
+            // arithmetic, so their latency overlaps the map
+            Real fa[CV_MAX_COMP], fb[CV_MAX_COMP];
+            if constexpr (I::kMode == 2) {
+                load_values<NDIM, Real, EDGE>(A, q, start, end, lane, fa);
+                if (!EDGE) load_values<NDIM, Real, EDGE>(A, q + 1, start, end, lane, fb);
+            }
+            sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2, fa);
             if (EDGE) {
                 sobol_step<NDIM, W>(X, q, li);
             } else {
                 sobol_step_even<NDIM, W>(X, li);
-                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2);
+                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2, fb);
                 sobol_step<NDIM, W>(X, q + 1, li);
             }
         }
@@ -627,6 +655,10 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
     const unsigned long long twarps = (unsigned long long)gridDim.x * kWarpsPerBlock;
     unsigned long long plen = (nblk + twarps - 1) / twarps;
     if (plen < (unsigned long long)A.chunk_min) plen = A.chunk_min;
+    // materialised samples: short chunks taken in rounds, so that at any
+    // time all warps read or write within one window of the point arrays
+    // (DRAM locality) instead of one long stretch each
+    if (I::kMode != 0 && plen > kRun) plen = kRun;
     plen = (plen + 1ull) & ~1ull;
     const unsigned long long nchunk = (nblk + plen - 1) / plen;
 
