@@ -585,7 +585,7 @@ def measure_serve(ctx, cg, W, duration: float = 1.0, rate: float = 2000.0,
             "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": st.max_ms,
             "throughput": {"value": samples / wall, "unit": UNIT},
             "requests_per_s": len(reqs) / wall, "rounds": st.rounds, "max_live": st.max_live,
-            "wall_s": wall, "busy_s": st.busy_s,
+            "wall_s": wall, "busy_s": st.busy_s, "gpu_s": st.gpu_s,
             "served_first_requests": {"requests": plain_subset, "p50_ms": st_sub.p50_ms,
                                       "p99_ms": st_sub.p99_ms},
             "plain_fp64_fifo": {"requests": len(service), "p50_ms": q(0.5), "p99_ms": q(0.99),

@@ -384,6 +384,7 @@ typedef struct {
     int pending;               /* requests waiting for admission now          */
     double p50_ms, p99_ms, max_ms;  /* submit-to-result latency               */
     double busy_s, wall_s;     /* time in rounds, time since start            */
+    double gpu_s;              /* device time of the rounds (CUDA events)     */
 } cv_serve_stats;
 
 typedef struct cv_server cv_server;

@@ -124,7 +124,7 @@ class ServeStats(ctypes.Structure):
                 ("max_live", ctypes.c_int), ("pending", ctypes.c_int),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("busy_s", ctypes.c_double),
-                ("wall_s", ctypes.c_double)]
+                ("wall_s", ctypes.c_double), ("gpu_s", ctypes.c_double)]
 
 
 _P = ctypes.POINTER

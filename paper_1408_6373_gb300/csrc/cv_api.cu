@@ -1447,12 +1447,13 @@ struct cv_server {
     // statistics
     int64_t submitted = 0, completed = 0, rounds = 0, samples = 0;
     int max_live_seen = 0;
-    double busy_s = 0;
+    double busy_s = 0, gpu_s = 0;
     Clock::time_point t_start;
     // device resources (worker thread only)
     cudaStream_t stream = nullptr;
     cudaStream_t side[kSideStreams] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[kSideStreams] = {};
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // device time of a round
     void *arena_mem = nullptr;
     BatchItem *d_items = nullptr;
     CombineArgs *d_cargs = nullptr;
@@ -1498,6 +1499,7 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         if ((int)live.size() > S->max_live_seen) S->max_live_seen = (int)live.size();
     }
     const auto t0 = Clock::now();
+    CV_CUDA(ctx, cudaEventRecord(S->ev_t0, S->stream));
     // descriptors of newly admitted requests
     const size_t sz_state = (sizeof(DevState) + 255) & ~(size_t)255;
     for (const Request &r : live) {
@@ -1626,14 +1628,18 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
     CV_CUDA(ctx, launch_batch_combine(S->d_cargs, nlive, S->stream, S->d_lists + nfresh));
     CV_CUDA(ctx, launch_gather_states(S->d_items, S->d_lists + nfresh, nlive, S->d_gather, S->stream));
     CV_CUDA(ctx, cudaMemcpyAsync(S->h_gather, S->d_gather, nlive * sizeof(DevState), cudaMemcpyDeviceToHost, S->stream));
+    CV_CUDA(ctx, cudaEventRecord(S->ev_t1, S->stream));
     CV_CUDA(ctx, cudaStreamSynchronize(S->stream));
     const auto t1 = Clock::now();
+    float gpu_ms = 0.0f;
+    CV_CUDA(ctx, cudaEventElapsedTime(&gpu_ms, S->ev_t0, S->ev_t1));
     // ---- retire finished requests, advance the rest
     std::vector<Request> keep;
     keep.reserve(live.size());
     {
         std::lock_guard<std::mutex> lk(S->mu);
         S->busy_s += std::chrono::duration<double>(t1 - t0).count();
+        S->gpu_s += 1e-3 * gpu_ms;
         ++S->rounds;
         S->samples += round_samples;
         for (int k = 0; k < nlive; ++k) {
@@ -1713,6 +1719,8 @@ extern "C" int cv_server_start(cv_ctx *ctx, const cv_server_opts *opts, cv_serve
     S->class_grid.assign(2 * (CV_MAX_DIM + 1) * (CV_MAX_BINS + 1), 0);
     cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&S->ev_t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&S->ev_t1);
     for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&S->side[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_join[k], cudaEventDisableTiming);
@@ -1816,6 +1824,7 @@ extern "C" int cv_server_stats(cv_server *S, cv_serve_stats *out)
     out->max_live = S->max_live_seen;
     out->pending = (int)S->pending.size();
     out->busy_s = S->busy_s;
+    out->gpu_s = S->gpu_s;
     out->wall_s = std::chrono::duration<double>(Clock::now() - S->t_start).count();
     std::vector<double> lat;
     lat.reserve(S->latency_ms.size());
@@ -1854,6 +1863,8 @@ static void server_release(cv_server *S)
         if (S->ev_join[k]) cudaEventDestroy(S->ev_join[k]);
     }
     if (S->ev_fork) cudaEventDestroy(S->ev_fork);
+    if (S->ev_t0) cudaEventDestroy(S->ev_t0);
+    if (S->ev_t1) cudaEventDestroy(S->ev_t1);
     delete S;
 }
 
