@@ -619,6 +619,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
             // [kWarpsPerBlock][NDIM][N]: every warp's own copy
             for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * N; i += blockDim.x) sm.h[i] = 0.0f;
         }
+        // (by bin: coalesced reads of the FP64 grid)
         for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
             const int d = idx / N, k = idx - d * N;
             const double *e = A.edges + (size_t)d * (N + 1);
@@ -699,8 +700,11 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         const int c = threadIdx.x >> 1;
         atomicAdd((threadIdx.x & 1) ? &A.S2[c] : &A.S1[c], t);
     }
+    // (by bin: the FP64 atomics of a warp go to consecutive addresses,
+    // which the L2 merges; every block flushes at about the same time)
     for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-        const int d = idx / N, k = idx - d * N;
+        const int d = idx / N;
+        const int k = idx - d * N;
         Real v;
         if constexpr (sizeof(Real) == 4) {
             const int p = slot_of_bin(k, A.map);
@@ -715,7 +719,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         } else {
             v = sm.h[d * kStride + k];
         }
-        if (v != Real(0)) atomicAdd(&A.H[idx], (double)v);
+        if (v != Real(0)) atomicAdd(&A.H[d * N + k], (double)v);
     }
 }
 
@@ -747,7 +751,7 @@ k_batch_sample(const BatchSampleArgs B)
     sm.hs = stride;
     sm.ew = reinterpret_cast<float2 *>(smem_raw);
     float *hist = reinterpret_cast<float *>(sm.ew + NDIM * stride);  // [kWarpsPerBlock][NDIM][stride]
-    __shared__ SampleArgs<float> A;
+    __shared__ __align__(16) SampleArgs<float> A;
     __shared__ int s_tile;
     __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -774,9 +778,10 @@ k_batch_sample(const BatchSampleArgs B)
             __syncthreads();
             const int N = A.nbins;
             for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-                const int d = idx / N, k = idx - d * N;
+                const int d = idx / N, sl = idx - d * N;
+                const int k = bin_of_slot(sl, A.map);
                 const double *e = it.edges + (size_t)d * (N + 1);
-                const int p = d * stride + slot_of_bin(k, A.map);
+                const int p = d * stride + sl;
                 const double w = e[k + 1] - e[k];
                 sm.ew[p] = make_float2(__double2float_rn(e[k] - w), __double2float_rn(POW2 ? (double)N * w : w));
             }
@@ -823,15 +828,15 @@ k_batch_sample(const BatchSampleArgs B)
         // the tile's histogram: warp copies summed in warp order, then cleared
         const int N = A.nbins;
         for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-            const int d = idx / N, k = idx - d * N;
-            const int p = d * stride + slot_of_bin(k, A.map);
+            const int d = idx / N, sl = idx - d * N;  // (by slot: conflict-free)
+            const int p = d * stride + sl;
             float v = 0.0f;
 #pragma unroll
             for (int w = 0; w < kWarpsPerBlock; ++w) {
                 v += hist[w * hsize + p];
                 hist[w * hsize + p] = 0.0f;
             }
-            if (v != 0.0f) atomicAdd(&it.H[idx], (double)v);
+            if (v != 0.0f) atomicAdd(&it.H[d * N + bin_of_slot(sl, A.map)], (double)v);
         }
         __syncthreads();
     }

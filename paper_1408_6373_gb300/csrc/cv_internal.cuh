@@ -57,8 +57,10 @@ struct GenzParams {
     int ndim;
     int ncomp;
     int family[CV_MAX_COMP];
-    Real p0[CV_MAX_COMP][CV_MAX_DIM];
-    Real p1[CV_MAX_COMP][CV_MAX_DIM];
+    // (16-byte aligned: runs of four parameters can be read with one
+    // vector load when they sit in shared memory)
+    alignas(16) Real p0[CV_MAX_COMP][CV_MAX_DIM];
+    alignas(16) Real p1[CV_MAX_COMP][CV_MAX_DIM];
     Real q0[CV_MAX_COMP];
 };
 
