@@ -390,6 +390,7 @@ def run_ours(args):
     }
     if not args.no_batch:
         line["batch4096"] = measure_batch(ctx, cg, W, args.warmup, args.steps)
+    line["gaussian3d"] = measure_gaussian3d(ctx, cg, W)
     if not args.no_large:
         line["large30d"] = measure_large(ctx, cg, W)
     if not args.no_materialised:
@@ -488,6 +489,36 @@ def measure_materialised(ctx, cg, W) -> dict:
             "library_bytes_per_sample": lib_bytes, "all_bytes_per_sample": all_bytes,
             "hbm_gbs_all_kernels": rate * all_bytes / 1e9,
             "integral": list(r.integral)}
+
+
+def measure_gaussian3d(ctx, cg, W, reps: int = 20) -> dict:
+    """The small FP64 case (Gaussian a = 5, u = 1/2, ndim 3, 50 bins,
+    10 x 1e4 points): latency-bound, so reported as time per iteration, for
+    the graph-replayed integral and the one-launch-per-iteration plain form;
+    device-timed, and the result against the closed form."""
+    import torch
+    p = W.gaussian3d()
+    g = cg.genz(p.ndim, p.families, p.a, p.u)
+    out = {"workload": "gaussian3d: FP64, Gaussian a = 5, u = 1/2, ndim 3, 50 bins, 10 iterations x 1e4 points"}
+    for name, flags in (("graph", cg.FP64), ("plain", cg.FP64 | cg.PLAIN)):
+        I = ctx.integral(cg.spec(g, nbins=p.nbins, maxeval=p.maxeval, nstart=p.nstart, flags=flags))
+        for _ in range(3):
+            I.reset()
+            I.run()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(reps):
+            I.reset()
+            I.run()
+        s1.record()
+        torch.cuda.synchronize()
+        r = I.result()
+        out[f"{name}_us_per_iteration"] = 1e3 * s0.elapsed_time(s1) / (reps * r.iterations)
+        I.close()
+    exact = (math.sqrt(math.pi) / 5 * math.erf(2.5)) ** 3
+    out["integral"], out["error"], out["exact"] = r.integral[0], r.error[0], exact
+    return out
 
 
 def measure_large(ctx, cg, W, steps: int = 1) -> dict:

@@ -67,6 +67,8 @@ class _Problem(ctypes.Structure):
         ("family", ctypes.c_int * MAX_COMP),
         ("a", (ctypes.c_double * MAX_DIM) * MAX_COMP),
         ("u", (ctypes.c_double * MAX_DIM) * MAX_COMP),
+        ("gen", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
     ]
 
 
@@ -83,6 +85,9 @@ def _bind(lib):
                 "or_sobol_directions": (_int, [_int, _vp, _vp, _int, _vp]),
                 "or_sobol_word": (None, [_int, _vp, _u64, _vp]),
                 "or_sobol_coords": (_int, [_int, _vp, _u64, _i64, _int, _vp]),
+                "or_philox4x64": (None, [_vp, _vp, _vp]),
+                "or_point_words": (None, [_int, _u64, _int, _vp, _u64, _vp]),
+                "or_point_coords": (_int, [_int, _u64, _int, _vp, _u64, _i64, _int, _vp]),
                 "or_grid_uniform": (None, [_int, _int, _vp]),
                 "or_map": (_d, [_int, _int, _vp, _vp, _int, _vp, _vp]),
                 "or_genz": (_d, [_int, _int, _vp, _vp, _vp]),
@@ -209,6 +214,41 @@ def sobol_coords(ndim: int, start: int, n: int, bits: int, V=None) -> np.ndarray
     return Y
 
 
+SOBOL, SCRAMBLED, PSEUDO = 0, 1, 2
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x64-10 block of counter ctr[4] under key[2] (uint64)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    _load().or_philox4x64(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def point_words(gen: int, seed: int, ndim: int, indices, V=None) -> np.ndarray:
+    """64-bit words of any generator, shape [ndim, len(indices)]."""
+    V = sobol_directions(ndim) if V is None else V
+    idx = np.asarray(indices, dtype=np.uint64)
+    out = np.zeros((ndim, idx.size), dtype=np.uint64)
+    X = np.zeros(ndim, dtype=np.uint64)
+    lib = _load()
+    for j, i in enumerate(idx):
+        lib.or_point_words(gen, seed, ndim, _ptr(V), int(i), _ptr(X))
+        out[:, j] = X
+    return out
+
+
+def point_coords(gen: int, seed: int, ndim: int, start: int, n: int, bits: int, V=None) -> np.ndarray:
+    """y-coordinates of any generator, [ndim, n] integers."""
+    V = sobol_directions(ndim) if V is None else V
+    Y = np.zeros((ndim, n), dtype=np.uint64)
+    rc = _load().or_point_coords(gen, seed, ndim, _ptr(V), start, n, bits, _ptr(Y))
+    if rc != 0:
+        raise ValueError("bad arguments")
+    return Y
+
+
 # --------------------------------------------------------------------------
 # Grid, integrands
 # --------------------------------------------------------------------------
@@ -260,6 +300,8 @@ class Problem:
     nbins: int = 50
     bits: int = 52         # fraction bits of y: 52 (FP64 path) or 23 (FP32 path)
     fp32_decide: bool = False
+    gen: int = 0           # point generator: SOBOL, SCRAMBLED or PSEUDO
+    seed: int = 0          # Philox key of the scrambled and pseudo-random generators
     V: np.ndarray = field(default=None, repr=False)
 
     @property
@@ -270,6 +312,7 @@ class Problem:
         p = _Problem()
         p.ndim, p.ncomp, p.nbins, p.bits = self.ndim, self.ncomp, self.nbins, self.bits
         p.fp32_decide = 1 if self.fp32_decide else 0
+        p.gen, p.seed = int(self.gen), int(self.seed)
         a = np.asarray(self.a, dtype=np.float64).reshape(self.ncomp, self.ndim)
         u = np.asarray(self.u, dtype=np.float64).reshape(self.ncomp, self.ndim)
         for c in range(self.ncomp):

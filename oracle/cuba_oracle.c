@@ -64,6 +64,8 @@ typedef struct {
     int family[OR_MAX_COMP];
     double a[OR_MAX_COMP][OR_MAX_DIM];
     double u[OR_MAX_COMP][OR_MAX_DIM];
+    int gen;           /* point generator: OR_GEN_SOBOL, _SCRAMBLED, _PSEUDO */
+    uint64_t seed;     /* key of the counter-based generator */
 } or_problem;
 
 /* ------------------------------------------------------------------ */
@@ -166,6 +168,96 @@ int or_sobol_coords(int ndim, const uint64_t *V, uint64_t start, int64_t n,
     uint64_t X[OR_MAX_DIM];
     for (int64_t j = 0; j < n; ++j) {
         or_sobol_word(ndim, V, start + (uint64_t)j, X);
+        for (int d = 0; d < ndim; ++d)
+            Y[(size_t)d * n + j] = X[d] >> (64 - bits);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* 1b. Counter-based random words and the other point generators.      */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Philox4x64-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC 2011): a 256-bit counter c and a 128-bit key k go
+ * through ten rounds; each round multiplies c0 and c2 by fixed odd
+ * constants into 128-bit products (hi, lo) and forms
+ *     c' = (hi(M1 c2) ^ c1 ^ k0,  lo(M1 c2),  hi(M0 c0) ^ c3 ^ k1,  lo(M0 c0)),
+ * and the key advances by the Weyl constants (golden ratio, sqrt(3) - 1)
+ * between rounds.  The output is the final counter block.
+ */
+void or_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        const unsigned __int128 p0 = (unsigned __int128)M0 * c0;
+        const unsigned __int128 p1 = (unsigned __int128)M1 * c2;
+        const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+enum { OR_GEN_SOBOL = 0, OR_GEN_SCRAMBLED = 1, OR_GEN_PSEUDO = 2 };
+
+/* Word d of the Philox block (a, d / 4, b, 0) under key (seed, 0). */
+static uint64_t philox_word(uint64_t seed, uint64_t a, int d, uint64_t b)
+{
+    const uint64_t ctr[4] = {a, (uint64_t)(d / 4), b, 0};
+    const uint64_t key[2] = {seed, 0};
+    uint64_t out[4];
+    or_philox4x64(ctr, key, out);
+    return out[d % 4];
+}
+
+/*
+ * Word of point i in dimension d for each generator:
+ *   Sobol      X_d(i) as above;
+ *   scrambled  X_d(i) ^ S_d, a random digital shift per dimension,
+ *              S_d = Philox word (0, d/4, 1, 0)[d mod 4]: every point moves
+ *              by the same XOR, so every net property of the sequence is
+ *              kept, and independent seeds give independent replicates
+ *              (randomized QMC);
+ *   pseudo     Philox word (i, d/4, 0, 0)[d mod 4]: independent uniform
+ *              64-bit words, no net structure.
+ * The y-coordinate takes the top b bits of the word in every case.
+ */
+void or_point_words(int gen, uint64_t seed, int ndim, const uint64_t *V, uint64_t i,
+                    uint64_t *X)
+{
+    if (gen == OR_GEN_PSEUDO) {
+        for (int d = 0; d < ndim; ++d)
+            X[d] = philox_word(seed, i, d, 0);
+        return;
+    }
+    or_sobol_word(ndim, V, i, X);
+    if (gen == OR_GEN_SCRAMBLED)
+        for (int d = 0; d < ndim; ++d)
+            X[d] ^= philox_word(seed, 0, d, 1);
+}
+
+/* y-coordinates of any generator, dimension-major as or_sobol_coords. */
+int or_point_coords(int gen, uint64_t seed, int ndim, const uint64_t *V, uint64_t start,
+                    int64_t n, int bits, uint64_t *Y)
+{
+    if (bits < 1 || bits > 63 || n < 0 || gen < 0 || gen > 2)
+        return -1;
+    uint64_t X[OR_MAX_DIM];
+    for (int64_t j = 0; j < n; ++j) {
+        or_point_words(gen, seed, ndim, V, start + (uint64_t)j, X);
         for (int d = 0; d < ndim; ++d)
             Y[(size_t)d * n + j] = X[d] >> (64 - bits);
     }
@@ -421,7 +513,7 @@ static void *sample_range(void *arg)
     int kbin[OR_MAX_DIM];
     const uint64_t mask = (((uint64_t)1) << p->bits) - 1;
     for (int64_t j = 0; j < job->n; ++j) {
-        or_sobol_word(ndim, job->V, job->start + (uint64_t)j, X);
+        or_point_words(p->gen, p->seed, ndim, job->V, job->start + (uint64_t)j, X);
         for (int d = 0; d < ndim; ++d)
             Y[d] = X[d] >> (64 - p->bits);
         double J = map_point(ndim, N, job->edges, Y, p->bits, x, kbin);
