@@ -98,6 +98,23 @@ extern "C" {
  * process; without NVRTC, or if a compile fails, the generic kernel runs.
  * Results equal those of the generic kernel. */
 #define CV_JIT 0x800
+/* Point generators other than the plain Sobol sequence (SURVEY's NEXT-2),
+ * both keyed by a 64-bit seed through the counter-based generator
+ * Philox4x64-10 (Salmon et al., SC 2011):
+ *   CV_SCRAMBLE  randomized QMC: every coordinate of every Sobol point is
+ *                XORed with a random digital shift of its dimension, the
+ *                Philox word (0, d/4, 1, 0)[d mod 4] under key (seed, 0).
+ *                All net properties of the sequence are kept; runs with
+ *                independent seeds are independent unbiased replicates.
+ *   CV_PSEUDO    pseudo-random sampling: the word of point i in dimension d
+ *                is the Philox word (i, d/4, 0, 0)[d mod 4] under key
+ *                (seed, 0).  Single integrals only (cv_sample, cv_points,
+ *                cv_vegas, cv_integral_*); the batched, served and
+ *                materialised paths return CV_EINVAL.
+ * The y-coordinate takes the top 23 (FP32 path) or 52 (CV_FP64) bits of
+ * the 64-bit word, as for Sobol points.  At most one of the two. */
+#define CV_SCRAMBLE 0x1000
+#define CV_PSEUDO 0x2000
 
 /* One integral: ncomp components of one ndim-dimensional Genz problem.
  * a[c][i], u[c][i] are the parameters of component c (unused entries
@@ -135,17 +152,22 @@ int cv_synchronize(cv_ctx *ctx);
  * 1 <= ndim <= CV_MAX_DIM, n >= 0, start + n <= CV_INDEX_LIMIT. */
 int cv_sobol(cv_ctx *ctx, int ndim, uint64_t start, int64_t n, int bits,
              uint64_t *Y_dev);
+/* The same for any point generator: flags 0 (Sobol), CV_SCRAMBLE or
+ * CV_PSEUDO, keyed by seed (see the flags). */
+int cv_points(cv_ctx *ctx, int ndim, uint64_t start, int64_t n, int bits, int flags,
+              uint64_t seed, uint64_t *Y_dev);
 
 /* One sampling pass (DoSample, Sect. 2.1): the n points with Sobol indices
  * start..start+n-1 mapped through the grid edges_dev, evaluated by the
  * built-in integrand, ADDED to the accumulators:
  *   S1_dev[c] += sum J f_c,  S2_dev[c] += sum (J f_c)^2,
  *   hist_dev[d*nbins + k] += sum over points in bin k of axis d of (J f_0)^2
- * with J = prod_d nbins (e_(k_d+1) - e_(k_d)).  flags: CV_FP64 or 0 (see
- * above).  2 <= nbins <= CV_MAX_BINS, edges increasing from 0 to 1. */
+ * with J = prod_d nbins (e_(k_d+1) - e_(k_d)).  flags: CV_FP64 or 0, plus
+ * CV_JIT and CV_SCRAMBLE or CV_PSEUDO with their seed (see above).
+ * 2 <= nbins <= CV_MAX_BINS, edges increasing from 0 to 1. */
 int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins,
               const double *edges_dev, uint64_t start, int64_t n, int flags,
-              double *S1_dev, double *S2_dev, double *hist_dev);
+              uint64_t seed, double *S1_dev, double *S2_dev, double *hist_dev);
 
 /* Grid refinement (Lepage 1978) in FP64, in place, per axis: smooth the
  * histogram, compress with exponent 1.5, and rebin so that every new bin
@@ -163,8 +185,8 @@ int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_dev,
  * neval >= mineval and every component has error <= max(epsabs,
  * epsrel |integral|), or with fail = 1 when the next iteration would exceed
  * maxeval.  nbatch is a performance hint only (it never changes results);
- * seed is accepted for interface parity (the Sobol stream is unscrambled
- * and seed-independent).  integral/error/prob receive ncomp values each;
+ * seed keys the CV_SCRAMBLE / CV_PSEUDO generators (the plain Sobol stream
+ * does not depend on it).  integral/error/prob receive ncomp values each;
  * prob is the chi-square probability that the iteration results are not
  * consistent (P((m-1)/2, chi2/2) over m iterations). */
 int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g,
@@ -219,12 +241,13 @@ int cv_genz_callback(const int *ndim, const void *x_dev, const int *ncomp, void 
  * *available is 1 if run-time compilation can be used at all. */
 int cv_jit_info(int *available, int *compiled);
 /* Compile (without loading) the specialised sampling kernel CV_JIT would
- * build for integrand g with nbins bins: a check that run-time
+ * build for integrand g with nbins bins and the point generator of flags
+ * (0, CV_SCRAMBLE or CV_PSEUDO): a check that run-time
  * compilation works here and accepts this problem.  Needs no device.
  * Returns CV_OK, CV_EINVAL for an invalid g or nbins, or CV_ENOTFOUND when
  * NVRTC is missing or rejects the source; then `log` (log_len bytes,
  * may be null) receives the reason. */
-int cv_jit_check(const cv_genz *g, int nbins, char *log, int log_len);
+int cv_jit_check(const cv_genz *g, int nbins, int flags, char *log, int log_len);
 
 /* Bytes cv_vegas moves between host and device per call for an integral of
  * this shape: kernel parameters in (h2d), the final state out (d2h). */
@@ -267,9 +290,10 @@ int cv_vegas_noalloc(int device, void *stream, int ndim, int ncomp,
 typedef struct {
     cv_genz g;
     int nbins;
-    int flags;                 /* CV_FP64, CV_PLAIN, verbosity            */
+    int flags;                 /* CV_FP64, CV_PLAIN, CV_JIT, CV_SCRAMBLE, CV_PSEUDO */
     double epsrel, epsabs;
     int64_t mineval, maxeval, nstart, nincrease, nbatch;
+    uint64_t seed;             /* key of CV_SCRAMBLE / CV_PSEUDO          */
 } cv_spec;
 
 typedef struct {

@@ -31,6 +31,8 @@ FP64 = 0x100
 PLAIN = 0x200
 AOS = 0x400
 JIT = 0x800
+SCRAMBLE = 0x1000  # randomized QMC: Sobol points with a random digital shift per dimension
+PSEUDO = 0x2000    # pseudo-random points (Philox4x64-10 keyed by the seed)
 
 OK, EINVAL, ENOMEM, ECUDA, EABORT, ETIMEOUT, EADMIT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
 ESCRATCH = -9
@@ -85,6 +87,7 @@ class Spec(ctypes.Structure):
         ("nstart", ctypes.c_int64),
         ("nincrease", ctypes.c_int64),
         ("nbatch", ctypes.c_int64),
+        ("seed", ctypes.c_uint64),
     ]
 
 
@@ -103,11 +106,12 @@ class Result(ctypes.Structure):
 
 
 def spec(g: Genz, nbins=64, flags=0, epsrel=0.0, epsabs=0.0, mineval=0, maxeval=10 ** 6,
-         nstart=10 ** 4, nincrease=0, nbatch=1000) -> Spec:
+         nstart=10 ** 4, nincrease=0, nbatch=1000, seed=0) -> Spec:
     s = Spec()
     s.g = g
     s.nbins, s.flags, s.epsrel, s.epsabs = nbins, flags, epsrel, epsabs
     s.mineval, s.maxeval, s.nstart, s.nincrease, s.nbatch = mineval, maxeval, nstart, nincrease, nbatch
+    s.seed = seed
     return s
 
 
@@ -152,13 +156,14 @@ _SIGNATURES = {
     "cv_last_error": (ctypes.c_char_p, [_vp]),
     "cv_synchronize": (_i, [_vp]),
     "cv_sobol": (_i, [_vp, _i, _u64, _i64, _i, _vp]),
-    "cv_sample": (_i, [_vp, _P(Genz), _i, _vp, _u64, _i64, _i, _vp, _vp, _vp]),
+    "cv_points": (_i, [_vp, _i, _u64, _i64, _i, _i, _u64, _vp]),
+    "cv_sample": (_i, [_vp, _P(Genz), _i, _vp, _u64, _i64, _i, _u64, _vp, _vp, _vp]),
     "cv_refine": (_i, [_vp, _i, _i, _vp, _vp]),
     "cv_vegas": (_i, [_vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64, _i64,
                       _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_vegas_io_bytes": (_i, [_i, _i, _P(_i64), _P(_i64)]),
     "cv_jit_info": (_i, [_P(_i), _P(_i)]),
-    "cv_jit_check": (_i, [_vp, _i, ctypes.c_char_p, _i]),
+    "cv_jit_check": (_i, [_vp, _i, _i, ctypes.c_char_p, _i]),
     "cv_vegas_noalloc": (_i, [_i, _vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64,
                               _i64, _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_integral_create": (_i, [_vp, _P(Spec), _P(_vp)]),
@@ -281,10 +286,15 @@ class Context:
         """Y[d, j] = X_d(start+j) >> (64-bits) into `out` (int64 [ndim, n])."""
         self._check(self._lib.cv_sobol(self._h, ndim, start, n, bits, _ptr(out)), "cv_sobol")
 
-    def sample(self, g: Genz, nbins: int, edges, start: int, n: int, flags: int, S1, S2, H):
+    def points(self, ndim: int, start: int, n: int, bits: int, flags: int, seed: int, out):
+        """cv_points: the coordinates of any point generator (flags 0,
+        SCRAMBLE or PSEUDO, keyed by seed) into `out` (int64 [ndim, n])."""
+        self._check(self._lib.cv_points(self._h, ndim, start, n, bits, flags, seed, _ptr(out)), "cv_points")
+
+    def sample(self, g: Genz, nbins: int, edges, start: int, n: int, flags: int, S1, S2, H, seed: int = 0):
         """DoSample: add sum J f, sum (J f)^2 and the f^2 histogram of n points."""
         self._check(self._lib.cv_sample(self._h, ctypes.byref(g), nbins, _ptr(edges), start, n,
-                                        flags, _ptr(S1), _ptr(S2), _ptr(H)), "cv_sample")
+                                        flags, seed, _ptr(S1), _ptr(S2), _ptr(H)), "cv_sample")
 
     def refine(self, ndim: int, nbins: int, H, edges):
         self._check(self._lib.cv_refine(self._h, ndim, nbins, _ptr(H), _ptr(edges)), "cv_refine")
@@ -376,11 +386,11 @@ def jit_info():
     return bool(a.value), c.value
 
 
-def jit_check(g: Genz, nbins: int):
+def jit_check(g: Genz, nbins: int, flags: int = 0):
     """cv_jit_check: compile, without loading, the specialised kernel CV_JIT
-    would build for g and nbins.  Returns (ok, reason)."""
+    would build for g, nbins and the generator of flags.  Returns (ok, reason)."""
     buf = ctypes.create_string_buffer(512)
-    rc = lib().cv_jit_check(ctypes.byref(g), nbins, buf, len(buf))
+    rc = lib().cv_jit_check(ctypes.byref(g), nbins, flags, buf, len(buf))
     if rc == EINVAL:
         raise CubaGpuError(rc, "cv_jit_check")
     return rc == OK, buf.value.decode(errors="replace")

@@ -25,9 +25,11 @@ namespace cv {
     extern template cudaError_t sample_occupancy<D, float>(int, int *);                     \
     extern template cudaError_t sample_occupancy<D, double>(int, int *);                    \
     extern template cudaError_t launch_sobol<D, unsigned int>(                              \
-        unsigned long long, long long, int, unsigned long long *, int, cudaStream_t);       \
+        unsigned long long, long long, int, const PointArgs &, unsigned long long *, int,   \
+        cudaStream_t);                                                                      \
     extern template cudaError_t launch_sobol<D, unsigned long long>(                        \
-        unsigned long long, long long, int, unsigned long long *, int, cudaStream_t);
+        unsigned long long, long long, int, const PointArgs &, unsigned long long *, int,   \
+        cudaStream_t);
 CV_FOR_EACH_NDIM(CV_EXTERN)
 #undef CV_EXTERN
 
@@ -55,10 +57,10 @@ static cudaError_t dispatch_occupancy(int ndim, int nbins, int *occ)
 
 template <typename W>
 static cudaError_t dispatch_sobol(int ndim, unsigned long long start, long long n, int bits,
-                                  unsigned long long *Y, int grid, cudaStream_t s)
+                                  const PointArgs &pa, unsigned long long *Y, int grid, cudaStream_t s)
 {
     switch (ndim) {
-#define CV_CASE(D) case D: return launch_sobol<D, W>(start, n, bits, Y, grid, s);
+#define CV_CASE(D) case D: return launch_sobol<D, W>(start, n, bits, pa, Y, grid, s);
         CV_FOR_EACH_NDIM(CV_CASE)
 #undef CV_CASE
     }
@@ -277,13 +279,19 @@ static int occupancy(cv_ctx *ctx, int ndim, int nbins, bool fp64, int *occ)
     return CV_OK;
 }
 
-// Blocks for a pass over n points: enough warps that every warp gets a few
-// dozen 32-point steps, at most one full wave of resident blocks.
+// Blocks for a pass over n points: about 16 32-point blocks per warp, at
+// most one full wave of resident CTAs.  A pass too small to fill that wave
+// spreads over more warps instead (down to 2 blocks each): its time is the
+// dependent arithmetic of one warp's blocks (FP64 especially), not issue.
 static int sample_grid(cv_ctx *ctx, int occ, long long n)
 {
     const long long nblk = (n + 63) / 32;
-    long long want = (nblk + (long long)kWarpsPerBlock * 16 - 1) / ((long long)kWarpsPerBlock * 16);
     const long long cap = (long long)ctx->sms * occ;
+    long long want = (nblk + (long long)kWarpsPerBlock * 16 - 1) / ((long long)kWarpsPerBlock * 16);
+    if (want < cap) {
+        want = (nblk + (long long)kWarpsPerBlock * 2 - 1) / ((long long)kWarpsPerBlock * 2);
+        if (want > cap) want = cap;
+    }
     if (want > cap) want = cap;
     if (want < 1) want = 1;
     return (int)want;
@@ -294,14 +302,16 @@ static int sample_grid(cv_ctx *ctx, int occ, long long n)
 template <typename Real>
 static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *edges,
                        unsigned long long start, long long n, long long n_grid,
-                       double *S1, double *S2, double *H, DevState *st, bool jit = false)
+                       double *S1, double *S2, double *H, DevState *st, int flags, uint64_t seed)
 {
     SampleArgs<Real> a;
     memset(&a, 0, sizeof(a));
     fill_params<Real>(g, &a.g);
     a.nbins = nbins;
-    a.chunk_min = 4;
+    a.chunk_min = 2;
     a.map = make_map(nbins, g->ndim, sizeof(Real) == 8);
+    set_generator(&a, g->ndim, flags, seed);
+    const bool jit = (flags & CV_JIT) != 0;
     a.edges = edges;
     a.S1 = S1;
     a.S2 = S2;
@@ -331,7 +341,7 @@ static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *e
     return CV_OK;
 }
 
-extern "C" int cv_jit_check(const cv_genz *g, int nbins, char *log, int log_len)
+extern "C" int cv_jit_check(const cv_genz *g, int nbins, int flags, char *log, int log_len)
 {
     if (log && log_len > 0) log[0] = '\0';
     if (check_genz(nullptr, g) || nbins < CV_MIN_BINS || nbins > CV_MAX_BINS) return CV_EINVAL;
@@ -340,6 +350,7 @@ extern "C" int cv_jit_check(const cv_genz *g, int nbins, char *log, int log_len)
     fill_params<float>(g, &a.g);
     a.nbins = nbins;
     a.map = make_map(nbins, g->ndim, false);
+    set_generator(&a, g->ndim, flags, 1);
     std::string err;
     const int rc = jit_compile_check(a, g->ndim, a.map.pow2 != 0, min_blocks_f32(g->ndim), &err);
     if (rc && log && log_len > 0) snprintf(log, (size_t)log_len, "%s", err.c_str());
@@ -359,7 +370,15 @@ extern "C" int cv_jit_info(int *available, int *compiled)
 extern "C" int cv_sobol(cv_ctx *ctx, int ndim, uint64_t start, int64_t n, int bits,
                         uint64_t *Y_dev)
 {
+    return cv_points(ctx, ndim, start, n, bits, 0, 0, Y_dev);
+}
+
+extern "C" int cv_points(cv_ctx *ctx, int ndim, uint64_t start, int64_t n, int bits, int flags,
+                         uint64_t seed, uint64_t *Y_dev)
+{
     if (!ctx) return CV_EINVAL;
+    if ((flags & CV_SCRAMBLE) && (flags & CV_PSEUDO))
+        return fail_msg(ctx, CV_EINVAL, "CV_SCRAMBLE and CV_PSEUDO exclude each other");
     if (ndim < 1 || ndim > CV_MAX_DIM) return fail_msg(ctx, CV_EINVAL, "ndim %d outside 1..%d", ndim, CV_MAX_DIM);
     if (bits != 23 && bits != 52) return fail_msg(ctx, CV_EINVAL, "bits must be 23 or 52");
     if (n < 0 || start > CV_INDEX_LIMIT || (uint64_t)n > CV_INDEX_LIMIT - start)
@@ -370,16 +389,28 @@ extern "C" int cv_sobol(cv_ctx *ctx, int ndim, uint64_t start, int64_t n, int bi
     long long nblk = (n + 63) / 32;
     long long grid = (nblk + kWarpsPerBlock * 4 - 1) / (kWarpsPerBlock * 4);
     if (grid > (long long)ctx->sms * 8) grid = (long long)ctx->sms * 8;
+    // the generator, with unpermuted shift words (the plain Sobol table)
+    PointArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    {
+        SampleArgs<double> a;
+        memset(&a, 0, sizeof(a));
+        set_generator(&a, ndim, flags, seed);
+        pa.gen = a.gen;
+        pa.seed = a.seed;
+        for (int d = 0; d < ndim; ++d) pa.shift[d] = bits == 23 ? (a.shift[d] >> 32) : a.shift[d];
+    }
     cudaError_t e = bits == 23
-        ? dispatch_sobol<unsigned int>(ndim, start, n, bits, (unsigned long long *)Y_dev, (int)grid, ctx->stream)
-        : dispatch_sobol<unsigned long long>(ndim, start, n, bits, (unsigned long long *)Y_dev, (int)grid, ctx->stream);
+        ? dispatch_sobol<unsigned int>(ndim, start, n, bits, pa, (unsigned long long *)Y_dev, (int)grid, ctx->stream)
+        : dispatch_sobol<unsigned long long>(ndim, start, n, bits, pa, (unsigned long long *)Y_dev, (int)grid,
+                                             ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sobol kernel launch");
     return CV_OK;
 }
 
 extern "C" int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins, const double *edges_dev,
-                         uint64_t start, int64_t n, int flags, double *S1_dev, double *S2_dev,
-                         double *hist_dev)
+                         uint64_t start, int64_t n, int flags, uint64_t seed, double *S1_dev,
+                         double *S2_dev, double *hist_dev)
 {
     if (!ctx) return CV_EINVAL;
     int rc = check_genz(ctx, g);
@@ -391,10 +422,13 @@ extern "C" int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins, const double 
     if (n == 0) return CV_OK;
     if (!edges_dev || !S1_dev || !S2_dev || !hist_dev) return fail_msg(ctx, CV_EINVAL, "null buffer");
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    if ((flags & CV_SCRAMBLE) && (flags & CV_PSEUDO))
+        return fail_msg(ctx, CV_EINVAL, "CV_SCRAMBLE and CV_PSEUDO exclude each other");
     if (flags & CV_FP64)
-        return launch_pass<double>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr);
+        return launch_pass<double>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr,
+                                   flags, seed);
     return launch_pass<float>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr,
-                              (flags & CV_JIT) != 0);
+                              flags, seed);
 }
 
 extern "C" int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_dev, double *edges_dev)
@@ -438,6 +472,8 @@ static int check_spec(cv_ctx *ctx, const cv_spec *sp)
     if ((uint64_t)sp->maxeval >= CV_INDEX_LIMIT)
         return fail_msg(ctx, CV_EINVAL, "maxeval beyond the 2^52 Sobol index range");
     if (!(sp->epsrel >= 0) || !(sp->epsabs >= 0)) return fail_msg(ctx, CV_EINVAL, "negative tolerance");
+    if ((sp->flags & CV_SCRAMBLE) && (sp->flags & CV_PSEUDO))
+        return fail_msg(ctx, CV_EINVAL, "CV_SCRAMBLE and CV_PSEUDO exclude each other");
     return CV_OK;
 }
 
@@ -463,9 +499,10 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
     cudaStream_t keep = ctx->stream;
     ctx->stream = s;
     int rc = (sp.flags & CV_FP64)
-        ? launch_pass<double>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st)
+        ? launch_pass<double>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st,
+                              sp.flags, sp.seed)
         : launch_pass<float>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st,
-                             (sp.flags & CV_JIT) != 0);
+                             sp.flags, sp.seed);
     ctx->stream = keep;
     if (rc) return rc;
     CombineArgs ca;
@@ -506,6 +543,7 @@ static int capture_graph(cv_integral *I)
         fill_params<float>(&I->spec.g, &a.g);
         a.nbins = I->spec.nbins;
         a.map = make_map(I->spec.nbins, I->spec.g.ndim, false);
+        set_generator(&a, I->spec.g.ndim, I->spec.flags, I->spec.seed);
         JitKernel k;
         std::string err;
         jit_sample_kernel(ctx->device, a, I->spec.g.ndim, a.map.pow2 != 0, min_blocks_f32(I->spec.g.ndim), &k, &err);
@@ -685,6 +723,7 @@ extern "C" int cv_integral_step(cv_integral *I, int max_iter)
         fill_params<float>(&I->spec.g, &a.g);
         a.nbins = I->spec.nbins;
         a.map = make_map(I->spec.nbins, I->spec.g.ndim, false);
+        set_generator(&a, I->spec.g.ndim, I->spec.flags, I->spec.seed);
         JitKernel k;
         std::string err;
         jit_sample_kernel(ctx->device, a, I->spec.g.ndim, a.map.pow2 != 0, min_blocks_f32(I->spec.g.ndim), &k, &err);
@@ -707,18 +746,19 @@ struct StateFileHeader {
     double a[CV_MAX_COMP][CV_MAX_DIM], u[CV_MAX_COMP][CV_MAX_DIM];
     double epsrel, epsabs;
     long long mineval, maxeval, nstart, nincrease;
+    unsigned long long seed;
 };
 
 void fill_header(const cv_spec &sp, StateFileHeader *h)
 {
     memset(h, 0, sizeof(*h));
     memcpy(h->magic, "CUBAGPU", 8);
-    h->version = 1;
+    h->version = 2;
     h->state_bytes = (unsigned)sizeof(DevState);
     h->ndim = sp.g.ndim;
     h->ncomp = sp.g.ncomp;
     h->nbins = sp.nbins;
-    h->flags = sp.flags & (CV_FP64 | CV_JIT);
+    h->flags = sp.flags & (CV_FP64 | CV_JIT | CV_SCRAMBLE | CV_PSEUDO);
     for (int c = 0; c < sp.g.ncomp; ++c) {
         h->family[c] = sp.g.family[c];
         for (int d = 0; d < sp.g.ndim; ++d) {
@@ -732,6 +772,7 @@ void fill_header(const cv_spec &sp, StateFileHeader *h)
     h->maxeval = sp.maxeval;
     h->nstart = sp.nstart;
     h->nincrease = sp.nincrease;
+    h->seed = sp.seed;
 }
 }  // namespace
 
@@ -826,7 +867,6 @@ extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, doub
                         int64_t *neval, int *fail, double integral[], double error[],
                         double prob[])
 {
-    (void)seed;
     if (!ctx) return CV_EINVAL;
     if (!g) return fail_msg(ctx, CV_EINVAL, "null integrand description");
     if (g->ndim != ndim || g->ncomp != ncomp)
@@ -844,6 +884,7 @@ extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, doub
     sp.nstart = nstart;
     sp.nincrease = nincrease;
     sp.nbatch = nbatch;
+    sp.seed = (uint64_t)(int64_t)seed;
     cv_integral *I = nullptr;
     int rc = cv_integral_create(ctx, &sp, &I);
     if (rc) return rc;
@@ -1111,6 +1152,8 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         if (rc) return rc;
         if (specs[i].flags & (CV_FP64 | CV_PLAIN))
             return fail_msg(ctx, CV_EINVAL, "batched runs use the FP32 path (item %d asks for CV_FP64/CV_PLAIN)", i);
+        if (specs[i].flags & CV_PSEUDO)
+            return fail_msg(ctx, CV_EINVAL, "batched runs take Sobol or scrambled Sobol points (item %d)", i);
     }
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
     cv_batch *B = new cv_batch();
@@ -1186,6 +1229,7 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         it.a.chunk_min = 4;
         it.a.map = make_map(N, ndim, false);
         it.a.map.priv = it.a.map.pow2;  // every warp has its own histogram
+        set_generator(&it.a, ndim, sp.flags, sp.seed);
         it.st = (DevState *)p;
         it.edges = (double *)(p + sz_state);
         it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
@@ -1514,6 +1558,7 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         it.a.chunk_min = 4;
         it.a.map = make_map(N, ndim, false);
         it.a.map.priv = it.a.map.pow2;  // every warp has its own histogram
+        set_generator(&it.a, ndim, sp.flags, sp.seed);
         it.st = (DevState *)p;
         it.edges = (double *)(p + sz_state);
         it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
@@ -1761,6 +1806,8 @@ extern "C" int cv_submit(cv_server *S, const cv_spec *spec, uint64_t *id)
     if (rc) return rc;
     if (spec->flags & (CV_FP64 | CV_PLAIN))
         return fail_msg(S->ctx, CV_EINVAL, "served requests use the FP32 path");
+    if (spec->flags & CV_PSEUDO)
+        return fail_msg(S->ctx, CV_EINVAL, "served requests take Sobol or scrambled Sobol points");
     if (batch_smem_bytes(spec->g.ndim, spec->nbins) > 223 * 1024)
         return fail_msg(S->ctx, CV_EINVAL, "%d dimensions x %d bins exceed the batched path's shared memory",
                         spec->g.ndim, spec->nbins);
@@ -2005,6 +2052,7 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     a.nbins = N;
     a.chunk_min = 4;
     a.map = make_map(N, ndim, sizeof(Real) == 8);
+    set_generator(&a, ndim, sp.flags, sp.seed);
     a.edges = edges;
     a.ld = tile;
     a.aos = aos ? 1 : 0;
@@ -2075,10 +2123,11 @@ extern "C" int cv_vegas_cb(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev in
                            int64_t nincrease, int64_t nbatch, int nbins, int64_t *neval, int *fail,
                            double integral[], double error[], double prob[])
 {
-    (void)seed;
     (void)nbatch;
     if (!ctx) return CV_EINVAL;
     if (!integrand) return fail_msg(ctx, CV_EINVAL, "null integrand");
+    if (flags & CV_PSEUDO)
+        return fail_msg(ctx, CV_EINVAL, "materialised samples take Sobol or scrambled Sobol points");
     if (ndim < 1 || ndim > CV_MAX_DIM || ncomp < 1 || ncomp > CV_MAX_COMP)
         return fail_msg(ctx, CV_EINVAL, "ndim/ncomp out of range");
     if (nvec < 1) return fail_msg(ctx, CV_EINVAL, "nvec must be >= 1");
@@ -2094,6 +2143,7 @@ extern "C" int cv_vegas_cb(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev in
     sp.maxeval = maxeval;
     sp.nstart = nstart;
     sp.nincrease = nincrease;
+    sp.seed = (uint64_t)(int64_t)seed;
     int rc = check_spec(ctx, &sp);
     if (rc) return rc;
     if (!neval || !fail || !integral || !error || !prob) return fail_msg(ctx, CV_EINVAL, "null output");

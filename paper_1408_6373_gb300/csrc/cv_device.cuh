@@ -89,6 +89,22 @@ __device__ __forceinline__ void sobol_step(W (&X)[NDIM], unsigned long long q, i
         X[d] ^= Dir<W>::w(li, d, 5 + c);
 }
 
+// Pseudo-random words of point i (CV_PSEUDO): word d is Philox4x64-10 block
+// (i, d/4, 0, 0)[d mod 4] under key (seed, 0); the FP32 path keeps the top
+// 32 bits (its y takes the top 23 of them).
+template <int NDIM, typename W>
+__device__ __forceinline__ void pseudo_words(W (&X)[NDIM], unsigned long long seed, unsigned long long i)
+{
+#pragma unroll
+    for (int d0 = 0; d0 < NDIM; d0 += 4) {
+        unsigned long long c[4] = {i, (unsigned long long)(d0 / 4), 0ull, 0ull};
+        philox4x64_10(c, seed, 0ull);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (d0 + j < NDIM) X[d0 + j] = (W)(sizeof(W) == 8 ? c[j] : (c[j] >> 32));
+    }
+}
+
 // The step from an even block q (q + 1 is odd, c = 0): a fixed word.
 template <int NDIM, typename W>
 __device__ __forceinline__ void sobol_step_even(W (&X)[NDIM], int li = 0)
@@ -167,6 +183,7 @@ __device__ __forceinline__ float ipow(float r)
 template <typename Real>
 struct RuntimeIntegrand {
     static constexpr int kMode = 0;  // the integrand is evaluated in the pass
+    static constexpr int kGen = 0;   // Sobol points (optionally digitally shifted)
     template <int C> __device__ __forceinline__ static int family(const GenzParams<Real> &g) { return g.family[C]; }
     __device__ __forceinline__ static int ncomp(const GenzParams<Real> &g) { return g.ncomp; }
     template <int C> __device__ __forceinline__ static Real p0(const GenzParams<Real> &g, int d) { return g.p0[C][d]; }
@@ -175,6 +192,13 @@ struct RuntimeIntegrand {
     __device__ __forceinline__ static int table(const MapParams &m) { return m.li; }
     __device__ __forceinline__ static bool priv(const MapParams &m) { return m.priv != 0; }
     __device__ __forceinline__ static int nbins(int n) { return n; }
+};
+
+// Pseudo-random points (Philox words per point instead of the Sobol
+// recurrence) with the integrand evaluated in the pass.
+template <typename Real>
+struct PseudoIntegrand : RuntimeIntegrand<Real> {
+    static constexpr int kGen = 2;
 };
 
 // Materialised samples (the caller's integrand): the same pass either
@@ -561,6 +585,16 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
                 load_values<NDIM, Real, EDGE>(A, q, start, end, lane, fa);
                 if (!EDGE) load_values<NDIM, Real, EDGE>(A, q + 1, start, end, lane, fb);
             }
+            if constexpr (I::kGen == 2) {
+                // pseudo-random points: fresh words for every block
+                pseudo_words<NDIM, W>(X, A.seed, q * 32ull + (unsigned long long)lane);
+                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2, fa);
+                if (!EDGE) {
+                    pseudo_words<NDIM, W>(X, A.seed, (q + 1) * 32ull + (unsigned long long)lane);
+                    sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2, fb);
+                }
+                continue;
+            }
             sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2, fa);
             if (EDGE) {
                 sobol_step<NDIM, W>(X, q, li);
@@ -669,7 +703,13 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         const unsigned long long q0 = qa + ch * plen;
         const unsigned long long q1 = min(q0 + plen, qb);
         W X[NDIM];
-        sobol_skip<NDIM, W>(X, q0, lane, (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0);
+        if constexpr (I::kGen != 2) {
+            sobol_skip<NDIM, W>(X, q0, lane, (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0);
+            if (A.gen == kGenScrambled) {
+#pragma unroll
+                for (int d = 0; d < NDIM; ++d) X[d] ^= (W)A.shift[d];
+            }
+        }
         const bool interior = (q0 * 32ull >= start) && (q1 * 32ull <= end) && !((q0 | q1) & 1ull);
         if (interior)
             run_steps<NDIM, Real, POW2, false, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
@@ -728,6 +768,14 @@ __global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, Real>))
 k_sample(const __grid_constant__ SampleArgs<Real> A)
 {
     sample_pass<NDIM, Real, POW2, RuntimeIntegrand<Real>>(A);
+}
+
+// The pass with pseudo-random points (CV_PSEUDO), on the generic map.
+template <int NDIM, typename Real>
+__global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, Real>))
+k_sample_pseudo(const __grid_constant__ SampleArgs<Real> A)
+{
+    sample_pass<NDIM, Real, false, PseudoIntegrand<Real>>(A);
 }
 
 // ------------------------------------------------------------ batched kernel
@@ -800,6 +848,10 @@ k_batch_sample(const BatchSampleArgs B)
             smw.h = hist + warp * hsize;
             unsigned X[NDIM];
             sobol_skip<NDIM, unsigned>(X, w0, lane, POW2 ? A.map.li : 0);
+            if (A.gen == kGenScrambled) {
+#pragma unroll
+                for (int d = 0; d < NDIM; ++d) X[d] ^= (unsigned)A.shift[d];
+            }
             const bool interior = (w0 * 32ull >= start) && (w1 * 32ull <= end) && !((w0 | w1) & 1ull);
             if (interior)
                 run_steps<NDIM, float, POW2, false>(A, smw, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
@@ -882,10 +934,12 @@ k_genz_points(const __grid_constant__ GenzParams<Real> g, const Real *x, Real *f
 }
 
 // Sobol coordinates only (the point generator of the sampling kernels,
-// written out for bit-exact checks): Y[d*n + j] = X_d(start + j) >> shift.
+// written out for bit-exact checks): Y[d*n + j] = X_d(start + j) >> shift,
+// for the Sobol, digitally shifted (P.shift) or pseudo-random generator.
 template <int NDIM, typename W>
 __global__ void __launch_bounds__(kBlock)
-k_sobol(unsigned long long start, long long n, int shift, unsigned long long *Y)
+k_sobol(unsigned long long start, long long n, int shift, const __grid_constant__ PointArgs P,
+        unsigned long long *Y)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long qa = start >> 5;
@@ -902,8 +956,13 @@ k_sobol(unsigned long long start, long long n, int shift, unsigned long long *Y)
         const unsigned long long q1 = min(q0 + plen, qb);
         W X[NDIM];
         sobol_skip<NDIM, W>(X, q0, lane);
+        if (P.gen == kGenScrambled) {
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) X[d] ^= (W)P.shift[d];
+        }
         for (unsigned long long q = q0; q < q1; ++q) {
             const unsigned long long i = q * 32ull + (unsigned long long)lane;
+            if (P.gen == kGenPseudo) pseudo_words<NDIM, W>(X, P.seed, i);
             if (i >= start && i < end) {
                 const unsigned long long j = i - start;
 #pragma unroll
@@ -931,7 +990,9 @@ cudaError_t launch_sample(const SampleArgs<Real> &a, int grid, cudaStream_t s)
 {
     // (sample_occupancy, always called first, sets the shared-memory limit)
     const size_t smem = sample_smem_bytes(NDIM, a.nbins, sizeof(Real) == 8, a.map.priv != 0);
-    if constexpr (sizeof(Real) == 4) {
+    if (a.gen == kGenPseudo) {
+        k_sample_pseudo<NDIM, Real><<<grid, kBlock, smem, s>>>(a);
+    } else if constexpr (sizeof(Real) == 4) {
         if (a.map.pow2) k_sample<NDIM, float, true><<<grid, kBlock, smem, s>>>(a);
         else k_sample<NDIM, float, false><<<grid, kBlock, smem, s>>>(a);
     } else {
@@ -955,6 +1016,14 @@ cudaError_t sample_occupancy(int nbins, int *blocks_per_sm)
         // (the limit, not the launch size: static shared memory counts too)
         e = cudaFuncSetAttribute(sample_fn<NDIM, Real>(v == 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+    }
+    {
+        void *f = (void *)k_sample_pseudo<NDIM, Real>;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return e;
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sample_fn<NDIM, Real>(m.pow2 != 0),
@@ -1016,11 +1085,11 @@ cudaError_t launch_genz_points(const GenzParams<Real> &g, const Real *x, Real *f
 }
 
 template <int NDIM, typename W>
-cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
+cudaError_t launch_sobol(unsigned long long start, long long n, int bits, const PointArgs &pa,
                          unsigned long long *Y, int grid, cudaStream_t s)
 {
     const int shift = (int)(8 * sizeof(W)) - bits;
-    k_sobol<NDIM, W><<<grid, kBlock, 0, s>>>(start, n, shift, Y);
+    k_sobol<NDIM, W><<<grid, kBlock, 0, s>>>(start, n, shift, pa, Y);
     return cudaGetLastError();
 }
 
@@ -1049,7 +1118,9 @@ cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
     template cudaError_t cv::launch_genz_points<D, double, false>(const cv::GenzParams<double> &, const double *, double *, long long, long long, int, cudaStream_t); \
     template cudaError_t cv::launch_genz_points<D, double, true>(const cv::GenzParams<double> &, const double *, double *, long long, long long, int, cudaStream_t); \
     template cudaError_t cv::launch_sobol<D, unsigned int>(unsigned long long, long long,   \
-                                                           int, unsigned long long *, int,  \
+                                                           int, const cv::PointArgs &,      \
+                                                           unsigned long long *, int,       \
                                                            cudaStream_t);                   \
     template cudaError_t cv::launch_sobol<D, unsigned long long>(                           \
-        unsigned long long, long long, int, unsigned long long *, int, cudaStream_t);
+        unsigned long long, long long, int, const cv::PointArgs &, unsigned long long *, int, \
+        cudaStream_t);

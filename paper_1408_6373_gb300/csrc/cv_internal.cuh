@@ -64,6 +64,54 @@ struct GenzParams {
     Real q0[CV_MAX_COMP];
 };
 
+// ---- point generators ----
+enum { kGenSobol = 0, kGenScrambled = 1, kGenPseudo = 2 };
+
+// The generator of a point-only launch (cv_points): shift[d] in the
+// launch's word layout (64-bit words, or their unpermuted top halves).
+struct PointArgs {
+    int gen;
+    unsigned long long seed;
+    unsigned long long shift[CV_MAX_DIM];
+};
+
+// Philox4x64-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC 2011): ten rounds on a 256-bit counter block c under
+// a 128-bit key k; a round takes the 128-bit products of c0 and c2 with two
+// odd constants and forms (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), and the
+// key advances by two Weyl constants (golden ratio, sqrt(3) - 1) between
+// rounds.  c is replaced by the output block.
+__host__ __device__ inline void mulhilo64(unsigned long long a, unsigned long long b,
+                                          unsigned long long &hi, unsigned long long &lo)
+{
+#if defined(__CUDA_ARCH__)
+    lo = a * b;
+    hi = __umul64hi(a, b);
+#else
+    const unsigned __int128 p = (unsigned __int128)a * b;
+    hi = (unsigned long long)(p >> 64);
+    lo = (unsigned long long)p;
+#endif
+}
+
+__host__ __device__ inline void philox4x64_10(unsigned long long (&c)[4], unsigned long long k0,
+                                              unsigned long long k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        unsigned long long hi0, lo0, hi1, lo1;
+        mulhilo64(0xD2E7470EE14C6C93ull, c[0], hi0, lo0);
+        mulhilo64(0xCA5A826395121157ull, c[2], hi1, lo1);
+        const unsigned long long c1 = c[1], c3 = c[3];
+        c[0] = hi1 ^ c1 ^ k0;
+        c[1] = lo1;
+        c[2] = hi0 ^ c3 ^ k1;
+        c[3] = lo0;
+        k0 += 0x9E3779B97F4A7C15ull;
+        k1 += 0xBB67AE8584CAA73Bull;
+    }
+}
+
 // Uniform constants of the FP32 map for N = 2^L (see cv_device.cuh).
 struct MapParams {
     int pow2;                       // N = 2^L with L >= 5: the bit-level map below
@@ -99,6 +147,11 @@ struct SampleArgs {
     const Real *f;
     long long ld;
     int aos;
+    // point generator: kGenSobol, kGenScrambled (Sobol words XOR shift[d],
+    // in the kernel's word layout) or kGenPseudo (Philox words keyed by seed)
+    int gen;
+    unsigned long long seed;
+    unsigned long long shift[CV_MAX_DIM];
 };
 
 struct CombineArgs {
@@ -153,7 +206,7 @@ cudaError_t launch_batch_sample(const BatchSampleArgs &b, int grid, cudaStream_t
 template <int NDIM>
 cudaError_t batch_occupancy(bool pow2, int stride, int *blocks_per_sm);
 template <int NDIM, typename Word>
-cudaError_t launch_sobol(unsigned long long start, long long n, int bits,
+cudaError_t launch_sobol(unsigned long long start, long long n, int bits, const PointArgs &pa,
                          unsigned long long *Y, int grid, cudaStream_t s);
 
 // materialised samples: store the points (mode 1) or accumulate the
@@ -245,6 +298,55 @@ inline MapParams make_map(int N, int ndim, bool fp64)
                  (size_t)blocks * (sample_smem_bytes(ndim, N, false, true) + kSmemBlockReserve) <= kSmemPerSM;
     }
     return m;
+}
+
+// The bit permutation of the FP32 direction words for N = 2^L (5 <= L <= 8):
+// with y_t the bit of weight 2^-t of w / 2^32, the slot bits
+// (y_6..y_L, y_5, y_1..y_4) go to the top L bits, y_(L+1)..y_23 to mantissa
+// bits 22..L, and y_24..y_32 fill the rest (the layout the table generator
+// writes).  A digital shift of the scrambled generator is permuted the same
+// way, since a permutation commutes with XOR.
+inline unsigned slot_perm(unsigned w, int L)
+{
+    unsigned out = 0;
+    for (int t = 1; t <= 32; ++t) {
+        const unsigned bit = (w >> (32 - t)) & 1u;
+        int pos;
+        if (t <= 4) pos = 32 - L + (4 - t);
+        else if (t == 5) pos = 32 - L + 4;
+        else if (t <= L) pos = 37 - t;
+        else if (t <= 23) pos = 23 + L - t;
+        else if (t <= 32 - L) pos = 55 - L - t;
+        else pos = 32 - t;
+        out |= bit << pos;
+    }
+    return out;
+}
+
+// The point generator of a launch from the flags: the digital shifts of
+// CV_SCRAMBLE in the kernel's word layout (64-bit words on the FP64 path,
+// top halves -- permuted on the power-of-two FP32 map -- on the FP32 path);
+// CV_PSEUDO takes the generic map with block histograms, since its points
+// have no net structure.
+template <typename Real>
+inline void set_generator(SampleArgs<Real> *a, int ndim, int flags, unsigned long long seed)
+{
+    a->gen = (flags & CV_PSEUDO) ? kGenPseudo : ((flags & CV_SCRAMBLE) ? kGenScrambled : kGenSobol);
+    a->seed = seed;
+    memset(a->shift, 0, sizeof(a->shift));
+    if (a->gen == kGenPseudo) {
+        a->map.pow2 = 0;
+        a->map.priv = 0;
+        a->map.li = 0;
+    } else if (a->gen == kGenScrambled) {
+        for (int d = 0; d < ndim; ++d) {
+            unsigned long long c[4] = {0ull, (unsigned long long)(d / 4), 1ull, 0ull};
+            philox4x64_10(c, seed, 0ull);
+            const unsigned long long S = c[d % 4];
+            if (sizeof(Real) == 8) a->shift[d] = S;
+            else a->shift[d] = a->map.pow2 ? slot_perm((unsigned)(S >> 32), a->map.L) : (unsigned)(S >> 32);
+        }
+    }
 }
 #endif
 

@@ -88,6 +88,7 @@ std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, 
     const GenzParams<float> &g = a.g;
     std::string s = "#include \"cv_device.cuh\"\nnamespace cv {\nstruct JitIntegrand {\n";
     s += "  static constexpr int kMode = 0;\n";
+    s += std::string("  static constexpr int kGen = ") + (a.gen == kGenPseudo ? "2" : "0") + ";\n";
     s += "  template <int C> __device__ __forceinline__ static constexpr int family(const GenzParams<float>&) { constexpr int f[4] = {";
     for (int c = 0; c < 4; ++c) s += std::to_string(c < g.ncomp ? g.family[c] : CV_CONST) + (c < 3 ? "," : "");
     s += "}; return f[C]; }\n";

@@ -119,8 +119,8 @@ cudaError_t launch_of(int ndim, const cv::SampleArgs<Real> &a, int grid, cudaStr
 }
 
 template <typename Real>
-cudaError_t run(const cv_genz *g, int nbins, int sms, long long nmax, int jmax, bool poll,
-                const cv::CombineArgs &ca, double *edges, double *H, cv::DevState *st,
+cudaError_t run(const cv_genz *g, int nbins, int flags, unsigned long long seed, int sms, long long nmax,
+                int jmax, bool poll, const cv::CombineArgs &ca, double *edges, double *H, cv::DevState *st,
                 cudaStream_t s)
 {
     cv::SampleArgs<Real> a;
@@ -129,6 +129,7 @@ cudaError_t run(const cv_genz *g, int nbins, int sms, long long nmax, int jmax, 
     a.nbins = nbins;
     a.chunk_min = 4;
     a.map = cv::make_map(nbins, g->ndim, sizeof(Real) == 8);
+    cv::set_generator(&a, g->ndim, flags, seed);
     a.edges = edges;
     a.S1 = st->S1;
     a.S2 = st->S2;
@@ -167,9 +168,9 @@ extern "C" int cv_vegas_noalloc(int device, void *stream, int ndim, int ncomp, c
                                 int64_t nincrease, int64_t nbatch, int nbins, int64_t *neval,
                                 int *fail, double integral[], double error[], double prob[])
 {
-    (void)seed;
     (void)nbatch;
     if (!g || g->ndim != ndim || g->ncomp != ncomp) return CV_EINVAL;
+    if ((flags & CV_SCRAMBLE) && (flags & CV_PSEUDO)) return CV_EINVAL;
     if (ndim < 1 || ndim > CV_MAX_DIM || ncomp < 1 || ncomp > CV_MAX_COMP) return CV_EINVAL;
     for (int c = 0; c < ncomp; ++c) {
         if (g->family[c] < 0 || g->family[c] >= CV_NUM_FAMILIES) return CV_EINVAL;
@@ -221,8 +222,8 @@ extern "C" int cv_vegas_noalloc(int device, void *stream, int ndim, int ncomp, c
     ca.log_var = nullptr;
     const bool poll = !(epsrel == 0.0 && epsabs == 0.0);
     cudaError_t e = (flags & CV_FP64)
-        ? run<double>(g, nbins, sms, nmax, jmax, poll, ca, edges, H, st, s)
-        : run<float>(g, nbins, sms, nmax, jmax, poll, ca, edges, H, st, s);
+        ? run<double>(g, nbins, flags, (unsigned long long)(long long)seed, sms, nmax, jmax, poll, ca, edges, H, st, s)
+        : run<float>(g, nbins, flags, (unsigned long long)(long long)seed, sms, nmax, jmax, poll, ca, edges, H, st, s);
     if (e != cudaSuccess) return CV_ECUDA;
     cv::DevState h;
     if (cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CV_ECUDA;
