@@ -391,6 +391,7 @@ def run_ours(args):
     if not args.no_batch:
         line["batch4096"] = measure_batch(ctx, cg, W, args.warmup, args.steps)
     line["gaussian3d"] = measure_gaussian3d(ctx, cg, W)
+    line["generators"] = measure_generators(ctx, cg, W)
     if not args.no_large:
         line["large30d"] = measure_large(ctx, cg, W)
     if not args.no_materialised:
@@ -489,6 +490,44 @@ def measure_materialised(ctx, cg, W) -> dict:
             "library_bytes_per_sample": lib_bytes, "all_bytes_per_sample": all_bytes,
             "hbm_gbs_all_kernels": rate * all_bytes / 1e9,
             "integral": list(r.integral)}
+
+
+def measure_generators(ctx, cg, W, replicates: int = 8) -> dict:
+    """genz8d4c (FP32, run-time specialised) with the other point
+    generators: scrambled Sobol (randomized QMC: `replicates` independent
+    digital shifts; the spread of their results is the RQMC error estimate,
+    reported beside Vegas's own error) and pseudo-random Philox points.
+    Device-timed samples/s over the replicates."""
+    import numpy as np
+    import torch
+    p = W.genz8d4c()
+    g = cg.genz(p.ndim, p.families, p.a, p.u)
+    out = {"workload": f"genz8d4c with scrambled Sobol ({replicates} seeds) and pseudo-random points"}
+    for name, flag in (("scrambled", cg.SCRAMBLE), ("pseudo", cg.PSEUDO)):
+        res, ms = [], 0.0
+        for r in range(replicates if flag == cg.SCRAMBLE else 2):
+            I = ctx.integral(cg.spec(g, nbins=p.nbins, flags=cg.JIT | flag, maxeval=p.maxeval, nstart=p.nstart,
+                                     nincrease=p.nincrease, seed=1000 + r))
+            I.reset()
+            I.run()  # compiles the specialised kernel once
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            I.reset()
+            I.run()
+            s1.record()
+            torch.cuda.synchronize()
+            ms += s0.elapsed_time(s1)
+            res.append(I.result())
+            I.close()
+        ints = np.array([[r.integral[c] for c in range(p.ncomp)] for r in res])
+        errs = np.array([[r.error[c] for c in range(p.ncomp)] for r in res])
+        out[name] = {"value": len(res) * p.maxeval / (ms * 1e-3), "unit": UNIT,
+                     "integral_mean": ints.mean(axis=0).tolist(),
+                     "vegas_error": errs.mean(axis=0).tolist()}
+        if flag == cg.SCRAMBLE:
+            out[name]["rqmc_error"] = (ints.std(axis=0, ddof=1) / math.sqrt(len(res))).tolist()
+    return out
 
 
 def measure_gaussian3d(ctx, cg, W, reps: int = 20) -> dict:
