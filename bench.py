@@ -177,6 +177,12 @@ def _kernel_source_hash() -> str:
 def _profile_traffic(name: str):
     """DRAM bytes per launch of the sampling kernel from the committed ncu
     summary `name`, if it was taken on the current kernel sources."""
+    return _profile_value(name, "traffic_bytes_per_launch")
+
+
+def _profile_value(name: str, key: str):
+    """A figure ("- key: value") of the committed ncu summary `name`, if it
+    was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         text = open(path).read()
@@ -190,8 +196,8 @@ def _profile_traffic(name: str):
     if vals.get("source_sha") != _kernel_source_hash():
         return None
     try:
-        return float(vals["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
+        return float(vals[key].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
 
 
@@ -335,8 +341,17 @@ def run_ours(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(sm_max)
-    traffic = _profile_traffic("sampling_specialised_genz8d4c.md" if jit_compiled
-                               else "k_sample_generic_genz8d4c.md")
+    prof = "sampling_specialised_genz8d4c.md" if jit_compiled else "k_sample_generic_genz8d4c.md"
+    traffic = _profile_traffic(prof)
+    # the bound this kernel actually meets: instruction issue (one warp
+    # instruction per cycle per SM sub-partition), with the warp instructions
+    # of one launch from the committed ncu summary
+    inst = _profile_value(prof, "warp instructions")
+    issue_peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9
+    issue = None if inst is None else {
+        "warp_instructions_per_launch": inst, "achieved": inst / (k_ms / 1e3) / 1e9, "peak": issue_peak,
+        "unit": "G warp instructions/s", "frac": inst / (k_ms / 1e3) / 1e9 / issue_peak,
+        "peak_basis": f"{SM_COUNT} SMs x 4 schedulers x 1 instruction per cycle x {sm_max:.0f} MHz"}
 
     # ---- end to end through cv_vegas (host description in, host results out)
     h2d, d2h = cg.vegas_io_bytes(p.ndim, p.nbins)
@@ -378,6 +393,7 @@ def run_ours(args):
                      "kernel_ms": k_ms, "kernel_ms_generic": k_ms_generic,
                      "jit": {"available": jit_available, "compiled": jit_compiled},
                      "flops_per_sample": alg_flops_per_sample(p.ndim, p.families),
+                     "issue": issue,
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                    f"{sm_max:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"},
         "plain_fp64": {"value": world * samples_per_step / plain_s, "unit": UNIT,
@@ -404,6 +420,8 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"2 Vegas iterations x {n} points of the same workload, "
                                           f"FP64 oracle, {dt:.1f} s"}
+        if not args.no_sweep:
+            line["cost_sweep"] = measure_cost_sweep(ctx, cg, W, threads)
     if rank == 0:
         print(json.dumps(line), flush=True)
     integ.close()
@@ -527,6 +545,51 @@ def measure_generators(ctx, cg, W, replicates: int = 8) -> dict:
                      "vegas_error": errs.mean(axis=0).tolist()}
         if flag == cg.SCRAMBLE:
             out[name]["rqmc_error"] = (ints.std(axis=0, ddof=1) / math.sqrt(len(res))).tolist()
+    return out
+
+
+def measure_cost_sweep(ctx, cg, W, threads: int, delays=(0, 64, 256, 1024, 4096),
+                       cpu_seconds: float = 1.0) -> dict:
+    """Integrand cost against speed-up, the GPU counterpart of the paper's
+    calibrated-delay experiment (Sect. 4.1, Fig. 1): the Gaussian component of
+    genz8d4c with `delay` extra dependent multiply-adds per evaluation (the
+    value is unchanged).  Per delay: the run-time specialised GPU path on
+    5 x 1e7 points (device-timed) and the oracle on the host's cores on a
+    bounded sample (part of the CPU-baseline leg)."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    p = W.genz8d4c()
+    a, u = np.asarray(p.a)[3:4], np.asarray(p.u)[3:4]
+    out = {"workload": "genz8d4c's Gaussian component (ndim 8, 128 bins) with `delay` extra dependent "
+                       "multiply-adds per evaluation; GPU 5 x 1e7 points, FP32, specialised; oracle FP64 "
+                       f"on {threads} host threads", "points": []}
+    for dl in delays:
+        g = cg.genz(p.ndim, [3], a, u, delay=dl)
+        I = ctx.integral(cg.spec(g, nbins=p.nbins, flags=cg.JIT, maxeval=5 * p.nstart, nstart=p.nstart))
+        I.reset()
+        I.run()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        I.reset()
+        I.run()
+        s1.record()
+        torch.cuda.synchronize()
+        gpu = 5 * p.nstart / (s0.elapsed_time(s1) * 1e-3)
+        I.close()
+        prob = O.Problem(p.ndim, [3], a, u, nbins=p.nbins, bits=23, fp32_decide=True, delay=dl)
+        e = O.grid_uniform(p.ndim, p.nbins)
+        n = 4096 * threads
+        t = time.perf_counter()
+        O.sample(prob, e, 1, n, nthreads=threads)
+        dt = time.perf_counter() - t
+        n = max(n, int(n * cpu_seconds / max(dt, 1e-3)))
+        t = time.perf_counter()
+        O.sample(prob, e, 1, n, nthreads=threads)
+        cpu = n / (time.perf_counter() - t)
+        out["points"].append({"delay": dl, "gpu": gpu, "cpu": cpu, "speedup": gpu / cpu, "unit": UNIT})
     return out
 
 
@@ -674,6 +737,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-integral batch")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--no-materialised", action="store_true", help="skip the materialised-sample run")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the integrand-cost sweep")
     ap.add_argument("--no-large", action="store_true", help="skip the 30-dimension 1e9-point run")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window of the serving run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -118,13 +118,22 @@ extern "C" {
 
 /* One integral: ncomp components of one ndim-dimensional Genz problem.
  * a[c][i], u[c][i] are the parameters of component c (unused entries
- * ignored).  Component 0 drives the grid refinement. */
+ * ignored).  Component 0 drives the grid refinement.
+ * delay (0 <= delay <= CV_MAX_DELAY): an integrand-cost knob, the GPU
+ * counterpart of the calibrated delay the paper adds to its integrands
+ * (Sect. 4.1).  Every evaluation of every component also pays about delay
+ * dependent multiply-adds over the point's coordinates (the fused kernels
+ * run delay * ncomp of them as one chain per point, in rounds of ndim)
+ * whose bounded result enters as 0 * z: values are unchanged bit for bit,
+ * only the cost grows. */
+#define CV_MAX_DELAY (1 << 20)
 typedef struct {
     int ndim;
     int ncomp;
     int family[CV_MAX_COMP];
     double a[CV_MAX_COMP][CV_MAX_DIM];
     double u[CV_MAX_COMP][CV_MAX_DIM];
+    int delay;
 } cv_genz;
 
 typedef struct cv_ctx cv_ctx;

@@ -69,6 +69,7 @@ class _Problem(ctypes.Structure):
         ("u", (ctypes.c_double * MAX_DIM) * MAX_COMP),
         ("gen", ctypes.c_int),
         ("seed", ctypes.c_uint64),
+        ("delay", ctypes.c_int),
     ]
 
 
@@ -302,6 +303,7 @@ class Problem:
     fp32_decide: bool = False
     gen: int = 0           # point generator: SOBOL, SCRAMBLED or PSEUDO
     seed: int = 0          # Philox key of the scrambled and pseudo-random generators
+    delay: int = 0         # integrand-cost knob (extra multiply-adds per evaluation)
     V: np.ndarray = field(default=None, repr=False)
 
     @property
@@ -312,7 +314,7 @@ class Problem:
         p = _Problem()
         p.ndim, p.ncomp, p.nbins, p.bits = self.ndim, self.ncomp, self.nbins, self.bits
         p.fp32_decide = 1 if self.fp32_decide else 0
-        p.gen, p.seed = int(self.gen), int(self.seed)
+        p.gen, p.seed, p.delay = int(self.gen), int(self.seed), int(self.delay)
         a = np.asarray(self.a, dtype=np.float64).reshape(self.ncomp, self.ndim)
         u = np.asarray(self.u, dtype=np.float64).reshape(self.ncomp, self.ndim)
         for c in range(self.ncomp):

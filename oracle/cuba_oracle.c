@@ -66,6 +66,7 @@ typedef struct {
     double u[OR_MAX_COMP][OR_MAX_DIM];
     int gen;           /* point generator: OR_GEN_SOBOL, _SCRAMBLED, _PSEUDO */
     uint64_t seed;     /* key of the counter-based generator */
+    int delay;         /* integrand-cost knob: extra multiply-adds per evaluation */
 } or_problem;
 
 /* ------------------------------------------------------------------ */
@@ -534,6 +535,16 @@ static void *sample_range(void *arg)
         for (int c = 0; c < p->ncomp; ++c) {
             double f = genz_eval(p->family[c], ndim, p->a[c], p->u[c], x, x32,
                                  p->fp32_decide);
+            if (p->delay > 0) {
+                /* the cost knob (the paper's calibrated delay, Sect. 4.1):
+                 * rounds of ndim dependent multiply-adds z <- z/2 + x_d,
+                 * whose bounded result enters as 0 * z (value unchanged) */
+                double z = 0.0;
+                for (int j = 0; j < p->delay; j += ndim)
+                    for (int d = 0; d < ndim; ++d)
+                        z = fma(z, 0.5, x[d]);
+                f += 0.0 * z;
+            }
             double Jf = J * f;
             sum_add(&job->S1[c], Jf);
             sum_add(&job->S2[c], Jf * Jf);

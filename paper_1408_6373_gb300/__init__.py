@@ -55,11 +55,14 @@ class Genz(ctypes.Structure):
         ("family", ctypes.c_int * MAX_COMP),
         ("a", (ctypes.c_double * MAX_DIM) * MAX_COMP),
         ("u", (ctypes.c_double * MAX_DIM) * MAX_COMP),
+        ("delay", ctypes.c_int),
     ]
 
 
-def genz(ndim: int, families, a, u) -> Genz:
-    """Build a cv_genz from family ids and [ncomp, ndim] parameter arrays."""
+def genz(ndim: int, families, a, u, delay: int = 0) -> Genz:
+    """Build a cv_genz from family ids and [ncomp, ndim] parameter arrays
+    (delay: extra dependent multiply-adds per evaluation, a cost knob that
+    leaves the values unchanged)."""
     fams = [FAMILIES[f] if isinstance(f, str) else int(f) for f in families]
     nc = len(fams)
     a = np.broadcast_to(np.asarray(a, dtype=np.float64), (nc, ndim))
@@ -71,6 +74,7 @@ def genz(ndim: int, families, a, u) -> Genz:
         for d in range(ndim):
             g.a[c][d] = float(a[c, d])
             g.u[c][d] = float(u[c, d])
+    g.delay = int(delay)
     return g
 
 

@@ -228,6 +228,8 @@ static int check_genz(cv_ctx *ctx, const cv_genz *g)
             if (!std::isfinite(g->a[c][d]) || !std::isfinite(g->u[c][d]))
                 return fail_msg(ctx, CV_EINVAL, "non-finite parameter a/u[%d][%d]", c, d);
     }
+    if (g->delay < 0 || g->delay > CV_MAX_DELAY)
+        return fail_msg(ctx, CV_EINVAL, "delay %d outside 0..%d", g->delay, CV_MAX_DELAY);
     return CV_OK;
 }
 
@@ -239,6 +241,7 @@ static void fill_params(const cv_genz *g, GenzParams<Real> *p)
     memset(p, 0, sizeof(*p));
     p->ndim = g->ndim;
     p->ncomp = g->ncomp;
+    p->delay = g->delay;
     const bool f32 = sizeof(Real) == 4;
     for (int c = 0; c < g->ncomp; ++c) {
         const int fam = g->family[c];

@@ -189,6 +189,7 @@ struct RuntimeIntegrand {
     template <int C> __device__ __forceinline__ static Real p0(const GenzParams<Real> &g, int d) { return g.p0[C][d]; }
     template <int C> __device__ __forceinline__ static Real p1(const GenzParams<Real> &g, int d) { return g.p1[C][d]; }
     template <int C> __device__ __forceinline__ static Real q0(const GenzParams<Real> &g) { return g.q0[C]; }
+    __device__ __forceinline__ static int delay(const GenzParams<Real> &g) { return g.delay; }
     __device__ __forceinline__ static int table(const MapParams &m) { return m.li; }
     __device__ __forceinline__ static bool priv(const MapParams &m) { return m.priv != 0; }
     __device__ __forceinline__ static int nbins(int n) { return n; }
@@ -208,6 +209,22 @@ template <typename Real, int MODE>
 struct MatIntegrand : RuntimeIntegrand<Real> {
     static constexpr int kMode = MODE;
 };
+
+// The integrand-cost knob (cv_genz.delay): a chain of dependent
+// multiply-adds over the coordinates, in rounds of NDIM, z <- z/2 + x_d.
+// |z| stays below 2 max |x_d|, so 0 * z is an exact zero and the value it
+// is added to is unchanged; the compiler cannot drop the chain (0 * z would
+// not be zero for an infinite or NaN z).
+template <int NDIM, typename Real>
+__device__ __forceinline__ Real delay_chain(const Real (&x)[NDIM], int n)
+{
+    Real z = Real(0);
+    for (int j = 0; j < n; j += NDIM) {
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) z = fma_rn(z, Real(0.5), x[d]);
+    }
+    return z;
+}
 
 // FP32 Genz evaluation of component C.
 template <int NDIM, int C, class I>
@@ -485,7 +502,7 @@ __device__ __forceinline__ void sample_block(const SampleArgs<Real> &A, const Sm
                                              unsigned long long q, unsigned long long start,
                                              unsigned long long end, int lane, bool priv,
                                              Real (&p1)[CV_MAX_COMP], Real (&p2)[CV_MAX_COMP],
-                                             const Real (&fv)[CV_MAX_COMP])
+                                             const Real (&fv)[CV_MAX_COMP], int delay)
 {
     const int N = I::nbins(A.nbins);
     bool valid = true;
@@ -528,6 +545,9 @@ __device__ __forceinline__ void sample_block(const SampleArgs<Real> &A, const Sm
             }
         }
     } else {
+        // the integrand-cost knob: delay multiply-adds per component, run
+        // once per point and folded into J as J + 0 * z (exact: J is finite)
+        if (delay) J += Real(0) * delay_chain<NDIM>(x, delay * I::ncomp(A.g));
         eval_comp<NDIM, 0, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
         eval_comp<NDIM, 1, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
         eval_comp<NDIM, 2, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
@@ -571,6 +591,7 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
     const int li = (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0;  // direction table
     const bool priv = sizeof(Real) == 4 && POW2 && I::priv(A.map);
     const unsigned per = EDGE ? 1u : 2u;  // blocks per loop trip
+    const int delay = I::delay(A.g);      // (read once: the integrand-cost knob)
     for (unsigned r0 = 0; r0 < nsteps; r0 += kRun) {
         const unsigned r1 = min(r0 + kRun, nsteps);
         Real p1[CV_MAX_COMP], p2[CV_MAX_COMP];
@@ -588,19 +609,19 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
             if constexpr (I::kGen == 2) {
                 // pseudo-random points: fresh words for every block
                 pseudo_words<NDIM, W>(X, A.seed, q * 32ull + (unsigned long long)lane);
-                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2, fa);
+                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2, fa, delay);
                 if (!EDGE) {
                     pseudo_words<NDIM, W>(X, A.seed, (q + 1) * 32ull + (unsigned long long)lane);
-                    sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2, fb);
+                    sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2, fb, delay);
                 }
                 continue;
             }
-            sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2, fa);
+            sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2, fa, delay);
             if (EDGE) {
                 sobol_step<NDIM, W>(X, q, li);
             } else {
                 sobol_step_even<NDIM, W>(X, li);
-                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2, fb);
+                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2, fb, delay);
                 sobol_step<NDIM, W>(X, q + 1, li);
             }
         }
@@ -924,6 +945,11 @@ k_genz_points(const __grid_constant__ GenzParams<Real> g, const Real *x, Real *f
         if (g.ncomp > 1) v[1] = genz_eval<NDIM, 1>(g, xx);
         if (g.ncomp > 2) v[2] = genz_eval<NDIM, 2>(g, xx);
         if (g.ncomp > 3) v[3] = genz_eval<NDIM, 3>(g, xx);
+        if (g.delay) {
+#pragma unroll
+            for (int c = 0; c < CV_MAX_COMP; ++c)
+                if (c < g.ncomp) v[c] += Real(0) * delay_chain<NDIM>(xx, g.delay);
+        }
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c)
             if (c < g.ncomp) {

@@ -62,6 +62,7 @@ struct GenzParams {
     alignas(16) Real p0[CV_MAX_COMP][CV_MAX_DIM];
     alignas(16) Real p1[CV_MAX_COMP][CV_MAX_DIM];
     Real q0[CV_MAX_COMP];
+    int delay;                      // extra dependent FMAs per evaluation (cost knob)
 };
 
 // ---- point generators ----

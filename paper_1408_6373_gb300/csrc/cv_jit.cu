@@ -116,6 +116,8 @@ std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, 
         if (c < 3) s += ",";
     }
     s += "}; return v[C]; }\n";
+    s += "  __device__ __forceinline__ static constexpr int delay(const GenzParams<float>&) { return " +
+         std::to_string(g.delay) + "; }\n";
     s += "  __device__ __forceinline__ static constexpr int table(const MapParams&) { return " +
          std::to_string(pow2 ? a.map.li : 0) + "; }\n";
     s += "  __device__ __forceinline__ static constexpr bool priv(const MapParams&) { return " +

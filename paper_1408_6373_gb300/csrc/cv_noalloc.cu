@@ -63,6 +63,7 @@ void fill(const cv_genz *g, cv::GenzParams<Real> *p)
 {
     memset(p, 0, sizeof(*p));
     p->ndim = g->ndim;
+    p->delay = g->delay;
     p->ncomp = g->ncomp;
     const bool f32 = sizeof(Real) == 4;
     for (int c = 0; c < g->ncomp; ++c) {

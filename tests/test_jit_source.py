@@ -19,6 +19,14 @@ CASES = [
 ]
 
 
+def test_specialised_source_with_delay_compiles():
+    g = cg.genz(5, [cg.GAUSSIAN], 1.0, 0.5, delay=300)
+    ok, why = cg.jit_check(g, 64)
+    if not ok and "libnvrtc" in why:
+        pytest.skip(why)
+    assert ok, why
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _built():
     cg.build_library()

@@ -122,3 +122,14 @@ def test_vegas_with_random_points_meets_the_closed_form(gen):
     p = _gauss_problem(gen, 11)
     r = O.vegas(p, maxeval=8 * 20000, nstart=20000)
     assert abs(r.integral[0] - p.exact()[0]) < 4 * r.error[0]
+
+
+def test_delay_leaves_values_unchanged():
+    # the integrand-cost knob adds work, never value
+    edges = O.grid_uniform(3, 16)
+    base = O.sample(_gauss_problem(O.SOBOL, 0), edges, 1, 5000)
+    p = _gauss_problem(O.SOBOL, 0)
+    p.delay = 100
+    slow = O.sample(p, edges, 1, 5000)
+    for x, y in zip(base, slow):
+        assert np.array_equal(x, y)
