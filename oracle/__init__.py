@@ -89,6 +89,8 @@ def _bind(lib):
                 "or_philox4x64": (None, [_vp, _vp, _vp]),
                 "or_point_words": (None, [_int, _u64, _int, _vp, _u64, _vp]),
                 "or_point_coords": (_int, [_int, _u64, _int, _vp, _u64, _i64, _int, _vp]),
+                "or_suave": (_int, [_P(_Problem), _vp, _d, _d, _i64, _i64, _i64, _d, _int, _int, _int,
+                                    _P(_int), _P(_i64), _P(_int), _vp, _vp, _vp]),
                 "or_grid_uniform": (None, [_int, _int, _vp]),
                 "or_map": (_d, [_int, _int, _vp, _vp, _int, _vp, _vp]),
                 "or_genz": (_d, [_int, _int, _vp, _vp, _vp]),
@@ -421,3 +423,29 @@ def vegas(prob: Problem, epsrel=0.0, epsabs=0.0, mineval=0, maxeval=10**4,
     m = niter.value
     return VegasResult(neval.value, fail.value, m, out["integral"], out["error"],
                        out["chi2"], out["prob"], e, iI[:m], iV[:m])
+
+
+@dataclass
+class SuaveResult:
+    nregions: int
+    neval: int
+    fail: int
+    integral: np.ndarray
+    error: np.ndarray
+    boxes: np.ndarray      # [nregions, ndim, 2] final regions (lo, hi)
+
+
+def suave(prob: Problem, epsrel=0.0, epsabs=0.0, mineval=0, maxeval=10 ** 5, nnew=1000,
+          flatness=2.0, width=1, max_regions=4096, nthreads=1) -> SuaveResult:
+    """Suave (subregion-adaptive Vegas) as read in the C source."""
+    nc = prob.ncomp
+    integral, error = np.zeros(nc), np.zeros(nc)
+    boxes = np.zeros((max_regions, prob.ndim, 2))
+    nreg, neval, fail = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+    p = prob._c()
+    rc = _load().or_suave(ctypes.byref(p), _ptr(prob.directions()), epsrel, epsabs, mineval, maxeval,
+                          nnew, flatness, width, max_regions, nthreads, ctypes.byref(nreg),
+                          ctypes.byref(neval), ctypes.byref(fail), _ptr(integral), _ptr(error), _ptr(boxes))
+    if rc != 0:
+        raise ValueError(f"or_suave failed ({rc})")
+    return SuaveResult(nreg.value, neval.value, fail.value, integral, error, boxes[: nreg.value])

@@ -659,8 +659,10 @@ static void rebin_axis(int N, const double *r, const double *e, double *e_new)
     for (int k = 0; k < N; ++k)
         C[k + 1] = C[k] + r[k];
     double R = C[N];
-    e_new[0] = 0.0;
-    e_new[N] = 1.0;
+    /* only the interior edges move: the outer ones bound the domain (the
+     * unit interval for Vegas, a box side for a Suave region) */
+    e_new[0] = e[0];
+    e_new[N] = e[N];
     int k = 0;
     for (int m = 1; m < N; ++m) {
         double t = ((double)m * R) / (double)N;
@@ -916,5 +918,216 @@ int or_vegas(const or_problem *p, const uint64_t *V, double epsrel,
     free(Ij);
     free(Vj);
     free(H);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* 9. Suave: subregion-adaptive Vegas (the paper gives only its        */
+/*    argument list, Sect. 3.2.2; this is the reading stated below).   */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Every region is an axis-aligned box carrying its own Vegas grid, whose
+ * outer edges are the box (e_0 = lo, e_N = hi per axis), so the Vegas map
+ * of the box's grid puts points into the box and J includes its volume.
+ * Sampling a region: nnew fresh Sobol points (indices continuing one
+ * global stream from 1), estimate I = S1/n, var = (S2/n - I^2)/(n - 1),
+ * then the region's grid is refined from its histogram.  The refined grid
+ * shows where the integrand has structure: along an axis it does not
+ * depend on, the bins stay even.  So the fluctuation of axis d is the
+ * p-norm (p = flatness) of |ln(w_k / mean w)| over its bins,
+ *     fl_d = ((1/N) sum_k |ln(w_k / mean w)|^p)^(1/p).
+ * A round: stop with fail = 0 once neval >= mineval and every component
+ * has sqrt(sum var) <= max(epsabs, epsrel |sum I|); otherwise take the
+ * `width` regions of largest var (component 0; ties by position, only
+ * var > 0), split each along the axis of largest fluctuation (ties by the
+ * lower axis) at its middle edge e_(N/2) (equal shares of the grid), the children
+ * inheriting the grid with the split axis's half subdivided into N bins
+ * (each parent bin halved), and sample the children in order (left child
+ * first); the left child takes the parent's place, the right one is
+ * appended.  Adaptation also stops when a round, plus the final pass,
+ * would exceed maxeval, or max_regions.
+ * The samples that chose the partition are biased by that choice (a region
+ * is kept because its own sample looked flat), so they only steer: the
+ * result comes from a final pass that samples every region once more with
+ * nnew fresh points (in region order): integral = sum of the final I,
+ * error = sqrt(sum of the final var), fail = 0 if that error meets the
+ * goal, else 1.
+ */
+typedef struct {
+    double I[OR_MAX_COMP], var[OR_MAX_COMP];
+    double fluct[OR_MAX_DIM];
+} suave_region;
+
+static void suave_sample(const or_problem *p, const uint64_t *V, double *edges,
+                         uint64_t start, int64_t n, int nthreads, double flatness,
+                         suave_region *r)
+{
+    const int ndim = p->ndim, N = p->nbins;
+    double S1[OR_MAX_COMP], S2[OR_MAX_COMP];
+    double *H = calloc((size_t)ndim * N, sizeof(double));
+    or_sample(p, V, edges, start, n, nthreads, S1, S2, H);
+    for (int c = 0; c < p->ncomp; ++c) {
+        r->I[c] = S1[c] / (double)n;
+        r->var[c] = (S2[c] / (double)n - r->I[c] * r->I[c]) / (double)(n - 1);
+        if (!(r->var[c] > 0.0))
+            r->var[c] = 0.0;
+    }
+    or_refine(ndim, N, H, edges);
+    for (int d = 0; d < ndim; ++d) {
+        const double *e = edges + (size_t)d * (N + 1);
+        const double mean = (e[N] - e[0]) / N;
+        or_sum acc = {0, 0};
+        for (int k = 0; k < N; ++k)
+            sum_add(&acc, pow(fabs(log((e[k + 1] - e[k]) / mean)), flatness));
+        r->fluct[d] = pow(sum_value(&acc) / N, 1.0 / flatness);
+    }
+    free(H);
+}
+
+/* Children grids of a split of `pe` along axis a at edge N/2. */
+static void suave_children(int ndim, int N, int a, const double *pe, double *le, double *re)
+{
+    for (int d = 0; d < ndim; ++d) {
+        const double *e = pe + (size_t)d * (N + 1);
+        double *l = le + (size_t)d * (N + 1), *r = re + (size_t)d * (N + 1);
+        if (d != a) {
+            memcpy(l, e, sizeof(double) * (N + 1));
+            memcpy(r, e, sizeof(double) * (N + 1));
+            continue;
+        }
+        for (int j = 0; j < N / 2; ++j) {
+            l[2 * j] = e[j];
+            l[2 * j + 1] = 0.5 * (e[j] + e[j + 1]);
+            r[2 * j] = e[N / 2 + j];
+            r[2 * j + 1] = 0.5 * (e[N / 2 + j] + e[N / 2 + j + 1]);
+        }
+        l[N] = e[N / 2];
+        r[N] = e[N];
+    }
+}
+
+/* Suave as read above.  box_out (optional, [max_regions][ndim][2]) gets the
+ * final regions' boxes.  Returns 0, or -1 on bad arguments. */
+int or_suave(const or_problem *p, const uint64_t *V, double epsrel, double epsabs,
+             int64_t mineval, int64_t maxeval, int64_t nnew, double flatness, int width,
+             int max_regions, int nthreads, int *nregions, int64_t *neval, int *fail,
+             double *integral, double *error, double *box_out)
+{
+    const int ndim = p->ndim, N = p->nbins, nc = p->ncomp;
+    if (nnew < 2 || maxeval < nnew || width < 1 || max_regions < 1 || !(flatness > 0.0) ||
+        (N & 1) || N < 2)
+        return -1;
+    const size_t ge = (size_t)ndim * (N + 1);
+    double *grids = malloc(sizeof(double) * ge * (size_t)max_regions);
+    suave_region *R = malloc(sizeof(suave_region) * (size_t)max_regions);
+    int *order = malloc(sizeof(int) * (size_t)max_regions);
+    or_grid_uniform(ndim, N, grids);
+    uint64_t next = 1;
+    int nr = 1;
+    suave_sample(p, V, grids, next, nnew, nthreads, flatness, &R[0]);
+    next += (uint64_t)nnew;
+    int64_t done = nnew;
+    int status = 1;
+    for (;;) {
+        int ok = done >= mineval;
+        for (int c = 0; c < nc; ++c) {
+            or_sum I = {0, 0}, v = {0, 0};
+            for (int k = 0; k < nr; ++k) {
+                sum_add(&I, R[k].I[c]);
+                sum_add(&v, R[k].var[c]);
+            }
+            integral[c] = sum_value(&I);
+            error[c] = sqrt(sum_value(&v));
+            if (!(error[c] <= fmax(epsabs, epsrel * fabs(integral[c]))))
+                ok = 0;
+        }
+        if (ok) {
+            status = 0;
+            break;
+        }
+        /* the regions to split: largest var of component 0 first */
+        int K = 0;
+        for (int k = 0; k < nr; ++k)
+            if (R[k].var[0] > 0.0)
+                order[K++] = k;
+        for (int i = 1; i < K; ++i) { /* stable insertion sort, descending */
+            int x = order[i], j = i - 1;
+            while (j >= 0 && R[order[j]].var[0] < R[x].var[0]) {
+                order[j + 1] = order[j];
+                --j;
+            }
+            order[j + 1] = x;
+        }
+        if (K > width)
+            K = width;
+        if (K == 0) {
+            status = 0; /* every region exact */
+            break;
+        }
+        /* (room for this round and for the final pass over every region) */
+        const int64_t room = maxeval - done - (int64_t)nr * nnew;
+        if ((int64_t)K > room / (3 * nnew))
+            K = (int)(room / (3 * nnew));
+        if (K > (max_regions - nr))
+            K = max_regions - nr;
+        if (K <= 0)
+            break; /* fail = 1 */
+        for (int i = 0; i < K; ++i) {
+            const int k = order[i];
+            int a = 0;
+            for (int d = 1; d < ndim; ++d)
+                if (R[k].fluct[d] > R[k].fluct[a])
+                    a = d;
+            double *pe = grids + ge * (size_t)k;
+            double *le = malloc(sizeof(double) * ge), *re = grids + ge * (size_t)nr;
+            suave_children(ndim, N, a, pe, le, re);
+            memcpy(pe, le, sizeof(double) * ge);
+            free(le);
+            suave_sample(p, V, pe, next, nnew, nthreads, flatness, &R[k]);
+            next += (uint64_t)nnew;
+            suave_sample(p, V, re, next, nnew, nthreads, flatness, &R[nr]);
+            next += (uint64_t)nnew;
+            ++nr;
+            done += 2 * nnew;
+        }
+    }
+    /* the final pass: every region sampled afresh, the result from it alone */
+    if (done + (int64_t)nr * nnew <= maxeval || nr == 1) {
+        double *tmp = malloc(sizeof(double) * ge);
+        for (int k = 0; k < nr; ++k) {
+            memcpy(tmp, grids + ge * (size_t)k, sizeof(double) * ge);
+            suave_sample(p, V, tmp, next, nnew, nthreads, flatness, &R[k]);
+            next += (uint64_t)nnew;
+            done += nnew;
+        }
+        free(tmp);
+    }
+    status = 0;
+    for (int c = 0; c < nc; ++c) {
+        or_sum I = {0, 0}, v = {0, 0};
+        for (int k = 0; k < nr; ++k) {
+            sum_add(&I, R[k].I[c]);
+            sum_add(&v, R[k].var[c]);
+        }
+        integral[c] = sum_value(&I);
+        error[c] = sqrt(sum_value(&v));
+        if (!(error[c] <= fmax(epsabs, epsrel * fabs(integral[c]))))
+            status = 1;
+    }
+    if (done < mineval)
+        status = 1;
+    *nregions = nr;
+    *neval = done;
+    *fail = status;
+    if (box_out)
+        for (int k = 0; k < nr; ++k)
+            for (int d = 0; d < ndim; ++d) {
+                box_out[((size_t)k * ndim + d) * 2] = grids[ge * (size_t)k + (size_t)d * (N + 1)];
+                box_out[((size_t)k * ndim + d) * 2 + 1] = grids[ge * (size_t)k + (size_t)d * (N + 1) + N];
+            }
+    free(grids);
+    free(R);
+    free(order);
     return 0;
 }
