@@ -262,6 +262,41 @@ int cv_jit_check(const cv_genz *g, int nbins, int flags, char *log, int log_len)
  * this shape: kernel parameters in (h2d), the final state out (d2h). */
 int cv_vegas_io_bytes(int ndim, int nbins, int64_t *h2d, int64_t *d2h);
 
+/* ------------------------------------------------------------- Suave */
+/* Suave, the subregion-adaptive Vegas of the paper's argument list
+ * (Sect. 3.2.2: nnew, flatness, nregions; the paper gives no algorithm,
+ * so this is a stated reading).  Regions are axis-aligned boxes, each with
+ * its own Vegas grid of nbins bins per axis (nbins even) spanning the box.
+ *   Start: [0,1]^ndim sampled with nnew points, its grid refined.
+ *   Round: stop once neval >= mineval and every component's
+ *     sqrt(sum var) <= max(epsabs, epsrel |sum I|); else take the `width`
+ *     regions of largest variance of component 0 (ties by position, only
+ *     var > 0) and split each along the axis whose refined grid is least
+ *     even -- the flatness-norm of |ln(w_k / mean w)| over its bins, ties
+ *     by the lower axis -- at its middle edge; the children inherit the
+ *     grid with the split axis's half subdivided into nbins bins, and are
+ *     sampled (left first) with nnew fresh points each and refined.  The
+ *     left child replaces the parent, the right one is appended.
+ *   Stop adapting when a round plus the final pass would exceed maxeval or
+ *     max_regions.
+ *   Final pass: every region is sampled once more with nnew fresh points,
+ *     and the result comes from that pass alone (the samples that chose the
+ *     partition are biased by the choice): integral = sum of the regions'
+ *     I, error = sqrt(sum var); *fail = 0 if the goal is met, else 1.
+ * Points: one stream of indices from 1, never reused, mapped through each
+ * region's grid; flags as cv_vegas (CV_FP64, CV_JIT, CV_SCRAMBLE or
+ * CV_PSEUDO with seed).  With Sobol or scrambled points the final pass is
+ * correlated with the partition, so on discontinuous integrands the error
+ * can be underestimated; CV_PSEUDO gives independent points.
+ * boxes (host, may be null): [max_regions][ndim][2], the final regions'
+ * (lo, hi).  *nregions, *neval, *fail, integral[ncomp], error[ncomp] are
+ * host outputs.  Errors: CV_EINVAL (arguments), CV_ENOMEM, CV_ECUDA. */
+int cv_suave(cv_ctx *ctx, const cv_genz *g, int nbins, int flags, uint64_t seed,
+             double epsrel, double epsabs, int64_t mineval, int64_t maxeval,
+             int64_t nnew, double flatness, int width, int max_regions,
+             int *nregions, int64_t *neval, int *fail, double integral[],
+             double error[], double *boxes);
+
 /* ------------------------------------------- no-allocation Vegas call */
 /* cv_vegas for callers that cannot allocate device memory.  The paper has
  * no counterpart; this entry point exists because some callers of a GPU

@@ -119,6 +119,16 @@ def spec(g: Genz, nbins=64, flags=0, epsrel=0.0, epsabs=0.0, mineval=0, maxeval=
     return s
 
 
+@dataclass
+class SuaveResult:
+    nregions: int
+    neval: int
+    fail: int
+    integral: np.ndarray
+    error: np.ndarray
+    boxes: np.ndarray      # [nregions, ndim, 2] final regions (lo, hi)
+
+
 class ServerOpts(ctypes.Structure):
     """cv_server_opts."""
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_live", ctypes.c_int),
@@ -161,6 +171,8 @@ _SIGNATURES = {
     "cv_synchronize": (_i, [_vp]),
     "cv_sobol": (_i, [_vp, _i, _u64, _i64, _i, _vp]),
     "cv_points": (_i, [_vp, _i, _u64, _i64, _i, _i, _u64, _vp]),
+    "cv_suave": (_i, [_vp, _P(Genz), _i, _i, _u64, ctypes.c_double, ctypes.c_double, _i64, _i64, _i64,
+                      ctypes.c_double, _i, _i, _P(_i), _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_sample": (_i, [_vp, _P(Genz), _i, _vp, _u64, _i64, _i, _u64, _vp, _vp, _vp]),
     "cv_refine": (_i, [_vp, _i, _i, _vp, _vp]),
     "cv_vegas": (_i, [_vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64, _i64,
@@ -299,6 +311,19 @@ class Context:
         """DoSample: add sum J f, sum (J f)^2 and the f^2 histogram of n points."""
         self._check(self._lib.cv_sample(self._h, ctypes.byref(g), nbins, _ptr(edges), start, n,
                                         flags, seed, _ptr(S1), _ptr(S2), _ptr(H)), "cv_sample")
+
+    def suave(self, g: Genz, nbins=16, flags=0, seed=0, epsrel=0.0, epsabs=0.0, mineval=0,
+              maxeval=10 ** 5, nnew=1000, flatness=2.0, width=1, max_regions=4096) -> "SuaveResult":
+        """cv_suave: subregion-adaptive Vegas (see cubagpu.h for the reading)."""
+        nc = g.ncomp
+        integral, error = np.zeros(nc), np.zeros(nc)
+        boxes = np.zeros((max_regions, g.ndim, 2))
+        nreg, neval, fail = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        self._check(self._lib.cv_suave(self._h, ctypes.byref(g), nbins, flags, seed, epsrel, epsabs, mineval,
+                                       maxeval, nnew, flatness, width, max_regions, ctypes.byref(nreg),
+                                       ctypes.byref(neval), ctypes.byref(fail), integral.ctypes.data,
+                                       error.ctypes.data, boxes.ctypes.data), "cv_suave")
+        return SuaveResult(nreg.value, neval.value, fail.value, integral, error, boxes[: nreg.value])
 
     def refine(self, ndim: int, nbins: int, H, edges):
         self._check(self._lib.cv_refine(self._h, ndim, nbins, _ptr(H), _ptr(edges)), "cv_refine")

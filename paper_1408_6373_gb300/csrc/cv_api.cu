@@ -2164,3 +2164,245 @@ extern "C" int cv_vegas_cb(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev in
     }
     return rc;
 }
+
+// ------------------------------------------------------------ Suave
+// Subregion-adaptive Vegas as declared in cubagpu.h: the host takes every
+// decision from FP64 values read back from the device; the device samples
+// and refines the regions of a round concurrently on the side streams
+// (each region has its own grid, histogram and sums).
+namespace {
+
+struct SuaveRegion {
+    double I[CV_MAX_COMP], var[CV_MAX_COMP];
+    double fluct[CV_MAX_DIM];
+};
+
+struct SuaveMem {
+    double *edges = nullptr;  // [max_regions][ndim][N+1]
+    double *H = nullptr;      // [max_regions][ndim][N]
+    double *S = nullptr;      // [max_regions][2][CV_MAX_COMP]: S1 then S2
+};
+
+// Sample the regions of `list` (region list[i] with the nnew Sobol indices
+// from start + i nnew), refine their grids if `refine`, and read back their
+// estimates (and refined grids, with their fluctuation per axis).
+template <typename Real>
+int suave_pass(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, long long nnew,
+               const std::vector<int> &list, unsigned long long start, bool refine, double flatness,
+               const SuaveMem &m, std::vector<double> &h_edges, std::vector<SuaveRegion> &R)
+{
+    const int ndim = g->ndim, nc = g->ncomp;
+    const size_t ge = (size_t)ndim * (N + 1), gh = (size_t)ndim * N, gs = 2 * CV_MAX_COMP;
+    const cudaStream_t main = ctx->stream;
+    for (int r : list) {
+        CV_CUDA(ctx, cudaMemsetAsync(m.H + gh * r, 0, gh * sizeof(double), main));
+        CV_CUDA(ctx, cudaMemsetAsync(m.S + gs * r, 0, gs * sizeof(double), main));
+    }
+    CV_CUDA(ctx, cudaEventRecord(ctx->ev_fork, main));
+    for (int k = 0; k < kSideStreams; ++k) CV_CUDA(ctx, cudaStreamWaitEvent(ctx->side[k], ctx->ev_fork, 0));
+    int rc = CV_OK;
+    for (size_t i = 0; i < list.size() && rc == CV_OK; ++i) {
+        const int r = list[i];
+        ctx->stream = ctx->side[i % kSideStreams];
+        rc = launch_pass<Real>(ctx, g, N, m.edges + ge * r, start + (unsigned long long)i * nnew, nnew, nnew,
+                               m.S + gs * r, m.S + gs * r + CV_MAX_COMP, m.H + gh * r, nullptr, flags, seed);
+        if (rc == CV_OK && refine) {
+            cudaError_t e = launch_refine(ndim, N, m.H + gh * r, m.edges + ge * r, ctx->stream);
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "refine kernel launch");
+        }
+    }
+    ctx->stream = main;
+    for (int k = 0; k < kSideStreams; ++k) {
+        CV_CUDA(ctx, cudaEventRecord(ctx->ev_join[k], ctx->side[k]));
+        CV_CUDA(ctx, cudaStreamWaitEvent(main, ctx->ev_join[k], 0));
+    }
+    if (rc) return rc;
+    std::vector<double> S(gs * list.size());
+    for (size_t i = 0; i < list.size(); ++i) {
+        CV_CUDA(ctx, cudaMemcpyAsync(&S[gs * i], m.S + gs * list[i], gs * sizeof(double), cudaMemcpyDeviceToHost, main));
+        if (refine)
+            CV_CUDA(ctx, cudaMemcpyAsync(&h_edges[ge * list[i]], m.edges + ge * list[i], ge * sizeof(double),
+                                         cudaMemcpyDeviceToHost, main));
+    }
+    CV_CUDA(ctx, cudaStreamSynchronize(main));
+    for (size_t i = 0; i < list.size(); ++i) {
+        SuaveRegion &q = R[list[i]];
+        const double dn = (double)nnew;
+        for (int c = 0; c < nc; ++c) {
+            q.I[c] = S[gs * i + c] / dn;
+            q.var[c] = (S[gs * i + CV_MAX_COMP + c] / dn - q.I[c] * q.I[c]) / (dn - 1.0);
+            if (!(q.var[c] > 0.0)) q.var[c] = 0.0;
+        }
+        if (refine) {
+            for (int d = 0; d < ndim; ++d) {
+                const double *e = &h_edges[ge * list[i] + (size_t)d * (N + 1)];
+                const double mean = (e[N] - e[0]) / N;
+                double acc = 0.0;
+                for (int k = 0; k < N; ++k) acc += pow(fabs(log((e[k + 1] - e[k]) / mean)), flatness);
+                q.fluct[d] = pow(acc / N, 1.0 / flatness);
+            }
+        }
+    }
+    return CV_OK;
+}
+
+// The children of a split of grid pe along axis a at edge N/2.
+void suave_children(int ndim, int N, int a, const double *pe, double *le, double *re)
+{
+    for (int d = 0; d < ndim; ++d) {
+        const double *e = pe + (size_t)d * (N + 1);
+        double *l = le + (size_t)d * (N + 1), *r = re + (size_t)d * (N + 1);
+        if (d != a) {
+            memcpy(l, e, sizeof(double) * (N + 1));
+            memcpy(r, e, sizeof(double) * (N + 1));
+            continue;
+        }
+        for (int j = 0; j < N / 2; ++j) {
+            l[2 * j] = e[j];
+            l[2 * j + 1] = 0.5 * (e[j] + e[j + 1]);
+            r[2 * j] = e[N / 2 + j];
+            r[2 * j + 1] = 0.5 * (e[N / 2 + j] + e[N / 2 + j + 1]);
+        }
+        l[N] = e[N / 2];
+        r[N] = e[N];
+    }
+}
+
+template <typename Real>
+int suave_run(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, double epsrel, double epsabs,
+              long long mineval, long long maxeval, long long nnew, double flatness, int width, int max_regions,
+              const SuaveMem &m, int *nregions, int64_t *neval, int *fail, double *integral, double *error,
+              double *boxes)
+{
+    const int ndim = g->ndim, nc = g->ncomp;
+    const size_t ge = (size_t)ndim * (N + 1);
+    std::vector<double> h_edges(ge * (size_t)max_regions);
+    std::vector<SuaveRegion> R((size_t)max_regions);
+    for (int d = 0; d < ndim; ++d)
+        for (int k = 0; k <= N; ++k) h_edges[(size_t)d * (N + 1) + k] = (double)k / (double)N;
+    CV_CUDA(ctx, cudaMemcpyAsync(m.edges, h_edges.data(), ge * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    unsigned long long next = 1;
+    int nr = 1;
+    int rc = suave_pass<Real>(ctx, g, N, flags, seed, nnew, {0}, next, true, flatness, m, h_edges, R);
+    if (rc) return rc;
+    next += (unsigned long long)nnew;
+    long long done = nnew;
+    std::vector<int> order;
+    for (;;) {
+        bool ok = done >= mineval;
+        for (int c = 0; c < nc; ++c) {
+            double I = 0.0, v = 0.0;
+            for (int k = 0; k < nr; ++k) {
+                I += R[k].I[c];
+                v += R[k].var[c];
+            }
+            if (!(sqrt(v) <= std::max(epsabs, epsrel * fabs(I)))) ok = false;
+        }
+        if (ok) break;
+        order.clear();
+        for (int k = 0; k < nr; ++k)
+            if (R[k].var[0] > 0.0) order.push_back(k);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return R[x].var[0] > R[y].var[0]; });
+        long long K = std::min<long long>((long long)order.size(), width);
+        if (K == 0) break;
+        const long long room = maxeval - done - (long long)nr * nnew;
+        K = std::min(K, room / (3 * nnew));
+        K = std::min<long long>(K, max_regions - nr);
+        if (K <= 0) break;
+        std::vector<int> list;
+        std::vector<double> child((size_t)ge);
+        for (long long i = 0; i < K; ++i) {
+            const int k = order[(size_t)i];
+            int a = 0;
+            for (int d = 1; d < ndim; ++d)
+                if (R[k].fluct[d] > R[k].fluct[a]) a = d;
+            double *pe = &h_edges[ge * k];
+            double *re = &h_edges[ge * nr];
+            suave_children(ndim, N, a, pe, child.data(), re);
+            memcpy(pe, child.data(), sizeof(double) * ge);
+            CV_CUDA(ctx, cudaMemcpyAsync(m.edges + ge * k, pe, ge * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            CV_CUDA(ctx, cudaMemcpyAsync(m.edges + ge * nr, re, ge * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            // (pageable copies: the host buffers may change only after the copy)
+            CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            list.push_back(k);
+            list.push_back(nr);
+            ++nr;
+        }
+        rc = suave_pass<Real>(ctx, g, N, flags, seed, nnew, list, next, true, flatness, m, h_edges, R);
+        if (rc) return rc;
+        next += (unsigned long long)list.size() * nnew;
+        done += (long long)list.size() * nnew;
+    }
+    // the final pass: every region sampled afresh, its grid kept
+    if (done + (long long)nr * nnew <= maxeval || nr == 1) {
+        std::vector<int> all((size_t)nr);
+        for (int k = 0; k < nr; ++k) all[(size_t)k] = k;
+        rc = suave_pass<Real>(ctx, g, N, flags, seed, nnew, all, next, false, flatness, m, h_edges, R);
+        if (rc) return rc;
+        done += (long long)nr * nnew;
+    }
+    int status = 0;
+    for (int c = 0; c < nc; ++c) {
+        double I = 0.0, v = 0.0;
+        for (int k = 0; k < nr; ++k) {
+            I += R[k].I[c];
+            v += R[k].var[c];
+        }
+        integral[c] = I;
+        error[c] = sqrt(v);
+        if (!(error[c] <= std::max(epsabs, epsrel * fabs(I)))) status = 1;
+    }
+    if (done < mineval) status = 1;
+    *nregions = nr;
+    *neval = done;
+    *fail = status;
+    if (boxes)
+        for (int k = 0; k < nr; ++k)
+            for (int d = 0; d < ndim; ++d) {
+                boxes[((size_t)k * ndim + d) * 2] = h_edges[ge * k + (size_t)d * (N + 1)];
+                boxes[((size_t)k * ndim + d) * 2 + 1] = h_edges[ge * k + (size_t)d * (N + 1) + N];
+            }
+    return CV_OK;
+}
+
+}  // namespace
+
+extern "C" int cv_suave(cv_ctx *ctx, const cv_genz *g, int nbins, int flags, uint64_t seed, double epsrel,
+                        double epsabs, int64_t mineval, int64_t maxeval, int64_t nnew, double flatness, int width,
+                        int max_regions, int *nregions, int64_t *neval, int *fail, double integral[],
+                        double error[], double *boxes)
+{
+    if (!ctx) return CV_EINVAL;
+    int rc = check_genz(ctx, g);
+    if (rc) return rc;
+    if (nbins < CV_MIN_BINS || nbins > CV_MAX_BINS || (nbins & 1))
+        return fail_msg(ctx, CV_EINVAL, "nbins must be even, %d..%d", CV_MIN_BINS, CV_MAX_BINS);
+    if (nnew < 2 || maxeval < nnew || mineval < 0 || width < 1 || max_regions < 1 || !(flatness > 0.0) ||
+        !(epsrel >= 0) || !(epsabs >= 0))
+        return fail_msg(ctx, CV_EINVAL, "need nnew >= 2, maxeval >= nnew, width, max_regions >= 1, flatness > 0");
+    if ((uint64_t)maxeval >= CV_INDEX_LIMIT) return fail_msg(ctx, CV_EINVAL, "maxeval beyond the 2^52 index range");
+    if ((flags & CV_SCRAMBLE) && (flags & CV_PSEUDO))
+        return fail_msg(ctx, CV_EINVAL, "CV_SCRAMBLE and CV_PSEUDO exclude each other");
+    if (!nregions || !neval || !fail || !integral || !error) return fail_msg(ctx, CV_EINVAL, "null output");
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int ndim = g->ndim;
+    const size_t ge = (size_t)ndim * (nbins + 1), gh = (size_t)ndim * nbins, gs = 2 * CV_MAX_COMP;
+    SuaveMem m;
+    const size_t bytes = sizeof(double) * (ge + gh + gs) * (size_t)max_regions;
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_msg(ctx, CV_ENOMEM, "device allocation for %d regions failed", max_regions);
+    }
+    m.edges = (double *)mem;
+    m.H = m.edges + ge * (size_t)max_regions;
+    m.S = m.H + gh * (size_t)max_regions;
+    rc = (flags & CV_FP64)
+        ? suave_run<double>(ctx, g, nbins, flags, seed, epsrel, epsabs, mineval, maxeval, nnew, flatness, width,
+                            max_regions, m, nregions, neval, fail, integral, error, boxes)
+        : suave_run<float>(ctx, g, nbins, flags, seed, epsrel, epsabs, mineval, maxeval, nnew, flatness, width,
+                           max_regions, m, nregions, neval, fail, integral, error, boxes);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(mem);
+    return rc;
+}
