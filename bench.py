@@ -408,6 +408,7 @@ def run_ours(args):
         line["batch4096"] = measure_batch(ctx, cg, W, args.warmup, args.steps)
     line["gaussian3d"] = measure_gaussian3d(ctx, cg, W)
     line["generators"] = measure_generators(ctx, cg, W)
+    line["suave"] = measure_suave(ctx, cg)
     if not args.no_large:
         line["large30d"] = measure_large(ctx, cg, W)
     if not args.no_materialised:
@@ -422,6 +423,7 @@ def run_ours(args):
                                           f"FP64 oracle, {dt:.1f} s"}
         if not args.no_sweep:
             line["cost_sweep"] = measure_cost_sweep(ctx, cg, W, threads)
+        line["suave"]["cpu_baseline"] = suave_cpu_rate(threads)
     if rank == 0:
         print(json.dumps(line), flush=True)
     integ.close()
@@ -591,6 +593,43 @@ def measure_cost_sweep(ctx, cg, W, threads: int, delays=(0, 64, 256, 1024, 4096)
         cpu = n / (time.perf_counter() - t)
         out["points"].append({"delay": dl, "gpu": gpu, "cpu": cpu, "speedup": gpu / cpu, "unit": UNIT})
     return out
+
+
+SUAVE_PROBLEM = dict(ndim=6, a=[8.0, 6.0, 7.0, 5.0, 9.0, 6.5], u=[0.3, 0.6, 0.45, 0.7, 0.5, 0.35])
+
+
+def measure_suave(ctx, cg) -> dict:
+    """Suave (subregion-adaptive Vegas) on a peaked 6-dimensional Gaussian,
+    FP32 with the run-time specialised kernel: 32 splits per round, 2^18
+    points per region sampling, to relative accuracy 1e-5; wall time to the
+    result (host decisions and device passes)."""
+    import numpy as np
+    P = SUAVE_PROBLEM
+    g = cg.genz(P["ndim"], [3], np.array([P["a"]]), np.array([P["u"]]))
+    kw = dict(nbins=32, flags=cg.JIT, epsrel=1e-5, maxeval=2 * 10 ** 9, nnew=1 << 18, width=32, max_regions=4096)
+    ctx.suave(g, **dict(kw, maxeval=4 << 18))  # compiles the specialised kernel
+    t = time.perf_counter()
+    r = ctx.suave(g, **kw)
+    dt = time.perf_counter() - t
+    return {"workload": "suave: Gaussian ndim 6, a = 5..9, FP32 specialised, 32 bins, 32 splits per round, "
+                        "2^18 points per region sampling, epsrel 1e-5",
+            "value": r.neval / dt, "unit": UNIT, "seconds": dt, "neval": r.neval, "nregions": r.nregions,
+            "fail": r.fail, "integral": float(r.integral[0]), "error": float(r.error[0])}
+
+
+def suave_cpu_rate(threads: int, budget: int = 1 << 22) -> dict:
+    """The oracle's Suave on the same problem and settings with a bounded
+    budget (CPU-baseline leg): samples/s on the host's cores."""
+    import numpy as np
+
+    import oracle as O
+    P = SUAVE_PROBLEM
+    prob = O.Problem(P["ndim"], [3], np.array([P["a"]]), np.array([P["u"]]), nbins=32)
+    t = time.perf_counter()
+    r = O.suave(prob, epsrel=1e-5, maxeval=budget, nnew=1 << 15, width=32, max_regions=4096, nthreads=threads)
+    dt = time.perf_counter() - t
+    return {"value": r.neval / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"oracle Suave, {r.neval} points (2^15 per region sampling), FP64, {dt:.1f} s"}
 
 
 def measure_gaussian3d(ctx, cg, W, reps: int = 20) -> dict:
