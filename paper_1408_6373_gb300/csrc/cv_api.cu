@@ -1179,7 +1179,8 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         off[i] = total;
         total += sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255) +
                  ((((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255);
-        const bool p2 = (N & (N - 1)) == 0;
+        // (the map's form decides the kernel: powers of two from 32 bins)
+        const bool p2 = make_map(N, ndim, false).pow2 != 0;
         int c = -1;
         for (size_t k = 0; k < B->classes.size(); ++k)
             if (B->classes[k].ndim == ndim && B->classes[k].pow2 == p2) c = (int)k;
@@ -1594,7 +1595,7 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
     int64_t round_samples = 0;
     for (const Request &r : live) {
         const int ndim = r.spec.g.ndim;
-        const bool p2 = (r.spec.nbins & (r.spec.nbins - 1)) == 0;
+        const bool p2 = make_map(r.spec.nbins, ndim, false).pow2 != 0;  // (powers of two from 32 bins)
         Cls *c = nullptr;
         for (Cls &k : cls)
             if (k.ndim == ndim && k.pow2 == p2) c = &k;
@@ -2168,8 +2169,13 @@ extern "C" int cv_vegas_cb(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev in
 // ------------------------------------------------------------ Suave
 // Subregion-adaptive Vegas as declared in cubagpu.h: the host takes every
 // decision from FP64 values read back from the device; the device samples
-// and refines the regions of a round concurrently on the side streams
-// (each region has its own grid, histogram and sums).
+// and refines the regions of a pass together (each region has its own grid,
+// histogram and sums).  In FP32 with Sobol or scrambled points a pass is one
+// launch of the batched sampling kernel over a queue of tiles of all its
+// regions (regions are batch items), one batched refinement and two small
+// kernels that stage the regions in and their results out through mapped
+// pinned memory; otherwise every region is one sampling launch (FP64 and
+// pseudo-random points), spread over the side streams.
 namespace {
 
 struct SuaveRegion {
@@ -2177,24 +2183,186 @@ struct SuaveRegion {
     double fluct[CV_MAX_DIM];
 };
 
+// One region of a batched pass: its Sobol indices start at `start`; its
+// grid is taken from the host mirror first if `upload`.
+struct SuaveEntry {
+    int region;
+    int upload;
+    unsigned long long start;
+};
+
 struct SuaveMem {
     double *edges = nullptr;  // [max_regions][ndim][N+1]
     double *H = nullptr;      // [max_regions][ndim][N]
     double *S = nullptr;      // [max_regions][2][CV_MAX_COMP]: S1 then S2
+    double *h_edges = nullptr;  // pinned host mirrors of edges, S and (batched) fluct
+    double *h_S = nullptr;
+    double *h_fluct = nullptr;  // [max_regions][CV_MAX_DIM]
+    // batched form
+    bool batched = false;
+    bool pow2 = false;
+    int grid = 0;               // persistent sampling grid
+    int tile_cap = 0;           // tiles one pass may queue
+    BatchItem *d_items = nullptr;  // [max_regions]: region k is item k
+    int *d_counter = nullptr;
+    char *d_stage = nullptr, *h_stage = nullptr;  // entries, tiles, axes of a pass
+    double *dh_edges = nullptr, *dh_S = nullptr, *dh_fluct = nullptr;  // device addresses of the mirrors
 };
+
+__global__ void k_suave_prep(const SuaveEntry *E, const BatchItem *items, const double *dh_edges, int ndim,
+                             int N, long long nnew, int *counter)
+{
+    const SuaveEntry e = E[blockIdx.x];
+    const BatchItem &it = items[e.region];
+    const int ge = ndim * (N + 1);
+    if (e.upload)
+        for (int i = threadIdx.x; i < ge; i += blockDim.x) it.edges[i] = dh_edges[(size_t)ge * e.region + i];
+    for (int i = threadIdx.x; i < ndim * N; i += blockDim.x) it.H[i] = 0.0;
+    if (threadIdx.x < CV_MAX_COMP) {
+        it.st->S1[threadIdx.x] = 0.0;
+        it.st->S2[threadIdx.x] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        it.st->next_index = e.start;
+        it.st->n_cur = nnew;
+        it.st->stopped = 0;
+        if (blockIdx.x == 0) *counter = 0;
+    }
+}
+
+// The listed regions' sums, and after a refinement their grids and the
+// fluctuation of each axis, (mean_k |ln(w_k / mean w)|^flatness)^(1/flatness)
+// (one warp per axis), into the host mirrors.
+__global__ void k_suave_gather(const SuaveEntry *E, const BatchItem *items, double *dh_S, double *dh_edges,
+                               double *dh_fluct, int ndim, int N, int refined, double flatness)
+{
+    const int r = E[blockIdx.x].region;
+    const BatchItem &it = items[r];
+    const int ge = ndim * (N + 1);
+    if (threadIdx.x < CV_MAX_COMP) {
+        dh_S[(size_t)2 * CV_MAX_COMP * r + threadIdx.x] = it.st->S1[threadIdx.x];
+        dh_S[(size_t)2 * CV_MAX_COMP * r + CV_MAX_COMP + threadIdx.x] = it.st->S2[threadIdx.x];
+    }
+    if (!refined) return;
+    for (int i = threadIdx.x; i < ge; i += blockDim.x) dh_edges[(size_t)ge * r + i] = it.edges[i];
+    const int lane = threadIdx.x & 31;
+    for (int d = threadIdx.x >> 5; d < ndim; d += blockDim.x >> 5) {
+        const double *e = it.edges + (size_t)d * (N + 1);
+        const double mean = (e[N] - e[0]) / N;
+        double acc = 0.0;
+        for (int k = lane; k < N; k += 32) acc += pow(fabs(log((e[k + 1] - e[k]) / mean)), flatness);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) dh_fluct[(size_t)CV_MAX_DIM * r + d] = pow(acc / N, 1.0 / flatness);
+    }
+}
+
+// The estimates of the listed regions from their sums in the host mirror,
+// and (refined grids) the fluctuation of each axis of their grids.
+void suave_read(const cv_genz *g, int N, long long nnew, const std::vector<int> &list, bool refined,
+                double flatness, const SuaveMem &m, std::vector<SuaveRegion> &R)
+{
+    const int ndim = g->ndim, nc = g->ncomp;
+    const size_t ge = (size_t)ndim * (N + 1), gs = 2 * CV_MAX_COMP;
+    for (size_t i = 0; i < list.size(); ++i) {
+        SuaveRegion &q = R[list[i]];
+        const double dn = (double)nnew;
+        const double *S = m.h_S + gs * list[i];
+        for (int c = 0; c < nc; ++c) {
+            q.I[c] = S[c] / dn;
+            q.var[c] = (S[CV_MAX_COMP + c] / dn - q.I[c] * q.I[c]) / (dn - 1.0);
+            if (!(q.var[c] > 0.0)) q.var[c] = 0.0;
+        }
+        if (refined && m.batched) {
+            for (int d = 0; d < ndim; ++d) q.fluct[d] = m.h_fluct[(size_t)CV_MAX_DIM * list[i] + d];
+        } else if (refined) {
+            for (int d = 0; d < ndim; ++d) {
+                const double *e = &m.h_edges[ge * list[i] + (size_t)d * (N + 1)];
+                const double mean = (e[N] - e[0]) / N;
+                double acc = 0.0;
+                for (int k = 0; k < N; ++k) acc += pow(fabs(log((e[k + 1] - e[k]) / mean)), flatness);
+                q.fluct[d] = pow(acc / N, 1.0 / flatness);
+            }
+        }
+    }
+}
+
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// A batched pass: the listed regions' tiles in one queue.  Tiles are powers
+// of two of 32-point blocks, at least 64, large enough to keep the queue
+// within tile_cap and no larger than needed for four tiles per resident CTA.
+int suave_pass_batched(cv_ctx *ctx, const cv_genz *g, int N, long long nnew, const std::vector<int> &list,
+                       unsigned long long start, bool refine, bool upload, double flatness, const SuaveMem &m,
+                       std::vector<SuaveRegion> &R)
+{
+    const int ndim = g->ndim;
+    const long long nl = (long long)list.size();
+    const long long span = (nnew + 31) / 32 + 2;  // 32-point blocks of one region, with the even alignment
+    long long TB = 64;
+    while (TB < 1024 && nl * ((span + TB - 1) / TB) > 4LL * m.grid) TB <<= 1;
+    while (nl * ((span + TB - 1) / TB + 1) > m.tile_cap) TB <<= 1;
+    SuaveEntry *E = reinterpret_cast<SuaveEntry *>(m.h_stage);
+    const size_t off_t = align16((size_t)nl * sizeof(SuaveEntry));
+    Tile *T = reinterpret_cast<Tile *>(m.h_stage + off_t);
+    int nt = 0;
+    for (long long i = 0; i < nl; ++i) {
+        const unsigned long long s = start + (unsigned long long)i * (unsigned long long)nnew;
+        E[i].region = list[(size_t)i];
+        E[i].upload = upload ? 1 : 0;
+        E[i].start = s;
+        // (tiles start on even 32-point blocks: see run_steps)
+        const unsigned long long qa = (s >> 5) & ~1ull, qb = (s + (unsigned long long)nnew + 31) >> 5;
+        for (unsigned long long q = qa; q < qb; q += (unsigned long long)TB) {
+            T[nt].item = list[(size_t)i];
+            T[nt].nblk = (int)(qb - q < (unsigned long long)TB ? qb - q : (unsigned long long)TB);
+            T[nt].q0 = q;
+            ++nt;
+        }
+    }
+    const size_t off_a = off_t + align16((size_t)nt * sizeof(Tile));
+    int2 *A = reinterpret_cast<int2 *>(m.h_stage + off_a);
+    const int naxes = refine ? (int)nl * ndim : 0;
+    for (int i = 0; i < naxes; ++i) A[i] = make_int2(list[(size_t)(i / ndim)], i % ndim);
+    const size_t bytes = off_a + (size_t)naxes * sizeof(int2);
+    const cudaStream_t s = ctx->stream;
+    CV_CUDA(ctx, cudaMemcpyAsync(m.d_stage, m.h_stage, bytes, cudaMemcpyHostToDevice, s));
+    const SuaveEntry *dE = reinterpret_cast<const SuaveEntry *>(m.d_stage);
+    k_suave_prep<<<(unsigned)nl, 256, 0, s>>>(dE, m.d_items, m.dh_edges, ndim, N, nnew, m.d_counter);
+    CV_CUDA(ctx, cudaGetLastError());
+    BatchSampleArgs a;
+    a.items = m.d_items;
+    a.tiles = reinterpret_cast<const Tile *>(m.d_stage + off_t);
+    a.ntiles = nt;
+    a.stride = N;
+    a.counter = m.d_counter;
+    CV_CUDA(ctx, dispatch_batch_sample(ndim, m.pow2, a, m.grid < nt ? m.grid : nt, s));
+    if (refine)
+        CV_CUDA(ctx, launch_batch_refine(m.d_items, reinterpret_cast<const int2 *>(m.d_stage + off_a), naxes, s));
+    k_suave_gather<<<(unsigned)nl, 256, 0, s>>>(dE, m.d_items, m.dh_S, m.dh_edges, m.dh_fluct, ndim, N,
+                                                 refine ? 1 : 0, flatness);
+    CV_CUDA(ctx, cudaGetLastError());
+    CV_CUDA(ctx, cudaStreamSynchronize(s));
+    suave_read(g, N, nnew, list, refine, flatness, m, R);
+    return CV_OK;
+}
 
 // Sample the regions of `list` (region list[i] with the nnew Sobol indices
 // from start + i nnew), refine their grids if `refine`, and read back their
 // estimates (and refined grids, with their fluctuation per axis).
 template <typename Real>
 int suave_pass(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, long long nnew,
-               const std::vector<int> &list, unsigned long long start, bool refine, double flatness,
-               const SuaveMem &m, std::vector<double> &h_edges, std::vector<SuaveRegion> &R)
+               const std::vector<int> &list, unsigned long long start, bool refine, bool upload, double flatness,
+               const SuaveMem &m, std::vector<SuaveRegion> &R)
 {
-    const int ndim = g->ndim, nc = g->ncomp;
+    if (m.batched) return suave_pass_batched(ctx, g, N, nnew, list, start, refine, upload, flatness, m, R);
+    double *const h_edges = m.h_edges;
+    const int ndim = g->ndim;
     const size_t ge = (size_t)ndim * (N + 1), gh = (size_t)ndim * N, gs = 2 * CV_MAX_COMP;
     const cudaStream_t main = ctx->stream;
     for (int r : list) {
+        if (upload)
+            CV_CUDA(ctx, cudaMemcpyAsync(m.edges + ge * r, h_edges + ge * r, ge * sizeof(double),
+                                         cudaMemcpyHostToDevice, main));
         CV_CUDA(ctx, cudaMemsetAsync(m.H + gh * r, 0, gh * sizeof(double), main));
         CV_CUDA(ctx, cudaMemsetAsync(m.S + gs * r, 0, gs * sizeof(double), main));
     }
@@ -2217,32 +2385,16 @@ int suave_pass(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, l
         CV_CUDA(ctx, cudaStreamWaitEvent(main, ctx->ev_join[k], 0));
     }
     if (rc) return rc;
-    std::vector<double> S(gs * list.size());
+    // (pinned mirrors: the copies queue without host round trips)
     for (size_t i = 0; i < list.size(); ++i) {
-        CV_CUDA(ctx, cudaMemcpyAsync(&S[gs * i], m.S + gs * list[i], gs * sizeof(double), cudaMemcpyDeviceToHost, main));
+        CV_CUDA(ctx, cudaMemcpyAsync(m.h_S + gs * list[i], m.S + gs * list[i], gs * sizeof(double),
+                                     cudaMemcpyDeviceToHost, main));
         if (refine)
             CV_CUDA(ctx, cudaMemcpyAsync(&h_edges[ge * list[i]], m.edges + ge * list[i], ge * sizeof(double),
                                          cudaMemcpyDeviceToHost, main));
     }
     CV_CUDA(ctx, cudaStreamSynchronize(main));
-    for (size_t i = 0; i < list.size(); ++i) {
-        SuaveRegion &q = R[list[i]];
-        const double dn = (double)nnew;
-        for (int c = 0; c < nc; ++c) {
-            q.I[c] = S[gs * i + c] / dn;
-            q.var[c] = (S[gs * i + CV_MAX_COMP + c] / dn - q.I[c] * q.I[c]) / (dn - 1.0);
-            if (!(q.var[c] > 0.0)) q.var[c] = 0.0;
-        }
-        if (refine) {
-            for (int d = 0; d < ndim; ++d) {
-                const double *e = &h_edges[ge * list[i] + (size_t)d * (N + 1)];
-                const double mean = (e[N] - e[0]) / N;
-                double acc = 0.0;
-                for (int k = 0; k < N; ++k) acc += pow(fabs(log((e[k + 1] - e[k]) / mean)), flatness);
-                q.fluct[d] = pow(acc / N, 1.0 / flatness);
-            }
-        }
-    }
+    suave_read(g, N, nnew, list, refine, flatness, m, R);
     return CV_OK;
 }
 
@@ -2276,14 +2428,13 @@ int suave_run(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, do
 {
     const int ndim = g->ndim, nc = g->ncomp;
     const size_t ge = (size_t)ndim * (N + 1);
-    std::vector<double> h_edges(ge * (size_t)max_regions);
+    double *const h_edges = m.h_edges;
     std::vector<SuaveRegion> R((size_t)max_regions);
     for (int d = 0; d < ndim; ++d)
         for (int k = 0; k <= N; ++k) h_edges[(size_t)d * (N + 1) + k] = (double)k / (double)N;
-    CV_CUDA(ctx, cudaMemcpyAsync(m.edges, h_edges.data(), ge * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     unsigned long long next = 1;
     int nr = 1;
-    int rc = suave_pass<Real>(ctx, g, N, flags, seed, nnew, {0}, next, true, flatness, m, h_edges, R);
+    int rc = suave_pass<Real>(ctx, g, N, flags, seed, nnew, {0}, next, true, true, flatness, m, R);
     if (rc) return rc;
     next += (unsigned long long)nnew;
     long long done = nnew;
@@ -2302,8 +2453,11 @@ int suave_run(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, do
         order.clear();
         for (int k = 0; k < nr; ++k)
             if (R[k].var[0] > 0.0) order.push_back(k);
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return R[x].var[0] > R[y].var[0]; });
         long long K = std::min<long long>((long long)order.size(), width);
+        // the K largest var[0], ties in region order (as a stable sort would)
+        std::partial_sort(order.begin(), order.begin() + K, order.end(), [&](int x, int y) {
+            return R[x].var[0] > R[y].var[0] || (R[x].var[0] == R[y].var[0] && x < y);
+        });
         if (K == 0) break;
         const long long room = maxeval - done - (long long)nr * nnew;
         K = std::min(K, room / (3 * nnew));
@@ -2320,15 +2474,11 @@ int suave_run(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, do
             double *re = &h_edges[ge * nr];
             suave_children(ndim, N, a, pe, child.data(), re);
             memcpy(pe, child.data(), sizeof(double) * ge);
-            CV_CUDA(ctx, cudaMemcpyAsync(m.edges + ge * k, pe, ge * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-            CV_CUDA(ctx, cudaMemcpyAsync(m.edges + ge * nr, re, ge * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-            // (pageable copies: the host buffers may change only after the copy)
-            CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
             list.push_back(k);
             list.push_back(nr);
             ++nr;
         }
-        rc = suave_pass<Real>(ctx, g, N, flags, seed, nnew, list, next, true, flatness, m, h_edges, R);
+        rc = suave_pass<Real>(ctx, g, N, flags, seed, nnew, list, next, true, true, flatness, m, R);
         if (rc) return rc;
         next += (unsigned long long)list.size() * nnew;
         done += (long long)list.size() * nnew;
@@ -2337,7 +2487,7 @@ int suave_run(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, do
     if (done + (long long)nr * nnew <= maxeval || nr == 1) {
         std::vector<int> all((size_t)nr);
         for (int k = 0; k < nr; ++k) all[(size_t)k] = k;
-        rc = suave_pass<Real>(ctx, g, N, flags, seed, nnew, all, next, false, flatness, m, h_edges, R);
+        rc = suave_pass<Real>(ctx, g, N, flags, seed, nnew, all, next, false, false, flatness, m, R);
         if (rc) return rc;
         done += (long long)nr * nnew;
     }
@@ -2362,6 +2512,73 @@ int suave_run(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, do
                 boxes[((size_t)k * ndim + d) * 2] = h_edges[ge * k + (size_t)d * (N + 1)];
                 boxes[((size_t)k * ndim + d) * 2 + 1] = h_edges[ge * k + (size_t)d * (N + 1) + N];
             }
+    return CV_OK;
+}
+
+// The batched form's descriptors (one batch item per region, states, tile
+// queue and staging), when the pass can take it: FP32, Sobol or scrambled
+// points, a region's pass within the tiles' int range and a grid that fits
+// the batched kernel's shared memory.  Otherwise m stays per-region.
+int suave_batched_setup(cv_ctx *ctx, const cv_genz *g, int N, int flags, uint64_t seed, long long nnew,
+                        int max_regions, SuaveMem &m, void **bmem, void **hstage)
+{
+    const int ndim = g->ndim;
+    if ((flags & (CV_FP64 | CV_PSEUDO)) || nnew > (1LL << 31)) return CV_OK;
+    const bool pow2 = make_map(N, ndim, false).pow2 != 0;  // (powers of two from 32 bins)
+    int occ = 0;
+    if (dispatch_batch_occupancy(ndim, pow2, N, &occ) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return CV_OK;
+    }
+    const int tile_cap = std::max(1 << 16, 4 * max_regions);
+    const size_t sz_items = align16((size_t)max_regions * sizeof(BatchItem));
+    const size_t sz_state = align16((size_t)max_regions * sizeof(DevState));
+    const size_t sz_stage = align16((size_t)max_regions * sizeof(SuaveEntry)) + (size_t)tile_cap * sizeof(Tile) +
+                            (size_t)max_regions * ndim * sizeof(int2) + 64;
+    char *d = nullptr;
+    if (cudaMalloc((void **)&d, sz_items + sz_state + sz_stage + 16) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_msg(ctx, CV_ENOMEM, "device allocation of the batched regions failed");
+    }
+    *bmem = d;
+    if (cudaMallocHost(hstage, sz_stage) != cudaSuccess) {
+        cudaGetLastError();
+        *hstage = nullptr;
+        return fail_msg(ctx, CV_ENOMEM, "pinned staging allocation failed");
+    }
+    // (the mirrors are one mapped pinned allocation starting at h_edges)
+    CV_CUDA(ctx, cudaHostGetDevicePointer((void **)&m.dh_edges, m.h_edges, 0));
+    m.dh_S = m.dh_edges + (m.h_S - m.h_edges);
+    m.dh_fluct = m.dh_edges + (m.h_fluct - m.h_edges);
+    m.d_items = reinterpret_cast<BatchItem *>(d);
+    DevState *st = reinterpret_cast<DevState *>(d + sz_items);
+    m.d_stage = d + sz_items + sz_state;
+    m.d_counter = reinterpret_cast<int *>(m.d_stage + sz_stage);
+    m.h_stage = static_cast<char *>(*hstage);
+    m.tile_cap = tile_cap;
+    m.grid = ctx->sms * occ;
+    m.pow2 = pow2;
+    const size_t ge = (size_t)ndim * (N + 1), gh = (size_t)ndim * N;
+    std::vector<BatchItem> items((size_t)max_regions);
+    BatchItem proto;
+    memset(&proto, 0, sizeof(proto));
+    fill_params<float>(g, &proto.a.g);
+    proto.a.nbins = N;
+    proto.a.chunk_min = 4;
+    proto.a.map = make_map(N, ndim, false);
+    proto.a.map.priv = proto.a.map.pow2;  // every warp has its own histogram
+    set_generator(&proto.a, ndim, flags, seed);
+    for (int k = 0; k < max_regions; ++k) {
+        items[(size_t)k] = proto;
+        items[(size_t)k].st = st + k;
+        items[(size_t)k].edges = m.edges + ge * k;
+        items[(size_t)k].H = m.H + gh * k;
+    }
+    CV_CUDA(ctx, cudaMemsetAsync(st, 0, sz_state, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(m.d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    m.batched = true;
     return CV_OK;
 }
 
@@ -2397,12 +2614,26 @@ extern "C" int cv_suave(cv_ctx *ctx, const cv_genz *g, int nbins, int flags, uin
     m.edges = (double *)mem;
     m.H = m.edges + ge * (size_t)max_regions;
     m.S = m.H + gh * (size_t)max_regions;
-    rc = (flags & CV_FP64)
+    void *hmem = nullptr;
+    if (cudaMallocHost(&hmem, sizeof(double) * (ge + gs + CV_MAX_DIM) * (size_t)max_regions) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(mem);
+        return fail_msg(ctx, CV_ENOMEM, "pinned host allocation for %d regions failed", max_regions);
+    }
+    m.h_edges = (double *)hmem;
+    m.h_S = m.h_edges + ge * (size_t)max_regions;
+    m.h_fluct = m.h_S + gs * (size_t)max_regions;
+    void *bmem = nullptr, *hstage = nullptr;
+    rc = suave_batched_setup(ctx, g, nbins, flags, seed, nnew, max_regions, m, &bmem, &hstage);
+    if (rc == CV_OK) rc = (flags & CV_FP64)
         ? suave_run<double>(ctx, g, nbins, flags, seed, epsrel, epsabs, mineval, maxeval, nnew, flatness, width,
                             max_regions, m, nregions, neval, fail, integral, error, boxes)
         : suave_run<float>(ctx, g, nbins, flags, seed, epsrel, epsabs, mineval, maxeval, nnew, flatness, width,
                            max_regions, m, nregions, neval, fail, integral, error, boxes);
     cudaStreamSynchronize(ctx->stream);
     cudaFree(mem);
+    cudaFreeHost(hmem);
+    if (bmem) cudaFree(bmem);
+    if (hstage) cudaFreeHost(hstage);
     return rc;
 }

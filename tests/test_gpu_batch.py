@@ -54,6 +54,18 @@ def test_batch_matches_single_runs(ctx):
         assert abs(r.integral[0] - exact) <= 4 * r.error[0] + 2e-6 * abs(exact) + 1e-12
 
 
+def test_batch_small_power_of_two_bins(ctx):
+    # 2..16 bins take the general map (the bit-permuted form starts at 32)
+    specs, probs = _specs(12, 11, nbins_choices=(2, 4, 8, 16, 32))
+    res = ctx.batch_vegas(specs)
+    for sp, r, p in zip(specs, res, probs):
+        single = ctx.vegas(sp.g, flags=0, maxeval=sp.maxeval, nstart=sp.nstart, nbins=sp.nbins)
+        assert (r.neval, r.fail) == (single.neval, single.fail)
+        assert abs(r.integral[0] - single.integral[0]) <= 2e-5 * abs(single.integral[0]) + 1e-2 * single.error[0]
+        exact = p.exact()[0]
+        assert abs(r.integral[0] - exact) <= 4 * r.error[0] + 2e-6 * abs(exact) + 1e-12
+
+
 def test_batch_alone_equals_in_mix(ctx):
     # an integral's tiles and their FP32 sums do not depend on the rest of
     # the batch: only the order of FP64 additions differs

@@ -2,8 +2,9 @@
 
 FP64: the same decisions (regions, evaluations, boxes) and the integral
 within 1e-10 (the region sums differ from the oracle's only in summation
-order; the decisions are taken from FP64 values on both sides).  FP32 and
-the other generators: the closed form within 4 sigma.
+order; the decisions are taken from FP64 values on both sides).  FP32 (the
+batched passes): the FP64 run's decisions, its integral within 1e-5.  FP32
+and the other generators: the closed form within 4 sigma.
 """
 import numpy as np
 import pytest
@@ -65,6 +66,35 @@ def test_fp32_meets_the_closed_form(ctx, flags):
     assert abs(r.integral[0] - exact) < 4 * r.error[0] + 1e-6 * exact
     vol = np.prod(r.boxes[:, :, 1] - r.boxes[:, :, 0], axis=1)
     assert abs(vol.sum() - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("ndim,fam,a,u,width", CASES)
+@pytest.mark.parametrize("nbins", [16, 32])
+def test_fp32_takes_the_fp64_decisions(ctx, ndim, fam, a, u, width, nbins):
+    # FP32 passes (one batched sampling launch over all regions of a pass)
+    # reach the FP64 run's regions and evaluations; boxes and the integral
+    # agree to the FP32 sums' rounding
+    a, u = np.array([a]), np.array([u])
+    kw = dict(nbins=nbins, epsrel=2e-4, maxeval=400000, nnew=4000, width=width, max_regions=512)
+    g = cg.genz(ndim, [fam], a, u)
+    r64 = ctx.suave(g, flags=cg.FP64, **kw)
+    r32 = ctx.suave(g, flags=0, **kw)
+    assert (r32.nregions, r32.neval, r32.fail) == (r64.nregions, r64.neval, r64.fail)
+    np.testing.assert_allclose(r32.boxes, r64.boxes, rtol=0, atol=1e-5)
+    np.testing.assert_allclose(r32.integral, r64.integral, rtol=1e-5)
+    np.testing.assert_allclose(r32.error, r64.error, rtol=1e-3)
+
+
+@pytest.mark.parametrize("flags", [cg.SCRAMBLE, cg.PSEUDO])
+def test_fp32_generators_meet_the_closed_form(ctx, flags):
+    # scrambled points take the batched passes, pseudo-random points one
+    # launch per region
+    a, u = np.array([[6.0, 4.0, 5.0, 3.0, 5.5]]), np.array([[0.3, 0.6, 0.5, 0.4, 0.55]])
+    r = ctx.suave(cg.genz(5, [O.GAUSSIAN], a, u), nbins=32, flags=flags, seed=3, epsrel=1e-4,
+                  maxeval=4000000, nnew=1 << 15, width=32, max_regions=2048)
+    exact = O.genz_exact(O.GAUSSIAN, a[0], u[0])
+    assert r.nregions > 32
+    assert abs(r.integral[0] - exact) < 4 * r.error[0] + 1e-6 * exact
 
 
 def test_bad_arguments(ctx):
