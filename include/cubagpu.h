@@ -178,6 +178,28 @@ int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins,
               const double *edges_dev, uint64_t start, int64_t n, int flags,
               uint64_t seed, double *S1_dev, double *S2_dev, double *hist_dev);
 
+/* The FP32 pass as an integral's iterations run it: its refinement stages
+ * the grid once into a table the sampling kernel copies as it is, instead
+ * of every CTA converting the FP64 edges (FP64 arithmetic is slow on this
+ * GPU).  cv_stage_grid writes that table for edges_dev:
+ *   table_dev[d*nbins + s] = {e_k - w_k, w_k (times nbins when nbins is a
+ *   power of two >= 32 and flags has no CV_PSEUDO)}, float2 (8 bytes),
+ *   w_k = e_(k+1) - e_k computed in FP64 and each entry rounded once to
+ *   FP32, s = the kernel's slot of bin k (a bit permutation of k for those
+ *   power-of-two bin counts, k otherwise);
+ * table_dev holds ndim*nbins float2, 8-byte aligned, caller-owned; flags
+ * are the sampling flags the table is for (the generator decides the
+ * layout).  cv_sample_staged is cv_sample (FP32 only: CV_FP64 is refused)
+ * reading such a table in place of the edges: the same sums as cv_sample
+ * over the edges the table came from, up to the order of FP64 additions.
+ * Both enqueue on the context's stream and return CV_OK, CV_EINVAL (bad
+ * sizes, null buffers, CV_FP64) or CV_ECUDA. */
+int cv_stage_grid(cv_ctx *ctx, int ndim, int nbins, int flags, const double *edges_dev,
+                  void *table_dev);
+int cv_sample_staged(cv_ctx *ctx, const cv_genz *g, int nbins, const void *table_dev,
+                     uint64_t start, int64_t n, int flags, uint64_t seed, double *S1_dev,
+                     double *S2_dev, double *hist_dev);
+
 /* Grid refinement (Lepage 1978) in FP64, in place, per axis: smooth the
  * histogram, compress with exponent 1.5, and rebin so that every new bin
  * holds an equal share.  An axis whose histogram is all zero or not finite
@@ -257,6 +279,16 @@ int cv_jit_info(int *available, int *compiled);
  * NVRTC is missing or rejects the source; then `log` (log_len bytes,
  * may be null) receives the reason. */
 int cv_jit_check(const cv_genz *g, int nbins, int flags, char *log, int log_len);
+
+/* The FP32 pipe's measured rate on this device, the denominator beside
+ * the nominal one (SMs x 128 lanes x 2 flops x clock) for the fused
+ * sampling kernel, which is bound by FP32 arithmetic and instruction issue:
+ * one ~20 ms launch, four 256-thread blocks per SM, every thread 8
+ * independent FMA chains (2 flops per FMA), timed with CUDA events on the
+ * context's stream after a shorter warm-up launch.  *tflops receives
+ * TFLOP/s, *ms (may be null) the timed launch's milliseconds.  Returns
+ * CV_OK, CV_EINVAL for null ctx/tflops, or CV_ECUDA. */
+int cv_fp32_fma_rate(cv_ctx *ctx, double *tflops, double *ms);
 
 /* Bytes cv_vegas moves between host and device per call for an integral of
  * this shape: kernel parameters in (h2d), the final state out (d2h). */

@@ -174,10 +174,13 @@ _SIGNATURES = {
     "cv_suave": (_i, [_vp, _P(Genz), _i, _i, _u64, ctypes.c_double, ctypes.c_double, _i64, _i64, _i64,
                       ctypes.c_double, _i, _i, _P(_i), _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_sample": (_i, [_vp, _P(Genz), _i, _vp, _u64, _i64, _i, _u64, _vp, _vp, _vp]),
+    "cv_stage_grid": (_i, [_vp, _i, _i, _i, _vp, _vp]),
+    "cv_sample_staged": (_i, [_vp, _P(Genz), _i, _vp, _u64, _i64, _i, _u64, _vp, _vp, _vp]),
     "cv_refine": (_i, [_vp, _i, _i, _vp, _vp]),
     "cv_vegas": (_i, [_vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64, _i64,
                       _i, _P(_i64), _P(_i), _vp, _vp, _vp]),
     "cv_vegas_io_bytes": (_i, [_i, _i, _P(_i64), _P(_i64)]),
+    "cv_fp32_fma_rate": (_i, [_vp, _P(_d), _P(_d)]),
     "cv_jit_info": (_i, [_P(_i), _P(_i)]),
     "cv_jit_check": (_i, [_vp, _i, _i, ctypes.c_char_p, _i]),
     "cv_vegas_noalloc": (_i, [_i, _vp, _i, _i, _P(Genz), _d, _d, _i, _i, _i64, _i64, _i64, _i64,
@@ -312,6 +315,18 @@ class Context:
         self._check(self._lib.cv_sample(self._h, ctypes.byref(g), nbins, _ptr(edges), start, n,
                                         flags, seed, _ptr(S1), _ptr(S2), _ptr(H)), "cv_sample")
 
+    def stage_grid(self, ndim: int, nbins: int, flags: int, edges, table):
+        """cv_stage_grid: the FP32 sampling table of a grid (table: ndim*nbins float2, e.g.
+        a float32 tensor of shape [ndim, nbins, 2])."""
+        self._check(self._lib.cv_stage_grid(self._h, ndim, nbins, flags, _ptr(edges), _ptr(table)),
+                    "cv_stage_grid")
+
+    def sample_staged(self, g: Genz, nbins: int, table, start: int, n: int, flags: int, S1, S2, H,
+                      seed: int = 0):
+        """cv_sample_staged: sample over a grid table from stage_grid."""
+        self._check(self._lib.cv_sample_staged(self._h, ctypes.byref(g), nbins, _ptr(table), start, n,
+                                               flags, seed, _ptr(S1), _ptr(S2), _ptr(H)), "cv_sample_staged")
+
     def suave(self, g: Genz, nbins=16, flags=0, seed=0, epsrel=0.0, epsabs=0.0, mineval=0,
               maxeval=10 ** 5, nnew=1000, flatness=2.0, width=1, max_regions=4096) -> "SuaveResult":
         """cv_suave: subregion-adaptive Vegas (see cubagpu.h for the reading)."""
@@ -324,6 +339,12 @@ class Context:
                                        ctypes.byref(neval), ctypes.byref(fail), integral.ctypes.data,
                                        error.ctypes.data, boxes.ctypes.data), "cv_suave")
         return SuaveResult(nreg.value, neval.value, fail.value, integral, error, boxes[: nreg.value])
+
+    def fp32_fma_rate(self):
+        """cv_fp32_fma_rate: measured FP32 FMA rate (TFLOP/s, launch ms)."""
+        t, ms = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.cv_fp32_fma_rate(self._h, ctypes.byref(t), ctypes.byref(ms)), "cv_fp32_fma_rate")
+        return t.value, ms.value
 
     def refine(self, ndim: int, nbins: int, H, edges):
         self._check(self._lib.cv_refine(self._h, ndim, nbins, _ptr(H), _ptr(edges)), "cv_refine")

@@ -305,7 +305,8 @@ static int sample_grid(cv_ctx *ctx, int occ, long long n)
 template <typename Real>
 static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *edges,
                        unsigned long long start, long long n, long long n_grid,
-                       double *S1, double *S2, double *H, DevState *st, int flags, uint64_t seed)
+                       double *S1, double *S2, double *H, DevState *st, int flags, uint64_t seed,
+                       const float2 *ew32 = nullptr)
 {
     SampleArgs<Real> a;
     memset(&a, 0, sizeof(a));
@@ -316,6 +317,7 @@ static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *e
     set_generator(&a, g->ndim, flags, seed);
     const bool jit = (flags & CV_JIT) != 0;
     a.edges = edges;
+    if constexpr (sizeof(Real) == 4) a.ew32 = ew32;
     a.S1 = S1;
     a.S2 = S2;
     a.H = H;
@@ -434,6 +436,54 @@ extern "C" int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins, const double 
                               flags, seed);
 }
 
+// The sampling map an FP32 pass takes for nbins bins and these flags (the
+// pseudo-random generator takes the general map).
+static MapParams sampling_map(int nbins, int ndim, int flags)
+{
+    SampleArgs<float> a;
+    memset(&a, 0, sizeof(a));
+    a.map = make_map(nbins, ndim, false);
+    set_generator(&a, ndim, flags, 0);
+    return a.map;
+}
+
+extern "C" int cv_stage_grid(cv_ctx *ctx, int ndim, int nbins, int flags, const double *edges_dev,
+                             void *table_dev)
+{
+    if (!ctx) return CV_EINVAL;
+    if (ndim < 1 || ndim > CV_MAX_DIM) return fail_msg(ctx, CV_EINVAL, "ndim %d outside 1..%d", ndim, CV_MAX_DIM);
+    if (nbins < CV_MIN_BINS || nbins > CV_MAX_BINS) return fail_msg(ctx, CV_EINVAL, "nbins out of range");
+    if (!edges_dev || !table_dev || ((uintptr_t)table_dev & 7u)) return fail_msg(ctx, CV_EINVAL, "null or unaligned buffer");
+    if (flags & CV_FP64) return fail_msg(ctx, CV_EINVAL, "the staged grid is the FP32 path's");
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaError_t e = launch_stage_grid(ndim, nbins, edges_dev, static_cast<float2 *>(table_dev),
+                                      sampling_map(nbins, ndim, flags), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "grid staging kernel launch");
+    return CV_OK;
+}
+
+extern "C" int cv_sample_staged(cv_ctx *ctx, const cv_genz *g, int nbins, const void *table_dev,
+                                uint64_t start, int64_t n, int flags, uint64_t seed, double *S1_dev,
+                                double *S2_dev, double *hist_dev)
+{
+    if (!ctx) return CV_EINVAL;
+    int rc = check_genz(ctx, g);
+    if (rc) return rc;
+    if (nbins < CV_MIN_BINS || nbins > CV_MAX_BINS)
+        return fail_msg(ctx, CV_EINVAL, "nbins %d outside %d..%d", nbins, CV_MIN_BINS, CV_MAX_BINS);
+    if (n < 0 || start > CV_INDEX_LIMIT || (uint64_t)n > CV_INDEX_LIMIT - start)
+        return fail_msg(ctx, CV_EINVAL, "index range beyond 2^52");
+    if (flags & CV_FP64) return fail_msg(ctx, CV_EINVAL, "the staged grid is the FP32 path's");
+    if ((flags & CV_SCRAMBLE) && (flags & CV_PSEUDO))
+        return fail_msg(ctx, CV_EINVAL, "CV_SCRAMBLE and CV_PSEUDO exclude each other");
+    if (n == 0) return CV_OK;
+    if (!table_dev || ((uintptr_t)table_dev & 7u) || !S1_dev || !S2_dev || !hist_dev)
+        return fail_msg(ctx, CV_EINVAL, "null or unaligned buffer");
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    return launch_pass<float>(ctx, g, nbins, nullptr, start, n, n, S1_dev, S2_dev, hist_dev, nullptr, flags, seed,
+                              static_cast<const float2 *>(table_dev));
+}
+
 extern "C" int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_dev, double *edges_dev)
 {
     if (!ctx) return CV_EINVAL;
@@ -456,6 +506,8 @@ struct cv_integral {
     void *mem = nullptr;
     DevState *st = nullptr;
     double *edges = nullptr, *H = nullptr, *log_I = nullptr, *log_var = nullptr;
+    float2 *ew32 = nullptr;    // FP32 runs: the grid staged for the sampling kernel
+    MapParams map;             // its slot order
     int jmax = 0;              // iterations the sample budget allows
     long long nmax = 0;        // largest iteration
     int K = 0;                 // iterations per graph replay
@@ -505,7 +557,7 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
         ? launch_pass<double>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st,
                               sp.flags, sp.seed)
         : launch_pass<float>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st,
-                             sp.flags, sp.seed);
+                             sp.flags, sp.seed, I->ew32);
     ctx->stream = keep;
     if (rc) return rc;
     CombineArgs ca;
@@ -519,7 +571,7 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
     ca.nincrease = sp.nincrease;
     ca.log_I = I->log_I;
     ca.log_var = I->log_var;
-    cudaError_t e = launch_refine_combine(sp.g.ndim, sp.nbins, I->H, I->edges, ca, s);
+    cudaError_t e = launch_refine_combine(sp.g.ndim, sp.nbins, I->H, I->edges, ca, I->ew32, I->map, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "refine/combine kernel launch");
     return CV_OK;
 }
@@ -583,7 +635,9 @@ extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral 
     const size_t sz_edges = (((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255;
     const size_t sz_H = (((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255;
     const size_t sz_log = (size_t)kLogCap * CV_MAX_COMP * sizeof(double);
-    if (cudaMalloc(&I->mem, sz_state + sz_edges + sz_H + 2 * sz_log) != cudaSuccess) {
+    const bool fp32 = !(spec->flags & CV_FP64);
+    const size_t sz_ew = fp32 ? (size_t)ndim * N * sizeof(float2) : 0;
+    if (cudaMalloc(&I->mem, sz_state + sz_edges + sz_H + 2 * sz_log + sz_ew) != cudaSuccess) {
         cudaGetLastError();
         delete I;
         return fail_msg(ctx, CV_ENOMEM, "device allocation of the Vegas state failed");
@@ -594,6 +648,11 @@ extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral 
     I->H = (double *)(p + sz_state + sz_edges);
     I->log_I = (double *)(p + sz_state + sz_edges + sz_H);
     I->log_var = (double *)(p + sz_state + sz_edges + sz_H + sz_log);
+    if (fp32) I->ew32 = (float2 *)(p + sz_state + sz_edges + sz_H + 2 * sz_log);
+    {
+        // the map the sampling kernel takes (the point generator can change it)
+        I->map = sampling_map(N, ndim, spec->flags);
+    }
     I->launched_kernels = 1 + 2 * I->jmax;
     ctx->integrals.insert(I);
     *out = I;
@@ -623,7 +682,7 @@ extern "C" int cv_integral_reset(cv_integral *I)
     cv_ctx *ctx = I->ctx;
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
     cudaError_t e = launch_reset(I->st, I->edges, I->H, I->spec.g.ndim, I->spec.nbins,
-                                 I->spec.nstart, ctx->stream);
+                                 I->spec.nstart, I->ew32, I->map, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reset kernel launch");
     return CV_OK;
 }
@@ -838,6 +897,7 @@ extern "C" int cv_integral_load(cv_integral *I, const char *path)
     CV_CUDA(ctx, cudaMemcpyAsync(I->H, H.data(), H.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CV_CUDA(ctx, cudaMemcpyAsync(I->log_I, lI.data(), lI.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CV_CUDA(ctx, cudaMemcpyAsync(I->log_var, lV.data(), lV.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (I->ew32) CV_CUDA(ctx, launch_stage_grid(ndim, N, I->edges, I->ew32, I->map, ctx->stream));
     CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return CV_OK;
 }
@@ -855,6 +915,7 @@ extern "C" int cv_integral_set_grid(cv_integral *I, const double *edges)
     }
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
     CV_CUDA(ctx, cudaMemcpyAsync(I->edges, edges, (size_t)ndim * (N + 1) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (I->ew32) CV_CUDA(ctx, launch_stage_grid(ndim, N, I->edges, I->ew32, I->map, ctx->stream));
     CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return CV_OK;
 }
@@ -912,6 +973,65 @@ extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, doub
         error[c] = res.error[c];
         prob[c] = res.prob[c];
     }
+    return CV_OK;
+}
+
+// ------------------------------------------------------------ FP32 peak
+// The FP32 pipe's measured rate: every thread runs 8 independent chains
+// x <- x b + c (b and c are launch arguments, so nothing folds), 16 steps
+// per loop trip; an FMA counts 2 flops.  Four 256-thread blocks per SM keep
+// 8 warps per scheduler, far more independent FMAs than the pipe's latency.
+namespace {
+constexpr int kFmaChains = 8, kFmaUnroll = 16;
+
+__global__ void __launch_bounds__(256) k_fma_chains(float b, float c, int trips, float *sink)
+{
+    float x[kFmaChains];
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) x[j] = 1e-3f * (float)threadIdx.x + (float)j;
+    for (int t = 0; t < trips; ++t) {
+#pragma unroll
+        for (int u = 0; u < kFmaUnroll; ++u) {
+#pragma unroll
+            for (int j = 0; j < kFmaChains; ++j) x[j] = __fmaf_rn(x[j], b, c);
+        }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) s += x[j];
+    if (s == -1.0f) *sink = s;  // (never true: keeps the chains live)
+}
+}  // namespace
+
+extern "C" int cv_fp32_fma_rate(cv_ctx *ctx, double *tflops, double *ms)
+{
+    if (!ctx || !tflops) return CV_EINVAL;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    float *sink = nullptr;
+    CV_CUDA(ctx, cudaMalloc(&sink, sizeof(float)));
+    const int grid = 4 * ctx->sms, trips = 40000;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        k_fma_chains<<<grid, 256, 0, ctx->stream>>>(0.999f, 1e-3f, trips / 10, sink);  // warm-up
+        e = cudaEventRecord(e0, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        k_fma_chains<<<grid, 256, 0, ctx->stream>>>(0.999f, 1e-3f, trips, sink);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "FP32 FMA rate kernel");
+    const double flops = 2.0 * kFmaChains * kFmaUnroll * (double)trips * grid * 256.0;
+    *tflops = flops / (t * 1e-3) / 1e12;
+    if (ms) *ms = t;
     return CV_OK;
 }
 
@@ -2070,7 +2190,7 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     if (rc) return rc;
     pin[0] = 1;
     int aborted = 0;
-    cudaError_t e = launch_reset(st, edges, H, ndim, N, sp.nstart, s);
+    cudaError_t e = launch_reset(st, edges, H, ndim, N, sp.nstart, nullptr, a.map, s);
     unsigned long long start = 1;
     for (int j = 0; j < jmax && e == cudaSuccess && !aborted; ++j) {
         const long long nj = sp.nstart + (long long)j * sp.nincrease;
@@ -2092,7 +2212,7 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
         }
         if (aborted || e != cudaSuccess) break;
         e = cudaMemcpyAsync(&st->pass_active, &pin[0], sizeof(int), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = launch_refine_combine(ndim, N, H, edges, ca, s);
+        if (e == cudaSuccess) e = launch_refine_combine(ndim, N, H, edges, ca, nullptr, a.map, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&pin[1], &st->stopped, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         start += (unsigned long long)nj;

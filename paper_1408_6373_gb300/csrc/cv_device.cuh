@@ -142,22 +142,6 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 
 // slot of bin k (staging and flush run once per block; the sampling loop
 // takes the slot straight from the permuted Sobol word)
-__device__ __forceinline__ int slot_of_bin(int k, const MapParams &m)
-{
-    if (m.pow2) {
-        const int L = m.L;
-        return ((k & ((1 << (L - 5)) - 1)) << 5) | (((k >> (L - 5)) & 1) << 4) | (k >> (L - 4));
-    }
-    return k;
-}
-__device__ __forceinline__ int bin_of_slot(int p, const MapParams &m)
-{
-    if (m.pow2) {
-        const int L = m.L;
-        return ((p & 15) << (L - 4)) | (((p >> 4) & 1) << (L - 5)) | (p >> 5);
-    }
-    return p;
-}
 
 // ------------------------------------------------------------ integrands
 template <int E>
@@ -674,14 +658,25 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
             // [kWarpsPerBlock][NDIM][N]: every warp's own copy
             for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * N; i += blockDim.x) sm.h[i] = 0.0f;
         }
-        // (by bin: coalesced reads of the FP64 grid)
-        for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-            const int d = idx / N, k = idx - d * N;
-            const double *e = A.edges + (size_t)d * (N + 1);
-            const int p = d * kStride + slot_of_bin(k, A.map);
-            const double w = e[k + 1] - e[k];
-            sm.ew[p] = make_float2(__double2float_rn(e[k] - w), __double2float_rn(POW2 ? (double)N * w : w));
-            if (!priv) sm.h[p] = 0.0f;
+        if (A.ew32) {
+            // the table the refinement staged (FP64 arithmetic is slow here:
+            // done once per pass there instead of once per CTA)
+            for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+                const int d = idx / N, sl = idx - d * N;
+                const int p = d * kStride + sl;
+                sm.ew[p] = A.ew32[idx];
+                if (!priv) sm.h[p] = 0.0f;
+            }
+        } else {
+            // (by bin: coalesced reads of the FP64 grid)
+            for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+                const int d = idx / N, k = idx - d * N;
+                const double *e = A.edges + (size_t)d * (N + 1);
+                const int p = d * kStride + slot_of_bin(k, A.map);
+                const double w = e[k + 1] - e[k];
+                sm.ew[p] = make_float2(__double2float_rn(e[k] - w), __double2float_rn(POW2 ? (double)N * w : w));
+                if (!priv) sm.h[p] = 0.0f;
+            }
         }
     } else {
         sm.ew = reinterpret_cast<double2 *>(smem_raw);

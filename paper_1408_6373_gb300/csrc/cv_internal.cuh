@@ -124,6 +124,27 @@ struct MapParams {
     int priv;                       // per-warp f^2 histograms updated without atomics
 };
 
+// Grid slot of bin k of an axis (and back).  Power-of-two N >= 32: the bit
+// permutation of the direction words puts bin bits (y_6..y_L) above y_5 above
+// (y_1..y_4), so the 32 points of an aligned block occupy 32 distinct slots
+// modulo 32 (distinct shared-memory banks); other N: the identity.
+__host__ __device__ __forceinline__ int slot_of_bin(int k, const MapParams &m)
+{
+    if (m.pow2) {
+        const int L = m.L;
+        return ((k & ((1 << (L - 5)) - 1)) << 5) | (((k >> (L - 5)) & 1) << 4) | (k >> (L - 4));
+    }
+    return k;
+}
+__host__ __device__ __forceinline__ int bin_of_slot(int p, const MapParams &m)
+{
+    if (m.pow2) {
+        const int L = m.L;
+        return ((p & 15) << (L - 4)) | (((p >> 4) & 1) << (L - 5)) | (p >> 5);
+    }
+    return p;
+}
+
 // Arguments of one sampling launch.  When `st` is non-null the launch reads
 // its index range from the device state (and returns at once if the run has
 // stopped), which is what lets a captured graph replay iterations whose
@@ -135,6 +156,11 @@ struct SampleArgs {
     int chunk_min;                  // minimum warp-steps per chunk
     MapParams map;
     const double *edges;            // [ndim][nbins+1]
+    // FP32 path: the grid already staged for the kernel, {e_k - w_k, w_k}
+    // (w_k scaled by N for power-of-two N) in slot order, [ndim][nbins],
+    // written by the refinement that produced `edges`; null: the kernel
+    // converts `edges` itself (the same FP64 operations, so the same values)
+    const float2 *ew32;
     double *S1;                     // [ncomp]
     double *S2;                     // [ncomp]
     double *H;                      // [ndim][nbins]
@@ -221,10 +247,15 @@ cudaError_t launch_genz_points(const GenzParams<Real> &g, const Real *x, Real *f
 
 // cv_refine.cu
 cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, cudaStream_t s);
+// (ew32, map: when ew32 is non-null the kernels also write the FP32 grid
+// table of SampleArgs::ew32 for the grid they leave, in map's slot order)
 cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
-                                  const CombineArgs &a, cudaStream_t s);
+                                  const CombineArgs &a, float2 *ew32, const MapParams &map,
+                                  cudaStream_t s);
 cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int nbins,
-                         long long nstart, cudaStream_t s);
+                         long long nstart, float2 *ew32, const MapParams &map, cudaStream_t s);
+cudaError_t launch_stage_grid(int ndim, int nbins, const double *edges, float2 *ew32,
+                              const MapParams &map, cudaStream_t s);
 // (list: optional indices of the integrals to act on, else 0..count-1)
 cudaError_t launch_batch_reset(const BatchItem *items, const CombineArgs *cargs, int count,
                                cudaStream_t s, const int *list = nullptr);

@@ -143,12 +143,12 @@ cudaError_t run(const cv_genz *g, int nbins, int flags, unsigned long long seed,
     long long grid = (nblk + (long long)cv::kWarpsPerBlock * 16 - 1) / ((long long)cv::kWarpsPerBlock * 16);
     if (grid > (long long)sms * (occ > 0 ? occ : 1)) grid = (long long)sms * (occ > 0 ? occ : 1);
     if (grid < 1) grid = 1;
-    e = cv::launch_reset(st, edges, H, g->ndim, nbins, ca.nstart, s);
+    e = cv::launch_reset(st, edges, H, g->ndim, nbins, ca.nstart, nullptr, a.map, s);
     if (e != cudaSuccess) return e;
     for (int j = 0; j < jmax; ++j) {
         e = launch_of<Real>(g->ndim, a, (int)grid, s);
         if (e != cudaSuccess) return e;
-        e = cv::launch_refine_combine(g->ndim, nbins, H, edges, ca, s);
+        e = cv::launch_refine_combine(g->ndim, nbins, H, edges, ca, nullptr, a.map, s);
         if (e != cudaSuccess) return e;
         if (poll && (j & 31) == 31 && j + 1 < jmax) {
             int stopped = 0;

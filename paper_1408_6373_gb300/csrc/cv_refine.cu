@@ -54,6 +54,22 @@ __device__ double gamma_p(double a, double x)
     return 1.0 - Q;
 }
 
+// The FP32 sampling kernel's table of bins [k0, N) of axis d (step dk),
+// from the FP64 edges: {e_k - w_k, w_k} with w_k = e_(k+1) - e_k, w_k scaled
+// by N for the bit-level map, each rounded once to FP32, at the bin's slot.
+// The same FP64 operations the sampling kernel applies when it converts the
+// grid itself, so either way it samples with the same values.
+__device__ __forceinline__ void stage_axis(int d, int N, const double *edges, float2 *ew32, const MapParams &map,
+                                           int k0, int dk)
+{
+    const double *e = edges + (size_t)d * (N + 1);
+    for (int k = k0; k < N; k += dk) {
+        const double w = e[k + 1] - e[k];
+        ew32[(size_t)d * N + slot_of_bin(k, map)] =
+            make_float2(__double2float_rn(e[k] - w), __double2float_rn(map.pow2 ? (double)N * w : w));
+    }
+}
+
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
@@ -80,7 +96,8 @@ __device__ __forceinline__ long long warp_max_bits(long long v)
 // 1.5 ulp of the quotient).  FP64 results take ~200 cycles here, so the
 // refinement is bound by its chain of dependent FP64 operations: maxima
 // and searches over non-negative doubles compare bit patterns instead.
-__device__ void refine_axis(int d, int N, double *H, double *edges, int zero_hist)
+__device__ void refine_axis(int d, int N, double *H, double *edges, int zero_hist, float2 *ew32 = nullptr,
+                            const MapParams *map = nullptr)
 {
     double *Hd = H + (size_t)d * N;
     double *e = edges + (size_t)d * (N + 1);
@@ -183,6 +200,10 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
         }
     }
     if (zero_hist && k < N) Hd[k] = 0.0;
+    if (ew32) {
+        __syncthreads();  // (the new edges of this axis, written by every thread)
+        stage_axis(d, N, edges, ew32, *map, k, blockDim.x);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_refine(int N, double *H, double *edges)
@@ -288,16 +309,17 @@ __device__ void combine_iteration(const CombineArgs &A)
 // axis each from the histogram (and clear it), block ndim combines the
 // iteration.  Runs only if the sampling launch before it ran.
 __global__ void __launch_bounds__(256)
-k_refine_combine(int ndim, int N, double *H, double *edges, const CombineArgs A)
+k_refine_combine(int ndim, int N, double *H, double *edges, const CombineArgs A, float2 *ew32, MapParams map)
 {
     if (!*(volatile const int *)&A.st->pass_active) return;
-    if ((int)blockIdx.x < ndim) refine_axis(blockIdx.x, N, H, edges, 1);
+    if ((int)blockIdx.x < ndim) refine_axis(blockIdx.x, N, H, edges, 1, ew32, &map);
     else combine_iteration(A);
 }
 
 // Start of a run: uniform grid e_k = k/N, empty histogram and sums, Sobol
 // index 1 (index 0, the all-zero point, is skipped).
-__global__ void k_reset(DevState *st, double *edges, double *H, int ndim, int N, long long nstart)
+__global__ void k_reset(DevState *st, double *edges, double *H, int ndim, int N, long long nstart, float2 *ew32,
+                        MapParams map)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
@@ -313,6 +335,13 @@ __global__ void k_reset(DevState *st, double *edges, double *H, int ndim, int N,
         st->next_index = 1ull;
         st->n_cur = nstart;
     }
+    if (ew32)  // (one block: the edges above are this block's own writes)
+        for (int d = 0; d < ndim; ++d) stage_axis(d, N, edges, ew32, map, tid, stride);
+}
+
+__global__ void k_stage_grid(int ndim, int N, const double *edges, float2 *ew32, MapParams map)
+{
+    stage_axis(blockIdx.x, N, edges, ew32, map, threadIdx.x, blockDim.x);
 }
 
 // ---- batched forms: one CTA per integral (reset, combine) or per
@@ -391,9 +420,16 @@ cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream
 }
 
 cudaError_t launch_reset(DevState *st, double *edges, double *H, int ndim, int nbins,
-                         long long nstart, cudaStream_t s)
+                         long long nstart, float2 *ew32, const MapParams &map, cudaStream_t s)
 {
-    k_reset<<<1, 256, 0, s>>>(st, edges, H, ndim, nbins, nstart);
+    k_reset<<<1, 256, 0, s>>>(st, edges, H, ndim, nbins, nstart, ew32, map);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_grid(int ndim, int nbins, const double *edges, float2 *ew32,
+                              const MapParams &map, cudaStream_t s)
+{
+    k_stage_grid<<<ndim, 256, 0, s>>>(ndim, nbins, edges, ew32, map);
     return cudaGetLastError();
 }
 
@@ -408,9 +444,10 @@ cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, cudaStr
 }
 
 cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
-                                  const CombineArgs &a, cudaStream_t s)
+                                  const CombineArgs &a, float2 *ew32, const MapParams &map,
+                                  cudaStream_t s)
 {
-    k_refine_combine<<<ndim + 1, refine_threads(nbins), 0, s>>>(ndim, nbins, H, edges, a);
+    k_refine_combine<<<ndim + 1, refine_threads(nbins), 0, s>>>(ndim, nbins, H, edges, a, ew32, map);
     return cudaGetLastError();
 }
 

@@ -303,6 +303,65 @@ def test_fp32_iterations_with_grid_handed_to_oracle(ctx):
         start += n
 
 
+@pytest.mark.parametrize("flags", [0, cg.JIT, cg.PSEUDO, cg.SCRAMBLE | cg.JIT])
+@pytest.mark.parametrize("nbins", [128, 50])
+def test_staged_grid_samples_like_the_fp64_grid(ctx, flags, nbins):
+    # an integral's FP32 passes read the grid table its reset, refinement or
+    # set_grid staged; a pass over the same grid that converts the FP64 edges
+    # in the kernel (cv_sample) gives the same sums, up to the order of the
+    # blocks' FP64 additions
+    ndim, n, iters = 8, 200000, 4
+    a, u = _params(ndim, 4, 33)
+    g = cg.genz(ndim, [O.OSCILLATORY, O.PRODUCT_PEAK, O.CORNER_PEAK, O.GAUSSIAN], a, u)
+    I = ctx.integral(cg.spec(g, nbins=nbins, maxeval=(iters + 1) * n, nstart=n, flags=flags))
+    I.reset()
+    start = 1
+    for j in range(iters + 1):
+        if j == iters:  # a grid set from the host
+            I.set_grid(_random_grid(ndim, nbins, 5))
+        edges = I.grid()
+        I.step(1)
+        Ij, Vj = I.log(j + 1)
+        S1, S2, _ = _gpu_sample(ctx, g, edges, start, n, flags)
+        for c in range(4):
+            np.testing.assert_allclose(Ij[j, c], S1[c] / n, rtol=1e-12, atol=1e-15)
+            var = (S2[c] / n - (S1[c] / n) ** 2) / (n - 1)
+            np.testing.assert_allclose(Vj[j, c], var, rtol=1e-9)
+        start += n
+    I.close()
+
+
+@pytest.mark.parametrize("flags", [0, cg.JIT, cg.PSEUDO, cg.SCRAMBLE])
+@pytest.mark.parametrize("nbins", [128, 50, 16])
+def test_sample_staged_equals_sample(ctx, flags, nbins):
+    ndim, n = 6, 300000
+    a, u = _params(ndim, 2, 8)
+    g = cg.genz(ndim, [O.GAUSSIAN, O.OSCILLATORY], a, u)
+    edges = _random_grid(ndim, nbins, 9)
+    e = torch.tensor(edges, dtype=torch.float64, device="cuda")
+    table = torch.empty((ndim, nbins, 2), dtype=torch.float32, device="cuda")
+    ctx.stage_grid(ndim, nbins, flags, e, table)
+    S1 = torch.zeros(2, dtype=torch.float64, device="cuda")
+    S2, H = torch.zeros_like(S1), torch.zeros((ndim, nbins), dtype=torch.float64, device="cuda")
+    ctx.sample_staged(g, nbins, table, 7, n, flags, S1, S2, H, seed=3)
+    ctx.synchronize()
+    rS1, rS2, rH = (t.cpu().numpy() for t in (S1, S2, H))
+    S1, S2, H = (t.zero_() for t in (S1, S2, H))
+    ctx.sample(g, nbins, e, 7, n, flags, S1, S2, H, seed=3)
+    ctx.synchronize()
+    np.testing.assert_allclose(rS1, S1.cpu().numpy(), rtol=1e-13)
+    np.testing.assert_allclose(rS2, S2.cpu().numpy(), rtol=1e-13)
+    # (warp-private FP32 histograms, for 2^L >= 32 bins and Sobol points, are
+    # summed in a fixed order; the block histogram of the other layouts takes
+    # FP32 shared-memory atomics in run-dependent order)
+    private = nbins >= 32 and nbins & (nbins - 1) == 0 and not flags & cg.PSEUDO
+    np.testing.assert_allclose(rH, H.cpu().numpy(), rtol=1e-12 if private else 1e-6, atol=1e-300)
+    with pytest.raises(cg.CubaGpuError):
+        ctx.sample_staged(g, nbins, table, 7, n, cg.FP64, S1, S2, H)
+    with pytest.raises(cg.CubaGpuError):
+        ctx.stage_grid(ndim, nbins, cg.FP64, e, table)
+
+
 @pytest.mark.parametrize("nbins", [2, 16, 32, 64, 96, 256])
 def test_sample_fp32_every_bin_layout(ctx, nbins):
     # power-of-two N >= 32 use the stratum-major shared-memory layout, other
