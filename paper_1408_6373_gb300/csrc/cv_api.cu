@@ -93,6 +93,10 @@ struct cv_ctx {
     // stop check of that mode
     void *mat_mem = nullptr;
     size_t mat_cap = 0;
+    // the state of cv_vegas's one-shot integral, grown on demand and kept
+    // (no allocation, and no free with its device synchronisation, per call)
+    void *vegas_mem = nullptr;
+    size_t vegas_cap = 0;
     int *pinned = nullptr;  // [0] = 1 (pass_active), [1] = stopped read back
 };
 
@@ -200,6 +204,7 @@ extern "C" void cv_destroy(cv_ctx *ctx)
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->mat_mem) cudaFree(ctx->mat_mem);
+    if (ctx->vegas_mem) cudaFree(ctx->vegas_mem);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -513,6 +518,7 @@ struct cv_integral {
     int K = 0;                 // iterations per graph replay
     cudaGraphExec_t exec = nullptr;
     int launched_kernels = 0;  // kernels in one run (reset + iterations)
+    bool oneshot = false;      // cv_vegas's: run once, kernels enqueued directly, state in ctx->vegas_mem
 };
 
 static int check_spec(cv_ctx *ctx, const cv_spec *sp)
@@ -619,7 +625,7 @@ static int capture_graph(cv_integral *I)
     return CV_OK;
 }
 
-extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral **out)
+static int integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral **out, bool oneshot)
 {
     if (!ctx || !out) return CV_EINVAL;
     *out = nullptr;
@@ -629,6 +635,7 @@ extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral 
     cv_integral *I = new cv_integral();
     I->ctx = ctx;
     I->spec = *spec;
+    I->oneshot = oneshot;
     plan(spec->nstart, spec->nincrease, spec->maxeval, &I->jmax, &I->nmax);
     const int ndim = spec->g.ndim, N = spec->nbins;
     const size_t sz_state = (sizeof(DevState) + 255) & ~(size_t)255;
@@ -637,12 +644,30 @@ extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral 
     const size_t sz_log = (size_t)kLogCap * CV_MAX_COMP * sizeof(double);
     const bool fp32 = !(spec->flags & CV_FP64);
     const size_t sz_ew = fp32 ? (size_t)ndim * N * sizeof(float2) : 0;
-    if (cudaMalloc(&I->mem, sz_state + sz_edges + sz_H + 2 * sz_log + sz_ew) != cudaSuccess) {
-        cudaGetLastError();
-        delete I;
-        return fail_msg(ctx, CV_ENOMEM, "device allocation of the Vegas state failed");
+    const size_t bytes = sz_state + sz_edges + sz_H + 2 * sz_log + sz_ew;
+    char *p = nullptr;
+    if (oneshot) {
+        if (bytes > ctx->vegas_cap) {
+            if (ctx->vegas_mem) cudaFree(ctx->vegas_mem);
+            ctx->vegas_mem = nullptr;
+            ctx->vegas_cap = 0;
+            if (cudaMalloc(&ctx->vegas_mem, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                ctx->vegas_mem = nullptr;
+                delete I;
+                return fail_msg(ctx, CV_ENOMEM, "device allocation of the Vegas state failed");
+            }
+            ctx->vegas_cap = bytes;
+        }
+        p = (char *)ctx->vegas_mem;
+    } else {
+        if (cudaMalloc(&I->mem, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete I;
+            return fail_msg(ctx, CV_ENOMEM, "device allocation of the Vegas state failed");
+        }
+        p = (char *)I->mem;
     }
-    char *p = (char *)I->mem;
     I->st = (DevState *)p;
     I->edges = (double *)(p + sz_state);
     I->H = (double *)(p + sz_state + sz_edges);
@@ -659,10 +684,15 @@ extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral 
     return CV_OK;
 }
 
+extern "C" int cv_integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral **out)
+{
+    return integral_create(ctx, spec, out, false);
+}
+
 static void integral_free(cv_integral *I)
 {
     if (I->exec) cudaGraphExecDestroy(I->exec);
-    if (I->mem) cudaFree(I->mem);
+    if (I->mem) cudaFree(I->mem);  // (a one-shot integral's state is the context's)
     delete I;
 }
 
@@ -702,13 +732,32 @@ extern "C" int cv_integral_run(cv_integral *I)
         }
         return CV_OK;
     }
+    const bool fixed = I->spec.epsrel == 0.0 && I->spec.epsabs == 0.0;
+    if (I->oneshot) {
+        // a single run: capturing and instantiating a graph would cost more
+        // than the launches it saves, so the iterations are enqueued directly
+        // (32 at a time, the device's stop decision read in between unless
+        // the iteration count is fixed)
+        for (int done = 0; done < I->jmax && !stopped;) {
+            const int K = I->jmax - done < 32 ? I->jmax - done : 32;
+            for (int j = 0; j < K; ++j) {
+                rc = enqueue_iteration(I, ctx->stream);
+                if (rc) return rc;
+            }
+            done += K;
+            if (!fixed && done < I->jmax) {
+                rc = read_stopped(I, &stopped);
+                if (rc) return rc;
+            }
+        }
+        return CV_OK;
+    }
     if (!I->exec) {
         rc = capture_graph(I);
         if (rc) return rc;
     }
     // Without an accuracy goal the iteration count is fixed and every replay
     // is enqueued at once; otherwise poll the device between replays.
-    const bool fixed = I->spec.epsrel == 0.0 && I->spec.epsabs == 0.0;
     for (int done = 0; done < I->jmax && !stopped; done += I->K) {
         cudaError_t e = cudaGraphLaunch(I->exec, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
@@ -950,7 +999,7 @@ extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, doub
     sp.nbatch = nbatch;
     sp.seed = (uint64_t)(int64_t)seed;
     cv_integral *I = nullptr;
-    int rc = cv_integral_create(ctx, &sp, &I);
+    int rc = integral_create(ctx, &sp, &I, true);
     if (rc) return rc;
     cv_result res;
     rc = cv_integral_reset(I);
