@@ -621,10 +621,12 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
 
 // ------------------------------------------------------------ the kernel
 // Register budget: three resident blocks of 256 threads per SM for up to 8
-// FP32 dimensions (80 registers), two up to 16; wider problems get what
-// they need.
+// FP32 dimensions (80 registers), two for 9..32 (128 registers: the batched
+// kernel spills a little from 24 dimensions on, and is still 30-40% faster
+// than at one block of up to 255 registers, which hides too little
+// latency with 8 warps); FP64 kernels get what they need.
 template <int NDIM, typename Real>
-constexpr int kMinBlocks = sizeof(Real) != 4 ? 1 : (NDIM <= 8 ? 3 : (NDIM <= 16 ? 2 : 1));
+constexpr int kMinBlocks = sizeof(Real) != 4 ? 1 : (NDIM <= 8 ? 3 : 2);
 
 // One fused sampling pass (the kernel body, shared by every specialisation).
 template <int NDIM, typename Real, bool POW2, class I>

@@ -294,9 +294,8 @@ inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64, bool priv) {
 }
 
 // Resident 256-thread blocks per SM the FP32 sampling kernels are compiled
-// for (their __launch_bounds__): three up to 8 dimensions, two up to 16,
-// else one.
-inline int min_blocks_f32(int ndim) { return ndim <= 8 ? 3 : (ndim <= 16 ? 2 : 1); }
+// for (their __launch_bounds__): three up to 8 dimensions, else two.
+inline int min_blocks_f32(int ndim) { return ndim <= 8 ? 3 : 2; }
 
 constexpr size_t kSmemPerSM = 228 * 1024;     // shared memory of one SM
 constexpr size_t kSmemBlockReserve = 2048;    // per block: runtime reserve + static arrays
