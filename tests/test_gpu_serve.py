@@ -96,7 +96,7 @@ def test_arrivals_while_busy_join_later_rounds(ctx):
 def test_budget_admission_and_rejection(ctx):
     rng = np.random.default_rng(9)
     sp = _request(rng)
-    # 20 dimensions x 256 bins need 82,944 bytes of state: a 120 KB budget
+    # 20 dimensions x 256 bins need 82,688 bytes of state: a 120 KB budget
     # holds one such request at a time, and all still complete, one by one
     def big():
         g = cg.genz(20, [cg.GAUSSIAN], 0.5 + rng.random(20), rng.random(20))
