@@ -320,6 +320,12 @@ int cv_vegas_io_bytes(int ndim, int nbins, int64_t *h2d, int64_t *d2h);
  * CV_PSEUDO with seed).  With Sobol or scrambled points the final pass is
  * correlated with the partition, so on discontinuous integrands the error
  * can be underestimated; CV_PSEUDO gives independent points.
+ * Execution: in FP32 with Sobol or scrambled points every pass is one
+ * batched sampling launch over all its regions (CV_JIT has no effect), the
+ * flatness measure computed on the device; FP64 and CV_PSEUDO passes launch
+ * once per region and take every decision value on the host.  Device
+ * memory: ndim ((nbins+1) + nbins) doubles and a few hundred bytes of
+ * descriptors per region of max_regions, allocated per call.
  * boxes (host, may be null): [max_regions][ndim][2], the final regions'
  * (lo, hi).  *nregions, *neval, *fail, integral[ncomp], error[ncomp] are
  * host outputs.  Errors: CV_EINVAL (arguments), CV_ENOMEM, CV_ECUDA. */
