@@ -323,9 +323,11 @@ int cv_vegas_io_bytes(int ndim, int nbins, int64_t *h2d, int64_t *d2h);
  * Execution: in FP32 with Sobol or scrambled points every pass is one
  * batched sampling launch over all its regions (CV_JIT has no effect), the
  * flatness measure computed on the device; FP64 and CV_PSEUDO passes launch
- * once per region and take every decision value on the host.  Device
- * memory: ndim ((nbins+1) + nbins) doubles and a few hundred bytes of
- * descriptors per region of max_regions, allocated per call.
+ * once per region and take every decision value on the host.  Memory,
+ * allocated per call for max_regions regions: per region ndim (2 nbins + 1)
+ * doubles of grid and histogram and ~2 KB of descriptors and state on the
+ * device, its grid and sums in pinned host memory, and a staging area for
+ * up to max(65536, 4 max_regions) tiles.
  * boxes (host, may be null): [max_regions][ndim][2], the final regions'
  * (lo, hi).  *nregions, *neval, *fail, integral[ncomp], error[ncomp] are
  * host outputs.  Errors: CV_EINVAL (arguments), CV_ENOMEM, CV_ECUDA. */
