@@ -222,6 +222,44 @@ def cpu_oracle_rate(p, target_s: float, threads: int):
     return 2 * n / dt, dt, n
 
 
+def oracle_pass_rate(problems, cap: int, threads: int) -> tuple:
+    """The oracle's sampling rate over a list of problems: one pass of
+    min(nstart, cap) points each on the uniform grid (a Vegas iteration's
+    sampling, its refinement left out), FP32-decided like the GPU path."""
+    import numpy as np
+
+    import oracle as O
+    total, dt = 0, 0.0
+    for p in problems:
+        prob = O.Problem(p.ndim, list(p.families), np.asarray(p.a), np.asarray(p.u),
+                         nbins=p.nbins, bits=23, fp32_decide=True)
+        prob.directions()
+        e = O.grid_uniform(p.ndim, p.nbins)
+        n = min(int(p.nstart), cap)
+        t = time.perf_counter()
+        O.sample(prob, e, 1, n, nthreads=threads)
+        dt += time.perf_counter() - t
+        total += n
+    return total / dt, total, dt
+
+
+def oracle_more_rates(p, W, threads: int) -> dict:
+    """Further oracle figures of the CPU-baseline leg: the headline on one
+    thread, and bounded samples of the batched and large workloads."""
+    out = {}
+    rate, dt, n = cpu_oracle_rate(p, 3.0, 1)
+    out["single_thread"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"2 Vegas iterations x {n} points of the headline workload, {dt:.1f} s"}
+    rate, total, dt = oracle_pass_rate(W.batch4096()[:64], 10 ** 6, threads)
+    out["batch4096"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                        "sample": f"the first 64 of the 4096 integrals, one pass of min(n, 1e6) points each "
+                                  f"({total} points, {dt:.1f} s)"}
+    rate, total, dt = oracle_pass_rate(W.large30d(), 10 ** 7, threads)
+    out["large30d"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                       "sample": f"both integrals, one pass of 1e7 points each ({total} points, {dt:.1f} s)"}
+    return out
+
+
 # ------------------------------------------------------------------ arms
 def run_reference(args):
     world, rank, _ = _dist()
@@ -434,6 +472,11 @@ def run_ours(args):
         if not args.no_sweep:
             line["cost_sweep"] = measure_cost_sweep(ctx, cg, W, threads)
         line["suave"]["cpu_baseline"] = suave_cpu_rate(threads)
+        more = oracle_more_rates(p, W, threads)
+        line["cpu_baseline"]["single_thread"] = more["single_thread"]
+        for k in ("batch4096", "large30d"):
+            if k in line:
+                line[k]["cpu_baseline"] = more[k]
     if rank == 0:
         print(json.dumps(line), flush=True)
     integ.close()
