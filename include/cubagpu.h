@@ -98,8 +98,8 @@ extern "C" {
  * process; without NVRTC, or if a compile fails, the generic kernel runs.
  * Results equal those of the generic kernel. */
 #define CV_JIT 0x800
-/* Point generators other than the plain Sobol sequence (SURVEY's NEXT-2),
- * both keyed by a 64-bit seed through the counter-based generator
+/* Point generators other than the plain Sobol sequence (the seed argument
+ * of Sect. 3.2.2), both keyed by a 64-bit seed through the counter-based generator
  * Philox4x64-10 (Salmon et al., SC 2011):
  *   CV_SCRAMBLE  randomized QMC: every coordinate of every Sobol point is
  *                XORed with a random digital shift of its dimension, the
