@@ -63,7 +63,7 @@ class _Problem(ctypes.Structure):
         ("ncomp", ctypes.c_int),
         ("nbins", ctypes.c_int),
         ("bits", ctypes.c_int),
-        ("fp32_decide", ctypes.c_int),
+        ("band_bits", ctypes.c_int),
         ("family", ctypes.c_int * MAX_COMP),
         ("a", (ctypes.c_double * MAX_DIM) * MAX_COMP),
         ("u", (ctypes.c_double * MAX_DIM) * MAX_COMP),
@@ -98,6 +98,8 @@ def _bind(lib):
                 "or_corner_peak_incl_excl": (_d, [_int, _vp]),
                 "or_sample": (_int, [_P(_Problem), _vp, _vp, _u64, _i64, _int,
                                      _vp, _vp, _vp]),
+                "or_sample_bounds": (_int, [_P(_Problem), _vp, _vp, _u64, _i64, _int,
+                                            _vp, _vp, _vp, _vp, _vp, _vp]),
                 "or_refine": (None, [_int, _int, _vp, _vp]),
                 "or_rebin": (None, [_int, _int, _vp, _vp]),
                 "or_chi2_cdf": (_d, [_d, _int]),
@@ -302,7 +304,10 @@ class Problem:
     u: np.ndarray          # [ncomp, ndim]
     nbins: int = 50
     bits: int = 52         # fraction bits of y: 52 (FP64 path) or 23 (FP32 path)
-    fp32_decide: bool = False
+    # significand bits of the evaluation a pass is compared with, for the
+    # discontinuity band of sample_bounds: None = 24 (binary32) when
+    # bits == 23, else 0 (no band: an FP64 evaluation decides as the oracle)
+    band_bits: int = None
     gen: int = 0           # point generator: SOBOL, SCRAMBLED or PSEUDO
     seed: int = 0          # Philox key of the scrambled and pseudo-random generators
     delay: int = 0         # integrand-cost knob (extra multiply-adds per evaluation)
@@ -315,7 +320,8 @@ class Problem:
     def _c(self) -> _Problem:
         p = _Problem()
         p.ndim, p.ncomp, p.nbins, p.bits = self.ndim, self.ncomp, self.nbins, self.bits
-        p.fp32_decide = 1 if self.fp32_decide else 0
+        bb = self.band_bits
+        p.band_bits = int(bb) if bb is not None else (24 if self.bits == 23 else 0)
         p.gen, p.seed, p.delay = int(self.gen), int(self.seed), int(self.delay)
         a = np.asarray(self.a, dtype=np.float64).reshape(self.ncomp, self.ndim)
         u = np.asarray(self.u, dtype=np.float64).reshape(self.ncomp, self.ndim)
@@ -350,6 +356,38 @@ def sample(prob: Problem, edges: np.ndarray, start: int, n: int, nthreads: int =
     if rc != 0:
         raise ValueError(f"or_sample failed ({rc})")
     return S1, S2, H
+
+
+@dataclass
+class PassBounds:
+    """One sampling pass with what bounds a lower-precision evaluation of it:
+    A1[c] = sum |J f_c|; B1[c], B2[c] the boundary mass of the discontinuity
+    band (points a binary32 evaluation may decide either way, see the C
+    source): such an evaluation may differ by up to B1 in S1, B2 in S2 and
+    B2[0] in any histogram bin."""
+    S1: np.ndarray
+    S2: np.ndarray
+    H: np.ndarray
+    A1: np.ndarray
+    B1: np.ndarray
+    B2: np.ndarray
+
+
+def sample_bounds(prob: Problem, edges: np.ndarray, start: int, n: int,
+                  nthreads: int = 1) -> PassBounds:
+    """sample() plus sum |J f| and the boundary mass of the pass."""
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    nc = prob.ncomp
+    out = [np.zeros(nc) for _ in range(5)]
+    H = np.zeros((prob.ndim, prob.nbins))
+    p = prob._c()
+    S1, S2, A1, B1, B2 = out
+    rc = _load().or_sample_bounds(ctypes.byref(p), _ptr(prob.directions()), _ptr(edges),
+                                  start, n, nthreads, _ptr(S1), _ptr(S2), _ptr(H),
+                                  _ptr(A1), _ptr(B1), _ptr(B2))
+    if rc != 0:
+        raise ValueError(f"or_sample_bounds failed ({rc})")
+    return PassBounds(S1, S2, H, A1, B1, B2)
 
 
 def refine(edges: np.ndarray, H: np.ndarray) -> np.ndarray:

@@ -60,7 +60,9 @@ typedef struct {
     int ncomp;
     int nbins;
     int bits;          /* fraction bits b of the y-coordinate */
-    int fp32_decide;   /* discontinuous family: decide x > u in binary32 */
+    int band_bits;     /* significand bits p of the evaluation a pass is
+                        * compared with (24: binary32), 0: none; sets the
+                        * discontinuity band of or_sample_bounds */
     int family[OR_MAX_COMP];
     double a[OR_MAX_COMP][OR_MAX_DIM];
     double u[OR_MAX_COMP][OR_MAX_DIM];
@@ -310,11 +312,9 @@ double or_map(int ndim, int nbins, const double *edges, const uint64_t *Y,
 
 static const double OR_PI = 3.14159265358979323846264338327950288;
 
-/* f for one component; x holds the FP64 point.  For the discontinuous
- * family the branch x_i > u_i may be taken on a binary32 copy of the point
- * (x32, u32), which is how the FP32 sampling path decides it. */
+/* f for one component at the FP64 point x. */
 static double genz_eval(int family, int ndim, const double *a, const double *u,
-                        const double *x, const float *x32, int fp32_decide)
+                        const double *x)
 {
     double s = 0.0, p = 1.0;
     switch (family) {
@@ -344,11 +344,9 @@ static double genz_eval(int family, int ndim, const double *a, const double *u,
         return exp(-s);
     case OR_DISCONTINUOUS: {
         int ncut = ndim < 2 ? ndim : 2;
-        for (int i = 0; i < ncut; ++i) {
-            int outside = fp32_decide ? (x32[i] > (float)u[i]) : (x[i] > u[i]);
-            if (outside)
+        for (int i = 0; i < ncut; ++i)
+            if (x[i] > u[i])
                 return 0.0;
-        }
         for (int i = 0; i < ndim; ++i)
             s += a[i] * x[i];
         return exp(s);
@@ -362,7 +360,7 @@ static double genz_eval(int family, int ndim, const double *a, const double *u,
 double or_genz(int family, int ndim, const double *a, const double *u,
                const double *x)
 {
-    return genz_eval(family, ndim, a, u, x, NULL, 0);
+    return genz_eval(family, ndim, a, u, x);
 }
 
 /* Gauss-Legendre nodes/weights on [-1,1] by Newton's method on P_n. */
@@ -500,8 +498,50 @@ typedef struct {
     uint64_t start;
     int64_t n;
     or_sum S1[OR_MAX_COMP], S2[OR_MAX_COMP];
+    or_sum A1[OR_MAX_COMP];            /* sum |J f_c| */
+    or_sum B1[OR_MAX_COMP], B2[OR_MAX_COMP]; /* boundary mass, see below */
     or_sum *H; /* [ndim][nbins] */
 } sample_job;
+
+/*
+ * The discontinuity band.  The discontinuous family switches between 0 and
+ * exp(sum a_i x_i) where x_1 or x_2 crosses u_1 or u_2.  The oracle takes
+ * that decision on its FP64 point.  An evaluation in a precision of p
+ * significand bits (binary32: p = 24) forms the point from the FP64 edge
+ * e_k and width w_k of its bin: rounding e_k (or e_k - w_k, or e_k - 2 w_k)
+ * and w_k once each, one fused multiply-add for e_k + w_k frac, and the
+ * comparison value u_i rounded once, moves x - u by at most
+ *   2^-p (|e_k - 2 w_k| + 3 w_k + |x| + u) <= 7 * 2^-p * e_(k+1)
+ * (x <= e_(k+1), u within the band of x), so a point whose FP64 coordinate
+ * lies within 2^(3-p) e_(k+1) of u_i may be decided either way there, and
+ * nowhere else.  Such a point is "ambiguous" when no other cut already
+ * puts it outside; its alternative value is g = exp(sum a_i x_i).  The
+ * boundary mass of a pass is B1_c = sum |J g| and B2_c = sum (J g)^2 over
+ * its ambiguous points: a binary32 pass may differ from the oracle's by at
+ * most that much in S1_c and S2_c (and in any histogram bin, by B2_0).
+ * Returns g for an ambiguous point, else 0.
+ */
+static double disc_ambiguous(int ndim, const double *a, const double *u, const double *x,
+                             const int *kbin, const double *edges, int N, int band_bits)
+{
+    if (band_bits <= 0)
+        return 0.0;
+    int ncut = ndim < 2 ? ndim : 2, amb = 0;
+    for (int i = 0; i < ncut; ++i) {
+        const double right = edges[(size_t)i * (N + 1) + kbin[i] + 1];
+        const double band = ldexp(right, 3 - band_bits);
+        if (fabs(x[i] - u[i]) <= band)
+            amb = 1;
+        else if (x[i] > u[i])
+            return 0.0;  /* outside whichever way the other cut goes */
+    }
+    if (!amb)
+        return 0.0;
+    double s = 0.0;
+    for (int i = 0; i < ndim; ++i)
+        s += a[i] * x[i];
+    return exp(s);
+}
 
 static void *sample_range(void *arg)
 {
@@ -510,31 +550,15 @@ static void *sample_range(void *arg)
     const int ndim = p->ndim, N = p->nbins;
     uint64_t X[OR_MAX_DIM], Y[OR_MAX_DIM];
     double x[OR_MAX_DIM];
-    float x32[OR_MAX_DIM];
     int kbin[OR_MAX_DIM];
-    const uint64_t mask = (((uint64_t)1) << p->bits) - 1;
     for (int64_t j = 0; j < job->n; ++j) {
         or_point_words(p->gen, p->seed, ndim, job->V, job->start + (uint64_t)j, X);
         for (int d = 0; d < ndim; ++d)
             Y[d] = X[d] >> (64 - p->bits);
         double J = map_point(ndim, N, job->edges, Y, p->bits, x, kbin);
-        if (p->fp32_decide) {
-            /* the binary32 point as the FP32 path forms it: with
-             * w = e_(k+1) - e_k, x = fmaf((float)w, 1 + frac, (float)(e_k - w))
-             * (w (1 + frac) is exact in binary32, so one rounding) */
-            for (int d = 0; d < ndim; ++d) {
-                const double *e = job->edges + (size_t)d * (N + 1);
-                int k = kbin[d];
-                uint64_t t = Y[d] * (uint64_t)N;
-                double frac = ldexp((double)(t & mask), -p->bits);
-                double w = e[k + 1] - e[k];
-                x32[d] = fmaf((float)w, (float)(1.0 + frac), (float)(e[k] - w));
-            }
-        }
         double Jf0 = 0.0;
         for (int c = 0; c < p->ncomp; ++c) {
-            double f = genz_eval(p->family[c], ndim, p->a[c], p->u[c], x, x32,
-                                 p->fp32_decide);
+            double f = genz_eval(p->family[c], ndim, p->a[c], p->u[c], x);
             if (p->delay > 0) {
                 /* the cost knob (the paper's calibrated delay, Sect. 4.1):
                  * rounds of ndim dependent multiply-adds z <- z/2 + x_d,
@@ -548,6 +572,15 @@ static void *sample_range(void *arg)
             double Jf = J * f;
             sum_add(&job->S1[c], Jf);
             sum_add(&job->S2[c], Jf * Jf);
+            sum_add(&job->A1[c], fabs(Jf));
+            if (p->family[c] == OR_DISCONTINUOUS) {
+                double g = disc_ambiguous(ndim, p->a[c], p->u[c], x, kbin, job->edges, N,
+                                          p->band_bits);
+                if (g != 0.0) {
+                    sum_add(&job->B1[c], fabs(J * g));
+                    sum_add(&job->B2[c], (J * g) * (J * g));
+                }
+            }
             if (c == 0)
                 Jf0 = Jf;
         }
@@ -561,18 +594,20 @@ static void *sample_range(void *arg)
 /*
  * Sample n points with indices start..start+n-1 on the grid `edges`
  * ([ndim][nbins+1]).  Outputs: S1[c] = sum J f_c, S2[c] = sum (J f_c)^2,
- * H[d*nbins + k] = sum over points in bin k of axis d of (J f_0)^2.
+ * H[d*nbins + k] = sum over points in bin k of axis d of (J f_0)^2; and,
+ * when A1 is not NULL, A1[c] = sum |J f_c| and the boundary mass B1[c],
+ * B2[c] of the discontinuity band (above; zero unless p->band_bits > 0).
  * nthreads > 1 splits the index range into contiguous chunks (the CPU
  * analogue of the paper's n/N points per core); the partial sums are
  * combined in chunk order.
  */
-int or_sample(const or_problem *p, const uint64_t *V, const double *edges,
-              uint64_t start, int64_t n, int nthreads, double *S1, double *S2,
-              double *H)
+int or_sample_bounds(const or_problem *p, const uint64_t *V, const double *edges,
+                     uint64_t start, int64_t n, int nthreads, double *S1, double *S2,
+                     double *H, double *A1, double *B1, double *B2)
 {
     if (p->ndim < 1 || p->ndim > OR_MAX_DIM || p->ncomp < 1 ||
         p->ncomp > OR_MAX_COMP || p->nbins < 2 || p->nbins > OR_MAX_BINS ||
-        p->bits < 1 || p->bits > 55 || n < 0)
+        p->bits < 1 || p->bits > 55 || n < 0 || p->band_bits < 0 || p->band_bits > 53)
         return -1;
     if (nthreads < 1)
         nthreads = 1;
@@ -610,13 +645,21 @@ int or_sample(const or_problem *p, const uint64_t *V, const double *edges,
             pthread_join(th[t], NULL);
     }
     for (int c = 0; c < p->ncomp; ++c) {
-        or_sum a1 = {0, 0}, a2 = {0, 0};
+        or_sum a1 = {0, 0}, a2 = {0, 0}, aa = {0, 0}, b1 = {0, 0}, b2 = {0, 0};
         for (int t = 0; t < nthreads; ++t) {
             sum_add(&a1, sum_value(&jobs[t].S1[c]));
             sum_add(&a2, sum_value(&jobs[t].S2[c]));
+            sum_add(&aa, sum_value(&jobs[t].A1[c]));
+            sum_add(&b1, sum_value(&jobs[t].B1[c]));
+            sum_add(&b2, sum_value(&jobs[t].B2[c]));
         }
         S1[c] = sum_value(&a1);
         S2[c] = sum_value(&a2);
+        if (A1) {
+            A1[c] = sum_value(&aa);
+            B1[c] = sum_value(&b1);
+            B2[c] = sum_value(&b2);
+        }
     }
     for (size_t b = 0; b < nh; ++b) {
         or_sum a = {0, 0};
@@ -628,6 +671,14 @@ int or_sample(const or_problem *p, const uint64_t *V, const double *edges,
     free(hbuf);
     free(th);
     return 0;
+}
+
+/* The pass without the error bounds. */
+int or_sample(const or_problem *p, const uint64_t *V, const double *edges,
+              uint64_t start, int64_t n, int nthreads, double *S1, double *S2,
+              double *H)
+{
+    return or_sample_bounds(p, V, edges, start, n, nthreads, S1, S2, H, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------ */

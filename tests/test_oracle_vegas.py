@@ -137,18 +137,92 @@ def test_thread_split_is_sum_invariant():
         np.testing.assert_allclose(x1, x4, rtol=1e-14, atol=1e-300)
 
 
-def test_fp32_decision_changes_only_boundary_points():
-    # deciding x > u in binary32 moves at most a handful of points across
-    # the discontinuity.
+def _scipy_points(ndim, start, n):
+    # scipy's unscrambled Sobol points at 23 bits (a library special case of
+    # the oracle's generator, pinned in test_oracle_sobol.py)
+    eng = stats.qmc.Sobol(ndim, scramble=False, bits=52)
+    pts = eng.random_base2(int(math.ceil(math.log2(start + n))))[start:start + n]
+    return np.floor(pts * 2.0 ** 23) / 2.0 ** 23
+
+
+@pytest.mark.parametrize("j0", [5, 17, 40])
+def test_boundary_mass_counts_exactly_the_points_in_the_band(j0):
+    # Discontinuous family on the uniform power-of-two grid (J = 1, x = y).
+    # The cut u_1 is put at point j0's own coordinate, u_2 = 1 (never cuts):
+    # the only point within the band is j0, and its boundary mass is the
+    # value it would have inside, exp(sum a x).  Fixed by the definition of
+    # the band, checked against scipy's points.
+    ndim, N, start, n = 3, 64, 1, 64
+    a = np.array([0.7, 1.1, 0.4])
+    y = _scipy_points(ndim, start, n)
+    u = np.array([y[j0, 0], 1.0, 0.5])
+    p = _problem(ndim, [O.DISCONTINUOUS], a, u, nbins=N, bits=23)
+    r = O.sample_bounds(p, O.grid_uniform(ndim, N), start, n)
+    g = math.exp(float(a @ y[j0]))
+    # (no other point within 2^-21 e_(k+1) of either cut)
+    assert np.sum(np.abs(y[:, 0] - u[0]) <= 2.0 ** -21) == 1
+    assert r.B1[0] == pytest.approx(g, rel=1e-15)
+    assert r.B2[0] == pytest.approx(g * g, rel=1e-15)
+    # the oracle's own decision is the FP64 one: x = u is inside
+    inside = (y[:, 0] <= u[0]) & (y[:, 1] <= u[1])
+    assert r.S1[0] == pytest.approx(np.sum(np.exp(y[inside] @ a)), rel=1e-14)
+    # a cut on the other axis that puts the point outside anyway removes it
+    u2 = u.copy()
+    u2[1] = y[j0, 1] - 1e-3
+    r2 = O.sample_bounds(_problem(ndim, [O.DISCONTINUOUS], a, u2, nbins=N, bits=23),
+                         O.grid_uniform(ndim, N), start, n)
+    assert r2.B1[0] == 0.0 and r2.B2[0] == 0.0
+    # an FP64 comparison (52-bit coordinates, no band) has no boundary mass
+    r3 = O.sample_bounds(_problem(ndim, [O.DISCONTINUOUS], a, u, nbins=N, bits=52),
+                         O.grid_uniform(ndim, N), start, n)
+    assert r3.B1[0] == 0.0
+
+
+def test_boundary_band_width_is_eight_binary32_units_of_the_right_edge():
+    # the band is |x - u| <= 2^-21 e_(k+1): a cut 0.9 band widths from the
+    # point keeps it ambiguous, 1.1 widths does not
+    ndim, N, start, n, j0 = 2, 32, 1, 32, 9
+    a = np.array([0.5, 0.5])
+    y = _scipy_points(ndim, start, n)
+    k = int(y[j0, 0] * N)
+    band = 2.0 ** -21 * (k + 1) / N
+    got = []
+    for t in (0.9, 1.1, -0.9, -1.1):
+        u = np.array([y[j0, 0] + t * band, 1.0])
+        p = _problem(ndim, [O.DISCONTINUOUS], a, u, nbins=N, bits=23)
+        got.append(O.sample_bounds(p, O.grid_uniform(ndim, N), start, n).B1[0] > 0)
+    assert got == [True, False, True, False]
+
+
+def test_abs_sum_bounds_the_sum():
+    # sum |J f| equals S1 bit for bit for a positive integrand and exceeds
+    # |S1| for an oscillatory one; no family but the discontinuous one has
+    # boundary mass
+    e = _random_grid(4, 32, 3)
+    fams = [O.GAUSSIAN, O.OSCILLATORY, O.CORNER_PEAK, O.C0]
+    p = _problem(4, fams, [2.0, 3.0, 1.0, 0.5], [0.3, 0.6, 0.5, 0.45], nbins=32, bits=23)
+    p.a[1] *= 4
+    r = O.sample_bounds(p, e, 1, 20000, nthreads=3)
+    assert r.A1[0] == r.S1[0] and r.A1[2] == r.S1[2] and r.A1[3] == r.S1[3]
+    assert r.A1[1] > abs(r.S1[1])
+    assert np.all(r.B1 == 0) and np.all(r.B2 == 0)
+    S1, S2, H = O.sample(p, e, 1, 20000)
+    np.testing.assert_allclose(S1, r.S1, rtol=1e-14)
+    np.testing.assert_allclose(H, r.H, rtol=1e-14)
+
+
+def test_boundary_mass_is_small_and_scales_with_the_band():
+    # on a random grid the ambiguous points are those within ~1e-6 of a
+    # cut: their mass is a small fraction of the pass, and it vanishes in
+    # FP64 (band_bits 53: a band of 2^-50)
     a, u = [0.5, 0.5, 0.5], [0.3, 0.7, 0.5]
-    p64 = _problem(3, [O.DISCONTINUOUS], a, u, nbins=64, bits=23)
-    p32 = _problem(3, [O.DISCONTINUOUS], a, u, nbins=64, bits=23)
-    p32.fp32_decide = True
     e = _random_grid(3, 64, 2)
-    n = 50000
-    s64 = O.sample(p64, e, 1, n)[0][0]
-    s32 = O.sample(p32, e, 1, n)[0][0]
-    assert abs(s64 - s32) <= 10 * math.exp(1.5) * 64 ** 3 * (e[:, 1:] - e[:, :-1]).max(axis=1).prod()
+    n = 200000
+    p = _problem(3, [O.DISCONTINUOUS], a, u, nbins=64, bits=23)
+    r = O.sample_bounds(p, e, 1, n, nthreads=4)
+    assert 0.0 <= r.B1[0] <= 1e-3 * r.S1[0]
+    p.band_bits = 53
+    assert O.sample_bounds(p, e, 1, n, nthreads=4).B1[0] <= r.B1[0]
 
 
 # ---------------------------------------------------------------- refinement
