@@ -209,7 +209,7 @@ def cpu_oracle_rate(p, target_s: float, threads: int):
 
     import oracle as O
     prob = O.Problem(p.ndim, list(p.families), np.asarray(p.a), np.asarray(p.u),
-                     nbins=p.nbins, bits=23, fp32_decide=True)
+                     nbins=p.nbins, bits=23)
     prob.directions()
     n0 = 2000 * threads
     t = time.perf_counter()
@@ -232,7 +232,7 @@ def oracle_pass_rate(problems, cap: int, threads: int) -> tuple:
     total, dt = 0, 0.0
     for p in problems:
         prob = O.Problem(p.ndim, list(p.families), np.asarray(p.a), np.asarray(p.u),
-                         nbins=p.nbins, bits=23, fp32_decide=True)
+                         nbins=p.nbins, bits=23)
         prob.directions()
         e = O.grid_uniform(p.ndim, p.nbins)
         n = min(int(p.nstart), cap)
@@ -634,7 +634,7 @@ def measure_cost_sweep(ctx, cg, W, threads: int, delays=(0, 64, 256, 1024, 4096)
         torch.cuda.synchronize()
         gpu = 5 * p.nstart / (s0.elapsed_time(s1) * 1e-3)
         I.close()
-        prob = O.Problem(p.ndim, [3], a, u, nbins=p.nbins, bits=23, fp32_decide=True, delay=dl)
+        prob = O.Problem(p.ndim, [3], a, u, nbins=p.nbins, bits=23, delay=dl)
         e = O.grid_uniform(p.ndim, p.nbins)
         n = 4096 * threads
         t = time.perf_counter()

@@ -56,6 +56,8 @@ extern "C" {
 #define CV_ENOTFOUND (-8)      /* unknown request id                       */
 #define CV_ESCRATCH (-9)       /* the problem does not fit the static scratch
                                   area of cv_vegas_noalloc                 */
+#define CV_ENONFINITE (-10)    /* an iteration result was NaN or infinite:
+                                  the run stopped there with fail = 1      */
 
 /* ------------------------------------------------- built-in integrands */
 /* Genz (1984) test families over [0,1]^ndim with parameters a_i > 0 and
@@ -219,7 +221,10 @@ int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_dev,
  * seed keys the CV_SCRAMBLE / CV_PSEUDO generators (the plain Sobol stream
  * does not depend on it).  integral/error/prob receive ncomp values each;
  * prob is the chi-square probability that the iteration results are not
- * consistent (P((m-1)/2, chi2/2) over m iterations). */
+ * consistent (P((m-1)/2, chi2/2) over m iterations).  An iteration whose
+ * result is NaN or infinite stops the run there: the call fills the
+ * outputs with *fail = 1 and returns CV_ENONFINITE (cv_result.status bit 0
+ * in the integral, batch and server calls). */
 int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g,
              double epsrel, double epsabs, int flags, int seed,
              int64_t mineval, int64_t maxeval, int64_t nstart,
@@ -247,7 +252,9 @@ typedef int (*cv_integrand_dev)(const int *ndim, const void *x_dev, const int *n
  * per tile, and the values are accumulated, with bins and Jacobians
  * recomputed from the Sobol index.  Arguments and results as cv_vegas;
  * flags may add CV_AOS.  Returns CV_EABORT (and *fail = -999) when the
- * integrand returns -999.  The points, values and state live in a device
+ * integrand returns -999, and CV_ENONFINITE (*fail = 1, outputs filled)
+ * when an iteration's result is NaN or infinite -- e.g. the integrand wrote
+ * a NaN.  The points, values and state live in a device
  * scratch area of the context (about (ndim + ncomp) * nvec values), grown
  * on demand and kept until cv_destroy, so calls on one context must not
  * overlap. */
@@ -348,12 +355,18 @@ int cv_suave(cv_ctx *ctx, const cv_genz *g, int nbins, int flags, uint64_t seed,
  * grid and histogram of the run live in one static device array of
  * CV_STATIC_SCRATCH_BYTES that every GPU loading this library holds until
  * the process exits.  No context is needed: `device` is the CUDA device and
- * `stream` the cudaStream_t to run on (NULL = the legacy default stream).
- * Limits: ndim * (2 nbins + 1) * 8 + 512 bytes must fit the array, else the
- * call returns CV_ESCRATCH (16 dimensions x 256 bins fit, 32 x 256 do
- * not); otherwise the arguments and return codes are those of cv_vegas.
+ * `stream` the cudaStream_t to run on (NULL = the legacy default stream);
+ * a stream that belongs to another device is refused with CV_EINVAL.  The
+ * call makes `device` current for its own work and restores the caller's
+ * current device before it returns, on every path.  It waits for its work
+ * on `stream` (it synchronises the stream) before returning the results.
+ * Limits: the run needs 512 + R(ndim * (nbins + 1) * 8) + ndim * nbins * 8
+ * bytes of the array, R() rounding up to a multiple of 256, and must fit
+ * CV_STATIC_SCRATCH_BYTES, else the call returns CV_ESCRATCH (16
+ * dimensions x 256 bins fit, and 32 x 254; 32 x 255 do not); otherwise
+ * the arguments and return codes are those of cv_vegas.
  * The first call on a device looks up the array's device address, so make
- * it before capturing a stream into a CUDA graph.  Every call on a device
+ * it before any stream capture.  Every call on a device
  * shares the one array and leaves its last contents there (each run clears
  * what must start at zero itself); calls whose GPU work overlaps -- two
  * streams, two host threads -- race and corrupt each other: serialise
@@ -458,6 +471,15 @@ int cv_batch_results(cv_batch *B, cv_result *out);
  * 2^17 points and keep the fastest (resets the integrals; call before
  * run). */
 int cv_batch_autotune(cv_batch *B);
+/* The per-iteration results of integral `item` of the batch's last run,
+ * as cv_integral_log: iter_I[j*ncomp + c] = S1/n_j, iter_var[j*ncomp + c] =
+ * (S2/n_j - (S1/n_j)^2)/(n_j - 1) for j < min(max_iter, the iterations its
+ * budget allows), ncomp its component count; host arrays of that size.
+ * cv_batch_grid copies its current grid edges[ndim][nbins+1] (after a run:
+ * refined once per iteration run).  Both synchronise the context's stream
+ * and return CV_OK, CV_EINVAL (bad handle, item or pointer) or CV_ECUDA. */
+int cv_batch_log(cv_batch *B, int item, int max_iter, double *iter_I, double *iter_var);
+int cv_batch_grid(cv_batch *B, int item, double *edges);
 /* Points per tile the batch uses for an iteration of n points. */
 int cv_batch_tile_points(const cv_batch *B, long long n);
 /* Kernels one cv_batch_run enqueues. */

@@ -36,6 +36,7 @@ PSEUDO = 0x2000    # pseudo-random points (Philox4x64-10 keyed by the seed)
 
 OK, EINVAL, ENOMEM, ECUDA, EABORT, ETIMEOUT, EADMIT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7, -8
 ESCRATCH = -9
+ENONFINITE = -10
 STATIC_SCRATCH_BYTES = 128 * 1024
 
 STREAM_LEGACY = 1  # cudaStreamLegacy
@@ -203,6 +204,8 @@ _SIGNATURES = {
     "cv_batch_autotune": (_i, [_vp]),
     "cv_batch_tile_points": (_i, [_vp, ctypes.c_longlong]),
     "cv_batch_kernels_per_run": (_i, [_vp]),
+    "cv_batch_log": (_i, [_vp, _i, _i, _vp, _vp]),
+    "cv_batch_grid": (_i, [_vp, _i, _vp]),
     "cv_batch_destroy": (None, [_vp]),
     "cv_batch_vegas": (_i, [_vp, _i, _vp, _vp]),
     "cv_vegas_cb": (_i, [_vp, _i, _i, _vp, _vp, _i64, _d, _d, _i, _i, _i64, _i64, _i64, _i64,
@@ -256,6 +259,7 @@ class VegasResult:
     integral: np.ndarray
     error: np.ndarray
     prob: np.ndarray
+    code: int = 0          # the call's return code when it is EABORT or ENONFINITE
 
 
 class Context:
@@ -385,8 +389,8 @@ class Context:
                                    epsrel, epsabs, flags, seed, mineval, maxeval, nstart,
                                    nincrease, nbatch, nbins, ctypes.byref(neval), ctypes.byref(fail),
                                    integral.ctypes.data, error.ctypes.data, prob.ctypes.data)
-        if rc == EABORT:
-            return VegasResult(neval.value, fail.value, integral, error, prob)
+        if rc in (EABORT, ENONFINITE):
+            return VegasResult(neval.value, fail.value, integral, error, prob, rc)
         self._check(rc, "cv_vegas_cb")
         return VegasResult(neval.value, fail.value, integral, error, prob)
 
@@ -560,6 +564,22 @@ class Batch:
 
     def kernels_per_run(self) -> int:
         return self.ctx._lib.cv_batch_kernels_per_run(self._h)
+
+    def log(self, item: int, max_iter: int):
+        """cv_batch_log: (I[m, ncomp], var[m, ncomp]) of integral `item`."""
+        nc = self._specs[item].g.ncomp
+        lI = np.zeros((max_iter, nc))
+        lV = np.zeros((max_iter, nc))
+        self.ctx._check(self.ctx._lib.cv_batch_log(self._h, item, max_iter, lI.ctypes.data, lV.ctypes.data),
+                        "cv_batch_log")
+        return lI, lV
+
+    def grid(self, item: int) -> np.ndarray:
+        """cv_batch_grid: the current edges [ndim, nbins+1] of integral `item`."""
+        sp = self._specs[item]
+        e = np.zeros((sp.g.ndim, sp.nbins + 1))
+        self.ctx._check(self.ctx._lib.cv_batch_grid(self._h, item, e.ctypes.data), "cv_batch_grid")
+        return e
 
 
 class Server:

@@ -1,5 +1,6 @@
 // cv_api.cu -- the C ABI (include/cubagpu.h): contexts, argument checks,
 // launch configuration, and the Vegas iteration driver.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -139,6 +140,7 @@ extern "C" const char *cv_strerror(int code)
     case CV_EBUSY: return "busy";
     case CV_ENOTFOUND: return "not found";
     case CV_ESCRATCH: return "problem too large for the static scratch area";
+    case CV_ENONFINITE: return "an iteration result was not finite";
     }
     return "unknown error";
 }
@@ -239,6 +241,77 @@ static int check_genz(cv_ctx *ctx, const cv_genz *g)
 }
 
 static const double kTwoPi = 6.283185307179586476925286766559;
+
+namespace cv {
+// The FP32 path's range precondition for a built-in integrand.  Its sums
+// hold J f and (J f)^2 in binary32, whose normal range ends at 2^-126 and
+// 2^128, so a component is accepted only when its largest value over the
+// cube and its value at the centre (1/2, ..., 1/2) -- where a grid starts
+// sampling, and a proxy for where its mass lies -- have squares within
+// [2^-120, 2^120]: |f| within [2^-60, 2^60] there (log2 bounds from the
+// closed formulas of each family).  The oscillatory family (|f| <= 1, zeros
+// anywhere) and the constant pass; the discontinuous family's centre is
+// checked only where it lies inside both cuts.  A component that fails
+// needs CV_FP64.  Returns the first failing component (and a message), or -1.
+int fp32_range_check(const cv_genz *g, char *msg, size_t len)
+{
+    const double log2e = 1.4426950408889634;
+    for (int c = 0; c < g->ncomp; ++c) {
+        const int D = g->ndim;
+        const double *a = g->a[c], *u = g->u[c];
+        double lmax = 0.0, lcen = 0.0;
+        bool has_centre = true;
+        switch (g->family[c]) {
+        case CV_PRODUCT_PEAK:
+            for (int d = 0; d < D; ++d) {
+                lmax += 2.0 * std::log2(a[d]);
+                lcen -= std::log2(1.0 / (a[d] * a[d]) + (0.5 - u[d]) * (0.5 - u[d]));
+            }
+            break;
+        case CV_CORNER_PEAK: {
+            double s = 0.0;
+            for (int d = 0; d < D; ++d) s += a[d];
+            lcen = -(D + 1) * std::log2(1.0 + 0.5 * s);
+            break;
+        }
+        case CV_GAUSSIAN:
+            for (int d = 0; d < D; ++d) lcen -= a[d] * a[d] * (0.5 - u[d]) * (0.5 - u[d]) * log2e;
+            break;
+        case CV_C0:
+            for (int d = 0; d < D; ++d) lcen -= a[d] * std::fabs(0.5 - u[d]) * log2e;
+            break;
+        case CV_DISCONTINUOUS: {
+            double smax = 0.0, scen = 0.0;
+            for (int d = 0; d < D; ++d) {
+                smax += a[d] * (d < 2 ? std::min(std::max(u[d], 0.0), 1.0) : 1.0);
+                scen += 0.5 * a[d];
+                if (d < 2 && u[d] < 0.5) has_centre = false;
+            }
+            lmax = smax * log2e;
+            lcen = scen * log2e;
+            break;
+        }
+        default:
+            has_centre = false;
+            break;
+        }
+        if (lmax > 60.0 || (has_centre && lcen < -60.0)) {
+            if (msg)
+                snprintf(msg, len, "component %d: values up to 2^%.0f, 2^%.0f at the centre: outside the "
+                         "FP32 path's range (squares must stay in binary32); use CV_FP64", c, lmax, lcen);
+            return c;
+        }
+    }
+    return -1;
+}
+}  // namespace cv
+
+static int check_fp32_range(cv_ctx *ctx, const cv_genz *g)
+{
+    char msg[256];
+    if (fp32_range_check(g, msg, sizeof(msg)) >= 0) return fail_msg(ctx, CV_EINVAL, "%s", msg);
+    return CV_OK;
+}
 
 template <typename Real>
 static void fill_params(const cv_genz *g, GenzParams<Real> *p)
@@ -437,6 +510,7 @@ extern "C" int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins, const double 
     if (flags & CV_FP64)
         return launch_pass<double>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr,
                                    flags, seed);
+    if ((rc = check_fp32_range(ctx, g))) return rc;
     return launch_pass<float>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr,
                               flags, seed);
 }
@@ -481,6 +555,7 @@ extern "C" int cv_sample_staged(cv_ctx *ctx, const cv_genz *g, int nbins, const 
     if (flags & CV_FP64) return fail_msg(ctx, CV_EINVAL, "the staged grid is the FP32 path's");
     if ((flags & CV_SCRAMBLE) && (flags & CV_PSEUDO))
         return fail_msg(ctx, CV_EINVAL, "CV_SCRAMBLE and CV_PSEUDO exclude each other");
+    if ((rc = check_fp32_range(ctx, g))) return rc;
     if (n == 0) return CV_OK;
     if (!table_dev || ((uintptr_t)table_dev & 7u) || !S1_dev || !S2_dev || !hist_dev)
         return fail_msg(ctx, CV_EINVAL, "null or unaligned buffer");
@@ -535,6 +610,7 @@ static int check_spec(cv_ctx *ctx, const cv_spec *sp)
     if (!(sp->epsrel >= 0) || !(sp->epsabs >= 0)) return fail_msg(ctx, CV_EINVAL, "negative tolerance");
     if ((sp->flags & CV_SCRAMBLE) && (sp->flags & CV_PSEUDO))
         return fail_msg(ctx, CV_EINVAL, "CV_SCRAMBLE and CV_PSEUDO exclude each other");
+    if (!(sp->flags & CV_FP64)) return check_fp32_range(ctx, &sp->g);
     return CV_OK;
 }
 
@@ -577,6 +653,7 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
     ca.nincrease = sp.nincrease;
     ca.log_I = I->log_I;
     ca.log_var = I->log_var;
+    ca.log_cap = kLogCap;
     cudaError_t e = launch_refine_combine(sp.g.ndim, sp.nbins, I->H, I->edges, ca, I->ew32, I->map, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "refine/combine kernel launch");
     return CV_OK;
@@ -1022,6 +1099,7 @@ extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, doub
         error[c] = res.error[c];
         prob[c] = res.prob[c];
     }
+    if (res.status & 1) return fail_msg(ctx, CV_ENONFINITE, "iteration %d gave a non-finite result", res.iterations);
     return CV_OK;
 }
 
@@ -1149,7 +1227,9 @@ struct cv_batch {
     std::vector<cv_spec> specs;
     std::vector<int> jmax;                       // iterations of each integral
     std::vector<long long> n0;                   // first iteration size
-    void *mem = nullptr;                         // states, grids, histograms
+    void *mem = nullptr;                         // states, grids, histograms, logs
+    std::vector<double *> edges, log_I, log_var; // per integral (device)
+    std::vector<int> log_cap;                    // iterations each log holds
     BatchItem *d_items = nullptr;
     CombineArgs *d_cargs = nullptr;
     int2 *d_axes = nullptr;
@@ -1346,8 +1426,10 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         B->n0[i] = specs[i].nstart;
         B->J = B->J > B->jmax[i] ? B->J : B->jmax[i];
         off[i] = total;
+        const size_t lcap = (size_t)(B->jmax[i] < kLogCap ? B->jmax[i] : kLogCap);
         total += sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255) +
-                 ((((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255);
+                 ((((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255) +
+                 ((2 * lcap * CV_MAX_COMP * sizeof(double) + 255) & ~(size_t)255);
         // (the map's form decides the kernel: powers of two from 32 bins)
         const bool p2 = make_map(N, ndim, false).pow2 != 0;
         int c = -1;
@@ -1406,6 +1488,12 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         it.st = (DevState *)p;
         it.edges = (double *)(p + sz_state);
         it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
+        const int lcap = B->jmax[i] < kLogCap ? B->jmax[i] : kLogCap;
+        double *logs = it.H + (((((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255) / sizeof(double));
+        B->edges.push_back(it.edges);
+        B->log_I.push_back(logs);
+        B->log_var.push_back(logs + (size_t)lcap * CV_MAX_COMP);
+        B->log_cap.push_back(lcap);
         CombineArgs &ca = cargs[i];
         ca.st = it.st;
         ca.ncomp = sp.g.ncomp;
@@ -1415,8 +1503,9 @@ extern "C" int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_
         ca.maxeval = sp.maxeval;
         ca.nstart = sp.nstart;
         ca.nincrease = sp.nincrease;
-        ca.log_I = nullptr;
-        ca.log_var = nullptr;
+        ca.log_I = B->log_I[i];
+        ca.log_var = B->log_var[i];
+        ca.log_cap = lcap;
         for (int d = 0; d < ndim; ++d) axes.push_back(make_int2(i, d));
     }
     int rc = CV_OK;
@@ -1493,6 +1582,38 @@ extern "C" int cv_batch_results(cv_batch *B, cv_result *out)
             r.chi2[c] = h.chi2[c];
         }
     }
+    return CV_OK;
+}
+
+extern "C" int cv_batch_log(cv_batch *B, int item, int max_iter, double *iter_I, double *iter_var)
+{
+    if (!B || !iter_I || !iter_var || item < 0 || item >= B->count || max_iter < 0) return CV_EINVAL;
+    cv_ctx *ctx = B->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int lc = B->log_cap[item], nc = B->specs[item].g.ncomp;
+    std::vector<double> lI((size_t)lc * CV_MAX_COMP), lV((size_t)lc * CV_MAX_COMP);
+    if (lc > 0) {
+        CV_CUDA(ctx, cudaMemcpyAsync(lI.data(), B->log_I[item], lI.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CV_CUDA(ctx, cudaMemcpyAsync(lV.data(), B->log_var[item], lV.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int m = max_iter < lc ? max_iter : lc;
+    for (int j = 0; j < m; ++j)
+        for (int c = 0; c < nc; ++c) {
+            iter_I[j * nc + c] = lI[(size_t)j * CV_MAX_COMP + c];
+            iter_var[j * nc + c] = lV[(size_t)j * CV_MAX_COMP + c];
+        }
+    return CV_OK;
+}
+
+extern "C" int cv_batch_grid(cv_batch *B, int item, double *edges)
+{
+    if (!B || !edges || item < 0 || item >= B->count) return CV_EINVAL;
+    cv_ctx *ctx = B->ctx;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t n = (size_t)B->specs[item].g.ndim * (B->specs[item].nbins + 1);
+    CV_CUDA(ctx, cudaMemcpyAsync(edges, B->edges[item], n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return CV_OK;
 }
 
@@ -1746,6 +1867,7 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         ca.nincrease = sp.nincrease;
         ca.log_I = nullptr;
         ca.log_var = nullptr;
+        ca.log_cap = 0;
         CV_CUDA(ctx, cudaMemcpyAsync(S->d_items + r.slot, &it, sizeof(it), cudaMemcpyHostToDevice, S->stream));
         CV_CUDA(ctx, cudaMemcpyAsync(S->d_cargs + r.slot, &ca, sizeof(ca), cudaMemcpyHostToDevice, S->stream));
     }
@@ -2280,6 +2402,7 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     memset(res, 0, sizeof(*res));
     res->neval = h.neval;
     res->iterations = h.iter;
+    res->status = h.status;
     res->fail = aborted ? -999 : (h.stopped ? h.fail : 1);
     for (int c = 0; c < ncomp; ++c) {
         res->integral[c] = h.integral[c];
@@ -2332,6 +2455,8 @@ extern "C" int cv_vegas_cb(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev in
         error[c] = res.error[c];
         prob[c] = res.prob[c];
     }
+    if (!rc && (res.status & 1))
+        return fail_msg(ctx, CV_ENONFINITE, "iteration %d gave a non-finite result", res.iterations);
     return rc;
 }
 
@@ -2770,6 +2895,7 @@ extern "C" int cv_suave(cv_ctx *ctx, const cv_genz *g, int nbins, int flags, uin
     if ((flags & CV_SCRAMBLE) && (flags & CV_PSEUDO))
         return fail_msg(ctx, CV_EINVAL, "CV_SCRAMBLE and CV_PSEUDO exclude each other");
     if (!nregions || !neval || !fail || !integral || !error) return fail_msg(ctx, CV_EINVAL, "null output");
+    if (!(flags & CV_FP64) && (rc = check_fp32_range(ctx, g))) return rc;
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
     const int ndim = g->ndim;
     const size_t ge = (size_t)ndim * (nbins + 1), gh = (size_t)ndim * nbins, gs = 2 * CV_MAX_COMP;

@@ -186,8 +186,9 @@ struct CombineArgs {
     int ncomp;
     double epsrel, epsabs;
     long long mineval, maxeval, nstart, nincrease;
-    double *log_I;                  // [kLogCap][CV_MAX_COMP] or null
+    double *log_I;                  // [log_cap][CV_MAX_COMP] or null
     double *log_var;
+    int log_cap;                    // iterations the log holds (<= kLogCap)
 };
 
 // ---- batched persistent launch (many integrals) ----
@@ -282,6 +283,9 @@ int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow
 int jit_compile_check(const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks, std::string *err);
 cudaError_t launch_jit_sample(const JitKernel &k, const SampleArgs<float> &a, int grid, cudaStream_t s);
 int jit_info(int *compiled);
+// cv_api.cu: the FP32 path's range precondition for built-in integrands
+// (first failing component and a message, or -1)
+int fp32_range_check(const cv_genz *g, char *msg, size_t len);
 #endif  // !__CUDACC_RTC__
 
 // Shared memory of a sampling block: the grid {e, w} with CV_MAX_BINS slots

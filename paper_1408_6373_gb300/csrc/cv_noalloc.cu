@@ -17,6 +17,10 @@
 // by clearing its state and histogram and writing a uniform grid), so
 // calls whose GPU work overlaps -- on two streams, or from two host
 // threads -- race and give wrong results; serialise them.
+//
+// The caller's thread state is left as it was: the call makes `device`
+// current only for its own work and restores the previous current device
+// on every return, and it refuses a stream that belongs to another device.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -29,6 +33,7 @@ namespace {
 static __device__ __align__(256) unsigned char g_scratch[CV_STATIC_SCRATCH_BYTES];
 
 constexpr size_t kStateBytes = (sizeof(cv::DevState) + 255) & ~(size_t)255;
+static_assert(kStateBytes == 512, "the size rule documented in cubagpu.h counts 512 bytes of state");
 constexpr int kMaxDevices = 64;
 
 std::mutex g_setup_mutex;
@@ -55,6 +60,25 @@ cudaError_t scratch_address(int device, char **out)
     *out = static_cast<char *>(g_scratch_dev[device]);
     return cudaSuccess;
 }
+
+// Makes a device current for the life of the guard, then restores the
+// device that was current before.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int device)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            prev = -1;
+            return;
+        }
+        ok = prev == device || cudaSetDevice(device) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 const double kTwoPi = 6.283185307179586476925286766559;
 
@@ -182,14 +206,26 @@ extern "C" int cv_vegas_noalloc(int device, void *stream, int ndim, int ncomp, c
     if (nstart < 2 || nincrease < 0 || maxeval < nstart || mineval < 0) return CV_EINVAL;
     if ((uint64_t)maxeval >= CV_INDEX_LIMIT || !(epsrel >= 0) || !(epsabs >= 0)) return CV_EINVAL;
     if (!neval || !fail || !integral || !error || !prob) return CV_EINVAL;
+    if (!(flags & CV_FP64) && cv::fp32_range_check(g, nullptr, 0) >= 0) return CV_EINVAL;
     // the run's scratch must fit the static area
     if (scratch_need(ndim, nbins) > CV_STATIC_SCRATCH_BYTES) return CV_ESCRATCH;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev ||
         device >= kMaxDevices)
         return CV_EINVAL;
-    if (cudaSetDevice(device) != cudaSuccess) return CV_ECUDA;
+    DeviceGuard guard(device);
+    if (!guard.ok) return CV_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    // a stream of another device would run this device's kernels there (the
+    // legacy and per-thread default handles mean the current device)
+    if (s && s != cudaStreamLegacy && s != cudaStreamPerThread) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return CV_EINVAL;
+        }
+        if (sdev != device) return CV_EINVAL;
+    }
     char *base = nullptr;
     if (scratch_address(device, &base) != cudaSuccess) return CV_ECUDA;
     cv::DevState *st = reinterpret_cast<cv::DevState *>(base);
@@ -221,6 +257,7 @@ extern "C" int cv_vegas_noalloc(int device, void *stream, int ndim, int ncomp, c
     ca.nincrease = nincrease;
     ca.log_I = nullptr;
     ca.log_var = nullptr;
+    ca.log_cap = 0;
     const bool poll = !(epsrel == 0.0 && epsabs == 0.0);
     cudaError_t e = (flags & CV_FP64)
         ? run<double>(g, nbins, flags, (unsigned long long)(long long)seed, sms, nmax, jmax, poll, ca, edges, H, st, s)
@@ -236,5 +273,5 @@ extern "C" int cv_vegas_noalloc(int device, void *stream, int ndim, int ncomp, c
         error[c] = h.error[c];
         prob[c] = h.prob[c];
     }
-    return CV_OK;
+    return (h.status & 1) ? CV_ENONFINITE : CV_OK;
 }

@@ -221,6 +221,7 @@ __device__ void combine_iteration(const CombineArgs &A)
     const long long n = st->n_cur;
     const int j = st->iter;
     __shared__ int s_ok[CV_MAX_COMP];
+    __shared__ int s_bad[CV_MAX_COMP];
     __shared__ int s_stop;
     if (c < A.ncomp) {
         // every input first (independent loads), then the arithmetic: FP64
@@ -234,11 +235,13 @@ __device__ void combine_iteration(const CombineArgs &A)
         const double inv_n1 = __drcp_rn((double)(n - 1));
         const double I = __dmul_rn(S1, inv_n);
         const double var = __dmul_rn(__fma_rn(-I, I, __dmul_rn(S2, inv_n)), inv_n1);
-        if (A.log_I && j < kLogCap) {
+        if (A.log_I && j < A.log_cap) {
             A.log_I[j * CV_MAX_COMP + c] = I;
             A.log_var[j * CV_MAX_COMP + c] = var;
         }
-        if (!isfinite(I) || !isfinite(var)) atomicOr(&st->status, 1);
+        const bool bad = !isfinite(I) || !isfinite(var);
+        if (bad) atomicOr(&st->status, 1);
+        s_bad[c] = bad;
         const int m = j + 1;
         const double sumI = sumI0 + I;
         st->sumI[c] = sumI;
@@ -269,20 +272,28 @@ __device__ void combine_iteration(const CombineArgs &A)
         st->error[c] = error;
         st->chi2[c] = chi2;
         const double tol = fmax(A.epsabs, A.epsrel * fabs(integral));
-        s_ok[c] = error <= tol;
+        s_ok[c] = !bad && error <= tol;
         st->S1[c] = 0.0;
         st->S2[c] = 0.0;
     }
     __syncthreads();
     if (c == 0) {
-        int ok = 1;
-        for (int i = 0; i < A.ncomp; ++i) ok &= s_ok[i];
+        int ok = 1, bad = 0;
+        for (int i = 0; i < A.ncomp; ++i) {
+            ok &= s_ok[i];
+            bad |= s_bad[i];
+        }
         const long long neval = st->neval + n;
         st->neval = neval;
         st->iter = j + 1;
         const long long next = A.nstart + (long long)(j + 1) * A.nincrease;
         int stop = 0;
-        if (neval >= A.mineval && ok) {
+        if (bad) {
+            // a non-finite iteration result (the integrand returned NaN or
+            // Inf, or its squares overflowed): the run stops unconverged
+            st->fail = 1;
+            stop = 1;
+        } else if (neval >= A.mineval && ok) {
             st->fail = 0;
             stop = 1;
         } else if (neval + next > A.maxeval) {

@@ -15,7 +15,8 @@ Workloads (sizes as the benchmark configurations name them):
   batch4096    4096 integrals, ndim ~ U{2..16}, family ~ U{0..5}, points per
                iteration log-uniform in [1e4, 1e7], 10 iterations, 64 bins
   serve        Poisson arrivals, ndim ~ U{2..32}, ncomp ~ U{1..4}, epsrel
-               log-uniform in [1e-5, 1e-3], maxeval 1e8
+               log-uniform in [1e-5, 1e-3], maxeval 1e8 (a corner-peak
+               component's a scaled down where needed: fp32_corner_peak)
   large30d     ndim 30, C0 and discontinuous, a_i = 1/2, u ~ U(0,1),
                256 bins, 15 x 1e9
 """
@@ -81,6 +82,20 @@ class Problem:
         return self.maxeval // self.nstart if self.nincrease == 0 else -1
 
 
+def fp32_corner_peak(a: np.ndarray) -> np.ndarray:
+    """A corner-peak component's parameters scaled (down only) so that its
+    value at the cube's centre, (1 + sum a / 2)^-(ndim+1), is at least
+    2^-48: its squares then stay well inside binary32's normal range, which
+    the FP32 path's sums of (J f)^2 need (in high dimensions the unscaled
+    U(1/2, 3/2) draws put the values near 2^-120 and their squares below
+    2^-126)."""
+    a = np.asarray(a, dtype=np.float64)
+    ndim = a.shape[-1]
+    smax = 2.0 * (2.0 ** (48.0 / (ndim + 1)) - 1.0)
+    s = a.sum(axis=-1, keepdims=True)
+    return a * np.minimum(1.0, smax / s)
+
+
 def gaussian3d() -> Problem:
     return Problem(3, [3], np.full((1, 3), 5.0), np.full((1, 3), 0.5), nbins=50,
                    nstart=10 ** 4, nincrease=0, maxeval=10 * 10 ** 4, fp64=True)
@@ -129,6 +144,9 @@ def serve_requests(seed: int = 4, rate: float = 2000.0, duration: float = 10.0,
         fams = [rng.integer(0, 5) for _ in range(ncomp)]
         a = 0.5 + np.array([rng.uniforms(ndim) for _ in range(ncomp)])
         u = np.array([rng.uniforms(ndim) for _ in range(ncomp)])
+        for c in range(ncomp):
+            if fams[c] == 2:
+                a[c] = fp32_corner_peak(a[c])
         eps = rng.log_uniform(1e-5, 1e-3)
         out.append((t, Problem(ndim, fams, a, u, nbins=64, nstart=nstart,
                                nincrease=nincrease, maxeval=maxeval, epsrel=eps)))

@@ -1,6 +1,6 @@
 """GPU tests of the batched persistent path (cv_batch_*): every integral of
 a batch against the same integral run alone (cv_vegas, FP32 path) and
-against the FP64 oracle's closed forms; uneven sizes, mixed dimensions and
+against the Genz closed forms within 3 sigma; uneven sizes, mixed dimensions and
 bin counts, early stops, and the tile autotuner."""
 import math
 
@@ -37,7 +37,7 @@ def _specs(count, seed, nmin=300, nmax=60000, iters=5, nbins_choices=(64, 32, 50
         nbins = int(rng.choice(nbins_choices))
         g = cg.genz(ndim, [fam], a, u)
         specs.append(cg.spec(g, nbins=nbins, maxeval=iters * n, nstart=n))
-        probs.append(O.Problem(ndim, [fam], a[None], u[None], nbins=nbins, bits=23, fp32_decide=True))
+        probs.append(O.Problem(ndim, [fam], a[None], u[None], nbins=nbins, bits=23))
     return specs, probs
 
 
@@ -51,7 +51,7 @@ def test_batch_matches_single_runs(ctx):
         # the 1e-7 level, far below the statistical error
         assert abs(r.integral[0] - single.integral[0]) <= 2e-5 * abs(single.integral[0]) + 1e-2 * single.error[0]
         exact = p.exact()[0]
-        assert abs(r.integral[0] - exact) <= 4 * r.error[0] + 2e-6 * abs(exact) + 1e-12
+        assert abs(r.integral[0] - exact) <= 3 * r.error[0] + 2e-6 * abs(exact) + 1e-12
 
 
 def test_batch_small_power_of_two_bins(ctx):
@@ -63,7 +63,7 @@ def test_batch_small_power_of_two_bins(ctx):
         assert (r.neval, r.fail) == (single.neval, single.fail)
         assert abs(r.integral[0] - single.integral[0]) <= 2e-5 * abs(single.integral[0]) + 1e-2 * single.error[0]
         exact = p.exact()[0]
-        assert abs(r.integral[0] - exact) <= 4 * r.error[0] + 2e-6 * abs(exact) + 1e-12
+        assert abs(r.integral[0] - exact) <= 3 * r.error[0] + 2e-6 * abs(exact) + 1e-12
 
 
 def test_batch_alone_equals_in_mix(ctx):

@@ -1,0 +1,138 @@
+"""The batched persistent sampling kernel (cv_batch_*, the kernel behind the
+4096-integral batch and the serving loop) against the FP64 oracle, element
+by element: every integral's first two iterations, read from the batch's
+per-iteration log, against the oracle's sampling pass on the same grid --
+the uniform grid for the first, the grid the batch's own first refinement
+produced for the second.
+
+72 integrals cover 2..32 dimensions (both sides of the 16/17 kernel
+boundary), all six Genz families, 50, 64, 128 and 256 bins (256 up to 22
+dimensions, the batched path's shared-memory limit), and iterations of up
+to a million points, so that tiles reach the largest size.  The FP32
+tolerances are those of tests/tolerances.py (1e-6 of sum |J f| plus the
+boundary mass for I, the implied variance bound)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.tolerances import check_fp32_iteration
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1408_6373_gb300 as cg  # noqa: E402
+from paper_1408_6373_gb300 import workloads as W  # noqa: E402
+
+THREADS = os.cpu_count() or 1
+COUNT = 72
+
+
+def _items():
+    rng = np.random.default_rng(2025)
+    out = []
+    for i in range(COUNT):
+        ndim = 2 + (5 * i) % 31
+        fam = i % 6
+        nbins = (64, 50, 256)[i % 3]
+        if nbins == 256 and ndim > 22:
+            nbins = 128
+        n = 10 ** 6 if i % 9 == 0 else int(np.exp(rng.uniform(np.log(2000), np.log(300000))))
+        a = 0.5 + rng.random(ndim)
+        u = rng.random(ndim)
+        if fam == O.CORNER_PEAK:
+            a = W.fp32_corner_peak(a)
+        out.append((ndim, fam, nbins, n, a, u))
+    return out
+
+
+def _specs(items, iters):
+    return [cg.spec(cg.genz(nd, [f], a, u), nbins=N, maxeval=iters * n, nstart=n)
+            for nd, f, N, n, a, u in items]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cg.build_library()
+    c = cg.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def runs(ctx):
+    items = _items()
+    B2 = ctx.batch(_specs(items, 2))
+    B2.run()
+    logs = [B2.log(i, 2) for i in range(COUNT)]
+    assert B2.tile_points(10 ** 6) >= 32768  # the million-point iterations use full tiles
+    B2.close()
+    B1 = ctx.batch(_specs(items, 1))
+    B1.run()
+    grids = [B1.grid(i) for i in range(COUNT)]
+    B1.close()
+    return items, logs, grids
+
+
+def _oracle(item, edges, start):
+    nd, f, N, n, a, u = item
+    p = O.Problem(nd, [f], a[None], u[None], nbins=N, bits=23)
+    return O.sample_bounds(p, edges, start, n, nthreads=THREADS)
+
+
+def test_batched_first_iteration_matches_oracle(runs):
+    items, logs, _ = runs
+    for i, item in enumerate(items):
+        nd, f, N, n, _, _ = item
+        (lI, lV) = logs[i]
+        ob = _oracle(item, O.grid_uniform(nd, N), 1)
+        check_fp32_iteration(lI[0], lV[0], ob, n, what=(i, nd, f, N, n))
+
+
+def test_batched_second_iteration_on_refined_grid_matches_oracle(runs):
+    items, logs, grids = runs
+    for i, item in enumerate(items):
+        nd, f, N, n, _, _ = item
+        (lI, lV) = logs[i]
+        assert np.all(np.diff(grids[i], axis=1) > 0)
+        ob = _oracle(item, grids[i], 1 + n)
+        check_fp32_iteration(lI[1], lV[1], ob, n, what=(i, nd, f, N, n))
+
+
+def test_batched_refinement_follows_the_oracle(runs):
+    # the batch's refined grid against the oracle's refinement of the
+    # oracle's own histogram: they differ only through the FP32 histogram
+    # (1e-5 of a bin's share at most), so edges agree to 1e-5 of the bin
+    items, _, grids = runs
+    for i, item in enumerate(items):
+        nd, f, N, n, _, _ = item
+        if n < 50000:
+            continue
+        ob = _oracle(item, O.grid_uniform(nd, N), 1)
+        ref = O.refine(O.grid_uniform(nd, N), ob.H)
+        assert np.max(np.abs(grids[i] - ref)) <= 1e-5 / N, (i, nd, f, N)
+
+
+def test_autotuned_tiles_and_alone_runs_match_oracle(ctx, runs):
+    # other tile sizes group the FP32 sums differently; an integral run alone
+    # has the same tiles as in the mix
+    items, logs, _ = runs
+    B = ctx.batch(_specs(items, 2))
+    B.autotune()
+    B.run()
+    for i in range(0, COUNT, 4):
+        lI, lV = B.log(i, 2)
+        nd, f, N, n, _, _ = items[i]
+        ob = _oracle(items[i], O.grid_uniform(nd, N), 1)
+        check_fp32_iteration(lI[0], lV[0], ob, n, what=("autotuned", i))
+    B.close()
+    for i in (0, 17, 45):
+        A = ctx.batch(_specs([items[i]], 2))
+        A.run()
+        aI, aV = A.log(0, 2)
+        A.close()
+        np.testing.assert_allclose(aI, logs[i][0], rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(aV, logs[i][1], rtol=1e-9, atol=1e-300)

@@ -115,3 +115,34 @@ def test_aos_layout_seen_by_integrand(ctx):
     assert shapes[0] == (2048, 3)
     # integral of x1 + x2 + x3 over the unit cube
     assert r.integral[0] == pytest.approx(1.5, rel=1e-4)
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+@pytest.mark.parametrize("flags", [0, cg.FP64])
+def test_nonfinite_integrand_value_stops_the_run(ctx, bad, flags):
+    # the integrand contract (Sect. 3.2.1-3.2.2) on the device: a value that
+    # is not finite, written by the caller's integrand into one tile of the
+    # third iteration, is detected in that iteration's combination; the run
+    # stops there with fail = 1 (not "accuracy reached", whatever the goal)
+    # and the call reports CV_ENONFINITE
+    n, nvec = 6000, 2500
+    calls = []
+
+    def poisoned(x, f, nvec_, stream):
+        calls.append(nvec_)
+        f[0].copy_(x.sum(0))
+        if len(calls) == 8:  # iterations of 3 tiles each: the 2nd tile of the 3rd
+            f[0, 17] = bad
+        return 0
+
+    # (mineval: the goal alone could not stop the run before iteration 5)
+    r = ctx.vegas_cb(poisoned, 3, 1, nvec=nvec, flags=flags, epsrel=1e-1, mineval=5 * n, maxeval=10 * n,
+                     nstart=n, nbins=16)
+    assert r.code == cg.ENONFINITE and r.fail == 1
+    assert r.neval == 3 * n and sum(calls) == 3 * n
+    assert not math.isfinite(r.integral[0]) or not math.isfinite(r.error[0])
+    # the same integrand without the bad value converges on the goal
+    ok = ctx.vegas_cb(lambda x, f, m, s: (f[0].copy_(x.sum(0)), 0)[1], 3, 1, nvec=nvec, flags=flags,
+                      epsrel=1e-1, mineval=5 * n, maxeval=10 * n, nstart=n, nbins=16)
+    assert ok.code == 0 and ok.fail == 0 and ok.neval == 5 * n
+    assert ok.integral[0] == pytest.approx(1.5, rel=1e-3)

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tests.tolerances import check_fp32_pass
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -95,12 +96,8 @@ def test_sample_fp32_matches_oracle(ctx, flag, gen, jit, N):
     g = cg.genz(ndim, fams, a, u)
     edges = _random_grid(ndim, N, 3)
     S1, S2, H = _gpu_sample(ctx, g, edges, 1, n, flag | jit, seed)
-    p = O.Problem(ndim, fams, a, u, nbins=N, bits=23, fp32_decide=True, gen=gen, seed=seed)
-    oS1, oS2, oH = O.sample(p, edges, 1, n, nthreads=8)
-    for c in range(4):
-        assert abs(S1[c] - oS1[c]) <= 1e-6 * math.sqrt(n * oS2[c]), (c, S1[c], oS1[c])
-        assert abs(S2[c] - oS2[c]) <= 1e-6 * oS2[c]
-    assert np.max(np.abs(H - oH)) <= 1e-5 * oH.max()
+    p = O.Problem(ndim, fams, a, u, nbins=N, bits=23, gen=gen, seed=seed)
+    check_fp32_pass(S1, S2, H, O.sample_bounds(p, edges, 1, n, nthreads=8), n)
 
 
 @pytest.mark.parametrize("flag,gen", GENS)

@@ -3,13 +3,14 @@ benchmark times: genz8d4c (ndim 8; oscillatory, product peak, corner peak,
 Gaussian; 128 bins; 20 iterations x 1e7 Sobol points), FP32 with the
 run-time specialised kernel, one device-resident integral.
 
-- The run meets every component's Genz closed form within 4 sigma (plus
+- The run meets every component's Genz closed form within 3 sigma (plus
   1e-6 relative for the FP32 evaluation bias).
 - One full 1e7-point pass over the run's final grid, sampled through the
   staged grid exactly as an iteration samples, against the oracle on the
-  same grid, element by element: S1 within 1e-6 of sqrt(n S2), S2 within
-  1e-6 relative, the histogram within 1e-5 of its row maximum (the oracle
-  decides float branches in binary32).
+  same grid, element by element, with the FP32 tolerances of
+  tests/tolerances.py (S1 within 1e-6 of sum |J f|, S2 within 1e-6
+  relative, the implied variance bound, the histogram within 1e-5 of its
+  row maximum).
 - f = 1 over an aligned full-size range gives exact sums and exactly n/N
   points in every bin of every axis.
 """
@@ -20,6 +21,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tests.tolerances import check_fp32_pass
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -56,7 +58,7 @@ def test_headline_run_meets_closed_forms(run):
     assert r.neval == p.maxeval and r.iterations == 20
     for c, fam in enumerate(p.families):
         exact = O.genz_exact(fam, p.a[c], p.u[c])
-        assert abs(r.integral[c] - exact) <= 4 * r.error[c] + 1e-6 * abs(exact), (c, r.integral[c], exact)
+        assert abs(r.integral[c] - exact) <= 3 * r.error[c] + 1e-6 * abs(exact), (c, r.integral[c], exact)
 
 
 def test_full_size_pass_matches_oracle(ctx, run):
@@ -70,12 +72,8 @@ def test_full_size_pass_matches_oracle(ctx, run):
     ctx.sample_staged(g, p.nbins, table, 1, n, cg.JIT, S1, S2, H)
     ctx.synchronize()
     S1, S2, H = S1.cpu().numpy(), S2.cpu().numpy(), H.cpu().numpy()
-    prob = O.Problem(p.ndim, list(p.families), p.a, p.u, nbins=p.nbins, bits=23, fp32_decide=True)
-    oS1, oS2, oH = O.sample(prob, edges, 1, n, nthreads=os.cpu_count() or 1)
-    for c in range(4):
-        assert abs(S1[c] - oS1[c]) <= 1e-6 * math.sqrt(n * oS2[c]), (c, S1[c], oS1[c])
-        assert abs(S2[c] - oS2[c]) <= 1e-6 * oS2[c], (c, S2[c], oS2[c])
-    assert np.max(np.abs(H - oH)) <= 1e-5 * oH.max()
+    prob = O.Problem(p.ndim, list(p.families), p.a, p.u, nbins=p.nbins, bits=23)
+    check_fp32_pass(S1, S2, H, O.sample_bounds(prob, edges, 1, n, nthreads=os.cpu_count() or 1), n)
 
 
 def test_full_size_constant_gives_exact_counts(ctx):

@@ -12,6 +12,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle as O  # noqa: E402
 import paper_1408_6373_gb300 as cg  # noqa: E402
+from paper_1408_6373_gb300 import workloads as W  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -30,6 +31,9 @@ def _request(rng):
     fams = [int(f) for f in rng.integers(0, 6, ncomp)]
     a = 0.5 + rng.random((ncomp, ndim))
     u = rng.random((ncomp, ndim))
+    for c in range(ncomp):
+        if fams[c] == cg.CORNER_PEAK:
+            a[c] = W.fp32_corner_peak(a[c])
     eps = float(np.exp(rng.uniform(np.log(1e-4), np.log(1e-2))))
     g = cg.genz(ndim, fams, a, u)
     return cg.spec(g, nbins=64, epsrel=eps, maxeval=2 * 10 ** 6, nstart=4000, nincrease=8000)
@@ -62,21 +66,27 @@ def test_each_result_same_alone_and_in_the_mix(ctx):
         for c in range(sp.g.ncomp):
             assert r.integral[c] == pytest.approx(alone.integral[c], rel=1e-10, abs=1e-15)
             assert r.error[c] == pytest.approx(alone.error[c], rel=1e-8)
-    # against the mathematics: wherever the single-integral path is
-    # consistent with the Genz closed form (pathological requests, e.g. a
-    # discontinuous integrand in 29 dimensions, defeat every Vegas run), the
-    # served result is too
-    checked = 0
-    for sp, r in zip(specs, res):
-        ref = ctx.vegas(sp.g, epsrel=sp.epsrel, flags=0, maxeval=sp.maxeval, nstart=sp.nstart,
-                        nincrease=sp.nincrease, nbins=sp.nbins)
+    # against the mathematics: every served estimate within 3 sigma of its
+    # Genz closed form.  A miss is accepted only where Vegas itself misses:
+    # the oracle's FP64 Vegas run of the same request (same points, grid and
+    # schedule) must then be more than 2 sigma off as well, and both misses
+    # are listed in the message.
+    misses, total = [], 0
+    for k, (sp, r) in enumerate(zip(specs, res)):
+        nd = sp.g.ndim
         for c in range(sp.g.ncomp):
-            ex = O.genz_exact(sp.g.family[c], np.array(sp.g.a[c][:sp.g.ndim]),
-                              np.array(sp.g.u[c][:sp.g.ndim]))
-            if abs(ref.integral[c] - ex) < 3 * ref.error[c]:
-                assert abs(r.integral[c] - ex) < 4 * r.error[c] + 1e-6 * abs(ex)
-                checked += 1
-    assert checked >= 40
+            total += 1
+            a, u = np.array(sp.g.a[c][:nd]), np.array(sp.g.u[c][:nd])
+            ex = O.genz_exact(sp.g.family[c], a, u)
+            z = abs(r.integral[c] - ex) / max(r.error[c], 1e-300)
+            if z >= 3:
+                p = O.Problem(nd, [sp.g.family[c]], a[None], u[None], nbins=sp.nbins)
+                o = O.vegas(p, epsrel=sp.epsrel, maxeval=sp.maxeval, nstart=sp.nstart,
+                            nincrease=sp.nincrease, nthreads=16)
+                zo = abs(o.integral[0] - ex) / max(o.error[0], 1e-300)
+                misses.append((k, c, nd, sp.g.family[c], round(z, 2), round(zo, 2)))
+    assert all(m[5] > 2 for m in misses), misses
+    assert len(misses) <= 0.03 * total, misses
 
 
 def test_arrivals_while_busy_join_later_rounds(ctx):

@@ -61,3 +61,36 @@ def test_noalloc_accuracy_goal_and_too_large_problem(ctx):
     with pytest.raises(cg.CubaGpuError) as ei:
         cg.vegas_noalloc(big, device=0, maxeval=4000, nstart=2000, nbins=256)
     assert ei.value.code == cg.ESCRATCH
+
+
+def test_noalloc_leaves_the_current_device_and_takes_a_side_stream(ctx):
+    # a caller embedded in another framework keeps its thread's current
+    # device; the work may run on any stream of that device
+    g = _problem()
+    kw = dict(flags=cg.FP64, maxeval=4 * 8000, nstart=8000, nbins=32)
+    ref = ctx.vegas(g, **kw)
+    before = torch.cuda.current_device()
+    side = torch.cuda.Stream(device=0)
+    r = cg.vegas_noalloc(g, device=0, stream=side.cuda_stream, **kw)
+    assert torch.cuda.current_device() == before
+    np.testing.assert_allclose(r.integral, ref.integral, rtol=1e-12)
+    with pytest.raises(cg.CubaGpuError) as ei:
+        cg.vegas_noalloc(g, device=torch.cuda.device_count(), **kw)  # no such device
+    assert ei.value.code == cg.EINVAL
+    assert torch.cuda.current_device() == before
+
+
+def test_noalloc_size_rule_at_its_boundary(ctx):
+    # 512 + R256(ndim (nbins+1) 8) + ndim nbins 8 <= CV_STATIC_SCRATCH_BYTES:
+    # 32 dimensions fit up to 254 bins
+    def need(ndim, nbins):
+        return 512 + -(-ndim * (nbins + 1) * 8 // 256) * 256 + ndim * nbins * 8
+    assert need(32, 254) <= 128 * 1024 < need(32, 255)
+    g = cg.genz(32, [cg.GAUSSIAN], 0.25, 0.5)
+    kw = dict(flags=cg.FP64, maxeval=2 * 4096, nstart=4096)
+    ref = ctx.vegas(g, nbins=254, **kw)
+    r = cg.vegas_noalloc(g, device=0, nbins=254, **kw)
+    np.testing.assert_allclose(r.integral, ref.integral, rtol=1e-12)
+    with pytest.raises(cg.CubaGpuError) as ei:
+        cg.vegas_noalloc(g, device=0, nbins=255, **kw)
+    assert ei.value.code == cg.ESCRATCH
