@@ -508,28 +508,28 @@ typedef struct {
  * exp(sum a_i x_i) where x_1 or x_2 crosses u_1 or u_2.  The oracle takes
  * that decision on its FP64 point.  An evaluation in a precision of p
  * significand bits (binary32: p = 24) forms the point from the FP64 edge
- * e_k and width w_k of its bin: rounding e_k (or e_k - w_k, or e_k - 2 w_k)
- * and w_k once each, one fused multiply-add for e_k + w_k frac, and the
- * comparison value u_i rounded once, moves x - u by at most
- *   2^-p (|e_k - 2 w_k| + 3 w_k + |x| + u) <= 7 * 2^-p * e_(k+1)
- * (x <= e_(k+1), u within the band of x), so a point whose FP64 coordinate
- * lies within 2^(3-p) e_(k+1) of u_i may be decided either way there, and
- * nowhere else.  Such a point is "ambiguous" when no other cut already
- * puts it outside; its alternative value is g = exp(sum a_i x_i).  The
- * boundary mass of a pass is B1_c = sum |J g| and B2_c = sum (J g)^2 over
- * its ambiguous points: a binary32 pass may differ from the oracle's by at
- * most that much in S1_c and S2_c (and in any histogram bin, by B2_0).
+ * e_k and width w_k of its bin with a few roundings of quantities no larger
+ * than a small multiple of the unit interval -- e_k shifted by a few widths
+ * or by a constant origin (1/2 to centre the coordinate) and w_k rounded
+ * once each, one fused multiply-add for the point, the comparison value
+ * rounded once -- which moves x - u by at most about 2^-p (2 + 9 w_k) <=
+ * 11 * 2^-p.  So a point whose FP64 coordinate lies within 2^(4-p) of u_i
+ * may be decided either way there, and nowhere else.  Such a point is
+ * "ambiguous" when no other cut already puts it outside; its alternative
+ * value is g = exp(sum a_i x_i).  The boundary mass of a pass is
+ * B1_c = sum |J g| and B2_c = sum (J g)^2 over its ambiguous points: a
+ * binary32 pass may differ from the oracle's by at most that much in S1_c
+ * and S2_c (and in any histogram bin, by B2_0).
  * Returns g for an ambiguous point, else 0.
  */
 static double disc_ambiguous(int ndim, const double *a, const double *u, const double *x,
-                             const int *kbin, const double *edges, int N, int band_bits)
+                             int band_bits)
 {
     if (band_bits <= 0)
         return 0.0;
+    const double band = ldexp(1.0, 4 - band_bits);
     int ncut = ndim < 2 ? ndim : 2, amb = 0;
     for (int i = 0; i < ncut; ++i) {
-        const double right = edges[(size_t)i * (N + 1) + kbin[i] + 1];
-        const double band = ldexp(right, 3 - band_bits);
         if (fabs(x[i] - u[i]) <= band)
             amb = 1;
         else if (x[i] > u[i])
@@ -574,8 +574,7 @@ static void *sample_range(void *arg)
             sum_add(&job->S2[c], Jf * Jf);
             sum_add(&job->A1[c], fabs(Jf));
             if (p->family[c] == OR_DISCONTINUOUS) {
-                double g = disc_ambiguous(ndim, p->a[c], p->u[c], x, kbin, job->edges, N,
-                                          p->band_bits);
+                double g = disc_ambiguous(ndim, p->a[c], p->u[c], x, p->band_bits);
                 if (g != 0.0) {
                     sum_add(&job->B1[c], fabs(J * g));
                     sum_add(&job->B2[c], (J * g) * (J * g));

@@ -159,8 +159,9 @@ def test_boundary_mass_counts_exactly_the_points_in_the_band(j0):
     p = _problem(ndim, [O.DISCONTINUOUS], a, u, nbins=N, bits=23)
     r = O.sample_bounds(p, O.grid_uniform(ndim, N), start, n)
     g = math.exp(float(a @ y[j0]))
-    # (no other point within 2^-21 e_(k+1) of either cut)
-    assert np.sum(np.abs(y[:, 0] - u[0]) <= 2.0 ** -21) == 1
+    # (no other point within the band, 2^-20, of either cut)
+    assert np.sum(np.abs(y[:, 0] - u[0]) <= 2.0 ** -20) == 1
+    assert np.all(np.abs(y[:, 1] - u[1]) > 2.0 ** -20)
     assert r.B1[0] == pytest.approx(g, rel=1e-15)
     assert r.B2[0] == pytest.approx(g * g, rel=1e-15)
     # the oracle's own decision is the FP64 one: x = u is inside
@@ -178,14 +179,13 @@ def test_boundary_mass_counts_exactly_the_points_in_the_band(j0):
     assert r3.B1[0] == 0.0
 
 
-def test_boundary_band_width_is_eight_binary32_units_of_the_right_edge():
-    # the band is |x - u| <= 2^-21 e_(k+1): a cut 0.9 band widths from the
-    # point keeps it ambiguous, 1.1 widths does not
+def test_boundary_band_width_is_sixteen_binary32_units():
+    # the band is |x - u| <= 2^-20 (16 units of 2^-24): a cut 0.9 band
+    # widths from the point keeps it ambiguous, 1.1 widths does not
     ndim, N, start, n, j0 = 2, 32, 1, 32, 9
     a = np.array([0.5, 0.5])
     y = _scipy_points(ndim, start, n)
-    k = int(y[j0, 0] * N)
-    band = 2.0 ** -21 * (k + 1) / N
+    band = 2.0 ** -20
     got = []
     for t in (0.9, 1.1, -0.9, -1.1):
         u = np.array([y[j0, 0] + t * band, 1.0])
@@ -213,8 +213,8 @@ def test_abs_sum_bounds_the_sum():
 
 def test_boundary_mass_is_small_and_scales_with_the_band():
     # on a random grid the ambiguous points are those within ~1e-6 of a
-    # cut: their mass is a small fraction of the pass, and it vanishes in
-    # FP64 (band_bits 53: a band of 2^-50)
+    # cut: their mass is a small fraction of the pass, and it shrinks with
+    # the band (band_bits 53: a band of 2^-49)
     a, u = [0.5, 0.5, 0.5], [0.3, 0.7, 0.5]
     e = _random_grid(3, 64, 2)
     n = 200000

@@ -13,9 +13,9 @@ does not vanish for an oscillatory integrand whose sum cancels:
   |H - Ho|   <= 1e-5 * max_k Ho[d, k] + B2[0]   per bin
 
 B1, B2 are the oracle's boundary mass: the discontinuous family's points
-whose FP64 coordinate lies within 2^-21 e_(k+1) of a cut, which a binary32
-evaluation of the point may put on either side (zero for every other
-family).  The histogram bound is looser than the sums' because each bin is a
+whose FP64 coordinate lies within 2^-20 (sixteen binary32 units at 1) of a
+cut, which a binary32 evaluation of the point may put on either side (zero
+for every other family).  The histogram bound is looser than the sums' because each bin is a
 short FP32 running sum in shared memory before it reaches FP64.
 
 The iteration variance var = (S2/n - (S1/n)^2)/(n-1) follows from the two
