@@ -40,8 +40,13 @@ if ROOT not in sys.path:
 
 METRIC = "Vegas samples/s"
 UNIT = "samples/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+
+
+def sm_count(device: int = 0) -> int:
+    """Streaming multiprocessors of the device, queried at run time."""
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
 
 
 def _workload_name(p) -> str:
@@ -53,10 +58,13 @@ def _workload_name(p) -> str:
 # ------------------------------------------------------------------ FLOP count
 def alg_flops_per_sample(ndim: int, families) -> int:
     """Algorithmic FP32 FLOPs of one sample of the fused pass (FMA = 2; the
-    special-function unit's exp/cos/rcp are not FP32-pipe FLOPs):
-    map 5/dim (frac, x FMA, Jacobian 2 mul); per component J*f, (J f)^2 and
-    two Kahan additions (4 each) = 10; the histogram value f0^2 = 1; and the
-    family's own arithmetic."""
+    special-function unit's exp/cos/rcp are not FP32-pipe FLOPs): the map
+    3/dim (the point's FMA and the Jacobian's multiply); per component J*f,
+    (J f)^2 and two Kahan additions (4 each) = 10; the histogram, f0^2 and
+    one addition per axis = ndim + 1; and the family's own arithmetic.  The
+    count is of the method's work, not of the instructions a kernel issues
+    (the FP32 kernel adds Newton steps and compensation terms for accuracy,
+    which count against it)."""
     per = {
         0: 2 * ndim + 2,                      # phase FMAs, wrap, scale
         1: 4 * ndim,                          # sub, FMA, mul per dim
@@ -66,15 +74,15 @@ def alg_flops_per_sample(ndim: int, families) -> int:
         5: 2 * ndim + 1,
         6: 0,
     }
-    return 5 * ndim + sum(per[f] + 10 for f in families) + 1
+    return 3 * ndim + sum(per[f] + 10 for f in families) + ndim + 1
 
 
 def _ipow_muls(e: int) -> int:
     return max(0, e.bit_length() - 1) + max(0, bin(e).count("1") - 1)
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz: float, sms: int) -> float:
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 def measured_peaks() -> dict:
@@ -87,15 +95,18 @@ def measured_peaks() -> dict:
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi clock / throttle sampling every 20 ms, started before the
+    timed region; only the samples taken inside the region (host clock,
+    between mark_start and mark_end) are reported, or, if the region was
+    shorter than the sampling period, the one sample nearest to it."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-               "-lms", "200"]
+               "-lms", "20"]
         uuid = _gpu_uuid(device_index)
         if uuid:
             cmd += ["-i", uuid]
@@ -103,6 +114,15 @@ class ClockSampler:
             self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        self.t0 = self.t1 = None
+        time.sleep(0.3)  # (the sampler's first rows)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+        time.sleep(0.05)
 
     def stop(self) -> dict:
         if self.p is not None:
@@ -117,19 +137,27 @@ class ClockSampler:
         self.f.close()
         os.unlink(self.f.name)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        sm, mx, reasons = [], [], set()
+        samples = []
         for r in rows:
             try:
-                sm.append(float(r[0]))
-                mx.append(float(r[1]))
+                ts = time.mktime(time.strptime(r[0].strip().split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + r[0].strip().split(".")[1]) if "." in r[0] else 0.0
+                samples.append((ts, float(r[1]), float(r[2]),
+                                {nm for nm, v in zip(names, r[4:8]) if v.strip().lower() == "active"}))
             except (ValueError, IndexError):
                 continue
-            for nm, v in zip(names, r[3:7]):
-                if v.strip().lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [s for s in samples if self.t0 is not None and self.t0 <= s[0] <= (self.t1 or s[0])]
+        basis = "inside the timed region"
+        if not inside and samples and self.t0 is not None:
+            mid = 0.5 * (self.t0 + (self.t1 or self.t0))
+            inside = [min(samples, key=lambda s: abs(s[0] - mid))]
+            basis = "nearest sample to a timed region shorter than the 20 ms period"
+        reasons = set()
+        for s in inside:
+            reasons |= s[3]
+        return {"sm_mhz": statistics.median(s[1] for s in inside) if inside else None,
+                "sm_max_mhz": max(s[2] for s in inside) if inside else None,
+                "reasons": sorted(reasons), "samples": len(inside), "period_ms": 20, "basis": basis}
 
 
 def _gpu_uuid(idx: int):
@@ -254,10 +282,150 @@ def oracle_more_rates(p, W, threads: int) -> dict:
     out["batch4096"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                         "sample": f"the first 64 of the 4096 integrals, one pass of min(n, 1e6) points each "
                                   f"({total} points, {dt:.1f} s)"}
-    rate, total, dt = oracle_pass_rate(W.large30d(), 10 ** 7, threads)
+    rate, total, dt = oracle_pass_rate(W.large30d(), 10 ** 8, threads)
     out["large30d"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                       "sample": f"both integrals, one pass of 1e7 points each ({total} points, {dt:.1f} s)"}
+                       "sample": f"both integrals, one pass of 1e8 points each (one of the 15 iterations the "
+                                 f"oracle's share of the workload takes; {total} points, {dt:.1f} s)"}
     return out
+
+
+def _z(I: float, E: float, exact: float) -> float:
+    """Distance of an estimate from the exact value in units of its error."""
+    if E > 0:
+        return abs(I - exact) / E
+    return 0.0 if I == exact else float("inf")
+
+
+def accuracy_leg(line: dict, W, threads: int) -> dict:
+    """Every result's distance from its Genz closed form in units of its own
+    error estimate, z = |I - exact| / error, per leg (max and share within
+    3), and the largest difference from the oracle's own Vegas run of the
+    same integrals on seeded subsets.  Part of the CPU-baseline leg: the
+    closed forms and the runs are the oracle's."""
+    import numpy as np
+
+    import oracle as O
+    out = {}
+    p = W.genz8d4c()
+    ex = [O.genz_exact(f, np.asarray(p.a[c]), np.asarray(p.u[c])) for c, f in enumerate(p.families)]
+    r = line["result"]
+    out["headline"] = {"z": [_z(r["integral"][c], r["error"][c], ex[c]) for c in range(p.ncomp)]}
+    out["plain_fp64"] = {"z": [_z(r["plain_fp64_integral"][c], r["plain_fp64_error"][c], ex[c])
+                               for c in range(p.ncomp)]}
+    if "materialised" in line:
+        res = line["materialised"].pop("_results")
+        out["materialised"] = {"z": [_z(I, E, ex[c]) for c, (I, E) in enumerate(res)]}
+    if "generators" in line:
+        gen = line["generators"]
+        out["generators"] = {k: {"z": [_z(gen[k]["integral_mean"][c], gen[k]["vegas_error"][c], ex[c])
+                                       for c in range(p.ncomp)]} for k in ("scrambled", "pseudo") if k in gen}
+    if "gaussian3d" in line:
+        g3 = line["gaussian3d"]
+        out["gaussian3d"] = {"z": _z(g3["integral"], g3["error"], g3["exact"])}
+    if "suave" in line:
+        sv = line["suave"]
+        P = SUAVE_PROBLEM
+        exs = O.genz_exact(3, np.array(P["a"]), np.array(P["u"]))
+        out["suave"] = {"z": _z(sv["integral"], sv["error"], exs)}
+    if "large30d" in line:
+        zl = []
+        for item in line["large30d"]["results"]:
+            q = item.pop("_p")
+            zl.append(_z(item["integral"], item["error"], O.genz_exact(q.families[0], q.a[0], q.u[0])))
+        out["large30d"] = {"z": zl}
+    if "batch4096" in line:
+        b = line["batch4096"]
+        probs, res = b.pop("_problems"), b.pop("_results")
+        exact = [O.genz_exact(q.families[0], q.a[0], q.u[0]) for q in probs]
+        zs = np.array([_z(I, E, x) for (I, E), x in zip(res, exact)])
+        plain = b["plain_fp64_subset"].pop("_results")
+        zp = [_z(I, E, exact[i]) for i, (I, E) in plain]
+        # the oracle's own Vegas run of the 8 integrals with the fewest points
+        idx = sorted(range(len(probs)), key=lambda i: probs[i].maxeval)[:8]
+        dz = []
+        for i in idx:
+            q = probs[i]
+            o = O.vegas(O.Problem(q.ndim, list(q.families), np.asarray(q.a), np.asarray(q.u), nbins=q.nbins,
+                                  bits=23), maxeval=q.maxeval, nstart=q.nstart, nthreads=threads)
+            dz.append(abs(res[i][0] - o.integral[0]) / max(res[i][1], o.error[0]))
+        out["batch4096"] = {"integrals": len(zs), "z_max": float(zs.max()), "within_3": float((zs <= 3).mean()),
+                            "plain_fp64_subset_z_max": max(zp),
+                            "oracle_subset": {"integrals": len(idx), "max_diff_in_sigma": max(dz)}}
+    if "serve" in line:
+        raw = line["serve"].pop("_results")
+        zs, small = [], []
+        for q, rc, neval in raw:
+            for c, (I, E) in enumerate(rc):
+                x = O.genz_exact(q.families[c], np.asarray(q.a[c]), np.asarray(q.u[c]))
+                # the mixed-precision bound 1e-6 int |f| (|f| <= 1 for the oscillatory family)
+                floor = 1e-6 * (1.0 if q.families[c] == 0 else abs(x))
+                zs.append(abs(I - x) / (E + floor / 3) if E + floor > 0 else 0.0)
+            if len(small) < 5 and neval <= 3 * 10 ** 5:
+                small.append((q, rc))
+        zs = np.array(zs)
+        dz = []
+        for q, rc in small:
+            # the same request, goal and schedule (it stops where the GPU run stopped)
+            o = O.vegas(O.Problem(q.ndim, list(q.families), np.asarray(q.a), np.asarray(q.u), nbins=q.nbins, bits=23),
+                        epsrel=q.epsrel, maxeval=q.maxeval, nstart=q.nstart, nincrease=q.nincrease,
+                        nthreads=threads)
+            dz.append(max(abs(I - o.integral[c]) / max(E, o.error[c]) for c, (I, E) in enumerate(rc)))
+        out["serve"] = {"components": len(zs), "z_max": float(zs.max()), "within_3": float((zs <= 3).mean()),
+                        "basis": "z with the FP32 floor 1e-6 int|f| added to 3 sigma; the grid follows component 0, "
+                                 "so later components of a request can be sampled badly and their error "
+                                 "underestimated by Vegas itself",
+                        "oracle_subset": {"requests": len(dz), "max_diff_in_sigma": max(dz) if dz else None,
+                                          "basis": "the first requests the GPU finished within 3e5 points, "
+                                                   "rerun by the oracle with the same goal and schedule"}}
+    return out
+
+
+def legs_summary(line: dict) -> dict:
+    """A short form of every leg, printed last on the line (so that a record
+    that keeps only the end of the output still holds every leg)."""
+    def g(v, nd=4):
+        return float(f"{v:.{nd}g}") if isinstance(v, (int, float)) and v is not None else v
+    acc = line.get("accuracy", {})
+    out = {"headline": {"Gsps": g(line["value"] / 1e9), "e2e_Gsps": g(line["e2e"]["value"] / 1e9),
+                        "frac": g(line["roofline"]["frac"], 3), "kernel_us": g(1e3 * line["roofline"]["kernel_ms"]),
+                        "z": [g(z, 2) for z in acc.get("headline", {}).get("z", [])]},
+           "plain_fp64": {"Gsps": g(line["plain_fp64"]["value"] / 1e9),
+                          "z": [g(z, 2) for z in acc.get("plain_fp64", {}).get("z", [])]}}
+    if "batch4096" in line:
+        b, a = line["batch4096"], acc.get("batch4096", {})
+        out["batch4096"] = {"Gsps": g(b["value"] / 1e9), "frac": g(b["roofline"]["frac"], 3),
+                            "plain_fp64_Gsps": g(b["plain_fp64_subset"]["value"] / 1e9),
+                            "z_max": g(a.get("z_max"), 3), "within_3": g(a.get("within_3"), 4),
+                            "oracle_dz": g(a.get("oracle_subset", {}).get("max_diff_in_sigma"), 2)}
+    if "large30d" in line:
+        out["large30d"] = {"Gsps": g(line["large30d"]["value"] / 1e9),
+                           "z": [g(z, 2) for z in acc.get("large30d", {}).get("z", [])]}
+    if "materialised" in line:
+        m = line["materialised"]
+        out["materialised"] = {"Gsps": g(m["value"] / 1e9), "hbm_frac": g(m["hbm_frac_all_kernels"], 3),
+                               "z": [g(z, 2) for z in acc.get("materialised", {}).get("z", [])]}
+    if "serve" in line:
+        s, a = line["serve"], acc.get("serve", {})
+        out["serve"] = {"req_s": g(s["requests_per_s"]), "p50_ms": g(s["p50_ms"]), "p99_ms": g(s["p99_ms"]),
+                        "Gsps": g(s["throughput"]["value"] / 1e9), "fifo_fp64_p50_ms": g(s["plain_fp64_fifo"]["p50_ms"]),
+                        "z_max": g(a.get("z_max"), 3), "within_3": g(a.get("within_3"), 4)}
+    if "gaussian3d" in line:
+        out["gaussian3d"] = {"us_it": g(line["gaussian3d"]["graph_us_per_iteration"]),
+                             "z": g(acc.get("gaussian3d", {}).get("z"), 2)}
+    if "suave" in line:
+        out["suave"] = {"Gsps": g(line["suave"]["value"] / 1e9), "z": g(acc.get("suave", {}).get("z"), 2)}
+    if "cpu_baseline" in line:
+        out["oracle_Msps"] = g(line["cpu_baseline"]["value"] / 1e6)
+    return out
+
+
+def _strip_private(d):
+    """Drop the raw results kept for the accuracy leg (keys starting with _)."""
+    if isinstance(d, dict):
+        return {k: _strip_private(v) for k, v in d.items() if not k.startswith("_")}
+    if isinstance(d, list):
+        return [_strip_private(v) for v in d]
+    return d
 
 
 # ------------------------------------------------------------------ arms
@@ -329,13 +497,14 @@ def run_ours(args):
         integ.reset()
         integ.run()
 
-    # ---- device-timed steps
+    # ---- device-timed steps (the clock sampler runs from before the warm-up)
+    clocks = ClockSampler(local)
     for _ in range(args.warmup):
         flush.fill_(1)
         step()
     barrier()
-    clocks = ClockSampler(local)
     events = []
+    clocks.mark_start()
     t0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
@@ -346,6 +515,7 @@ def run_ours(args):
         events.append((s, e))
     barrier()
     wall = time.perf_counter() - t0
+    clocks.mark_end()
     clk = clocks.stop()
     dev_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in events), device="cuda")
     res = integ.result()
@@ -362,18 +532,19 @@ def run_ours(args):
     ctx.stage_grid(p.ndim, p.nbins, flags, edges, table)
 
     def time_kernel(kflags):
+        # the sampling launch alone: the library records CUDA events on its
+        # stream immediately around each sampling launch (cv_kernel_timer),
+        # so the pass's histogram-partials launch after it is not counted
         for _ in range(3):
             ctx.sample_staged(g, p.nbins, table, 1, p.nstart, kflags, S1, S2, H)
         torch.cuda.synchronize()
-        kev = []
+        ctx.kernel_timer(True)
         for _ in range(10):
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record()
             ctx.sample_staged(g, p.nbins, table, 1, p.nstart, kflags, S1, S2, H)
-            e.record()
-            kev.append((s, e))
-        torch.cuda.synchronize()
-        return statistics.mean(s.elapsed_time(e) for s, e in kev)
+        ctx.kernel_timer(False)
+        times = ctx.kernel_times()
+        assert len(times) == 10, times
+        return statistics.mean(times)
 
     k_ms = time_kernel(flags)
     k_ms_generic = time_kernel(0)
@@ -382,18 +553,19 @@ def run_ours(args):
     achieved = flops / (k_ms / 1e3) / 1e12
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(sm_max)
+    sms = sm_count(local)
+    peak = fp32_peak_tflops(sm_max, sms)
     prof = "sampling_specialised_genz8d4c.md" if jit_compiled else "k_sample_generic_genz8d4c.md"
     traffic = _profile_traffic(prof)
     # the bound this kernel actually meets: instruction issue (one warp
     # instruction per cycle per SM sub-partition), with the warp instructions
     # of one launch from the committed ncu summary
     inst = _profile_value(prof, "warp instructions")
-    issue_peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9
+    issue_peak = sms * 4 * sm_max * 1e6 / 1e9
     issue = None if inst is None else {
         "warp_instructions_per_launch": inst, "achieved": inst / (k_ms / 1e3) / 1e9, "peak": issue_peak,
         "unit": "G warp instructions/s", "frac": inst / (k_ms / 1e3) / 1e9 / issue_peak,
-        "peak_basis": f"{SM_COUNT} SMs x 4 schedulers x 1 instruction per cycle x {sm_max:.0f} MHz"}
+        "peak_basis": f"{sms} SMs x 4 schedulers x 1 instruction per cycle x {sm_max:.0f} MHz"}
 
     # the FP32 pipe's measured rate (FMA chains), beside the nominal peak
     fma_tflops, fma_ms = ctx.fp32_fma_rate()
@@ -406,12 +578,18 @@ def run_ours(args):
     ctx.vegas(g, flags=flags, maxeval=p.maxeval, nstart=p.nstart, nincrease=p.nincrease, nbins=p.nbins)
     barrier()
     e2e_t = []
+    ctx.kernel_timer(True)
     for _ in range(args.steps):
         t = time.perf_counter()
         ctx.vegas(g, flags=flags, maxeval=p.maxeval, nstart=p.nstart, nincrease=p.nincrease,
                   nbins=p.nbins)
         e2e_t.append(time.perf_counter() - t)
+    ctx.kernel_timer(False)
     e2e_value = world * samples_per_step / statistics.mean(e2e_t)
+    # the same sampling kernel inside those runs (cv_vegas enqueues its
+    # iterations directly, so each launch is timed): the sustained figure
+    in_run = ctx.kernel_times()
+    k_ms_in_run = statistics.mean(in_run) if in_run else None
 
     # ---- the plain FP64 one-launch-per-iteration comparator
     plain_steps = max(1, min(2, args.steps))
@@ -439,10 +617,11 @@ def run_ours(args):
                      "kernel": f"sampling kernel, ndim {p.ndim}, FP32, specialised at run time"
                                if jit_compiled else f"k_sample<{p.ndim},float>",
                      "kernel_ms": k_ms, "kernel_ms_generic": k_ms_generic,
+                     "kernel_ms_in_vegas_runs": k_ms_in_run, "launches_in_vegas_runs": len(in_run),
                      "jit": {"available": jit_available, "compiled": jit_compiled},
                      "flops_per_sample": alg_flops_per_sample(p.ndim, p.families),
                      "issue": issue, "fma_measured": fma,
-                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                    f"{sm_max:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"},
         "plain_fp64": {"value": world * samples_per_step / plain_s, "unit": UNIT,
                        "ms_per_step": 1e3 * plain_s,
@@ -477,7 +656,10 @@ def run_ours(args):
         for k in ("batch4096", "large30d"):
             if k in line:
                 line[k]["cpu_baseline"] = more[k]
+        line["accuracy"] = accuracy_leg(line, W, threads)
     if rank == 0:
+        line = _strip_private(line)
+        line["legs"] = legs_summary(line)  # (last: kept by a tail of the output)
         print(json.dumps(line), flush=True)
     integ.close()
     ctx.close()
@@ -520,22 +702,34 @@ def measure_batch(ctx, cg, W, warmup: int, steps: int, subset: int = 32) -> dict
     idx = list(range(0, len(probs), len(probs) // subset))[:subset]
     sub_samples = sum(probs[i].maxeval for i in idx)
     t = time.perf_counter()
-    dev = []
+    dev, plain = [], []
     for i in idx:
         p = probs[i]
         rp = ctx.vegas(cg.genz(p.ndim, p.families, p.a, p.u), flags=cg.FP64 | cg.PLAIN,
                        maxeval=p.maxeval, nstart=p.nstart, nbins=p.nbins)
         r = res[i]
         dev.append(abs(r.integral[0] - rp.integral[0]) / max(rp.error[0], 1e-300))
+        plain.append((rp.integral[0], rp.error[0]))
     plain_s = time.perf_counter() - t
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    flops = sum(p.maxeval * alg_flops_per_sample(p.ndim, p.families) for p in probs)
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = fp32_peak_tflops(sm_max, sm_count(torch.cuda.current_device()))
     return {"workload": "batch4096: 4096 integrals, ndim U{2..16}, family U{0..5}, n/iter "
                         "log-uniform 1e4..1e7, 10 iterations, 64 bins, FP32 eval / FP64 reduce",
             "value": samples / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "basis": "algorithmic FP32 FLOPs of every integral's samples over the device time "
+                                  "of the whole batched run (sampling, refinement and combination)"},
+            "_results": [(r.integral[0], r.error[0]) for r in res], "_problems": probs,
             "samples_per_step": samples, "gpu_launches_per_step": launches,
             "autotune_s": tune_s, "tile_points_by_iteration_size": tiles,
             "plain_fp64_subset": {"integrals": len(idx), "value": sub_samples / plain_s,
                                   "unit": UNIT,
-                                  "max_abs_diff_in_sigma": max(dev)}}
+                                  "max_abs_diff_in_sigma": max(dev),
+                                  "_results": [(i, plain[k]) for k, i in enumerate(idx)]}}
 
 
 def measure_materialised(ctx, cg, W) -> dict:
@@ -562,7 +756,8 @@ def measure_materialised(ctx, cg, W) -> dict:
             "value": rate, "unit": UNIT, "ms_per_step": 1e3 * dt,
             "library_bytes_per_sample": lib_bytes, "all_bytes_per_sample": all_bytes,
             "hbm_gbs_all_kernels": rate * all_bytes / 1e9,
-            "integral": list(r.integral)}
+            "hbm_frac_all_kernels": rate * all_bytes / 1e9 / float(measured_peaks().get("hbm_gbs", 6684.8)),
+            "integral": list(r.integral), "_results": list(zip(r.integral, r.error))}
 
 
 def measure_generators(ctx, cg, W, replicates: int = 8) -> dict:
@@ -604,47 +799,56 @@ def measure_generators(ctx, cg, W, replicates: int = 8) -> dict:
 
 
 def measure_cost_sweep(ctx, cg, W, threads: int, delays=(0, 64, 256, 1024, 4096),
-                       cpu_seconds: float = 1.0) -> dict:
+                       cpu_seconds: float = 0.5) -> dict:
     """Integrand cost against speed-up, the GPU counterpart of the paper's
     calibrated-delay experiment (Sect. 4.1, Fig. 1): the Gaussian component of
     genz8d4c with `delay` extra dependent multiply-adds per evaluation (the
-    value is unchanged).  Per delay: the run-time specialised GPU path on
-    5 x 1e7 points (device-timed) and the oracle on the host's cores on a
-    bounded sample (part of the CPU-baseline leg)."""
+    value is unchanged).  Both sides do the same work, one sampling pass on
+    the uniform grid: the run-time specialised GPU pass over 1e7 points
+    (device-timed) and the oracle on a bounded sample on 1, 4 and all host
+    threads (the core-count axis of the paper's figure; part of the
+    CPU-baseline leg)."""
     import numpy as np
     import torch
 
     import oracle as O
     p = W.genz8d4c()
     a, u = np.asarray(p.a)[3:4], np.asarray(p.u)[3:4]
-    out = {"workload": "genz8d4c's Gaussian component (ndim 8, 128 bins) with `delay` extra dependent "
-                       "multiply-adds per evaluation; GPU 5 x 1e7 points, FP32, specialised; oracle FP64 "
-                       f"on {threads} host threads", "points": []}
+    counts = sorted({1, min(4, threads), threads})
+    out = {"workload": "one sampling pass of genz8d4c's Gaussian component (ndim 8, 128 bins, uniform grid) with "
+                       "`delay` extra dependent multiply-adds per evaluation: GPU 1e7 points FP32 specialised, "
+                       f"oracle FP64 on {counts} host threads", "points": []}
+    edges = O.grid_uniform(p.ndim, p.nbins)
+    e = torch.tensor(edges, dtype=torch.float64, device="cuda")
+    S1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    S2 = torch.zeros_like(S1)
+    H = torch.zeros((p.ndim, p.nbins), dtype=torch.float64, device="cuda")
     for dl in delays:
         g = cg.genz(p.ndim, [3], a, u, delay=dl)
-        I = ctx.integral(cg.spec(g, nbins=p.nbins, flags=cg.JIT, maxeval=5 * p.nstart, nstart=p.nstart))
-        I.reset()
-        I.run()
+        for _ in range(3):
+            ctx.sample(g, p.nbins, e, 1, p.nstart, cg.JIT, S1, S2, H)
         torch.cuda.synchronize()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
-        I.reset()
-        I.run()
+        for _ in range(5):
+            ctx.sample(g, p.nbins, e, 1, p.nstart, cg.JIT, S1, S2, H)
         s1.record()
         torch.cuda.synchronize()
         gpu = 5 * p.nstart / (s0.elapsed_time(s1) * 1e-3)
-        I.close()
         prob = O.Problem(p.ndim, [3], a, u, nbins=p.nbins, bits=23, delay=dl)
-        e = O.grid_uniform(p.ndim, p.nbins)
-        n = 4096 * threads
-        t = time.perf_counter()
-        O.sample(prob, e, 1, n, nthreads=threads)
-        dt = time.perf_counter() - t
-        n = max(n, int(n * cpu_seconds / max(dt, 1e-3)))
-        t = time.perf_counter()
-        O.sample(prob, e, 1, n, nthreads=threads)
-        cpu = n / (time.perf_counter() - t)
-        out["points"].append({"delay": dl, "gpu": gpu, "cpu": cpu, "speedup": gpu / cpu, "unit": UNIT})
+        cpu = {}
+        for th in counts:
+            n = 2048 * th
+            t = time.perf_counter()
+            O.sample(prob, edges, 1, n, nthreads=th)
+            dt = time.perf_counter() - t
+            n = max(n, int(n * cpu_seconds / max(dt, 1e-3)))
+            t = time.perf_counter()
+            O.sample(prob, edges, 1, n, nthreads=th)
+            cpu[th] = n / (time.perf_counter() - t)
+        out["points"].append({"delay": dl, "gpu": gpu, "unit": UNIT,
+                              "cpu": {str(th): v for th, v in cpu.items()},
+                              "speedup": {str(th): gpu / v for th, v in cpu.items()}})
     return out
 
 
@@ -741,7 +945,7 @@ def measure_large(ctx, cg, W, steps: int = 1) -> dict:
             total_ms += s0.elapsed_time(s1)
             total += p.maxeval
         r = I.result()
-        res.append({"family": p.families[0], "integral": r.integral[0], "error": r.error[0]})
+        res.append({"family": p.families[0], "integral": r.integral[0], "error": r.error[0], "_p": p})
         I.close()
     out.update({"value": total / (total_ms / 1e3), "unit": UNIT, "ms_per_step": total_ms / steps,
                 "samples_per_step": total // steps, "results": res})
@@ -776,6 +980,7 @@ def measure_serve(ctx, cg, W, duration: float = 1.0, rate: float = 2000.0,
     S.stop()
     samples = sum(r.neval for r in res)
     ok = sum(1 for r in res if r.fail == 0)
+    raw = [(p, [(r.integral[c], r.error[c]) for c in range(p.ncomp)], r.neval) for (_, p), r in zip(reqs, res)]
     # the same first requests served alone, at their arrival times: the
     # latency to compare with the plain FP64 server below
     S = ctx.server(hbm_budget_bytes=8 << 30)
@@ -816,7 +1021,8 @@ def measure_serve(ctx, cg, W, duration: float = 1.0, rate: float = 2000.0,
             "plain_fp64_fifo": {"requests": len(service), "p50_ms": q(0.5), "p99_ms": q(0.99),
                                 "throughput": {"value": sum(r.neval for r in res[:plain_subset]) / sum(service),
                                                "unit": UNIT},
-                                "mean_service_ms": 1e3 * sum(service) / len(service)}}
+                                "mean_service_ms": 1e3 * sum(service) / len(service)},
+            "_results": raw}
 
 
 def main():

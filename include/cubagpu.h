@@ -154,6 +154,24 @@ const char *cv_last_error(const cv_ctx *ctx);
 /* Wait for all work enqueued by the context. */
 int cv_synchronize(cv_ctx *ctx);
 
+/* Device time of individual sampling-kernel launches (the kernel of the
+ * sampling pass, Sect. 3.1's DoSample, without the launches around it).
+ * cv_kernel_timer(ctx, 1) clears the record and starts timing: every
+ * sampling launch the context then makes on its stream outside stream
+ * capture (cv_sample, cv_sample_staged, the iterations of cv_vegas and of
+ * a CV_PLAIN integral) gets a CUDA event recorded on that stream immediately
+ * before and after it, for the first CV_TIMER_CAP launches; later launches
+ * and launches inside a graph (an integral's captured iterations) are not
+ * timed.  cv_kernel_timer(ctx, 0) stops timing and keeps the record.  The
+ * first enable creates 2 * CV_TIMER_CAP events (released by cv_destroy).
+ * cv_kernel_times waits for the recorded launches and writes the first
+ * min(cap, count) durations, in milliseconds, to the host array ms[cap];
+ * *count receives the number recorded.  The events add one event record
+ * before and after each timed launch on the stream. */
+#define CV_TIMER_CAP 256
+int cv_kernel_timer(cv_ctx *ctx, int enable);
+int cv_kernel_times(cv_ctx *ctx, float *ms, int cap, int *count);
+
 /* ------------------------------------------------ DoSample building blocks */
 
 /* Sobol coordinates (Sect. 2: the master alone generates samples, each
@@ -184,11 +202,12 @@ int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins,
  * the grid once into a table the sampling kernel copies as it is, instead
  * of every CTA converting the FP64 edges (FP64 arithmetic is slow on this
  * GPU).  cv_stage_grid writes that table for edges_dev:
- *   table_dev[d*nbins + s] = {e_k - w_k, w_k (times nbins when nbins is a
- *   power of two >= 32 and flags has no CV_PSEUDO)}, float2 (8 bytes),
+ *   table_dev[d*nbins + s] = {e_k - c w_k - 1/2, m w_k}, float2 (8 bytes),
  *   w_k = e_(k+1) - e_k computed in FP64 and each entry rounded once to
- *   FP32, s = the kernel's slot of bin k (a bit permutation of k for those
- *   power-of-two bin counts, k otherwise);
+ *   FP32; when nbins = 2^L >= 32 and flags has no CV_PSEUDO, m = nbins and
+ *   c = 2^max(0, L-6), and s is the kernel's slot of bin k (a bit
+ *   permutation of k); otherwise m = c = 1 and s = k (the FP32 kernels
+ *   map to the centred coordinate x - 1/2);
  * table_dev holds ndim*nbins float2, 8-byte aligned, caller-owned; flags
  * are the sampling flags the table is for (the generator decides the
  * layout).  cv_sample_staged is cv_sample (FP32 only: CV_FP64 is refused)

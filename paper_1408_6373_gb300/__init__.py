@@ -22,6 +22,7 @@ MAX_COMP = 4
 MIN_BINS = 2
 MAX_BINS = 256
 INDEX_LIMIT = 1 << 52
+KERNEL_TIMER_CAP = 256
 
 OSCILLATORY, PRODUCT_PEAK, CORNER_PEAK, GAUSSIAN, C0, DISCONTINUOUS, CONST = range(7)
 FAMILIES = {"oscillatory": 0, "product_peak": 1, "corner_peak": 2, "gaussian": 3,
@@ -170,6 +171,8 @@ _SIGNATURES = {
     "cv_strerror": (ctypes.c_char_p, [_i]),
     "cv_last_error": (ctypes.c_char_p, [_vp]),
     "cv_synchronize": (_i, [_vp]),
+    "cv_kernel_timer": (_i, [_vp, _i]),
+    "cv_kernel_times": (_i, [_vp, _vp, _i, _P(_i)]),
     "cv_sobol": (_i, [_vp, _i, _u64, _i64, _i, _vp]),
     "cv_points": (_i, [_vp, _i, _u64, _i64, _i, _i, _u64, _vp]),
     "cv_suave": (_i, [_vp, _P(Genz), _i, _i, _u64, ctypes.c_double, ctypes.c_double, _i64, _i64, _i64,
@@ -303,6 +306,18 @@ class Context:
 
     def synchronize(self):
         self._check(self._lib.cv_synchronize(self._h), "cv_synchronize")
+
+    def kernel_timer(self, enable: bool):
+        """Start (clearing the record) or stop timing the sampling launches."""
+        self._check(self._lib.cv_kernel_timer(self._h, 1 if enable else 0), "cv_kernel_timer")
+
+    def kernel_times(self) -> list:
+        """Device milliseconds of each timed sampling launch, in order."""
+        buf = (ctypes.c_float * KERNEL_TIMER_CAP)()
+        n = ctypes.c_int(0)
+        self._check(self._lib.cv_kernel_times(self._h, buf, KERNEL_TIMER_CAP, ctypes.byref(n)),
+                    "cv_kernel_times")
+        return [float(buf[k]) for k in range(min(n.value, KERNEL_TIMER_CAP))]
 
     # ---------------------------------------------------- building blocks
     def sobol(self, ndim: int, start: int, n: int, bits: int, out):

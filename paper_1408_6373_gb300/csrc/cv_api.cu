@@ -98,7 +98,15 @@ struct cv_ctx {
     // (no allocation, and no free with its device synchronisation, per call)
     void *vegas_mem = nullptr;
     size_t vegas_cap = 0;
+    // per-block partials of standalone deterministic passes (cv_sample),
+    // grown on demand: room for parts_G blocks of the largest problem
+    void *parts_mem = nullptr;
+    size_t parts_cap = 0;
+    int parts_G = 0;
     int *pinned = nullptr;  // [0] = 1 (pass_active), [1] = stopped read back
+    // cv_kernel_timer: event pairs around the sampling launches
+    cudaEvent_t tev[2 * CV_TIMER_CAP] = {};
+    int timer_on = 0, timer_n = 0;
 };
 
 static void integral_free(struct cv_integral *I);
@@ -205,11 +213,63 @@ extern "C" void cv_destroy(cv_ctx *ctx)
         if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    for (cudaEvent_t ev : ctx->tev)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->mat_mem) cudaFree(ctx->mat_mem);
     if (ctx->vegas_mem) cudaFree(ctx->vegas_mem);
+    if (ctx->parts_mem) cudaFree(ctx->parts_mem);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+}
+
+extern "C" int cv_kernel_timer(cv_ctx *ctx, int enable)
+{
+    if (!ctx) return CV_EINVAL;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (enable && !ctx->tev[0]) {
+        for (cudaEvent_t &ev : ctx->tev) CV_CUDA(ctx, cudaEventCreate(&ev));
+    }
+    ctx->timer_on = enable ? 1 : 0;
+    if (enable) ctx->timer_n = 0;
+    return CV_OK;
+}
+
+extern "C" int cv_kernel_times(cv_ctx *ctx, float *ms, int cap, int *count)
+{
+    if (!ctx || !count || cap < 0 || (cap > 0 && !ms)) return CV_EINVAL;
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int n = ctx->timer_n < cap ? ctx->timer_n : cap;
+    for (int k = 0; k < n; ++k) {
+        CV_CUDA(ctx, cudaEventSynchronize(ctx->tev[2 * k + 1]));
+        CV_CUDA(ctx, cudaEventElapsedTime(&ms[k], ctx->tev[2 * k], ctx->tev[2 * k + 1]));
+    }
+    *count = ctx->timer_n;
+    return CV_OK;
+}
+
+// The event pair for the next sampling launch on ctx->stream: -1 when the
+// timer is off or full, or the stream is being captured into a graph.
+static int timer_begin(cv_ctx *ctx)
+{
+    if (!ctx->timer_on || ctx->timer_n >= CV_TIMER_CAP) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (cudaEventRecord(ctx->tev[2 * ctx->timer_n], ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return ctx->timer_n;
+}
+
+static void timer_end(cv_ctx *ctx, int k)
+{
+    if (k < 0) return;
+    if (cudaEventRecord(ctx->tev[2 * k + 1], ctx->stream) == cudaSuccess) ctx->timer_n = k + 1;
+    else cudaGetLastError();
 }
 
 extern "C" int cv_synchronize(cv_ctx *ctx)
@@ -313,37 +373,78 @@ static int check_fp32_range(cv_ctx *ctx, const cv_genz *g)
     return CV_OK;
 }
 
+namespace cv {
+// The per-component parameters of GenzParams (their forms are listed with
+// the struct): FP64 for x in [0, 1]; FP32 for the centred coordinate
+// z = x - 1/2 with base-2 exponents, constants that the evaluation adds to
+// a small sum split into a binary32 pair q0 + q1, rounded once each.
 template <typename Real>
-static void fill_params(const cv_genz *g, GenzParams<Real> *p)
+void fill_genz_params(const cv_genz *g, GenzParams<Real> *p)
 {
     memset(p, 0, sizeof(*p));
     p->ndim = g->ndim;
     p->ncomp = g->ncomp;
     p->delay = g->delay;
     const bool f32 = sizeof(Real) == 4;
+    const double l2e = 1.4426950408889634, sl2e = std::sqrt(1.4426950408889634);
     for (int c = 0; c < g->ncomp; ++c) {
         const int fam = g->family[c];
+        const double *a = g->a[c], *u = g->u[c];
         p->family[c] = fam;
+        double sa = 0.0;
+        for (int d = 0; d < g->ndim; ++d) sa += a[d];
         for (int d = 0; d < g->ndim; ++d) {
-            const double a = g->a[c][d], u = g->u[c][d];
             double p0 = 0.0, p1 = 0.0;
             switch (fam) {
-            case CV_OSCILLATORY: p0 = f32 ? a / kTwoPi : a; break;
-            case CV_PRODUCT_PEAK: p0 = 1.0 / (a * a); p1 = u; break;
-            case CV_CORNER_PEAK: p0 = a; break;
-            case CV_GAUSSIAN:
-                if (f32) { p0 = a; p1 = a * u; }
-                else { p0 = a * a; p1 = u; }
+            case CV_OSCILLATORY: p0 = f32 ? a[d] / kTwoPi : a[d]; break;
+            case CV_PRODUCT_PEAK: p0 = 1.0 / (a[d] * a[d]); p1 = f32 ? 0.5 - u[d] : u[d]; break;
+            case CV_CORNER_PEAK:
+                p0 = a[d];
+                if (f32) p1 = a[d] - (double)(float)a[d];  // the low half of a
                 break;
-            case CV_C0: p0 = a; p1 = u; break;
-            case CV_DISCONTINUOUS: p0 = a; p1 = u; break;
+            case CV_GAUSSIAN:
+                if (f32) { p0 = a[d] * sl2e; p1 = a[d] * sl2e * (0.5 - u[d]); }
+                else { p0 = a[d] * a[d]; p1 = u[d]; }
+                break;
+            case CV_C0:
+                if (f32) { p0 = a[d] * l2e; p1 = 0.5 - u[d]; }
+                else { p0 = a[d]; p1 = u[d]; }
+                break;
+            case CV_DISCONTINUOUS:
+                if (f32) { p0 = a[d] * l2e; p1 = u[d] - 0.5; }
+                else { p0 = a[d]; p1 = u[d]; }
+                break;
             default: break;
             }
             p->p0[c][d] = (Real)p0;
             p->p1[c][d] = (Real)p1;
         }
-        if (fam == CV_OSCILLATORY) p->q0[c] = (Real)(f32 ? g->u[c][0] : 2.0 * 3.14159265358979323846264338327950288 * g->u[c][0]);
+        double q = 0.0;
+        bool split = false;
+        if (fam == CV_OSCILLATORY) {
+            if (f32) {
+                // phase in turns at z = 0, reduced to [-1/2, 1/2]
+                q = u[0] + sa / (2.0 * kTwoPi);
+                q -= std::nearbyint(q);
+                split = true;
+            } else {
+                q = kTwoPi * u[0];
+            }
+        } else if (fam == CV_DISCONTINUOUS && f32) {
+            q = std::exp(0.5 * sa);
+        }
+        p->q0[c] = (Real)q;
+        if (split) p->q1[c] = (Real)(q - (double)p->q0[c]);
     }
+}
+template void fill_genz_params<float>(const cv_genz *, GenzParams<float> *);
+template void fill_genz_params<double>(const cv_genz *, GenzParams<double> *);
+}  // namespace cv
+
+template <typename Real>
+static void fill_params(const cv_genz *g, GenzParams<Real> *p)
+{
+    fill_genz_params<Real>(g, p);
 }
 
 static int occupancy(cv_ctx *ctx, int ndim, int nbins, bool fp64, int *occ)
@@ -380,11 +481,59 @@ static int sample_grid(cv_ctx *ctx, int occ, long long n)
 
 
 
+// Per-block partials of a deterministic pass, in one device block laid out
+// as [ticket (256 bytes)][S: G_cap x 2 CV_MAX_COMP doubles][H: G_cap x ndim
+// x nbins values] (zeroed once; the ticket is reset by each launch's last
+// block).
+struct PassParts {
+    void *mem = nullptr;
+    int G_cap = 0;
+};
+
+static void parts_args(const PassParts *pp, int grid, double **S, void **H, unsigned **ticket)
+{
+    char *base = static_cast<char *>(pp->mem);
+    *ticket = reinterpret_cast<unsigned *>(base);
+    *S = reinterpret_cast<double *>(base + 256);
+    *H = base + 256 + (size_t)pp->G_cap * 2 * CV_MAX_COMP * sizeof(double);
+    (void)grid;
+}
+
+// The grid of a sampling pass over n_grid points as launch_pass chooses it
+// (the run-time specialised kernel's occupancy when CV_JIT compiles, else
+// the generic kernel's).
+template <typename Real>
+static int pass_grid(cv_ctx *ctx, const cv_genz *g, int nbins, int flags, long long n_grid, int *grid)
+{
+    if constexpr (sizeof(Real) == 4) {
+        if (flags & CV_JIT) {
+            SampleArgs<float> a;
+            memset(&a, 0, sizeof(a));
+            fill_params<float>(g, &a.g);
+            a.nbins = nbins;
+            a.map = make_map(nbins, g->ndim, false);
+            set_generator(&a, g->ndim, flags, 0);
+            JitKernel k;
+            std::string err;
+            if (jit_sample_kernel(ctx->device, a, g->ndim, a.map.pow2 != 0, min_blocks_f32(g->ndim), &k, &err) == 0) {
+                *grid = sample_grid(ctx, k.occ, n_grid);
+                return CV_OK;
+            }
+        }
+    }
+    int occ = 0, rc = occupancy(ctx, g->ndim, nbins, sizeof(Real) == 8, &occ);
+    if (rc) return rc;
+    *grid = sample_grid(ctx, occ, n_grid);
+    return CV_OK;
+}
+
+// One sampling pass.  pp: per-block partials for a deterministic reduction
+// (else FP64 atomics); *grid_out receives the grid used.
 template <typename Real>
 static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *edges,
                        unsigned long long start, long long n, long long n_grid,
                        double *S1, double *S2, double *H, DevState *st, int flags, uint64_t seed,
-                       const float2 *ew32 = nullptr)
+                       const float2 *ew32 = nullptr, const PassParts *pp = nullptr, int *grid_out = nullptr)
 {
     SampleArgs<Real> a;
     memset(&a, 0, sizeof(a));
@@ -402,14 +551,24 @@ static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *e
     a.start = start;
     a.n = n;
     a.st = st;
+    auto use_parts = [&](int grid) {
+        if (grid_out) *grid_out = grid;
+        if (pp && pp->mem && grid <= pp->G_cap) {
+            parts_args(pp, grid, &a.part_S, &a.part_H, &a.part_ticket);
+            a.part_G = grid;
+        }
+    };
     if constexpr (sizeof(Real) == 4) {
         if (jit) {
             JitKernel k;
             std::string err;
             if (jit_sample_kernel(ctx->device, a, g->ndim, a.map.pow2 != 0, min_blocks_f32(g->ndim), &k, &err) == 0) {
                 const int grid = sample_grid(ctx, k.occ, n_grid);
+                use_parts(grid);
+                const int tk = timer_begin(ctx);
                 cudaError_t e = launch_jit_sample(k, a, grid, ctx->stream);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "specialised sampling kernel launch");
+                timer_end(ctx, tk);
                 return CV_OK;
             }
             snprintf(ctx->msg, sizeof(ctx->msg), "run-time specialisation unavailable (%s); generic kernel used",
@@ -419,8 +578,50 @@ static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *e
     int occ = 0, rc = occupancy(ctx, g->ndim, nbins, sizeof(Real) == 8, &occ);
     if (rc) return rc;
     const int grid = sample_grid(ctx, occ, n_grid);
+    use_parts(grid);
+    const int tk = timer_begin(ctx);
     cudaError_t e = dispatch_sample<Real>(g->ndim, a, grid, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sampling kernel launch");
+    timer_end(ctx, tk);
+    return CV_OK;
+}
+
+// A standalone pass adds its histogram partials to H (its sums were added
+// by its last block).
+static int finish_parts(cv_ctx *ctx, const PassParts *pp, int grid, int nh, bool fp64, double *H)
+{
+    if (!pp || !pp->mem || grid > pp->G_cap) return CV_OK;
+    double *S;
+    void *Hp;
+    unsigned *t;
+    parts_args(pp, grid, &S, &Hp, &t);
+    CV_CUDA(ctx, launch_add_parts(Hp, grid, fp64 ? 0 : 1, nh, H, ctx->stream));
+    return CV_OK;
+}
+
+// The context's partial buffer for standalone passes: room for `grid`
+// blocks of the largest problem (32 dimensions x 256 bins, FP64), grown
+// when a pass needs more blocks.
+static int ctx_parts(cv_ctx *ctx, int grid, PassParts *out)
+{
+    if (grid > ctx->parts_G) {
+        if (ctx->parts_mem) cudaFree(ctx->parts_mem);
+        ctx->parts_mem = nullptr;
+        ctx->parts_cap = 0;
+        ctx->parts_G = 0;
+        const int G = grid;
+        const size_t bytes = pass_parts_bytes(G, CV_MAX_DIM, CV_MAX_BINS, true) + 256;
+        if (cudaMalloc(&ctx->parts_mem, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->parts_mem = nullptr;
+            return fail_msg(ctx, CV_ENOMEM, "device allocation of the pass partials failed");
+        }
+        CV_CUDA(ctx, cudaMemsetAsync(ctx->parts_mem, 0, bytes, ctx->stream));
+        ctx->parts_cap = bytes;
+        ctx->parts_G = G;
+    }
+    out->mem = ctx->parts_mem;
+    out->G_cap = ctx->parts_G;
     return CV_OK;
 }
 
@@ -507,12 +708,21 @@ extern "C" int cv_sample(cv_ctx *ctx, const cv_genz *g, int nbins, const double 
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
     if ((flags & CV_SCRAMBLE) && (flags & CV_PSEUDO))
         return fail_msg(ctx, CV_EINVAL, "CV_SCRAMBLE and CV_PSEUDO exclude each other");
-    if (flags & CV_FP64)
-        return launch_pass<double>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr,
-                                   flags, seed);
-    if ((rc = check_fp32_range(ctx, g))) return rc;
-    return launch_pass<float>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr,
-                              flags, seed);
+    const bool fp64 = (flags & CV_FP64) != 0;
+    if (!fp64 && (rc = check_fp32_range(ctx, g))) return rc;
+    // (deterministic sums: per-block partials added in block order)
+    int grid = 0;
+    rc = fp64 ? pass_grid<double>(ctx, g, nbins, flags, n, &grid) : pass_grid<float>(ctx, g, nbins, flags, n, &grid);
+    if (rc) return rc;
+    PassParts pp;
+    if ((rc = ctx_parts(ctx, grid, &pp))) return rc;
+    int used = 0;
+    rc = fp64 ? launch_pass<double>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr,
+                                    flags, seed, nullptr, &pp, &used)
+              : launch_pass<float>(ctx, g, nbins, edges_dev, start, n, n, S1_dev, S2_dev, hist_dev, nullptr,
+                                   flags, seed, nullptr, &pp, &used);
+    if (rc) return rc;
+    return finish_parts(ctx, &pp, used, g->ndim * nbins, fp64, hist_dev);
 }
 
 // The sampling map an FP32 pass takes for nbins bins and these flags (the
@@ -560,8 +770,15 @@ extern "C" int cv_sample_staged(cv_ctx *ctx, const cv_genz *g, int nbins, const 
     if (!table_dev || ((uintptr_t)table_dev & 7u) || !S1_dev || !S2_dev || !hist_dev)
         return fail_msg(ctx, CV_EINVAL, "null or unaligned buffer");
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
-    return launch_pass<float>(ctx, g, nbins, nullptr, start, n, n, S1_dev, S2_dev, hist_dev, nullptr, flags, seed,
-                              static_cast<const float2 *>(table_dev));
+    int grid = 0;
+    if ((rc = pass_grid<float>(ctx, g, nbins, flags, n, &grid))) return rc;
+    PassParts pp;
+    if ((rc = ctx_parts(ctx, grid, &pp))) return rc;
+    int used = 0;
+    rc = launch_pass<float>(ctx, g, nbins, nullptr, start, n, n, S1_dev, S2_dev, hist_dev, nullptr, flags, seed,
+                            static_cast<const float2 *>(table_dev), &pp, &used);
+    if (rc) return rc;
+    return finish_parts(ctx, &pp, used, g->ndim * nbins, false, hist_dev);
 }
 
 extern "C" int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_dev, double *edges_dev)
@@ -592,6 +809,7 @@ struct cv_integral {
     long long nmax = 0;        // largest iteration
     int K = 0;                 // iterations per graph replay
     cudaGraphExec_t exec = nullptr;
+    PassParts parts;           // per-block partials of the passes (deterministic sums)
     int launched_kernels = 0;  // kernels in one run (reset + iterations)
     bool oneshot = false;      // cv_vegas's: run once, kernels enqueued directly, state in ctx->vegas_mem
 };
@@ -635,14 +853,15 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
     const cv_spec &sp = I->spec;
     cudaStream_t keep = ctx->stream;
     ctx->stream = s;
+    int grid = 0;
     int rc = (sp.flags & CV_FP64)
         ? launch_pass<double>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st,
-                              sp.flags, sp.seed)
+                              sp.flags, sp.seed, nullptr, &I->parts, &grid)
         : launch_pass<float>(ctx, &sp.g, sp.nbins, I->edges, 0, 0, I->nmax, I->st->S1, I->st->S2, I->H, I->st,
-                             sp.flags, sp.seed, I->ew32);
+                             sp.flags, sp.seed, I->ew32, &I->parts, &grid);
     ctx->stream = keep;
     if (rc) return rc;
-    CombineArgs ca;
+    CombineArgs ca = {};
     ca.st = I->st;
     ca.ncomp = sp.g.ncomp;
     ca.epsrel = sp.epsrel;
@@ -654,6 +873,17 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
     ca.log_I = I->log_I;
     ca.log_var = I->log_var;
     ca.log_cap = kLogCap;
+    if (grid <= I->parts.G_cap) {
+        // the refinement sums the pass's histogram partials in block order
+        double *S;
+        void *Hp;
+        unsigned *t;
+        parts_args(&I->parts, grid, &S, &Hp, &t);
+        ca.part_H = Hp;
+        ca.part_G = grid;
+        ca.part_nh = sp.g.ndim * sp.nbins;
+        ca.part_f32 = (sp.flags & CV_FP64) ? 0 : 1;
+    }
     cudaError_t e = launch_refine_combine(sp.g.ndim, sp.nbins, I->H, I->edges, ca, I->ew32, I->map, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "refine/combine kernel launch");
     return CV_OK;
@@ -721,7 +951,16 @@ static int integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral **out, 
     const size_t sz_log = (size_t)kLogCap * CV_MAX_COMP * sizeof(double);
     const bool fp32 = !(spec->flags & CV_FP64);
     const size_t sz_ew = fp32 ? (size_t)ndim * N * sizeof(float2) : 0;
-    const size_t bytes = sz_state + sz_edges + sz_H + 2 * sz_log + sz_ew;
+    // the passes' per-block partials, for the grid every pass of this run uses
+    int G = 0;
+    rc = fp32 ? pass_grid<float>(ctx, &spec->g, N, spec->flags, I->nmax, &G)
+              : pass_grid<double>(ctx, &spec->g, N, spec->flags, I->nmax, &G);
+    if (rc) {
+        delete I;
+        return rc;
+    }
+    const size_t sz_parts = ((pass_parts_bytes(G, ndim, N, !fp32) + 256) + 255) & ~(size_t)255;
+    const size_t bytes = sz_state + sz_edges + sz_H + 2 * sz_log + ((sz_ew + 255) & ~(size_t)255) + sz_parts;
     char *p = nullptr;
     if (oneshot) {
         if (bytes > ctx->vegas_cap) {
@@ -751,6 +990,10 @@ static int integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral **out, 
     I->log_I = (double *)(p + sz_state + sz_edges + sz_H);
     I->log_var = (double *)(p + sz_state + sz_edges + sz_H + sz_log);
     if (fp32) I->ew32 = (float2 *)(p + sz_state + sz_edges + sz_H + 2 * sz_log);
+    I->parts.mem = p + sz_state + sz_edges + sz_H + 2 * sz_log + ((sz_ew + 255) & ~(size_t)255);
+    I->parts.G_cap = G;
+    // (the ticket starts at zero; every pass's last block leaves it so)
+    CV_CUDA(ctx, cudaMemsetAsync(I->parts.mem, 0, 256, ctx->stream));
     {
         // the map the sampling kernel takes (the point generator can change it)
         I->map = sampling_map(N, ndim, spec->flags);
@@ -1856,7 +2099,7 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         it.st = (DevState *)p;
         it.edges = (double *)(p + sz_state);
         it.H = (double *)(p + sz_state + ((((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255));
-        CombineArgs ca;
+        CombineArgs ca = {};
         ca.st = it.st;
         ca.ncomp = sp.g.ncomp;
         ca.epsrel = sp.epsrel;
@@ -2330,7 +2573,7 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     Real *f = (Real *)(p + sz_state + sz_edges + sz_H + sz_x);
     int rc = CV_OK;
     cudaStream_t s = ctx->stream;
-    CombineArgs ca;
+    CombineArgs ca = {};
     memset(&ca, 0, sizeof(ca));
     ca.st = st;
     ca.ncomp = ncomp;

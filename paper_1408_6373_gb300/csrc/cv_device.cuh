@@ -115,20 +115,23 @@ __device__ __forceinline__ void sobol_step_even(W (&X)[NDIM], int li = 0)
 }
 
 // ------------------------------------------------------------ maps
-// FP32 path: the 32-bit word is the top half of the 64-bit Sobol word and y
-// keeps its top 23 bits, so frac is exact as the mantissa of 1.frac minus 1.
-// FP64 path: 64-bit word, y keeps 52 bits.
+// FP32 path: the 32-bit word is the top half of the 64-bit Sobol word and
+// the coordinate keeps its top 23 bits; the kernels map to the centred
+// coordinate z = x - 1/2 through the grid table of grid_entry_f32.
+// FP64 path: 64-bit word, y keeps 52 bits, x in [0, 1].
 //
-// Shared-memory layout of a block's grid and histogram.  For N = 2^L >= 32
-// the bins of an axis are stored stratum-major.  Writing the bin index
+// Shared-memory layout (FP32) for N = 2^L >= 32.  Writing the bin index
 // k = y_1 .. y_L (the top L bits of y), bin k sits at slot
 //   s = (y_6 .. y_L) * 32 + y_5 * 16 + (y_1 .. y_4),
-// which is exactly the top L bits of the point's permuted word.  The 32
-// lanes of a warp always hold 32 distinct 1/32-strata (y_1 .. y_5), so their
-// slots are distinct mod 32 -- every histogram access of a warp hits 32
-// distinct banks -- and each half-warp (lanes 0-15 or 16-31: Gray-code
-// bit 4 fixed) holds 16 distinct y_1 .. y_4, so the 8-byte {e, w} gathers
-// are conflict-free too.  Other N use slot = k.
+// the top L bits of the point's mapped word (slot_perm), followed there by
+// three zero bits, so the word shifted right by 29 - L is the byte offset
+// 8 s of the bin's grid entry.  The 32 lanes of a warp always hold 32
+// distinct 1/32-strata (y_1 .. y_5), so their slots are distinct mod 32 and
+// each half-warp (Gray-code bit 4 fixed) holds 16 distinct y_1 .. y_4: the
+// 8-byte grid gathers and the histogram updates are free of bank
+// conflicts.  Every warp's own f^2 histogram sits at the grid's stride (a
+// pair of warps shares 8-byte entries, one float each), so the same offset
+// plus a per-warp constant addresses it.  Other N use slot = k.
 
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -137,11 +140,35 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// 1/x: the special-function unit's reciprocal refined by one Newton step,
+// r + r (1 - x r), which brings it to about half an ulp; the corner and
+// product peaks raise or use it directly, so its error must not be biased.
+__device__ __forceinline__ float rcp_refined(float x)
+{
+    const float r = rcp_approx(x);
+    return __fmaf_rn(r, __fmaf_rn(-x, r, 1.0f), r);
+}
+
+// 2^x on the special-function unit (the FP32 exponential families take
+// their arguments already scaled by log2 e).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// slot of bin k (staging and flush run once per block; the sampling loop
-// takes the slot straight from the permuted Sobol word)
+// Packed FP32 pairs: one FFMA2 / FADD2 / FMUL2 instruction performs the
+// operation on both halves of a register pair.  The FP32 pipe's rate is the
+// same as for two scalar instructions, but the pair takes one issue slot, and
+// the sampling pass is bound by instruction issue: the integrands' sums over
+// axes go two axes per instruction, the accumulations two components.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 // ------------------------------------------------------------ integrands
 template <int E>
@@ -150,20 +177,57 @@ __device__ __forceinline__ float ipow(float r)
     // r^E by repeated squaring (E is a compile-time constant)
     float acc = 1.0f, b = r;
     int e = E;
+    bool first = true;
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
-        if (e & 1) acc *= b;
+        if (e & 1) {
+            acc = first ? b : acc * b;
+            first = false;
+        }
         e >>= 1;
         if (e) b *= b;
     }
     return acc;
 }
 
+// (h + l)^E for h + l carried to about twice binary32 precision: each
+// product of pairs keeps its rounding error (FMA) and the cross terms,
+// (ah + al)(bh + bl) = ah bh + [err(ah bh) + al bh + ah bl] + al bl, the
+// last term below the pair's precision.  Returns the high part, the low
+// part in lo.
+__device__ __forceinline__ void mul_df(float ah, float al, float bh, float bl, float &h, float &l)
+{
+    h = ah * bh;
+    l = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -h)));
+}
+template <int E>
+__device__ __forceinline__ float ipow_df(float h, float l, float &lo)
+{
+    float ah = 1.0f, al = 0.0f, bh = h, bl = l;
+    int e = E;
+    bool first = true;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        if (e & 1) {
+            if (first) {
+                ah = bh;
+                al = bl;
+            } else {
+                mul_df(ah, al, bh, bl, ah, al);
+            }
+            first = false;
+        }
+        e >>= 1;
+        if (e) mul_df(bh, bl, bh, bl, bh, bl);
+    }
+    lo = al;
+    return ah;
+}
+
 // Integrand policies: where component C's family and parameters come from.
 // RuntimeIntegrand reads them from the launch's parameter block (constant
 // bank operands).  A policy generated for one problem returns compile-time
-// constants instead, so the family dispatch folds away and the parameters
-// become instruction immediates.
+// constants instead, so the family dispatch folds away.
 template <typename Real>
 struct RuntimeIntegrand {
     static constexpr int kMode = 0;  // the integrand is evaluated in the pass
@@ -173,6 +237,7 @@ struct RuntimeIntegrand {
     template <int C> __device__ __forceinline__ static Real p0(const GenzParams<Real> &g, int d) { return g.p0[C][d]; }
     template <int C> __device__ __forceinline__ static Real p1(const GenzParams<Real> &g, int d) { return g.p1[C][d]; }
     template <int C> __device__ __forceinline__ static Real q0(const GenzParams<Real> &g) { return g.q0[C]; }
+    template <int C> __device__ __forceinline__ static Real q1(const GenzParams<Real> &g) { return g.q1[C]; }
     __device__ __forceinline__ static int delay(const GenzParams<Real> &g) { return g.delay; }
     __device__ __forceinline__ static int table(const MapParams &m) { return m.li; }
     __device__ __forceinline__ static bool priv(const MapParams &m) { return m.priv != 0; }
@@ -210,63 +275,145 @@ __device__ __forceinline__ Real delay_chain(const Real (&x)[NDIM], int n)
     return z;
 }
 
-// FP32 Genz evaluation of component C.
+// s0 + sum_d w[d] z[d] for component C with w = p0 (P = 0) or p1 (P = 1):
+// scalar FMAs, whose parameter operands are immediates or constant-bank
+// operands (a packed instruction would need its parameter pair in
+// registers), in two interleaved chains.
+template <int NDIM, int C, int P, class I>
+__device__ __forceinline__ float axis_dot(const GenzParams<float> &g, const float (&z)[NDIM], float s0)
+{
+    float a0 = s0, a1 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        const float w = P == 0 ? I::template p0<C>(g, d) : I::template p1<C>(g, d);
+        if (d & 1) a1 = __fmaf_rn(w, z[d], a1);
+        else a0 = __fmaf_rn(w, z[d], a0);
+    }
+    return a0 + a1;
+}
+
+// FP32 Genz evaluation of component C at the centred point z = x - 1/2,
+// with the parameter forms of GenzParams (base-2 exponents, q0 + q1 pairs).
+// Steps whose operands are all computed values (squares, the product over
+// axes) go two axes per packed instruction.
 template <int NDIM, int C, class I>
-__device__ __forceinline__ float genz_f32(const GenzParams<float> &g, const float (&x)[NDIM])
+__device__ __forceinline__ float genz_f32(const GenzParams<float> &g, const float (&z)[NDIM])
 {
     switch (I::template family<C>(g)) {
     case CV_OSCILLATORY: {
-        float t = I::template q0<C>(g);  // phase in turns, reduced to [-1/2, 1/2]
-#pragma unroll
-        for (int d = 0; d < NDIM; ++d) t = __fmaf_rn(I::template p0<C>(g, d), x[d], t);
+        // phase in turns: (q0 + q1) + sum p0 z, reduced to [-1/2, 1/2]
+        float t = I::template q0<C>(g) + axis_dot<NDIM, C, 0, I>(g, z, I::template q1<C>(g));
         t -= rintf(t);
         return __cosf(6.28318530717958647692f * t);
     }
     case CV_PRODUCT_PEAK: {
-        float P = 1.0f;
+        // prod (1/a^2 + (z - (u - 1/2))^2), then one refined reciprocal
+        float q[NDIM];
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) {
-            const float dx = x[d] - I::template p1<C>(g, d);
-            P *= __fmaf_rn(dx, dx, I::template p0<C>(g, d));
+            const float dz = z[d] + I::template p1<C>(g, d);
+            q[d] = __fmaf_rn(dz, dz, I::template p0<C>(g, d));
         }
-        return rcp_approx(P);
+        float2 P = make_float2(q[0], NDIM > 1 ? q[NDIM > 1 ? 1 : 0] : 1.0f);
+#pragma unroll
+        for (int d = 2; d + 1 < NDIM; d += 2) P = mul2(P, make_float2(q[d], q[d + 1]));
+        float Pr = P.x * P.y;
+        if ((NDIM & 1) && NDIM > 1) Pr *= q[NDIM - 1];
+        return rcp_refined(Pr);
     }
     case CV_CORNER_PEAK: {
-        float s = 1.0f;
+        // s^-(NDIM+1) with s = 1 + sum a x over the uncentred x = z + 1/2.
+        // Every term is non-negative, so near the corner, where f is
+        // largest, the sum is small beside the 1 and its roundings are small
+        // against s (the centred form 1 + sum a/2 + sum a z cancels there:
+        // partial sums of size sum a/2 for an s near 1).  Every relative
+        // error of s or of 1/s comes back NDIM + 1 times larger, so s is
+        // carried as sh + sl to about twice binary32 precision: a = p0 + p1
+        // as high and low halves, the exact products (FMA), TwoSum for the
+        // additions -- each one from 9 axes on, the final 1 + t below that.
+        // 1/s is r (1 + w) to first order; below 9 axes the power takes w to
+        // first order, r^k (1 + k w), from 9 axes on it is a product of
+        // pairs, whose roundings would otherwise add up to about k units.
+        float sh, sl;
+        if (NDIM >= 9) {
+            sh = 1.0f;
+            sl = 0.0f;
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(I::template p0<C>(g, d), x[d], s);
-        return ipow<NDIM + 1>(rcp_approx(s));
+            for (int d = 0; d < NDIM; ++d) {
+                const float x = z[d] + 0.5f;
+                const float a = I::template p0<C>(g, d);
+                const float p = a * x;
+                const float pe = __fmaf_rn(a, x, -p);
+                const float t1 = sh + p;
+                const float bb = t1 - sh;
+                sl += ((sh - (t1 - bb)) + (p - bb)) + pe;
+                sl = __fmaf_rn(I::template p1<C>(g, d), x, sl);
+                sh = t1;
+            }
+        } else {
+            // the high sum in two chains
+            float t0 = 0.0f, t1 = 0.0f, te = 0.0f;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                const float x = z[d] + 0.5f;
+                if (d & 1) t1 = __fmaf_rn(I::template p0<C>(g, d), x, t1);
+                else t0 = __fmaf_rn(I::template p0<C>(g, d), x, t0);
+                te = __fmaf_rn(I::template p1<C>(g, d), x, te);
+            }
+            const float t = t0 + t1;
+            sh = 1.0f + t;
+            const float bb = sh - 1.0f;
+            sl = ((1.0f - (sh - bb)) + (t - bb)) + te;
+        }
+        // 1/(sh + sl) = r (1 + w) to first order, w = (1 - sh r) - sl r
+        // (the first term exact by FMA: the reciprocal's own error)
+        const float r = rcp_refined(sh);
+        const float w = __fmaf_rn(-sl, r, __fmaf_rn(-sh, r, 1.0f));
+        if (NDIM >= 9) {
+            float fl;
+            const float fh = ipow_df<NDIM + 1>(r, r * w, fl);
+            return fh + fl;
+        }
+        const float f = ipow<NDIM + 1>(r);
+        return __fmaf_rn(f, (float)(NDIM + 1) * w, f);
     }
     case CV_GAUSSIAN: {
-        float s = 0.0f;
+        // 2^-(sum (p0 z + p1)^2)
+        float t[NDIM];
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) {
-            const float t = __fmaf_rn(I::template p0<C>(g, d), x[d], -I::template p1<C>(g, d));
-            s = __fmaf_rn(t, t, s);
+        for (int d = 0; d < NDIM; ++d) t[d] = __fmaf_rn(I::template p0<C>(g, d), z[d], I::template p1<C>(g, d));
+        float2 s2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int d = 0; d + 1 < NDIM; d += 2) {
+            const float2 tt = make_float2(t[d], t[d + 1]);
+            s2 = fma2(tt, tt, s2);
         }
-        return __expf(-s);
+        if (NDIM & 1) s2.x = __fmaf_rn(t[NDIM - 1], t[NDIM - 1], s2.x);
+        return ex2_approx(-(s2.x + s2.y));
     }
     case CV_C0: {
-        float s = 0.0f;
+        // 2^-(sum p0 |z + p1|)
+        float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d)
-            s = __fmaf_rn(I::template p0<C>(g, d), fabsf(x[d] - I::template p1<C>(g, d)), s);
-        return __expf(-s);
+        for (int d = 0; d < NDIM; ++d) {
+            const float v = __fmaf_rn(I::template p0<C>(g, d), fabsf(z[d] + I::template p1<C>(g, d)), d & 1 ? a1 : a0);
+            if (d & 1) a1 = v;
+            else a0 = v;
+        }
+        return ex2_approx(-(a0 + a1));
     }
     case CV_DISCONTINUOUS: {
-        bool out = x[0] > I::template p1<C>(g, 0);
-        if (NDIM > 1) out = out || (x[NDIM > 1 ? 1 : 0] > I::template p1<C>(g, NDIM > 1 ? 1 : 0));
-        float s = 0.0f;
-#pragma unroll
-        for (int d = 0; d < NDIM; ++d) s = __fmaf_rn(I::template p0<C>(g, d), x[d], s);
-        return out ? 0.0f : __expf(s);
+        bool out = z[0] > I::template p1<C>(g, 0);
+        if (NDIM > 1) out = out || (z[NDIM > 1 ? 1 : 0] > I::template p1<C>(g, NDIM > 1 ? 1 : 0));
+        const float s = axis_dot<NDIM, C, 0, I>(g, z, 0.0f);
+        return out ? 0.0f : I::template q0<C>(g) * ex2_approx(s);
     }
     default:
         return 1.0f;
     }
 }
 
-// FP64 Genz evaluation of component C (same formulas in double).
+// FP64 Genz evaluation of component C (x in [0, 1]).
 template <int NDIM, int C, class I>
 __device__ __forceinline__ double genz_f64(const GenzParams<double> &g, const double (&x)[NDIM])
 {
@@ -377,17 +524,21 @@ __device__ __forceinline__ double warp_total(const Acc<double> &a)
 }
 
 // ------------------------------------------------------------ sampling steps
-// Shared-memory views of one block.  Every axis owns a stride of
-// CV_MAX_BINS slots, so the offsets of axis d in the three arrays are
-// compile-time constants and one register (the slot) addresses all three.
+// Shared-memory views of one block.  FP64: every axis owns a stride of
+// CV_MAX_BINS slots.  FP32: `stride` entries per axis (nbins, or the batch
+// class's largest nbins), a compile-time constant in the specialised kernel.
 constexpr int kStride = CV_MAX_BINS;
 
 template <typename Real> struct Smem;
 template <> struct Smem<float> {
-    float2 *ew;        // [NDIM][stride]: {e_k - w_k, w_k} (w_k scaled by N on the power-of-two map)
-    float *h;          // [NDIM][hs]: the f^2 histogram (block's, or this warp's own copy)
-    int stride;        // grid slots per axis (kStride, a compile-time constant, in k_sample)
-    int hs;            // histogram slots per axis
+    float2 *ew;        // [NDIM][stride]: grid_entry_f32 of each slot (8N-aligned)
+    float *h;          // the histogram copy this warp updates: its own [NDIM][stride], or the block's
+    int stride;
+    // 32-bit shared-window addresses; for the power-of-two map the grid's
+    // and this warp's histogram's, shifted down by 3 + L and 2 + L (both
+    // bases are multiples of 8N and 4N), so one funnel shift of a point's
+    // word gives the absolute address of its bin's entry
+    unsigned g_sa, h_sa, g_hi, h_hi;
 };
 template <> struct Smem<double> {
     double2 *ew;       // [NDIM][stride] {e_k, w_k}
@@ -395,32 +546,76 @@ template <> struct Smem<double> {
     int stride, hs;
 };
 
-// Map one FP32 coordinate: returns x, multiplies the Jacobian, and gives the
-// axis-local slot of its bin.  The grid holds e'_k = e_k - w_k (rounded
-// once from FP64) beside w_k, so with the mantissa trick's 1 + frac the
-// point is x = fma(w, 1 + frac, e') -- w (1 + frac) is exact, one rounding.
-// Power-of-two N: 2^-L (1 + frac) straight from the word's bits and
-// N w_k stored (the scalings are exact), J *= N w.
+// How a block accumulates its FP32 f^2 histogram: one copy per warp,
+// updated with plain loads and stores when the 32 lanes' bins are distinct
+// (N = 2^L >= 32) or with shared atomics otherwise; or one block copy with
+// shared atomics.
+enum { kHistWarpPlain = 0, kHistWarpAtomic = 1, kHistBlock = 2 };
+
+// The shared-window addresses of a block's FP32 grid and histogram copy
+// (L = log2 N of the power-of-two map, else 0).
+__device__ __forceinline__ void set_addresses(Smem<float> &sm, int L)
+{
+    sm.g_sa = (unsigned)__cvta_generic_to_shared(sm.ew);
+    sm.h_sa = (unsigned)__cvta_generic_to_shared(sm.h);
+    sm.g_hi = L ? sm.g_sa >> (3 + L) : 0u;
+    sm.h_hi = L ? sm.h_sa >> (2 + L) : 0u;
+}
+
+// The FP32 grid table in a block's dynamic shared memory: the first
+// multiple of 8N bytes (the funnel-shift addressing needs the alignment;
+// the allocation has 8N bytes to spare for it).
+__device__ __forceinline__ float2 *align_table(unsigned char *raw, int N)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(raw);
+    const unsigned al = 8u * (unsigned)N;
+    return reinterpret_cast<float2 *>(raw + ((al - a % al) % al));
+}
+
+// Shared-memory accesses through 32-bit shared-window addresses.
+__device__ __forceinline__ float2 lds_f2(unsigned a)
+{
+    float2 v;
+    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float lds_f(unsigned a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts_f(unsigned a, float v)
+{
+    asm volatile("st.shared.f32 [%0], %1;" :: "r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void reds_add_f(unsigned a, float v)
+{
+    asm volatile("red.shared.add.f32 [%0], %1;" :: "r"(a), "f"(v) : "memory");
+}
+
+// Map one FP32 coordinate: returns z = x - 1/2 and multiplies the
+// Jacobian; `slot` receives the bin's slot (general map only: the
+// power-of-two map takes it from the word again when it updates the
+// histogram).
 template <bool POW2>
 __device__ __forceinline__ float map_f32(unsigned X, int d, int N, const MapParams &m,
-                                         const Smem<float> &sm, float &J, int &slot)
+                                         const Smem<float> &sm, float &J, unsigned &slot)
 {
     if (POW2) {
-        // X is the permuted word (table m.li): slot in the top L bits, the
-        // fraction's 23 - L bits at mantissa bits 22..L
-        const float f1 = __uint_as_float((X & m.mF) | m.expL);  // 2^-L (1 + frac)
-        const int p = (int)(X >> m.sK);
-        const float2 ew = sm.ew[d * sm.stride + p];
+        // X is the mapped word (table m.li): the grid entry's address from
+        // one funnel shift, 2^(G-L) (1 + frac 2^-G) from the fraction's bits
+        const float f1 = __uint_as_float((X & m.mF) | m.expE);
+        const float2 ew = lds_f2(__funnelshift_r(X, sm.g_hi, m.sA) + (unsigned)(d * sm.stride * 8));
         J *= ew.y;
-        slot = p;
+        slot = 0u;
         return __fmaf_rn(ew.y, f1, ew.x);
     } else {
         const unsigned t = (X >> 9) * (unsigned)N;
         const float f1 = __uint_as_float(0x3f800000u | (t & 0x7fffffu));  // 1 + frac
-        const int p = (int)(t >> 23);
-        const float2 ew = sm.ew[d * sm.stride + p];
+        slot = t >> 23;
+        const float2 ew = lds_f2(sm.g_sa + (unsigned)((d * sm.stride + (int)slot) * 8));
         J = J * ((float)N * ew.y);
-        slot = p;
         return __fmaf_rn(ew.y, f1, ew.x);
     }
 }
@@ -442,20 +637,28 @@ template <typename Real> struct Word;
 template <> struct Word<float> { using type = unsigned int; };
 template <> struct Word<double> { using type = unsigned long long; };
 
-// Evaluate component C of the point and add it to the partial sums.
-template <int NDIM, int C, typename Real, bool EDGE, class I>
-__device__ __forceinline__ void eval_comp(const GenzParams<Real> &g, const Real (&x)[NDIM],
-                                          Real J, bool valid, Real (&p1)[CV_MAX_COMP],
-                                          Real (&p2)[CV_MAX_COMP], Real &f0)
-{
-    if (C < I::ncomp(g)) {
-        Real v = J * genz_eval<NDIM, C, I>(g, x);
-        if (EDGE && !valid) v = Real(0);
-        p1[C] += v;
-        p2[C] += v * v;
-        if (C == 0) f0 = v;
+// Per-lane partial sums of a run of blocks: FP32 pairs of components
+// (0, 1) and (2, 3); FP64 one value per component.
+template <typename Real> struct Partial;
+template <> struct Partial<float> {
+    float2 s1[2], s2[2];
+    __device__ __forceinline__ void zero()
+    {
+        s1[0] = s1[1] = s2[0] = s2[1] = make_float2(0.0f, 0.0f);
     }
-}
+    __device__ __forceinline__ float v1(int c) const { return (c & 1) ? s1[c >> 1].y : s1[c >> 1].x; }
+    __device__ __forceinline__ float v2(int c) const { return (c & 1) ? s2[c >> 1].y : s2[c >> 1].x; }
+};
+template <> struct Partial<double> {
+    double s1[CV_MAX_COMP], s2[CV_MAX_COMP];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int c = 0; c < CV_MAX_COMP; ++c) s1[c] = s2[c] = 0.0;
+    }
+    __device__ __forceinline__ double v1(int c) const { return s1[c]; }
+    __device__ __forceinline__ double v2(int c) const { return s2[c]; }
+};
 
 // The caller's values of this lane's point in block q (materialised
 // samples, accumulate mode), 0 outside [start, end).
@@ -477,16 +680,26 @@ __device__ __forceinline__ void load_values(const SampleArgs<Real> &A, unsigned 
     }
 }
 
-// One aligned 32-point block q: map, integrand, partial sums, histogram.
-// EDGE: the block may hold indices outside [start, end), which add nothing.
-// fv: the caller's values of the block (accumulate mode only).
-template <int NDIM, typename Real, bool POW2, bool EDGE, class I>
-__device__ __forceinline__ void sample_block(const SampleArgs<Real> &A, const Smem<Real> &sm,
-                                             const typename Word<Real>::type (&X)[NDIM],
-                                             unsigned long long q, unsigned long long start,
-                                             unsigned long long end, int lane, bool priv,
-                                             Real (&p1)[CV_MAX_COMP], Real (&p2)[CV_MAX_COMP],
-                                             const Real (&fv)[CV_MAX_COMP], int delay)
+// Store one point for the caller's integrand (materialised samples, store
+// mode): coordinate d of point j = index - start at x[j sj + d sd].
+template <int NDIM, typename Real>
+__device__ __forceinline__ void store_point(const SampleArgs<Real> &A, long long j, const Real (&x)[NDIM])
+{
+    const long long sj = A.aos ? NDIM : 1, sd = A.aos ? 1 : A.ld;
+    Real *xp = A.x + j * sj;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) xp[d * sd] = x[d];
+}
+
+// One aligned 32-point block q, FP32: map, integrand, partial sums,
+// histogram.  EDGE: the block may hold indices outside [start, end), which
+// add nothing.  fv: the caller's values of the block (accumulate mode only).
+template <int NDIM, bool POW2, bool EDGE, class I>
+__device__ __forceinline__ void sample_block(const SampleArgs<float> &A, const Smem<float> &sm,
+                                             const unsigned (&X)[NDIM], unsigned long long q,
+                                             unsigned long long start, unsigned long long end, int lane,
+                                             int hmode, Partial<float> &P, const float (&fv)[CV_MAX_COMP],
+                                             int delay)
 {
     const int N = I::nbins(A.nbins);
     bool valid = true;
@@ -494,54 +707,115 @@ __device__ __forceinline__ void sample_block(const SampleArgs<Real> &A, const Sm
         const unsigned long long i = q * 32ull + (unsigned long long)lane;
         valid = (i >= start) && (i < end);
     }
-    Real x[NDIM];
-    int slot[NDIM];
-    Real J = Real(1);
+    float z[NDIM];
+    unsigned slot[NDIM];
+    float J = 1.0f;
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-        if constexpr (sizeof(Real) == 4)
-            x[d] = map_f32<POW2>(X[d], d, N, A.map, sm, J, slot[d]);
-        else
-            x[d] = map_f64(X[d], d, N, sm, J, slot[d]);
-    }
-    const long long j = (long long)(q * 32ull + (unsigned long long)lane - start);  // materialised slot
+    for (int d = 0; d < NDIM; ++d) z[d] = map_f32<POW2>(X[d], d, N, A.map, sm, J, slot[d]);
     if constexpr (I::kMode == 1) {
-        // store the point for the caller's integrand
+        // store the point (x = z + 1/2) for the caller's integrand
         if (!EDGE || valid) {
-            // both layouts as strides: coordinate d of point j at x[j sj + d sd]
-            const long long sj = A.aos ? NDIM : 1, sd = A.aos ? 1 : A.ld;
-            Real *xp = A.x + j * sj;
+            float x[NDIM];
 #pragma unroll
-            for (int d = 0; d < NDIM; ++d) xp[d * sd] = x[d];
+            for (int d = 0; d < NDIM; ++d) x[d] = z[d] + 0.5f;
+            store_point<NDIM, float>(A, (long long)(q * 32ull + (unsigned long long)lane - start), x);
         }
         return;
     }
-    Real f0 = Real(0);
+    const int ncomp = I::ncomp(A.g);
+    float f[CV_MAX_COMP];
     if constexpr (I::kMode == 2) {
-        // the caller's values (loaded ahead by the caller of this function)
 #pragma unroll
-        for (int c = 0; c < CV_MAX_COMP; ++c) {
-            if (c < A.g.ncomp) {
-                const Real v = J * fv[c];
-                p1[c] += v;
-                p2[c] += v * v;
-                if (c == 0) f0 = v;
-            }
-        }
+        for (int c = 0; c < CV_MAX_COMP; ++c) f[c] = fv[c];
     } else {
         // the integrand-cost knob: delay multiply-adds per component, run
-        // once per point and folded into J as J + 0 * z (exact: J is finite)
-        if (delay) J += Real(0) * delay_chain<NDIM>(x, delay * I::ncomp(A.g));
-        eval_comp<NDIM, 0, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-        eval_comp<NDIM, 1, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-        eval_comp<NDIM, 2, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
-        eval_comp<NDIM, 3, Real, EDGE, I>(A.g, x, J, valid, p1, p2, f0);
+        // once per point and folded into J as J + 0 * t (exact: J is finite)
+        if (delay) J += 0.0f * delay_chain<NDIM>(z, delay * ncomp);
+        f[0] = genz_f32<NDIM, 0, I>(A.g, z);
+    }
+    if (EDGE && !valid) J = 0.0f;  // (f is finite at every point of the block)
+    // the f^2 histogram needs component 0 only: updated before the other
+    // components are evaluated, so the bins' offsets are dead by then
+    const float v0 = J * f[0];
+    if (!EDGE || valid) {
+        const float h = v0 * v0;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            // the bin's float in the histogram copy: one funnel shift of the
+            // word (power-of-two map), or slot * 4 (general map)
+            const unsigned ha = (POW2 ? __funnelshift_r(X[d], sm.h_hi, A.map.sA + 1u) : sm.h_sa + slot[d] * 4u) +
+                                (unsigned)(d * sm.stride * 4);
+            if (hmode == kHistWarpPlain) sts_f(ha, lds_f(ha) + h);
+            else reds_add_f(ha, h);
+        }
+    }
+    if constexpr (I::kMode != 2) {
+        f[1] = ncomp > 1 ? genz_f32<NDIM, 1, I>(A.g, z) : 0.0f;
+        f[2] = ncomp > 2 ? genz_f32<NDIM, 2, I>(A.g, z) : 0.0f;
+        f[3] = ncomp > 3 ? genz_f32<NDIM, 3, I>(A.g, z) : 0.0f;
+    }
+    // the partial sums of J f and (J f)^2, two components per packed
+    // instruction
+    const float2 v01 = make_float2(v0, J * f[1]);
+    P.s1[0] = add2(P.s1[0], v01);
+    P.s2[0] = fma2(v01, v01, P.s2[0]);
+    if (ncomp > 2) {
+        const float2 v23 = make_float2(J * f[2], J * f[3]);
+        P.s1[1] = add2(P.s1[1], v23);
+        P.s2[1] = fma2(v23, v23, P.s2[1]);
+    }
+    // the next block's reads of the warp's own copy see this block's writes
+    if (hmode == kHistWarpPlain) __syncwarp();
+}
+
+// One aligned 32-point block q, FP64.
+template <int NDIM, bool EDGE, class I>
+__device__ __forceinline__ void sample_block(const SampleArgs<double> &A, const Smem<double> &sm,
+                                             const unsigned long long (&X)[NDIM], unsigned long long q,
+                                             unsigned long long start, unsigned long long end, int lane,
+                                             int hmode, Partial<double> &P, const double (&fv)[CV_MAX_COMP],
+                                             int delay)
+{
+    const int N = A.nbins;
+    bool valid = true;
+    if (EDGE) {
+        const unsigned long long i = q * 32ull + (unsigned long long)lane;
+        valid = (i >= start) && (i < end);
+    }
+    double x[NDIM];
+    int slot[NDIM];
+    double J = 1.0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) x[d] = map_f64(X[d], d, N, sm, J, slot[d]);
+    if constexpr (I::kMode == 1) {
+        if (!EDGE || valid) store_point<NDIM, double>(A, (long long)(q * 32ull + (unsigned long long)lane - start), x);
+        return;
+    }
+    const int ncomp = A.g.ncomp;
+    double f0 = 0.0;
+#pragma unroll
+    for (int c = 0; c < CV_MAX_COMP; ++c) {
+        if (c < ncomp) {
+            double f;
+            if constexpr (I::kMode == 2) {
+                f = fv[c];
+            } else {
+                if (c == 0 && delay) J += 0.0 * delay_chain<NDIM>(x, delay * ncomp);
+                f = c == 0 ? genz_f64<NDIM, 0, I>(A.g, x)
+                  : c == 1 ? genz_f64<NDIM, 1, I>(A.g, x)
+                  : c == 2 ? genz_f64<NDIM, 2, I>(A.g, x) : genz_f64<NDIM, 3, I>(A.g, x);
+            }
+            double v = J * f;
+            if (EDGE && !valid) v = 0.0;
+            P.s1[c] += v;
+            P.s2[c] += v * v;
+            if (c == 0) f0 = v;
+        }
     }
     if (!EDGE || valid) {
-        const Real h = f0 * f0;
-        if (priv) {
-            // a warp-private histogram (FP32, N = 2^L >= 32): the lanes'
-            // bins are distinct, so the update is a plain read-modify-write
+        const double h = f0 * f0;
+        if (hmode == kHistWarpPlain) {
+            // the warp's own copy: its 32 points are in 32 distinct bins
 #pragma unroll
             for (int d = 0; d < NDIM; ++d) sm.h[d * sm.hs + slot[d]] += h;
         } else {
@@ -549,13 +823,13 @@ __device__ __forceinline__ void sample_block(const SampleArgs<Real> &A, const Sm
             for (int d = 0; d < NDIM; ++d) atomicAdd(&sm.h[d * sm.hs + slot[d]], h);
         }
     }
-    // the next block's reads of the private copy see this block's writes
-    if (priv) __syncwarp();
+    if (hmode == kHistWarpPlain) __syncwarp();
 }
 
 // nsteps consecutive 32-point blocks starting at block q0, every lane's
-// words advanced past them.  FP32: the values are summed in FP32 over runs
-// of kRun blocks, and each run's sum is added to the Kahan accumulators.
+// words advanced past them.  The values are summed in FP32 (FP64) over
+// runs of kRun blocks, and each run's sum is added to the per-thread
+// accumulators.
 //   EDGE = false: every index of the range is inside [start, end), q0 and
 //   nsteps are even; the blocks go in (even, odd) pairs, and the step out
 //   of an even block is the fixed word W_5.
@@ -568,19 +842,17 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
                                           typename Word<Real>::type (&X)[NDIM],
                                           unsigned long long q0, unsigned nsteps,
                                           unsigned long long start, unsigned long long end,
-                                          int lane, Acc<Real> (&s1)[CV_MAX_COMP],
+                                          int lane, int hmode, Acc<Real> (&s1)[CV_MAX_COMP],
                                           Acc<Real> (&s2)[CV_MAX_COMP])
 {
     using W = typename Word<Real>::type;
     const int li = (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0;  // direction table
-    const bool priv = sizeof(Real) == 4 && POW2 && I::priv(A.map);
     const unsigned per = EDGE ? 1u : 2u;  // blocks per loop trip
     const int delay = I::delay(A.g);      // (read once: the integrand-cost knob)
     for (unsigned r0 = 0; r0 < nsteps; r0 += kRun) {
         const unsigned r1 = min(r0 + kRun, nsteps);
-        Real p1[CV_MAX_COMP], p2[CV_MAX_COMP];
-#pragma unroll
-        for (int c = 0; c < CV_MAX_COMP; ++c) p1[c] = p2[c] = Real(0);
+        Partial<Real> P;
+        P.zero();
         for (unsigned st = r0; st < r1; st += per) {
             const unsigned long long q = q0 + st;
             // accumulate mode: both blocks' values are requested before any
@@ -590,30 +862,36 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
                 load_values<NDIM, Real, EDGE>(A, q, start, end, lane, fa);
                 if (!EDGE) load_values<NDIM, Real, EDGE>(A, q + 1, start, end, lane, fb);
             }
+            auto block = [&](unsigned long long qq, const Real (&fv)[CV_MAX_COMP]) {
+                if constexpr (sizeof(Real) == 4)
+                    sample_block<NDIM, POW2, EDGE, I>(A, sm, X, qq, start, end, lane, hmode, P, fv, delay);
+                else
+                    sample_block<NDIM, EDGE, I>(A, sm, X, qq, start, end, lane, hmode, P, fv, delay);
+            };
             if constexpr (I::kGen == 2) {
                 // pseudo-random points: fresh words for every block
                 pseudo_words<NDIM, W>(X, A.seed, q * 32ull + (unsigned long long)lane);
-                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2, fa, delay);
+                block(q, fa);
                 if (!EDGE) {
                     pseudo_words<NDIM, W>(X, A.seed, (q + 1) * 32ull + (unsigned long long)lane);
-                    sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2, fb, delay);
+                    block(q + 1, fb);
                 }
                 continue;
             }
-            sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q, start, end, lane, priv, p1, p2, fa, delay);
+            block(q, fa);
             if (EDGE) {
                 sobol_step<NDIM, W>(X, q, li);
             } else {
                 sobol_step_even<NDIM, W>(X, li);
-                sample_block<NDIM, Real, POW2, EDGE, I>(A, sm, X, q + 1, start, end, lane, priv, p1, p2, fb, delay);
+                block(q + 1, fb);
                 sobol_step<NDIM, W>(X, q + 1, li);
             }
         }
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c) {
             if (c < I::ncomp(A.g)) {
-                s1[c].add(p1[c]);
-                s2[c].add(p2[c]);
+                s1[c].add(P.v1(c));
+                s2[c].add(P.v2(c));
             }
         }
     }
@@ -627,6 +905,47 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
 // latency with 8 warps); FP64 kernels get what they need.
 template <int NDIM, typename Real>
 constexpr int kMinBlocks = sizeof(Real) != 4 ? 1 : (NDIM <= 8 ? 3 : 2);
+
+// Stage an FP32 block's grid table from the FP64 edges (slot order).
+__device__ __forceinline__ void stage_grid_f32(float2 *ew, int ndim, int N, int stride, const double *edges,
+                                               const MapParams &map)
+{
+    // (by bin: coalesced reads of the FP64 grid)
+    for (int idx = threadIdx.x; idx < ndim * N; idx += blockDim.x) {
+        const int d = idx / N, k = idx - d * N;
+        const double *e = edges + (size_t)d * (N + 1);
+        ew[d * stride + slot_of_bin(k, map)] = grid_entry_f32(e[k], e[k + 1] - e[k], N, map);
+    }
+}
+
+// The last block of a deterministic pass to finish adds every block's sums
+// to S1, S2 in a fixed order: warp v sums value v (S1 and S2 of each
+// component) over the blocks, lane l taking blocks l, l + 32, ..., then a
+// fixed shuffle tree.  The ticket counts finished blocks (no block waits
+// for another) and is reset for the next launch.
+__device__ __forceinline__ void last_block_sums(const double *part_S, unsigned *ticket, double *S1, double *S2,
+                                                int ncomp)
+{
+    __shared__ int s_last;
+    __threadfence();  // this block's partials, before its ticket
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31;
+    for (int v = threadIdx.x >> 5; v < 2 * ncomp; v += kWarpsPerBlock) {
+        double acc = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) acc += __ldcg(&part_S[b * (2 * CV_MAX_COMP) + v]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            double *dst = (v & 1) ? &S2[v >> 1] : &S1[v >> 1];
+            *dst += acc;
+        }
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
 
 // One fused sampling pass (the kernel body, shared by every specialisation).
 template <int NDIM, typename Real, bool POW2, class I>
@@ -648,54 +967,47 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
     const int N = I::nbins(A.nbins);
     const int ncomp = A.g.ncomp;
     const bool priv = sizeof(Real) == 4 && POW2 && I::priv(A.map);
+    // FP64: warp copies for Sobol points and N = 2^L >= 32 when they fit
+    const bool priv64 = sizeof(Real) == 8 && I::kGen != 2 && A.map.priv != 0;
+    const int hmode = (priv || priv64) ? kHistWarpPlain : kHistBlock;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<Real> sm;
-    sm.stride = kStride;
-    sm.hs = kStride;
     if constexpr (sizeof(Real) == 4) {
-        sm.ew = reinterpret_cast<float2 *>(smem_raw);
-        sm.h = reinterpret_cast<float *>(sm.ew + NDIM * kStride);
-        if (priv && I::kMode != 1) {
-            // [kWarpsPerBlock][NDIM][N]: every warp's own copy
-            for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * N; i += blockDim.x) sm.h[i] = 0.0f;
+        sm.stride = N;
+        sm.ew = align_table(smem_raw, N);
+        float *hist = reinterpret_cast<float *>(sm.ew + NDIM * N);
+        if (I::kMode != 1) {
+            // the histogram copies: every warp's [NDIM][N], or the block's
+            const int nh = priv ? kWarpsPerBlock * NDIM * N : NDIM * N;
+            for (int i = threadIdx.x; i < nh; i += blockDim.x) hist[i] = 0.0f;
         }
+        const int warp = threadIdx.x >> 5;
+        sm.h = priv ? hist + warp * NDIM * N : hist;
+        set_addresses(sm, POW2 ? A.map.L : 0);
         if (A.ew32) {
             // the table the refinement staged (FP64 arithmetic is slow here:
             // done once per pass there instead of once per CTA)
-            for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-                const int d = idx / N, sl = idx - d * N;
-                const int p = d * kStride + sl;
-                sm.ew[p] = A.ew32[idx];
-                if (!priv) sm.h[p] = 0.0f;
-            }
+            for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) sm.ew[idx] = A.ew32[idx];
         } else {
-            // (by bin: coalesced reads of the FP64 grid)
-            for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-                const int d = idx / N, k = idx - d * N;
-                const double *e = A.edges + (size_t)d * (N + 1);
-                const int p = d * kStride + slot_of_bin(k, A.map);
-                const double w = e[k + 1] - e[k];
-                sm.ew[p] = make_float2(__double2float_rn(e[k] - w), __double2float_rn(POW2 ? (double)N * w : w));
-                if (!priv) sm.h[p] = 0.0f;
-            }
+            stage_grid_f32(sm.ew, NDIM, N, N, A.edges, A.map);
         }
     } else {
+        sm.stride = kStride;
         sm.ew = reinterpret_cast<double2 *>(smem_raw);
-        sm.h = reinterpret_cast<double *>(sm.ew + NDIM * kStride);
+        double *hist = reinterpret_cast<double *>(sm.ew + NDIM * kStride);
+        // the block's histogram (kStride slots per axis), or every warp's [NDIM][N]
+        sm.hs = priv64 ? N : kStride;
+        sm.h = priv64 ? hist + (threadIdx.x >> 5) * NDIM * N : hist;
+        for (int i = threadIdx.x; i < (priv64 ? kWarpsPerBlock * NDIM * N : NDIM * kStride); i += blockDim.x)
+            hist[i] = 0.0;
         for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
             const int d = idx / N, k = idx - d * N;
             const double *e = A.edges + (size_t)d * (N + 1);
             sm.ew[d * kStride + k] = make_double2(e[k], e[k + 1] - e[k]);
-            sm.h[d * kStride + k] = 0.0;
         }
     }
     __syncthreads();
-    float *const hblock = reinterpret_cast<float *>(sm.h);  // (FP32: the private copies' base)
-    if (priv) {
-        sm.h = sm.h + (threadIdx.x >> 5) * NDIM * N;
-        sm.hs = N;
-    }
 
     const int lane = threadIdx.x & 31;
     // blocks [qa, qb) cover the pass; qa and the chunk length are even, so
@@ -730,9 +1042,9 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         }
         const bool interior = (q0 * 32ull >= start) && (q1 * 32ull <= end) && !((q0 | q1) & 1ull);
         if (interior)
-            run_steps<NDIM, Real, POW2, false, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
+            run_steps<NDIM, Real, POW2, false, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, hmode, s1, s2);
         else
-            run_steps<NDIM, Real, POW2, true, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, s1, s2);
+            run_steps<NDIM, Real, POW2, true, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, hmode, s1, s2);
     }
 
     if constexpr (I::kMode == 1) return;  // points stored: nothing to reduce
@@ -752,33 +1064,45 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         }
     }
     __syncthreads();
+    const bool parts = A.part_S != nullptr;
     if (threadIdx.x < 2 * ncomp) {
         double t = 0.0;
         for (int w = 0; w < kWarpsPerBlock; ++w) t += red[w][threadIdx.x];
         const int c = threadIdx.x >> 1;
-        atomicAdd((threadIdx.x & 1) ? &A.S2[c] : &A.S1[c], t);
+        if (parts) A.part_S[blockIdx.x * (2 * CV_MAX_COMP) + threadIdx.x] = t;
+        else atomicAdd((threadIdx.x & 1) ? &A.S2[c] : &A.S1[c], t);
     }
     // (by bin: the FP64 atomics of a warp go to consecutive addresses,
     // which the L2 merges; every block flushes at about the same time)
+    Real *ph = parts ? reinterpret_cast<Real *>(A.part_H) + (size_t)blockIdx.x * NDIM * N : nullptr;
     for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
         const int d = idx / N;
         const int k = idx - d * N;
         Real v;
         if constexpr (sizeof(Real) == 4) {
             const int p = slot_of_bin(k, A.map);
+            const float *hist = reinterpret_cast<const float *>(sm.ew + NDIM * N);
             if (priv) {
                 // the warps' copies, summed in warp order
                 v = 0.0f;
 #pragma unroll
-                for (int w = 0; w < kWarpsPerBlock; ++w) v += hblock[(w * NDIM + d) * N + p];
+                for (int w = 0; w < kWarpsPerBlock; ++w) v += hist[(w * NDIM + d) * N + p];
             } else {
-                v = hblock[d * kStride + p];
+                v = hist[d * N + p];
             }
+        } else if (priv64) {
+            // the warps' copies, summed in warp order
+            const double *hist = reinterpret_cast<const double *>(sm.ew + NDIM * kStride);
+            v = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarpsPerBlock; ++w) v += hist[(w * NDIM + d) * N + k];
         } else {
             v = sm.h[d * kStride + k];
         }
-        if (v != Real(0)) atomicAdd(&A.H[d * N + k], (double)v);
+        if (parts) ph[d * N + k] = v;
+        else if (v != Real(0)) atomicAdd(&A.H[d * N + k], (double)v);
     }
+    if (parts) last_block_sums(A.part_S, A.part_ticket, A.S1, A.S2, ncomp);
 }
 
 template <int NDIM, typename Real, bool POW2>
@@ -814,14 +1138,14 @@ k_batch_sample(const BatchSampleArgs B)
     const int stride = B.stride;
     Smem<float> sm;
     sm.stride = stride;
-    sm.hs = stride;
-    sm.ew = reinterpret_cast<float2 *>(smem_raw);
+    sm.ew = align_table(smem_raw, stride);
     float *hist = reinterpret_cast<float *>(sm.ew + NDIM * stride);  // [kWarpsPerBlock][NDIM][stride]
     __shared__ __align__(16) SampleArgs<float> A;
     __shared__ int s_tile;
     __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int hsize = NDIM * stride;
+    const int hsize = NDIM * stride;  // floats per warp copy
+    sm.h = hist + warp * hsize;
     for (int i = threadIdx.x; i < kWarpsPerBlock * hsize; i += blockDim.x) hist[i] = 0.0f;
     int cur = -1;
     for (;;) {
@@ -842,15 +1166,10 @@ k_batch_sample(const BatchSampleArgs B)
             for (int i = threadIdx.x; i < (int)(sizeof(SampleArgs<float>) / sizeof(int)); i += blockDim.x)
                 dst[i] = src[i];
             __syncthreads();
-            const int N = A.nbins;
-            for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
-                const int d = idx / N, sl = idx - d * N;
-                const int k = bin_of_slot(sl, A.map);
-                const double *e = it.edges + (size_t)d * (N + 1);
-                const int p = d * stride + sl;
-                const double w = e[k + 1] - e[k];
-                sm.ew[p] = make_float2(__double2float_rn(e[k] - w), __double2float_rn(POW2 ? (double)N * w : w));
-            }
+            stage_grid_f32(sm.ew, NDIM, A.nbins, stride, it.edges, A.map);
+            // (the grid and histogram bases are multiples of 8 stride and
+            // 4 stride, stride a multiple of this integral's N)
+            set_addresses(sm, POW2 ? A.map.L : 0);
             cur = tile.item;
             __syncthreads();
         }
@@ -861,9 +1180,8 @@ k_batch_sample(const BatchSampleArgs B)
         const unsigned per = ((((unsigned)tile.nblk + kWarpsPerBlock - 1) / kWarpsPerBlock) + 1u) & ~1u;
         const unsigned long long w0 = tile.q0 + (unsigned long long)warp * per;
         const unsigned long long w1 = min(w0 + per, tile.q0 + (unsigned long long)tile.nblk);
+        const int hmode = A.map.priv ? kHistWarpPlain : kHistWarpAtomic;
         if (w0 < w1) {
-            Smem<float> smw = sm;
-            smw.h = hist + warp * hsize;
             unsigned X[NDIM];
             sobol_skip<NDIM, unsigned>(X, w0, lane, POW2 ? A.map.li : 0);
             if (A.gen == kGenScrambled) {
@@ -872,9 +1190,9 @@ k_batch_sample(const BatchSampleArgs B)
             }
             const bool interior = (w0 * 32ull >= start) && (w1 * 32ull <= end) && !((w0 | w1) & 1ull);
             if (interior)
-                run_steps<NDIM, float, POW2, false>(A, smw, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
+                run_steps<NDIM, float, POW2, false>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, hmode, s1, s2);
             else
-                run_steps<NDIM, float, POW2, true>(A, smw, X, w0, (unsigned)(w1 - w0), start, end, lane, s1, s2);
+                run_steps<NDIM, float, POW2, true>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, hmode, s1, s2);
         }
         const int ncomp = A.g.ncomp;
 #pragma unroll
@@ -903,8 +1221,9 @@ k_batch_sample(const BatchSampleArgs B)
             float v = 0.0f;
 #pragma unroll
             for (int w = 0; w < kWarpsPerBlock; ++w) {
-                v += hist[w * hsize + p];
-                hist[w * hsize + p] = 0.0f;
+                float &e = hist[w * hsize + p];
+                v += e;
+                e = 0.0f;
             }
             if (v != 0.0f) atomicAdd(&it.H[d * N + bin_of_slot(sl, A.map)], (double)v);
         }
@@ -934,9 +1253,11 @@ k_genz_points(const __grid_constant__ GenzParams<Real> g, const Real *x, Real *f
 {
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (long long)gridDim.x * blockDim.x) {
+        // (FP32 evaluates at the centred coordinate x - 1/2, FP64 at x)
+        const Real c = sizeof(Real) == 4 ? Real(0.5) : Real(0);
         Real xx[NDIM];
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) xx[d] = AOS ? x[j * NDIM + d] : x[(long long)d * ld + j];
+        for (int d = 0; d < NDIM; ++d) xx[d] = (AOS ? x[j * NDIM + d] : x[(long long)d * ld + j]) - c;
         Real v[CV_MAX_COMP];
         v[0] = genz_eval<NDIM, 0>(g, xx);
         if (g.ncomp > 1) v[1] = genz_eval<NDIM, 1>(g, xx);

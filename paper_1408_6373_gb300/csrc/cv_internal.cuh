@@ -45,13 +45,19 @@ struct DevState {
 };
 
 // Per-component integrand parameters in the precision of the evaluation,
-// pre-transformed on the host so the inner loop is FMA-shaped:
-//   oscillatory   p0 = a/(2 pi) (turns) [FP32] or a [FP64];  q0 = u_1 or 2 pi u_1
-//   product peak  p0 = 1/a^2, p1 = u
-//   corner peak   p0 = a
-//   gaussian      p0 = a, p1 = a u [FP32];  p0 = a^2, p1 = u [FP64]
-//   c0            p0 = a, p1 = u
-//   discontinuous p0 = a, p1 = u
+// pre-transformed on the host so the inner loop is FMA-shaped.  FP64 takes
+// x in [0, 1]:
+//   oscillatory   p0 = a, q0 = 2 pi u_1;  product peak p0 = 1/a^2, p1 = u
+//   corner peak   p0 = a;  gaussian p0 = a^2, p1 = u
+//   c0, discontinuous p0 = a, p1 = u
+// FP32 takes the centred coordinate z = x - 1/2 and base-2 exponents
+// (l = log2 e; pairs q0 + q1 carry a constant to twice binary32 precision):
+//   oscillatory   p0 = a/(2 pi) (turns); q0 + q1 = u_1 + sum a/(4 pi), mod 1
+//   product peak  p0 = 1/a^2, p1 = 1/2 - u
+//   corner peak   p0 + p1 = a (high and low halves), taken on x = z + 1/2
+//   gaussian      p0 = a sqrt(l), p1 = a sqrt(l) (1/2 - u)
+//   c0            p0 = a l, p1 = 1/2 - u
+//   discontinuous p0 = a l, p1 = u - 1/2, q0 = exp(sum a / 2)
 template <typename Real>
 struct GenzParams {
     int ndim;
@@ -62,6 +68,7 @@ struct GenzParams {
     alignas(16) Real p0[CV_MAX_COMP][CV_MAX_DIM];
     alignas(16) Real p1[CV_MAX_COMP][CV_MAX_DIM];
     Real q0[CV_MAX_COMP];
+    Real q1[CV_MAX_COMP];           // FP32: the low half of a constant held as q0 + q1
     int delay;                      // extra dependent FMAs per evaluation (cost knob)
 };
 
@@ -117,12 +124,31 @@ __host__ __device__ inline void philox4x64_10(unsigned long long (&c)[4], unsign
 struct MapParams {
     int pow2;                       // N = 2^L with L >= 5: the bit-level map below
     int L;                          // log2 N
-    unsigned mF;                    // mantissa bits of frac in the permuted word
-    unsigned expL;                  // exponent field of 2^-L
+    unsigned mF;                    // the fraction's mantissa bits in the permuted word
+    unsigned expE;                  // exponent field of 2^(G - L)
     int li;                         // direction table: L - 4 (permuted words), else 0
-    unsigned sK;                    // slot = permuted word >> sK, sK = 32 - L
+    unsigned sA;                    // byte offset of the bin's grid entry = word >> sA, sA = 29 - L
+    int G;                          // the fraction sits 2^-G below the mantissa's top (G = max(0, L - 6))
     int priv;                       // per-warp f^2 histograms updated without atomics
 };
+
+// The FP32 sampling kernels' table entry of a bin with left edge e and
+// width w (both FP64), each half rounded once to binary32.  The kernels map
+// to the centred coordinate x - 1/2 (binary32 keeps absolute precision
+// near 0, so the integrands' sums over coordinates round far less than over
+// [0, 1] values): x - 1/2 = fma(s w, f1, e - c w - 1/2), f1 the mantissa
+// construction of the fraction, c = 2^G and s = N for the power-of-two map,
+// c = s = 1 for the general one (where the kernel multiplies J by N).
+__host__ __device__ __forceinline__ float2 grid_entry_f32(double e, double w, int N, const MapParams &m)
+{
+    const double c = m.pow2 ? (double)(1 << m.G) : 1.0;
+    const double s = m.pow2 ? (double)N : 1.0;
+#if defined(__CUDA_ARCH__)
+    return make_float2(__double2float_rn(e - c * w - 0.5), __double2float_rn(s * w));
+#else
+    return make_float2((float)(e - c * w - 0.5), (float)(s * w));
+#endif
+}
 
 // Grid slot of bin k of an axis (and back).  Power-of-two N >= 32: the bit
 // permutation of the direction words puts bin bits (y_6..y_L) above y_5 above
@@ -179,7 +205,26 @@ struct SampleArgs {
     int gen;
     unsigned long long seed;
     unsigned long long shift[CV_MAX_DIM];
+    // Deterministic reduction (part_S non-null; the launch's grid must be
+    // part_G blocks): block b writes its sums to part_S[b][2 c + {0, 1}] and
+    // its histogram to part_H[b][ndim][nbins] (Real), no atomics; the last
+    // block to finish (a ticket, zero before the launch and reset by that
+    // block) adds the blocks' sums to S1, S2 in block order, and the
+    // histogram partials are summed per bin in block order by the kernel
+    // that consumes them (refinement, or a reduction after a plain pass).
+    // Null: FP64 atomics, whose order varies from run to run.
+    double *part_S;                 // [part_G][2 CV_MAX_COMP]
+    void *part_H;                   // [part_G][ndim][nbins]
+    unsigned *part_ticket;
+    int part_G;
 };
+
+// Bytes of the per-block partials of a deterministic pass.
+inline size_t pass_parts_bytes(int G, int ndim, int nbins, bool fp64)
+{
+    return (size_t)G * 2 * CV_MAX_COMP * sizeof(double) +
+           (size_t)G * ndim * nbins * (fp64 ? sizeof(double) : sizeof(float)) + 256;
+}
 
 struct CombineArgs {
     DevState *st;
@@ -189,6 +234,12 @@ struct CombineArgs {
     double *log_I;                  // [log_cap][CV_MAX_COMP] or null
     double *log_var;
     int log_cap;                    // iterations the log holds (<= kLogCap)
+    // the sampling pass's histogram partials (SampleArgs::part_H), summed by
+    // the refinement in block order; null: the pass added them to H itself
+    const void *part_H;
+    int part_G;
+    int part_nh;                    // ndim * nbins: values per block
+    int part_f32;                   // partials are floats (FP32 pass)
 };
 
 // ---- batched persistent launch (many integrals) ----
@@ -217,9 +268,10 @@ struct BatchSampleArgs {
 };
 
 // Shared memory of a batched sampling block: grid e, w and one f^2
-// histogram per warp, `stride` slots per axis each.
+// histogram per warp, `stride` slots per axis each, and 8 stride bytes to
+// align the grid for the kernels' funnel-shift addressing.
 inline size_t batch_smem_bytes(int ndim, int stride) {
-    return (size_t)(2 + kWarpsPerBlock) * ndim * stride * sizeof(float);
+    return (size_t)(2 + kWarpsPerBlock) * ndim * stride * sizeof(float) + 8 * (size_t)stride;
 }
 
 #if !defined(__CUDACC_RTC__)
@@ -248,6 +300,8 @@ cudaError_t launch_genz_points(const GenzParams<Real> &g, const Real *x, Real *f
 
 // cv_refine.cu
 cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, cudaStream_t s);
+// H[i] += the G blocks' partials of bin i (nh bins), in block order
+cudaError_t launch_add_parts(const void *part_H, int G, int f32, int nh, double *H, cudaStream_t s);
 // (ew32, map: when ew32 is non-null the kernels also write the FP32 grid
 // table of SampleArgs::ew32 for the grid they leave, in map's slot order)
 cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
@@ -283,18 +337,27 @@ int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow
 int jit_compile_check(const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks, std::string *err);
 cudaError_t launch_jit_sample(const JitKernel &k, const SampleArgs<float> &a, int grid, cudaStream_t s);
 int jit_info(int *compiled);
+// cv_api.cu: the parameters of a built-in integrand in the kernels' forms
+template <typename Real>
+void fill_genz_params(const cv_genz *g, GenzParams<Real> *p);
 // cv_api.cu: the FP32 path's range precondition for built-in integrands
 // (first failing component and a message, or -1)
 int fp32_range_check(const cv_genz *g, char *msg, size_t len);
 #endif  // !__CUDACC_RTC__
 
-// Shared memory of a sampling block: the grid {e, w} with CV_MAX_BINS slots
-// per axis, then either one block histogram (CV_MAX_BINS slots per axis) or,
-// with private histograms, one copy of nbins slots per axis for each warp.
+// Shared memory of a sampling block.  FP64: grid {e, w} with CV_MAX_BINS
+// slots per axis, then the block's histogram with CV_MAX_BINS slots per
+// axis or, with private histograms, one [ndim][nbins] copy per warp.  FP32: the grid table [ndim][nbins] (8-byte
+// entries, aligned to 8 nbins bytes), then either one block histogram
+// [ndim][nbins] of floats or, with private histograms, one such copy per
+// warp.
 inline size_t sample_smem_bytes(int ndim, int nbins, bool fp64, bool priv) {
-    if (fp64) return (size_t)ndim * CV_MAX_BINS * 3 * sizeof(double);
-    return (size_t)ndim * CV_MAX_BINS * 2 * sizeof(float) +
-           (priv ? (size_t)kWarpsPerBlock * ndim * nbins : (size_t)ndim * CV_MAX_BINS) * sizeof(float);
+    if (fp64)
+        return (size_t)ndim * CV_MAX_BINS * 2 * sizeof(double) +
+               (priv ? (size_t)kWarpsPerBlock * ndim * nbins : (size_t)ndim * CV_MAX_BINS) * sizeof(double);
+    return (size_t)ndim * nbins * 2 * sizeof(float) +
+           (priv ? (size_t)kWarpsPerBlock * ndim * nbins : (size_t)ndim * nbins) * sizeof(float) +
+           8 * (size_t)nbins;  // (to align the grid to 8 nbins bytes)
 }
 
 // Resident 256-thread blocks per SM the FP32 sampling kernels are compiled
@@ -324,37 +387,53 @@ inline MapParams make_map(int N, int ndim, bool fp64)
         int L = 0;
         while ((1 << L) < N) ++L;
         m.L = L;
-        m.mF = 0x7fffffu & ~((1u << L) - 1u);
-        m.expL = (unsigned)(127 - L) << 23;
+        // (the layout slot_perm writes: slot, three zero bits, the 23 - L
+        // fraction bits from mantissa bit `top` down)
+        const int top = 28 - L < 22 ? 28 - L : 22;
+        const int F = 23 - L;
+        m.G = 22 - top;
+        m.mF = ((1u << F) - 1u) << (top - F + 1);
+        m.expE = (unsigned)(127 + m.G - L) << 23;
         m.li = L - 4;
-        m.sK = 32 - L;
+        m.sA = 29 - L;
         const int blocks = min_blocks_f32(ndim);
-        m.priv = !fp64 &&
-                 (size_t)blocks * (sample_smem_bytes(ndim, N, false, true) + kSmemBlockReserve) <= kSmemPerSM;
+        // (FP64: the kernel is compiled for one block per SM; its copies must
+        // still leave room for a second)
+        m.priv = fp64 ? 2 * (sample_smem_bytes(ndim, N, true, true) + kSmemBlockReserve) <= kSmemPerSM
+                      : (size_t)blocks * (sample_smem_bytes(ndim, N, false, true) + kSmemBlockReserve) <= kSmemPerSM;
     }
     return m;
 }
 
-// The bit permutation of the FP32 direction words for N = 2^L (5 <= L <= 8):
-// with y_t the bit of weight 2^-t of w / 2^32, the slot bits
-// (y_6..y_L, y_5, y_1..y_4) go to the top L bits, y_(L+1)..y_23 to mantissa
-// bits 22..L, and y_24..y_32 fill the rest (the layout the table generator
-// writes).  A digital shift of the scrambled generator is permuted the same
-// way, since a permutation commutes with XOR.
+// The bit layout of the FP32 direction words for N = 2^L (5 <= L <= 8),
+// a linear map of the word's bits (it commutes with XOR, so a point's word
+// is the map of its unmapped word).  With y_t the bit of weight 2^-t of
+// w / 2^32:
+//   bits 31..32-L   the bin's slot (y_6..y_L, y_5, y_1..y_4),
+//   bits 31-L..29-L zero, so that word >> (29 - L) is the slot times 8, the
+//                   byte offset of the bin's 8-byte grid entry,
+//   y_(L+1)..y_23   the fraction within the bin, at mantissa bits
+//                   top .. top - 22 + L with top = min(22, 28 - L),
+//   y_24..y_29      the remaining bits; y_30..y_32 are dropped
+// (the FP32 path's coordinate keeps 23 bits).  A digital shift of the
+// scrambled generator is mapped the same way.
 inline unsigned slot_perm(unsigned w, int L)
 {
+    const int top = 28 - L < 22 ? 28 - L : 22;
+    unsigned used = 0;
     unsigned out = 0;
-    for (int t = 1; t <= 32; ++t) {
-        const unsigned bit = (w >> (32 - t)) & 1u;
-        int pos;
-        if (t <= 4) pos = 32 - L + (4 - t);
-        else if (t == 5) pos = 32 - L + 4;
-        else if (t <= L) pos = 37 - t;
-        else if (t <= 23) pos = 23 + L - t;
-        else if (t <= 32 - L) pos = 55 - L - t;
-        else pos = 32 - t;
-        out |= bit << pos;
-    }
+    int pos[33];
+    for (int t = 1; t <= 32; ++t) pos[t] = -1;
+    for (int t = 1; t <= 4; ++t) pos[t] = 32 - L + (4 - t);
+    pos[5] = 32 - L + 4;
+    for (int t = 6; t <= L; ++t) pos[t] = 37 - t;
+    for (int t = L + 1; t <= 23; ++t) pos[t] = top - (t - L - 1);
+    for (int t = 1; t <= 23; ++t) used |= 1u << pos[t];
+    used |= 7u << (29 - L);
+    int t = 24;
+    for (int b = 31; b >= 0 && t <= 29; --b)
+        if (!((used >> b) & 1u)) pos[t++] = b;
+    for (int u = 1; u <= 29; ++u) out |= ((w >> (32 - u)) & 1u) << pos[u];
     return out;
 }
 

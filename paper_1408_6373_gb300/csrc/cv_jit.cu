@@ -110,12 +110,18 @@ std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, 
         }
         s += "}; return v[C][d]; }\n";
     }
-    s += "  template <int C> __device__ __forceinline__ static float q0(const GenzParams<float>&) { constexpr float v[4] = {";
-    for (int c = 0; c < 4; ++c) {
-        hexf(s, c < g.ncomp ? g.q0[c] : 0.0f);
-        if (c < 3) s += ",";
+    const float *qs[2] = {g.q0, g.q1};
+    const char *qnames[2] = {"q0", "q1"};
+    for (int t = 0; t < 2; ++t) {
+        s += "  template <int C> __device__ __forceinline__ static float ";
+        s += qnames[t];
+        s += "(const GenzParams<float>&) { constexpr float v[4] = {";
+        for (int c = 0; c < 4; ++c) {
+            hexf(s, c < g.ncomp ? qs[t][c] : 0.0f);
+            if (c < 3) s += ",";
+        }
+        s += "}; return v[C]; }\n";
     }
-    s += "}; return v[C]; }\n";
     s += "  __device__ __forceinline__ static constexpr int delay(const GenzParams<float>&) { return " +
          std::to_string(g.delay) + "; }\n";
     s += "  __device__ __forceinline__ static constexpr int table(const MapParams&) { return " +

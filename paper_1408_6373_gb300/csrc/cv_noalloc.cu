@@ -80,42 +80,6 @@ struct DeviceGuard {
     }
 };
 
-const double kTwoPi = 6.283185307179586476925286766559;
-
-template <typename Real>
-void fill(const cv_genz *g, cv::GenzParams<Real> *p)
-{
-    memset(p, 0, sizeof(*p));
-    p->ndim = g->ndim;
-    p->delay = g->delay;
-    p->ncomp = g->ncomp;
-    const bool f32 = sizeof(Real) == 4;
-    for (int c = 0; c < g->ncomp; ++c) {
-        const int fam = g->family[c];
-        p->family[c] = fam;
-        for (int d = 0; d < g->ndim; ++d) {
-            const double a = g->a[c][d], u = g->u[c][d];
-            double p0 = 0.0, p1 = 0.0;
-            switch (fam) {
-            case CV_OSCILLATORY: p0 = f32 ? a / kTwoPi : a; break;
-            case CV_PRODUCT_PEAK: p0 = 1.0 / (a * a); p1 = u; break;
-            case CV_CORNER_PEAK: p0 = a; break;
-            case CV_GAUSSIAN:
-                if (f32) { p0 = a; p1 = a * u; }
-                else { p0 = a * a; p1 = u; }
-                break;
-            case CV_C0:
-            case CV_DISCONTINUOUS: p0 = a; p1 = u; break;
-            default: break;
-            }
-            p->p0[c][d] = (Real)p0;
-            p->p1[c][d] = (Real)p1;
-        }
-        if (fam == CV_OSCILLATORY)
-            p->q0[c] = (Real)(f32 ? g->u[c][0] : kTwoPi * g->u[c][0]);
-    }
-}
-
 #define CV_NA_FOR_EACH_NDIM(X)                                                               \
     X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) \
     X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30)    \
@@ -150,7 +114,7 @@ cudaError_t run(const cv_genz *g, int nbins, int flags, unsigned long long seed,
 {
     cv::SampleArgs<Real> a;
     memset(&a, 0, sizeof(a));
-    fill<Real>(g, &a.g);
+    cv::fill_genz_params<Real>(g, &a.g);
     a.nbins = nbins;
     a.chunk_min = 4;
     a.map = cv::make_map(nbins, g->ndim, sizeof(Real) == 8);
@@ -246,7 +210,7 @@ extern "C" int cv_vegas_noalloc(int device, void *stream, int ndim, int ncomp, c
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return CV_ECUDA;
 
-    cv::CombineArgs ca;
+    cv::CombineArgs ca = {};
     ca.st = st;
     ca.ncomp = ncomp;
     ca.epsrel = epsrel;

@@ -55,19 +55,15 @@ __device__ double gamma_p(double a, double x)
 }
 
 // The FP32 sampling kernel's table of bins [k0, N) of axis d (step dk),
-// from the FP64 edges: {e_k - w_k, w_k} with w_k = e_(k+1) - e_k, w_k scaled
-// by N for the bit-level map, each rounded once to FP32, at the bin's slot.
-// The same FP64 operations the sampling kernel applies when it converts the
-// grid itself, so either way it samples with the same values.
+// from the FP64 edges: grid_entry_f32 of each bin at its slot.  The same
+// FP64 operations the sampling kernel applies when it converts the grid
+// itself, so either way it samples with the same values.
 __device__ __forceinline__ void stage_axis(int d, int N, const double *edges, float2 *ew32, const MapParams &map,
                                            int k0, int dk)
 {
     const double *e = edges + (size_t)d * (N + 1);
-    for (int k = k0; k < N; k += dk) {
-        const double w = e[k + 1] - e[k];
-        ew32[(size_t)d * N + slot_of_bin(k, map)] =
-            make_float2(__double2float_rn(e[k] - w), __double2float_rn(map.pow2 ? (double)N * w : w));
-    }
+    for (int k = k0; k < N; k += dk)
+        ew32[(size_t)d * N + slot_of_bin(k, map)] = grid_entry_f32(e[k], e[k + 1] - e[k], N, map);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v)
@@ -96,8 +92,34 @@ __device__ __forceinline__ long long warp_max_bits(long long v)
 // 1.5 ulp of the quotient).  FP64 results take ~200 cycles here, so the
 // refinement is bound by its chain of dependent FP64 operations: maxima
 // and searches over non-negative doubles compare bit patterns instead.
+// Bin `off` of the G blocks' partial histograms (stride `stride` values
+// between blocks), summed in block order: FP32 partials in four interleaved
+// Kahan sums in FP32 (FP64 throughput is a small fraction of FP32 here),
+// FP64 partials in four plain FP64 sums; the four are then added in a fixed
+// order in FP64.  Deterministic: the same partials give the same bits.
+__device__ __forceinline__ double sum_parts(const void *part_H, int G, int f32, size_t stride, size_t off)
+{
+    if (f32) {
+        const float *p = static_cast<const float *>(part_H) + off;
+        float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int b = 0; b < G; ++b) {
+            const int j = b & 3;
+            const float y = p[(size_t)b * stride] - c[j];
+            const float t = s[j] + y;
+            c[j] = (t - s[j]) - y;
+            s[j] = t;
+        }
+        return (((double)s[0] - (double)c[0]) + ((double)s[1] - (double)c[1])) +
+               (((double)s[2] - (double)c[2]) + ((double)s[3] - (double)c[3]));
+    }
+    const double *p = static_cast<const double *>(part_H) + off;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < G; ++b) s[b & 3] += p[(size_t)b * stride];
+    return (s[0] + s[1]) + (s[2] + s[3]);
+}
+
 __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_hist, float2 *ew32 = nullptr,
-                            const MapParams *map = nullptr)
+                            const MapParams *map = nullptr, const CombineArgs *pa = nullptr)
 {
     double *Hd = H + (size_t)d * N;
     double *e = edges + (size_t)d * (N + 1);
@@ -110,7 +132,13 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
     const int nw = blockDim.x >> 5;
     const double invN = __drcp_rn((double)N);  // (off the dependent chain)
 
-    if (k < N) sH[k] = Hd[k];
+    if (k < N) {
+        if (pa && pa->part_H) {
+            sH[k] = sum_parts(pa->part_H, pa->part_G, pa->part_f32, (size_t)pa->part_nh, (size_t)d * N + k);
+        } else {
+            sH[k] = Hd[k];
+        }
+    }
     for (int i = k; i <= N; i += blockDim.x) se[i] = e[i];
     __syncthreads();
     const bool bad = k < N && !isfinite(sH[k]);
@@ -203,6 +231,41 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
     if (ew32) {
         __syncthreads();  // (the new edges of this axis, written by every thread)
         stage_axis(d, N, edges, ew32, *map, k, blockDim.x);
+    }
+}
+
+// After a deterministic standalone pass: H[i] += the G blocks' partials of
+// bin i.  32 bins per CTA, 8 threads per bin: thread j sums the blocks
+// b = j (mod 8) in order (Kahan in FP32 for FP32 partials, FP64 else), and
+// the 8 results are added in j order -- a fixed order, so deterministic.
+__global__ void __launch_bounds__(256) k_add_parts(const void *part_H, int G, int f32, int nh, double *H)
+{
+    __shared__ double part[8][32];
+    const int bin = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + bin;
+    double v = 0.0;
+    if (i < nh) {
+        if (f32) {
+            const float *p = static_cast<const float *>(part_H) + i;
+            float s = 0.0f, c = 0.0f;
+            for (int b = j; b < G; b += 8) {
+                const float y = p[(size_t)b * nh] - c;
+                const float t = s + y;
+                c = (t - s) - y;
+                s = t;
+            }
+            v = (double)s - (double)c;
+        } else {
+            const double *p = static_cast<const double *>(part_H) + i;
+            for (int b = j; b < G; b += 8) v += p[(size_t)b * nh];
+        }
+    }
+    part[j][bin] = v;
+    __syncthreads();
+    if (j == 0 && i < nh) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += part[q][bin];
+        H[i] += t;
     }
 }
 
@@ -323,7 +386,7 @@ __global__ void __launch_bounds__(256)
 k_refine_combine(int ndim, int N, double *H, double *edges, const CombineArgs A, float2 *ew32, MapParams map)
 {
     if (!*(volatile const int *)&A.st->pass_active) return;
-    if ((int)blockIdx.x < ndim) refine_axis(blockIdx.x, N, H, edges, 1, ew32, &map);
+    if ((int)blockIdx.x < ndim) refine_axis(blockIdx.x, N, H, edges, 1, ew32, &map, &A);
     else combine_iteration(A);
 }
 
@@ -447,6 +510,12 @@ cudaError_t launch_stage_grid(int ndim, int nbins, const double *edges, float2 *
 // Threads of a refinement CTA: the bins rounded up to whole warps, at least
 // two warps (the combination CTA of k_refine_combine needs one).
 static int refine_threads(int nbins) { return nbins <= 64 ? 64 : (nbins + 31) / 32 * 32; }
+
+cudaError_t launch_add_parts(const void *part_H, int G, int f32, int nh, double *H, cudaStream_t s)
+{
+    k_add_parts<<<(nh + 31) / 32, 256, 0, s>>>(part_H, G, f32, nh, H);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_refine(int ndim, int nbins, double *H, double *edges, cudaStream_t s)
 {

@@ -59,35 +59,42 @@ def direction_words(ndim: int) -> list:
     return table
 
 
-def slot_perm(w32: int, L: int) -> int:
-    """Bit permutation of a 32-bit word for N = 2^L bins, 5 <= L <= 8.
+def slot_positions(L: int) -> dict:
+    """Bit position of y_t (t = 1..29) in the mapped 32-bit word for
+    N = 2^L bins, 5 <= L <= 8.
 
-    With y_t the bit of weight 2^-t of y = w / 2^32 (y_1 = bit 31), the
-    permuted word holds
-      bits 31..32-L  the bin's shared-memory slot
-                     s = (y_6 .. y_L) * 32 + y_5 * 16 + (y_1 .. y_4)
-      bits 22..L     y_(L+1) .. y_23, the fraction within the bin, at
-                     mantissa position
-      other bits     y_24 .. y_32 (unused)
-    so the slot is word >> (32 - L) and the fraction's mantissa bits are
-    word & 0x7fffff & ~(N - 1).
+    With y_t the bit of weight 2^-t of y = w / 2^32 (y_1 = bit 31):
+      bits 31..32-L     the bin's shared-memory slot
+                        s = (y_6 .. y_L) * 32 + y_5 * 16 + (y_1 .. y_4)
+      bits 31-L..29-L   zero, so word >> (29 - L) = 8 s, the byte offset of
+                        the bin's 8-byte grid entry
+      y_(L+1) .. y_23   the fraction within the bin, at mantissa bits
+                        top .. top - 22 + L, top = min(22, 28 - L)
+      y_24 .. y_29      the free positions from the top down
+    y_30 .. y_32 are dropped (the FP32 coordinate keeps 23 bits); the map is
+    linear over GF(2), so it commutes with the XOR recurrence.
     """
+    top = min(22, 28 - L)
+    pos = {}
+    for t in range(1, 5):
+        pos[t] = 32 - L + (4 - t)
+    pos[5] = 32 - L + 4
+    for t in range(6, L + 1):
+        pos[t] = 37 - t
+    for t in range(L + 1, 24):
+        pos[t] = top - (t - L - 1)
+    used = set(pos.values()) | {31 - L, 30 - L, 29 - L}
+    free = [b for b in range(31, -1, -1) if b not in used]
+    for t, b in zip(range(24, 30), free):
+        pos[t] = b
+    return pos
+
+
+def slot_perm(w32: int, L: int) -> int:
+    """The mapped word of slot_positions(L)."""
     out = 0
-    for t in range(1, 33):
-        bit = (w32 >> (32 - t)) & 1
-        if t <= 4:
-            pos = 32 - L + (4 - t)
-        elif t == 5:
-            pos = 32 - L + 4
-        elif t <= L:
-            pos = 37 - t
-        elif t <= 23:
-            pos = 23 + L - t
-        elif t <= 32 - L:
-            pos = 55 - L - t
-        else:
-            pos = 32 - t
-        out |= bit << pos
+    for t, b in slot_positions(L).items():
+        out |= ((w32 >> (32 - t)) & 1) << b
     return out
 
 
@@ -118,7 +125,10 @@ def main():
     check_against_scipy(table)
     steps = [step_form(words) for words in table]
     for L in (5, 6, 7, 8):
-        assert sorted(slot_perm(1 << b, L) for b in range(32)) == [1 << b for b in range(32)]
+        pos = slot_positions(L)
+        # 29 source bits to 29 distinct positions, the three gap bits never set
+        assert len(set(pos.values())) == 29 and not {31 - L, 30 - L, 29 - L} & set(pos.values())
+        assert all(slot_perm(1 << (32 - t), L) == 1 << b for t, b in pos.items())
     for words, w in zip(table, steps):
         assert [x if k < 5 else x ^ w[4] for k, x in enumerate(w)] == words
     lines = [
@@ -128,8 +138,8 @@ def main():
         " * V[d][k] = m_{d,k+1} << (63-k), the direction number of Gray-code index",
         " * bit k in dimension d as a 64-bit fraction, entry [d][k] is V[d][k] for",
         " * k < 5 and V[d][4] ^ V[d][k] for k >= 5; as 64-bit words (W64) and as",
-        " * their top 32 bits (W32P[0]), also bit-permuted for N = 2^L bins,",
-        " * L = 5..8 (W32P[L - 4]; see slot_perm in the generator). */",
+        " * their top 32 bits (W32P[0]), also bit-mapped for N = 2^L bins,",
+        " * L = 5..8 (W32P[L - 4]; see slot_positions in the generator). */",
         "#pragma once",
         f"#define CV_SOBOL_DIMS {MAX_DIM}",
         f"#define CV_SOBOL_BITS {NBITS}",

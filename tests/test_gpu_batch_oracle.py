@@ -105,15 +105,23 @@ def test_batched_second_iteration_on_refined_grid_matches_oracle(runs):
 def test_batched_refinement_follows_the_oracle(runs):
     # the batch's refined grid against the oracle's refinement of the
     # oracle's own histogram: they differ only through the FP32 histogram
-    # (1e-5 of a bin's share at most), so edges agree to 1e-5 of the bin
+    # (1e-5 of a bin's share at most), so edges agree to 1e-5 of the bin.
+    # A pass with boundary mass (a point a binary32 evaluation may put on
+    # the other side of a cut) can move a whole point's weight between
+    # bins, so those are left to the sum checks above.
     items, _, grids = runs
+    checked = 0
     for i, item in enumerate(items):
         nd, f, N, n, _, _ = item
         if n < 50000:
             continue
         ob = _oracle(item, O.grid_uniform(nd, N), 1)
+        if ob.B2[0] > 0:
+            continue
         ref = O.refine(O.grid_uniform(nd, N), ob.H)
         assert np.max(np.abs(grids[i] - ref)) <= 1e-5 / N, (i, nd, f, N)
+        checked += 1
+    assert checked >= 10
 
 
 def test_autotuned_tiles_and_alone_runs_match_oracle(ctx, runs):

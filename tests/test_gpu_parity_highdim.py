@@ -22,6 +22,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_1408_6373_gb300 as cg  # noqa: E402
+from paper_1408_6373_gb300 import workloads as W  # noqa: E402
 
 THREADS = os.cpu_count() or 1
 
@@ -55,12 +56,13 @@ def ctx():
 def _inputs(case):
     ndim, nbins, fams, start, n = case
     rng = np.random.default_rng(1000 * ndim + nbins)
-    a = rng.uniform(0.3, 1.5, (len(fams), ndim))
-    a *= 8.0 / a.sum(axis=1, keepdims=True)
+    a = rng.uniform(0.5, 1.5, (len(fams), ndim))
     u = rng.uniform(0.1, 0.9, (len(fams), ndim))
     for c, f in enumerate(fams):
         if f in (O.C0, O.DISCONTINUOUS):
             a[c] = 0.5  # the large single integral's parameters
+        elif f == O.CORNER_PEAK:
+            a[c] = W.fp32_corner_peak(a[c])  # inside the FP32 path's range
     w = rng.uniform(0.2, 1.0, (ndim, nbins))
     cs = np.concatenate([np.zeros((ndim, 1)), np.cumsum(w, axis=1)], axis=1)
     edges = cs / cs[:, -1:]

@@ -75,7 +75,7 @@ def test_noalloc_leaves_the_current_device_and_takes_a_side_stream(ctx):
     assert torch.cuda.current_device() == before
     np.testing.assert_allclose(r.integral, ref.integral, rtol=1e-12)
     with pytest.raises(cg.CubaGpuError) as ei:
-        cg.vegas_noalloc(g, device=torch.cuda.device_count(), **kw)  # no such device
+        cg.vegas_noalloc(g, device=torch.cuda.device_count(), stream=side.cuda_stream, **kw)  # no such device
     assert ei.value.code == cg.EINVAL
     assert torch.cuda.current_device() == before
 
