@@ -160,6 +160,88 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside), "period_ms": 20, "basis": basis}
 
 
+class NvmlClockSampler:
+    """The same record as ClockSampler, read through NVML (libnvidia-ml,
+    loaded with ctypes) every 2 ms by a host thread: the SM clock, its
+    maximum and the active clock-event reasons (NVML's bit mask).  Only
+    reads: no setting of the GPU is touched."""
+    PERIOD_S = 0.002
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device_index: int):
+        import ctypes
+        import threading
+        uuid = _gpu_uuid(device_index)
+        if not uuid:
+            raise OSError("no device UUID")
+        self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle for " + uuid)
+        self.ct = ctypes
+        self.nv.nvmlDeviceGetCurrentClocksEventReasons  # (AttributeError on an older NVML)
+        if self._read() is None:
+            raise OSError("NVML clock queries failed")
+        self.samples = []
+        self.t0 = self.t1 = None
+        self.run = True
+        self.th = threading.Thread(target=self._loop, daemon=True)
+        self.th.start()
+        time.sleep(0.05)
+
+    def _read(self):
+        ct = self.ct
+        mhz, mx, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        ok = (self.nv.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0 and
+              self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(mx)) == 0 and
+              self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h, ct.byref(rs)) == 0)
+        return (time.time(), float(mhz.value), float(mx.value),
+                {nm for bit, nm in self.REASONS.items() if rs.value & bit}) if ok else None
+
+    def _loop(self):
+        while self.run:
+            r = self._read()
+            if r is not None:
+                self.samples.append(r)
+            time.sleep(self.PERIOD_S)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+        time.sleep(0.01)
+
+    def stop(self) -> dict:
+        self.run = False
+        self.th.join(timeout=2)
+        self.nv.nvmlShutdown()
+        inside = [x for x in self.samples if self.t0 is not None and self.t0 <= x[0] <= (self.t1 or x[0])]
+        basis = "NVML every 2 ms, samples inside the timed region"
+        if not inside and self.samples and self.t0 is not None:
+            mid = 0.5 * (self.t0 + (self.t1 or self.t0))
+            inside = [min(self.samples, key=lambda x: abs(x[0] - mid))]
+            basis = "NVML every 2 ms, nearest sample to the timed region"
+        reasons = set()
+        for x in inside:
+            reasons |= x[3]
+        return {"sm_mhz": statistics.median(x[1] for x in inside) if inside else None,
+                "sm_max_mhz": max(x[2] for x in inside) if inside else None,
+                "reasons": sorted(reasons), "samples": len(inside), "period_ms": 1e3 * self.PERIOD_S,
+                "basis": basis}
+
+
+def clock_sampler(device_index: int):
+    """NVML sampling where the driver library loads, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(device_index)
+    except (OSError, AttributeError):
+        return ClockSampler(device_index)
+
+
 def _gpu_uuid(idx: int):
     try:
         import torch
@@ -353,16 +435,20 @@ def accuracy_leg(line: dict, W, threads: int) -> dict:
                             "oracle_subset": {"integrals": len(idx), "max_diff_in_sigma": max(dz)}}
     if "serve" in line:
         raw = line["serve"].pop("_results")
-        zs, small = [], []
+        zs, z0, zero_err, small = [], [], 0, []
         for q, rc, neval in raw:
             for c, (I, E) in enumerate(rc):
                 x = O.genz_exact(q.families[c], np.asarray(q.a[c]), np.asarray(q.u[c]))
                 # the mixed-precision bound 1e-6 int |f| (|f| <= 1 for the oscillatory family)
                 floor = 1e-6 * (1.0 if q.families[c] == 0 else abs(x))
-                zs.append(abs(I - x) / (E + floor / 3) if E + floor > 0 else 0.0)
+                z = abs(I - x) / (E + floor / 3) if E + floor > 0 else 0.0
+                zs.append(z)
+                if c == 0:
+                    z0.append(z)
+                zero_err += E == 0.0
             if len(small) < 5 and neval <= 3 * 10 ** 5:
                 small.append((q, rc))
-        zs = np.array(zs)
+        zs, z0 = np.array(zs), np.array(z0)
         dz = []
         for q, rc in small:
             # the same request, goal and schedule (it stops where the GPU run stopped)
@@ -371,6 +457,9 @@ def accuracy_leg(line: dict, W, threads: int) -> dict:
                         nthreads=threads)
             dz.append(max(abs(I - o.integral[c]) / max(E, o.error[c]) for c, (I, E) in enumerate(rc)))
         out["serve"] = {"components": len(zs), "z_max": float(zs.max()), "within_3": float((zs <= 3).mean()),
+                        "component0": {"z_max": float(z0.max()), "within_3": float((z0 <= 3).mean()),
+                                       "basis": "the component whose histogram refines the grid"},
+                        "zero_error_components": int(zero_err),
                         "basis": "z with the FP32 floor 1e-6 int|f| added to 3 sigma; the grid follows component 0, "
                                  "so later components of a request can be sampled badly and their error "
                                  "underestimated by Vegas itself",
@@ -408,7 +497,9 @@ def legs_summary(line: dict) -> dict:
         s, a = line["serve"], acc.get("serve", {})
         out["serve"] = {"req_s": g(s["requests_per_s"]), "p50_ms": g(s["p50_ms"]), "p99_ms": g(s["p99_ms"]),
                         "Gsps": g(s["throughput"]["value"] / 1e9), "fifo_fp64_p50_ms": g(s["plain_fp64_fifo"]["p50_ms"]),
-                        "z_max": g(a.get("z_max"), 3), "within_3": g(a.get("within_3"), 4)}
+                        "z_max": g(a.get("z_max"), 3), "within_3": g(a.get("within_3"), 4),
+                        "c0_within_3": g(a.get("component0", {}).get("within_3"), 4),
+                        "oracle_dz": g(a.get("oracle_subset", {}).get("max_diff_in_sigma"), 2)}
     if "gaussian3d" in line:
         out["gaussian3d"] = {"us_it": g(line["gaussian3d"]["graph_us_per_iteration"]),
                              "z": g(acc.get("gaussian3d", {}).get("z"), 2)}
@@ -498,7 +589,7 @@ def run_ours(args):
         integ.run()
 
     # ---- device-timed steps (the clock sampler runs from before the warm-up)
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     for _ in range(args.warmup):
         flush.fill_(1)
         step()
@@ -1028,7 +1119,7 @@ def measure_serve(ctx, cg, W, duration: float = 1.0, rate: float = 2000.0,
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

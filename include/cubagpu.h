@@ -456,6 +456,18 @@ int cv_integral_step(cv_integral *I, int max_iter);
  * run stopped, Sobol index included. */
 int cv_integral_save(cv_integral *I, const char *path);
 int cv_integral_load(cv_integral *I, const char *path);
+/* The checks cv_integral_load makes before it copies anything to the
+ * device, on the host alone (no device, no context): the file must hold
+ * exactly one saved state of the problem `spec` (as above); each grid axis
+ * must run from 0 to 1 and increase strictly; the histogram must be finite
+ * and non-negative; and the saved counters must follow the schedule the
+ * spec implies -- iteration j of nstart + j nincrease points, neval the sum
+ * over the iterations done (at most maxeval), the next iteration's size and
+ * its first Sobol index 1 + the points sampled before it (the last
+ * iteration's points not yet counted once the run has stopped).  Returns
+ * CV_OK, or CV_EINVAL with the reason written to msg[len] (NUL-terminated;
+ * msg may be NULL when len is 0). */
+int cv_integral_check_file(const cv_spec *spec, const char *path, char *msg, int len);
 /* Grid reuse (the role of Vegas's gridno): replace the grid of I, after a
  * reset, with edges[ndim][nbins+1] (increasing from 0 to 1), e.g. the
  * refined grid of an earlier integral from cv_integral_grid. */

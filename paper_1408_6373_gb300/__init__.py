@@ -200,6 +200,7 @@ _SIGNATURES = {
     "cv_integral_step": (_i, [_vp, _i]),
     "cv_integral_save": (_i, [_vp, ctypes.c_char_p]),
     "cv_integral_load": (_i, [_vp, ctypes.c_char_p]),
+    "cv_integral_check_file": (_i, [_P(Spec), ctypes.c_char_p, ctypes.c_char_p, _i]),
     "cv_integral_set_grid": (_i, [_vp, _vp]),
     "cv_batch_create": (_i, [_vp, _i, _vp, _P(_vp)]),
     "cv_batch_run": (_i, [_vp]),
@@ -445,6 +446,14 @@ def vegas_noalloc(g: Genz, device: int = 0, stream=None, epsrel=0.0, epsabs=0.0,
     if rc != OK:
         raise CubaGpuError(rc, "cv_vegas_noalloc: " + lib().cv_strerror(rc).decode())
     return VegasResult(neval.value, fail.value, integral, error, prob)
+
+
+def check_state_file(sp: Spec, path: str):
+    """cv_integral_check_file: (ok, reason) for a file written by
+    Integral.save, checked against the problem sp on the host alone."""
+    buf = ctypes.create_string_buffer(512)
+    rc = lib().cv_integral_check_file(ctypes.byref(sp), os.fsencode(path), buf, len(buf))
+    return rc == OK, buf.value.decode(errors="replace")
 
 
 def jit_info():

@@ -1236,36 +1236,111 @@ extern "C" int cv_integral_save(cv_integral *I, const char *path)
     return CV_OK;
 }
 
+namespace {
+// A state file read into host memory.
+struct StateImage {
+    std::vector<char> st;
+    std::vector<double> e, H, lI, lV;
+};
+
+// Read a file written by cv_integral_save for the problem sp and check it
+// before anything reaches a device: the problem description, the grid (each
+// axis from 0 to 1, strictly increasing), the histogram (finite, >= 0) and
+// the counters of the saved run against the schedule sp implies -- iteration
+// j has nstart + j nincrease points, so after `iter` iterations neval is
+// their sum (at most maxeval), the next iteration's size follows, and the
+// next Sobol index is 1 + the points before it (the last iteration's own
+// points not yet counted once the run has stopped).  The reason for a
+// refusal goes to msg.
+int read_state_file(const cv_spec &sp, const char *path, StateImage *img, char *msg, size_t len)
+{
+    auto refuse = [&](const char *why) {
+        if (msg && len) snprintf(msg, len, "%s: %s", path, why);
+        return CV_EINVAL;
+    };
+    FILE *f = fopen(path, "rb");
+    if (!f) return refuse("cannot open");
+    StateFileHeader h, want;
+    fill_header(sp, &want);
+    const int ndim = sp.g.ndim, N = sp.nbins;
+    img->st.assign(sizeof(DevState), 0);
+    img->e.assign((size_t)ndim * (N + 1), 0.0);
+    img->H.assign((size_t)ndim * N, 0.0);
+    img->lI.assign((size_t)kLogCap * CV_MAX_COMP, 0.0);
+    img->lV.assign((size_t)kLogCap * CV_MAX_COMP, 0.0);
+    bool ok = fread(&h, sizeof(h), 1, f) == 1;
+    if (ok && memcmp(&h, &want, sizeof(h)) != 0) {
+        fclose(f);
+        return refuse("holds the state of another problem or format");
+    }
+    ok = ok && fread(img->st.data(), img->st.size(), 1, f) == 1 &&
+         fread(img->e.data(), sizeof(double), img->e.size(), f) == img->e.size() &&
+         fread(img->H.data(), sizeof(double), img->H.size(), f) == img->H.size() &&
+         fread(img->lI.data(), sizeof(double), img->lI.size(), f) == img->lI.size() &&
+         fread(img->lV.data(), sizeof(double), img->lV.size(), f) == img->lV.size();
+    const bool extra = ok && fgetc(f) != EOF;
+    fclose(f);
+    if (!ok) return refuse("is truncated");
+    if (extra) return refuse("has bytes after the saved state");
+    for (int d = 0; d < ndim; ++d) {
+        const double *e = img->e.data() + (size_t)d * (N + 1);
+        if (e[0] != 0.0 || e[N] != 1.0) return refuse("a grid axis does not run from 0 to 1");
+        for (int k = 0; k < N; ++k)
+            if (!(e[k + 1] > e[k])) return refuse("a grid axis is not increasing");
+    }
+    for (double v : img->H)
+        if (!(v >= 0.0) || !std::isfinite(v)) return refuse("the histogram holds a negative or non-finite value");
+    DevState S;
+    memcpy(&S, img->st.data(), sizeof(S));
+    int jmax = 0;
+    long long nmax = 0;
+    plan(sp.nstart, sp.nincrease, sp.maxeval, &jmax, &nmax);
+    if (S.iter < 0 || S.iter > jmax) return refuse("the iteration count is outside the schedule");
+    if ((S.stopped != 0 && S.stopped != 1) || (S.fail != 0 && S.fail != 1) || (S.status & ~1) != 0)
+        return refuse("the run's flags are not 0 or 1");
+    if (S.stopped && S.iter == 0) return refuse("a run stopped before its first iteration");
+    long long neval = 0;
+    for (int j = 0; j < S.iter; ++j) neval += sp.nstart + (long long)j * sp.nincrease;
+    if (S.neval != neval || S.neval > sp.maxeval)
+        return refuse("the sample count disagrees with the iterations done");
+    const long long n_next = sp.nstart + (long long)S.iter * sp.nincrease;
+    const long long n_last = S.iter > 0 ? n_next - sp.nincrease : 0;
+    const long long n_cur = S.stopped ? n_last : n_next;
+    const unsigned long long next = 1ull + (unsigned long long)(S.stopped ? neval - n_last : neval);
+    if (S.n_cur != n_cur) return refuse("the next iteration's size disagrees with the schedule");
+    if (S.next_index != next || S.next_index + (unsigned long long)S.n_cur > CV_INDEX_LIMIT)
+        return refuse("the next Sobol index disagrees with the samples taken");
+    return CV_OK;
+}
+}  // namespace
+
+extern "C" int cv_integral_check_file(const cv_spec *spec, const char *path, char *msg, int len)
+{
+    if (msg && len > 0) msg[0] = '\0';
+    if (!spec || !path || len < 0 || (len > 0 && !msg)) return CV_EINVAL;
+    cv_ctx tmp;  // (host-side messages only: no device is touched)
+    if (check_spec(&tmp, spec)) {
+        if (msg && len > 0) snprintf(msg, (size_t)len, "%s", tmp.msg);
+        return CV_EINVAL;
+    }
+    StateImage img;
+    return read_state_file(*spec, path, &img, msg, (size_t)len);
+}
+
 extern "C" int cv_integral_load(cv_integral *I, const char *path)
 {
     if (!I || !path) return CV_EINVAL;
     cv_ctx *ctx = I->ctx;
-    CV_CUDA(ctx, cudaSetDevice(ctx->device));
-    FILE *f = fopen(path, "rb");
-    if (!f) return fail_msg(ctx, CV_EINVAL, "cannot open %s", path);
-    StateFileHeader h, want;
-    fill_header(I->spec, &want);
+    StateImage img;
+    int rc = read_state_file(I->spec, path, &img, ctx->msg, sizeof(ctx->msg));
+    if (rc) return rc;
     const int ndim = I->spec.g.ndim, N = I->spec.nbins;
-    std::vector<char> st(sizeof(DevState));
-    std::vector<double> e((size_t)ndim * (N + 1)), H((size_t)ndim * N);
-    std::vector<double> lI((size_t)kLogCap * CV_MAX_COMP), lV((size_t)kLogCap * CV_MAX_COMP);
-    bool ok = fread(&h, sizeof(h), 1, f) == 1;
-    if (ok && memcmp(&h, &want, sizeof(h)) != 0) {
-        fclose(f);
-        return fail_msg(ctx, CV_EINVAL, "%s holds the state of another problem or format", path);
-    }
-    ok = ok && fread(st.data(), st.size(), 1, f) == 1 &&
-         fread(e.data(), sizeof(double), e.size(), f) == e.size() &&
-         fread(H.data(), sizeof(double), H.size(), f) == H.size() &&
-         fread(lI.data(), sizeof(double), lI.size(), f) == lI.size() &&
-         fread(lV.data(), sizeof(double), lV.size(), f) == lV.size();
-    fclose(f);
-    if (!ok) return fail_msg(ctx, CV_EINVAL, "%s is truncated", path);
-    CV_CUDA(ctx, cudaMemcpyAsync(I->st, st.data(), st.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CV_CUDA(ctx, cudaMemcpyAsync(I->edges, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CV_CUDA(ctx, cudaMemcpyAsync(I->H, H.data(), H.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CV_CUDA(ctx, cudaMemcpyAsync(I->log_I, lI.data(), lI.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CV_CUDA(ctx, cudaMemcpyAsync(I->log_var, lV.data(), lV.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaSetDevice(ctx->device));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->st, img.st.data(), img.st.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->edges, img.e.data(), img.e.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->H, img.H.data(), img.H.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->log_I, img.lI.data(), img.lI.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(I->log_var, img.lV.data(), img.lV.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     if (I->ew32) CV_CUDA(ctx, launch_stage_grid(ndim, N, I->edges, I->ew32, I->map, ctx->stream));
     CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return CV_OK;
@@ -2537,13 +2612,19 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     long long nmax = 0;
     plan(sp.nstart, sp.nincrease, sp.maxeval, &jmax, &nmax);
     const long long tile = nvec < nmax ? nvec : nmax;
-    // device memory: state, grid, histogram, x, f
+    // row stride of the dimension-major layout: a multiple of 32 values, so
+    // that with 256-byte aligned arrays every aligned 32-point group of a
+    // row is whole 128-byte lines
+    const long long ldx = aos ? tile : (tile + 31) / 32 * 32;
+    const bool fp32 = sizeof(Real) == 4;
+    // device memory: state, grid, histogram, staged FP32 grid, x, f
     const size_t sz_state = (sizeof(DevState) + 255) & ~(size_t)255;
     const size_t sz_edges = (((size_t)ndim * (N + 1) * sizeof(double)) + 255) & ~(size_t)255;
     const size_t sz_H = (((size_t)ndim * N * sizeof(double)) + 255) & ~(size_t)255;
-    const size_t sz_x = (((size_t)ndim * tile * sizeof(Real)) + 255) & ~(size_t)255;
-    const size_t sz_f = (size_t)ncomp * tile * sizeof(Real);
-    const size_t need = sz_state + sz_edges + sz_H + sz_x + sz_f;
+    const size_t sz_ew = fp32 ? (((size_t)ndim * N * sizeof(float2)) + 255) & ~(size_t)255 : 0;
+    const size_t sz_x = (((size_t)ndim * ldx * sizeof(Real)) + 255) & ~(size_t)255;
+    const size_t sz_f = (size_t)ncomp * ldx * sizeof(Real);
+    const size_t need = sz_state + sz_edges + sz_H + sz_ew + sz_x + sz_f;
     if (!ctx->pinned) {
         if (cudaHostAlloc((void **)&ctx->pinned, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
@@ -2569,8 +2650,9 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     DevState *st = (DevState *)p;
     double *edges = (double *)(p + sz_state);
     double *H = (double *)(p + sz_state + sz_edges);
-    Real *x = (Real *)(p + sz_state + sz_edges + sz_H);
-    Real *f = (Real *)(p + sz_state + sz_edges + sz_H + sz_x);
+    float2 *ew32 = fp32 ? (float2 *)(p + sz_state + sz_edges + sz_H) : nullptr;
+    Real *x = (Real *)(p + sz_state + sz_edges + sz_H + sz_ew);
+    Real *f = (Real *)(p + sz_state + sz_edges + sz_H + sz_ew + sz_x);
     int rc = CV_OK;
     cudaStream_t s = ctx->stream;
     CombineArgs ca = {};
@@ -2592,7 +2674,8 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     a.map = make_map(N, ndim, sizeof(Real) == 8);
     set_generator(&a, ndim, sp.flags, sp.seed);
     a.edges = edges;
-    a.ld = tile;
+    if constexpr (sizeof(Real) == 4) a.ew32 = ew32;  // (staged by reset and by each refinement)
+    a.ld = ldx;
     a.aos = aos ? 1 : 0;
     a.x = x;
     a.f = f;
@@ -2604,34 +2687,57 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     if (rc) return rc;
     pin[0] = 1;
     int aborted = 0;
-    cudaError_t e = launch_reset(st, edges, H, ndim, N, sp.nstart, nullptr, a.map, s);
+    // (the dimension-major FP32 kernels for N = 2^L flag the refinement
+    // themselves: their accumulate pass sets pass_active from the stop flag)
+    const bool lean = fp32 && a.map.pow2 && !aos && a.gen != kGenPseudo && a.map.priv;
+    if (lean) a.st = st;
+    cudaEvent_t ev_stop = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev_stop, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = launch_reset(st, edges, H, ndim, N, sp.nstart, ew32, a.map, s);
+    // Per iteration: for each tile the store pass, the integrand, the
+    // accumulate pass; then refinement and combination, and the device's
+    // stop flag copied back.  The next iteration's first store pass is
+    // enqueued before the host waits for that flag, so the GPU writes the
+    // next points while the host decides whether to call the integrand
+    // again (if the run stopped, those points are never used).
     unsigned long long start = 1;
+    auto store = [&](unsigned long long s0, long long m) {
+        a.start = s0;
+        a.n = m;
+        // (the same grid as a fused pass: the kernels share its occupancy)
+        return dispatch_matpass<Real>(ndim, false, a, sample_grid(ctx, occ, m), s);
+    };
+    if (e == cudaSuccess && jmax > 0) e = store(start, sp.nstart < tile ? sp.nstart : tile);
     for (int j = 0; j < jmax && e == cudaSuccess && !aborted; ++j) {
         const long long nj = sp.nstart + (long long)j * sp.nincrease;
         for (long long off = 0; off < nj && e == cudaSuccess; off += tile) {
             const long long m = nj - off < tile ? nj - off : tile;
-            a.start = start + (unsigned long long)off;
-            a.n = m;
-            // (the same grid as a fused pass: the kernels share its occupancy)
-            const int grid = sample_grid(ctx, occ, m);
-            e = dispatch_matpass<Real>(ndim, false, a, grid, s);
+            if (off > 0) e = store(start + (unsigned long long)off, m);
             if (e != cudaSuccess) break;
-            const int64_t nv = m, ld = tile;
+            const int64_t nv = m, ld = ldx;
             const int r = cb(&ndim, x, &ncomp, f, userdata, &nv, &ld, (void *)s);
             if (r == -999) {
                 aborted = 1;
                 break;
             }
-            e = dispatch_matpass<Real>(ndim, true, a, grid, s);
+            a.start = start + (unsigned long long)off;
+            a.n = m;
+            e = dispatch_matpass<Real>(ndim, true, a, sample_grid(ctx, occ, m), s);
         }
         if (aborted || e != cudaSuccess) break;
-        e = cudaMemcpyAsync(&st->pass_active, &pin[0], sizeof(int), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = launch_refine_combine(ndim, N, H, edges, ca, nullptr, a.map, s);
+        if (!lean) e = cudaMemcpyAsync(&st->pass_active, &pin[0], sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_refine_combine(ndim, N, H, edges, ca, ew32, a.map, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&pin[1], &st->stopped, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_stop, s);
         start += (unsigned long long)nj;
+        if (e == cudaSuccess && j + 1 < jmax) {
+            const long long nn = nj + sp.nincrease;
+            e = store(start, nn < tile ? nn : tile);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev_stop);
         if (pin[1]) break;
     }
+    if (ev_stop) cudaEventDestroy(ev_stop);
     if (e != cudaSuccess) rc = cuda_fail(ctx, e, "materialised pass");
     DevState h;
     memset(&h, 0, sizeof(h));

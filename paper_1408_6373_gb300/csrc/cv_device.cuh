@@ -579,6 +579,12 @@ __device__ __forceinline__ float2 lds_f2(unsigned a)
     asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
     return v;
 }
+__device__ __forceinline__ unsigned lds_u(unsigned a)
+{
+    unsigned v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
 __device__ __forceinline__ float lds_f(unsigned a)
 {
     float v;
@@ -1245,6 +1251,272 @@ k_matpass(const __grid_constant__ SampleArgs<Real> A)
     sample_pass<NDIM, Real, POW2, MatIntegrand<Real, MODE>>(A);
 }
 
+// ---- materialised samples, FP32, dimension-major, N = 2^L >= 32
+// The two passes of the common case as kernels of their own: the store
+// pass is bound by HBM writes and the accumulate pass by its reads, so both
+// keep to the instructions the point needs (no integrand, no runtime
+// layout or component loops).
+
+// Asynchronous 4-byte copies global -> shared (cp.async; bytes = 0 copies
+// nothing and writes a zero), grouped, and the wait for all but the newest
+// N groups of this thread.
+__device__ __forceinline__ void cp_async4(unsigned dst, const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Blocks of values the accumulate pass has requested ahead of the one it
+// works on (each a warp's 32 points x CV_MAX_COMP values).
+constexpr int kMatAhead = 4;
+
+// The grid table of a materialised pass in a block's shared memory: the
+// staged table when there is one, else converted from the FP64 edges.
+template <int NDIM>
+__device__ __forceinline__ void mat_table(const SampleArgs<float> &A, Smem<float> &sm, unsigned char *raw, int N)
+{
+    sm.stride = N;
+    sm.ew = align_table(raw, N);
+    if (A.ew32) {
+        for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) sm.ew[idx] = A.ew32[idx];
+    } else {
+        stage_grid_f32(sm.ew, NDIM, N, N, A.edges, A.map);
+    }
+}
+
+// Sobol words of index i for this lane alone (lanes may hold any indices):
+// XOR over the set bits k of g(i) of V_k, in the tables' step form (entry k
+// >= 5 is V_4 ^ V_k, so V_4 enters once per set bit above bit 4).
+template <int NDIM>
+__device__ __forceinline__ void sobol_at(unsigned (&X)[NDIM], unsigned long long i, int li)
+{
+    const unsigned long long g = i ^ (i >> 1);
+    unsigned long long ghi = g >> 5;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        unsigned x = 0u;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) x ^= ((g >> k) & 1ull) ? Dir<unsigned>::w(li, d, k) : 0u;
+        if (__popcll(ghi) & 1) x ^= Dir<unsigned>::w(li, d, 4);
+        X[d] = x;
+    }
+    while (ghi) {
+        const int k = __ffsll((long long)ghi) - 1 + 5;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) X[d] ^= Dir<unsigned>::w(li, d, k);
+        ghi &= ghi - 1;
+    }
+}
+
+// Store pass: the points of indices [start, start + n) at x[d ld + j],
+// j = index - start.  A warp writes 32 consecutive j of a tile aligned in
+// j (one full 128-byte line per coordinate when x and ld are aligned), so
+// its lanes' indices straddle two aligned Sobol blocks whenever start is
+// not a multiple of 32: every lane carries its own block counter and steps
+// its words by the Gray-code rule for its own block, g(32(q+1)+k) ^
+// g(32q+k) = 2^4 ^ 2^(5 + ctz(q+1)).  The direction words of the table sit
+// in shared memory, where the two blocks' lookups of a step are one
+// broadcast each.  Tiles go to warps in rounds of kRun so that all warps
+// write within one window of x at a time.
+template <int NDIM>
+__global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, float>))
+k_mat_store(const __grid_constant__ SampleArgs<float> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned sdir[NDIM][CV_SOBOL_BITS];
+    const int N = A.nbins;
+    const int li = A.map.li;
+    Smem<float> sm;
+    mat_table<NDIM>(A, sm, smem_raw, N);
+    sm.h = nullptr;
+    set_addresses(sm, A.map.L);
+    for (int idx = threadIdx.x; idx < NDIM * CV_SOBOL_BITS; idx += blockDim.x)
+        sdir[idx / CV_SOBOL_BITS][idx % CV_SOBOL_BITS] = Dir<unsigned>::w(li, idx / CV_SOBOL_BITS, idx % CV_SOBOL_BITS);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const long long n = A.n;
+    const long long ntile = (n + 31) / 32;
+    const long long gwarp = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const long long twarps = (long long)gridDim.x * kWarpsPerBlock;
+    const long long nchunk = (ntile + kRun - 1) / kRun;
+    const unsigned mF = A.map.mF, expE = A.map.expE, sA = A.map.sA;
+    const long long ld = A.ld;
+    // this lane's direction-word row base (shared window): + 4 (5 + c) + d rows
+    const unsigned sdir_sa = (unsigned)__cvta_generic_to_shared(&sdir[0][0]);
+    for (long long ch = gwarp; ch < nchunk; ch += twarps) {
+        const long long j0 = ch * kRun * 32 + lane;
+        const int nt = (int)min((long long)kRun, ntile - ch * kRun);
+        const long long rem = n - j0;  // (this lane's point of tile tt is valid while 32 tt < rem)
+        unsigned long long q = (A.start + (unsigned long long)j0) >> 5;  // this lane's Sobol block
+        unsigned X[NDIM];
+        sobol_at<NDIM>(X, A.start + (unsigned long long)j0, li);
+        if (A.gen == kGenScrambled) {
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) X[d] ^= (unsigned)A.shift[d];
+        }
+        float *px = A.x + j0;
+        for (int tt = 0; tt < nt; ++tt) {
+            const bool valid = 32ll * tt < rem;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                const float f1 = __uint_as_float((X[d] & mF) | expE);
+                const float2 ew = lds_f2(__funnelshift_r(X[d], sm.g_hi, sA) + (unsigned)(d * N * 8));
+                const float z = __fmaf_rn(ew.y, f1, ew.x);
+                if (valid) px[d * ld] = z + 0.5f;
+            }
+            // this lane's block q steps to q + 1
+            const int c = min(__ffsll((long long)(q + 1ull)) - 1, CV_SOBOL_BITS - 6);
+            const unsigned da = sdir_sa + (unsigned)((5 + c) * 4);
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) X[d] ^= lds_u(da + (unsigned)(d * CV_SOBOL_BITS * 4));
+            ++q;
+            px += 32;
+        }
+    }
+}
+
+// Accumulate pass: the caller's values f[c ld + j] of the points of
+// [start, start + n), with every point's bins and Jacobian recomputed from
+// its Sobol words in aligned 32-index blocks (lane = the index's low five
+// bits), so each warp's f^2 histogram copy takes plain updates (the 32
+// lanes' bins are distinct); sums and histogram as the fused pass.
+template <int NDIM>
+__global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, float>))
+k_mat_accum(const __grid_constant__ SampleArgs<float> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = A.nbins;
+    const int li = A.map.li;
+    const int ncomp = A.g.ncomp;
+    Smem<float> sm;
+    mat_table<NDIM>(A, sm, smem_raw, N);
+    float *hist = reinterpret_cast<float *>(sm.ew + NDIM * N);
+    for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * N; i += blockDim.x) hist[i] = 0.0f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    sm.h = hist + warp * NDIM * N;
+    set_addresses(sm, A.map.L);
+    // this warp's ring of value stages, after the histogram copies
+    const unsigned ring = (unsigned)__cvta_generic_to_shared(hist + kWarpsPerBlock * NDIM * N) +
+                          (unsigned)(warp * kMatAhead * CV_MAX_COMP * 32 * 4);
+    __syncthreads();
+
+    // (st, when given, only carries the run's stop flag to the refinement
+    // that follows: start and n are the launch's)
+    if (A.st && blockIdx.x == 0 && threadIdx.x == 0)
+        A.st->pass_active = *(volatile const int *)&A.st->stopped ? 0 : 1;
+    const unsigned long long start = A.start, end = start + (unsigned long long)A.n;
+    const unsigned long long qa = start >> 5;
+    const unsigned long long nblk = A.n > 0 ? ((end + 31ull) >> 5) - qa : 0ull;
+    const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarpsPerBlock + warp;
+    const unsigned long long twarps = (unsigned long long)gridDim.x * kWarpsPerBlock;
+    const unsigned long long nchunk = (nblk + kRun - 1) / kRun;
+    const unsigned sA = A.map.sA;
+    const long long ld = A.ld;
+    Acc<float> s1[CV_MAX_COMP], s2[CV_MAX_COMP];
+    for (unsigned long long ch = gwarp; ch < nchunk; ch += twarps) {
+        const unsigned long long q0 = qa + ch * kRun;
+        const unsigned long long q1 = min(q0 + (unsigned long long)kRun, qa + nblk);
+        unsigned X[NDIM];
+        sobol_skip<NDIM, unsigned>(X, q0, lane, li);
+        if (A.gen == kGenScrambled) {
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) X[d] ^= (unsigned)A.shift[d];
+        }
+        Partial<float> P;
+        P.zero();
+        // the values of block q + kMatAhead are requested while block q is
+        // worked on: asynchronous copies into this warp's ring of stages
+        // (each lane copies and later reads only its own words; lanes
+        // outside [start, end) copy zeros)
+        auto request = [&](unsigned long long q) {
+            const unsigned stage = ring + (unsigned)((q - q0) % kMatAhead) * (CV_MAX_COMP * 32 * 4);
+            const unsigned long long i = q * 32ull + (unsigned long long)lane;
+            const bool valid = q < q1 && i >= start && i < end;
+            const float *src = A.f + (valid ? (long long)(i - start) : 0ll);
+#pragma unroll
+            for (int c = 0; c < CV_MAX_COMP; ++c)
+                if (c < ncomp) cp_async4(stage + (unsigned)((c * 32 + lane) * 4), src + c * ld, valid ? 4u : 0u);
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int k = 0; k < kMatAhead; ++k) request(q0 + k);
+        for (unsigned long long q = q0; q < q1; ++q) {
+            cp_async_wait<kMatAhead - 1>();  // (block q's copies have landed)
+            const unsigned stage = ring + (unsigned)((q - q0) % kMatAhead) * (CV_MAX_COMP * 32 * 4);
+            float f[CV_MAX_COMP];
+#pragma unroll
+            for (int c = 0; c < CV_MAX_COMP; ++c) f[c] = c < ncomp ? lds_f(stage + (unsigned)((c * 32 + lane) * 4)) : 0.0f;
+            const unsigned long long i = q * 32ull + (unsigned long long)lane;
+            float J = (i >= start && i < end) ? 1.0f : 0.0f;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d)
+                J *= lds_f(__funnelshift_r(X[d], sm.g_hi, sA) + (unsigned)(d * N * 8 + 4));
+            const float v0 = J * f[0];
+            const float h = v0 * v0;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                const unsigned ha = __funnelshift_r(X[d], sm.h_hi, sA + 1u) + (unsigned)(d * N * 4);
+                sts_f(ha, lds_f(ha) + h);
+            }
+            const float2 v01 = make_float2(v0, J * f[1]);
+            P.s1[0] = add2(P.s1[0], v01);
+            P.s2[0] = fma2(v01, v01, P.s2[0]);
+            if (ncomp > 2) {
+                const float2 v23 = make_float2(J * f[2], J * f[3]);
+                P.s1[1] = add2(P.s1[1], v23);
+                P.s2[1] = fma2(v23, v23, P.s2[1]);
+            }
+            __syncwarp();
+            sobol_step<NDIM, unsigned>(X, q, li);
+            request(q + kMatAhead);
+        }
+        cp_async_wait<0>();  // (the ring is reused by the next chunk)
+#pragma unroll
+        for (int c = 0; c < CV_MAX_COMP; ++c) {
+            if (c < ncomp) {
+                s1[c].add(P.v1(c));
+                s2[c].add(P.v2(c));
+            }
+        }
+    }
+
+    __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
+#pragma unroll
+    for (int c = 0; c < CV_MAX_COMP; ++c) {
+        if (c < ncomp) {
+            const double a = warp_total(s1[c]);
+            const double b = warp_total(s2[c]);
+            if (lane == 0) {
+                red[warp][2 * c] = a;
+                red[warp][2 * c + 1] = b;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * ncomp) {
+        double t = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) t += red[w][threadIdx.x];
+        const int c = threadIdx.x >> 1;
+        atomicAdd((threadIdx.x & 1) ? &A.S2[c] : &A.S1[c], t);
+    }
+    // the warps' copies, summed in warp order
+    for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
+        const int d = idx / N;
+        const int k = idx - d * N;
+        const int p = slot_of_bin(k, A.map);
+        float v = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kWarpsPerBlock; ++w) v += hist[(w * NDIM + d) * N + p];
+        if (v != 0.0f) atomicAdd(&A.H[d * N + k], (double)v);
+    }
+}
+
 // Built-in integrand on materialised points (the library's own callback):
 // f_c(x_j) for the Genz components of g, same formulas as the fused pass.
 template <int NDIM, typename Real, bool AOS>
@@ -1403,6 +1675,29 @@ cudaError_t batch_occupancy(bool pow2, int stride, int *blocks_per_sm)
 template <int NDIM, typename Real, bool POW2, int MODE>
 static cudaError_t launch_matpass_v(const SampleArgs<Real> &a, int grid, cudaStream_t s)
 {
+    if constexpr (sizeof(Real) == 4 && POW2) {
+        // the common case's own kernels (dimension-major, Sobol points; the
+        // accumulate pass needs the warps' histogram copies to fit)
+        if (!a.aos && a.gen != kGenPseudo) {
+            if (MODE == 1) {
+                const size_t smem = (size_t)NDIM * a.nbins * 8 + 8 * (size_t)a.nbins;
+                cudaError_t e = cudaFuncSetAttribute(k_mat_store<NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
+                if (e != cudaSuccess) return e;
+                k_mat_store<NDIM><<<grid, kBlock, smem, s>>>(a);
+                return cudaGetLastError();
+            }
+            if (a.map.priv) {
+                const size_t smem = sample_smem_bytes(NDIM, a.nbins, false, true) +
+                                    (size_t)kWarpsPerBlock * kMatAhead * CV_MAX_COMP * 32 * 4;
+                cudaError_t e = cudaFuncSetAttribute(k_mat_accum<NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
+                if (e != cudaSuccess) return e;
+                k_mat_accum<NDIM><<<grid, kBlock, smem, s>>>(a);
+                return cudaGetLastError();
+            }
+        }
+    }
     const size_t smem = sample_smem_bytes(NDIM, a.nbins, sizeof(Real) == 8, a.map.priv != 0);
     cudaError_t e = cudaFuncSetAttribute(k_matpass<NDIM, Real, POW2, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -92,30 +92,126 @@ __device__ __forceinline__ long long warp_max_bits(long long v)
 // 1.5 ulp of the quotient).  FP64 results take ~200 cycles here, so the
 // refinement is bound by its chain of dependent FP64 operations: maxima
 // and searches over non-negative doubles compare bit patterns instead.
-// Bin `off` of the G blocks' partial histograms (stride `stride` values
-// between blocks), summed in block order: FP32 partials in four interleaved
-// Kahan sums in FP32 (FP64 throughput is a small fraction of FP32 here),
-// FP64 partials in four plain FP64 sums; the four are then added in a fixed
-// order in FP64.  Deterministic: the same partials give the same bits.
-__device__ __forceinline__ double sum_parts(const void *part_H, int G, int f32, size_t stride, size_t off)
+// The G blocks' partial histograms of axis d, summed into sH[0, N) by all
+// the CTA's threads: thread t takes the V-wide column q = t mod (N/V) of
+// the rows r, r + R, r + 2R, ... (r = t div (N/V), R row groups), so a
+// warp's loads are contiguous vectors and each thread keeps four in flight;
+// the R group sums of a bin are then added in group order.  FP32 partials
+// are summed with Kahan's compensation in FP32 throughout (FP64 throughput,
+// conversions included, is a small fraction of FP32 here) and converted
+// once per bin; FP64 partials are summed in FP64.  The assignment of rows
+// to threads is fixed, so the same partials give the same bits.  Called by
+// every thread of the CTA (it synchronises).
+template <typename T, int V>
+__device__ __forceinline__ void load_vec(const T *p, T (&v)[V])
 {
-    if (f32) {
-        const float *p = static_cast<const float *>(part_H) + off;
-        float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int b = 0; b < G; ++b) {
-            const int j = b & 3;
-            const float y = p[(size_t)b * stride] - c[j];
-            const float t = s[j] + y;
-            c[j] = (t - s[j]) - y;
-            s[j] = t;
-        }
-        return (((double)s[0] - (double)c[0]) + ((double)s[1] - (double)c[1])) +
-               (((double)s[2] - (double)c[2]) + ((double)s[3] - (double)c[3]));
+    if constexpr (V == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (V == 2 && sizeof(T) == 4) {
+        const float2 q = *reinterpret_cast<const float2 *>(p);
+        v[0] = q.x; v[1] = q.y;
+    } else if constexpr (V == 2) {
+        const double2 q = *reinterpret_cast<const double2 *>(p);
+        v[0] = q.x; v[1] = q.y;
+    } else {
+        v[0] = *p;
     }
-    const double *p = static_cast<const double *>(part_H) + off;
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = 0; b < G; ++b) s[b & 3] += p[(size_t)b * stride];
-    return (s[0] + s[1]) + (s[2] + s[3]);
+}
+
+// s + y with the running compensation c (Kahan), FP32
+__device__ __forceinline__ void kahan_add(float &s, float &c, float y)
+{
+    const float t = y - c;
+    const float u = s + t;
+    c = (u - s) - t;
+    s = u;
+}
+
+// Group sums: FP32 as (sum, compensation) pairs, FP64 as (sum, 0).
+template <typename T>
+struct GroupSum { using type = float2; };
+template <>
+struct GroupSum<double> { using type = double2; };
+
+template <typename T, int V>
+__device__ __forceinline__ void sum_rows(const T *P, int G, size_t nh, int N,
+                                         typename GroupSum<T>::type *grp)
+{
+    const int cols = N / V, R = (int)blockDim.x / cols;
+    const int t = threadIdx.x, q = t % cols, r = t / cols;
+    if (r >= R) return;
+    T s[V], c[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) s[i] = c[i] = T(0);
+    auto add = [&](const T (&v)[V]) {
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            if constexpr (sizeof(T) == 4) kahan_add(s[i], c[i], v[i]);
+            else s[i] += v[i];
+        }
+    };
+    const T *p = P + (size_t)q * V;
+    int b = r;
+    for (; b + 3 * R < G; b += 4 * R) {
+        T v0[V], v1[V], v2[V], v3[V];
+        load_vec<T, V>(p + (size_t)b * nh, v0);
+        load_vec<T, V>(p + (size_t)(b + R) * nh, v1);
+        load_vec<T, V>(p + (size_t)(b + 2 * R) * nh, v2);
+        load_vec<T, V>(p + (size_t)(b + 3 * R) * nh, v3);
+        add(v0);
+        add(v1);
+        add(v2);
+        add(v3);
+    }
+    for (; b < G; b += R) {
+        T v[V];
+        load_vec<T, V>(p + (size_t)b * nh, v);
+        add(v);
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) grp[r * N + q * V + i] = {s[i], c[i]};
+}
+
+__device__ void sum_parts_axis(const CombineArgs *pa, int d, int N, double *sH)
+{
+    // R x N group sums, R N <= 4 blockDim (FP32), 2 blockDim (FP64)
+    __shared__ __align__(16) unsigned char grp_raw[4096 * sizeof(float2)];
+    const size_t nh = (size_t)pa->part_nh;
+    const int G = pa->part_G;
+    const int k = threadIdx.x;
+    if (pa->part_f32) {
+        float2 *grp = reinterpret_cast<float2 *>(grp_raw);
+        const float *P = static_cast<const float *>(pa->part_H) + (size_t)d * N;
+        const int V = N % 4 == 0 ? 4 : N % 2 == 0 ? 2 : 1;
+        if (V == 4) sum_rows<float, 4>(P, G, nh, N, grp);
+        else if (V == 2) sum_rows<float, 2>(P, G, nh, N, grp);
+        else sum_rows<float, 1>(P, G, nh, N, grp);
+        __syncthreads();
+        if (k < N) {
+            const int R = (int)blockDim.x / (N / V);
+            float s = 0.0f, c = 0.0f;
+            for (int r = 0; r < R; ++r) {
+                const float2 g = grp[r * N + k];
+                kahan_add(s, c, g.x);
+                kahan_add(s, c, -g.y);
+            }
+            sH[k] = (double)s - (double)c;
+        }
+    } else {
+        double2 *grp = reinterpret_cast<double2 *>(grp_raw);
+        const double *P = static_cast<const double *>(pa->part_H) + (size_t)d * N;
+        const int V = N % 2 == 0 ? 2 : 1;
+        if (V == 2) sum_rows<double, 2>(P, G, nh, N, grp);
+        else sum_rows<double, 1>(P, G, nh, N, grp);
+        __syncthreads();
+        if (k < N) {
+            const int R = (int)blockDim.x / (N / V);
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int r = 0; r < R; ++r) a[r & 3] += grp[r * N + k].x;
+            sH[k] = (a[0] + a[1]) + (a[2] + a[3]);
+        }
+    }
 }
 
 __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_hist, float2 *ew32 = nullptr,
@@ -125,20 +221,18 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
     double *e = edges + (size_t)d * (N + 1);
     __shared__ double sH[CV_MAX_BINS], sq[CV_MAX_BINS];
     __shared__ double sC[CV_MAX_BINS + 1], se[CV_MAX_BINS + 1];
-    __shared__ double wred[8];
+    __shared__ double wred[32];
     __shared__ double s_sum, s_inv, s_rmax, s_RN;
     const int k = threadIdx.x;            // bin of this thread
     const int lane = k & 31, warp = k >> 5;
-    const int nw = blockDim.x >> 5;
+    // the warps holding bins; the others (a CTA sized for the partial sums)
+    // only meet the barriers: the FP64 pipe is a small fraction of FP32 here
+    const int nw = (N + 31) >> 5;
+    const bool act = warp < nw;
     const double invN = __drcp_rn((double)N);  // (off the dependent chain)
 
-    if (k < N) {
-        if (pa && pa->part_H) {
-            sH[k] = sum_parts(pa->part_H, pa->part_G, pa->part_f32, (size_t)pa->part_nh, (size_t)d * N + k);
-        } else {
-            sH[k] = Hd[k];
-        }
-    }
+    if (pa && pa->part_H) sum_parts_axis(pa, d, N, sH);
+    else if (k < N) sH[k] = Hd[k];
     for (int i = k; i <= N; i += blockDim.x) se[i] = e[i];
     __syncthreads();
     const bool bad = k < N && !isfinite(sH[k]);
@@ -156,8 +250,10 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
         }
         // s = sum_k h_k (warp sums, then the warps in order by one thread;
         // the per-axis scalars are computed once and shared)
-        double ws = warp_sum_d(h);
-        if (lane == 0) wred[warp] = ws;
+        if (act) {
+            const double ws = warp_sum_d(h);
+            if (lane == 0) wred[warp] = ws;
+        }
         __syncthreads();
         if (k == 0) {
             double t = 0.0;
@@ -179,8 +275,10 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
                 r = __dmul_rn(q, sqrt(q));
             }
         }
-        const long long wm = warp_max_bits(__double_as_longlong(r));
-        if (lane == 0) wred[warp] = __longlong_as_double(wm);
+        if (act) {
+            const long long wm = warp_max_bits(__double_as_longlong(r));
+            if (lane == 0) wred[warp] = __longlong_as_double(wm);
+        }
         __syncthreads();
         if (k == 0) {
             long long t = 0;
@@ -192,23 +290,28 @@ __device__ void refine_axis(int d, int N, double *H, double *edges, int zero_his
         const long long rmax_bits = __double_as_longlong(s_rmax);
         if (rmax_bits > 0) {
             // scale to max 1 (the largest bins exactly 1)
-            r = (__double_as_longlong(r) == rmax_bits) ? 1.0 : __dmul_rn(r, s_inv);
-            if (k < N) sq[k] = r > 0.0 ? __drcp_rn(r) : 0.0;
-            // inclusive prefix sum C_(k+1) = r_0 + ... + r_k
-            double c = r;
+            double c = 0.0;
+            if (act) {
+                r = (__double_as_longlong(r) == rmax_bits) ? 1.0 : __dmul_rn(r, s_inv);
+                if (k < N) sq[k] = r > 0.0 ? __drcp_rn(r) : 0.0;
+                // inclusive prefix sum C_(k+1) = r_0 + ... + r_k
+                c = r;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const double t = __shfl_up_sync(0xffffffffu, c, o);
-                if (lane >= o) c = __dadd_rn(t, c);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double t = __shfl_up_sync(0xffffffffu, c, o);
+                    if (lane >= o) c = __dadd_rn(t, c);
+                }
+                if (lane == 31) wred[warp] = c;
             }
-            if (lane == 31) wred[warp] = c;
             __syncthreads();
-            double off = 0.0;
-            for (int w = 0; w < warp; ++w) off = __dadd_rn(off, wred[w]);
-            c = __dadd_rn(off, c);
-            if (k < N) sC[k + 1] = c;
-            if (k == 0) sC[0] = 0.0;
-            if (k == N - 1) s_RN = __dmul_rn(c, invN);  // R / N, R = C_N
+            if (act) {
+                double off = 0.0;
+                for (int w = 0; w < warp; ++w) off = __dadd_rn(off, wred[w]);
+                c = __dadd_rn(off, c);
+                if (k < N) sC[k + 1] = c;
+                if (k == 0) sC[0] = 0.0;
+                if (k == N - 1) s_RN = __dmul_rn(c, invN);  // R / N, R = C_N
+            }
             __syncthreads();
             const int m = k;
             if (m >= 1 && m < N) {
@@ -382,7 +485,7 @@ __device__ void combine_iteration(const CombineArgs &A)
 // One Vegas iteration after its sampling pass: blocks 0..ndim-1 refine one
 // axis each from the histogram (and clear it), block ndim combines the
 // iteration.  Runs only if the sampling launch before it ran.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 k_refine_combine(int ndim, int N, double *H, double *edges, const CombineArgs A, float2 *ew32, MapParams map)
 {
     if (!*(volatile const int *)&A.st->pass_active) return;
@@ -527,7 +630,9 @@ cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
                                   const CombineArgs &a, float2 *ew32, const MapParams &map,
                                   cudaStream_t s)
 {
-    k_refine_combine<<<ndim + 1, refine_threads(nbins), 0, s>>>(ndim, nbins, H, edges, a, ew32, map);
+    // (with block partials to add, a full CTA per axis: see sum_parts_axis)
+    const int threads = a.part_H ? 1024 : refine_threads(nbins);
+    k_refine_combine<<<ndim + 1, threads, 0, s>>>(ndim, nbins, H, edges, a, ew32, map);
     return cudaGetLastError();
 }
 

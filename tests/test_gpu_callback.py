@@ -4,11 +4,13 @@ the actual count passed, -999 aborts -- in both layouts, against the fused
 path and the FP64 oracle."""
 import ctypes
 import math
+import os
 
 import numpy as np
 import pytest
 
 import oracle as O
+from tests.tolerances import check_fp32_iteration
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -57,6 +59,32 @@ def test_builtin_integrand_fp32_close_to_fused(ctx):
     fused = ctx.vegas(g, flags=0, **kw)
     for c in range(2):
         assert abs(r.integral[c] - fused.integral[c]) <= 2e-5 * abs(fused.integral[c]) + 1e-2 * fused.error[c]
+
+
+# One FP32 iteration on the uniform grid through the materialised passes
+# (points written, the library's integrand, values read back) against the
+# oracle's pass: I_1 and var_1 (error^2 of a one-iteration run) within the
+# FP32 bounds.  Tiles of 3333 points start at unaligned indices (the store
+# pass's shifted warps, ragged last tiles); 64 and 128 bins take the
+# dimension-major power-of-two kernels, 50 bins the general pass; scrambled
+# points too.
+@pytest.mark.parametrize("gen", ["sobol", "scrambled"])
+@pytest.mark.parametrize("nbins", [64, 128, 50])
+@pytest.mark.parametrize("nvec", [3333, 1 << 16])
+def test_materialised_fp32_pass_matches_oracle(ctx, nvec, nbins, gen):
+    ndim, fams = 8, [O.GAUSSIAN, O.PRODUCT_PEAK, O.OSCILLATORY, O.C0]
+    rng = np.random.default_rng(17 + nbins)
+    a = rng.uniform(0.5, 1.5, (4, ndim))
+    u = rng.uniform(0.1, 0.9, (4, ndim))
+    n = 100003
+    flags, seed = (cg.SCRAMBLE, 11) if gen == "scrambled" else (0, 0)
+    g = cg.genz(ndim, fams, a, u)
+    r = ctx.vegas_cb(cg.builtin_integrand(), ndim, 4, userdata=cg.GenzCallbackData(g, 0), nvec=nvec,
+                     flags=flags, seed=seed, maxeval=n, nstart=n, nbins=nbins)
+    assert (r.neval, r.fail) == (n, 1)
+    p = O.Problem(ndim, fams, a, u, nbins=nbins, bits=23, gen=O.SCRAMBLED if flags else O.SOBOL, seed=seed)
+    ob = O.sample_bounds(p, O.grid_uniform(ndim, nbins), 1, n, nthreads=os.cpu_count() or 1)
+    check_fp32_iteration(r.integral, r.error ** 2, ob, n, what=(nvec, nbins, gen))
 
 
 def test_tiles_do_not_change_results(ctx):

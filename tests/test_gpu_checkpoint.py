@@ -2,6 +2,8 @@
 and grid reuse (the role of gridno): an interrupted run resumed from a
 saved state equals the uninterrupted run; a saved state only loads into
 the same problem; a refined grid can seed another integral."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -46,6 +48,8 @@ def test_resume_from_saved_state_equals_uninterrupted_run(ctx, tmp_path, flags):
     path = str(tmp_path / "vegas.state")
     a.save(path)
     a.close()
+    # the saved file passes the host-side checks load makes
+    assert cg.check_state_file(_spec(flags, maxeval=10 ** 6), path) == (True, "")
     b = ctx.integral(_spec(flags, maxeval=10 ** 6))
     b.load(path)
     b.step(5)
@@ -107,6 +111,21 @@ def test_state_of_another_problem_is_refused(ctx, tmp_path):
         other.load(path)
     with pytest.raises(cg.CubaGpuError):
         other.load(str(tmp_path / "missing"))
+    # a damaged copy (the next Sobol index moved by one) is refused before
+    # it reaches the device, and the integral it was meant for still runs
+    from tests.test_state_file import Header
+    data = bytearray(open(path, "rb").read())
+    off = ctypes.sizeof(Header)
+    data[off:off + 8] = (int.from_bytes(data[off:off + 8], "little") + 1).to_bytes(8, "little")
+    bad = str(tmp_path / "bad")
+    open(bad, "wb").write(bytes(data))
+    same = ctx.integral(_spec(cg.FP64))
+    with pytest.raises(cg.CubaGpuError, match="Sobol index"):
+        same.load(bad)
+    same.load(path)
+    same.step(1)
+    assert same.result().iterations == 3
+    same.close()
     a.close()
     other.close()
 
