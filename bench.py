@@ -788,6 +788,8 @@ def measure_batch(ctx, cg, W, warmup: int, steps: int, subset: int = 32) -> dict
     res = B.results()
     launches = B.kernels_per_run()
     tiles = {str(n): B.tile_points(n) for n in (10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7)}
+    # (a tile is shared by a CTA's 256 threads)
+    ppt = {n: t // 256 for n, t in tiles.items()}
     B.close()
     # plain FP64 comparator on a subset (the full set would take ~30 s)
     idx = list(range(0, len(probs), len(probs) // subset))[:subset]
@@ -817,6 +819,7 @@ def measure_batch(ctx, cg, W, warmup: int, steps: int, subset: int = 32) -> dict
             "_results": [(r.integral[0], r.error[0]) for r in res], "_problems": probs,
             "samples_per_step": samples, "gpu_launches_per_step": launches,
             "autotune_s": tune_s, "tile_points_by_iteration_size": tiles,
+            "points_per_thread_by_iteration_size": ppt,
             "plain_fp64_subset": {"integrals": len(idx), "value": sub_samples / plain_s,
                                   "unit": UNIT,
                                   "max_abs_diff_in_sigma": max(dev),
@@ -832,7 +835,7 @@ def measure_materialised(ctx, cg, W) -> dict:
     import torch
     p = W.genz8d4c()
     g = cg.genz(p.ndim, p.families, p.a, p.u)
-    ud = cg.GenzCallbackData(g, 0)
+    ud = cg.GenzCallbackData(g, cg.JIT)  # (the library's integrand, specialised at run time)
     kw = dict(userdata=ud, nvec=p.nstart, flags=0, maxeval=p.maxeval, nstart=p.nstart, nbins=p.nbins)
     ctx.vegas_cb(cg.builtin_integrand(), p.ndim, p.ncomp, **dict(kw, maxeval=2 * p.nstart))
     torch.cuda.synchronize()
@@ -843,7 +846,7 @@ def measure_materialised(ctx, cg, W) -> dict:
     all_bytes = 2 * lib_bytes
     rate = p.maxeval / dt
     return {"workload": "genz8d4c with the integrand called on materialised points (nvec = 1e7, "
-                        "x and f dimension-major in HBM, library's own Genz integrand)",
+                        "x and f dimension-major in HBM, library's own Genz integrand specialised at run time)",
             "value": rate, "unit": UNIT, "ms_per_step": 1e3 * dt,
             "library_bytes_per_sample": lib_bytes, "all_bytes_per_sample": all_bytes,
             "hbm_gbs_all_kernels": rate * all_bytes / 1e9,

@@ -155,7 +155,7 @@ const char *cv_last_error(const cv_ctx *ctx);
 int cv_synchronize(cv_ctx *ctx);
 
 /* Device time of individual sampling-kernel launches (the kernel of the
- * sampling pass, Sect. 3.1's DoSample, without the launches around it).
+ * sampling pass, Sect. 2.1's DoSample, without the launches around it).
  * cv_kernel_timer(ctx, 1) clears the record and starts timing: every
  * sampling launch the context then makes on its stream outside stream
  * capture (cv_sample, cv_sample_staged, the iterations of cv_vegas and of
@@ -286,7 +286,11 @@ int cv_vegas_cb(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev integrand,
 
 /* A ready-made device integrand: the Genz components of `g` evaluated on
  * the materialised points (userdata = cv_genz_cb_data*; its flags carry
- * CV_FP64 / CV_AOS to match the call). */
+ * CV_FP64 / CV_AOS to match the call).  CV_JIT in those flags (FP32,
+ * dimension-major): the kernel is compiled at run time with the families
+ * and parameters as constants (NVRTC, cached per problem for the process;
+ * without NVRTC the generic kernel runs, with the same values).  Returns 0,
+ * or -999 when a launch fails. */
 typedef struct {
     cv_genz g;
     int flags;
@@ -299,7 +303,8 @@ int cv_genz_callback(const int *ndim, const void *x_dev, const int *ncomp, void 
 int cv_jit_info(int *available, int *compiled);
 /* Compile (without loading) the specialised sampling kernel CV_JIT would
  * build for integrand g with nbins bins and the point generator of flags
- * (0, CV_SCRAMBLE or CV_PSEUDO): a check that run-time
+ * (0, CV_SCRAMBLE or CV_PSEUDO), and the specialised built-in integrand
+ * (cv_genz_callback with CV_JIT) for g: a check that run-time
  * compilation works here and accepts this problem.  Needs no device.
  * Returns CV_OK, CV_EINVAL for an invalid g or nbins, or CV_ENOTFOUND when
  * NVRTC is missing or rejects the source; then `log` (log_len bytes,
@@ -499,8 +504,10 @@ int cv_batch_run(cv_batch *B);
 /* Synchronise and copy count results. */
 int cv_batch_results(cv_batch *B, cv_result *out);
 /* Time the first iteration's sampling with tile caps of 2^13, 2^15 and
- * 2^17 points and keep the fastest (resets the integrals; call before
- * run). */
+ * 2^17 points and, below the cap, iterations cut into at most 8, 16 or 32
+ * tiles (a tile is shared by the eight warps of a CTA, so these set the
+ * points per thread), and keep the fastest pair (resets the integrals;
+ * call before run). */
 int cv_batch_autotune(cv_batch *B);
 /* The per-iteration results of integral `item` of the batch's last run,
  * as cv_integral_log: iter_I[j*ncomp + c] = S1/n_j, iter_var[j*ncomp + c] =

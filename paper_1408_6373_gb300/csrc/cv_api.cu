@@ -1528,11 +1528,16 @@ static cudaError_t dispatch_batch_occupancy(int ndim, bool pow2, int stride, int
 // about 16 tiles per iteration, a power of two between 64 and cap.  It
 // depends on the integral alone, so a batch or a serving round never
 // changes how an integral's points are grouped and summed.
-static int tile_blocks_for(long long n, int cap)
+// Tile of an iteration of n points: the smallest power of two >= 64
+// blocks that cuts the iteration into at most `split` tiles, capped at
+// `cap` blocks.  A tile is shared evenly by a CTA's eight warps, so the
+// points each thread takes from a tile are tile / 8: split and cap set the
+// points per thread (the autotuner picks both).
+static int tile_blocks_for(long long n, int cap, int split = 16)
 {
     const long long blocks = (n + 31) / 32 + 1;
     long long t = 64;
-    while (t < cap && t * 16 < blocks) t <<= 1;
+    while (t < cap && t * split < blocks) t <<= 1;
     return (int)t;
 }
 
@@ -1560,6 +1565,7 @@ struct cv_batch {
     struct Class { int ndim; bool pow2; int stride; int grid; };
     std::vector<Class> classes;
     int tile_cap = 2048;                         // largest tile, in 32-point blocks
+    int tile_split = 16;                         // an iteration's tiles (at most), below the cap
     int tile_fixed = 0;                          // CUBAGPU_TILE: every tile this size
     std::vector<int> item_class;
     // launch plan: per iteration, per class: tile offset and count, counter index
@@ -1599,7 +1605,7 @@ static int batch_build_tiles(cv_batch *B, int only_first_iteration)
                 unsigned long long s = 1;
                 for (int jj = 0; jj < j; ++jj) s += (unsigned long long)(sp.nstart + (long long)jj * sp.nincrease);
                 const unsigned long long n = (unsigned long long)(sp.nstart + (long long)j * sp.nincrease);
-                const int TB = B->tile_fixed ? B->tile_fixed : tile_blocks_for((long long)n, B->tile_cap);
+                const int TB = B->tile_fixed ? B->tile_fixed : tile_blocks_for((long long)n, B->tile_cap, B->tile_split);
                 // (tiles start on even 32-point blocks: see run_steps)
                 const unsigned long long qa = (s >> 5) & ~1ull, qb = (s + n + 31) >> 5;
                 for (unsigned long long q = qa; q < qb; q += (unsigned long long)TB) {
@@ -1940,60 +1946,66 @@ extern "C" int cv_batch_kernels_per_run(const cv_batch *B) { return B ? B->kerne
 extern "C" int cv_batch_tile_points(const cv_batch *B, long long n)
 {
     if (!B) return 0;
-    return 32 * (B->tile_fixed ? B->tile_fixed : tile_blocks_for(n, B->tile_cap));
+    return 32 * (B->tile_fixed ? B->tile_fixed : tile_blocks_for(n, B->tile_cap, B->tile_split));
 }
 
-// Measured tuning of the tile cap: time the first iteration's sampling
-// launches of every class with caps of 256, 1024 and 4096 blocks (a reset
-// before each trial, so no result is affected) and keep the fastest total.
-// The cap only bounds how an iteration is cut into tiles; an integral's
-// tiles still depend on that integral alone.
+// Measured tuning of the tiles: time the first iteration's sampling
+// launches of every class for tile caps of 256, 1024 and 4096 blocks and
+// iterations cut into at most 8, 16 or 32 tiles below the cap (the points
+// per thread), a reset before each trial so no result is affected, and
+// keep the fastest total.  The tiles still depend on each integral alone.
 extern "C" int cv_batch_autotune(cv_batch *B)
 {
     if (!B) return CV_EINVAL;
     if (B->tile_fixed) return CV_OK;
     cv_ctx *ctx = B->ctx;
     CV_CUDA(ctx, cudaSetDevice(ctx->device));
-    static const int cand[] = {256, 1024, 4096};
+    static const int caps[] = {256, 1024, 4096};
+    static const int splits[] = {8, 16, 32};
     float best = 1e30f;
-    int best_cap = B->tile_cap;
+    int best_cap = B->tile_cap, best_split = B->tile_split;
     cudaEvent_t e0, e1;
     CV_CUDA(ctx, cudaEventCreate(&e0));
     CV_CUDA(ctx, cudaEventCreate(&e1));
     int rc = CV_OK;
     for (int ci = 0; ci < 3 && !rc; ++ci) {
-        B->tile_cap = cand[ci];
-        rc = batch_build_tiles(B, 1);
-        if (rc) break;
-        if (B->counters_cap) cudaMemsetAsync(B->d_counters, 0, B->counters_cap * sizeof(int), ctx->stream);
-        launch_batch_reset(B->d_items, B->d_cargs, B->count, ctx->stream);
-        cudaEventRecord(e0, ctx->stream);
-        for (const cv_batch::Launch &L : B->plan) {
-            const cv_batch::Class &C = B->classes[L.cls];
-            BatchSampleArgs a;
-            a.items = B->d_items;
-            a.tiles = B->d_tiles + L.tile_off;
-            a.ntiles = L.ntiles;
-            a.stride = C.stride;
-            a.counter = B->d_counters + L.counter;
-            cudaError_t e = dispatch_batch_sample(C.ndim, C.pow2, a, C.grid < L.ntiles ? C.grid : L.ntiles, ctx->stream);
-            if (e != cudaSuccess) {
-                rc = cuda_fail(ctx, e, "autotune launch");
-                break;
+        for (int si = 0; si < 3 && !rc; ++si) {
+            B->tile_cap = caps[ci];
+            B->tile_split = splits[si];
+            rc = batch_build_tiles(B, 1);
+            if (rc) break;
+            if (B->counters_cap) cudaMemsetAsync(B->d_counters, 0, B->counters_cap * sizeof(int), ctx->stream);
+            launch_batch_reset(B->d_items, B->d_cargs, B->count, ctx->stream);
+            cudaEventRecord(e0, ctx->stream);
+            for (const cv_batch::Launch &L : B->plan) {
+                const cv_batch::Class &C = B->classes[L.cls];
+                BatchSampleArgs a;
+                a.items = B->d_items;
+                a.tiles = B->d_tiles + L.tile_off;
+                a.ntiles = L.ntiles;
+                a.stride = C.stride;
+                a.counter = B->d_counters + L.counter;
+                cudaError_t e = dispatch_batch_sample(C.ndim, C.pow2, a, C.grid < L.ntiles ? C.grid : L.ntiles, ctx->stream);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(ctx, e, "autotune launch");
+                    break;
+                }
             }
-        }
-        cudaEventRecord(e1, ctx->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_cap = cand[ci];
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_cap = caps[ci];
+                best_split = splits[si];
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B->tile_cap = best_cap;
+    B->tile_split = best_split;
     if (!rc) rc = batch_build_tiles(B, 0);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
@@ -2584,10 +2596,29 @@ extern "C" int cv_genz_callback(const int *ndim, const void *x_dev, const int *n
     if (!u || !ndim || !ncomp || !nvec || !ld || *ndim != u->g.ndim || *ncomp != u->g.ncomp) return -999;
     const long long n = *nvec;
     if (n <= 0) return 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return -999;
+    }
     long long grid = (n + kBlock - 1) / kBlock;
-    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid > (long long)sms * 16) grid = (long long)sms * 16;
     const bool aos = (u->flags & CV_AOS) != 0;
     cudaError_t e;
+    if ((u->flags & CV_JIT) && !(u->flags & CV_FP64) && !aos) {
+        // families and parameters compiled in (NVRTC, cached per problem);
+        // without NVRTC the generic kernel below runs
+        GenzParams<float> g;
+        fill_params<float>(&u->g, &g);
+        JitKernel k;
+        std::string err;
+        if (jit_points_kernel(dev, g, *ndim, &k, &err) == 0) {
+            const long long cap = (long long)sms * k.occ;
+            e = launch_jit_points(k, g, (const float *)x_dev, (float *)f_dev, n, *ld,
+                                  (int)(grid < cap ? grid : cap), (cudaStream_t)stream);
+            return e == cudaSuccess ? 0 : -999;
+        }
+    }
     if (u->flags & CV_FP64) {
         GenzParams<double> g;
         fill_params<double>(&u->g, &g);

@@ -279,8 +279,8 @@ __device__ __forceinline__ Real delay_chain(const Real (&x)[NDIM], int n)
 // scalar FMAs, whose parameter operands are immediates or constant-bank
 // operands (a packed instruction would need its parameter pair in
 // registers), in two interleaved chains.
-template <int NDIM, int C, int P, class I>
-__device__ __forceinline__ float axis_dot(const GenzParams<float> &g, const float (&z)[NDIM], float s0)
+template <int NDIM, int C, int P, class I, class G>
+__device__ __forceinline__ float axis_dot(const G &g, const float (&z)[NDIM], float s0)
 {
     float a0 = s0, a1 = 0.0f;
 #pragma unroll
@@ -296,8 +296,8 @@ __device__ __forceinline__ float axis_dot(const GenzParams<float> &g, const floa
 // with the parameter forms of GenzParams (base-2 exponents, q0 + q1 pairs).
 // Steps whose operands are all computed values (squares, the product over
 // axes) go two axes per packed instruction.
-template <int NDIM, int C, class I>
-__device__ __forceinline__ float genz_f32(const GenzParams<float> &g, const float (&z)[NDIM])
+template <int NDIM, int C, class I, class G>
+__device__ __forceinline__ float genz_f32(const G &g, const float (&z)[NDIM])
 {
     switch (I::template family<C>(g)) {
     case CV_OSCILLATORY: {
@@ -700,12 +700,12 @@ __device__ __forceinline__ void store_point(const SampleArgs<Real> &A, long long
 // One aligned 32-point block q, FP32: map, integrand, partial sums,
 // histogram.  EDGE: the block may hold indices outside [start, end), which
 // add nothing.  fv: the caller's values of the block (accumulate mode only).
-template <int NDIM, bool POW2, bool EDGE, class I>
+template <int NDIM, bool POW2, bool EDGE, class I, class G>
 __device__ __forceinline__ void sample_block(const SampleArgs<float> &A, const Smem<float> &sm,
                                              const unsigned (&X)[NDIM], unsigned long long q,
                                              unsigned long long start, unsigned long long end, int lane,
                                              int hmode, Partial<float> &P, const float (&fv)[CV_MAX_COMP],
-                                             int delay)
+                                             int delay, const G &gp)
 {
     const int N = I::nbins(A.nbins);
     bool valid = true;
@@ -728,7 +728,7 @@ __device__ __forceinline__ void sample_block(const SampleArgs<float> &A, const S
         }
         return;
     }
-    const int ncomp = I::ncomp(A.g);
+    const int ncomp = I::ncomp(gp);
     float f[CV_MAX_COMP];
     if constexpr (I::kMode == 2) {
 #pragma unroll
@@ -737,7 +737,7 @@ __device__ __forceinline__ void sample_block(const SampleArgs<float> &A, const S
         // the integrand-cost knob: delay multiply-adds per component, run
         // once per point and folded into J as J + 0 * t (exact: J is finite)
         if (delay) J += 0.0f * delay_chain<NDIM>(z, delay * ncomp);
-        f[0] = genz_f32<NDIM, 0, I>(A.g, z);
+        f[0] = genz_f32<NDIM, 0, I>(gp, z);
     }
     if (EDGE && !valid) J = 0.0f;  // (f is finite at every point of the block)
     // the f^2 histogram needs component 0 only: updated before the other
@@ -756,9 +756,9 @@ __device__ __forceinline__ void sample_block(const SampleArgs<float> &A, const S
         }
     }
     if constexpr (I::kMode != 2) {
-        f[1] = ncomp > 1 ? genz_f32<NDIM, 1, I>(A.g, z) : 0.0f;
-        f[2] = ncomp > 2 ? genz_f32<NDIM, 2, I>(A.g, z) : 0.0f;
-        f[3] = ncomp > 3 ? genz_f32<NDIM, 3, I>(A.g, z) : 0.0f;
+        f[1] = ncomp > 1 ? genz_f32<NDIM, 1, I>(gp, z) : 0.0f;
+        f[2] = ncomp > 2 ? genz_f32<NDIM, 2, I>(gp, z) : 0.0f;
+        f[3] = ncomp > 3 ? genz_f32<NDIM, 3, I>(gp, z) : 0.0f;
     }
     // the partial sums of J f and (J f)^2, two components per packed
     // instruction
@@ -843,18 +843,20 @@ __device__ __forceinline__ void sample_block(const SampleArgs<double> &A, const 
 //   at a time.
 constexpr unsigned kRun = 16;
 
-template <int NDIM, typename Real, bool POW2, bool EDGE, class I = RuntimeIntegrand<Real>>
+// gp: where the integrand policy reads its parameters (the launch's
+// GenzParams, or a register copy of one integral's).
+template <int NDIM, typename Real, bool POW2, bool EDGE, class I = RuntimeIntegrand<Real>, class G = GenzParams<Real>>
 __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<Real> &sm,
                                           typename Word<Real>::type (&X)[NDIM],
                                           unsigned long long q0, unsigned nsteps,
                                           unsigned long long start, unsigned long long end,
                                           int lane, int hmode, Acc<Real> (&s1)[CV_MAX_COMP],
-                                          Acc<Real> (&s2)[CV_MAX_COMP])
+                                          Acc<Real> (&s2)[CV_MAX_COMP], const G &gp)
 {
     using W = typename Word<Real>::type;
     const int li = (sizeof(Real) == 4 && POW2) ? I::table(A.map) : 0;  // direction table
     const unsigned per = EDGE ? 1u : 2u;  // blocks per loop trip
-    const int delay = I::delay(A.g);      // (read once: the integrand-cost knob)
+    const int delay = I::delay(gp);       // (read once: the integrand-cost knob)
     for (unsigned r0 = 0; r0 < nsteps; r0 += kRun) {
         const unsigned r1 = min(r0 + kRun, nsteps);
         Partial<Real> P;
@@ -870,7 +872,7 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
             }
             auto block = [&](unsigned long long qq, const Real (&fv)[CV_MAX_COMP]) {
                 if constexpr (sizeof(Real) == 4)
-                    sample_block<NDIM, POW2, EDGE, I>(A, sm, X, qq, start, end, lane, hmode, P, fv, delay);
+                    sample_block<NDIM, POW2, EDGE, I>(A, sm, X, qq, start, end, lane, hmode, P, fv, delay, gp);
                 else
                     sample_block<NDIM, EDGE, I>(A, sm, X, qq, start, end, lane, hmode, P, fv, delay);
             };
@@ -895,7 +897,7 @@ __device__ __forceinline__ void run_steps(const SampleArgs<Real> &A, const Smem<
         }
 #pragma unroll
         for (int c = 0; c < CV_MAX_COMP; ++c) {
-            if (c < I::ncomp(A.g)) {
+            if (c < I::ncomp(gp)) {
                 s1[c].add(P.v1(c));
                 s2[c].add(P.v2(c));
             }
@@ -1048,9 +1050,9 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         }
         const bool interior = (q0 * 32ull >= start) && (q1 * 32ull <= end) && !((q0 | q1) & 1ull);
         if (interior)
-            run_steps<NDIM, Real, POW2, false, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, hmode, s1, s2);
+            run_steps<NDIM, Real, POW2, false, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, hmode, s1, s2, A.g);
         else
-            run_steps<NDIM, Real, POW2, true, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, hmode, s1, s2);
+            run_steps<NDIM, Real, POW2, true, I>(A, sm, X, q0, (unsigned)(q1 - q0), start, end, lane, hmode, s1, s2, A.g);
     }
 
     if constexpr (I::kMode == 1) return;  // points stored: nothing to reduce
@@ -1127,6 +1129,66 @@ k_sample_pseudo(const __grid_constant__ SampleArgs<Real> A)
 }
 
 // ------------------------------------------------------------ batched kernel
+// The policy of one single-component integral of family F (a batched
+// tile's integral): family, component count and the loop over components
+// are compile-time; the parameters are read from the staged description.
+template <int F>
+struct TileIntegrand {
+    static constexpr int kMode = 0;
+    static constexpr int kGen = 0;
+    template <int C> __device__ __forceinline__ static constexpr int family(const GenzParams<float> &)
+    {
+        return C == 0 ? F : CV_CONST;
+    }
+    __device__ __forceinline__ static constexpr int ncomp(const GenzParams<float> &) { return 1; }
+    template <int C> __device__ __forceinline__ static float p0(const GenzParams<float> &g, int d) { return g.p0[0][d]; }
+    template <int C> __device__ __forceinline__ static float p1(const GenzParams<float> &g, int d) { return g.p1[0][d]; }
+    template <int C> __device__ __forceinline__ static float q0(const GenzParams<float> &g) { return g.q0[0]; }
+    template <int C> __device__ __forceinline__ static float q1(const GenzParams<float> &g) { return g.q1[0]; }
+    __device__ __forceinline__ static int delay(const GenzParams<float> &g) { return g.delay; }
+    __device__ __forceinline__ static int table(const MapParams &m) { return m.li; }
+    __device__ __forceinline__ static bool priv(const MapParams &m) { return m.priv != 0; }
+    __device__ __forceinline__ static int nbins(int n) { return n; }
+};
+
+// Dimension counts up to which the batched kernel evaluates single-component
+// integrals through TileIntegrand (the build compiles six more loops per
+// dimension count; the 17-32 dimension classes keep the general policy).
+constexpr int kTileSpecMaxDim = 16;
+
+// A warp's share of a batched tile: single-component integrals of the six
+// Genz families through their own policy, anything else through the
+// run-time one (parameters read from the staged description).  Both give
+// the same values: the same operations on the same parameters.
+template <int NDIM, bool POW2, bool EDGE>
+__device__ __forceinline__ void batch_steps(const SampleArgs<float> &A, const Smem<float> &sm, unsigned (&X)[NDIM],
+                                            unsigned long long w0, unsigned nsteps, unsigned long long start,
+                                            unsigned long long end, int lane, int hmode,
+                                            Acc<float> (&s1)[CV_MAX_COMP], Acc<float> (&s2)[CV_MAX_COMP])
+{
+    if constexpr (NDIM <= kTileSpecMaxDim) {
+        const int fam = A.g.family[0];
+        if (A.g.ncomp == 1 && fam >= 0 && fam < CV_CONST) {
+            switch (fam) {
+#define CV_TILE_FAMILY(F)                                                                                   \
+    case F:                                                                                                 \
+        run_steps<NDIM, float, POW2, EDGE, TileIntegrand<F>>(A, sm, X, w0, nsteps, start, end, lane, hmode, \
+                                                             s1, s2, A.g);                                 \
+        return;
+                CV_TILE_FAMILY(CV_OSCILLATORY)
+                CV_TILE_FAMILY(CV_PRODUCT_PEAK)
+                CV_TILE_FAMILY(CV_CORNER_PEAK)
+                CV_TILE_FAMILY(CV_GAUSSIAN)
+                CV_TILE_FAMILY(CV_C0)
+                CV_TILE_FAMILY(CV_DISCONTINUOUS)
+#undef CV_TILE_FAMILY
+            default: break;
+            }
+        }
+    }
+    run_steps<NDIM, float, POW2, EDGE>(A, sm, X, w0, nsteps, start, end, lane, hmode, s1, s2, A.g);
+}
+
 // Persistent sampling over a queue of tiles of many integrals (one
 // dimension class per launch).  A CTA takes the next tile from a device
 // counter, stages the tile's integral (grid and parameters) when it differs
@@ -1196,9 +1258,9 @@ k_batch_sample(const BatchSampleArgs B)
             }
             const bool interior = (w0 * 32ull >= start) && (w1 * 32ull <= end) && !((w0 | w1) & 1ull);
             if (interior)
-                run_steps<NDIM, float, POW2, false>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, hmode, s1, s2);
+                batch_steps<NDIM, POW2, false>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, hmode, s1, s2);
             else
-                run_steps<NDIM, float, POW2, true>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, hmode, s1, s2);
+                batch_steps<NDIM, POW2, true>(A, sm, X, w0, (unsigned)(w1 - w0), start, end, lane, hmode, s1, s2);
         }
         const int ncomp = A.g.ncomp;
 #pragma unroll
@@ -1264,7 +1326,22 @@ __device__ __forceinline__ void cp_async4(unsigned dst, const void *src, unsigne
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async4_full(unsigned dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Funnel shift right by a compile-time amount: the low word of (hi:lo) >>
+// SH, one instruction (the compiler would split a constant-amount funnel
+// shift into several).
+template <unsigned SH>
+__device__ __forceinline__ unsigned funnel_r(unsigned lo, unsigned hi)
+{
+    unsigned r;
+    asm("shf.r.wrap.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(lo), "r"(hi), "n"(SH));
+    return r;
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait()
 {
@@ -1274,6 +1351,10 @@ __device__ __forceinline__ void cp_async_wait()
 // Blocks of values the accumulate pass has requested ahead of the one it
 // works on (each a warp's 32 points x CV_MAX_COMP values).
 constexpr int kMatAhead = 4;
+// Blocks per unrolled group of the accumulate pass (its chunks start on
+// multiples of it, so the Gray-code steps inside a group are known in
+// advance).
+constexpr int kMatGroup = 8;
 
 // The grid table of a materialised pass in a block's shared memory: the
 // staged table when there is one, else converted from the FP64 edges.
@@ -1289,29 +1370,22 @@ __device__ __forceinline__ void mat_table(const SampleArgs<float> &A, Smem<float
     }
 }
 
-// Sobol words of index i for this lane alone (lanes may hold any indices):
-// XOR over the set bits k of g(i) of V_k, in the tables' step form (entry k
-// >= 5 is V_4 ^ V_k, so V_4 enters once per set bit above bit 4).
-template <int NDIM>
-__device__ __forceinline__ void sobol_at(unsigned (&X)[NDIM], unsigned long long i, int li)
-{
-    const unsigned long long g = i ^ (i >> 1);
-    unsigned long long ghi = g >> 5;
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-        unsigned x = 0u;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) x ^= ((g >> k) & 1ull) ? Dir<unsigned>::w(li, d, k) : 0u;
-        if (__popcll(ghi) & 1) x ^= Dir<unsigned>::w(li, d, 4);
-        X[d] = x;
-    }
-    while (ghi) {
-        const int k = __ffsll((long long)ghi) - 1 + 5;
-#pragma unroll
-        for (int d = 0; d < NDIM; ++d) X[d] ^= Dir<unsigned>::w(li, d, k);
-        ghi &= ghi - 1;
-    }
-}
+// Trailing zero bits of a nonzero constant.
+__host__ __device__ constexpr int ctz_const(unsigned v) { return (v & 1u) ? 0 : 1 + ctz_const(v >> 1); }
+
+// The bit-level map's constants for N = 2^L as compile-time values (the
+// same formulas as the host's make_map).
+template <int L>
+struct Pow2Map {
+    static constexpr int N = 1 << L;
+    static constexpr int top = 28 - L < 22 ? 28 - L : 22;
+    static constexpr int F = 23 - L;
+    static constexpr int G = 22 - top;
+    static constexpr unsigned mF = ((1u << F) - 1u) << (top - F + 1);
+    static constexpr unsigned expE = (unsigned)(127 + G - L) << 23;
+    static constexpr int li = L - 4;
+    static constexpr unsigned sA = 29 - L;
+};
 
 // Store pass: the points of indices [start, start + n) at x[d ld + j],
 // j = index - start.  A warp writes 32 consecutive j of a tile aligned in
@@ -1322,21 +1396,22 @@ __device__ __forceinline__ void sobol_at(unsigned (&X)[NDIM], unsigned long long
 // g(32q+k) = 2^4 ^ 2^(5 + ctz(q+1)).  The direction words of the table sit
 // in shared memory, where the two blocks' lookups of a step are one
 // broadcast each.  Tiles go to warps in rounds of kRun so that all warps
-// write within one window of x at a time.
-template <int NDIM>
+// write within one window of x at a time.  N = 2^L at compile time: table
+// offsets and map constants are immediates.
+template <int NDIM, int L>
 __global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, float>))
 k_mat_store(const __grid_constant__ SampleArgs<float> A)
 {
+    using P = Pow2Map<L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned sdir[NDIM][CV_SOBOL_BITS];
-    const int N = A.nbins;
-    const int li = A.map.li;
+    __shared__ unsigned sx0[kWarpsPerBlock][NDIM][32];
     Smem<float> sm;
-    mat_table<NDIM>(A, sm, smem_raw, N);
+    mat_table<NDIM>(A, sm, smem_raw, P::N);
     sm.h = nullptr;
-    set_addresses(sm, A.map.L);
+    set_addresses(sm, L);
     for (int idx = threadIdx.x; idx < NDIM * CV_SOBOL_BITS; idx += blockDim.x)
-        sdir[idx / CV_SOBOL_BITS][idx % CV_SOBOL_BITS] = Dir<unsigned>::w(li, idx / CV_SOBOL_BITS, idx % CV_SOBOL_BITS);
+        sdir[idx / CV_SOBOL_BITS][idx % CV_SOBOL_BITS] = Dir<unsigned>::w(P::li, idx / CV_SOBOL_BITS, idx % CV_SOBOL_BITS);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -1344,147 +1419,269 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
     const long long ntile = (n + 31) / 32;
     const long long gwarp = (long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const long long twarps = (long long)gridDim.x * kWarpsPerBlock;
-    const long long nchunk = (ntile + kRun - 1) / kRun;
-    const unsigned mF = A.map.mF, expE = A.map.expE, sA = A.map.sA;
+    constexpr int kSub = (int)kRun;  // tiles per sub-chunk (the unrolled loop)
+    // one chunk of consecutive tiles per warp (one skip-ahead each, an even
+    // share), walked in sub-chunks
+    const long long per = max(1ll, (ntile + twarps - 1) / twarps);
+    const long long nchunk = (ntile + per - 1) / per;
     const long long ld = A.ld;
-    // this lane's direction-word row base (shared window): + 4 (5 + c) + d rows
+    const unsigned g_hi = sm.g_hi;
     const unsigned sdir_sa = (unsigned)__cvta_generic_to_shared(&sdir[0][0]);
+    unsigned *x0s = &sx0[threadIdx.x >> 5][0][lane];  // this lane's running words, stride 32
     for (long long ch = gwarp; ch < nchunk; ch += twarps) {
-        const long long j0 = ch * kRun * 32 + lane;
-        const int nt = (int)min((long long)kRun, ntile - ch * kRun);
-        const long long rem = n - j0;  // (this lane's point of tile tt is valid while 32 tt < rem)
-        unsigned long long q = (A.start + (unsigned long long)j0) >> 5;  // this lane's Sobol block
-        unsigned X[NDIM];
-        sobol_at<NDIM>(X, A.start + (unsigned long long)j0, li);
-        if (A.gen == kGenScrambled) {
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d) X[d] ^= (unsigned)A.shift[d];
-        }
-        float *px = A.x + j0;
-        for (int tt = 0; tt < nt; ++tt) {
-            const bool valid = 32ll * tt < rem;
+        // the chunk's first words: lane 0's block qw holds this lane's index
+        // at offset k (carry 0) or the next block does (carry 1); the high
+        // part of the skip-ahead is the same for the whole warp
+        const unsigned long long iw = A.start + (unsigned long long)(ch * per * 32);
+        const unsigned long long qw = iw >> 5;
+        const unsigned kofs = (unsigned)(iw & 31ull) + (unsigned)lane;
+        {
+            unsigned X[NDIM];
+            sobol_skip<NDIM, unsigned>(X, qw, (int)(kofs & 31u), P::li);
+            const int cw = min(__ffsll((long long)(qw + 1ull)) - 1, CV_SOBOL_BITS - 6);
 #pragma unroll
             for (int d = 0; d < NDIM; ++d) {
-                const float f1 = __uint_as_float((X[d] & mF) | expE);
-                const float2 ew = lds_f2(__funnelshift_r(X[d], sm.g_hi, sA) + (unsigned)(d * N * 8));
-                const float z = __fmaf_rn(ew.y, f1, ew.x);
-                if (valid) px[d * ld] = z + 0.5f;
+                unsigned x = X[d];
+                if (kofs >= 32u) x ^= Dir<unsigned>::w(P::li, d, 5 + cw);
+                if (A.gen == kGenScrambled) x ^= (unsigned)A.shift[d];
+                x0s[d * 32] = x;
             }
-            // this lane's block q steps to q + 1
-            const int c = min(__ffsll((long long)(q + 1ull)) - 1, CV_SOBOL_BITS - 6);
-            const unsigned da = sdir_sa + (unsigned)((5 + c) * 4);
+        }
+        const long long tend = min(ntile, (ch + 1) * per);
+        for (long long t0 = ch * per; t0 < tend; t0 += kSub) {
+            const long long j0 = t0 * 32 + lane;
+            const int nt = (int)min((long long)kSub, tend - t0);
+            // this lane's point of tile tt exists while tt < nv
+            const long long r = n - j0;
+            const int nv = r <= 0 ? 0 : (int)min((long long)nt, (r + 31) / 32);
+            const bool full = nt == kSub && (t0 + kSub) * 32 <= n;  // (every lane's point of every tile)
+            // the step after tile tt: this lane's block to the next, Gray-code
+            // bit 5 + ctz(q + 1): its word's offset in the row
+            unsigned da[kSub];
+            {
+                unsigned long long q = (A.start + (unsigned long long)j0) >> 5;
 #pragma unroll
-            for (int d = 0; d < NDIM; ++d) X[d] ^= lds_u(da + (unsigned)(d * CV_SOBOL_BITS * 4));
-            ++q;
-            px += 32;
+                for (int tt = 0; tt < kSub; ++tt) {
+                    da[tt] = sdir_sa + 4u * (unsigned)(5 + min(__ffsll((long long)(q + 1ull)) - 1, CV_SOBOL_BITS - 6));
+                    ++q;
+                }
+            }
+            // one axis at a time: its row of x, kSub tiles of 32 points; the
+            // words after the last tile start the next sub-chunk
+#pragma unroll 1
+            for (int d = 0; d < NDIM; ++d) {
+                unsigned X = x0s[d * 32];
+                float *px = A.x + d * ld + j0;
+                const unsigned gd = g_hi + (unsigned)d;  // (table base of axis d >> (3 + L))
+                const unsigned dd = (unsigned)(d * CV_SOBOL_BITS * 4);
+                if (full) {
+#pragma unroll
+                    for (int tt = 0; tt < kSub; ++tt) {
+                        const float f1 = __uint_as_float((X & P::mF) | P::expE);
+                        const float2 ew = lds_f2(funnel_r<P::sA>(X, gd));
+                        const float z = __fmaf_rn(ew.y, f1, ew.x);
+                        px[32 * tt] = z + 0.5f;
+                        X ^= lds_u(da[tt] + dd);
+                    }
+                } else {
+#pragma unroll
+                    for (int tt = 0; tt < kSub; ++tt) {
+                        if (tt < nt) {
+                            const float f1 = __uint_as_float((X & P::mF) | P::expE);
+                            const float2 ew = lds_f2(funnel_r<P::sA>(X, gd));
+                            const float z = __fmaf_rn(ew.y, f1, ew.x);
+                            if (tt < nv) px[32 * tt] = z + 0.5f;
+                            X ^= lds_u(da[tt] + dd);
+                        }
+                    }
+                }
+                x0s[d * 32] = X;
+            }
         }
     }
+}
+
+// One chunk of the accumulate pass: blocks q0 .. q0 + nk - 1 (q0 a multiple of kMatGroup).
+// EDGE = false: every lane's point of every block is in [start, start + n)
+// and nk is a multiple of kMatGroup; EDGE = true: any chunk, points outside
+// add nothing.  The
+// values of block k + kMatAhead are requested while block k is worked on:
+// asynchronous copies into the warp's ring (each lane copies and later
+// reads only its own words; points outside copy zeros).
+template <int NDIM, int L, bool EDGE>
+__device__ __forceinline__ void mat_accum_chunk(const SampleArgs<float> &A, const Smem<float> &sm,
+                                                unsigned long long q0, int nk, int lane, unsigned ring,
+                                                int ncomp, Acc<float> (&s1)[CV_MAX_COMP],
+                                                Acc<float> (&s2)[CV_MAX_COMP])
+{
+    // plain FP32 partial sums over runs of kRun blocks, folded into the
+    // per-thread Kahan sums after each run (as the fused pass)
+    Partial<float> Pt;
+    Pt.zero();
+    auto fold = [&]() {
+#pragma unroll
+        for (int c = 0; c < CV_MAX_COMP; ++c) {
+            if (c < ncomp) {
+                s1[c].add(Pt.v1(c));
+                s2[c].add(Pt.v2(c));
+            }
+        }
+        Pt.zero();
+    };
+    using P = Pow2Map<L>;
+    const long long ld = A.ld;
+    const long long j0 = (long long)(q0 * 32ull + (unsigned long long)lane) - (long long)A.start;
+    int klo = 0, khi = nk;  // this lane's point of block k is j0 + 32 k, valid for k in [klo, khi)
+    if (EDGE) {
+        klo = j0 >= 0 ? 0 : (int)((31 - j0) / 32);
+        const long long r = A.n - j0;
+        khi = r <= 0 ? 0 : (int)min((long long)nk, (r + 31) / 32);
+    }
+    const float *pf = A.f + j0;  // (dereferenced at valid k only)
+    const float *pfc[CV_MAX_COMP];
+#pragma unroll
+    for (int c = 0; c < CV_MAX_COMP; ++c) pfc[c] = pf + c * ld;
+    unsigned X[NDIM];
+    sobol_skip<NDIM, unsigned>(X, q0, lane, P::li);
+    if (A.gen == kGenScrambled) {
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) X[d] ^= (unsigned)A.shift[d];
+    }
+    auto request = [&](int k) {
+        const unsigned stage = ring + (unsigned)((k & (kMatAhead - 1)) * (CV_MAX_COMP * 32 * 4));
+        if (EDGE) {
+            const bool v = k >= klo && k < khi;
+            const float *src = v ? pf + 32 * k : A.f;
+#pragma unroll
+            for (int c = 0; c < CV_MAX_COMP; ++c)
+                if (c < ncomp) cp_async4(stage + (unsigned)(c * 128), src + c * ld, v ? 4u : 0u);
+        } else if (k < nk) {
+#pragma unroll
+            for (int c = 0; c < CV_MAX_COMP; ++c)
+                if (c < ncomp) cp_async4_full(stage + (unsigned)(c * 128), pfc[c] + 32 * k);
+        }
+        cp_async_commit();
+    };
+    auto block = [&](int k) {
+        cp_async_wait<kMatAhead - 1>();  // (block k's copies have landed)
+        const unsigned stage = ring + (unsigned)((k & (kMatAhead - 1)) * (CV_MAX_COMP * 32 * 4));
+        float f[CV_MAX_COMP];
+#pragma unroll
+        for (int c = 0; c < CV_MAX_COMP; ++c) f[c] = c < ncomp ? lds_f(stage + (unsigned)(c * 128)) : 0.0f;
+        float J = (!EDGE || (k >= klo && k < khi)) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) J *= lds_f(funnel_r<P::sA>(X[d], sm.g_hi + (unsigned)d) + 4u);
+        const float v0 = J * f[0];
+        const float h = v0 * v0;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            const unsigned ha = funnel_r<P::sA + 1u>(X[d], sm.h_hi + (unsigned)d);
+            sts_f(ha, lds_f(ha) + h);
+        }
+        const float2 v01 = make_float2(v0, J * f[1]);
+        Pt.s1[0] = add2(Pt.s1[0], v01);
+        Pt.s2[0] = fma2(v01, v01, Pt.s2[0]);
+        if (ncomp > 2) {
+            const float2 v23 = make_float2(J * f[2], J * f[3]);
+            Pt.s1[1] = add2(Pt.s1[1], v23);
+            Pt.s2[1] = fma2(v23, v23, Pt.s2[1]);
+        }
+        __syncwarp();
+    };
+#pragma unroll
+    for (int k = 0; k < kMatAhead; ++k) request(k);
+    if constexpr (!EDGE) {
+        // groups of kMatGroup blocks from multiples of kMatGroup: the step
+        // out of block q0 + 8 m + kk flips Gray-code bits 4 and 5 +
+        // ctz(kk + 1), a word known at compile time (a constant-bank
+        // operand), except the step out of a group's last block (ctz >= 3:
+        // read at run time); the words after the chunk's last block are
+        // not needed
+        for (int k0 = 0; k0 < nk; k0 += kMatGroup) {
+#pragma unroll
+            for (int kk = 0; kk < kMatGroup; ++kk) {
+                const int k = k0 + kk;
+                block(k);
+                if (kk + 1 < kMatGroup) {
+#pragma unroll
+                    for (int d = 0; d < NDIM; ++d)
+                        X[d] ^= Dir<unsigned>::w(P::li, d, 5 + ctz_const((unsigned)(kk + 1)));
+                } else if (k + 1 < nk) {
+                    sobol_step<NDIM, unsigned>(X, q0 + (unsigned long long)k, P::li);
+                }
+                request(k + kMatAhead);
+            }
+            if (((k0 + kMatGroup) % (int)kRun) == 0) fold();
+        }
+    } else {
+        for (int k = 0; k < nk; k += 2) {
+            block(k);
+            sobol_step_even<NDIM, unsigned>(X, P::li);
+            request(k + kMatAhead);
+            if (k + 1 >= nk) break;
+            block(k + 1);
+            sobol_step<NDIM, unsigned>(X, q0 + (unsigned long long)(k + 1), P::li);
+            request(k + 1 + kMatAhead);
+            if (((k + 2) % (int)kRun) == 0) fold();
+        }
+    }
+    fold();
+    cp_async_wait<0>();  // (the ring is reused by the next chunk)
 }
 
 // Accumulate pass: the caller's values f[c ld + j] of the points of
 // [start, start + n), with every point's bins and Jacobian recomputed from
 // its Sobol words in aligned 32-index blocks (lane = the index's low five
 // bits), so each warp's f^2 histogram copy takes plain updates (the 32
-// lanes' bins are distinct); sums and histogram as the fused pass.
-template <int NDIM>
+// lanes' bins are distinct); sums and histogram as the fused pass.  N = 2^L
+// at compile time.
+template <int NDIM, int L>
 __global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, float>))
 k_mat_accum(const __grid_constant__ SampleArgs<float> A)
 {
+    using P = Pow2Map<L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = A.nbins;
-    const int li = A.map.li;
     const int ncomp = A.g.ncomp;
     Smem<float> sm;
-    mat_table<NDIM>(A, sm, smem_raw, N);
-    float *hist = reinterpret_cast<float *>(sm.ew + NDIM * N);
-    for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * N; i += blockDim.x) hist[i] = 0.0f;
+    mat_table<NDIM>(A, sm, smem_raw, P::N);
+    float *hist = reinterpret_cast<float *>(sm.ew + NDIM * P::N);
+    for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * P::N; i += blockDim.x) hist[i] = 0.0f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    sm.h = hist + warp * NDIM * N;
-    set_addresses(sm, A.map.L);
-    // this warp's ring of value stages, after the histogram copies
-    const unsigned ring = (unsigned)__cvta_generic_to_shared(hist + kWarpsPerBlock * NDIM * N) +
-                          (unsigned)(warp * kMatAhead * CV_MAX_COMP * 32 * 4);
+    sm.h = hist + warp * NDIM * P::N;
+    set_addresses(sm, L);
+    // this lane's words in its warp's ring of value stages, after the
+    // histogram copies: stage k at + k CV_MAX_COMP 128, value c at + c 128
+    const unsigned ring = (unsigned)__cvta_generic_to_shared(hist + kWarpsPerBlock * NDIM * P::N) +
+                          (unsigned)(warp * kMatAhead * CV_MAX_COMP * 32 * 4 + lane * 4);
     __syncthreads();
 
     // (st, when given, only carries the run's stop flag to the refinement
     // that follows: start and n are the launch's)
     if (A.st && blockIdx.x == 0 && threadIdx.x == 0)
         A.st->pass_active = *(volatile const int *)&A.st->stopped ? 0 : 1;
-    const unsigned long long start = A.start, end = start + (unsigned long long)A.n;
-    const unsigned long long qa = start >> 5;
-    const unsigned long long nblk = A.n > 0 ? ((end + 31ull) >> 5) - qa : 0ull;
+    const unsigned long long start = A.start;
+    const long long n = A.n;
+    // blocks [qa, qb) cover the pass; qa a multiple of kMatGroup, so every
+    // chunk starts on one (its steps' words are known in advance)
+    const unsigned long long qa = (start >> 5) & ~(unsigned long long)(kMatGroup - 1);
+    const unsigned long long qb = (start + (unsigned long long)n + 31ull) >> 5;
+    const unsigned long long nblk = n > 0 ? qb - qa : 0ull;
     const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarpsPerBlock + warp;
     const unsigned long long twarps = (unsigned long long)gridDim.x * kWarpsPerBlock;
-    const unsigned long long nchunk = (nblk + kRun - 1) / kRun;
-    const unsigned sA = A.map.sA;
-    const long long ld = A.ld;
+    // one chunk per warp (an even share, a multiple of kMatGroup blocks)
+    const unsigned long long per =
+        max((unsigned long long)kMatGroup, (nblk + twarps * kMatGroup - 1) / (twarps * kMatGroup) * kMatGroup);
+    const unsigned long long nchunk = (nblk + per - 1) / per;
     Acc<float> s1[CV_MAX_COMP], s2[CV_MAX_COMP];
     for (unsigned long long ch = gwarp; ch < nchunk; ch += twarps) {
-        const unsigned long long q0 = qa + ch * kRun;
-        const unsigned long long q1 = min(q0 + (unsigned long long)kRun, qa + nblk);
-        unsigned X[NDIM];
-        sobol_skip<NDIM, unsigned>(X, q0, lane, li);
-        if (A.gen == kGenScrambled) {
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d) X[d] ^= (unsigned)A.shift[d];
-        }
-        Partial<float> P;
-        P.zero();
-        // the values of block q + kMatAhead are requested while block q is
-        // worked on: asynchronous copies into this warp's ring of stages
-        // (each lane copies and later reads only its own words; lanes
-        // outside [start, end) copy zeros)
-        auto request = [&](unsigned long long q) {
-            const unsigned stage = ring + (unsigned)((q - q0) % kMatAhead) * (CV_MAX_COMP * 32 * 4);
-            const unsigned long long i = q * 32ull + (unsigned long long)lane;
-            const bool valid = q < q1 && i >= start && i < end;
-            const float *src = A.f + (valid ? (long long)(i - start) : 0ll);
-#pragma unroll
-            for (int c = 0; c < CV_MAX_COMP; ++c)
-                if (c < ncomp) cp_async4(stage + (unsigned)((c * 32 + lane) * 4), src + c * ld, valid ? 4u : 0u);
-            cp_async_commit();
-        };
-#pragma unroll
-        for (int k = 0; k < kMatAhead; ++k) request(q0 + k);
-        for (unsigned long long q = q0; q < q1; ++q) {
-            cp_async_wait<kMatAhead - 1>();  // (block q's copies have landed)
-            const unsigned stage = ring + (unsigned)((q - q0) % kMatAhead) * (CV_MAX_COMP * 32 * 4);
-            float f[CV_MAX_COMP];
-#pragma unroll
-            for (int c = 0; c < CV_MAX_COMP; ++c) f[c] = c < ncomp ? lds_f(stage + (unsigned)((c * 32 + lane) * 4)) : 0.0f;
-            const unsigned long long i = q * 32ull + (unsigned long long)lane;
-            float J = (i >= start && i < end) ? 1.0f : 0.0f;
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d)
-                J *= lds_f(__funnelshift_r(X[d], sm.g_hi, sA) + (unsigned)(d * N * 8 + 4));
-            const float v0 = J * f[0];
-            const float h = v0 * v0;
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d) {
-                const unsigned ha = __funnelshift_r(X[d], sm.h_hi, sA + 1u) + (unsigned)(d * N * 4);
-                sts_f(ha, lds_f(ha) + h);
-            }
-            const float2 v01 = make_float2(v0, J * f[1]);
-            P.s1[0] = add2(P.s1[0], v01);
-            P.s2[0] = fma2(v01, v01, P.s2[0]);
-            if (ncomp > 2) {
-                const float2 v23 = make_float2(J * f[2], J * f[3]);
-                P.s1[1] = add2(P.s1[1], v23);
-                P.s2[1] = fma2(v23, v23, P.s2[1]);
-            }
-            __syncwarp();
-            sobol_step<NDIM, unsigned>(X, q, li);
-            request(q + kMatAhead);
-        }
-        cp_async_wait<0>();  // (the ring is reused by the next chunk)
-#pragma unroll
-        for (int c = 0; c < CV_MAX_COMP; ++c) {
-            if (c < ncomp) {
-                s1[c].add(P.v1(c));
-                s2[c].add(P.v2(c));
-            }
-        }
+        const unsigned long long q0 = qa + ch * per;
+        const int nk = (int)min(per, qb - q0);
+        if ((unsigned long long)nk == per && q0 * 32ull >= start && (q0 + per) * 32ull <= start + (unsigned long long)n)
+            mat_accum_chunk<NDIM, L, false>(A, sm, q0, nk, lane, ring, ncomp, s1, s2);
+        else
+            mat_accum_chunk<NDIM, L, true>(A, sm, q0, nk, lane, ring, ncomp, s1, s2);
     }
+    const int N = P::N;
 
     __shared__ double red[kWarpsPerBlock][2 * CV_MAX_COMP];
 #pragma unroll
@@ -1519,10 +1716,43 @@ k_mat_accum(const __grid_constant__ SampleArgs<float> A)
 
 // Built-in integrand on materialised points (the library's own callback):
 // f_c(x_j) for the Genz components of g, same formulas as the fused pass.
+// FP32, dimension-major, with any integrand policy (the run-time
+// specialised one makes families and parameters constants).
+template <int NDIM, class I>
+__device__ __forceinline__ void genz_points_f32(const GenzParams<float> &g, const float *x, float *f, long long n,
+                                                long long ld)
+{
+    const int ncomp = I::ncomp(g);
+    const int delay = I::delay(g);
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        float z[NDIM];
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) z[d] = x[(long long)d * ld + j] - 0.5f;
+        float v[CV_MAX_COMP];
+        v[0] = genz_f32<NDIM, 0, I>(g, z);
+        v[1] = ncomp > 1 ? genz_f32<NDIM, 1, I>(g, z) : 0.0f;
+        v[2] = ncomp > 2 ? genz_f32<NDIM, 2, I>(g, z) : 0.0f;
+        v[3] = ncomp > 3 ? genz_f32<NDIM, 3, I>(g, z) : 0.0f;
+        if (delay) {
+#pragma unroll
+            for (int c = 0; c < CV_MAX_COMP; ++c)
+                if (c < ncomp) v[c] += 0.0f * delay_chain<NDIM>(z, delay);
+        }
+#pragma unroll
+        for (int c = 0; c < CV_MAX_COMP; ++c)
+            if (c < ncomp) f[(long long)c * ld + j] = v[c];
+    }
+}
+
 template <int NDIM, typename Real, bool AOS>
 __global__ void __launch_bounds__(kBlock)
 k_genz_points(const __grid_constant__ GenzParams<Real> g, const Real *x, Real *f, long long n, long long ld)
 {
+    if constexpr (sizeof(Real) == 4 && !AOS) {
+        genz_points_f32<NDIM, RuntimeIntegrand<float>>(g, x, f, n, ld);
+        return;
+    }
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (long long)gridDim.x * blockDim.x) {
         // (FP32 evaluates at the centred coordinate x - 1/2, FP64 at x)
@@ -1672,29 +1902,41 @@ cudaError_t batch_occupancy(bool pow2, int stride, int *blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBlock, want);
 }
 
+template <int NDIM, int L, int MODE>
+static cudaError_t launch_mat_lean(const SampleArgs<float> &a, int grid, cudaStream_t s)
+{
+    using P = Pow2Map<L>;
+    // (the compile-time map must be the one the host chose)
+    if (a.nbins != P::N || a.map.mF != P::mF || a.map.expE != P::expE || a.map.sA != P::sA || a.map.li != P::li)
+        return cudaErrorInvalidValue;
+    if (MODE == 1) {
+        const size_t smem = (size_t)NDIM * P::N * 8 + 8 * (size_t)P::N;
+        cudaError_t e = cudaFuncSetAttribute(k_mat_store<NDIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_mat_store<NDIM, L><<<grid, kBlock, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    const size_t smem = sample_smem_bytes(NDIM, P::N, false, true) +
+                        (size_t)kWarpsPerBlock * kMatAhead * CV_MAX_COMP * 32 * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_mat_accum<NDIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_mat_accum<NDIM, L><<<grid, kBlock, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NDIM, typename Real, bool POW2, int MODE>
 static cudaError_t launch_matpass_v(const SampleArgs<Real> &a, int grid, cudaStream_t s)
 {
     if constexpr (sizeof(Real) == 4 && POW2) {
         // the common case's own kernels (dimension-major, Sobol points; the
         // accumulate pass needs the warps' histogram copies to fit)
-        if (!a.aos && a.gen != kGenPseudo) {
-            if (MODE == 1) {
-                const size_t smem = (size_t)NDIM * a.nbins * 8 + 8 * (size_t)a.nbins;
-                cudaError_t e = cudaFuncSetAttribute(k_mat_store<NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)smem);
-                if (e != cudaSuccess) return e;
-                k_mat_store<NDIM><<<grid, kBlock, smem, s>>>(a);
-                return cudaGetLastError();
-            }
-            if (a.map.priv) {
-                const size_t smem = sample_smem_bytes(NDIM, a.nbins, false, true) +
-                                    (size_t)kWarpsPerBlock * kMatAhead * CV_MAX_COMP * 32 * 4;
-                cudaError_t e = cudaFuncSetAttribute(k_mat_accum<NDIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)smem);
-                if (e != cudaSuccess) return e;
-                k_mat_accum<NDIM><<<grid, kBlock, smem, s>>>(a);
-                return cudaGetLastError();
+        if (!a.aos && a.gen != kGenPseudo && (MODE == 1 || a.map.priv)) {
+            switch (a.map.L) {
+            case 5: return launch_mat_lean<NDIM, 5, MODE>(a, grid, s);
+            case 6: return launch_mat_lean<NDIM, 6, MODE>(a, grid, s);
+            case 7: return launch_mat_lean<NDIM, 7, MODE>(a, grid, s);
+            case 8: return launch_mat_lean<NDIM, 8, MODE>(a, grid, s);
+            default: break;
             }
         }
     }

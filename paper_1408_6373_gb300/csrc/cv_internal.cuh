@@ -336,6 +336,10 @@ int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow
 // compile the specialised source without loading it (checks NVRTC and the source)
 int jit_compile_check(const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks, std::string *err);
 cudaError_t launch_jit_sample(const JitKernel &k, const SampleArgs<float> &a, int grid, cudaStream_t s);
+// the built-in integrand on dimension-major FP32 points, specialised for g
+int jit_points_kernel(int device, const GenzParams<float> &g, int ndim, JitKernel *out, std::string *err);
+cudaError_t launch_jit_points(const JitKernel &k, const GenzParams<float> &g, const float *x, float *f, long long n,
+                              long long ld, int grid, cudaStream_t s);
 int jit_info(int *compiled);
 // cv_api.cu: the parameters of a built-in integrand in the kernels' forms
 template <typename Real>

@@ -82,8 +82,9 @@ void hexf(std::string &s, float v)
     s += buf;
 }
 
-// Source of the specialised kernel for these parameters.
-std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks)
+// The integrand policy of the specialised kernels: families, parameters
+// and (for the sampling kernel) map choices as compile-time constants.
+std::string policy_source(const SampleArgs<float> &a, int ndim, bool pow2)
 {
     const GenzParams<float> &g = a.g;
     std::string s = "#include \"cv_device.cuh\"\nnamespace cv {\nstruct JitIntegrand {\n";
@@ -131,12 +132,35 @@ std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, 
     s += "  __device__ __forceinline__ static constexpr int nbins(int) { return " + std::to_string(a.nbins) +
          "; }\n";
     s += "};\n}\n";
+    return s;
+}
+
+// Source of the specialised sampling kernel for these parameters.
+std::string specialised_source(const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks)
+{
+    std::string s = policy_source(a, ndim, pow2);
     s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(kBlock) + ", " +
          std::to_string(min_blocks) + ") cv_jit_sample(const __grid_constant__ cv::SampleArgs<float> A)\n{\n";
     s += "    cv::sample_pass<" + std::to_string(ndim) + ", float, " + (pow2 ? "true" : "false") +
          ", cv::JitIntegrand>(A);\n}\n";
     return s;
 }
+
+// Source of the specialised built-in integrand on materialised points
+// (dimension-major FP32): the policy's families and parameters only.
+std::string points_source(const GenzParams<float> &g, int ndim)
+{
+    SampleArgs<float> a;
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    std::string s = policy_source(a, ndim, false);
+    s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(kBlock) +
+         ") cv_jit_points(const __grid_constant__ cv::GenzParams<float> g, const float *x, float *f, "
+         "long long n, long long ld)\n{\n";
+    s += "    cv::genz_points_f32<" + std::to_string(ndim) + ", cv::JitIntegrand>(g, x, f, n, ld);\n}\n";
+    return s;
+}
+
 
 }  // namespace
 
@@ -175,13 +199,73 @@ int jit_compile_check(const SampleArgs<float> &a, int ndim, bool pow2, int min_b
 {
     std::vector<char> cubin;
     std::lock_guard<std::mutex> lk(g_mu);
-    return compile_source(specialised_source(a, ndim, pow2, min_blocks), &cubin, err);
+    if (compile_source(specialised_source(a, ndim, pow2, min_blocks), &cubin, err)) return -1;
+    // (and the built-in integrand's kernel for the same problem)
+    return compile_source(points_source(a.g, ndim), &cubin, err);
 }
+
+// Compile (once per device and source) and load a kernel named `name`.
+static int jit_load(int device, const std::string &src, const char *name, size_t smem, JitKernel *out,
+                    std::string *err);
+
+namespace {
+// Loaded kernels by the raw values their source is generated from, so that
+// a launch finds its kernel without generating the source text again.
+std::map<std::string, JitKernel> g_fast;
+
+void key_add(std::string &k, const void *p, size_t n) { k.append(static_cast<const char *>(p), n); }
+}  // namespace
 
 int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow2, int min_blocks,
                       JitKernel *out, std::string *err)
 {
-    const std::string src = specialised_source(a, ndim, pow2, min_blocks);
+    std::string key("S");
+    const int v[8] = {device, ndim, pow2 ? 1 : 0, min_blocks, a.nbins, a.gen == kGenPseudo ? 1 : 0,
+                      pow2 ? a.map.li : 0, pow2 && a.map.priv ? 1 : 0};
+    key_add(key, v, sizeof(v));
+    key_add(key, &a.g, sizeof(a.g));  // (GenzParams is zeroed before it is filled)
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_fast.find(key);
+        if (it != g_fast.end()) {
+            *out = it->second;
+            return 0;
+        }
+    }
+    const int rc = jit_load(device, specialised_source(a, ndim, pow2, min_blocks), "cv_jit_sample",
+                            sample_smem_bytes(ndim, a.nbins, false, pow2 && a.map.priv), out, err);
+    if (rc == 0) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_fast[key] = *out;
+    }
+    return rc;
+}
+
+int jit_points_kernel(int device, const GenzParams<float> &g, int ndim, JitKernel *out, std::string *err)
+{
+    std::string key("P");
+    const int v[2] = {device, ndim};
+    key_add(key, v, sizeof(v));
+    key_add(key, &g, sizeof(g));
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_fast.find(key);
+        if (it != g_fast.end()) {
+            *out = it->second;
+            return 0;
+        }
+    }
+    const int rc = jit_load(device, points_source(g, ndim), "cv_jit_points", 0, out, err);
+    if (rc == 0) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_fast[key] = *out;
+    }
+    return rc;
+}
+
+static int jit_load(int device, const std::string &src, const char *name, size_t smem, JitKernel *out,
+                    std::string *err)
+{
     const std::string key = std::to_string(device) + "\n" + src;
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
@@ -193,12 +277,12 @@ int jit_sample_kernel(int device, const SampleArgs<float> &a, int ndim, bool pow
     if (compile_source(src, &cubin, err)) return -1;
     JitKernel k;
     if (cudaLibraryLoadData(&k.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
-        cudaLibraryGetKernel(&k.kernel, k.lib, "cv_jit_sample") != cudaSuccess) {
+        cudaLibraryGetKernel(&k.kernel, k.lib, name) != cudaSuccess) {
         cudaGetLastError();
         *err = "loading the specialised kernel failed";
         return -1;
     }
-    k.smem = sample_smem_bytes(ndim, a.nbins, false, pow2 && a.map.priv);
+    k.smem = smem;
     if (cudaFuncSetAttribute((const void *)k.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)k.smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k.occ, (const void *)k.kernel, kBlock, k.smem) !=
@@ -220,6 +304,13 @@ int jit_info(int *compiled)
     const bool ok = load_nvrtc(&err);
     *compiled = (int)g_cache.size();
     return ok ? 1 : 0;
+}
+
+cudaError_t launch_jit_points(const JitKernel &k, const GenzParams<float> &g, const float *x, float *f, long long n,
+                              long long ld, int grid, cudaStream_t s)
+{
+    void *args[5] = {const_cast<GenzParams<float> *>(&g), &x, &f, &n, &ld};
+    return cudaLaunchKernel((const void *)k.kernel, dim3(grid), dim3(kBlock), args, 0, s);
 }
 
 cudaError_t launch_jit_sample(const JitKernel &k, const SampleArgs<float> &a, int grid, cudaStream_t s)

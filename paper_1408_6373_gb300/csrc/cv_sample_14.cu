@@ -1,0 +1,8 @@
+// cv_sample_14.cu -- instantiates the sampling, materialised-sample and Sobol
+// kernels for ndim 15 and 31 (the 32 dimension counts are spread over
+// sixteen files, a small count with a large one so the files take similar
+// time, and compiled in parallel).
+#include "cv_device.cuh"
+
+CV_INSTANTIATE_NDIM(15)
+CV_INSTANTIATE_NDIM(31)

@@ -1,0 +1,8 @@
+// cv_sample_15.cu -- instantiates the sampling, materialised-sample and Sobol
+// kernels for ndim 16 and 32 (the 32 dimension counts are spread over
+// sixteen files, a small count with a large one so the files take similar
+// time, and compiled in parallel).
+#include "cv_device.cuh"
+
+CV_INSTANTIATE_NDIM(16)
+CV_INSTANTIATE_NDIM(32)

@@ -1,0 +1,8 @@
+// cv_sample_8.cu -- instantiates the sampling, materialised-sample and Sobol
+// kernels for ndim 9 and 25 (the 32 dimension counts are spread over
+// sixteen files, a small count with a large one so the files take similar
+// time, and compiled in parallel).
+#include "cv_device.cuh"
+
+CV_INSTANTIATE_NDIM(9)
+CV_INSTANTIATE_NDIM(25)

@@ -1,0 +1,8 @@
+// cv_sample_9.cu -- instantiates the sampling, materialised-sample and Sobol
+// kernels for ndim 10 and 26 (the 32 dimension counts are spread over
+// sixteen files, a small count with a large one so the files take similar
+// time, and compiled in parallel).
+#include "cv_device.cuh"
+
+CV_INSTANTIATE_NDIM(10)
+CV_INSTANTIATE_NDIM(26)

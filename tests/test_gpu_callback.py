@@ -67,11 +67,12 @@ def test_builtin_integrand_fp32_close_to_fused(ctx):
 # FP32 bounds.  Tiles of 3333 points start at unaligned indices (the store
 # pass's shifted warps, ragged last tiles); 64 and 128 bins take the
 # dimension-major power-of-two kernels, 50 bins the general pass; scrambled
-# points too.
+# points too; the library's integrand generic or specialised at run time.
+@pytest.mark.parametrize("jit", [0, cg.JIT], ids=["generic", "jit"])
 @pytest.mark.parametrize("gen", ["sobol", "scrambled"])
 @pytest.mark.parametrize("nbins", [64, 128, 50])
 @pytest.mark.parametrize("nvec", [3333, 1 << 16])
-def test_materialised_fp32_pass_matches_oracle(ctx, nvec, nbins, gen):
+def test_materialised_fp32_pass_matches_oracle(ctx, nvec, nbins, gen, jit):
     ndim, fams = 8, [O.GAUSSIAN, O.PRODUCT_PEAK, O.OSCILLATORY, O.C0]
     rng = np.random.default_rng(17 + nbins)
     a = rng.uniform(0.5, 1.5, (4, ndim))
@@ -79,7 +80,7 @@ def test_materialised_fp32_pass_matches_oracle(ctx, nvec, nbins, gen):
     n = 100003
     flags, seed = (cg.SCRAMBLE, 11) if gen == "scrambled" else (0, 0)
     g = cg.genz(ndim, fams, a, u)
-    r = ctx.vegas_cb(cg.builtin_integrand(), ndim, 4, userdata=cg.GenzCallbackData(g, 0), nvec=nvec,
+    r = ctx.vegas_cb(cg.builtin_integrand(), ndim, 4, userdata=cg.GenzCallbackData(g, jit), nvec=nvec,
                      flags=flags, seed=seed, maxeval=n, nstart=n, nbins=nbins)
     assert (r.neval, r.fail) == (n, 1)
     p = O.Problem(ndim, fams, a, u, nbins=nbins, bits=23, gen=O.SCRAMBLED if flags else O.SOBOL, seed=seed)
