@@ -488,6 +488,7 @@ static int sample_grid(cv_ctx *ctx, int occ, long long n)
 struct PassParts {
     void *mem = nullptr;
     int G_cap = 0;
+    bool consumer_sums = false;  // the combination adds the sum partials (no ticket)
 };
 
 static void parts_args(const PassParts *pp, int grid, double **S, void **H, unsigned **ticket)
@@ -555,6 +556,7 @@ static int launch_pass(cv_ctx *ctx, const cv_genz *g, int nbins, const double *e
         if (grid_out) *grid_out = grid;
         if (pp && pp->mem && grid <= pp->G_cap) {
             parts_args(pp, grid, &a.part_S, &a.part_H, &a.part_ticket);
+            if (pp->consumer_sums) a.part_ticket = nullptr;
             a.part_G = grid;
         }
     };
@@ -880,6 +882,7 @@ static int enqueue_iteration(cv_integral *I, cudaStream_t s)
         unsigned *t;
         parts_args(&I->parts, grid, &S, &Hp, &t);
         ca.part_H = Hp;
+        ca.part_S = S;
         ca.part_G = grid;
         ca.part_nh = sp.g.ndim * sp.nbins;
         ca.part_f32 = (sp.flags & CV_FP64) ? 0 : 1;
@@ -992,6 +995,7 @@ static int integral_create(cv_ctx *ctx, const cv_spec *spec, cv_integral **out, 
     if (fp32) I->ew32 = (float2 *)(p + sz_state + sz_edges + sz_H + 2 * sz_log);
     I->parts.mem = p + sz_state + sz_edges + sz_H + 2 * sz_log + ((sz_ew + 255) & ~(size_t)255);
     I->parts.G_cap = G;
+    I->parts.consumer_sums = true;  // (the iteration's combination adds the sums)
     // (the ticket starts at zero; every pass's last block leaves it so)
     CV_CUDA(ctx, cudaMemsetAsync(I->parts.mem, 0, 256, ctx->stream));
     {

@@ -1110,7 +1110,7 @@ __device__ __forceinline__ void sample_pass(const SampleArgs<Real> &A)
         if (parts) ph[d * N + k] = v;
         else if (v != Real(0)) atomicAdd(&A.H[d * N + k], (double)v);
     }
-    if (parts) last_block_sums(A.part_S, A.part_ticket, A.S1, A.S2, ncomp);
+    if (parts && A.part_ticket) last_block_sums(A.part_S, A.part_ticket, A.S1, A.S2, ncomp);
 }
 
 template <int NDIM, typename Real, bool POW2>

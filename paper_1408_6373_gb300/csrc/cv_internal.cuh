@@ -207,12 +207,14 @@ struct SampleArgs {
     unsigned long long shift[CV_MAX_DIM];
     // Deterministic reduction (part_S non-null; the launch's grid must be
     // part_G blocks): block b writes its sums to part_S[b][2 c + {0, 1}] and
-    // its histogram to part_H[b][ndim][nbins] (Real), no atomics; the last
-    // block to finish (a ticket, zero before the launch and reset by that
-    // block) adds the blocks' sums to S1, S2 in block order, and the
-    // histogram partials are summed per bin in block order by the kernel
-    // that consumes them (refinement, or a reduction after a plain pass).
-    // Null: FP64 atomics, whose order varies from run to run.
+    // its histogram to part_H[b][ndim][nbins] (Real), no atomics.  With a
+    // ticket (zero before the launch and reset by that block) the last
+    // block to finish adds the blocks' sums to S1, S2 in block order;
+    // without one the sums are left to the kernel that consumes the pass
+    // (the combination of an integral's iteration).  The histogram partials
+    // are summed per bin in block order by that kernel too (refinement, or
+    // a reduction after a standalone pass).  Null: FP64 atomics, whose
+    // order varies from run to run.
     double *part_S;                 // [part_G][2 CV_MAX_COMP]
     void *part_H;                   // [part_G][ndim][nbins]
     unsigned *part_ticket;
@@ -240,6 +242,10 @@ struct CombineArgs {
     int part_G;
     int part_nh;                    // ndim * nbins: values per block
     int part_f32;                   // partials are floats (FP32 pass)
+    // the pass's sum partials (SampleArgs::part_S of a launch without a
+    // ticket), summed by the combination in block order; null: the pass
+    // added them to S1, S2 itself
+    const double *part_S;
 };
 
 // ---- batched persistent launch (many integrals) ----

@@ -389,11 +389,27 @@ __device__ void combine_iteration(const CombineArgs &A)
     __shared__ int s_ok[CV_MAX_COMP];
     __shared__ int s_bad[CV_MAX_COMP];
     __shared__ int s_stop;
+    __shared__ double s_sum[2 * CV_MAX_COMP];
+    if (A.part_S) {
+        // the pass's sums, block partials added in block order: warp w takes
+        // values w, w + warps, ...; lane l the blocks l, l + 32, ..., then a
+        // fixed shuffle tree (as a pass's last block would)
+        const int lane = c & 31, nwarp = (int)(blockDim.x >> 5);
+        for (int v = c >> 5; v < 2 * A.ncomp; v += nwarp) {
+            double acc = 0.0;
+            for (int b = lane; b < A.part_G; b += 32) acc += __ldcg(&A.part_S[b * (2 * CV_MAX_COMP) + v]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) s_sum[v] = acc;
+        }
+        __syncthreads();
+    }
     if (c < A.ncomp) {
         // every input first (independent loads), then the arithmetic: FP64
         // latency is high, so divisions are reciprocal multiplications
         // except where a reciprocal itself is the result
-        const double S1 = st->S1[c], S2 = st->S2[c];
+        const double S1 = A.part_S ? s_sum[2 * c] : st->S1[c];
+        const double S2 = A.part_S ? s_sum[2 * c + 1] : st->S2[c];
         const double sumI0 = st->sumI[c], W0 = st->W[c], mean0 = st->mean[c], M20 = st->M2[c];
         int zero = st->zero[c];
         const double dn = (double)n;
@@ -630,8 +646,9 @@ cudaError_t launch_refine_combine(int ndim, int nbins, double *H, double *edges,
                                   const CombineArgs &a, float2 *ew32, const MapParams &map,
                                   cudaStream_t s)
 {
-    // (with block partials to add, a full CTA per axis: see sum_parts_axis)
-    const int threads = a.part_H ? 1024 : refine_threads(nbins);
+    // (with many block partials to add, a full CTA per axis: see
+    // sum_parts_axis; a few are summed by the threads of the bins)
+    const int threads = a.part_H && a.part_G >= 64 ? 1024 : refine_threads(nbins);
     k_refine_combine<<<ndim + 1, threads, 0, s>>>(ndim, nbins, H, edges, a, ew32, map);
     return cudaGetLastError();
 }
