@@ -697,6 +697,9 @@ __device__ __forceinline__ void store_point(const SampleArgs<Real> &A, long long
     for (int d = 0; d < NDIM; ++d) xp[d * sd] = x[d];
 }
 
+// Axes whose histogram bins a lane reads before it writes them back.
+constexpr int kHistBatch = 4;
+
 // One aligned 32-point block q, FP32: map, integrand, partial sums,
 // histogram.  EDGE: the block may hold indices outside [start, end), which
 // add nothing.  fv: the caller's values of the block (accumulate mode only).
@@ -745,14 +748,26 @@ __device__ __forceinline__ void sample_block(const SampleArgs<float> &A, const S
     const float v0 = J * f[0];
     if (!EDGE || valid) {
         const float h = v0 * v0;
+        // the bin's float in the histogram copy: one funnel shift of the
+        // word (power-of-two map), or slot * 4 (general map)
+        auto haddr = [&](int d) {
+            return (POW2 ? __funnelshift_r(X[d], sm.h_hi, A.map.sA + 1u) : sm.h_sa + slot[d] * 4u) +
+                   (unsigned)(d * sm.stride * 4);
+        };
+        if (hmode == kHistWarpPlain) {
+            // a few axes' bins read first, then written (the axes' rows are
+            // disjoint, so the reads need not wait for the writes)
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) {
-            // the bin's float in the histogram copy: one funnel shift of the
-            // word (power-of-two map), or slot * 4 (general map)
-            const unsigned ha = (POW2 ? __funnelshift_r(X[d], sm.h_hi, A.map.sA + 1u) : sm.h_sa + slot[d] * 4u) +
-                                (unsigned)(d * sm.stride * 4);
-            if (hmode == kHistWarpPlain) sts_f(ha, lds_f(ha) + h);
-            else reds_add_f(ha, h);
+            for (int d0 = 0; d0 < NDIM; d0 += kHistBatch) {
+                float hv[kHistBatch];
+#pragma unroll
+                for (int d = d0; d < d0 + kHistBatch && d < NDIM; ++d) hv[d - d0] = lds_f(haddr(d));
+#pragma unroll
+                for (int d = d0; d < d0 + kHistBatch && d < NDIM; ++d) sts_f(haddr(d), hv[d - d0] + h);
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) reds_add_f(haddr(d), h);
         }
     }
     if constexpr (I::kMode != 2) {
@@ -1349,8 +1364,11 @@ __device__ __forceinline__ void cp_async_wait()
 }
 
 // Blocks of values the accumulate pass has requested ahead of the one it
-// works on (each a warp's 32 points x CV_MAX_COMP values).
-constexpr int kMatAhead = 4;
+// works on (each a warp's 32 points x CV_MAX_COMP values), and its resident
+// CTAs per SM (two: 128 registers, so a block's bins can all be read before
+// they are written; the ring keeps 16 warps x 8 blocks of values in flight).
+constexpr int kMatAhead = 8;
+constexpr int kMatAccumBlocks = 2;
 // Blocks per unrolled group of the accumulate pass (its chunks start on
 // multiples of it, so the Gray-code steps inside a group are known in
 // advance).
@@ -1573,10 +1591,17 @@ __device__ __forceinline__ void mat_accum_chunk(const SampleArgs<float> &A, cons
         for (int d = 0; d < NDIM; ++d) J *= lds_f(funnel_r<P::sA>(X[d], sm.g_hi + (unsigned)d) + 4u);
         const float v0 = J * f[0];
         const float h = v0 * v0;
+        // the bins of up to eight axes read first, then written (the axes'
+        // rows are disjoint, so the reads need not wait for the writes)
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) {
-            const unsigned ha = funnel_r<P::sA + 1u>(X[d], sm.h_hi + (unsigned)d);
-            sts_f(ha, lds_f(ha) + h);
+        for (int d0 = 0; d0 < NDIM; d0 += 8) {
+            float hv[8];
+#pragma unroll
+            for (int d = d0; d < d0 + 8 && d < NDIM; ++d)
+                hv[d - d0] = lds_f(funnel_r<P::sA + 1u>(X[d], sm.h_hi + (unsigned)d));
+#pragma unroll
+            for (int d = d0; d < d0 + 8 && d < NDIM; ++d)
+                sts_f(funnel_r<P::sA + 1u>(X[d], sm.h_hi + (unsigned)d), hv[d - d0] + h);
         }
         const float2 v01 = make_float2(v0, J * f[1]);
         Pt.s1[0] = add2(Pt.s1[0], v01);
@@ -1636,7 +1661,7 @@ __device__ __forceinline__ void mat_accum_chunk(const SampleArgs<float> &A, cons
 // lanes' bins are distinct); sums and histogram as the fused pass.  N = 2^L
 // at compile time.
 template <int NDIM, int L>
-__global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, float>))
+__global__ void __launch_bounds__(kBlock, kMatAccumBlocks)
 k_mat_accum(const __grid_constant__ SampleArgs<float> A)
 {
     using P = Pow2Map<L>;
@@ -1920,6 +1945,18 @@ static cudaError_t launch_mat_lean(const SampleArgs<float> &a, int grid, cudaStr
                         (size_t)kWarpsPerBlock * kMatAhead * CV_MAX_COMP * 32 * 4;
     cudaError_t e = cudaFuncSetAttribute(k_mat_accum<NDIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // (at most one wave of this kernel's own residency)
+    static int occ = 0;
+    int dev = 0, sms = 0;
+    if (!occ) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mat_accum<NDIM, L>, kBlock, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+    }
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (grid > sms * occ) grid = sms * occ;
     k_mat_accum<NDIM, L><<<grid, kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
