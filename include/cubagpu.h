@@ -273,7 +273,11 @@ typedef int (*cv_integrand_dev)(const int *ndim, const void *x_dev, const int *n
  * flags may add CV_AOS.  Returns CV_EABORT (and *fail = -999) when the
  * integrand returns -999, and CV_ENONFINITE (*fail = 1, outputs filled)
  * when an iteration's result is NaN or infinite -- e.g. the integrand wrote
- * a NaN.  The points, values and state live in a device
+ * a NaN.  The accumulate passes leave per-block partial rows that are
+ * added in block order (no floating-point atomics), so the same call gives
+ * the same bits on every run (with nbins other than 2^L >= 32 in FP32 the
+ * histogram takes shared-memory atomics within a block, in hardware order).
+ * The points, values and state live in a device
  * scratch area of the context (about (ndim + ncomp) * nvec values), grown
  * on demand and kept until cv_destroy, so calls on one context must not
  * overlap. */
@@ -493,10 +497,14 @@ void cv_integral_destroy(cv_integral *I);
  * <= 227 KiB, e.g. 32 x 128 or 20 x 256).  An integral's points are cut
  * into tiles by a rule that depends on that integral alone (about 16
  * tiles per iteration, 2^11 .. cap points each; CUBAGPU_TILE, points,
- * forces one size), and each tile's FP32 histogram is summed in a fixed
- * order, so an integral's result is the same alone and in any batch up to
- * the order of FP64 additions.  It agrees with cv_vegas within the FP32
- * tolerance (the single-integral kernel groups points differently). */
+ * forces one size), and each tile leaves its sums and histogram as
+ * partial rows that the refinement and combination add in tile order (no
+ * floating-point atomics), so an integral's result is the same alone, in
+ * any batch and on every run, bit for bit, for the same tile cap and split
+ * (with nbins other than 2^L >= 32 a warp's histogram copy takes shared-
+ * memory atomics, whose order within a tile the hardware picks).  It
+ * agrees with cv_vegas within the FP32 tolerance (the single-integral
+ * kernel groups points differently). */
 typedef struct cv_batch cv_batch;
 int cv_batch_create(cv_ctx *ctx, int count, const cv_spec *specs, cv_batch **out);
 /* Enqueue one complete run of every integral (asynchronous). */
@@ -536,8 +544,9 @@ int cv_batch_vegas(cv_ctx *ctx, int count, const cv_spec *specs, cv_result *out)
  * through the batched kernels (requests that arrive meanwhile join at the
  * next round boundary).  A request whose goal or budget is reached leaves
  * at once and frees its slot and memory.  Each request's result is the
- * same alone and in any mix of requests, up to the order of FP64 additions
- * (see cv_batch_create for the tiling rule and the ndim * nbins limit).
+ * same alone and in any mix of requests, bit for bit (see cv_batch_create
+ * for the tiling rule, the partial rows, the ndim * nbins limit and the
+ * bin counts this holds for).
  * The analogue of the paper's spinning cores (Sect. 3.2.3): the worker and
  * its device state persist between integrations until cv_server_stop. */
 typedef struct {

@@ -1575,6 +1575,12 @@ struct cv_batch {
     // launch plan: per iteration, per class: tile offset and count, counter index
     struct Launch { int j, cls, tile_off, ntiles, counter; };
     std::vector<Launch> plan;
+    // the tiles' partial rows (one iteration's at a time) and, per
+    // iteration and integral, where its rows are
+    double *d_part_S = nullptr;
+    float *d_part_H = nullptr;
+    TileParts *d_tparts = nullptr;
+    size_t part_rows_cap = 0, part_floats_cap = 0, tparts_cap = 0;
     cudaGraphExec_t exec = nullptr;
     int kernels_per_run = 0;
 };
@@ -1586,10 +1592,39 @@ static void batch_free_device(cv_batch *B)
     if (B->mem) cudaFree(B->mem);
     if (B->d_tiles) cudaFree(B->d_tiles);
     if (B->d_counters) cudaFree(B->d_counters);
+    if (B->d_part_S) cudaFree(B->d_part_S);
+    if (B->d_part_H) cudaFree(B->d_part_H);
+    if (B->d_tparts) cudaFree(B->d_tparts);
     B->mem = nullptr;
     B->d_tiles = nullptr;
     B->d_counters = nullptr;
+    B->d_part_S = nullptr;
+    B->d_part_H = nullptr;
+    B->d_tparts = nullptr;
+    B->part_rows_cap = B->part_floats_cap = B->tparts_cap = 0;
 }
+
+// A device buffer of at least `need` elements of T, grown (never shrunk)
+// when it is smaller; *cap counts elements.
+template <typename T>
+static int grow_device(cv_ctx *ctx, T **p, size_t *cap, size_t need, const char *what)
+{
+    if (need <= *cap && *p) return CV_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc((void **)p, std::max<size_t>(need, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail_msg(ctx, CV_ENOMEM, "device allocation of %s failed", what);
+    }
+    *cap = need;
+    return CV_OK;
+}
+
+// Histogram row stride of a tile partial: ndim nbins floats rounded up to
+// a multiple of 4 (16-byte aligned rows).
+static unsigned tile_row_floats(int ndim, int nbins) { return ((unsigned)(ndim * nbins) + 3u) & ~3u; }
 
 // Generate every tile of every iteration for the current tile sizes.
 static int batch_build_tiles(cv_batch *B, int only_first_iteration)
@@ -1599,11 +1634,21 @@ static int batch_build_tiles(cv_batch *B, int only_first_iteration)
     B->plan.clear();
     const int J = only_first_iteration ? 1 : B->J;
     int counter = 0;
+    // partial rows: numbered from 0 in every iteration (an iteration's
+    // launches finish before the next iteration's start)
+    std::vector<TileParts> tparts((size_t)J * B->count, TileParts{0, 0, 0u, 0});
+    size_t rows_max = 0, floats_max = 0;
     for (int j = 0; j < J; ++j) {
+        const size_t it0 = tiles.size();
+        size_t hf = 0;
         for (size_t c = 0; c < B->classes.size(); ++c) {
             const int off = (int)tiles.size();
             for (int i = 0; i < B->count; ++i) {
                 if (B->item_class[i] != (int)c || j >= B->jmax[i]) continue;
+                TileParts &tp = tparts[(size_t)j * B->count + i];
+                tp.row0 = (int)(tiles.size() - it0);
+                tp.hoff0 = (unsigned)hf;
+                tp.stride = (int)tile_row_floats(B->specs[i].g.ndim, B->specs[i].nbins);
                 const cv_spec &sp = B->specs[i];
                 // start index and size of iteration j (the device follows the same plan)
                 unsigned long long s = 1;
@@ -1617,12 +1662,25 @@ static int batch_build_tiles(cv_batch *B, int only_first_iteration)
                     t.item = i;
                     t.nblk = (int)(qb - q < (unsigned long long)TB ? qb - q : (unsigned long long)TB);
                     t.q0 = q;
+                    t.row = (int)(tiles.size() - it0);
+                    t.hoff = (unsigned)hf;
+                    hf += (size_t)tp.stride;
                     tiles.push_back(t);
+                    ++tp.count;
                 }
             }
             const int nt = (int)tiles.size() - off;
             if (nt > 0) B->plan.push_back({j, (int)c, off, nt, counter++});
         }
+        rows_max = std::max(rows_max, tiles.size() - it0);
+        floats_max = std::max(floats_max, hf);
+    }
+    if (floats_max > 0xffffffffull) return fail_msg(ctx, CV_ENOMEM, "tile partials beyond 2^32 floats per iteration");
+    {
+        int rc = grow_device(ctx, &B->d_part_S, &B->part_rows_cap, rows_max * 2 * CV_MAX_COMP, "tile sum partials");
+        if (!rc) rc = grow_device(ctx, &B->d_part_H, &B->part_floats_cap, floats_max, "tile histogram partials");
+        if (!rc) rc = grow_device(ctx, &B->d_tparts, &B->tparts_cap, tparts.size(), "tile partial maps");
+        if (rc) return rc;
     }
     if (tiles.size() > B->tiles_cap) {
         if (B->d_tiles) cudaFree(B->d_tiles);
@@ -1644,6 +1702,8 @@ static int batch_build_tiles(cv_batch *B, int only_first_iteration)
     }
     if (!tiles.empty()) {
         CV_CUDA(ctx, cudaMemcpyAsync(B->d_tiles, tiles.data(), tiles.size() * sizeof(Tile),
+                                     cudaMemcpyHostToDevice, ctx->stream));
+        CV_CUDA(ctx, cudaMemcpyAsync(B->d_tparts, tparts.data(), tparts.size() * sizeof(TileParts),
                                      cudaMemcpyHostToDevice, ctx->stream));
         CV_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     }
@@ -1675,6 +1735,8 @@ static int batch_enqueue(cv_batch *B, cudaStream_t s, int first_iteration_sampli
             a.ntiles = L.ntiles;
             a.stride = C.stride;
             a.counter = B->d_counters + L.counter;
+            a.part_S = B->d_part_S;
+            a.part_H = B->d_part_H;
             const int grid = C.grid < L.ntiles ? C.grid : L.ntiles;
             CV_CUDA(ctx, dispatch_batch_sample(C.ndim, C.pow2, a, grid, ctx->side[used % kSideStreams]));
             ++used;
@@ -1685,8 +1747,9 @@ static int batch_enqueue(cv_batch *B, cudaStream_t s, int first_iteration_sampli
             CV_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join[k], 0));
         }
         if (first_iteration_sampling_only) break;
-        CV_CUDA(ctx, launch_batch_refine(B->d_items, B->d_axes, B->naxes, s));
-        CV_CUDA(ctx, launch_batch_combine(B->d_cargs, B->count, s));
+        const TileParts *tp = B->d_tparts + (size_t)j * B->count;
+        CV_CUDA(ctx, launch_batch_refine(B->d_items, B->d_axes, B->naxes, s, tp, B->d_part_H));
+        CV_CUDA(ctx, launch_batch_combine(B->d_cargs, B->count, s, nullptr, tp, B->d_part_S));
         kernels += 2;
     }
     B->kernels_per_run = kernels;
@@ -1989,6 +2052,8 @@ extern "C" int cv_batch_autotune(cv_batch *B)
                 a.ntiles = L.ntiles;
                 a.stride = C.stride;
                 a.counter = B->d_counters + L.counter;
+                a.part_S = B->d_part_S;
+                a.part_H = B->d_part_H;
                 cudaError_t e = dispatch_batch_sample(C.ndim, C.pow2, a, C.grid < L.ntiles ? C.grid : L.ntiles, ctx->stream);
                 if (e != cudaSuccess) {
                     rc = cuda_fail(ctx, e, "autotune launch");
@@ -2137,6 +2202,13 @@ struct cv_server {
     DevState *d_gather = nullptr;
     DevState *h_gather = nullptr;        // pinned
     std::vector<int> class_grid;         // persistent grid per (ndim, pow2) class, 0 = unknown
+    // the round's tile partial rows, and per slot where its request's are
+    double *d_part_S = nullptr;
+    float *d_part_H = nullptr;
+    size_t part_rows_cap = 0, part_floats_cap = 0;
+    TileParts *d_tparts = nullptr;       // [max_live]
+    std::vector<TileParts> h_tparts;     // [max_live]
+    std::vector<unsigned> slot_stride;   // [max_live]: histogram row floats of the slot's request
 };
 
 namespace {
@@ -2220,6 +2292,7 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
     int64_t round_samples = 0;
     for (const Request &r : live) {
         const int ndim = r.spec.g.ndim;
+        S->slot_stride[r.slot] = tile_row_floats(ndim, r.spec.nbins);
         const bool p2 = make_map(r.spec.nbins, ndim, false).pow2 != 0;  // (powers of two from 32 bins)
         Cls *c = nullptr;
         for (Cls &k : cls)
@@ -2255,7 +2328,28 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
     std::vector<Tile> all;
     all.reserve(ntiles);
     for (const Cls &c : cls) all.insert(all.end(), c.tiles.begin(), c.tiles.end());
+    // the round's partial rows: tile k of the queue at row k, its histogram
+    // after the previous tiles'; a request's tiles are consecutive
+    size_t hf = 0;
+    for (size_t k = 0; k < all.size(); ++k) {
+        Tile &t = all[k];
+        TileParts &tp = S->h_tparts[t.item];
+        const unsigned stride = S->slot_stride[t.item];
+        if (k == 0 || all[k - 1].item != t.item) tp = TileParts{(int)k, 0, (unsigned)hf, (int)stride};
+        t.row = (int)k;
+        t.hoff = (unsigned)hf;
+        hf += stride;
+        ++tp.count;
+    }
+    if (hf > 0xffffffffull) return fail_msg(ctx, CV_ENOMEM, "tile partials beyond 2^32 floats per round");
+    {
+        int rc = grow_device(ctx, &S->d_part_S, &S->part_rows_cap, all.size() * 2 * CV_MAX_COMP, "tile sum partials");
+        if (!rc) rc = grow_device(ctx, &S->d_part_H, &S->part_floats_cap, hf, "tile histogram partials");
+        if (rc) return rc;
+    }
     CV_CUDA(ctx, cudaMemcpyAsync(S->d_tiles, all.data(), all.size() * sizeof(Tile), cudaMemcpyHostToDevice, S->stream));
+    CV_CUDA(ctx, cudaMemcpyAsync(S->d_tparts, S->h_tparts.data(), S->h_tparts.size() * sizeof(TileParts),
+                                 cudaMemcpyHostToDevice, S->stream));
     CV_CUDA(ctx, cudaMemcpyAsync(S->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, S->stream));
     CV_CUDA(ctx, cudaMemcpyAsync(S->d_axes, axes.data(), axes.size() * sizeof(int2), cudaMemcpyHostToDevice, S->stream));
     CV_CUDA(ctx, cudaMemsetAsync(S->d_counters, 0, 2 * (CV_MAX_DIM + 1) * sizeof(int), S->stream));
@@ -2290,6 +2384,8 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         a.ntiles = (int)c.tiles.size();
         a.stride = c.stride;
         a.counter = S->d_counters + (c.pow2 ? 1 : 0) * (CV_MAX_DIM + 1) + c.ndim;
+        a.part_S = S->d_part_S;
+        a.part_H = S->d_part_H;
         CV_CUDA(ctx, dispatch_batch_sample(c.ndim, c.pow2, a, std::min<int>(g, a.ntiles),
                                            S->side[used % kSideStreams]));
         ++used;
@@ -2298,8 +2394,9 @@ int server_round(cv_server *S, std::vector<Request> &live, Arena &arena,
         CV_CUDA(ctx, cudaEventRecord(S->ev_join[k], S->side[k]));
         CV_CUDA(ctx, cudaStreamWaitEvent(S->stream, S->ev_join[k], 0));
     }
-    CV_CUDA(ctx, launch_batch_refine(S->d_items, S->d_axes, (int)axes.size(), S->stream));
-    CV_CUDA(ctx, launch_batch_combine(S->d_cargs, nlive, S->stream, S->d_lists + nfresh));
+    CV_CUDA(ctx, launch_batch_refine(S->d_items, S->d_axes, (int)axes.size(), S->stream, S->d_tparts, S->d_part_H));
+    CV_CUDA(ctx, launch_batch_combine(S->d_cargs, nlive, S->stream, S->d_lists + nfresh, S->d_tparts,
+                                      S->d_part_S));
     CV_CUDA(ctx, launch_gather_states(S->d_items, S->d_lists + nfresh, nlive, S->d_gather, S->stream));
     CV_CUDA(ctx, cudaMemcpyAsync(S->h_gather, S->d_gather, nlive * sizeof(DevState), cudaMemcpyDeviceToHost, S->stream));
     CV_CUDA(ctx, cudaEventRecord(S->ev_t1, S->stream));
@@ -2407,6 +2504,7 @@ extern "C" int cv_server_start(cv_ctx *ctx, const cv_server_opts *opts, cv_serve
     if (e == cudaSuccess) e = cudaMalloc(&S->d_counters, 2 * (CV_MAX_DIM + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&S->d_gather, (size_t)L * sizeof(DevState));
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_gather, (size_t)L * sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMalloc(&S->d_tparts, (size_t)L * sizeof(TileParts));
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(S->arena_mem);
@@ -2416,11 +2514,14 @@ extern "C" int cv_server_start(cv_ctx *ctx, const cv_server_opts *opts, cv_serve
         cudaFree(S->d_axes);
         cudaFree(S->d_counters);
         cudaFree(S->d_gather);
+        cudaFree(S->d_tparts);
         if (S->h_gather) cudaFreeHost(S->h_gather);
         if (S->stream) cudaStreamDestroy(S->stream);
         delete S;
         return fail_msg(ctx, CV_ENOMEM, "server allocation failed: %s", cudaGetErrorString(e));
     }
+    S->h_tparts.assign((size_t)L, TileParts{0, 0, 0u, 0});
+    S->slot_stride.assign((size_t)L, 0u);
     S->t_start = Clock::now();
     S->worker = std::thread(server_main, S);
     ctx->servers.insert(S);
@@ -2532,6 +2633,9 @@ static void server_release(cv_server *S)
     cudaFree(S->d_counters);
     cudaFree(S->d_gather);
     if (S->d_tiles) cudaFree(S->d_tiles);
+    cudaFree(S->d_tparts);
+    if (S->d_part_S) cudaFree(S->d_part_S);
+    if (S->d_part_H) cudaFree(S->d_part_H);
     if (S->h_gather) cudaFreeHost(S->h_gather);
     if (S->stream) cudaStreamDestroy(S->stream);
     for (int k = 0; k < kSideStreams; ++k) {
@@ -2557,21 +2661,25 @@ extern "C" int cv_server_stop(cv_server *S)
 // ------------------------------------------------------------ user integrands
 namespace cv {
 #define CV_EXTERN_M(D)                                                                          \
-    extern template cudaError_t launch_matpass<D, float, 1>(const SampleArgs<float> &, int, cudaStream_t);   \
-    extern template cudaError_t launch_matpass<D, float, 2>(const SampleArgs<float> &, int, cudaStream_t);   \
-    extern template cudaError_t launch_matpass<D, double, 1>(const SampleArgs<double> &, int, cudaStream_t); \
-    extern template cudaError_t launch_matpass<D, double, 2>(const SampleArgs<double> &, int, cudaStream_t);
+    extern template cudaError_t launch_matpass<D, float, 1>(const SampleArgs<float> &, int, cudaStream_t, int *);   \
+    extern template cudaError_t launch_matpass<D, float, 2>(const SampleArgs<float> &, int, cudaStream_t, int *);   \
+    extern template cudaError_t launch_matpass<D, double, 1>(const SampleArgs<double> &, int, cudaStream_t, int *); \
+    extern template cudaError_t launch_matpass<D, double, 2>(const SampleArgs<double> &, int, cudaStream_t, int *);
 CV_FOR_EACH_NDIM(CV_EXTERN_M)
 #undef CV_EXTERN_M
 
-// acc = false: store the points; acc = true: accumulate the caller's values
+// acc = false: store the points; acc = true: accumulate the caller's values.
+// *grid_used: the launch's grid (the accumulate pass keeps to one wave of
+// its own residency)
 template <typename Real>
-static cudaError_t dispatch_matpass(int ndim, bool acc, const SampleArgs<Real> &a, int grid, cudaStream_t s)
+static cudaError_t dispatch_matpass(int ndim, bool acc, const SampleArgs<Real> &a, int grid, cudaStream_t s,
+                                   int *grid_used)
 {
     switch (ndim) {
-#define CV_CASE(D)                                                                       \
-    case D:                                                                              \
-        return acc ? launch_matpass<D, Real, 2>(a, grid, s) : launch_matpass<D, Real, 1>(a, grid, s);
+#define CV_CASE(D)                                                                 \
+    case D:                                                                        \
+        return acc ? launch_matpass<D, Real, 2>(a, grid, s, grid_used)             \
+                   : launch_matpass<D, Real, 1>(a, grid, s, grid_used);
         CV_FOR_EACH_NDIM(CV_CASE)
 #undef CV_CASE
     }
@@ -2726,6 +2834,15 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     // themselves: their accumulate pass sets pass_active from the stop flag)
     const bool lean = fp32 && a.map.pow2 && !aos && a.gen != kGenPseudo && a.map.priv;
     if (lean) a.st = st;
+    // the stop flag through host-mapped memory (no copy per iteration),
+    // where the pinned buffer has a device address
+    int *host_stop = nullptr;
+    if (cudaHostGetDevicePointer((void **)&host_stop, &pin[1], 0) != cudaSuccess) {
+        cudaGetLastError();
+        host_stop = nullptr;
+    }
+    pin[1] = 0;
+    ca.host_stop = host_stop;
     cudaEvent_t ev_stop = nullptr;
     cudaError_t e = cudaEventCreateWithFlags(&ev_stop, cudaEventDisableTiming);
     if (e == cudaSuccess) e = launch_reset(st, edges, H, ndim, N, sp.nstart, ew32, a.map, s);
@@ -2736,15 +2853,36 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
     // next points while the host decides whether to call the integrand
     // again (if the run stopped, those points are never used).
     unsigned long long start = 1;
+    // The accumulate passes' sums and histograms go through per-block
+    // partials, added in a fixed order: an iteration of one tile hands them
+    // to the refinement and combination (as a fused pass does); with more
+    // tiles each pass adds its own (its last block the sums, then the
+    // histogram rows) before the next.
+    PassParts pp;
+    if (e == cudaSuccess) {
+        const int rc_p = ctx_parts(ctx, sample_grid(ctx, occ, tile), &pp);
+        if (rc_p) {
+            cudaEventDestroy(ev_stop);
+            return rc_p;
+        }
+    }
+    const int nh = ndim * N;
+    int grid_used = 0;
     auto store = [&](unsigned long long s0, long long m) {
-        a.start = s0;
-        a.n = m;
+        SampleArgs<Real> b = a;
+        b.start = s0;
+        b.n = m;
         // (the same grid as a fused pass: the kernels share its occupancy)
-        return dispatch_matpass<Real>(ndim, false, a, sample_grid(ctx, occ, m), s);
+        return dispatch_matpass<Real>(ndim, false, b, sample_grid(ctx, occ, m), s, &grid_used);
     };
     if (e == cudaSuccess && jmax > 0) e = store(start, sp.nstart < tile ? sp.nstart : tile);
+    double *pp_S = nullptr;
+    void *pp_H = nullptr;
+    unsigned *pp_ticket = nullptr;
+    if (e == cudaSuccess) parts_args(&pp, 0, &pp_S, &pp_H, &pp_ticket);
     for (int j = 0; j < jmax && e == cudaSuccess && !aborted; ++j) {
         const long long nj = sp.nstart + (long long)j * sp.nincrease;
+        const bool one_tile = nj <= tile;
         for (long long off = 0; off < nj && e == cudaSuccess; off += tile) {
             const long long m = nj - off < tile ? nj - off : tile;
             if (off > 0) e = store(start + (unsigned long long)off, m);
@@ -2755,14 +2893,32 @@ static int vegas_cb_run(cv_ctx *ctx, int ndim, int ncomp, cv_integrand_dev cb, v
                 aborted = 1;
                 break;
             }
-            a.start = start + (unsigned long long)off;
-            a.n = m;
-            e = dispatch_matpass<Real>(ndim, true, a, sample_grid(ctx, occ, m), s);
+            SampleArgs<Real> b = a;
+            b.start = start + (unsigned long long)off;
+            b.n = m;
+            parts_args(&pp, 0, &b.part_S, &b.part_H, &b.part_ticket);
+            b.part_G = pp.G_cap;
+            if (one_tile) b.part_ticket = nullptr;  // (the combination adds the sums)
+            e = dispatch_matpass<Real>(ndim, true, b, sample_grid(ctx, occ, m), s, &grid_used);
+            if (e == cudaSuccess && !one_tile)
+                e = launch_add_parts(b.part_H, grid_used, fp32 ? 1 : 0, nh, H, s);
         }
         if (aborted || e != cudaSuccess) break;
+        if (one_tile) {
+            ca.part_S = reinterpret_cast<const double *>(pp_S);
+            ca.part_H = pp_H;
+            ca.part_G = grid_used;
+            ca.part_nh = nh;
+            ca.part_f32 = fp32 ? 1 : 0;
+        } else {
+            ca.part_S = nullptr;
+            ca.part_H = nullptr;
+            ca.part_G = 0;
+        }
         if (!lean) e = cudaMemcpyAsync(&st->pass_active, &pin[0], sizeof(int), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = launch_refine_combine(ndim, N, H, edges, ca, ew32, a.map, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&pin[1], &st->stopped, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && !host_stop)
+            e = cudaMemcpyAsync(&pin[1], &st->stopped, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev_stop, s);
         start += (unsigned long long)nj;
         if (e == cudaSuccess && j + 1 < jmax) {
@@ -3013,6 +3169,8 @@ int suave_pass_batched(cv_ctx *ctx, const cv_genz *g, int N, long long nnew, con
     a.ntiles = nt;
     a.stride = N;
     a.counter = m.d_counter;
+    a.part_S = nullptr;  // (FP64 atomics: the regions' sums are read from their states)
+    a.part_H = nullptr;
     CV_CUDA(ctx, dispatch_batch_sample(ndim, m.pow2, a, m.grid < nt ? m.grid : nt, s));
     if (refine)
         CV_CUDA(ctx, launch_batch_refine(m.d_items, reinterpret_cast<const int2 *>(m.d_stage + off_a), naxes, s));

@@ -1290,14 +1290,18 @@ k_batch_sample(const BatchSampleArgs B)
             }
         }
         __syncthreads();
+        // the tile's sums and histogram: its partial rows (part_S), else
+        // FP64 atomics into the integral's state
         if (threadIdx.x < 2 * ncomp) {
             double v = 0.0;
             for (int w = 0; w < kWarpsPerBlock; ++w) v += red[w][threadIdx.x];
             const int c = threadIdx.x >> 1;
-            atomicAdd((threadIdx.x & 1) ? &it.st->S2[c] : &it.st->S1[c], v);
+            if (B.part_S) B.part_S[(size_t)tile.row * (2 * CV_MAX_COMP) + threadIdx.x] = v;
+            else atomicAdd((threadIdx.x & 1) ? &it.st->S2[c] : &it.st->S1[c], v);
         }
-        // the tile's histogram: warp copies summed in warp order, then cleared
+        // (warp copies summed in warp order, then cleared)
         const int N = A.nbins;
+        float *ph = B.part_S ? B.part_H + tile.hoff : nullptr;
         for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
             const int d = idx / N, sl = idx - d * N;  // (by slot: conflict-free)
             const int p = d * stride + sl;
@@ -1308,7 +1312,8 @@ k_batch_sample(const BatchSampleArgs B)
                 v += e;
                 e = 0.0f;
             }
-            if (v != 0.0f) atomicAdd(&it.H[d * N + bin_of_slot(sl, A.map)], (double)v);
+            if (ph) ph[d * N + bin_of_slot(sl, A.map)] = v;
+            else if (v != 0.0f) atomicAdd(&it.H[d * N + bin_of_slot(sl, A.map)], (double)v);
         }
         __syncthreads();
     }
@@ -1486,13 +1491,13 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
             }
             // one axis at a time: its row of x, kSub tiles of 32 points; the
             // words after the last tile start the next sub-chunk
+            if (full) {
 #pragma unroll 1
-            for (int d = 0; d < NDIM; ++d) {
-                unsigned X = x0s[d * 32];
-                float *px = A.x + d * ld + j0;
-                const unsigned gd = g_hi + (unsigned)d;  // (table base of axis d >> (3 + L))
-                const unsigned dd = (unsigned)(d * CV_SOBOL_BITS * 4);
-                if (full) {
+                for (int d = 0; d < NDIM; ++d) {
+                    unsigned X = x0s[d * 32];
+                    float *px = A.x + d * ld + j0;
+                    const unsigned gd = g_hi + (unsigned)d;  // (table base of axis d >> (3 + L))
+                    const unsigned dd = (unsigned)(d * CV_SOBOL_BITS * 4);
 #pragma unroll
                     for (int tt = 0; tt < kSub; ++tt) {
                         const float f1 = __uint_as_float((X & P::mF) | P::expE);
@@ -1501,7 +1506,15 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
                         px[32 * tt] = z + 0.5f;
                         X ^= lds_u(da[tt] + dd);
                     }
-                } else {
+                    x0s[d * 32] = X;
+                }
+            } else {
+#pragma unroll 1
+                for (int d = 0; d < NDIM; ++d) {
+                    unsigned X = x0s[d * 32];
+                    float *px = A.x + d * ld + j0;
+                    const unsigned gd = g_hi + (unsigned)d;
+                    const unsigned dd = (unsigned)(d * CV_SOBOL_BITS * 4);
 #pragma unroll
                     for (int tt = 0; tt < kSub; ++tt) {
                         if (tt < nt) {
@@ -1512,133 +1525,158 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
                             X ^= lds_u(da[tt] + dd);
                         }
                     }
+                    x0s[d * 32] = X;
                 }
-                x0s[d * 32] = X;
             }
         }
     }
 }
 
-// One chunk of the accumulate pass: blocks q0 .. q0 + nk - 1 (q0 a multiple of kMatGroup).
-// EDGE = false: every lane's point of every block is in [start, start + n)
-// and nk is a multiple of kMatGroup; EDGE = true: any chunk, points outside
-// add nothing.  The
-// values of block k + kMatAhead are requested while block k is worked on:
-// asynchronous copies into the warp's ring (each lane copies and later
-// reads only its own words; points outside copy zeros).
+// One block of the accumulate pass on its values f (stage of the ring):
+// the Jacobian from the bins' widths (sm.g_hi: the float table of the
+// widths N w_k, its base >> (2 + L)), the warp's histogram, the partial
+// sums.  valid = 0 makes the block's points add nothing.
+template <int NDIM, int L>
+__device__ __forceinline__ void mat_accum_block(const Smem<float> &sm, const unsigned (&X)[NDIM], unsigned stage,
+                                                int ncomp, float valid, Partial<float> &Pt)
+{
+    using P = Pow2Map<L>;
+    float f[CV_MAX_COMP];
+#pragma unroll
+    for (int c = 0; c < CV_MAX_COMP; ++c) f[c] = c < ncomp ? lds_f(stage + (unsigned)(c * 128)) : 0.0f;
+    float J = valid;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) J *= lds_f(funnel_r<P::sA + 1u>(X[d], sm.g_hi + (unsigned)d));
+    const float v0 = J * f[0];
+    const float h = v0 * v0;
+    // the bins of up to eight axes read first, then written (the axes'
+    // rows are disjoint, so the reads need not wait for the writes)
+#pragma unroll
+    for (int d0 = 0; d0 < NDIM; d0 += 8) {
+        float hv[8];
+#pragma unroll
+        for (int d = d0; d < d0 + 8 && d < NDIM; ++d)
+            hv[d - d0] = lds_f(funnel_r<P::sA + 1u>(X[d], sm.h_hi + (unsigned)d));
+#pragma unroll
+        for (int d = d0; d < d0 + 8 && d < NDIM; ++d)
+            sts_f(funnel_r<P::sA + 1u>(X[d], sm.h_hi + (unsigned)d), hv[d - d0] + h);
+    }
+    const float2 v01 = make_float2(v0, J * f[1]);
+    Pt.s1[0] = add2(Pt.s1[0], v01);
+    Pt.s2[0] = fma2(v01, v01, Pt.s2[0]);
+    if (ncomp > 2) {
+        const float2 v23 = make_float2(J * f[2], J * f[3]);
+        Pt.s1[1] = add2(Pt.s1[1], v23);
+        Pt.s2[1] = fma2(v23, v23, Pt.s2[1]);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void mat_fold(Partial<float> &Pt, int ncomp, Acc<float> (&s1)[CV_MAX_COMP],
+                                         Acc<float> (&s2)[CV_MAX_COMP])
+{
+#pragma unroll
+    for (int c = 0; c < CV_MAX_COMP; ++c) {
+        if (c < ncomp) {
+            s1[c].add(Pt.v1(c));
+            s2[c].add(Pt.v2(c));
+        }
+    }
+    Pt.zero();
+}
+
+// One chunk of the accumulate pass: blocks q0 .. q0 + nk - 1 (q0 a multiple
+// of kMatGroup).  EDGE = false: every lane's point of every block is in
+// [start, start + n) and nk is a multiple of kMatGroup; EDGE = true: any
+// chunk, points outside add nothing.  The values of block k + kMatAhead are
+// requested while block k is worked on: asynchronous copies into the warp's
+// ring (each lane copies and later reads only its own words; points outside
+// copy zeros).  Plain FP32 partial sums over runs of kRun blocks are folded
+// into the per-thread Kahan sums after each run (as in the fused pass).
 template <int NDIM, int L, bool EDGE>
 __device__ __forceinline__ void mat_accum_chunk(const SampleArgs<float> &A, const Smem<float> &sm,
                                                 unsigned long long q0, int nk, int lane, unsigned ring,
                                                 int ncomp, Acc<float> (&s1)[CV_MAX_COMP],
                                                 Acc<float> (&s2)[CV_MAX_COMP])
 {
-    // plain FP32 partial sums over runs of kRun blocks, folded into the
-    // per-thread Kahan sums after each run (as the fused pass)
+    using P = Pow2Map<L>;
+    constexpr unsigned kStage = CV_MAX_COMP * 32 * 4;  // bytes of one block's values in the ring
     Partial<float> Pt;
     Pt.zero();
-    auto fold = [&]() {
-#pragma unroll
-        for (int c = 0; c < CV_MAX_COMP; ++c) {
-            if (c < ncomp) {
-                s1[c].add(Pt.v1(c));
-                s2[c].add(Pt.v2(c));
-            }
-        }
-        Pt.zero();
-    };
-    using P = Pow2Map<L>;
     const long long ld = A.ld;
     const long long j0 = (long long)(q0 * 32ull + (unsigned long long)lane) - (long long)A.start;
-    int klo = 0, khi = nk;  // this lane's point of block k is j0 + 32 k, valid for k in [klo, khi)
-    if (EDGE) {
-        klo = j0 >= 0 ? 0 : (int)((31 - j0) / 32);
-        const long long r = A.n - j0;
-        khi = r <= 0 ? 0 : (int)min((long long)nk, (r + 31) / 32);
-    }
-    const float *pf = A.f + j0;  // (dereferenced at valid k only)
-    const float *pfc[CV_MAX_COMP];
-#pragma unroll
-    for (int c = 0; c < CV_MAX_COMP; ++c) pfc[c] = pf + c * ld;
     unsigned X[NDIM];
     sobol_skip<NDIM, unsigned>(X, q0, lane, P::li);
     if (A.gen == kGenScrambled) {
 #pragma unroll
         for (int d = 0; d < NDIM; ++d) X[d] ^= (unsigned)A.shift[d];
     }
-    auto request = [&](int k) {
-        const unsigned stage = ring + (unsigned)((k & (kMatAhead - 1)) * (CV_MAX_COMP * 32 * 4));
-        if (EDGE) {
+    if constexpr (!EDGE) {
+        static_assert(kMatAhead == kMatGroup, "one ring stage per block of a group");
+        // this lane's values of the group's blocks: component c of block
+        // k0 + kk at pv[c] + 32 kk (the pointers advance by a group)
+        const float *pv[CV_MAX_COMP];
+#pragma unroll
+        for (int c = 0; c < CV_MAX_COMP; ++c) pv[c] = A.f + j0 + c * ld;
+#pragma unroll
+        for (int kk = 0; kk < kMatGroup; ++kk) {
+#pragma unroll
+            for (int c = 0; c < CV_MAX_COMP; ++c)
+                if (c < ncomp) cp_async4_full(ring + kk * kStage + (unsigned)(c * 128), pv[c] + 32 * kk);
+            cp_async_commit();
+        }
+        // groups of kMatGroup blocks from multiples of kMatGroup: the step
+        // out of block q0 + 8 m + kk flips Gray-code bits 4 and 5 +
+        // ctz(kk + 1), a word known at compile time (a constant-bank
+        // operand), except the step out of a group's last block (ctz >= 3:
+        // read at run time); block kk of the next group is requested into
+        // the stage block kk has just left
+        for (int k0 = 0; k0 < nk; k0 += kMatGroup) {
+            const bool more = k0 + kMatGroup < nk;
+#pragma unroll
+            for (int c = 0; c < CV_MAX_COMP; ++c) pv[c] += 32 * kMatGroup;
+#pragma unroll
+            for (int kk = 0; kk < kMatGroup; ++kk) {
+                cp_async_wait<kMatAhead - 1>();  // (block k0 + kk's copies have landed)
+                mat_accum_block<NDIM, L>(sm, X, ring + kk * kStage, ncomp, 1.0f, Pt);
+                if (kk + 1 < kMatGroup) {
+#pragma unroll
+                    for (int d = 0; d < NDIM; ++d)
+                        X[d] ^= Dir<unsigned>::w(P::li, d, 5 + ctz_const((unsigned)(kk + 1)));
+                } else if (more) {
+                    sobol_step<NDIM, unsigned>(X, q0 + (unsigned long long)(k0 + kk), P::li);
+                }
+                if (more) {
+#pragma unroll
+                    for (int c = 0; c < CV_MAX_COMP; ++c)
+                        if (c < ncomp) cp_async4_full(ring + kk * kStage + (unsigned)(c * 128), pv[c] + 32 * kk);
+                }
+                cp_async_commit();
+            }
+            if (((k0 + kMatGroup) % (int)kRun) == 0) mat_fold(Pt, ncomp, s1, s2);
+        }
+    } else {
+        // this lane's point of block k is j0 + 32 k, valid for k in [klo, khi)
+        const int klo = j0 >= 0 ? 0 : (int)((31 - j0) / 32);
+        const long long r = A.n - j0;
+        const int khi = r <= 0 ? 0 : (int)min((long long)nk, (r + 31) / 32);
+        const float *pf = A.f + j0;  // (dereferenced at valid k only)
+        auto request = [&](int k) {
+            const unsigned stage = ring + (unsigned)((k & (kMatAhead - 1)) * kStage);
             const bool v = k >= klo && k < khi;
             const float *src = v ? pf + 32 * k : A.f;
 #pragma unroll
             for (int c = 0; c < CV_MAX_COMP; ++c)
                 if (c < ncomp) cp_async4(stage + (unsigned)(c * 128), src + c * ld, v ? 4u : 0u);
-        } else if (k < nk) {
+            cp_async_commit();
+        };
+        auto block = [&](int k) {
+            cp_async_wait<kMatAhead - 1>();
+            mat_accum_block<NDIM, L>(sm, X, ring + (unsigned)((k & (kMatAhead - 1)) * kStage), ncomp,
+                                     (k >= klo && k < khi) ? 1.0f : 0.0f, Pt);
+        };
 #pragma unroll
-            for (int c = 0; c < CV_MAX_COMP; ++c)
-                if (c < ncomp) cp_async4_full(stage + (unsigned)(c * 128), pfc[c] + 32 * k);
-        }
-        cp_async_commit();
-    };
-    auto block = [&](int k) {
-        cp_async_wait<kMatAhead - 1>();  // (block k's copies have landed)
-        const unsigned stage = ring + (unsigned)((k & (kMatAhead - 1)) * (CV_MAX_COMP * 32 * 4));
-        float f[CV_MAX_COMP];
-#pragma unroll
-        for (int c = 0; c < CV_MAX_COMP; ++c) f[c] = c < ncomp ? lds_f(stage + (unsigned)(c * 128)) : 0.0f;
-        float J = (!EDGE || (k >= klo && k < khi)) ? 1.0f : 0.0f;
-#pragma unroll
-        for (int d = 0; d < NDIM; ++d) J *= lds_f(funnel_r<P::sA>(X[d], sm.g_hi + (unsigned)d) + 4u);
-        const float v0 = J * f[0];
-        const float h = v0 * v0;
-        // the bins of up to eight axes read first, then written (the axes'
-        // rows are disjoint, so the reads need not wait for the writes)
-#pragma unroll
-        for (int d0 = 0; d0 < NDIM; d0 += 8) {
-            float hv[8];
-#pragma unroll
-            for (int d = d0; d < d0 + 8 && d < NDIM; ++d)
-                hv[d - d0] = lds_f(funnel_r<P::sA + 1u>(X[d], sm.h_hi + (unsigned)d));
-#pragma unroll
-            for (int d = d0; d < d0 + 8 && d < NDIM; ++d)
-                sts_f(funnel_r<P::sA + 1u>(X[d], sm.h_hi + (unsigned)d), hv[d - d0] + h);
-        }
-        const float2 v01 = make_float2(v0, J * f[1]);
-        Pt.s1[0] = add2(Pt.s1[0], v01);
-        Pt.s2[0] = fma2(v01, v01, Pt.s2[0]);
-        if (ncomp > 2) {
-            const float2 v23 = make_float2(J * f[2], J * f[3]);
-            Pt.s1[1] = add2(Pt.s1[1], v23);
-            Pt.s2[1] = fma2(v23, v23, Pt.s2[1]);
-        }
-        __syncwarp();
-    };
-#pragma unroll
-    for (int k = 0; k < kMatAhead; ++k) request(k);
-    if constexpr (!EDGE) {
-        // groups of kMatGroup blocks from multiples of kMatGroup: the step
-        // out of block q0 + 8 m + kk flips Gray-code bits 4 and 5 +
-        // ctz(kk + 1), a word known at compile time (a constant-bank
-        // operand), except the step out of a group's last block (ctz >= 3:
-        // read at run time); the words after the chunk's last block are
-        // not needed
-        for (int k0 = 0; k0 < nk; k0 += kMatGroup) {
-#pragma unroll
-            for (int kk = 0; kk < kMatGroup; ++kk) {
-                const int k = k0 + kk;
-                block(k);
-                if (kk + 1 < kMatGroup) {
-#pragma unroll
-                    for (int d = 0; d < NDIM; ++d)
-                        X[d] ^= Dir<unsigned>::w(P::li, d, 5 + ctz_const((unsigned)(kk + 1)));
-                } else if (k + 1 < nk) {
-                    sobol_step<NDIM, unsigned>(X, q0 + (unsigned long long)k, P::li);
-                }
-                request(k + kMatAhead);
-            }
-            if (((k0 + kMatGroup) % (int)kRun) == 0) fold();
-        }
-    } else {
+        for (int k = 0; k < kMatAhead; ++k) request(k);
         for (int k = 0; k < nk; k += 2) {
             block(k);
             sobol_step_even<NDIM, unsigned>(X, P::li);
@@ -1647,10 +1685,10 @@ __device__ __forceinline__ void mat_accum_chunk(const SampleArgs<float> &A, cons
             block(k + 1);
             sobol_step<NDIM, unsigned>(X, q0 + (unsigned long long)(k + 1), P::li);
             request(k + 1 + kMatAhead);
-            if (((k + 2) % (int)kRun) == 0) fold();
+            if (((k + 2) % (int)kRun) == 0) mat_fold(Pt, ncomp, s1, s2);
         }
     }
-    fold();
+    mat_fold(Pt, ncomp, s1, s2);
     cp_async_wait<0>();  // (the ring is reused by the next chunk)
 }
 
@@ -1667,13 +1705,31 @@ k_mat_accum(const __grid_constant__ SampleArgs<float> A)
     using P = Pow2Map<L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ncomp = A.g.ncomp;
-    Smem<float> sm;
-    mat_table<NDIM>(A, sm, smem_raw, P::N);
-    float *hist = reinterpret_cast<float *>(sm.ew + NDIM * P::N);
+    // The pass needs only the bins' widths: a float table of N w_k per axis
+    // (the lanes of a block read 32 distinct slots, so a read is one
+    // wavefront, against two for the {e, w} pairs), then the warps' copies.
+    float *wt = reinterpret_cast<float *>(align_table(smem_raw, P::N));
+    float *hist = wt + NDIM * P::N;
+    if (A.ew32) {
+        for (int i = threadIdx.x; i < NDIM * P::N; i += blockDim.x) wt[i] = A.ew32[i].y;
+    } else {
+        // (converted from the FP64 edges in the histograms' space first)
+        float2 *tmp = reinterpret_cast<float2 *>(hist);
+        stage_grid_f32(tmp, NDIM, P::N, P::N, A.edges, A.map);
+        __syncthreads();
+        for (int i = threadIdx.x; i < NDIM * P::N; i += blockDim.x) wt[i] = tmp[i].y;
+        __syncthreads();
+    }
     for (int i = threadIdx.x; i < kWarpsPerBlock * NDIM * P::N; i += blockDim.x) hist[i] = 0.0f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Smem<float> sm;
+    sm.ew = reinterpret_cast<float2 *>(wt);
+    sm.stride = P::N;
     sm.h = hist + warp * NDIM * P::N;
     set_addresses(sm, L);
+    // (the width table's base >> (2 + L), as the histogram's: a multiple of 4N bytes)
+    sm.g_sa = (unsigned)__cvta_generic_to_shared(wt);
+    sm.g_hi = sm.g_sa >> (2 + L);
     // this lane's words in its warp's ring of value stages, after the
     // histogram copies: stage k at + k CV_MAX_COMP 128, value c at + c 128
     const unsigned ring = (unsigned)__cvta_generic_to_shared(hist + kWarpsPerBlock * NDIM * P::N) +
@@ -1721,13 +1777,18 @@ k_mat_accum(const __grid_constant__ SampleArgs<float> A)
         }
     }
     __syncthreads();
+    // the block's sums and histogram as its partial rows (with part_S), else
+    // added with FP64 atomics
+    const bool parts = A.part_S != nullptr;
     if (threadIdx.x < 2 * ncomp) {
         double t = 0.0;
         for (int w = 0; w < kWarpsPerBlock; ++w) t += red[w][threadIdx.x];
         const int c = threadIdx.x >> 1;
-        atomicAdd((threadIdx.x & 1) ? &A.S2[c] : &A.S1[c], t);
+        if (parts) A.part_S[blockIdx.x * (2 * CV_MAX_COMP) + threadIdx.x] = t;
+        else atomicAdd((threadIdx.x & 1) ? &A.S2[c] : &A.S1[c], t);
     }
     // the warps' copies, summed in warp order
+    float *ph = parts ? reinterpret_cast<float *>(A.part_H) + (size_t)blockIdx.x * NDIM * N : nullptr;
     for (int idx = threadIdx.x; idx < NDIM * N; idx += blockDim.x) {
         const int d = idx / N;
         const int k = idx - d * N;
@@ -1735,8 +1796,10 @@ k_mat_accum(const __grid_constant__ SampleArgs<float> A)
         float v = 0.0f;
 #pragma unroll
         for (int w = 0; w < kWarpsPerBlock; ++w) v += hist[(w * NDIM + d) * N + p];
-        if (v != 0.0f) atomicAdd(&A.H[d * N + k], (double)v);
+        if (parts) ph[d * N + k] = v;
+        else if (v != 0.0f) atomicAdd(&A.H[d * N + k], (double)v);
     }
+    if (parts && A.part_ticket) last_block_sums(A.part_S, A.part_ticket, A.S1, A.S2, ncomp);
 }
 
 // Built-in integrand on materialised points (the library's own callback):
@@ -1928,7 +1991,7 @@ cudaError_t batch_occupancy(bool pow2, int stride, int *blocks_per_sm)
 }
 
 template <int NDIM, int L, int MODE>
-static cudaError_t launch_mat_lean(const SampleArgs<float> &a, int grid, cudaStream_t s)
+static cudaError_t launch_mat_lean(const SampleArgs<float> &a, int grid, cudaStream_t s, int *grid_used)
 {
     using P = Pow2Map<L>;
     // (the compile-time map must be the one the host chose)
@@ -1938,10 +2001,13 @@ static cudaError_t launch_mat_lean(const SampleArgs<float> &a, int grid, cudaStr
         const size_t smem = (size_t)NDIM * P::N * 8 + 8 * (size_t)P::N;
         cudaError_t e = cudaFuncSetAttribute(k_mat_store<NDIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        *grid_used = grid;
         k_mat_store<NDIM, L><<<grid, kBlock, smem, s>>>(a);
         return cudaGetLastError();
     }
-    const size_t smem = sample_smem_bytes(NDIM, P::N, false, true) +
+    // (the width table, the warps' histogram copies, 8N bytes to align the
+    // table, the warps' value rings)
+    const size_t smem = (size_t)(1 + kWarpsPerBlock) * NDIM * P::N * 4 + 8 * (size_t)P::N +
                         (size_t)kWarpsPerBlock * kMatAhead * CV_MAX_COMP * 32 * 4;
     cudaError_t e = cudaFuncSetAttribute(k_mat_accum<NDIM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1957,22 +2023,24 @@ static cudaError_t launch_mat_lean(const SampleArgs<float> &a, int grid, cudaStr
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     if (grid > sms * occ) grid = sms * occ;
+    if (a.part_S && grid > a.part_G) return cudaErrorInvalidValue;  // (partial rows for every block)
+    *grid_used = grid;
     k_mat_accum<NDIM, L><<<grid, kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int NDIM, typename Real, bool POW2, int MODE>
-static cudaError_t launch_matpass_v(const SampleArgs<Real> &a, int grid, cudaStream_t s)
+static cudaError_t launch_matpass_v(const SampleArgs<Real> &a, int grid, cudaStream_t s, int *grid_used)
 {
     if constexpr (sizeof(Real) == 4 && POW2) {
         // the common case's own kernels (dimension-major, Sobol points; the
         // accumulate pass needs the warps' histogram copies to fit)
         if (!a.aos && a.gen != kGenPseudo && (MODE == 1 || a.map.priv)) {
             switch (a.map.L) {
-            case 5: return launch_mat_lean<NDIM, 5, MODE>(a, grid, s);
-            case 6: return launch_mat_lean<NDIM, 6, MODE>(a, grid, s);
-            case 7: return launch_mat_lean<NDIM, 7, MODE>(a, grid, s);
-            case 8: return launch_mat_lean<NDIM, 8, MODE>(a, grid, s);
+            case 5: return launch_mat_lean<NDIM, 5, MODE>(a, grid, s, grid_used);
+            case 6: return launch_mat_lean<NDIM, 6, MODE>(a, grid, s, grid_used);
+            case 7: return launch_mat_lean<NDIM, 7, MODE>(a, grid, s, grid_used);
+            case 8: return launch_mat_lean<NDIM, 8, MODE>(a, grid, s, grid_used);
             default: break;
             }
         }
@@ -1981,17 +2049,19 @@ static cudaError_t launch_matpass_v(const SampleArgs<Real> &a, int grid, cudaStr
     cudaError_t e = cudaFuncSetAttribute(k_matpass<NDIM, Real, POW2, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (a.part_S && grid > a.part_G) return cudaErrorInvalidValue;
+    *grid_used = grid;
     k_matpass<NDIM, Real, POW2, MODE><<<grid, kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int NDIM, typename Real, int MODE>
-cudaError_t launch_matpass(const SampleArgs<Real> &a, int grid, cudaStream_t s)
+cudaError_t launch_matpass(const SampleArgs<Real> &a, int grid, cudaStream_t s, int *grid_used)
 {
     if constexpr (sizeof(Real) == 4) {
-        if (a.map.pow2) return launch_matpass_v<NDIM, float, true, MODE>(a, grid, s);
+        if (a.map.pow2) return launch_matpass_v<NDIM, float, true, MODE>(a, grid, s, grid_used);
     }
-    return launch_matpass_v<NDIM, Real, false, MODE>(a, grid, s);
+    return launch_matpass_v<NDIM, Real, false, MODE>(a, grid, s, grid_used);
 }
 
 template <int NDIM, typename Real, bool AOS>
@@ -2027,10 +2097,10 @@ cudaError_t launch_sobol(unsigned long long start, long long n, int bits, const 
     template cudaError_t cv::launch_batch_sample<D, false>(const cv::BatchSampleArgs &, int, \
                                                            cudaStream_t);                   \
     template cudaError_t cv::batch_occupancy<D>(bool, int, int *);                          \
-    template cudaError_t cv::launch_matpass<D, float, 1>(const cv::SampleArgs<float> &, int, cudaStream_t);      \
-    template cudaError_t cv::launch_matpass<D, float, 2>(const cv::SampleArgs<float> &, int, cudaStream_t);      \
-    template cudaError_t cv::launch_matpass<D, double, 1>(const cv::SampleArgs<double> &, int, cudaStream_t);    \
-    template cudaError_t cv::launch_matpass<D, double, 2>(const cv::SampleArgs<double> &, int, cudaStream_t);    \
+    template cudaError_t cv::launch_matpass<D, float, 1>(const cv::SampleArgs<float> &, int, cudaStream_t, int *); \
+    template cudaError_t cv::launch_matpass<D, float, 2>(const cv::SampleArgs<float> &, int, cudaStream_t, int *); \
+    template cudaError_t cv::launch_matpass<D, double, 1>(const cv::SampleArgs<double> &, int, cudaStream_t, int *); \
+    template cudaError_t cv::launch_matpass<D, double, 2>(const cv::SampleArgs<double> &, int, cudaStream_t, int *); \
     template cudaError_t cv::launch_genz_points<D, float, false>(const cv::GenzParams<float> &, const float *, float *, long long, long long, int, cudaStream_t); \
     template cudaError_t cv::launch_genz_points<D, float, true>(const cv::GenzParams<float> &, const float *, float *, long long, long long, int, cudaStream_t); \
     template cudaError_t cv::launch_genz_points<D, double, false>(const cv::GenzParams<double> &, const double *, double *, long long, long long, int, cudaStream_t); \

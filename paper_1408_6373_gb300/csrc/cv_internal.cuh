@@ -246,6 +246,10 @@ struct CombineArgs {
     // ticket), summed by the combination in block order; null: the pass
     // added them to S1, S2 itself
     const double *part_S;
+    // a host-mapped word that receives the run's stop flag after every
+    // combination (the host reads it once the launch has completed); null:
+    // none
+    int *host_stop;
 };
 
 // ---- batched persistent launch (many integrals) ----
@@ -258,11 +262,24 @@ struct BatchItem {
 };
 
 // A tile: nblk consecutive 32-point Sobol blocks of one integral's
-// iteration, starting at absolute block q0.
+// iteration, starting at absolute block q0.  row, hoff: where the tile
+// leaves its sums and histogram when the launch reduces through partials.
 struct Tile {
     int item;
     int nblk;
     unsigned long long q0;
+    int row;                        // row of BatchSampleArgs::part_S
+    unsigned hoff;                  // first float of its [ndim][nbins] rows in part_H
+};
+
+// The partial rows of one integral's tiles in one iteration: count
+// consecutive sum rows from row0, and histogram rows of `stride` floats
+// (ndim nbins rounded up to a multiple of 4) from float hoff0.
+struct TileParts {
+    int row0;
+    int count;
+    unsigned hoff0;
+    int stride;
 };
 
 struct BatchSampleArgs {
@@ -271,6 +288,13 @@ struct BatchSampleArgs {
     int ntiles;
     int stride;                     // slots per axis: the class's largest nbins
     int *counter;                   // next tile to take (zero before the launch)
+    // Deterministic reduction (part_S non-null): tile t writes its sums to
+    // part_S[t.row][2 c + {0, 1}] and its histogram, by bin, to part_H +
+    // t.hoff, no atomics; the batched refinement and combination add an
+    // integral's rows in tile order.  Null: FP64 atomics into the
+    // integral's state and histogram.
+    double *part_S;
+    float *part_H;
 };
 
 // Shared memory of a batched sampling block: grid e, w and one f^2
@@ -298,7 +322,7 @@ cudaError_t launch_sobol(unsigned long long start, long long n, int bits, const 
 // materialised samples: store the points (mode 1) or accumulate the
 // caller's values (mode 2) over [a.start, a.start + a.n)
 template <int NDIM, typename Real, int MODE>
-cudaError_t launch_matpass(const SampleArgs<Real> &a, int grid, cudaStream_t s);
+cudaError_t launch_matpass(const SampleArgs<Real> &a, int grid, cudaStream_t s, int *grid_used);
 
 template <int NDIM, typename Real, bool AOS>
 cudaError_t launch_genz_points(const GenzParams<Real> &g, const Real *x, Real *f, long long n,
@@ -320,10 +344,15 @@ cudaError_t launch_stage_grid(int ndim, int nbins, const double *edges, float2 *
 // (list: optional indices of the integrals to act on, else 0..count-1)
 cudaError_t launch_batch_reset(const BatchItem *items, const CombineArgs *cargs, int count,
                                cudaStream_t s, const int *list = nullptr);
+// (parts, part_S, part_H: the tiles' partial rows of this iteration, parts
+// indexed by integral; null parts: the sums and histograms are in the
+// integrals' states)
 cudaError_t launch_batch_refine(const BatchItem *items, const int2 *axes, int naxes,
-                                cudaStream_t s);
+                                cudaStream_t s, const TileParts *parts = nullptr,
+                                const float *part_H = nullptr);
 cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream_t s,
-                                 const int *list = nullptr);
+                                 const int *list = nullptr, const TileParts *parts = nullptr,
+                                 const double *part_S = nullptr);
 cudaError_t launch_gather_states(const BatchItem *items, const int *list, int count,
                                  DevState *out, cudaStream_t s);
 

@@ -496,6 +496,7 @@ __device__ void combine_iteration(const CombineArgs &A)
     // read by the next sampling launch only, so no block of this launch
     // sees the change
     if (c == 0 && s_stop) st->stopped = 1;
+    if (c == 0 && A.host_stop) *(volatile int *)A.host_stop = s_stop;
 }
 
 // One Vegas iteration after its sampling pass: blocks 0..ndim-1 refine one
@@ -559,19 +560,41 @@ __global__ void k_batch_reset(const BatchItem *items, const CombineArgs *cargs, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_batch_refine(const BatchItem *items, const int2 *axes)
+__global__ void __launch_bounds__(256) k_batch_refine(const BatchItem *items, const int2 *axes,
+                                                      const TileParts *parts, const float *part_H)
 {
     const int2 ax = axes[blockIdx.x];
     const BatchItem &it = items[ax.x];
     if (*(volatile const int *)&it.st->stopped) return;
-    refine_axis(ax.y, it.a.nbins, it.H, it.edges, 1);
+    if (parts) {
+        // the histogram of the integral's tiles, rows added in tile order
+        const TileParts tp = parts[ax.x];
+        CombineArgs pa;
+        pa.part_H = part_H + tp.hoff0;
+        pa.part_G = tp.count;
+        pa.part_nh = tp.stride;
+        pa.part_f32 = 1;
+        refine_axis(ax.y, it.a.nbins, it.H, it.edges, 1, nullptr, nullptr, &pa);
+    } else {
+        refine_axis(ax.y, it.a.nbins, it.H, it.edges, 1);
+    }
 }
 
-__global__ void k_batch_combine(const CombineArgs *cargs, const int *list)
+__global__ void k_batch_combine(const CombineArgs *cargs, const int *list, const TileParts *parts,
+                                const double *part_S)
 {
-    const CombineArgs &A = cargs[list ? list[blockIdx.x] : (int)blockIdx.x];
+    const int i = list ? list[blockIdx.x] : (int)blockIdx.x;
+    const CombineArgs &A = cargs[i];
     if (*(volatile const int *)&A.st->stopped) return;
-    combine_iteration(A);
+    if (parts) {
+        // the sums of the integral's tiles, rows added in tile order
+        CombineArgs B = A;
+        B.part_S = part_S + (size_t)parts[i].row0 * (2 * CV_MAX_COMP);
+        B.part_G = parts[i].count;
+        combine_iteration(B);
+    } else {
+        combine_iteration(A);
+    }
 }
 
 cudaError_t launch_batch_reset(const BatchItem *items, const CombineArgs *cargs, int count,
@@ -598,17 +621,19 @@ cudaError_t launch_gather_states(const BatchItem *items, const int *list, int co
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_refine(const BatchItem *items, const int2 *axes, int naxes, cudaStream_t s)
+cudaError_t launch_batch_refine(const BatchItem *items, const int2 *axes, int naxes, cudaStream_t s,
+                                const TileParts *parts, const float *part_H)
 {
     if (naxes <= 0) return cudaSuccess;
-    k_batch_refine<<<naxes, 256, 0, s>>>(items, axes);
+    k_batch_refine<<<naxes, 256, 0, s>>>(items, axes, parts, part_H);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream_t s, const int *list)
+cudaError_t launch_batch_combine(const CombineArgs *cargs, int count, cudaStream_t s, const int *list,
+                                 const TileParts *parts, const double *part_S)
 {
     if (count <= 0) return cudaSuccess;
-    k_batch_combine<<<count, 32, 0, s>>>(cargs, list);
+    k_batch_combine<<<count, 32, 0, s>>>(cargs, list, parts, part_S);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,28 @@ def test_tiles_do_not_change_results(ctx):
     np.testing.assert_allclose(one.integral, many.integral, rtol=1e-13)
 
 
+# The accumulate passes reduce through per-block partials in a fixed order
+# (no floating-point atomics): the same run twice gives the same bits, with
+# one tile per iteration (partials summed by the combination) and with many
+# (each pass adds its own), in the FP32 power-of-two kernels and in FP64
+# and the point-major layout's general pass (warp-private histograms for
+# N = 2^L >= 32; other bin counts update one block copy with shared-memory
+# atomics).
+@pytest.mark.parametrize("flags,nbins", [(0, 128), (cg.JIT, 64), (cg.FP64, 32), (cg.FP64 | cg.AOS, 64)],
+                         ids=["f32-128", "f32-jit-64", "f64-32", "f64-aos-64"])
+@pytest.mark.parametrize("nvec", [1 << 17, 7777], ids=["one-tile", "tiles"])
+def test_materialised_runs_agree_bit_for_bit(ctx, flags, nbins, nvec):
+    g, _, _ = _genz(ndim=6, seed=9)
+    kw = dict(flags=flags & ~cg.JIT, maxeval=5 * 30000, nstart=30000, nincrease=10000, nbins=nbins)
+    ud = cg.GenzCallbackData(g, flags)
+    r = [ctx.vegas_cb(cg.builtin_integrand(), 6, 2, userdata=ud, nvec=nvec, **kw) for _ in range(3)]
+    for x in r[1:]:
+        assert (x.neval, x.fail) == (r[0].neval, r[0].fail)
+        for key in ("integral", "error", "prob"):
+            assert np.array_equal(np.asarray(getattr(x, key)).view(np.uint64),
+                                  np.asarray(getattr(r[0], key)).view(np.uint64)), (key, flags, nbins, nvec)
+
+
 def test_torch_integrand_and_nvec_contract(ctx):
     # a user integrand written with torch on the device buffers
     ndim = 4
