@@ -591,6 +591,14 @@ __device__ __forceinline__ float lds_f(unsigned a)
     asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
     return v;
 }
+// A read of a table that does not change while it is read (staged before
+// a barrier): free to move and combine like any load.
+__device__ __forceinline__ float lds_f_ro(unsigned a)
+{
+    float v;
+    asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
 __device__ __forceinline__ void sts_f(unsigned a, float v)
 {
     asm volatile("st.shared.f32 [%0], %1;" :: "r"(a), "f"(v) : "memory");
@@ -1144,23 +1152,32 @@ k_sample_pseudo(const __grid_constant__ SampleArgs<Real> A)
 }
 
 // ------------------------------------------------------------ batched kernel
+// A batched tile's single-component integral: its parameters held in
+// registers for the tile's loop (read once from the staged description).
+template <int NDIM>
+struct TileRegs {
+    float p0[NDIM], p1[NDIM];
+    float q0, q1;
+    int delay;
+};
+
 // The policy of one single-component integral of family F (a batched
 // tile's integral): family, component count and the loop over components
-// are compile-time; the parameters are read from the staged description.
+// are compile-time; the parameters come from a TileRegs.
 template <int F>
 struct TileIntegrand {
     static constexpr int kMode = 0;
     static constexpr int kGen = 0;
-    template <int C> __device__ __forceinline__ static constexpr int family(const GenzParams<float> &)
+    template <int C, class G> __device__ __forceinline__ static constexpr int family(const G &)
     {
         return C == 0 ? F : CV_CONST;
     }
-    __device__ __forceinline__ static constexpr int ncomp(const GenzParams<float> &) { return 1; }
-    template <int C> __device__ __forceinline__ static float p0(const GenzParams<float> &g, int d) { return g.p0[0][d]; }
-    template <int C> __device__ __forceinline__ static float p1(const GenzParams<float> &g, int d) { return g.p1[0][d]; }
-    template <int C> __device__ __forceinline__ static float q0(const GenzParams<float> &g) { return g.q0[0]; }
-    template <int C> __device__ __forceinline__ static float q1(const GenzParams<float> &g) { return g.q1[0]; }
-    __device__ __forceinline__ static int delay(const GenzParams<float> &g) { return g.delay; }
+    template <class G> __device__ __forceinline__ static constexpr int ncomp(const G &) { return 1; }
+    template <int C, class G> __device__ __forceinline__ static float p0(const G &g, int d) { return g.p0[d]; }
+    template <int C, class G> __device__ __forceinline__ static float p1(const G &g, int d) { return g.p1[d]; }
+    template <int C, class G> __device__ __forceinline__ static float q0(const G &g) { return g.q0; }
+    template <int C, class G> __device__ __forceinline__ static float q1(const G &g) { return g.q1; }
+    template <class G> __device__ __forceinline__ static int delay(const G &g) { return g.delay; }
     __device__ __forceinline__ static int table(const MapParams &m) { return m.li; }
     __device__ __forceinline__ static bool priv(const MapParams &m) { return m.priv != 0; }
     __device__ __forceinline__ static int nbins(int n) { return n; }
@@ -1184,11 +1201,20 @@ __device__ __forceinline__ void batch_steps(const SampleArgs<float> &A, const Sm
     if constexpr (NDIM <= kTileSpecMaxDim) {
         const int fam = A.g.family[0];
         if (A.g.ncomp == 1 && fam >= 0 && fam < CV_CONST) {
+            TileRegs<NDIM> tr;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                tr.p0[d] = A.g.p0[0][d];
+                tr.p1[d] = A.g.p1[0][d];
+            }
+            tr.q0 = A.g.q0[0];
+            tr.q1 = A.g.q1[0];
+            tr.delay = A.g.delay;
             switch (fam) {
 #define CV_TILE_FAMILY(F)                                                                                   \
     case F:                                                                                                 \
         run_steps<NDIM, float, POW2, EDGE, TileIntegrand<F>>(A, sm, X, w0, nsteps, start, end, lane, hmode, \
-                                                             s1, s2, A.g);                                 \
+                                                             s1, s2, tr);                                  \
         return;
                 CV_TILE_FAMILY(CV_OSCILLATORY)
                 CV_TILE_FAMILY(CV_PRODUCT_PEAK)
@@ -1544,9 +1570,17 @@ __device__ __forceinline__ void mat_accum_block(const Smem<float> &sm, const uns
     float f[CV_MAX_COMP];
 #pragma unroll
     for (int c = 0; c < CV_MAX_COMP; ++c) f[c] = c < ncomp ? lds_f(stage + (unsigned)(c * 128)) : 0.0f;
-    float J = valid;
+    // J = valid prod_d N w_d as a pairwise product (a dependent chain of
+    // log2 NDIM multiplies instead of NDIM)
+    float w[NDIM];
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) J *= lds_f(funnel_r<P::sA + 1u>(X[d], sm.g_hi + (unsigned)d));
+    for (int d = 0; d < NDIM; ++d) w[d] = lds_f_ro(funnel_r<P::sA + 1u>(X[d], sm.g_hi + (unsigned)d));
+#pragma unroll
+    for (int h = 1; h < NDIM; h <<= 1) {
+#pragma unroll
+        for (int d = 0; d + h < NDIM; d += 2 * h) w[d] *= w[d + h];
+    }
+    const float J = valid * w[0];
     const float v0 = J * f[0];
     const float h = v0 * v0;
     // the bins of up to eight axes read first, then written (the axes'
