@@ -1440,11 +1440,12 @@ struct Pow2Map {
 // j = index - start.  A warp writes 32 consecutive j of a tile aligned in
 // j (one full 128-byte line per coordinate when x and ld are aligned), so
 // its lanes' indices straddle two aligned Sobol blocks whenever start is
-// not a multiple of 32: every lane carries its own block counter and steps
-// its words by the Gray-code rule for its own block, g(32(q+1)+k) ^
-// g(32q+k) = 2^4 ^ 2^(5 + ctz(q+1)).  The direction words of the table sit
-// in shared memory, where the two blocks' lookups of a step are one
-// broadcast each.  Tiles go to warps in rounds of kRun so that all warps
+// not a multiple of 32: every lane steps its words by the Gray-code rule
+// for its own block, g(32(q+1)+k) ^ g(32q+k) = 2^4 ^ 2^(5 + ctz(q+1)).  Of
+// the two blocks a step leaves, one is even (step word W_5 of the axis, held
+// in a register) and one odd (its word index the same for the whole warp:
+// one constant-bank load), so no lane reads a table in shared memory.
+// Tiles go to warps in rounds of kRun so that all warps
 // write within one window of x at a time.  N = 2^L at compile time: table
 // offsets and map constants are immediates.
 template <int NDIM, int L>
@@ -1453,14 +1454,11 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
 {
     using P = Pow2Map<L>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ unsigned sdir[NDIM][CV_SOBOL_BITS];
     __shared__ unsigned sx0[kWarpsPerBlock][NDIM][32];
     Smem<float> sm;
     mat_table<NDIM>(A, sm, smem_raw, P::N);
     sm.h = nullptr;
     set_addresses(sm, L);
-    for (int idx = threadIdx.x; idx < NDIM * CV_SOBOL_BITS; idx += blockDim.x)
-        sdir[idx / CV_SOBOL_BITS][idx % CV_SOBOL_BITS] = Dir<unsigned>::w(P::li, idx / CV_SOBOL_BITS, idx % CV_SOBOL_BITS);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -1475,8 +1473,9 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
     const long long nchunk = (ntile + per - 1) / per;
     const long long ld = A.ld;
     const unsigned g_hi = sm.g_hi;
-    const unsigned sdir_sa = (unsigned)__cvta_generic_to_shared(&sdir[0][0]);
     unsigned *x0s = &sx0[threadIdx.x >> 5][0][lane];  // this lane's running words, stride 32
+    // this lane's index lies one block past lane 0's (start is not a multiple of 32)
+    const bool inB = (unsigned)(A.start & 31ull) + (unsigned)lane >= 32u;
     for (long long ch = gwarp; ch < nchunk; ch += twarps) {
         // the chunk's first words: lane 0's block qw holds this lane's index
         // at offset k (carry 0) or the next block does (carry 1); the high
@@ -1504,17 +1503,18 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
             const long long r = n - j0;
             const int nv = r <= 0 ? 0 : (int)min((long long)nt, (r + 31) / 32);
             const bool full = nt == kSub && (t0 + kSub) * 32 <= n;  // (every lane's point of every tile)
-            // the step after tile tt: this lane's block to the next, Gray-code
-            // bit 5 + ctz(q + 1): its word's offset in the row
-            unsigned da[kSub];
-            {
-                unsigned long long q = (A.start + (unsigned long long)j0) >> 5;
+            // the step after tile tt: lane 0's block is qa + tt, this lane's
+            // qa + tt + inB; the odd one of the two steps with word index
+            // kk[tt] = 5 + ctz(odd block + 1), the even one with 5
+            const unsigned long long qa = (A.start + (unsigned long long)(t0 * 32)) >> 5;
+            int kk[kSub];
 #pragma unroll
-                for (int tt = 0; tt < kSub; ++tt) {
-                    da[tt] = sdir_sa + 4u * (unsigned)(5 + min(__ffsll((long long)(q + 1ull)) - 1, CV_SOBOL_BITS - 6));
-                    ++q;
-                }
+            for (int tt = 0; tt < kSub; ++tt) {
+                const unsigned long long b = (qa + (unsigned long long)tt) | 1ull;
+                kk[tt] = 5 + min(__ffsll((long long)(b + 1ull)) - 1, CV_SOBOL_BITS - 6);
             }
+            // this lane's block at tile 0 is odd (then at tile tt iff tt is even)
+            const bool odd0 = ((qa + (inB ? 1ull : 0ull)) & 1ull) != 0ull;
             // one axis at a time: its row of x, kSub tiles of 32 points; the
             // words after the last tile start the next sub-chunk
             if (full) {
@@ -1523,14 +1523,15 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
                     unsigned X = x0s[d * 32];
                     float *px = A.x + d * ld + j0;
                     const unsigned gd = g_hi + (unsigned)d;  // (table base of axis d >> (3 + L))
-                    const unsigned dd = (unsigned)(d * CV_SOBOL_BITS * 4);
+                    const unsigned w5 = Dir<unsigned>::w(P::li, d, 5);
 #pragma unroll
                     for (int tt = 0; tt < kSub; ++tt) {
                         const float f1 = __uint_as_float((X & P::mF) | P::expE);
                         const float2 ew = lds_f2(funnel_r<P::sA>(X, gd));
                         const float z = __fmaf_rn(ew.y, f1, ew.x);
                         px[32 * tt] = z + 0.5f;
-                        X ^= lds_u(da[tt] + dd);
+                        const unsigned wo = Dir<unsigned>::w(P::li, d, kk[tt]);
+                        X ^= (odd0 == ((tt & 1) == 0)) ? wo : w5;
                     }
                     x0s[d * 32] = X;
                 }
@@ -1540,7 +1541,7 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
                     unsigned X = x0s[d * 32];
                     float *px = A.x + d * ld + j0;
                     const unsigned gd = g_hi + (unsigned)d;
-                    const unsigned dd = (unsigned)(d * CV_SOBOL_BITS * 4);
+                    const unsigned w5 = Dir<unsigned>::w(P::li, d, 5);
 #pragma unroll
                     for (int tt = 0; tt < kSub; ++tt) {
                         if (tt < nt) {
@@ -1548,7 +1549,8 @@ k_mat_store(const __grid_constant__ SampleArgs<float> A)
                             const float2 ew = lds_f2(funnel_r<P::sA>(X, gd));
                             const float z = __fmaf_rn(ew.y, f1, ew.x);
                             if (tt < nv) px[32 * tt] = z + 0.5f;
-                            X ^= lds_u(da[tt] + dd);
+                            const unsigned wo = Dir<unsigned>::w(P::li, d, kk[tt]);
+                            X ^= (odd0 == ((tt & 1) == 0)) ? wo : w5;
                         }
                     }
                     x0s[d * 32] = X;
