@@ -243,7 +243,11 @@ int cv_refine(cv_ctx *ctx, int ndim, int nbins, const double *hist_dev,
  * consistent (P((m-1)/2, chi2/2) over m iterations).  An iteration whose
  * result is NaN or infinite stops the run there: the call fills the
  * outputs with *fail = 1 and returns CV_ENONFINITE (cv_result.status bit 0
- * in the integral, batch and server calls). */
+ * in the integral, batch and server calls).  The context keeps the call's
+ * device state (and with it the iterations of a problem met twice in a
+ * row, as a captured CUDA graph, unless cv_kernel_timer is on): a call
+ * with the same arguments replays them, with the same results bit for
+ * bit. */
 int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g,
              double epsrel, double epsabs, int flags, int seed,
              int64_t mineval, int64_t maxeval, int64_t nstart,

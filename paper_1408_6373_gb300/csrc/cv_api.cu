@@ -98,6 +98,9 @@ struct cv_ctx {
     // (no allocation, and no free with its device synchronisation, per call)
     void *vegas_mem = nullptr;
     size_t vegas_cap = 0;
+    // cv_vegas's integral of the last call, kept for a call with the same
+    // problem (its iterations then replayed from a captured graph)
+    struct cv_integral *vegas_last = nullptr;
     // per-block partials of standalone deterministic passes (cv_sample),
     // grown on demand: room for parts_G blocks of the largest problem
     void *parts_mem = nullptr;
@@ -813,7 +816,8 @@ struct cv_integral {
     cudaGraphExec_t exec = nullptr;
     PassParts parts;           // per-block partials of the passes (deterministic sums)
     int launched_kernels = 0;  // kernels in one run (reset + iterations)
-    bool oneshot = false;      // cv_vegas's: run once, kernels enqueued directly, state in ctx->vegas_mem
+    bool oneshot = false;      // cv_vegas's: state in ctx->vegas_mem, kernels enqueued directly ...
+    bool replay = false;       // ... unless the same problem came again: then a captured graph
 };
 
 static int check_spec(cv_ctx *ctx, const cv_spec *sp)
@@ -1057,7 +1061,7 @@ extern "C" int cv_integral_run(cv_integral *I)
         return CV_OK;
     }
     const bool fixed = I->spec.epsrel == 0.0 && I->spec.epsabs == 0.0;
-    if (I->oneshot) {
+    if (I->oneshot && !I->replay) {
         // a single run: capturing and instantiating a graph would cost more
         // than the launches it saves, so the iterations are enqueued directly
         // (32 at a time, the device's stop decision read in between unless
@@ -1397,9 +1401,25 @@ extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, doub
     sp.nincrease = nincrease;
     sp.nbatch = nbatch;
     sp.seed = (uint64_t)(int64_t)seed;
-    cv_integral *I = nullptr;
-    int rc = integral_create(ctx, &sp, &I, true);
-    if (rc) return rc;
+    // The same problem as the previous call (every field of the spec): its
+    // integral again, its iterations from the second repeat on replayed from
+    // a graph captured once (the kernel timer needs direct launches).  Any
+    // other problem: a fresh one-shot integral with enqueued launches.
+    cv_integral *I = ctx->vegas_last;
+    int rc = CV_OK;
+    if (I && ctx->integrals.count(I) && memcmp(&I->spec, &sp, sizeof(sp)) == 0) {
+        I->replay = !ctx->timer_on;
+    } else {
+        if (I && ctx->integrals.erase(I)) {
+            CV_CUDA(ctx, cudaSetDevice(ctx->device));
+            cudaStreamSynchronize(ctx->stream);
+            integral_free(I);
+        }
+        ctx->vegas_last = nullptr;
+        rc = integral_create(ctx, &sp, &I, true);
+        if (rc) return rc;
+        ctx->vegas_last = I;
+    }
     cv_result res;
     rc = cv_integral_reset(I);
     if (!rc) rc = cv_integral_run(I);
@@ -1412,7 +1432,6 @@ extern "C" int cv_vegas(cv_ctx *ctx, int ndim, int ncomp, const cv_genz *g, doub
                     fprintf(stderr, "cv_vegas iteration %d comp %d: %.15g +- %.6g\n", j + 1, c,
                             lI[(size_t)j * ncomp + c], std::sqrt(std::fabs(lV[(size_t)j * ncomp + c])));
     }
-    cv_integral_destroy(I);
     if (rc) return rc;
     *neval = res.neval;
     *fail = res.fail;

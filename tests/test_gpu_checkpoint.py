@@ -100,6 +100,34 @@ def test_two_runs_agree_bit_for_bit(ctx, flags):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("flags", [0, cg.JIT, cg.FP64])
+def test_repeated_vegas_calls_give_the_same_bits(ctx, flags):
+    # cv_vegas keeps the last call's integral: a repeat of the same problem
+    # replays its iterations from a captured graph (the second call captures,
+    # later calls replay), another problem in between starts afresh, and the
+    # kernel timer forces direct launches: every path gives the same bits
+    sp = _spec(flags, maxeval=6 * 6000)
+    other = _spec(flags, maxeval=3 * 6000)
+    kw = dict(flags=flags, maxeval=sp.maxeval, nstart=sp.nstart, nincrease=sp.nincrease, nbins=sp.nbins)
+
+    def bits(r):
+        return [np.float64(v).view(np.uint64) for key in ("integral", "error", "prob") for v in getattr(r, key)]
+
+    first = ctx.vegas(sp.g, **kw)
+    runs = [ctx.vegas(sp.g, **kw) for _ in range(3)]
+    o = ctx.vegas(other.g, flags=flags, maxeval=other.maxeval, nstart=other.nstart,
+                  nincrease=other.nincrease, nbins=other.nbins)
+    assert o.fail == 1 and 0 < o.neval <= other.maxeval
+    runs.append(ctx.vegas(sp.g, **kw))
+    ctx.kernel_timer(True)
+    runs.append(ctx.vegas(sp.g, **kw))
+    ctx.kernel_timer(False)
+    runs.append(ctx.vegas(sp.g, **kw))
+    for r in runs:
+        assert (r.neval, r.fail) == (first.neval, first.fail)
+        assert bits(r) == bits(first)
+
+
 def test_state_of_another_problem_is_refused(ctx, tmp_path):
     a = ctx.integral(_spec(cg.FP64))
     a.reset()
