@@ -480,14 +480,18 @@ def legs_summary(line: dict) -> dict:
     def g(v, nd=4):
         return float(f"{v:.{nd}g}") if isinstance(v, (int, float)) and v is not None else v
     acc = line.get("accuracy", {})
+    iss = line["roofline"].get("issue") or {}
     out = {"headline": {"Gsps": g(line["value"] / 1e9), "e2e_Gsps": g(line["e2e"]["value"] / 1e9),
-                        "frac": g(line["roofline"]["frac"], 3), "kernel_us": g(1e3 * line["roofline"]["kernel_ms"]),
+                        "frac": g(line["roofline"]["frac"], 3), "issue_frac": g(iss.get("frac"), 3),
+                        "kernel_us": g(1e3 * line["roofline"]["kernel_ms"]),
                         "z": [g(z, 2) for z in acc.get("headline", {}).get("z", [])]},
            "plain_fp64": {"Gsps": g(line["plain_fp64"]["value"] / 1e9),
                           "z": [g(z, 2) for z in acc.get("plain_fp64", {}).get("z", [])]}}
     if "batch4096" in line:
         b, a = line["batch4096"], acc.get("batch4096", {})
+        bi = b["roofline"].get("issue") or {}
         out["batch4096"] = {"Gsps": g(b["value"] / 1e9), "frac": g(b["roofline"]["frac"], 3),
+                            "issue_frac": g(bi.get("frac"), 3),
                             "plain_fp64_Gsps": g(b["plain_fp64_subset"]["value"] / 1e9),
                             "z_max": g(a.get("z_max"), 3), "within_3": g(a.get("within_3"), 4),
                             "oracle_dz": g(a.get("oracle_subset", {}).get("max_diff_in_sigma"), 2)}
@@ -818,12 +822,23 @@ def measure_batch(ctx, cg, W, warmup: int, steps: int, subset: int = 32) -> dict
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     flops = sum(p.maxeval * alg_flops_per_sample(p.ndim, p.families) for p in probs)
     achieved = flops / (ms / 1e3) / 1e12
-    peak = fp32_peak_tflops(sm_max, sm_count(torch.cuda.current_device()))
+    sms = sm_count(torch.cuda.current_device())
+    peak = fp32_peak_tflops(sm_max, sms)
+    # the issue bound, from the committed count of one run's warp instructions
+    # (ncu, every class launch) when it was taken on the current sources
+    inst = _profile_value("k_batch_sample_batch4096.md", "warp_instructions_per_run")
+    issue = None
+    if inst:
+        issue_peak = sms * 4 * sm_max * 1e6 / 1e9
+        issue = {"warp_instructions_per_run": inst, "achieved": inst / (ms / 1e3) / 1e9, "peak": issue_peak,
+                 "unit": "G warp instructions/s", "frac": inst / (ms / 1e3) / 1e9 / issue_peak,
+                 "flop_frac_at_full_issue": flops / (inst / (issue_peak * 1e9)) / 1e12 / peak,
+                 "peak_basis": f"{sms} SMs x 4 schedulers x 1 instruction per cycle x {sm_max:.0f} MHz"}
     return {"workload": "batch4096: 4096 integrals, ndim U{2..16}, family U{0..5}, n/iter "
                         "log-uniform 1e4..1e7, 10 iterations, 64 bins, FP32 eval / FP64 reduce",
             "value": samples / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": None, "issue": issue,
                          "basis": "algorithmic FP32 FLOPs of every integral's samples over the device time "
                                   "of the whole batched run (sampling, refinement and combination)"},
             "_results": [(r.integral[0], r.error[0]) for r in res], "_problems": probs,
