@@ -1235,10 +1235,11 @@ __device__ __forceinline__ void batch_steps(const SampleArgs<float> &A, const Sm
 // counter, stages the tile's integral (grid and parameters) when it differs
 // from the last one, and splits the tile's 32-point blocks over its warps.
 // Every warp accumulates its own copy of the f^2 histogram, and after each
-// tile the copies are summed in warp order and added to the integral's FP64
-// histogram: the FP32 sums of a tile never depend on which CTA ran it or on
-// what else was in the queue, so an integral gives the same result alone
-// and in any mix (up to the order of FP64 additions).
+// tile the copies are summed in warp order and written as the tile's
+// partial row (or, without partial rows, added to the integral's FP64
+// histogram): the sums of a tile never depend on which CTA ran it or on
+// what else was in the queue, and the rows are added in tile order, so an
+// integral gives the same result alone and in any mix, bit for bit.
 template <int NDIM, bool POW2>
 __global__ void __launch_bounds__(kBlock, (kMinBlocks<NDIM, float>))
 k_batch_sample(const BatchSampleArgs B)
