@@ -8,7 +8,9 @@ produced for the second.
 72 integrals cover 2..32 dimensions (both sides of the 16/17 kernel
 boundary), all six Genz families, 50, 64, 128 and 256 bins (256 up to 22
 dimensions, the batched path's shared-memory limit), and iterations of up
-to a million points, so that tiles reach the largest size.  The FP32
+to a million points, so that tiles reach the largest size; 24 more have
+2..4 components of mixed families (the served requests' form) and half of
+them digitally shifted Sobol points.  The FP32
 tolerances are those of tests/tolerances.py (1e-6 of sum |J f| plus the
 boundary mass for I, the implied variance bound)."""
 import os
@@ -142,5 +144,46 @@ def test_autotuned_tiles_and_alone_runs_match_oracle(ctx, runs):
         A.run()
         aI, aV = A.log(0, 2)
         A.close()
-        np.testing.assert_allclose(aI, logs[i][0], rtol=1e-12, atol=1e-300)
-        np.testing.assert_allclose(aV, logs[i][1], rtol=1e-9, atol=1e-300)
+        # (power-of-two bins: warp-private histograms, and the tiles' partial
+        # rows added in tile order: the same bits)
+        np.testing.assert_array_equal(aI, logs[i][0])
+        np.testing.assert_array_equal(aV, logs[i][1])
+
+
+# Multi-component integrals (the general policy of the batched kernel, as
+# the server runs them) and digitally shifted Sobol points, against the
+# oracle's first pass on the uniform grid: 2..4 components of mixed
+# families, 2..32 dimensions, 50, 64 and 128 bins.
+def _multi_items():
+    rng = np.random.default_rng(77)
+    out = []
+    for i in range(24):
+        ndim = 2 + (7 * i) % 31
+        ncomp = 2 + i % 3
+        fams = [int(f) for f in rng.integers(0, 6, ncomp)]
+        nbins = (64, 50, 128)[i % 3]
+        n = int(np.exp(rng.uniform(np.log(5000), np.log(200000))))
+        a = 0.5 + rng.random((ncomp, ndim))
+        u = rng.random((ncomp, ndim))
+        for c in range(ncomp):
+            if fams[c] == O.CORNER_PEAK:
+                a[c] = W.fp32_corner_peak(a[c])
+        seed = 0 if i % 2 == 0 else 100 + i
+        out.append((ndim, fams, nbins, n, a, u, seed))
+    return out
+
+
+def test_batched_multicomponent_and_scrambled_first_iteration_match_oracle(ctx):
+    items = _multi_items()
+    specs = [cg.spec(cg.genz(nd, fams, a, u), nbins=N, maxeval=n, nstart=n,
+                     flags=cg.SCRAMBLE if seed else 0, seed=seed)
+             for nd, fams, N, n, a, u, seed in items]
+    B = ctx.batch(specs)
+    B.run()
+    logs = [B.log(i, 1) for i in range(len(items))]
+    B.close()
+    for i, (nd, fams, N, n, a, u, seed) in enumerate(items):
+        p = O.Problem(nd, fams, a, u, nbins=N, bits=23, gen=O.SCRAMBLED if seed else O.SOBOL, seed=seed)
+        ob = O.sample_bounds(p, O.grid_uniform(nd, N), 1, n, nthreads=THREADS)
+        lI, lV = logs[i]
+        check_fp32_iteration(lI[0], lV[0], ob, n, what=(i, nd, fams, N, n, seed))
