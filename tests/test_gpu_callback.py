@@ -88,6 +88,25 @@ def test_materialised_fp32_pass_matches_oracle(ctx, nvec, nbins, gen, jit):
     check_fp32_iteration(r.integral, r.error ** 2, ob, n, what=(nvec, nbins, gen))
 
 
+# The point-major layout in FP32 (the paper's x[j*ndim + d]; the general
+# materialised passes and the library's general integrand), one iteration
+# against the oracle's pass as above.
+@pytest.mark.parametrize("nbins", [64, 50])
+def test_materialised_fp32_point_major_pass_matches_oracle(ctx, nbins):
+    ndim, fams = 7, [O.PRODUCT_PEAK, O.GAUSSIAN, O.C0]
+    rng = np.random.default_rng(41 + nbins)
+    a = rng.uniform(0.5, 1.5, (3, ndim))
+    u = rng.uniform(0.1, 0.9, (3, ndim))
+    n = 70001
+    g = cg.genz(ndim, fams, a, u)
+    r = ctx.vegas_cb(cg.builtin_integrand(), ndim, 3, userdata=cg.GenzCallbackData(g, cg.AOS), nvec=4099,
+                     flags=cg.AOS, maxeval=n, nstart=n, nbins=nbins)
+    assert (r.neval, r.fail) == (n, 1)
+    p = O.Problem(ndim, fams, a, u, nbins=nbins, bits=23)
+    ob = O.sample_bounds(p, O.grid_uniform(ndim, nbins), 1, n, nthreads=os.cpu_count() or 1)
+    check_fp32_iteration(r.integral, r.error ** 2, ob, n, what=("aos", nbins))
+
+
 def test_tiles_do_not_change_results(ctx):
     g, _, _ = _genz(seed=5)
     ud = cg.GenzCallbackData(g, cg.FP64)

@@ -100,15 +100,19 @@ def test_two_runs_agree_bit_for_bit(ctx, flags):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("epsrel", [0.0, 2e-3], ids=["fixed", "goal"])
 @pytest.mark.parametrize("flags", [0, cg.JIT, cg.FP64])
-def test_repeated_vegas_calls_give_the_same_bits(ctx, flags):
+def test_repeated_vegas_calls_give_the_same_bits(ctx, flags, epsrel):
     # cv_vegas keeps the last call's integral: a repeat of the same problem
     # replays its iterations from a captured graph (the second call captures,
     # later calls replay), another problem in between starts afresh, and the
     # kernel timer forces direct launches: every path gives the same bits
-    sp = _spec(flags, maxeval=6 * 6000)
+    # (80 iterations: the graph holds 32, so a run is three replays, and with
+    # an accuracy goal the device's stop is polled between them)
+    sp = cg.spec(_spec(flags).g, nbins=64, flags=flags, maxeval=80 * 2000, nstart=2000)
     other = _spec(flags, maxeval=3 * 6000)
-    kw = dict(flags=flags, maxeval=sp.maxeval, nstart=sp.nstart, nincrease=sp.nincrease, nbins=sp.nbins)
+    kw = dict(flags=flags, maxeval=sp.maxeval, nstart=sp.nstart, nincrease=sp.nincrease, nbins=sp.nbins,
+              epsrel=epsrel)
 
     def bits(r):
         return [np.float64(v).view(np.uint64) for key in ("integral", "error", "prob") for v in getattr(r, key)]
@@ -123,6 +127,8 @@ def test_repeated_vegas_calls_give_the_same_bits(ctx, flags):
     runs.append(ctx.vegas(sp.g, **kw))
     ctx.kernel_timer(False)
     runs.append(ctx.vegas(sp.g, **kw))
+    if epsrel:
+        assert first.neval <= sp.maxeval and (first.fail == 0) == (first.neval < sp.maxeval)
     for r in runs:
         assert (r.neval, r.fail) == (first.neval, first.fail)
         assert bits(r) == bits(first)
