@@ -153,6 +153,15 @@ __device__ __forceinline__ void sum_rows(const T *P, int G, size_t nh, int N,
     };
     const T *p = P + (size_t)q * V;
     int b = r;
+    // (eight rows in flight, then four: the loads' latency, not their
+    // bandwidth, bounds this loop)
+    for (; b + 7 * R < G; b += 8 * R) {
+        T v[8][V];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) load_vec<T, V>(p + (size_t)(b + i * R) * nh, v[i]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) add(v[i]);
+    }
     for (; b + 3 * R < G; b += 4 * R) {
         T v0[V], v1[V], v2[V], v3[V];
         load_vec<T, V>(p + (size_t)b * nh, v0);
