@@ -138,6 +138,31 @@ def test_materialised_runs_agree_bit_for_bit(ctx, flags, nbins, nvec):
                                   np.asarray(getattr(r[0], key)).view(np.uint64)), (key, flags, nbins, nvec)
 
 
+# Tiles far smaller than a warp's 32 points (1, 7 and 31 points per call):
+# every tile's accumulate pass takes the edge path, adds its own partial
+# rows, and the iteration still equals the oracle's pass.
+@pytest.mark.parametrize("flags,nbins", [(0, 64), (cg.FP64, 32), (0, 50)], ids=["f32-64", "f64-32", "f32-50"])
+@pytest.mark.parametrize("nvec", [1, 7, 31])
+def test_tiny_tiles_match_oracle(ctx, flags, nbins, nvec):
+    ndim, fams = 3, [O.GAUSSIAN, O.C0]
+    rng = np.random.default_rng(5 + nvec)
+    a = rng.uniform(0.5, 1.5, (2, ndim))
+    u = rng.uniform(0.1, 0.9, (2, ndim))
+    n = 403
+    g = cg.genz(ndim, fams, a, u)
+    r = ctx.vegas_cb(cg.builtin_integrand(), ndim, 2, userdata=cg.GenzCallbackData(g, flags & cg.FP64),
+                     nvec=nvec, flags=flags, maxeval=n, nstart=n, nbins=nbins)
+    assert (r.neval, r.fail) == (n, 1)
+    if flags & cg.FP64:
+        o = O.vegas(O.Problem(ndim, fams, a, u, nbins=nbins), maxeval=n, nstart=n)
+        np.testing.assert_allclose(r.integral, o.integral, rtol=1e-12)
+        np.testing.assert_allclose(r.error, o.error, rtol=1e-10)
+    else:
+        p = O.Problem(ndim, fams, a, u, nbins=nbins, bits=23)
+        ob = O.sample_bounds(p, O.grid_uniform(ndim, nbins), 1, n, nthreads=1)
+        check_fp32_iteration(r.integral, r.error ** 2, ob, n, what=("tiny", nvec, nbins))
+
+
 def test_torch_integrand_and_nvec_contract(ctx):
     # a user integrand written with torch on the device buffers
     ndim = 4
