@@ -1420,8 +1420,17 @@ __device__ __forceinline__ void mat_table(const SampleArgs<float> &A, Smem<float
     }
 }
 
-// Trailing zero bits of a nonzero constant.
-__host__ __device__ constexpr int ctz_const(unsigned v) { return (v & 1u) ? 0 : 1 + ctz_const(v >> 1); }
+// Trailing zero bits of a nonzero constant (a loop, not a recursion, so
+// that a call with an unrolled loop's counter is inlined and folded).
+__host__ __device__ constexpr int ctz_const(unsigned v)
+{
+    int c = 0;
+    while (!(v & 1u)) {
+        v >>= 1;
+        ++c;
+    }
+    return c;
+}
 
 // The bit-level map's constants for N = 2^L as compile-time values (the
 // same formulas as the host's make_map).
@@ -1622,6 +1631,22 @@ __device__ __forceinline__ void mat_fold(Partial<float> &Pt, int ncomp, Acc<floa
     Pt.zero();
 }
 
+// Trailing zero bits of v != 0, as a call (a boundary the compiler does not
+// schedule across).
+static __device__ __noinline__ int ctz_call(unsigned v) { return __ffs((int)v) - 1; }
+
+// The Gray-code word of the step out of block kk (< kMatGroup - 1) of a
+// group: 5 + ctz(kk + 1).  Up to 16 dimensions a compile-time constant (the
+// words are constant-bank operands); beyond, from a call, so that the
+// compiler does not interleave the group's blocks and keep every axis's
+// words in registers (measured: 24 to 32 dimensions spill more without it).
+template <int NDIM>
+__device__ __forceinline__ int group_step_word(int kk)
+{
+    if constexpr (NDIM <= 16) return 5 + ctz_const((unsigned)(kk + 1));
+    else return 5 + ctz_call((unsigned)(kk + 1));
+}
+
 // One chunk of the accumulate pass: blocks q0 .. q0 + nk - 1 (q0 a multiple
 // of kMatGroup).  EDGE = false: every lane's point of every block is in
 // [start, start + n) and nk is a multiple of kMatGroup; EDGE = true: any
@@ -1678,8 +1703,11 @@ __device__ __forceinline__ void mat_accum_chunk(const SampleArgs<float> &A, cons
                 mat_accum_block<NDIM, L>(sm, X, ring + kk * kStage, ncomp, 1.0f, Pt);
                 if (kk + 1 < kMatGroup) {
 #pragma unroll
-                    for (int d = 0; d < NDIM; ++d)
-                        X[d] ^= Dir<unsigned>::w(P::li, d, 5 + ctz_const((unsigned)(kk + 1)));
+                    {
+                        const int k = group_step_word<NDIM>(kk);
+#pragma unroll
+                        for (int d = 0; d < NDIM; ++d) X[d] ^= Dir<unsigned>::w(P::li, d, k);
+                    }
                 } else if (more) {
                     sobol_step<NDIM, unsigned>(X, q0 + (unsigned long long)(k0 + kk), P::li);
                 }

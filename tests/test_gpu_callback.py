@@ -88,6 +88,24 @@ def test_materialised_fp32_pass_matches_oracle(ctx, nvec, nbins, gen, jit):
     check_fp32_iteration(r.integral, r.error ** 2, ob, n, what=(nvec, nbins, gen))
 
 
+# The dimension-major FP32 kernels above 16 dimensions (their group steps
+# take a run-time word), one iteration against the oracle's pass.
+@pytest.mark.parametrize("ndim", [17, 24, 30])
+def test_materialised_fp32_high_dimensions_match_oracle(ctx, ndim):
+    fams = [O.GAUSSIAN, O.C0]
+    rng = np.random.default_rng(ndim)
+    a = rng.uniform(0.2, 0.6, (2, ndim))
+    u = rng.uniform(0.1, 0.9, (2, ndim))
+    n = 150001
+    g = cg.genz(ndim, fams, a, u)
+    r = ctx.vegas_cb(cg.builtin_integrand(), ndim, 2, userdata=cg.GenzCallbackData(g, cg.JIT), nvec=40000,
+                     flags=0, maxeval=n, nstart=n, nbins=64)
+    assert (r.neval, r.fail) == (n, 1)
+    p = O.Problem(ndim, fams, a, u, nbins=64, bits=23)
+    ob = O.sample_bounds(p, O.grid_uniform(ndim, 64), 1, n, nthreads=os.cpu_count() or 1)
+    check_fp32_iteration(r.integral, r.error ** 2, ob, n, what=("highdim", ndim))
+
+
 # The point-major layout in FP32 (the paper's x[j*ndim + d]; the general
 # materialised passes and the library's general integrand), one iteration
 # against the oracle's pass as above.
